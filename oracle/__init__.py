@@ -1,0 +1,410 @@
+"""FP64 CPU oracle of the anchor-decoded Gaussian render path (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports, links or calls it.
+
+The arithmetic lives in ``ups_oracle.c`` (plain C, double precision, one view
+per call); this module marshals numpy arrays through ctypes and composes the
+per-view steps into the full loss and its gradients:
+
+  decode (Eq. 8-9) -> project (Eq. 1-2) -> blend (Eq. 3, Eq. 10)
+  -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ups_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libups_oracle.so")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (OpenMP when available)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:2] + ["-fopenmp"] + base[2:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_tile_lists.restype = C.c_long
+        _lib.orc_loss_view.restype = C.c_double
+        _lib.orc_num_threads.restype = C.c_int
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+class _Cam(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double), ("width", C.c_int), ("height", C.c_int),
+                ("Tcw", C.c_double * 16)]
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("alpha_min", C.c_double), ("alpha_max", C.c_double),
+                ("t_min", C.c_double), ("dilation", C.c_double),
+                ("near_z", C.c_double), ("guard", C.c_double),
+                ("tile", C.c_int), ("brute", C.c_int)]
+
+
+@dataclass
+class RenderCfg:
+    """Thresholds of the blending (readings of what Eq. 3 leaves open)."""
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    dilation: float = 0.3
+    near_z: float = 0.2
+    guard: float = 1.3
+    tile: int = 16
+    brute: bool = False
+
+    def c(self):
+        return _Cfg(self.alpha_min, self.alpha_max, self.t_min, self.dilation,
+                    self.near_z, self.guard, self.tile, int(self.brute))
+
+
+@dataclass
+class LossCfg:
+    """Image-loss weights (Eq. 4 / Eq. 14 with the per-pixel weight map)."""
+    lambda_color: float = 1.0
+    lambda_depth: float = 1.0
+    lambda_feat: float = 1.0
+    lambda_scale: float = 0.0
+    l2: bool = False
+
+
+def _cam(cam):
+    T = np.ascontiguousarray(np.asarray(cam.T_cw, dtype=np.float64).reshape(16))
+    return _Cam(float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                int(cam.width), int(cam.height), (C.c_double * 16)(*T))
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+def _zeros(*shape):
+    a = np.zeros(shape, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+# ----------------------------------------------------------------------------
+# per-view steps
+# ----------------------------------------------------------------------------
+
+def decode(anc, mlp, cam, k, n_feat):
+    """Eq. 8-9 for one view: returns mean, opacity, scale, quat, color, feat."""
+    A, F = anc["feat"].shape
+    H = mlp["w2"].shape[1]
+    keep = []
+    args = []
+    for name in ("pos", "feat", "offsets", "scaling"):
+        a, p = _d(anc[name]); keep.append(a); args.append(p)
+    for name in ("w1", "b1", "w2", "b2"):
+        a, p = _d(mlp[name]); keep.append(a); args.append(p)
+    N = A * k
+    mean, pm = _zeros(N, 3)
+    op, po = _zeros(N)
+    sc, ps = _zeros(N, 3)
+    qt, pq = _zeros(N, 4)
+    co, pc = _zeros(N, 3)
+    fe, pf = _zeros(N, n_feat)
+    c = _cam(cam)
+    lib().orc_decode_view(A, k, F, H, n_feat, *args, C.byref(c), C.c_double(cam.t_norm),
+                          pm, po, ps, pq, pc, pf)
+    return dict(mean=mean, opacity=op, scale=sc, quat=qt, color=co, feat=fe)
+
+
+def project(g, cam, cfg: RenderCfg):
+    """Eq. 1-2 for one view."""
+    N = g["mean"].shape[0]
+    keep = []
+    args = []
+    for name in ("mean", "opacity", "scale", "quat"):
+        a, p = _d(g[name]); keep.append(a); args.append(p)
+    valid = np.zeros(N, np.int32)
+    rect = np.zeros((N, 4), np.int32)
+    pcam, pp = _zeros(N, 3)
+    uv, pu = _zeros(N, 2)
+    cov, pcv = _zeros(N, 3)
+    conic, pcn = _zeros(N, 3)
+    ext, pe = _zeros(N, 4)
+    c = _cam(cam)
+    cf = cfg.c()
+    lib().orc_project_view(N, *args, C.byref(c), C.byref(cf), valid.ctypes.data_as(_ip),
+                           pp, pu, pcv, pcn, rect.ctypes.data_as(_ip), pe)
+    return dict(valid=valid, pcam=pcam, uv=uv, cov2d=cov, conic=conic, rect=rect,
+                extent=ext)
+
+
+def tile_lists(proj, cam, cfg: RenderCfg):
+    """Per-tile Gaussian lists in ascending (float32(z), id) and their ranges."""
+    N = proj["valid"].shape[0]
+    tx = (cam.width + cfg.tile - 1) // cfg.tile
+    ty = (cam.height + cfg.tile - 1) // cfg.tile
+    va, pv = _i(proj["valid"])
+    pc, ppc = _d(proj["pcam"])
+    rc, prc = _i(proj["rect"])
+    total = lib().orc_tile_lists(N, pv, ppc, prc, tx, ty, None, None)
+    lst = np.zeros(max(total, 1), np.int32)
+    rng = np.zeros((tx * ty, 2), np.int32)
+    lib().orc_tile_lists(N, pv, ppc, prc, tx, ty, lst.ctypes.data_as(_ip),
+                         rng.ctypes.data_as(_ip))
+    return lst[:total], rng
+
+
+def render(proj, g, cam, cfg: RenderCfg, n_feat):
+    """Eq. 3 / Eq. 10 for one view: colour, depth, feature, T_final, n_contrib."""
+    N = proj["valid"].shape[0]
+    H, W = cam.height, cam.width
+    keep = []
+    va, pv = _i(proj["valid"]); keep.append(va)
+    rc, prc = _i(proj["rect"]); keep.append(rc)
+    ptr = {}
+    for name, src in (("pcam", proj), ("uv", proj), ("conic", proj),
+                      ("opacity", g), ("color", g)):
+        a, p = _d(src[name]); keep.append(a); ptr[name] = p
+    fe, pf = _d(g["feat"] if n_feat else np.zeros((N, 0)))
+    col, pcol = _zeros(3, H, W)
+    dep, pdep = _zeros(H, W)
+    fo, pfo = _zeros(n_feat, H, W)
+    T, pT = _zeros(H, W)
+    nc = np.zeros((H, W), np.int32)
+    mg, pmg = _zeros(H, W)
+    c = _cam(cam)
+    cf = cfg.c()
+    lib().orc_render_view(N, n_feat, pv, ptr["pcam"], ptr["uv"], ptr["conic"],
+                          ptr["opacity"], ptr["color"], pf, prc, C.byref(c), C.byref(cf),
+                          pcol, pdep, pfo, pT, nc.ctypes.data_as(_ip), pmg)
+    return dict(color=col, depth=dep, feat=fo, T=T, n_contrib=nc, margin=mg)
+
+
+def loss_view(img, tgt, lcfg: LossCfg, n_feat, norm):
+    """Weighted image loss of one view and its image gradients."""
+    H, W = img["depth"].shape
+    keep = []
+    ptr = []
+    for a in (img["color"], img["depth"], img["feat"] if n_feat else np.zeros(1),
+              tgt["color"], tgt["depth"], tgt["feat"] if n_feat else np.zeros(1),
+              tgt["weight"]):
+        arr, p = _d(a); keep.append(arr); ptr.append(p)
+    gc, pgc = _zeros(3, H, W)
+    gd, pgd = _zeros(H, W)
+    gf, pgf = _zeros(n_feat, H, W)
+    L = lib().orc_loss_view(W, H, n_feat, *ptr, C.c_double(lcfg.lambda_color),
+                            C.c_double(lcfg.lambda_depth), C.c_double(lcfg.lambda_feat),
+                            int(lcfg.l2), C.c_double(norm), pgc, pgd,
+                            pgf if n_feat else None)
+    return L, dict(color=gc, depth=gd, feat=gf)
+
+
+def render_bwd(proj, g, cam, cfg: RenderCfg, n_feat, grads_img):
+    """Backward of Eq. 3 / Eq. 10: per-Gaussian 2D gradients of one view."""
+    N = proj["valid"].shape[0]
+    keep = []
+    va, pv = _i(proj["valid"]); keep.append(va)
+    rc, prc = _i(proj["rect"]); keep.append(rc)
+    ptr = {}
+    for name, src in (("pcam", proj), ("uv", proj), ("conic", proj),
+                      ("opacity", g), ("color", g)):
+        a, p = _d(src[name]); keep.append(a); ptr[name] = p
+    fe, pf = _d(g["feat"] if n_feat else np.zeros((N, 0)))
+    gi = []
+    for name in ("color", "depth", "feat", "T"):
+        v = grads_img.get(name)
+        if v is None or (name == "feat" and not n_feat):
+            gi.append(None)
+        else:
+            a, p = _d(v); keep.append(a); gi.append(p)
+    g_uv, p1 = _zeros(N, 2)
+    g_cn, p2 = _zeros(N, 3)
+    g_op, p3 = _zeros(N)
+    g_co, p4 = _zeros(N, 3)
+    g_z, p5 = _zeros(N)
+    g_fe, p6 = _zeros(N, max(n_feat, 0))
+    c = _cam(cam)
+    cf = cfg.c()
+    lib().orc_render_bwd_view(N, n_feat, pv, ptr["pcam"], ptr["uv"], ptr["conic"],
+                              ptr["opacity"], ptr["color"], pf, prc, C.byref(c), C.byref(cf),
+                              *gi, p1, p2, p3, p4, p5, p6)
+    return dict(uv=g_uv, conic=g_cn, opacity=g_op, color=g_co, z=g_z, feat=g_fe)
+
+
+def project_bwd(g, proj, cam, cfg: RenderCfg, g2d, scale_reg=0.0):
+    """Backward of Eq. 1-2: gradients of mean, scale, quaternion and pose."""
+    N = g["mean"].shape[0]
+    keep = []
+    args = []
+    for name in ("mean", "scale", "quat"):
+        a, p = _d(g[name]); keep.append(a); args.append(p)
+    va, pv = _i(proj["valid"]); keep.append(va)
+    gp = []
+    for name in ("uv", "conic", "z"):
+        a, p = _d(g2d[name]); keep.append(a); gp.append(p)
+    gm, p1 = _zeros(N, 3)
+    gs, p2 = _zeros(N, 3)
+    gq, p3 = _zeros(N, 4)
+    pose, p4 = _zeros(6)
+    c = _cam(cam)
+    cf = cfg.c()
+    lib().orc_project_bwd_view(N, *args, pv, C.byref(c), C.byref(cf), *gp,
+                               C.c_double(scale_reg), p1, p2, p3, p4)
+    return dict(mean=gm, scale=gs, quat=gq, pose=pose)
+
+
+def decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc):
+    """Backward of Eq. 8-9 for one view; accumulates into `acc`, returns pose[6]."""
+    A, F = anc["feat"].shape
+    H = mlp["w2"].shape[1]
+    keep = []
+    args = []
+    for name in ("pos", "feat", "offsets", "scaling"):
+        a, p = _d(anc[name]); keep.append(a); args.append(p)
+    for name in ("w1", "b1", "w2", "b2"):
+        a, p = _d(mlp[name]); keep.append(a); args.append(p)
+    gin = []
+    for name in ("mean", "opacity", "scale", "quat", "color", "feat"):
+        a, p = _d(g3d[name]); keep.append(a); gin.append(p)
+    outs = []
+    for name in ("w1", "b1", "w2", "b2", "pos", "feat", "offsets", "scaling"):
+        arr = acc[name]
+        assert arr.dtype == np.float64 and arr.flags.c_contiguous
+        outs.append(arr.ctypes.data_as(_dp))
+    pose, pp = _zeros(6)
+    c = _cam(cam)
+    lib().orc_decode_bwd_view(A, k, F, H, n_feat, *args, C.byref(c), C.c_double(cam.t_norm),
+                              *gin, *outs, pp)
+    return pose
+
+
+# ----------------------------------------------------------------------------
+# composed loss and gradients
+# ----------------------------------------------------------------------------
+
+def _norm(cams):
+    return float(sum(c.width * c.height for c in cams))
+
+
+def _scale_count(n_views_data, n):
+    return 3.0 * n_views_data * n
+
+
+def forward_plain(g, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, n_feat, keep=False):
+    """Loss of Gaussians given directly (shared by all views)."""
+    norm = _norm(cams)
+    L = 0.0
+    views = []
+    for cam, tgt in zip(cams, tgts):
+        pr = project(g, cam, cfg)
+        img = render(pr, g, cam, cfg, n_feat)
+        Lv, gimg = loss_view(img, tgt, lcfg, n_feat, norm)
+        L += Lv
+        views.append(dict(proj=pr, img=img, gimg=gimg))
+    if lcfg.lambda_scale:
+        L += lcfg.lambda_scale * float(np.mean(g["scale"]))
+    return (L, views) if keep else L
+
+
+def backward_plain(g, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, n_feat):
+    """Loss and analytic gradients for shared Gaussians + per-view pose."""
+    L, views = forward_plain(g, cams, tgts, cfg, lcfg, n_feat, keep=True)
+    N = g["mean"].shape[0]
+    out = dict(mean=np.zeros((N, 3)), scale=np.zeros((N, 3)), quat=np.zeros((N, 4)),
+               opacity=np.zeros(N), color=np.zeros((N, 3)), feat=np.zeros((N, n_feat)),
+               pose=np.zeros((len(cams), 6)))
+    reg = lcfg.lambda_scale / _scale_count(1, N) if lcfg.lambda_scale else 0.0
+    per_view = []
+    for v, (cam, vw) in enumerate(zip(cams, views)):
+        g2 = render_bwd(vw["proj"], g, cam, cfg, n_feat, vw["gimg"])
+        g3 = project_bwd(g, vw["proj"], cam, cfg, g2, reg if v == 0 else 0.0)
+        for k in ("mean", "scale", "quat"):
+            out[k] += g3[k]
+        out["opacity"] += g2["opacity"]
+        out["color"] += g2["color"]
+        out["feat"] += g2["feat"]
+        out["pose"][v] = g3["pose"]
+        per_view.append(dict(g2d=g2, g3d=g3))
+    return L, out, views, per_view
+
+
+def forward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_feat,
+                   keep=False):
+    """Loss of anchor-decoded Gaussians (decode per view, then render)."""
+    norm = _norm(cams)
+    L = 0.0
+    views = []
+    ssum = 0.0
+    for cam, tgt in zip(cams, tgts):
+        g = decode(anc, mlp, cam, k, n_feat)
+        pr = project(g, cam, cfg)
+        img = render(pr, g, cam, cfg, n_feat)
+        Lv, gimg = loss_view(img, tgt, lcfg, n_feat, norm)
+        L += Lv
+        ssum += float(np.sum(g["scale"]))
+        views.append(dict(g=g, proj=pr, img=img, gimg=gimg))
+    if lcfg.lambda_scale:
+        N = anc["pos"].shape[0] * k
+        L += lcfg.lambda_scale * ssum / _scale_count(len(cams), N)
+    return (L, views) if keep else L
+
+
+def backward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_feat):
+    """Loss and analytic gradients of MLP weights, anchors and per-view pose."""
+    L, views = forward_anchor(anc, mlp, cams, tgts, cfg, lcfg, k, n_feat, keep=True)
+    A = anc["pos"].shape[0]
+    N = A * k
+    acc = dict(w1=np.zeros_like(mlp["w1"]), b1=np.zeros_like(mlp["b1"]),
+               w2=np.zeros_like(mlp["w2"]), b2=np.zeros_like(mlp["b2"]),
+               pos=np.zeros_like(anc["pos"]), feat=np.zeros_like(anc["feat"]),
+               offsets=np.zeros_like(anc["offsets"]), scaling=np.zeros_like(anc["scaling"]))
+    acc = {kk: np.ascontiguousarray(v, dtype=np.float64) for kk, v in acc.items()}
+    pose = np.zeros((len(cams), 6))
+    reg = lcfg.lambda_scale / _scale_count(len(cams), N) if lcfg.lambda_scale else 0.0
+    per_view = []
+    for v, (cam, vw) in enumerate(zip(cams, views)):
+        g = vw["g"]
+        g2 = render_bwd(vw["proj"], g, cam, cfg, n_feat, vw["gimg"])
+        g3 = project_bwd(g, vw["proj"], cam, cfg, g2, reg)
+        g3d = dict(mean=g3["mean"], opacity=g2["opacity"], scale=g3["scale"],
+                   quat=g3["quat"], color=g2["color"], feat=g2["feat"])
+        pd = decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc)
+        pose[v] = g3["pose"] + pd
+        per_view.append(dict(g2d=g2, g3d=g3d, pose_project=g3["pose"], pose_decode=pd))
+    acc["pose"] = pose
+    return L, acc, views, per_view
