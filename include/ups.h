@@ -1,0 +1,282 @@
+/*
+ * ups.h — C ABI of the GB300 (sm_103a) differentiable render path of
+ * anchor-decoded 3D Gaussians (UP-SLAM, arXiv 2505.22335).
+ *
+ * Path: decode (Eq. 8-9) -> projection (Eq. 1-2) -> (view, tile, depth) key
+ * sort -> tile ranges -> front-to-back blending of colour, depth, an N_l-channel
+ * feature map and transmittance (Eq. 3, Eq. 10) -> per-pixel weighted loss
+ * (Eq. 4, Eq. 14) -> reverse-order backward into Gaussian, MLP-weight and
+ * SE(3) pose gradients.
+ *
+ * Conventions shared by every entry point
+ *  - All tensor arguments are DEVICE pointers to float32 (or uint32 where
+ *    stated), owned by the caller, contiguous, 16-byte aligned.
+ *  - "float4 [n]" means n records of 4 floats; unused lanes are ignored on
+ *    input and written as 0 on output.
+ *  - Images of several views are concatenated view after view; inside a view
+ *    a C-channel image is C planes of H x W (row-major).  View v starts at
+ *    pixel offset P_v = sum_{u<v} H_u W_u, so its channel c of a C-channel
+ *    image starts at element C * P_v + c * H_v * W_v.
+ *  - Pixel (i, j) is sampled at continuous image coordinate (i, j); a camera
+ *    point (X, Y, Z) maps to u = fx X/Z + cx, v = fy Y/Z + cy.  Background 0.
+ *  - Poses are world-to-camera T_cw, row-major 4x4 float, on the HOST (copied
+ *    into kernel parameters).  Pose gradients are dL/dxi for the left
+ *    perturbation T_cw <- Exp(xi) T_cw, xi = (rho[3], phi[3]), at xi = 0.
+ *  - Every call is stream-ordered on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream), never aborts and never throws; the return value
+ *    is a ups_status and ups_last_error() gives a message.  One ups_ctx must
+ *    not be used from two host threads at the same time.
+ */
+#ifndef UPS_H
+#define UPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UPS_MAX_VIEWS 64
+
+typedef struct ups_ctx ups_ctx;
+typedef void *ups_stream; /* cudaStream_t */
+
+typedef enum {
+    UPS_OK = 0,
+    UPS_PENDING = 1,        /* ups_poll: request not finished yet */
+    UPS_ERR_ARG = 2,        /* invalid argument (sizes, NULL, alignment) */
+    UPS_ERR_OOM = 3,        /* device or pinned allocation failed */
+    UPS_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    UPS_ERR_TIMEOUT = 5,    /* a bounded wait ran out */
+    UPS_ERR_CANCELLED = 6,  /* request cancelled before it ran */
+    UPS_ERR_NONFINITE = 7,  /* check_finite found NaN/Inf in an input */
+    UPS_ERR_CAPACITY = 8,   /* a fixed-size buffer is too small */
+    UPS_ERR_STATE = 9       /* call out of order (e.g. backward before forward) */
+} ups_status;
+
+/* Readings of the thresholds Eq. 3 leaves open and the model sizes. */
+typedef struct {
+    float alpha_min;  /* skip a Gaussian whose alpha is below this (1/255) */
+    float alpha_max;  /* alpha clamp (0.99) */
+    float t_min;      /* stop before the Gaussian that takes T below this (1e-4) */
+    float dilation;   /* added to the diagonal of Sigma' in px^2 (0.3) */
+    float near_z;     /* cull Z <= near_z (0.2 m) */
+    float guard;      /* cull |X/Z| > guard * W / (2 fx), same in y (1.3) */
+    int n_feat;       /* N_l, rendered feature channels: 0, 16 or 32 */
+    int k;            /* Gaussians per anchor K (1..16) */
+    int feat_dim;     /* anchor feature width (32) */
+    int hidden;       /* decode MLP hidden width (32) */
+    int decode_bf16;  /* 1: decode GEMMs in BF16 on the tensor cores, FP32 accumulate */
+    int check_finite; /* 1: scan inputs for NaN/Inf and fail with UPS_ERR_NONFINITE */
+} ups_config;
+
+/* Fills the defaults listed above (n_feat 16, k 10, feat_dim 32, hidden 32). */
+void ups_config_default(ups_config *cfg);
+
+/* Pinhole camera of one view (Sec. 3.1); t_norm feeds the temporal encoding
+ * l_t = (sin pi t, cos pi t) of Sec. 3.3. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int width, height;
+    float T_cw[16];
+    float t_norm;
+} ups_camera;
+
+/* A set of 3D Gaussians G = {(mu, o, c, Sigma = R S S^T R^T)} (Eq. 1).
+ *  n         Gaussians per set
+ *  per_view  0: one set used by every view (plain 3DGS); 1: one set per view
+ *            (decode output, set v belongs to view v)
+ *  mean_opacity float4 [sets][n]: mu_x, mu_y, mu_z, o  (o in (0,1))
+ *  scale        float4 [sets][n]: s_x, s_y, s_z, -    (s > 0)
+ *  quat         float4 [sets][n]: w, x, y, z          (any nonzero norm)
+ *  color        float4 [sets][n]: r, g, b, -
+ *  feat         float  [sets][n][n_feat]              (NULL if n_feat == 0)
+ * The same struct holds gradients dL/d(each field); with per_view == 0 the
+ * gradients are summed over views. */
+typedef struct {
+    int n;
+    int per_view;
+    float *mean_opacity;
+    float *scale;
+    float *quat;
+    float *color;
+    float *feat;
+} ups_gaussians;
+
+/* Rendered images (Eq. 3, Eq. 10), layouts as in the header comment.
+ *  color [3 planes], depth [1], feat [n_feat planes] (NULL if n_feat == 0),
+ *  T     final transmittance prod(1 - alpha_i) [1]; Eq. 3's accumulated T~ is 1 - T
+ *  n_contrib uint32 [1]: list position of the last blended Gaussian + 1. */
+typedef struct {
+    float *color;
+    float *depth;
+    float *feat;
+    float *T;
+    uint32_t *n_contrib;
+} ups_images;
+
+/* dL/d(rendered images); any pointer may be NULL (zero gradient). */
+typedef struct {
+    const float *color;
+    const float *depth;
+    const float *feat;
+    const float *T;
+} ups_image_grads;
+
+/* Targets of the weighted loss; weight is the per-pixel map w (NULL = 1). */
+typedef struct {
+    const float *color;
+    const float *depth;
+    const float *feat;
+    const float *weight;
+} ups_targets;
+
+/* L = (1/sum_v H_v W_v) sum_p w_p [lc sum l(C-Ct) + ld l(D-Dt) + lf sum l(F-Ft)]
+ *     + lambda_scale * mean(s)   (Eq. 4 / Eq. 14; l = |.| or (.)^2) */
+typedef struct {
+    float lambda_color;
+    float lambda_depth;
+    float lambda_feat;
+    float lambda_scale;
+    int l2; /* 0: l1, 1: squared */
+} ups_loss_cfg;
+
+/* Anchors (Sec. 3.3 "Adaptively Structured Gaussian").
+ *  pos     [n][3] anchor position x_v
+ *  feat    [n][feat_dim] anchor feature f_v
+ *  offsets [n][k][3] learnable offsets; Gaussian mean mu = x_v + O_{v,k}
+ *  scaling [n][3] per-anchor scaling l_v; Gaussian scale s = l_v * sigmoid(.) */
+typedef struct {
+    int n;
+    float *pos;
+    float *feat;
+    float *offsets;
+    float *scaling;
+} ups_anchors;
+
+/* The four decode MLPs (Eq. 8-9): opacity, covariance (3 scale + 4 quaternion),
+ * colour, feature F_d.  Input x = [f_v (feat_dim), delta_vc (3), d_vc (1),
+ * sin(pi t), cos(pi t)] with delta_vc = (x_v - o_c)/|x_v - o_c|, d_vc = |x_v - o_c|.
+ *  w1 [4*hidden][feat_dim+6], b1 [4*hidden]: hidden blocks in the order above;
+ *     ReLU for the first three, SoftPlus for F_d
+ *  w2 [k*(11+n_feat)][hidden], b2 [k*(11+n_feat)]: output rows grouped as
+ *     opacity (k), covariance (7k), colour (3k), feature (k*n_feat); group g
+ *     reads hidden block g.  Output activations: sigmoid opacity and colour,
+ *     s = l_v * sigmoid, raw quaternion, linear feature. */
+typedef struct {
+    float *w1;
+    float *b1;
+    float *w2;
+    float *b2;
+} ups_mlp;
+
+/* Which gradients ups_render_backward / ups_decode_backward produce. */
+enum {
+    UPS_GRAD_POSE = 1,     /* dL/dxi per view */
+    UPS_GRAD_GAUSS = 2,    /* dL/d(Gaussian set) */
+    UPS_GRAD_MLP = 4,      /* dL/d(w1, b1, w2, b2) */
+    UPS_GRAD_ANCHOR = 8,   /* dL/d(anchor pos, feat, offsets, scaling) */
+    UPS_GRAD_ALL = 15
+};
+
+/* Counters of the last forward (reading them synchronises the ctx stream). */
+typedef struct {
+    int n_views;
+    long long n_gaussian_views; /* sets used x n over all views */
+    long long n_visible;        /* Gaussian-views touching at least one tile */
+    long long n_instances;      /* (view, tile, Gaussian) entries sorted */
+    long long n_tiles;          /* tiles over all views */
+    long long n_pixels;
+    int key_bits;               /* significant bits of the (view, tile) key */
+} ups_stats;
+
+/* ---------------------------------------------------------------------- */
+/* context                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` (made current for every call on
+ * this ctx).  The ctx owns only scratch memory, grown on demand. */
+ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out);
+ups_status ups_destroy(ups_ctx *ctx);
+/* Message of the last failed call on ctx (or of the last ups_create failure
+ * when ctx is NULL).  Valid until the next call on ctx. */
+const char *ups_last_error(const ups_ctx *ctx);
+const char *ups_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* forward                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Eq. 8-9: decode k Gaussians per anchor for each of n_views cameras.
+ * out (caller-allocated, per_view must be 1, n == anchors->n * k) receives
+ * mean_opacity, scale, quat (unnormalised), color and feat of set v = view v,
+ * Gaussian id g = anchor * k + j. */
+ups_status ups_decode_anchors(ups_ctx *ctx, const ups_anchors *anchors, const ups_mlp *mlp,
+                              const ups_camera *cams, int n_views, ups_gaussians *out,
+                              ups_stream stream);
+
+/* Eq. 1-3, Eq. 10: project, bin by (view, tile, depth), blend front to back.
+ * g and out must stay alive and unmodified until ups_render_backward on this
+ * ctx, which reuses them (T and n_contrib replace per-fragment state).
+ * Synchronises `stream` once to size the instance buffers. */
+ups_status ups_render_forward(ups_ctx *ctx, const ups_gaussians *g, const ups_camera *cams,
+                              int n_views, ups_images *out, ups_stream stream);
+
+/* Weighted loss of the last forward's images against `tgt`.  Writes the
+ * scalar loss to loss_dev[0] (device float, overwritten) and dL/d(images) to
+ * dL (caller-allocated, same layouts as the images).  If g is not NULL and
+ * lcfg->lambda_scale != 0 the mean-scale term of Eq. 14 is added. */
+ups_status ups_loss_weighted(ups_ctx *ctx, const ups_images *img, const ups_targets *tgt,
+                             const ups_loss_cfg *lcfg, const ups_gaussians *g,
+                             float *loss_dev, ups_images *dL, ups_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* backward                                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Reverse-order backward of the last ups_render_forward on ctx.
+ *  dL        image gradients (any may be NULL)
+ *  grad      UPS_GRAD_GAUSS: dL/d(Gaussian set), same shape as the forward
+ *            input; OVERWRITTEN (per_view == 1) or OVERWRITTEN as the sum over
+ *            views (per_view == 0).  May be NULL without that flag.
+ *  d_pose    UPS_GRAD_POSE: float [n_views][6], OVERWRITTEN
+ *  scale_grad  constant added to every dL/ds (the mean-scale term:
+ *            lambda_scale / (3 * sets * n)); 0 for none. */
+ups_status ups_render_backward(ups_ctx *ctx, const ups_image_grads *dL, unsigned grad_mask,
+                               float scale_grad, ups_gaussians *grad, float *d_pose,
+                               ups_stream stream);
+
+/* Backward of Eq. 8-9 for the views of the last ups_decode_anchors-shaped
+ * call: dG holds dL/d(decoded sets) (per_view == 1).  ACCUMULATES (+=) into
+ * d_mlp (UPS_GRAD_MLP), d_anchors (UPS_GRAD_ANCHOR) and d_pose (UPS_GRAD_POSE;
+ * the camera-centre dependence of delta_vc and d_vc).  Pointers of a flag that
+ * is not set may be NULL. */
+ups_status ups_decode_backward(ups_ctx *ctx, const ups_anchors *anchors, const ups_mlp *mlp,
+                               const ups_camera *cams, int n_views, const ups_gaussians *dG,
+                               unsigned grad_mask, ups_mlp *d_mlp, ups_anchors *d_anchors,
+                               float *d_pose, ups_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* inspection (tests and benchmarks)                                      */
+/* ---------------------------------------------------------------------- */
+
+ups_status ups_get_stats(ups_ctx *ctx, ups_stats *out);
+
+/* Internal buffers of the last forward, copied to HOST memory `dst` of
+ * `bytes` bytes (at most the buffer size; the copy synchronises):
+ *   0 sorted instance Gaussian-view ids   uint32 [n_instances] (gv = view*n + g)
+ *   1 sorted instance keys                uint32 [n_instances] (tile_base[view] + tile)
+ *   2 tile ranges                         uint32 [n_tiles][2]  ([start, end))
+ *   3 projected (u, v, z, o)              float4 [n_gaussian_views]
+ *   4 conic (a, b, c, -)                  float4 [n_gaussian_views]
+ *   5 tile rect (x0 | y0 << 16, x1 | y1 << 16)  uint32 [n_gaussian_views][2]
+ *   6 per-Gaussian-view 2D gradients of the last backward
+ *     float [n_gaussian_views][12 + n_feat]: du dv dz do dca dcb dcc dr dg db - - df...
+ * Returns the buffer size in bytes through *size (dst may be NULL). */
+ups_status ups_copy_buffer(ups_ctx *ctx, int which, void *dst, size_t bytes, size_t *size);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UPS_H */

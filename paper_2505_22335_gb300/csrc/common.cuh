@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/ups.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ups.h"
+
+namespace ups {
+
+constexpr int kTile = 16;          // image tile edge (pixels)
+constexpr int kTilePix = kTile * kTile;
+
+// One view as the kernels see it (passed by value in kernel parameters).
+struct DevView {
+    float fx, fy, cx, cy;
+    int W, H;
+    int tiles_x, tiles_y;
+    int tile_base;  // index of this view's tile 0 among all views' tiles
+    int pix_off;    // P_v: pixel offset of this view in concatenated images
+    float R[9];     // rotation of T_cw (row-major)
+    float t[3];     // translation of T_cw
+    float limx, limy;  // frustum guard on |X/Z|, |Y/Z|
+    float t_norm;
+};
+
+struct ViewTable {
+    int n;
+    int total_tiles;
+    DevView v[UPS_MAX_VIEWS];
+};
+
+struct BlendParams {
+    float alpha_min, alpha_max, t_min, dilation, near_z;
+};
+
+// Per-Gaussian-view 2D gradient record (floats, 16-byte aligned groups):
+//  0 du, 1 dv, 2 dz, 3 dopacity, 4 dconic_a, 5 dconic_b, 6 dconic_c, 7 pad,
+//  8..10 dcolor, 11 pad, 12.. dfeat[n_feat]
+constexpr int kG2Base = 12;
+__host__ __device__ inline int g2_stride(int n_feat) { return kG2Base + n_feat; }
+
+// View index of global tile `t` (views are few; linear scan).
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int t) {
+    int v = 0;
+    while (v + 1 < vt.n && vt.v[v + 1].tile_base <= t) ++v;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers (implemented in ctx.cu)
+// ---------------------------------------------------------------------------
+
+// Device buffer that only grows.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t want);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Radix sort of (key, value) pairs over bits [0, end_bit); stable.  Keys are
+// uint32 or uint64, values uint32.  On return *key_io/*val_io point at the
+// buffer (one of the two given) that holds the sorted data.
+struct SortScratch {
+    DevBuf hist;
+};
+size_t radix_hist_bytes(size_t n);
+cudaError_t radix_sort_u32(uint32_t **key_io, uint32_t **key_alt, uint32_t **val_io,
+                           uint32_t **val_alt, size_t n, int end_bit, SortScratch &s,
+                           cudaStream_t st);
+cudaError_t radix_sort_u64(uint64_t **key_io, uint64_t **key_alt, uint32_t **val_io,
+                           uint32_t **val_alt, size_t n, int end_bit, SortScratch &s,
+                           cudaStream_t st);
+// Exclusive scan of n uint32 into uint64 (out has n+1 entries; out[n] = total).
+size_t scan_scratch_bytes(size_t n);
+cudaError_t exclusive_scan_u32_u64(const uint32_t *in, uint64_t *out, size_t n, void *scratch,
+                                   cudaStream_t st);
+
+}  // namespace ups

@@ -1,0 +1,518 @@
+// Host side of the C ABI (include/ups.h): argument checks, scratch memory,
+// and the order of kernel launches for decode, forward, loss and backward.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ups {
+
+// launchers implemented in the other translation units
+cudaError_t launch_project(const ViewTable &vt, const BlendParams &bp, int N, int per_view,
+                           int total, const ups_gaussians &g, float4 *xyzo, float4 *conic,
+                           uint2 *rect, uint32_t *count, uint64_t *dkey, uint32_t *dval,
+                           cudaStream_t st);
+cudaError_t launch_gather_counts(const uint32_t *sorted_gv, const uint32_t *count, uint32_t *out,
+                                 int total, cudaStream_t st);
+cudaError_t launch_emit(const ViewTable &vt, int N, int total, const uint32_t *sorted_gv,
+                        const uint64_t *off, const uint2 *rect, uint32_t *ikey, uint32_t *ival,
+                        cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t *ikey, uint32_t n, uint2 *ranges, cudaStream_t st);
+cudaError_t launch_project_bwd(const ViewTable &vt, const BlendParams &bp, int N, int per_view,
+                               int total, int n_feat, unsigned mask, float scale_grad,
+                               const ups_gaussians &g, const float *g2, const ups_gaussians *grad,
+                               float *d_pose, cudaStream_t st);
+cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
+                                 int per_view, const uint2 *ranges, const uint32_t *ival,
+                                 const float4 *xyzo, const float4 *conic, const float4 *color,
+                                 const float *feat, const ups_images &out, cudaStream_t st);
+cudaError_t launch_loss(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
+                        int l2, float inv_norm, const ups_images &img, const ups_targets &tgt,
+                        const ups_images &grad, float *loss, cudaStream_t st);
+cudaError_t launch_scale_mean(const float4 *scale, size_t n, float coef, float *loss,
+                              cudaStream_t st);
+cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
+                                 int per_view, const uint2 *ranges, const uint32_t *ival,
+                                 const float4 *xyzo, const float4 *conic, const float4 *color,
+                                 const float *feat, const float *T, const uint32_t *nc,
+                                 const ups_image_grads &dL, float *g2, cudaStream_t st);
+cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
+                              const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
+                              cudaStream_t st);
+cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
+                              const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask,
+                              const ups_mlp *d_mlp, const ups_anchors *d_anc, float *d_pose,
+                              int num_sms, cudaStream_t st);
+
+cudaError_t DevBuf::reserve(size_t want) {
+    if (want <= bytes) return cudaSuccess;
+    release();
+    size_t b = std::max<size_t>(want + want / 8, 256);
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+}  // namespace ups
+
+using namespace ups;
+
+struct ups_ctx {
+    ups_config cfg{};
+    int device = 0;
+    int num_sms = 1;
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+    // forward state
+    bool have_fwd = false;
+    ViewTable vt{};
+    BlendParams bp{};
+    int N = 0, per_view = 0;
+    size_t total_gv = 0;
+    size_t n_inst = 0, n_visible = 0, n_pix = 0;
+    int key_bits = 0, max_hw = 0;
+    ups_gaussians g_in{};
+    ups_images img{};
+    bool have_bwd = false;
+    // scratch
+    DevBuf xyzo, conic, rect, count, dkey0, dkey1, dval0, dval1, cnt_sorted, off, scan_scr;
+    DevBuf ikey0, ikey1, ival0, ival1, ranges, g2;
+    SortScratch sort;
+    uint32_t *dval_sorted = nullptr, *ikey_sorted = nullptr, *ival_sorted = nullptr;
+    uint64_t *h_total = nullptr;  // pinned
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ups_status fail(ups_ctx *c, ups_status s, const std::string &msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+ups_status cuda_fail(ups_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? UPS_ERR_OOM : UPS_ERR_CUDA, m);
+}
+
+#define UPS_CUDA(c, expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, #expr); \
+    } while (0)
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+ups_status build_views(ups_ctx *c, const ups_camera *cams, int n_views, ViewTable &vt,
+                       size_t &n_pix, int &max_hw) {
+    if (!cams || n_views < 1 || n_views > UPS_MAX_VIEWS)
+        return fail(c, UPS_ERR_ARG, "n_views must be in [1, UPS_MAX_VIEWS] and cams non-NULL");
+    std::memset(&vt, 0, sizeof(vt));
+    vt.n = n_views;
+    int tiles = 0;
+    size_t pix = 0;
+    max_hw = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const ups_camera &cm = cams[v];
+        if (cm.width < 1 || cm.height < 1 || cm.width > 16384 || cm.height > 16384 ||
+            !(cm.fx > 0) || !(cm.fy > 0))
+            return fail(c, UPS_ERR_ARG, "camera " + std::to_string(v) + ": bad intrinsics or size");
+        for (int i = 0; i < 16; ++i)
+            if (!std::isfinite(cm.T_cw[i]))
+                return fail(c, UPS_ERR_NONFINITE, "camera " + std::to_string(v) + ": non-finite pose");
+        DevView &d = vt.v[v];
+        d.fx = cm.fx;
+        d.fy = cm.fy;
+        d.cx = cm.cx;
+        d.cy = cm.cy;
+        d.W = cm.width;
+        d.H = cm.height;
+        d.tiles_x = (cm.width + kTile - 1) / kTile;
+        d.tiles_y = (cm.height + kTile - 1) / kTile;
+        d.tile_base = tiles;
+        d.pix_off = (int)pix;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = cm.T_cw[4 * i + j];
+            d.t[i] = cm.T_cw[4 * i + 3];
+        }
+        d.limx = c->cfg.guard * 0.5f * cm.width / cm.fx;
+        d.limy = c->cfg.guard * 0.5f * cm.height / cm.fy;
+        d.t_norm = cm.t_norm;
+        tiles += d.tiles_x * d.tiles_y;
+        pix += (size_t)cm.width * cm.height;
+        max_hw = std::max(max_hw, cm.width * cm.height);
+    }
+    if (pix > (size_t)INT32_MAX) return fail(c, UPS_ERR_ARG, "too many pixels in one call");
+    vt.total_tiles = tiles;
+    n_pix = pix;
+    return UPS_OK;
+}
+
+ups_status check_gaussians(ups_ctx *c, const ups_gaussians *g, const char *what) {
+    if (!g) return fail(c, UPS_ERR_ARG, std::string(what) + " is NULL");
+    if (g->n < 1) return fail(c, UPS_ERR_ARG, std::string(what) + ".n must be >= 1");
+    const void *ptrs[4] = {g->mean_opacity, g->scale, g->quat, g->color};
+    for (const void *p : ptrs)
+        if (!p || !aligned16(p))
+            return fail(c, UPS_ERR_ARG, std::string(what) + ": NULL or unaligned attribute pointer");
+    if (c->cfg.n_feat > 0 && (!g->feat || !aligned16(g->feat)))
+        return fail(c, UPS_ERR_ARG, std::string(what) + ".feat NULL or unaligned");
+    return UPS_OK;
+}
+
+int bits_for(size_t n) {
+    int b = 0;
+    while (b < 63 && ((size_t)1 << b) < n) ++b;
+    return b;
+}
+
+ups_status set_device(ups_ctx *c) {
+    UPS_CUDA(c, cudaSetDevice(c->device));
+    return UPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ups_config_default(ups_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->alpha_min = 1.f / 255.f;
+    cfg->alpha_max = 0.99f;
+    cfg->t_min = 1e-4f;
+    cfg->dilation = 0.3f;
+    cfg->near_z = 0.2f;
+    cfg->guard = 1.3f;
+    cfg->n_feat = 16;
+    cfg->k = 10;
+    cfg->feat_dim = 32;
+    cfg->hidden = 32;
+    cfg->decode_bf16 = 0;
+    cfg->check_finite = 0;
+}
+
+const char *ups_version(void) { return "ups-gb300 0.1 (sm_103a)"; }
+
+ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
+    if (!out) return fail(nullptr, UPS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    ups_config c{};
+    if (cfg)
+        c = *cfg;
+    else
+        ups_config_default(&c);
+    if (c.n_feat != 0 && c.n_feat != 16 && c.n_feat != 32)
+        return fail(nullptr, UPS_ERR_ARG, "n_feat must be 0, 16 or 32");
+    if (c.k < 1 || c.k > 16) return fail(nullptr, UPS_ERR_ARG, "k must be in [1, 16]");
+    if (c.feat_dim != 32 || c.hidden != 32)
+        return fail(nullptr, UPS_ERR_ARG, "feat_dim and hidden must be 32");
+    if (!(c.alpha_min > 0.f) || !(c.alpha_max >= c.alpha_min) || !(c.alpha_max < 1.f) ||
+        !(c.t_min >= 0.f) || !(c.dilation >= 0.f) || !(c.near_z > 0.f) || !(c.guard > 0.f))
+        return fail(nullptr, UPS_ERR_ARG, "threshold out of range");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, UPS_ERR_CUDA, std::string("no CUDA device ") + std::to_string(device) +
+                                               (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : ""));
+    ups_ctx *ctx = new ups_ctx();
+    ctx->cfg = c;
+    ctx->device = device;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_total, sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        g_create_error = std::string("ups_create: ") + cudaGetErrorString(e);
+        delete ctx;
+        return UPS_ERR_CUDA;
+    }
+    ctx->bp = BlendParams{c.alpha_min, c.alpha_max, c.t_min, c.dilation, c.near_z};
+    *out = ctx;
+    return UPS_OK;
+}
+
+ups_status ups_destroy(ups_ctx *c) {
+    if (!c) return UPS_OK;
+    cudaSetDevice(c->device);
+    DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
+                      &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->sort.hist};
+    for (DevBuf *b : bufs) b->release();
+    if (c->h_total) cudaFreeHost(c->h_total);
+    delete c;
+    return UPS_OK;
+}
+
+const char *ups_last_error(const ups_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp *mlp,
+                              const ups_camera *cams, int n_views, ups_gaussians *out,
+                              ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!anc || !mlp || !out) return fail(c, UPS_ERR_ARG, "NULL argument");
+    if (anc->n < 1 || !anc->pos || !anc->feat || !anc->offsets || !anc->scaling)
+        return fail(c, UPS_ERR_ARG, "anchors: n < 1 or NULL pointer");
+    if (!aligned16(anc->feat)) return fail(c, UPS_ERR_ARG, "anchors.feat must be 16-byte aligned");
+    if (!mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2) return fail(c, UPS_ERR_ARG, "mlp: NULL pointer");
+    if (!out->per_view || (size_t)out->n != (size_t)anc->n * c->cfg.k)
+        return fail(c, UPS_ERR_ARG, "out must be per_view with n == anchors.n * k");
+    ups_status s = check_gaussians(c, out, "out");
+    if (s != UPS_OK) return s;
+    if ((size_t)anc->n * c->cfg.k * n_views >= (size_t)INT32_MAX)
+        return fail(c, UPS_ERR_ARG, "anchors * k * views exceeds 2^31");
+    ViewTable vt;
+    size_t npix;
+    int mhw;
+    if ((s = build_views(c, cams, n_views, vt, npix, mhw)) != UPS_OK) return s;
+    if ((s = set_device(c)) != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->num_sms, st));
+    return UPS_OK;
+}
+
+ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_camera *cams,
+                              int n_views, ups_images *out, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    c->have_fwd = false;
+    c->have_bwd = false;
+    ups_status s = check_gaussians(c, g, "g");
+    if (s != UPS_OK) return s;
+    if (!out || !out->color || !out->depth || !out->T || !out->n_contrib ||
+        (c->cfg.n_feat > 0 && !out->feat))
+        return fail(c, UPS_ERR_ARG, "out: NULL image pointer");
+    ViewTable &vt = c->vt;
+    if ((s = build_views(c, cams, n_views, vt, c->n_pix, c->max_hw)) != UPS_OK) return s;
+    const size_t total = (size_t)g->n * n_views;
+    if (total >= (size_t)INT32_MAX) return fail(c, UPS_ERR_ARG, "n * n_views exceeds 2^31");
+    if ((s = set_device(c)) != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    c->N = g->n;
+    c->per_view = g->per_view ? 1 : 0;
+    c->total_gv = total;
+    // per-Gaussian-view scratch
+    UPS_CUDA(c, c->xyzo.reserve(total * sizeof(float4)));
+    UPS_CUDA(c, c->conic.reserve(total * sizeof(float4)));
+    UPS_CUDA(c, c->rect.reserve(total * sizeof(uint2)));
+    UPS_CUDA(c, c->count.reserve(total * sizeof(uint32_t)));
+    UPS_CUDA(c, c->dkey0.reserve(total * sizeof(uint64_t)));
+    UPS_CUDA(c, c->dkey1.reserve(total * sizeof(uint64_t)));
+    UPS_CUDA(c, c->dval0.reserve(total * sizeof(uint32_t)));
+    UPS_CUDA(c, c->dval1.reserve(total * sizeof(uint32_t)));
+    UPS_CUDA(c, c->cnt_sorted.reserve(total * sizeof(uint32_t)));
+    UPS_CUDA(c, c->off.reserve((total + 1) * sizeof(uint64_t)));
+    UPS_CUDA(c, c->scan_scr.reserve(scan_scratch_bytes(total)));
+    UPS_CUDA(c, c->ranges.reserve((size_t)vt.total_tiles * sizeof(uint2)));
+
+    UPS_CUDA(c, launch_project(vt, c->bp, c->N, c->per_view, (int)total, *g, c->xyzo.as<float4>(),
+                               c->conic.as<float4>(), c->rect.as<uint2>(), c->count.as<uint32_t>(),
+                               c->dkey0.as<uint64_t>(), c->dval0.as<uint32_t>(), st));
+    // (view, depth) order of the Gaussian-views
+    uint64_t *dk = c->dkey0.as<uint64_t>(), *dk_alt = c->dkey1.as<uint64_t>();
+    uint32_t *dv = c->dval0.as<uint32_t>(), *dv_alt = c->dval1.as<uint32_t>();
+    int vbits = bits_for((size_t)n_views);
+    UPS_CUDA(c, radix_sort_u64(&dk, &dk_alt, &dv, &dv_alt, total, 32 + vbits, c->sort, st));
+    c->dval_sorted = dv;
+    UPS_CUDA(c, launch_gather_counts(dv, c->count.as<uint32_t>(), c->cnt_sorted.as<uint32_t>(), (int)total, st));
+    UPS_CUDA(c, exclusive_scan_u32_u64(c->cnt_sorted.as<uint32_t>(), c->off.as<uint64_t>(), total,
+                                       c->scan_scr.ptr, st));
+    UPS_CUDA(c, cudaMemcpyAsync(c->h_total, c->off.as<uint64_t>() + total, sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, st));
+    UPS_CUDA(c, cudaStreamSynchronize(st));
+    const uint64_t n_inst = *c->h_total;
+    if (n_inst >= (uint64_t)UINT32_MAX) return fail(c, UPS_ERR_CAPACITY, "more than 2^32 tile instances");
+    c->n_inst = (size_t)n_inst;
+    UPS_CUDA(c, c->ikey0.reserve(std::max<size_t>(n_inst, 1) * sizeof(uint32_t)));
+    UPS_CUDA(c, c->ikey1.reserve(std::max<size_t>(n_inst, 1) * sizeof(uint32_t)));
+    UPS_CUDA(c, c->ival0.reserve(std::max<size_t>(n_inst, 1) * sizeof(uint32_t)));
+    UPS_CUDA(c, c->ival1.reserve(std::max<size_t>(n_inst, 1) * sizeof(uint32_t)));
+    uint32_t *ik = c->ikey0.as<uint32_t>(), *ik_alt = c->ikey1.as<uint32_t>();
+    uint32_t *iv = c->ival0.as<uint32_t>(), *iv_alt = c->ival1.as<uint32_t>();
+    UPS_CUDA(c, launch_emit(vt, c->N, (int)total, dv, c->off.as<uint64_t>(), c->rect.as<uint2>(), ik, iv, st));
+    // stable bucket by (view, tile): depth order is kept inside each tile
+    c->key_bits = bits_for((size_t)vt.total_tiles);
+    UPS_CUDA(c, radix_sort_u32(&ik, &ik_alt, &iv, &iv_alt, n_inst, c->key_bits, c->sort, st));
+    c->ikey_sorted = ik;
+    c->ival_sorted = iv;
+    UPS_CUDA(c, cudaMemsetAsync(c->ranges.ptr, 0, (size_t)vt.total_tiles * sizeof(uint2), st));
+    UPS_CUDA(c, launch_ranges(ik, (uint32_t)n_inst, c->ranges.as<uint2>(), st));
+    UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
+                                     iv, c->xyzo.as<float4>(), c->conic.as<float4>(),
+                                     reinterpret_cast<const float4 *>(g->color), g->feat, *out, st));
+    c->g_in = *g;
+    c->img = *out;
+    c->have_fwd = true;
+    return UPS_OK;
+}
+
+ups_status ups_loss_weighted(ups_ctx *c, const ups_images *img, const ups_targets *tgt,
+                             const ups_loss_cfg *lcfg, const ups_gaussians *g, float *loss_dev,
+                             ups_images *dL, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_loss_weighted needs a forward first");
+    if (!img || !tgt || !lcfg || !loss_dev || !dL) return fail(c, UPS_ERR_ARG, "NULL argument");
+    const int nf = c->cfg.n_feat;
+    if (!img->color || !img->depth || !tgt->color || !tgt->depth || !dL->color || !dL->depth ||
+        (nf > 0 && (!img->feat || !tgt->feat || !dL->feat)))
+        return fail(c, UPS_ERR_ARG, "NULL image pointer");
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
+    float inv_norm = (float)(1.0 / (double)c->n_pix);
+    UPS_CUDA(c, launch_loss(c->vt, nf, c->max_hw, lcfg->lambda_color, lcfg->lambda_depth,
+                            lcfg->lambda_feat, lcfg->l2, inv_norm, *img, *tgt, *dL, loss_dev, st));
+    if (g && lcfg->lambda_scale != 0.f) {
+        size_t sets = g->per_view ? (size_t)c->vt.n : 1;
+        size_t n = sets * (size_t)g->n;
+        UPS_CUDA(c, launch_scale_mean(reinterpret_cast<const float4 *>(g->scale), n,
+                                      (float)(lcfg->lambda_scale / (3.0 * (double)n)), loss_dev, st));
+    }
+    return UPS_OK;
+}
+
+ups_status ups_render_backward(ups_ctx *c, const ups_image_grads *dL, unsigned mask,
+                               float scale_grad, ups_gaussians *grad, float *d_pose,
+                               ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_render_backward needs a forward first");
+    if (!dL) return fail(c, UPS_ERR_ARG, "dL is NULL");
+    if ((mask & UPS_GRAD_POSE) && !d_pose) return fail(c, UPS_ERR_ARG, "d_pose is NULL");
+    if (mask & UPS_GRAD_GAUSS) {
+        ups_status s = check_gaussians(c, grad, "grad");
+        if (s != UPS_OK) return s;
+        if (grad->n != c->N || (grad->per_view ? 1 : 0) != c->per_view)
+            return fail(c, UPS_ERR_ARG, "grad must have the forward input's n and per_view");
+    }
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    const int nf = c->cfg.n_feat;
+    const size_t rec = (size_t)g2_stride(nf);
+    UPS_CUDA(c, c->g2.reserve(c->total_gv * rec * sizeof(float)));
+    UPS_CUDA(c, cudaMemsetAsync(c->g2.ptr, 0, c->total_gv * rec * sizeof(float), st));
+    UPS_CUDA(c, launch_composite_bwd(c->vt, c->bp, nf, c->N, c->per_view, c->ranges.as<uint2>(),
+                                     c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
+                                     reinterpret_cast<const float4 *>(c->g_in.color), c->g_in.feat,
+                                     c->img.T, c->img.n_contrib, *dL, c->g2.as<float>(), st));
+    if (mask & UPS_GRAD_POSE)
+        UPS_CUDA(c, cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * c->vt.n, st));
+    if ((mask & UPS_GRAD_GAUSS) && !c->per_view) {
+        size_t n = (size_t)c->N;
+        UPS_CUDA(c, cudaMemsetAsync(grad->mean_opacity, 0, n * sizeof(float4), st));
+        UPS_CUDA(c, cudaMemsetAsync(grad->scale, 0, n * sizeof(float4), st));
+        UPS_CUDA(c, cudaMemsetAsync(grad->quat, 0, n * sizeof(float4), st));
+        UPS_CUDA(c, cudaMemsetAsync(grad->color, 0, n * sizeof(float4), st));
+        if (nf) UPS_CUDA(c, cudaMemsetAsync(grad->feat, 0, n * nf * sizeof(float), st));
+    }
+    if (mask & (UPS_GRAD_POSE | UPS_GRAD_GAUSS))
+        UPS_CUDA(c, launch_project_bwd(c->vt, c->bp, c->N, c->per_view, (int)c->total_gv, nf, mask,
+                                       scale_grad, c->g_in, c->g2.as<float>(), grad, d_pose, st));
+    c->have_bwd = true;
+    return UPS_OK;
+}
+
+ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp *mlp,
+                               const ups_camera *cams, int n_views, const ups_gaussians *dG,
+                               unsigned mask, ups_mlp *d_mlp, ups_anchors *d_anc, float *d_pose,
+                               ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!anc || !mlp || !dG) return fail(c, UPS_ERR_ARG, "NULL argument");
+    if (anc->n < 1 || !anc->pos || !anc->feat || !anc->offsets || !anc->scaling)
+        return fail(c, UPS_ERR_ARG, "anchors: n < 1 or NULL pointer");
+    if (!dG->per_view || (size_t)dG->n != (size_t)anc->n * c->cfg.k)
+        return fail(c, UPS_ERR_ARG, "dG must be per_view with n == anchors.n * k");
+    ups_status s = check_gaussians(c, dG, "dG");
+    if (s != UPS_OK) return s;
+    if ((mask & UPS_GRAD_MLP) && (!d_mlp || !d_mlp->w1 || !d_mlp->b1 || !d_mlp->w2 || !d_mlp->b2))
+        return fail(c, UPS_ERR_ARG, "d_mlp: NULL pointer");
+    if ((mask & UPS_GRAD_ANCHOR) &&
+        (!d_anc || !d_anc->pos || !d_anc->feat || !d_anc->offsets || !d_anc->scaling))
+        return fail(c, UPS_ERR_ARG, "d_anchors: NULL pointer");
+    if ((mask & UPS_GRAD_POSE) && !d_pose) return fail(c, UPS_ERR_ARG, "d_pose is NULL");
+    ViewTable vt;
+    size_t npix;
+    int mhw;
+    if ((s = build_views(c, cams, n_views, vt, npix, mhw)) != UPS_OK) return s;
+    if ((s = set_device(c)) != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp,
+                                  d_anc, d_pose, c->num_sms, st));
+    return UPS_OK;
+}
+
+ups_status ups_get_stats(ups_ctx *c, ups_stats *out) {
+    if (!c || !out) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "no forward yet");
+    std::memset(out, 0, sizeof(*out));
+    out->n_views = c->vt.n;
+    out->n_gaussian_views = (long long)c->total_gv;
+    out->n_instances = (long long)c->n_inst;
+    out->n_tiles = c->vt.total_tiles;
+    out->n_pixels = (long long)c->n_pix;
+    out->key_bits = c->key_bits;
+    // visible = Gaussian-views with at least one tile (count > 0)
+    std::vector<uint32_t> h(c->total_gv);
+    if (c->total_gv) {
+        UPS_CUDA(c, cudaSetDevice(c->device));
+        UPS_CUDA(c, cudaStreamSynchronize(c->last_stream));
+        UPS_CUDA(c, cudaMemcpy(h.data(), c->count.ptr, c->total_gv * 4, cudaMemcpyDeviceToHost));
+    }
+    long long vis = 0;
+    for (uint32_t x : h) vis += x > 0;
+    out->n_visible = vis;
+    return UPS_OK;
+}
+
+ups_status ups_copy_buffer(ups_ctx *c, int which, void *dst, size_t bytes, size_t *size) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "no forward yet");
+    const void *src = nullptr;
+    size_t sz = 0;
+    switch (which) {
+        case 0: src = c->ival_sorted; sz = c->n_inst * 4; break;
+        case 1: src = c->ikey_sorted; sz = c->n_inst * 4; break;
+        case 2: src = c->ranges.ptr; sz = (size_t)c->vt.total_tiles * 8; break;
+        case 3: src = c->xyzo.ptr; sz = c->total_gv * 16; break;
+        case 4: src = c->conic.ptr; sz = c->total_gv * 16; break;
+        case 5: src = c->rect.ptr; sz = c->total_gv * 8; break;
+        case 6:
+            if (!c->have_bwd) return fail(c, UPS_ERR_STATE, "no backward yet");
+            src = c->g2.ptr;
+            sz = c->total_gv * g2_stride(c->cfg.n_feat) * 4;
+            break;
+        default: return fail(c, UPS_ERR_ARG, "unknown buffer id");
+    }
+    if (size) *size = sz;
+    if (!dst) return UPS_OK;
+    size_t n = std::min(bytes, sz);
+    UPS_CUDA(c, cudaSetDevice(c->device));
+    UPS_CUDA(c, cudaStreamSynchronize(c->last_stream));
+    if (n) UPS_CUDA(c, cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+    return UPS_OK;
+}
+
+}  // extern "C"

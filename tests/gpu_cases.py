@@ -1,0 +1,120 @@
+"""Shared helpers of the GPU parity tests: run one seeded case through the CUDA
+library (via the C ABI binding) and through the FP64 oracle on the same
+float32-rounded inputs, and compare."""
+import numpy as np
+
+import oracle
+from paper_2505_22335_gb300 import binding as B
+from paper_2505_22335_gb300 import scenes
+
+CFG = oracle.RenderCfg()
+PIX_ATOL, PIX_RTOL = 1e-5, 1e-4      # forward pixels
+GRAD_RTOL = 2e-3                     # relative L2 of gradients
+MARGIN = 1e-4                        # pixels this close to a threshold are compared separately
+
+
+def r32(x):
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
+def round_dict(d):
+    return {k: r32(v) for k, v in d.items()}
+
+
+def round_cams(cams):
+    for c in cams:
+        c.T_cw = r32(c.T_cw)
+        c.t_norm = float(np.float32(c.t_norm))
+    return cams
+
+
+def split_images(img, cams, nf):
+    """Flat library images -> per-view dicts of numpy arrays."""
+    out = []
+    P = 0
+    col = img["color"].cpu().numpy().astype(np.float64)
+    dep = img["depth"].cpu().numpy().astype(np.float64)
+    fea = img["feat"].cpu().numpy().astype(np.float64) if nf else None
+    T = img["T"].cpu().numpy().astype(np.float64)
+    nc = img["n_contrib"].cpu().numpy()
+    for c in cams:
+        h, w = c.height, c.width
+        hw = h * w
+        out.append(dict(color=col[3 * P:3 * P + 3 * hw].reshape(3, h, w),
+                        depth=dep[P:P + hw].reshape(h, w),
+                        feat=(fea[nf * P:nf * P + nf * hw].reshape(nf, h, w) if nf else np.zeros((0, h, w))),
+                        T=T[P:P + hw].reshape(h, w), n_contrib=nc[P:P + hw].reshape(h, w)))
+        P += hw
+    return out
+
+
+def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01):
+    flagged = 0
+    total = 0
+    for gv, rv in zip(gpu_views, ref_views):
+        ok = rv["margin"] > MARGIN
+        flagged += int((~ok).sum())
+        total += ok.size
+        for k in ("color", "depth", "T") + (("feat",) if nf else ()):
+            a, r = gv[k], rv[k]
+            diff = np.abs(a - r)
+            tol = PIX_ATOL + PIX_RTOL * np.abs(r)
+            bad = (diff > tol) & np.broadcast_to(ok, diff.shape)
+            assert not bad.any(), (k, int(bad.sum()), float(diff[bad].max()))
+        assert np.array_equal(gv["n_contrib"][ok], rv["n_contrib"][ok])
+    assert flagged <= max_flag_frac * total, (flagged, total)
+    return flagged
+
+
+def rel_l2(a, r):
+    a = np.asarray(a, np.float64).reshape(-1)
+    r = np.asarray(r, np.float64).reshape(-1)
+    return float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-30))
+
+
+def assert_grad(name, a, r, tol=GRAD_RTOL):
+    e = rel_l2(a, r)
+    assert e < tol, (name, e)
+    return e
+
+
+def gauss_grads(grad, nf, sets):
+    mo = grad.mean_opacity.cpu().numpy().astype(np.float64)
+    sc = grad.scale.cpu().numpy().astype(np.float64)
+    qt = grad.quat.cpu().numpy().astype(np.float64)
+    co = grad.color.cpu().numpy().astype(np.float64)
+    fe = grad.feat.cpu().numpy().astype(np.float64)
+    return dict(mean=mo[..., :3], opacity=mo[..., 3], scale=sc[..., :3], quat=qt,
+                color=co[..., :3], feat=fe)
+
+
+def plain_case(seed, n, cams, nf, weighted, l2=False, lambda_scale=0.0, g=None):
+    """Plain Gaussians shared by all views: GPU forward+loss+backward vs oracle."""
+    if g is None:
+        g = scenes.plain_gaussians(seed, n, nf)
+    g = round_dict(g)
+    cams = round_cams(cams)
+    tg = [round_dict(t) for t in scenes.targets(seed + 1, cams, nf, weighted=weighted)]
+    lc = oracle.LossCfg(lambda_scale=lambda_scale, l2=l2)
+    R = B.Renderer(n_feat=nf, k=1)
+    gs = B.to_set(g)
+    img = R.forward(gs, cams)
+    loss, dimg = R.loss(img, B.targets_to_device(tg), lambda_scale=lambda_scale, l2=l2, g=gs)
+    sg = lambda_scale / (3.0 * n) if lambda_scale else 0.0
+    grad, d_pose = R.backward(dimg, B.GRAD_POSE | B.GRAD_GAUSS, scale_grad=sg)
+    L, ref, views, per_view = oracle.backward_plain(g, cams, tg, CFG, lc, nf)
+    return dict(R=R, g=g, gs=gs, cams=cams, tg=tg, img=img, loss=float(loss.item()),
+                grad=grad, d_pose=d_pose.cpu().numpy().astype(np.float64), L=L, ref=ref,
+                views=views, per_view=per_view)
+
+
+def check_plain(res, nf, grads=True):
+    gpu_views = split_images(res["img"], res["cams"], nf)
+    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf)
+    assert abs(res["loss"] - res["L"]) <= 1e-5 + 1e-4 * abs(res["L"]), (res["loss"], res["L"])
+    if not grads:
+        return
+    gg = gauss_grads(res["grad"], nf, 1)
+    for k in ("mean", "scale", "quat", "opacity", "color") + (("feat",) if nf else ()):
+        assert_grad(k, gg[k][0], res["ref"][k])
+    assert_grad("pose", res["d_pose"], res["ref"]["pose"])

@@ -1,0 +1,210 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Bars: tile lists and sort order bit-exact; forward pixels within 1e-5 absolute
++ 1e-4 relative (pixels with a visited pair within 1e-4 relative of the
+alpha_min / alpha_max / t_min thresholds are counted, not compared); gradients
+within 2e-3 relative L2 (atomic accumulation order is not deterministic).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_cases import (CFG, assert_grad, assert_pixels, check_plain, gauss_grads, plain_case,
+                       r32, rel_l2, round_cams, round_dict, split_images)
+from paper_2505_22335_gb300 import binding as B
+from paper_2505_22335_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+# ---------------------------------------------------------------------------
+# plain 3DGS (2,000 Gaussians, 160x120, identity pose, RGB + depth, L1)
+# ---------------------------------------------------------------------------
+
+def test_plain_2k_forward_backward():
+    g, cams = scenes.workload_plain_2k(0)
+    res = plain_case(0, 2000, cams, 0, weighted=False, g=g)
+    check_plain(res, 0)
+
+
+def _ambiguous(proj, cam, eps=1e-3):
+    """Gaussians whose tile rect is decided within eps px of a tile/image edge."""
+    ext = proj["extent"]
+    amb = np.zeros(len(ext), bool)
+    for lo, hi, lim in ((ext[:, 0], ext[:, 2], cam.width - 1), (ext[:, 1], ext[:, 3], cam.height - 1)):
+        for e in (lo, hi):
+            m = np.abs(e - np.round(e / 16) * 16) < eps
+            m |= np.abs(e) < eps
+            m |= np.abs(e - lim) < eps
+            amb |= m
+    return amb
+
+
+def test_plain_2k_tile_lists_and_sort_bit_exact():
+    g, cams = scenes.workload_plain_2k(0)
+    res = plain_case(0, 2000, cams, 0, weighted=False, g=g)
+    R, cam = res["R"], res["cams"][0]
+    gv = R.copy_buffer(0)
+    keys = R.copy_buffer(1)
+    ranges = R.copy_buffer(2).reshape(-1, 2)
+    xyzo = R.copy_buffer(3).reshape(-1, 4)
+    rect = R.copy_buffer(5).reshape(-1, 2)
+    # (i) the sort stage: the GPU's own keys through numpy's stable sort
+    inst_t, inst_z, inst_g = [], [], []
+    tiles_x = (cam.width + 15) // 16
+    for i in range(len(rect)):
+        x0, y0, x1, y1 = rect[i, 0] & 0xffff, rect[i, 0] >> 16, rect[i, 1] & 0xffff, rect[i, 1] >> 16
+        for ty in range(y0, y1 + 1):
+            for tx in range(x0, x1 + 1):
+                inst_t.append(ty * tiles_x + tx)
+                inst_z.append(np.float32(xyzo[i, 2]).view(np.uint32))
+                inst_g.append(i)
+    # Gaussians with count 0 have rect (0,0,0,0) which also encodes tile 0: drop
+    # them using the GPU's own instance total
+    inst_t, inst_z, inst_g = map(np.array, (inst_t, inst_z, inst_g))
+    valid_g = np.unique(gv)
+    keep = np.isin(inst_g, valid_g)
+    inst_t, inst_z, inst_g = inst_t[keep], inst_z[keep], inst_g[keep]
+    order = np.lexsort((inst_g, inst_z, inst_t))
+    assert len(order) == len(gv)
+    assert np.array_equal(gv, inst_g[order])
+    assert np.array_equal(keys, inst_t[order])
+    counts = np.bincount(inst_t, minlength=len(ranges))
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], counts)
+    # (ii) tile lists against the oracle's own projection and stable sort
+    pr = res["views"][0]["proj"]
+    lst, orng = oracle.tile_lists(pr, cam, CFG)
+    amb = _ambiguous(pr, cam)
+    n_diff = 0
+    for t in range(len(ranges)):
+        a = gv[ranges[t, 0]:ranges[t, 1]]
+        b = lst[orng[t, 0]:orng[t, 1]]
+        a = a[~amb[a]]
+        b = b[~amb[b]]
+        if not np.array_equal(a, b):
+            n_diff += 1
+    assert n_diff == 0
+    assert amb.sum() <= 5
+
+
+def test_multiview_ragged_feat16_weighted_l2():
+    """Three views of different (ragged) sizes, 16 feature channels, uncertainty weights."""
+    base = scenes.cameras(7, 3, 100, 70, 90.0)
+    cams = [base[0], base[1].scaled(0.5), scenes.Camera(40.0, 40.0, 16.5, 8.5, 33, 17, base[2].T_cw)]
+    res = plain_case(11, 3000, cams, 16, weighted=True, l2=True, lambda_scale=0.01)
+    check_plain(res, 16)
+
+
+def test_feat32_large_footprints():
+    cams = scenes.cameras(3, 2, 96, 64, 60.0)
+    g = scenes.plain_gaussians(5, 800, 32, scale_lo=0.02, scale_hi=0.15)
+    res = plain_case(5, 800, cams, 32, weighted=True, g=g)
+    check_plain(res, 32)
+
+
+def test_empty_and_offscreen_scene():
+    cams = scenes.cameras(0, 1, 48, 40, 50.0, identity=True)
+    g = scenes.plain_gaussians(1, 50, 16)
+    g["mean"][:, 2] = -1.0  # behind the camera: everything culled
+    res = plain_case(1, 50, cams, 16, weighted=False, g=g)
+    v = split_images(res["img"], res["cams"], 16)[0]
+    assert np.all(v["color"] == 0) and np.all(v["T"] == 1) and np.all(v["n_contrib"] == 0)
+    gg = gauss_grads(res["grad"], 16, 1)
+    assert all(np.all(gg[k] == 0) for k in ("mean", "scale", "quat", "opacity", "color"))
+    assert np.all(res["d_pose"] == 0)
+    assert res["R"].stats()["n_instances"] == 0
+
+
+def test_single_gaussian_peak_alpha():
+    cams = scenes.cameras(0, 1, 64, 48, 100.0, identity=True)
+    g = dict(mean=np.array([[0.0, 0.0, 2.0]]), scale=np.full((1, 3), 0.05),
+             quat=np.array([[1.0, 0, 0, 0]]), opacity=np.array([0.8]),
+             color=np.array([[1.0, 0.5, 0.25]]), feat=np.zeros((1, 16)))
+    res = plain_case(2, 1, cams, 16, weighted=False, g=g)
+    v = split_images(res["img"], res["cams"], 16)[0]
+    assert abs(v["color"][0, 24, 32] - 0.8) < 1e-6
+    assert abs(v["T"][24, 32] - 0.2) < 1e-6
+    check_plain(res, 16)
+
+
+# ---------------------------------------------------------------------------
+# anchor decode + render (Eq. 8-9), FP32 decode
+# ---------------------------------------------------------------------------
+
+def anchor_case(seed, A, K, nf, cams, weighted=True, lambda_scale=0.01, mask=B.GRAD_ALL):
+    import torch
+    anc = round_dict(scenes.anchors(seed, A, K))
+    mlp = round_dict(scenes.mlp_weights(seed + 1, K, nf, bias_sigma=0.05))
+    cams = round_cams(cams)
+    tg = [round_dict(t) for t in scenes.targets(seed + 2, cams, nf, weighted=weighted)]
+    R = B.Renderer(n_feat=nf, k=K)
+    ad, md = B.anchors_to_device(anc, mlp)
+    g = R.decode(ad, md, cams)
+    img = R.forward(g, cams)
+    loss, dimg = R.loss(img, B.targets_to_device(tg), lambda_scale=lambda_scale, g=g)
+    V, N = len(cams), A * K
+    grad, d_pose = R.backward(dimg, B.GRAD_ALL, scale_grad=lambda_scale / (3.0 * V * N))
+    d_mlp = {k: torch.zeros_like(v) for k, v in md.items()}
+    d_anc = {k: torch.zeros_like(v) for k, v in ad.items()}
+    R.decode_backward(ad, md, cams, grad, mask, d_mlp, d_anc, d_pose)
+    torch.cuda.synchronize()
+    lc = oracle.LossCfg(lambda_scale=lambda_scale)
+    L, ref, views, per_view = oracle.backward_anchor(anc, mlp, cams, tg, CFG, lc, K, nf)
+    return dict(R=R, anc=anc, mlp=mlp, cams=cams, g=g, img=img, loss=float(loss.item()), L=L,
+                ref=ref, views=views, per_view=per_view, grad=grad,
+                d_pose=d_pose.cpu().numpy().astype(np.float64),
+                d_mlp={k: v.cpu().numpy().astype(np.float64) for k, v in d_mlp.items()},
+                d_anc={k: v.cpu().numpy().astype(np.float64) for k, v in d_anc.items()})
+
+
+def check_anchor(res, nf):
+    V = len(res["cams"])
+    # decode outputs per view
+    mo = res["g"].mean_opacity.cpu().numpy().astype(np.float64)
+    sc = res["g"].scale.cpu().numpy().astype(np.float64)
+    qt = res["g"].quat.cpu().numpy().astype(np.float64)
+    co = res["g"].color.cpu().numpy().astype(np.float64)
+    fe = res["g"].feat.cpu().numpy().astype(np.float64)
+    for v in range(V):
+        rg = res["views"][v]["g"]
+        np.testing.assert_allclose(mo[v, :, :3], rg["mean"], atol=1e-6, rtol=1e-6)
+        np.testing.assert_allclose(mo[v, :, 3], rg["opacity"], atol=2e-6, rtol=1e-5)
+        np.testing.assert_allclose(sc[v, :, :3], rg["scale"], atol=1e-7, rtol=1e-5)
+        np.testing.assert_allclose(qt[v], rg["quat"], atol=1e-5, rtol=1e-5)
+        np.testing.assert_allclose(co[v, :, :3], rg["color"], atol=2e-6, rtol=1e-5)
+        if nf:
+            np.testing.assert_allclose(fe[v], rg["feat"], atol=1e-5, rtol=1e-5)
+    gpu_views = split_images(res["img"], res["cams"], nf)
+    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf)
+    assert abs(res["loss"] - res["L"]) <= 1e-5 + 1e-4 * abs(res["L"]), (res["loss"], res["L"])
+    # per-view decoded-Gaussian gradients
+    gg = gauss_grads(res["grad"], nf, V)
+    for k in ("mean", "scale", "quat", "opacity", "color") + (("feat",) if nf else ()):
+        ref = np.stack([pv["g3d"][k] for pv in res["per_view"]])
+        assert_grad(k, gg[k], ref)
+    for k in ("w1", "b1", "w2", "b2"):
+        assert_grad(k, res["d_mlp"][k], res["ref"][k])
+    for k in ("pos", "feat", "offsets", "scaling"):
+        assert_grad("anchor_" + k, res["d_anc"][k], res["ref"][k])
+    assert_grad("pose", res["d_pose"], res["ref"]["pose"])
+
+
+def test_anchor_decode_render_small():
+    cams = scenes.cameras(21, 2, 160, 120, 150.0)
+    res = anchor_case(21, 600, 10, 16, cams)
+    check_anchor(res, 16)
+
+
+def test_anchor_decode_10k_anchors_640x480():
+    """10k anchors x K=10 (100k Gaussians), 16-ch features, 640x480, full backward."""
+    cams = scenes.cameras(0, 1, 640, 480, 600.0)
+    res = anchor_case(0, 10000, 10, 16, cams)
+    check_anchor(res, 16)
