@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the fwd+bwd render path (one JSON line on rank 0).
+
+Workload (default): mapping batch of 100k anchors x K=10 (1M Gaussians), 8
+keyframes at 640x480 (fx = fy = 600) on a 3 m arc, RGB + depth + 16-channel
+feature map, L1 loss weighted by a per-pixel uncertainty map U[0,1], mean-scale
+term 0.01; FP32 decode.  One step = decode -> project -> depth sort -> tile
+instances -> tile sort -> ranges -> blend -> loss -> blend backward ->
+projection backward -> decode backward (all through the C ABI).
+
+Metric: fwd+bwd Mpixel/s = views x H x W / step time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(the path has no exchange step here), time = max over ranks, value = all
+ranks' pixels / that time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpixel/s at 1M Gaussians 640x480"
+UNIT = "Mpixel/s"
+
+WORKLOADS = {
+    # name: anchors, K, n_feat, views, width, height, fx
+    "mapping_100k_anchors_x10_8x640x480": dict(A=100_000, K=10, NF=16, V=8, W=640, H=480, fx=600.0),
+    "decode_render_10k_anchors_x10_640x480": dict(A=10_000, K=10, NF=16, V=1, W=640, H=480, fx=600.0),
+}
+DEFAULT_WORKLOAD = "mapping_100k_anchors_x10_8x640x480"
+LAMBDA_SCALE = 0.01
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(smax)) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# the workload on the device
+# ---------------------------------------------------------------------------
+
+def make_inputs(wl, seed=0):
+    from paper_2505_22335_gb300 import scenes
+    anc = scenes.anchors(seed, wl["A"], wl["K"])
+    mlp = scenes.mlp_weights(seed + 1000, wl["K"], wl["NF"])
+    cams = scenes.cameras(seed, wl["V"], wl["W"], wl["H"], wl["fx"], identity=(wl["V"] == 1))
+    tg = scenes.targets(seed + 1, cams, wl["NF"], weighted=True)
+    return anc, mlp, cams, tg
+
+
+class Step:
+    """Preallocated buffers + one fwd+bwd step through the C ABI."""
+
+    def __init__(self, wl, anc, mlp, cams, tg, device):
+        import torch
+        from paper_2505_22335_gb300 import binding as B
+        self.B = B
+        self.wl = wl
+        self.cams = cams
+        self.R = B.Renderer(n_feat=wl["NF"], k=wl["K"], device=device)
+        self.ad, self.md = B.anchors_to_device(anc, mlp)
+        self.tgt = B.targets_to_device(tg)
+        V, N = len(cams), wl["A"] * wl["K"]
+        self.g = B.GaussianSet.empty(V, N, wl["NF"], True)
+        self.img = self.R.alloc_images(cams)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.dimg = dict(color=torch.zeros_like(self.img["color"]), depth=torch.zeros_like(self.img["depth"]),
+                         feat=torch.zeros_like(self.img["feat"]))
+        self.grad = B.GaussianSet.empty(V, N, wl["NF"], True)
+        self.d_pose = torch.zeros(V, 6, dtype=torch.float32, device="cuda")
+        self.d_mlp = {k: torch.zeros_like(v) for k, v in self.md.items()}
+        self.d_anc = {k: torch.zeros_like(v) for k, v in self.ad.items()}
+        self.scale_grad = LAMBDA_SCALE / (3.0 * V * N)
+
+    def run(self):
+        B, R = self.B, self.R
+        R.decode(self.ad, self.md, self.cams, out=self.g)
+        R.forward(self.g, self.cams, out=self.img)
+        R.loss(self.img, self.tgt, lambda_scale=LAMBDA_SCALE, g=self.g, loss_out=self.loss,
+               grad_out=self.dimg)
+        R.backward(self.dimg, B.GRAD_ALL, scale_grad=self.scale_grad, grad=self.grad, d_pose=self.d_pose)
+        for v in self.d_mlp.values():
+            v.zero_()
+        for v in self.d_anc.values():
+            v.zero_()
+        R.decode_backward(self.ad, self.md, self.cams, self.grad, B.GRAD_ALL, self.d_mlp, self.d_anc,
+                          self.d_pose)
+
+
+def processed_instances(img, cams):
+    """Sum over tiles of the longest blended prefix (entries the blend kernels read)."""
+    nc = img["n_contrib"].cpu().numpy()
+    total = 0
+    P = 0
+    for c in cams:
+        a = nc[P:P + c.width * c.height].reshape(c.height, c.width)
+        ty, tx = (c.height + 15) // 16, (c.width + 15) // 16
+        pad = np.zeros((ty * 16, tx * 16), a.dtype)
+        pad[:c.height, :c.width] = a
+        total += int(pad.reshape(ty, 16, tx, 16).max(axis=(1, 3)).sum())
+        P += c.width * c.height
+    return total
+
+
+def algorithmic(wl, stats, proc_inst):
+    """Algorithmic bytes (HBM-bound stages) and FP32 flops (ALU-bound stages) per launch."""
+    A, K, NF, V = wl["A"], wl["K"], wl["NF"], wl["V"]
+    N = A * K
+    GV = V * N
+    P = stats["n_pixels"]
+    I = stats["n_instances"]
+    anc_b = 12 + 4 * 32 + 12 * K + 12          # pos, feat, offsets, scaling
+    rec3d = 64 + 4 * NF                         # mean|o, scale, quat, colour, features
+    n_out = K * (11 + NF)
+    row_fwd = 2 * (38 * 128 + 32 * n_out)       # flops per (anchor, view) row
+    inst_b = 16 + 16 + 16 + 4 * NF + 4         # xyzo, conic, colour, features, id
+    pix_out = 4 * (3 + 1 + NF + 1) + 4
+    passes = lambda bits: (bits + 7) // 8
+    return {
+        "decode_fwd": dict(bytes=A * anc_b + GV * rec3d, flops=A * V * row_fwd),
+        "project": dict(bytes=GV * (48 + 56)),
+        "depth_sort": dict(bytes=passes(32 + (math.ceil(math.log2(V)) if V > 1 else 0)) * GV * 32),
+        "offsets": dict(bytes=GV * (4 + 4 + 4 + 8)),
+        "emit": dict(bytes=GV * 24 + I * 8),
+        "tile_sort": dict(bytes=passes(stats["key_bits"]) * I * 20),
+        "ranges": dict(bytes=I * 8 + stats["n_tiles"] * 8),
+        "composite_fwd": dict(bytes=proc_inst * inst_b + P * pix_out),
+        "loss": dict(bytes=P * 4 * (3 * (3 + 1 + NF) + 1)),
+        "composite_bwd": dict(bytes=proc_inst * inst_b + P * (pix_out + 4 * (3 + 1 + NF)) + GV * 4 * (12 + NF)),
+        "project_bwd": dict(bytes=GV * (48 + 4 * (12 + NF) + rec3d)),
+        "decode_bwd": dict(bytes=A * anc_b * 2 + GV * rec3d, flops=A * V * 3 * row_fwd),
+    }
+
+
+ALU_STAGES = {"decode_fwd", "decode_bwd", "composite_fwd", "composite_bwd"}
+
+
+def run_ours(args, wl_name):
+    import torch
+    import torch.distributed as dist
+    from paper_2505_22335_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[wl_name]
+    anc, mlp, cams, tg = make_inputs(wl, seed=0)
+    st = Step(wl, anc, mlp, cams, tg, local)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        st.run()
+    torch.cuda.synchronize()
+    stats = st.R.stats()
+    st.R.profile_read()  # reset counters
+    st.R.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    prof, launches = st.R.profile_read()
+    st.R.profile(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    pix = sum(c.width * c.height for c in cams)
+    value = world * pix / (ms_max / 1e3) / 1e6
+    proc = processed_instances(st.img, cams)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, st, anc, mlp, tg, world)
+
+    if rank == 0:
+        peaks = load_peaks()
+        alg = algorithmic(wl, stats, proc)
+        stages = {k: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
+                  for k, v in prof.items()}
+        dom = max(prof, key=lambda k: prof[k][0])
+        avg_ms = prof[dom][0] / prof[dom][1]
+        roof = roofline(dom, alg, avg_ms, peaks)
+        cpu = cpu_baseline(wl, anc, mlp, cams, tg) if not args.no_cpu else None
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded anchors, MLP weights, arc poses, targets)",
+            "config": {"workload": wl_name, "anchors": wl["A"], "k": wl["K"], "gaussians": wl["A"] * wl["K"],
+                       "views": wl["V"], "width": wl["W"], "height": wl["H"], "n_feat": wl["NF"],
+                       "decode": "fp32", "loss": "weighted l1 + 0.01 mean scale",
+                       "l2_policy": "inputs larger than L2 (decoded set alone is %.2f GB per step)"
+                                    % (wl["V"] * wl["A"] * wl["K"] * (64 + 4 * wl["NF"]) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "gaussians_per_s": round(world * wl["V"] * wl["A"] * wl["K"] / (ms_max / 1e3), 1),
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roof,
+            "stages": stages,
+            "counters": dict(stats, processed_instances=proc),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline(stage, alg, avg_ms, peaks):
+    a = alg.get(stage, {})
+    if stage in ALU_STAGES and "flops" in a:
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+        ach = a["flops"] / (avg_ms / 1e3) / 1e12
+        return dict(kernel=stage, bound="alu", achieved=round(ach, 3), peak=round(peak, 2), unit="TFLOP/s",
+                    frac=round(ach / peak, 4), traffic=None, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    avg_launch_ms=round(avg_ms, 4), algorithmic_flops=a["flops"],
+                    algorithmic_bytes=a.get("bytes"))
+    ach = a.get("bytes", 0) / (avg_ms / 1e3) / 1e9
+    return dict(kernel=stage, bound="hbm", achieved=round(ach, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=round(ach / peaks["hbm_gbs"], 4), traffic=None,
+                peak_source=peaks["source"], avg_launch_ms=round(avg_ms, 4), algorithmic_bytes=a.get("bytes"))
+
+
+def run_e2e(args, st, anc, mlp, tg, world):
+    """Same step through the public API, inputs copied from pinned host memory
+    and the loss + pose gradient read back, every step, inside the timed region."""
+    import torch
+    host = {}
+    for k in ("pos", "feat", "offsets", "scaling"):
+        host["a_" + k] = torch.tensor(np.ascontiguousarray(anc[k]), dtype=torch.float32).pin_memory()
+    for k in ("w1", "b1", "w2", "b2"):
+        host["m_" + k] = torch.tensor(np.ascontiguousarray(mlp[k]), dtype=torch.float32).pin_memory()
+    for k in ("color", "depth", "feat", "weight"):
+        host["t_" + k] = torch.tensor(np.concatenate([t[k].reshape(-1) for t in tg]),
+                                      dtype=torch.float32).pin_memory()
+    out_loss = torch.zeros(1, dtype=torch.float32).pin_memory()
+    out_pose = torch.zeros(st.d_pose.shape, dtype=torch.float32).pin_memory()
+    dev = {}
+    for k, v in host.items():
+        pre, name = k.split("_", 1)
+        dev[k] = st.ad[name] if pre == "a" else st.md[name] if pre == "m" else st.tgt[name]
+    h2d = sum(v.numel() * 4 for v in host.values())
+    d2h = out_loss.numel() * 4 + out_pose.numel() * 4
+    stream = torch.cuda.current_stream()
+
+    def one():
+        for k, v in host.items():
+            dev[k].copy_(v, non_blocking=True)
+        st.run()
+        out_loss.copy_(st.loss, non_blocking=True)
+        out_pose.copy_(st.d_pose, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(n):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    pix = sum(c.width * c.height for c in st.cams)
+    return dict(value=round(world * pix / (ms / 1e3) / 1e6, 3), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(d2h), ms_per_step=round(ms, 4), steps=n)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, anc, mlp, cams, tg, window):
+    """FP64 oracle fwd+bwd of one view (optionally a centred window of it) with
+    every anchor decoded; returns (pixels, seconds)."""
+    import oracle
+    from paper_2505_22335_gb300 import scenes
+    c = cams[0]
+    t = tg[0]
+    if window is not None:
+        ww, hh = window
+        x0, y0 = (c.width - ww) // 2, (c.height - hh) // 2
+        c = scenes.Camera(c.fx, c.fy, c.cx - x0, c.cy - y0, ww, hh, c.T_cw, c.t_norm)
+        t = {k: (v[..., y0:y0 + hh, x0:x0 + ww]) for k, v in t.items()}
+    t0 = time.perf_counter()
+    oracle.backward_anchor(anc, mlp, [c], [t], oracle.RenderCfg(),
+                           oracle.LossCfg(lambda_scale=LAMBDA_SCALE), wl["K"], wl["NF"])
+    return c.width * c.height, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, anc, mlp, cams, tg):
+    import oracle
+    pix, sec = oracle_sample(wl, anc, mlp, cams, tg, None)
+    return dict(value=round(pix / sec / 1e6, 5), unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"one {cams[0].width}x{cams[0].height} view of the {wl['V']}-view batch, all "
+                       f"{wl['A']} anchors decoded, FP64 fwd+bwd ({sec:.1f} s)")
+
+
+def run_reference(args, wl_name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[wl_name]
+    anc, mlp, cams, tg = make_inputs(wl, seed=0)
+    n = args.steps + args.warmup
+    window = (640, 480) if n <= 12 else (320, 240) if n <= 30 else (160, 120)
+    window = (min(window[0], wl["W"]), min(window[1], wl["H"]))
+    for _ in range(args.warmup):
+        oracle_sample(wl, anc, mlp, cams, tg, window)
+    tot_pix, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        p, s = oracle_sample(wl, anc, mlp, cams, tg, window)
+        tot_pix += p
+        tot_s += s
+    value = tot_pix / tot_s / 1e6
+    sample = (f"{window[0]}x{window[1]} centre window of one view of the {wl['V']}-view batch per step, "
+              f"all {wl['A']} anchors decoded, FP64 fwd+bwd")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot_s / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl_name, "anchors": wl["A"], "k": wl["K"], "views": wl["V"],
+                       "width": wl["W"], "height": wl["H"], "n_feat": wl["NF"]},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        import oracle
+        oracle.build()
+        run_reference(args, args.workload)
+        return
+    from paper_2505_22335_gb300 import build as _b
+    _b.build()
+    import oracle
+    oracle.build()
+    run_ours(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -276,6 +276,16 @@ ups_status ups_get_stats(ups_ctx *ctx, ups_stats *out);
  * Returns the buffer size in bytes through *size (dst may be NULL). */
 ups_status ups_copy_buffer(ups_ctx *ctx, int which, void *dst, size_t bytes, size_t *size);
 
+/* Stage profiler.  When enabled, every stage (one or more kernels) of the
+ * calls above is bracketed by CUDA events recorded on the call's stream.
+ * ups_profile_read synchronises on those events and writes a JSON object
+ * {"stage": [total_ms, calls], ...} into buf (NUL-terminated; UPS_ERR_ARG if
+ * len is too small), stores the number of kernels launched since the last
+ * read in *launches (may be NULL; counted whether or not profiling is on), and
+ * resets both. */
+ups_status ups_profile_enable(ups_ctx *ctx, int on);
+ups_status ups_profile_read(ups_ctx *ctx, char *buf, size_t len, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,7 +73,8 @@ class Stats(C.Structure):
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted",
-           "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer"]
+           "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
+           "ups_profile_enable", "ups_profile_read"]
 
 _lib = None
 
@@ -111,6 +112,8 @@ def load():
                                       C.POINTER(Anchors), _p, _p]
     L.ups_get_stats.argtypes = [_p, C.POINTER(Stats)]
     L.ups_copy_buffer.argtypes = [_p, _i, _p, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.ups_profile_enable.argtypes = [_p, _i]
+    L.ups_profile_read.argtypes = [_p, C.c_char_p, C.c_size_t, C.POINTER(_ll)]
     _lib = L
     return L
 
@@ -307,6 +310,17 @@ class Renderer:
         s = Stats()
         self._check(self._L.ups_get_stats(self._h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def profile(self, on=True):
+        self._check(self._L.ups_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        """-> ({stage: (total_ms, calls)}, kernel launches since the last read)."""
+        import json
+        buf = C.create_string_buffer(8192)
+        n = _ll(0)
+        self._check(self._L.ups_profile_read(self._h, buf, len(buf), C.byref(n)))
+        return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}, int(n.value)
 
     def copy_buffer(self, which):
         size = C.c_size_t(0)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -95,6 +96,18 @@ struct ups_ctx {
     SortScratch sort;
     uint32_t *dval_sorted = nullptr, *ikey_sorted = nullptr, *ival_sorted = nullptr;
     uint64_t *h_total = nullptr;  // pinned
+    // stage profiler (CUDA events on the launch stream) and kernel-launch count
+    bool prof = false;
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<double, long long>> acc;
+    long long launches = 0;
+    const char *cur_name = nullptr;
+    cudaEvent_t cur_a = nullptr;
 };
 
 namespace {
@@ -121,6 +134,40 @@ ups_status cuda_fail(ups_ctx *c, cudaError_t e, const char *where) {
     } while (0)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+cudaEvent_t ev_get(ups_ctx *c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Stage timing: begin/end bracket one stage (one or more kernels) on stream st;
+// `kernels` is the number of kernel launches of the stage.
+void stage_begin(ups_ctx *c, const char *name, cudaStream_t st) {
+    if (!c->prof) return;
+    c->cur_name = name;
+    c->cur_a = ev_get(c);
+    cudaEventRecord(c->cur_a, st);
+}
+
+void stage_end(ups_ctx *c, cudaStream_t st, long long kernels) {
+    c->launches += kernels;
+    if (!c->prof || !c->cur_a) return;
+    cudaEvent_t b = ev_get(c);
+    cudaEventRecord(b, st);
+    c->pending.push_back({c->cur_name, c->cur_a, b});
+    c->cur_a = nullptr;
+}
+
+long long radix_kernels(size_t n, int bits) {
+    if (n <= 1 || bits <= 0) return 0;
+    return (long long)((bits + 7) / 8) * 5;  // histogram + 3 scan kernels + scatter per pass
+}
 
 ups_status build_views(ups_ctx *c, const ups_camera *cams, int n_views, ViewTable &vt,
                        size_t &n_pix, int &max_hw) {
@@ -258,6 +305,11 @@ ups_status ups_destroy(ups_ctx *c) {
                       &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->sort.hist};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
+    for (auto &r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     delete c;
     return UPS_OK;
 }
@@ -286,7 +338,9 @@ ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp 
     if ((s = set_device(c)) != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
+    stage_begin(c, "decode_fwd", st);
     UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->num_sms, st));
+    stage_end(c, st, 1);
     return UPS_OK;
 }
 
@@ -324,18 +378,24 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     UPS_CUDA(c, c->scan_scr.reserve(scan_scratch_bytes(total)));
     UPS_CUDA(c, c->ranges.reserve((size_t)vt.total_tiles * sizeof(uint2)));
 
+    stage_begin(c, "project", st);
     UPS_CUDA(c, launch_project(vt, c->bp, c->N, c->per_view, (int)total, *g, c->xyzo.as<float4>(),
                                c->conic.as<float4>(), c->rect.as<uint2>(), c->count.as<uint32_t>(),
                                c->dkey0.as<uint64_t>(), c->dval0.as<uint32_t>(), st));
+    stage_end(c, st, 1);
     // (view, depth) order of the Gaussian-views
     uint64_t *dk = c->dkey0.as<uint64_t>(), *dk_alt = c->dkey1.as<uint64_t>();
     uint32_t *dv = c->dval0.as<uint32_t>(), *dv_alt = c->dval1.as<uint32_t>();
     int vbits = bits_for((size_t)n_views);
+    stage_begin(c, "depth_sort", st);
     UPS_CUDA(c, radix_sort_u64(&dk, &dk_alt, &dv, &dv_alt, total, 32 + vbits, c->sort, st));
+    stage_end(c, st, radix_kernels(total, 32 + vbits));
     c->dval_sorted = dv;
+    stage_begin(c, "offsets", st);
     UPS_CUDA(c, launch_gather_counts(dv, c->count.as<uint32_t>(), c->cnt_sorted.as<uint32_t>(), (int)total, st));
     UPS_CUDA(c, exclusive_scan_u32_u64(c->cnt_sorted.as<uint32_t>(), c->off.as<uint64_t>(), total,
                                        c->scan_scr.ptr, st));
+    stage_end(c, st, 4);
     UPS_CUDA(c, cudaMemcpyAsync(c->h_total, c->off.as<uint64_t>() + total, sizeof(uint64_t),
                                 cudaMemcpyDeviceToHost, st));
     UPS_CUDA(c, cudaStreamSynchronize(st));
@@ -348,17 +408,25 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     UPS_CUDA(c, c->ival1.reserve(std::max<size_t>(n_inst, 1) * sizeof(uint32_t)));
     uint32_t *ik = c->ikey0.as<uint32_t>(), *ik_alt = c->ikey1.as<uint32_t>();
     uint32_t *iv = c->ival0.as<uint32_t>(), *iv_alt = c->ival1.as<uint32_t>();
+    stage_begin(c, "emit", st);
     UPS_CUDA(c, launch_emit(vt, c->N, (int)total, dv, c->off.as<uint64_t>(), c->rect.as<uint2>(), ik, iv, st));
+    stage_end(c, st, 1);
     // stable bucket by (view, tile): depth order is kept inside each tile
     c->key_bits = bits_for((size_t)vt.total_tiles);
+    stage_begin(c, "tile_sort", st);
     UPS_CUDA(c, radix_sort_u32(&ik, &ik_alt, &iv, &iv_alt, n_inst, c->key_bits, c->sort, st));
+    stage_end(c, st, radix_kernels(n_inst, c->key_bits));
     c->ikey_sorted = ik;
     c->ival_sorted = iv;
+    stage_begin(c, "ranges", st);
     UPS_CUDA(c, cudaMemsetAsync(c->ranges.ptr, 0, (size_t)vt.total_tiles * sizeof(uint2), st));
     UPS_CUDA(c, launch_ranges(ik, (uint32_t)n_inst, c->ranges.as<uint2>(), st));
+    stage_end(c, st, n_inst ? 1 : 0);
+    stage_begin(c, "composite_fwd", st);
     UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
                                      iv, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                      reinterpret_cast<const float4 *>(g->color), g->feat, *out, st));
+    stage_end(c, st, 1);
     c->g_in = *g;
     c->img = *out;
     c->have_fwd = true;
@@ -379,6 +447,7 @@ ups_status ups_loss_weighted(ups_ctx *c, const ups_images *img, const ups_target
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
+    stage_begin(c, "loss", st);
     UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
     float inv_norm = (float)(1.0 / (double)c->n_pix);
     UPS_CUDA(c, launch_loss(c->vt, nf, c->max_hw, lcfg->lambda_color, lcfg->lambda_depth,
@@ -388,7 +457,9 @@ ups_status ups_loss_weighted(ups_ctx *c, const ups_images *img, const ups_target
         size_t n = sets * (size_t)g->n;
         UPS_CUDA(c, launch_scale_mean(reinterpret_cast<const float4 *>(g->scale), n,
                                       (float)(lcfg->lambda_scale / (3.0 * (double)n)), loss_dev, st));
+        c->launches += 1;
     }
+    stage_end(c, st, 1);
     return UPS_OK;
 }
 
@@ -413,10 +484,12 @@ ups_status ups_render_backward(ups_ctx *c, const ups_image_grads *dL, unsigned m
     const size_t rec = (size_t)g2_stride(nf);
     UPS_CUDA(c, c->g2.reserve(c->total_gv * rec * sizeof(float)));
     UPS_CUDA(c, cudaMemsetAsync(c->g2.ptr, 0, c->total_gv * rec * sizeof(float), st));
+    stage_begin(c, "composite_bwd", st);
     UPS_CUDA(c, launch_composite_bwd(c->vt, c->bp, nf, c->N, c->per_view, c->ranges.as<uint2>(),
                                      c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                      reinterpret_cast<const float4 *>(c->g_in.color), c->g_in.feat,
                                      c->img.T, c->img.n_contrib, *dL, c->g2.as<float>(), st));
+    stage_end(c, st, 1);
     if (mask & UPS_GRAD_POSE)
         UPS_CUDA(c, cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * c->vt.n, st));
     if ((mask & UPS_GRAD_GAUSS) && !c->per_view) {
@@ -427,9 +500,12 @@ ups_status ups_render_backward(ups_ctx *c, const ups_image_grads *dL, unsigned m
         UPS_CUDA(c, cudaMemsetAsync(grad->color, 0, n * sizeof(float4), st));
         if (nf) UPS_CUDA(c, cudaMemsetAsync(grad->feat, 0, n * nf * sizeof(float), st));
     }
-    if (mask & (UPS_GRAD_POSE | UPS_GRAD_GAUSS))
+    if (mask & (UPS_GRAD_POSE | UPS_GRAD_GAUSS)) {
+        stage_begin(c, "project_bwd", st);
         UPS_CUDA(c, launch_project_bwd(c->vt, c->bp, c->N, c->per_view, (int)c->total_gv, nf, mask,
                                        scale_grad, c->g_in, c->g2.as<float>(), grad, d_pose, st));
+        stage_end(c, st, 1);
+    }
     c->have_bwd = true;
     return UPS_OK;
 }
@@ -459,8 +535,10 @@ ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp
     if ((s = set_device(c)) != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
+    stage_begin(c, "decode_bwd", st);
     UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp,
                                   d_anc, d_pose, c->num_sms, st));
+    stage_end(c, st, 1);
     return UPS_OK;
 }
 
@@ -513,6 +591,47 @@ ups_status ups_copy_buffer(ups_ctx *c, int which, void *dst, size_t bytes, size_
     UPS_CUDA(c, cudaStreamSynchronize(c->last_stream));
     if (n) UPS_CUDA(c, cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
     return UPS_OK;
+}
+
+ups_status ups_profile_enable(ups_ctx *c, int on) {
+    if (!c) return UPS_ERR_ARG;
+    c->prof = on != 0;
+    return UPS_OK;
+}
+
+ups_status ups_profile_read(ups_ctx *c, char *buf, size_t len, long long *launches) {
+    if (!c) return UPS_ERR_ARG;
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    for (auto &r : c->pending) {
+        UPS_CUDA(c, cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        UPS_CUDA(c, cudaEventElapsedTime(&ms, r.a, r.b));
+        auto &a = c->acc[r.name];
+        a.first += ms;
+        a.second += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+    std::string js = "{";
+    bool first = true;
+    for (auto &kv : c->acc) {
+        char tmp[160];
+        std::snprintf(tmp, sizeof(tmp), "%s\"%s\": [%.6f, %lld]", first ? "" : ", ", kv.first.c_str(),
+                      kv.second.first, kv.second.second);
+        js += tmp;
+        first = false;
+    }
+    js += "}";
+    if (buf && len) {
+        std::strncpy(buf, js.c_str(), len - 1);
+        buf[len - 1] = 0;
+    }
+    if (launches) *launches = c->launches;
+    c->acc.clear();
+    c->launches = 0;
+    return js.size() < len ? UPS_OK : fail(c, UPS_ERR_ARG, "profile buffer too small");
 }
 
 }  // extern "C"
