@@ -286,6 +286,35 @@ ups_status ups_copy_buffer(ups_ctx *ctx, int which, void *dst, size_t bytes, siz
 ups_status ups_profile_enable(ups_ctx *ctx, int on);
 ups_status ups_profile_read(ups_ctx *ctx, char *buf, size_t len, long long *launches);
 
+/* ---------------------------------------------------------------------- */
+/* allocation-free forward                                                */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point.
+ *
+ * Same result as ups_render_forward (same kernels), for callers that cannot
+ * allocate GPU memory: a tracking front end running at camera rate inside a
+ * fixed memory budget cannot afford cudaMalloc/cudaFree (they synchronise the
+ * device and can stall for milliseconds) and may not grow its footprint, so it
+ * cannot use a ups_ctx, whose scratch grows on demand.  This call needs no
+ * context and allocates nothing: its scratch is one static device array of
+ * about 14 MB inside the library, held by every GPU that loads the library
+ * until the process exits.
+ *  cfg       thresholds and n_feat (k, feat_dim, hidden, decode_bf16 unused)
+ *  g, cams, n_views, out   as for ups_render_forward; runs on the CURRENT
+ *            device, stream-ordered on `stream`, and synchronises it once
+ * Limits, checked before any kernel runs (UPS_ERR_CAPACITY, message via
+ * ups_last_error(NULL)): n * n_views <= 65536, <= 8192 16x16 tiles over all
+ * views, <= 524288 tile instances.  No backward state is kept.
+ * The static array is shared by every call on a device and keeps the last
+ * call's contents (each call writes or clears what it reads); calls that
+ * overlap on the GPU race on it and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address; make that
+ * first call before any stream capture. */
+ups_status ups_render_forward_static(const ups_config *cfg, const ups_gaussians *g,
+                                     const ups_camera *cams, int n_views, ups_images *out,
+                                     ups_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,7 +74,7 @@ class Stats(C.Structure):
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
-           "ups_profile_enable", "ups_profile_read"]
+           "ups_profile_enable", "ups_profile_read", "ups_render_forward_static"]
 
 _lib = None
 
@@ -114,6 +114,8 @@ def load():
     L.ups_copy_buffer.argtypes = [_p, _i, _p, C.c_size_t, C.POINTER(C.c_size_t)]
     L.ups_profile_enable.argtypes = [_p, _i]
     L.ups_profile_read.argtypes = [_p, C.c_char_p, C.c_size_t, C.POINTER(_ll)]
+    L.ups_render_forward_static.argtypes = [C.POINTER(Config), C.POINTER(Gaussians), C.POINTER(Camera),
+                                            _i, C.POINTER(Images), _p]
     _lib = L
     return L
 
@@ -332,6 +334,26 @@ class Renderer:
             self._check(self._L.ups_copy_buffer(self._h, which, arr.ctypes.data_as(_p), size.value,
                                                 None))
         return arr
+
+
+def render_forward_static(g: GaussianSet, cams, out, n_feat, stream=None, **overrides):
+    """Allocation-free forward (no context): scratch lives in a static device
+    array of the library; `out` must be preallocated (see Renderer.alloc_images)."""
+    L = load()
+    cfg = Config()
+    L.ups_config_default(C.byref(cfg))
+    cfg.n_feat = n_feat
+    for key, val in overrides.items():
+        setattr(cfg, key, val)
+    ci = Images(_ptr(out["color"]), _ptr(out["depth"]), _ptr(out["feat"]) if n_feat else None,
+                _ptr(out["T"]), _ptr(out["n_contrib"]))
+    cg = g.c()
+    cc = make_cameras(cams)
+    st = L.ups_render_forward_static(C.byref(cfg), C.byref(cg), cc, len(cams), C.byref(ci),
+                                     _stream(stream))
+    if st != UPS_OK:
+        raise UpsError(st, L.ups_last_error(None).decode())
+    return out
 
 
 def version() -> str:

@@ -239,6 +239,11 @@ ups_status set_device(ups_ctx *c) {
 
 }  // namespace
 
+namespace ups {
+// Message returned by ups_last_error(NULL) (calls made without a context).
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace ups
+
 extern "C" {
 
 void ups_config_default(ups_config *cfg) {

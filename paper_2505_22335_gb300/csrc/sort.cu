@@ -263,7 +263,51 @@ cudaError_t radix_impl(K **key_io, K **key_alt, uint32_t **val_io, uint32_t **va
     return cudaSuccess;
 }
 
+// Same passes as radix_impl, with the histogram and scan scratch supplied by
+// the caller instead of a growable buffer.
+template <class K>
+cudaError_t radix_fixed(K **key_io, K **key_alt, uint32_t **val_io, uint32_t **val_alt, size_t n,
+                        int end_bit, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    if (n <= 1 || end_bit <= 0) return cudaSuccess;
+    int nblocks = (int)((n + kTileItems - 1) / kTileItems);
+    size_t hist_n = (size_t)kBins * nblocks;
+    size_t hist_bytes = (hist_n * sizeof(uint32_t) + 255) & ~size_t(255);
+    if (hist_bytes + scan_scratch_bytes(hist_n) > scratch_bytes) return cudaErrorInvalidValue;
+    uint32_t *hist = static_cast<uint32_t *>(scratch);
+    void *scr = static_cast<char *>(scratch) + hist_bytes;
+    for (int shift = 0; shift < end_bit; shift += 8) {
+        k_radix_hist<K><<<nblocks, kThreads, 0, st>>>(*key_io, n, shift, hist, nblocks);
+        cudaError_t e = scan_impl<uint32_t>(hist, hist, hist_n, scr, 0, st);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<K><<<nblocks, kThreads, 0, st>>>(*key_io, *val_io, *key_alt, *val_alt, n,
+                                                         shift, hist, nblocks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        K *tk = *key_io;
+        *key_io = *key_alt;
+        *key_alt = tk;
+        uint32_t *tv = *val_io;
+        *val_io = *val_alt;
+        *val_alt = tv;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
+
+cudaError_t radix_sort_u32_fixed(uint32_t **key_io, uint32_t **key_alt, uint32_t **val_io,
+                                 uint32_t **val_alt, size_t n, int end_bit, void *scratch,
+                                 size_t scratch_bytes, cudaStream_t st) {
+    return radix_fixed<uint32_t>(key_io, key_alt, val_io, val_alt, n, end_bit, scratch,
+                                 scratch_bytes, st);
+}
+
+cudaError_t radix_sort_u64_fixed(uint64_t **key_io, uint64_t **key_alt, uint32_t **val_io,
+                                 uint32_t **val_alt, size_t n, int end_bit, void *scratch,
+                                 size_t scratch_bytes, cudaStream_t st) {
+    return radix_fixed<uint64_t>(key_io, key_alt, val_io, val_alt, n, end_bit, scratch,
+                                 scratch_bytes, st);
+}
 
 size_t scan_scratch_bytes(size_t n) {
     size_t nb = (n + kScanTile - 1) / kScanTile + 1;
