@@ -39,6 +39,8 @@ WORKLOADS = {
     # name: anchors, K, n_feat, views, width, height, fx
     "mapping_100k_anchors_x10_8x640x480": dict(A=100_000, K=10, NF=16, V=8, W=640, H=480, fx=600.0),
     "decode_render_10k_anchors_x10_640x480": dict(A=10_000, K=10, NF=16, V=1, W=640, H=480, fx=600.0),
+    # smaller case for ncu captures (decoded set 0.26 GB > L2)
+    "profile_100k_anchors_x10_2x640x480": dict(A=100_000, K=10, NF=16, V=2, W=640, H=480, fx=600.0),
 }
 DEFAULT_WORKLOAD = "mapping_100k_anchors_x10_8x640x480"
 LAMBDA_SCALE = 0.01

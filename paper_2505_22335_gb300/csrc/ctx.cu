@@ -17,6 +17,10 @@ cudaError_t launch_project(const ViewTable &vt, const BlendParams &bp, int N, in
                            int total, const ups_gaussians &g, float4 *xyzo, float4 *conic,
                            uint2 *rect, uint32_t *count, uint64_t *dkey, uint32_t *dval,
                            cudaStream_t st);
+cudaError_t launch_project_k32(const ViewTable &vt, const BlendParams &bp, int N, int per_view,
+                               int total, const ups_gaussians &g, float4 *xyzo, float4 *conic,
+                               uint2 *rect, uint32_t *count, uint32_t *dkey32, uint32_t *dval,
+                               int vbits, cudaStream_t st);
 cudaError_t launch_gather_counts(const uint32_t *sorted_gv, const uint32_t *count, uint32_t *out,
                                  int total, cudaStream_t st);
 cudaError_t launch_emit(const ViewTable &vt, int N, int total, const uint32_t *sorted_gv,
@@ -383,18 +387,32 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     UPS_CUDA(c, c->scan_scr.reserve(scan_scratch_bytes(total)));
     UPS_CUDA(c, c->ranges.reserve((size_t)vt.total_tiles * sizeof(uint2)));
 
-    stage_begin(c, "project", st);
-    UPS_CUDA(c, launch_project(vt, c->bp, c->N, c->per_view, (int)total, *g, c->xyzo.as<float4>(),
-                               c->conic.as<float4>(), c->rect.as<uint2>(), c->count.as<uint32_t>(),
-                               c->dkey0.as<uint64_t>(), c->dval0.as<uint32_t>(), st));
-    stage_end(c, st, 1);
-    // (view, depth) order of the Gaussian-views
-    uint64_t *dk = c->dkey0.as<uint64_t>(), *dk_alt = c->dkey1.as<uint64_t>();
-    uint32_t *dv = c->dval0.as<uint32_t>(), *dv_alt = c->dval1.as<uint32_t>();
+    // (view, depth) order of the Gaussian-views: 32-bit keys (view in the top
+    // bits, depth bits above 0.125 m below) when the view index fits in 4 bits
+    // and the near plane is >= 0.125 m, else 64-bit keys
     int vbits = bits_for((size_t)n_views);
+    const bool k32 = vbits <= 4 && c->bp.near_z >= 0.125f;
+    uint32_t *dv = c->dval0.as<uint32_t>(), *dv_alt = c->dval1.as<uint32_t>();
+    stage_begin(c, "project", st);
+    if (k32)
+        UPS_CUDA(c, launch_project_k32(vt, c->bp, c->N, c->per_view, (int)total, *g, c->xyzo.as<float4>(),
+                                       c->conic.as<float4>(), c->rect.as<uint2>(), c->count.as<uint32_t>(),
+                                       c->dkey0.as<uint32_t>(), dv, vbits, st));
+    else
+        UPS_CUDA(c, launch_project(vt, c->bp, c->N, c->per_view, (int)total, *g, c->xyzo.as<float4>(),
+                                   c->conic.as<float4>(), c->rect.as<uint2>(), c->count.as<uint32_t>(),
+                                   c->dkey0.as<uint64_t>(), dv, st));
+    stage_end(c, st, 1);
     stage_begin(c, "depth_sort", st);
-    UPS_CUDA(c, radix_sort_u64(&dk, &dk_alt, &dv, &dv_alt, total, 32 + vbits, c->sort, st));
-    stage_end(c, st, radix_kernels(total, 32 + vbits));
+    if (k32) {
+        uint32_t *dk = c->dkey0.as<uint32_t>(), *dk_alt = c->dkey1.as<uint32_t>();
+        UPS_CUDA(c, radix_sort_u32(&dk, &dk_alt, &dv, &dv_alt, total, 32, c->sort, st));
+        stage_end(c, st, radix_kernels(total, 32));
+    } else {
+        uint64_t *dk = c->dkey0.as<uint64_t>(), *dk_alt = c->dkey1.as<uint64_t>();
+        UPS_CUDA(c, radix_sort_u64(&dk, &dk_alt, &dv, &dv_alt, total, 32 + vbits, c->sort, st));
+        stage_end(c, st, radix_kernels(total, 32 + vbits));
+    }
     c->dval_sorted = dv;
     stage_begin(c, "offsets", st);
     UPS_CUDA(c, launch_gather_counts(dv, c->count.as<uint32_t>(), c->cnt_sorted.as<uint32_t>(), (int)total, st));

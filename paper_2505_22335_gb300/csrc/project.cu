@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_project(
     const float4 *__restrict__ mean_op, const float4 *__restrict__ scale,
     const float4 *__restrict__ quat, float4 *__restrict__ xyzo, float4 *__restrict__ conic,
     uint2 *__restrict__ rect, uint32_t *__restrict__ count, uint64_t *__restrict__ dkey,
-    uint32_t *__restrict__ dval) {
+    uint32_t *__restrict__ dval, uint32_t *__restrict__ dkey32, int vbits32) {
     int gv = blockIdx.x * blockDim.x + threadIdx.x;
     if (gv >= total) return;
     int v = gv / N;
@@ -136,8 +136,18 @@ __global__ void __launch_bounds__(256) k_project(
     conic[gv] = cn;
     rect[gv] = rc;
     count[gv] = cnt;
-    uint32_t zb = cnt ? __float_as_uint(G.p[2]) : 0xffffffffu;
-    dkey[gv] = ((uint64_t)v << 32) | zb;
+    if (vbits32 < 0) {
+        uint32_t zb = cnt ? __float_as_uint(G.p[2]) : 0xffffffffu;
+        dkey[gv] = ((uint64_t)v << 32) | zb;
+    } else {
+        // 32-bit key: view in the top vbits32 bits, float bits of z above
+        // 0.125 m below (exact while z < 2^(32 - vbits32) ulps above 0.125 m;
+        // larger depths saturate and fall back to id order)
+        const uint32_t zmask = vbits32 == 0 ? 0xffffffffu : (0xffffffffu >> vbits32);
+        uint32_t zf = zmask;
+        if (cnt) zf = min(__float_as_uint(G.p[2]) - 0x3e000000u, zmask);
+        dkey32[gv] = (vbits32 == 0 ? 0u : ((uint32_t)v << (32 - vbits32))) | zf;
+    }
     dval[gv] = (uint32_t)gv;
 }
 
@@ -148,30 +158,51 @@ __global__ void k_gather_counts(const uint32_t *__restrict__ sorted_gv,
     if (s < total) out[s] = count[sorted_gv[s]];
 }
 
-// One thread per depth-ordered Gaussian-view: write its (view, tile) keys.
+// Instances of 32 consecutive depth-ordered Gaussian-views are written by one
+// warp: the warp walks its contiguous instance range 32 at a time, each lane
+// finds its source Gaussian by a binary search over the lanes' start offsets,
+// so stores are coalesced whatever the per-Gaussian tile counts are.
 __global__ void __launch_bounds__(256) k_emit(ViewTable vt, int N, int total,
                                               const uint32_t *__restrict__ sorted_gv,
                                               const uint64_t *__restrict__ off,
                                               const uint2 *__restrict__ rect,
                                               uint32_t *__restrict__ ikey,
                                               uint32_t *__restrict__ ival) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= total) return;
-    uint64_t o = off[s];
-    uint32_t n = (uint32_t)(off[s + 1] - o);
-    if (n == 0) return;
-    uint32_t gv = sorted_gv[s];
-    int v = (int)(gv / (uint32_t)N);
-    const DevView &cam = vt.v[v];
-    uint2 rc = rect[gv];
-    int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
-    uint32_t idx = (uint32_t)o;
-    for (int ty = y0; ty <= y1; ++ty)
-        for (int tx = x0; tx <= x1; ++tx) {
-            ikey[idx] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
-            ival[idx] = gv;
-            ++idx;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (s0 >= total) return;  // warp-uniform
+    const int s = s0 + lane;
+    const bool in = s < total;
+    const uint64_t o = off[in ? s : total];
+    const uint64_t o_end = off[min(s0 + 32, total)];
+    const uint64_t o_beg = __shfl_sync(full, o, 0);
+    uint32_t gv = in ? sorted_gv[s] : 0u;
+    uint2 rc = make_uint2(0u, 0u);
+    if (in && o_end > o) rc = rect[gv];
+    for (uint64_t b = o_beg; b < o_end; b += 32) {
+        const uint64_t i = b + lane;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            uint64_t oc = __shfl_sync(full, o, L + step);
+            if (oc <= i) L += step;
         }
+        const uint32_t g = __shfl_sync(full, gv, L);
+        const uint32_t r0 = __shfl_sync(full, rc.x, L);
+        const uint32_t r1 = __shfl_sync(full, rc.y, L);
+        const uint64_t oL = __shfl_sync(full, o, L);
+        if (i < o_end) {
+            const int v = (int)(g / (uint32_t)N);
+            const DevView &cam = vt.v[v];
+            const int x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
+            const int wdt = x1 - x0 + 1;
+            const int j = (int)(i - oL);
+            const int ty = y0 + j / wdt, tx = x0 + j % wdt;
+            ikey[i] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
+            ival[i] = g;
+        }
+    }
 }
 
 __global__ void k_ranges(const uint32_t *__restrict__ ikey, uint32_t n, uint2 *__restrict__ ranges) {
@@ -404,7 +435,20 @@ cudaError_t launch_project(const ViewTable &vt, const BlendParams &bp, int N, in
     k_project<<<(total + 255) / 256, 256, 0, st>>>(
         vt, bp, N, per_view, total, reinterpret_cast<const float4 *>(g.mean_opacity),
         reinterpret_cast<const float4 *>(g.scale), reinterpret_cast<const float4 *>(g.quat), xyzo,
-        conic, rect, count, dkey, dval);
+        conic, rect, count, dkey, dval, nullptr, -1);
+    return cudaGetLastError();
+}
+
+// Projection writing 32-bit (view, depth) keys (vbits = bits of the view index).
+cudaError_t launch_project_k32(const ViewTable &vt, const BlendParams &bp, int N, int per_view,
+                               int total, const ups_gaussians &g, float4 *xyzo, float4 *conic,
+                               uint2 *rect, uint32_t *count, uint32_t *dkey32, uint32_t *dval,
+                               int vbits, cudaStream_t st) {
+    if (total == 0) return cudaSuccess;
+    k_project<<<(total + 255) / 256, 256, 0, st>>>(
+        vt, bp, N, per_view, total, reinterpret_cast<const float4 *>(g.mean_opacity),
+        reinterpret_cast<const float4 *>(g.scale), reinterpret_cast<const float4 *>(g.quat), xyzo,
+        conic, rect, count, nullptr, dval, dkey32, vbits);
     return cudaGetLastError();
 }
 

@@ -13,22 +13,45 @@ namespace ups {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTileItems = kThreads * kItems;  // items per block
-constexpr int kBins = 256;                     // 8-bit digits
+constexpr int kBins = 256;  // 8-bit digits
 constexpr int kWarps = kThreads / 32;
+
+// Items per thread: the block tile (keys + values staged in shared memory)
+// stays under the 48 KB static limit for both key widths.
+template <class K> struct Radix {
+    static constexpr int items = sizeof(K) == 8 ? 8 : 16;
+    static constexpr int tile = kThreads * items;
+};
+
+// 256-wide exclusive scan across the block (one value per thread).
+__device__ __forceinline__ uint32_t scan256(uint32_t x, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) before += ww < w ? warp_tot[ww] : 0u;
+    return before + incl - x;
+}
 
 template <class K>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const K *__restrict__ keys, size_t n,
                                                          int shift, uint32_t *__restrict__ hist,
                                                          int nblocks) {
+    constexpr int TILE = Radix<K>::tile;
     __shared__ uint32_t h[kWarps][kBins];
     const int tid = threadIdx.x, w = tid >> 5;
     for (int i = tid; i < kWarps * kBins; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const size_t base = (size_t)blockIdx.x * kTileItems;
+    const size_t base = (size_t)blockIdx.x * TILE;
 #pragma unroll 4
-    for (int i = tid; i < kTileItems; i += kThreads) {
+    for (int i = tid; i < TILE; i += kThreads) {
         size_t idx = base + i;
         if (idx < n) {
             uint32_t d = (uint32_t)(keys[idx] >> shift) & (kBins - 1);
@@ -42,23 +65,32 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const K *__restrict__ k
     hist[(size_t)tid * nblocks + blockIdx.x] = s;
 }
 
+// Stable scatter of one block tile: ballot-based ranking inside each warp,
+// then the tile is reordered by digit in shared memory and written out in
+// order, so consecutive threads store consecutive addresses of a bucket.
 template <class K>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, size_t n, int shift, const uint32_t *__restrict__ offs,
     int nblocks) {
+    constexpr int ITEMS = Radix<K>::items, TILE = Radix<K>::tile;
     __shared__ uint32_t wcnt[kWarps][kBins];
+    __shared__ uint32_t dstart[kBins];
     __shared__ uint32_t gbase[kBins];
+    __shared__ uint32_t wtot[kWarps];
+    __shared__ K skey[TILE];
+    __shared__ uint32_t sval[TILE];
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kWarps * kBins; i += kThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const size_t base = (size_t)blockIdx.x * kTileItems + (size_t)w * (32 * kItems);
-    K key[kItems];
-    uint32_t val[kItems];
-    uint32_t rank[kItems];
+    const size_t tile_base = (size_t)blockIdx.x * TILE;
+    const size_t base = tile_base + (size_t)w * (32 * ITEMS);
+    K key[ITEMS];
+    uint32_t val[ITEMS];
+    uint32_t rank[ITEMS];
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         size_t idx = base + (size_t)j * 32 + lane;
         bool valid = idx < n;
         uint32_t d = kBins;  // sentinel for out-of-range lanes
@@ -67,7 +99,6 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
             val[j] = vin[idx];
             d = (uint32_t)(key[j] >> shift) & (kBins - 1);
         }
-        // lanes holding the same digit (among valid lanes)
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
@@ -83,27 +114,34 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
         rank[j] = prior + lt;
     }
     __syncthreads();
-    {
-        // exclusive prefix over warps for digit `tid`, plus the global offset
-        uint32_t run = 0;
+    uint32_t run = 0;
 #pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) {
-            uint32_t c = wcnt[ww][tid];
-            wcnt[ww][tid] = run;
-            run += c;
-        }
-        gbase[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
+    for (int ww = 0; ww < kWarps; ++ww) {
+        uint32_t c = wcnt[ww][tid];
+        wcnt[ww][tid] = run;
+        run += c;
     }
+    dstart[tid] = scan256(run, wtot);
+    gbase[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         size_t idx = base + (size_t)j * 32 + lane;
         if (idx < n) {
             uint32_t d = (uint32_t)(key[j] >> shift) & (kBins - 1);
-            uint32_t pos = gbase[d] + wcnt[w][d] + rank[j];
-            kout[pos] = key[j];
-            vout[pos] = val[j];
+            uint32_t lpos = dstart[d] + wcnt[w][d] + rank[j];
+            skey[lpos] = key[j];
+            sval[lpos] = val[j];
         }
+    }
+    __syncthreads();
+    const int nvalid = (int)min((size_t)TILE, n - tile_base);
+    for (int i = tid; i < nvalid; i += kThreads) {
+        K k = skey[i];
+        uint32_t d = (uint32_t)(k >> shift) & (kBins - 1);
+        uint32_t pos = gbase[d] + (uint32_t)i - dstart[d];
+        kout[pos] = k;
+        vout[pos] = sval[i];
     }
 }
 
@@ -238,7 +276,7 @@ template <class K>
 cudaError_t radix_impl(K **key_io, K **key_alt, uint32_t **val_io, uint32_t **val_alt, size_t n,
                        int end_bit, SortScratch &s, cudaStream_t st) {
     if (n <= 1 || end_bit <= 0) return cudaSuccess;
-    int nblocks = (int)((n + kTileItems - 1) / kTileItems);
+    int nblocks = (int)((n + Radix<K>::tile - 1) / Radix<K>::tile);
     size_t hist_n = (size_t)kBins * nblocks;
     size_t need = hist_n * sizeof(uint32_t) + scan_scratch_bytes(hist_n);
     cudaError_t e = s.hist.reserve(need);
@@ -269,7 +307,7 @@ template <class K>
 cudaError_t radix_fixed(K **key_io, K **key_alt, uint32_t **val_io, uint32_t **val_alt, size_t n,
                         int end_bit, void *scratch, size_t scratch_bytes, cudaStream_t st) {
     if (n <= 1 || end_bit <= 0) return cudaSuccess;
-    int nblocks = (int)((n + kTileItems - 1) / kTileItems);
+    int nblocks = (int)((n + Radix<K>::tile - 1) / Radix<K>::tile);
     size_t hist_n = (size_t)kBins * nblocks;
     size_t hist_bytes = (hist_n * sizeof(uint32_t) + 255) & ~size_t(255);
     if (hist_bytes + scan_scratch_bytes(hist_n) > scratch_bytes) return cudaErrorInvalidValue;
@@ -315,7 +353,7 @@ size_t scan_scratch_bytes(size_t n) {
 }
 
 size_t radix_hist_bytes(size_t n) {
-    size_t nblocks = (n + kTileItems - 1) / kTileItems;
+    size_t nblocks = (n + Radix<uint64_t>::tile - 1) / Radix<uint64_t>::tile;
     size_t hist_n = (size_t)kBins * nblocks;
     return hist_n * 4 + 256 + scan_scratch_bytes(hist_n);
 }
