@@ -72,72 +72,110 @@ __device__ __forceinline__ void stage_load(Stage<NF> &S, int slot, uint32_t gv, 
     }
 }
 
+// Each thread owns two pixels of the tile, (x, y) and (x, y + 8): the staged
+// Gaussian is read from shared memory once for both.
+constexpr int kThreadsBlend = 128;
+
+struct Tile2 {
+    int v, px, py0;
+    bool in0, in1;
+    const DevView *cam;
+};
+
+__device__ __forceinline__ Tile2 tile2(const ViewTable &vt) {
+    Tile2 c;
+    const int t = blockIdx.x;
+    c.v = view_of_tile(vt, t);
+    c.cam = &vt.v[c.v];
+    int local = t - c.cam->tile_base;
+    int ty = local / c.cam->tiles_x;
+    int tx = local - ty * c.cam->tiles_x;
+    c.px = tx * kTile + (threadIdx.x & (kTile - 1));
+    c.py0 = ty * kTile + (threadIdx.x / kTile);
+    c.in0 = c.px < c.cam->W && c.py0 < c.cam->H;
+    c.in1 = c.px < c.cam->W && c.py0 + 8 < c.cam->H;
+    return c;
+}
+
 template <int NF>
-__global__ void __launch_bounds__(256) k_composite_fwd(
+__global__ void __launch_bounds__(kThreadsBlend) k_composite_fwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
     const float *__restrict__ feat, float *__restrict__ out_color, float *__restrict__ out_depth,
     float *__restrict__ out_feat, float *__restrict__ out_T, uint32_t *__restrict__ out_nc) {
     __shared__ Stage<NF> S;
-    const TileCtx tc = tile_ctx(vt);
+    const Tile2 tc = tile2(vt);
     const uint2 rg = ranges[blockIdx.x];
-    const float fx = (float)tc.px, fy = (float)tc.py;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    float F[NF > 0 ? NF : 1];
+    const float fx = (float)tc.px;
+    const float fy[2] = {(float)tc.py0, (float)(tc.py0 + 8)};
+    float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f},
+          D[2] = {0.f, 0.f};
+    float F[2][NF > 0 ? NF : 1];
 #pragma unroll
-    for (int c = 0; c < NF; ++c) F[c] = 0.f;
-    uint32_t last = 0;
-    bool done = !tc.inside;
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < NF; ++c) F[q][c] = 0.f;
+    uint32_t last[2] = {0u, 0u};
+    bool done[2] = {!tc.in0, !tc.in1};
     const int set_base = per_view ? 0 : tc.v * N;
     for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
-        if (__syncthreads_count(done) == kBatch) break;
-        uint32_t i = base + threadIdx.x;
-        if (i < rg.y) {
-            uint32_t gv = ival[i];
-            stage_load<NF>(S, threadIdx.x, gv, (int)gv - set_base, xyzo, conic, color, feat);
+        if (__syncthreads_count(done[0] && done[1]) == kThreadsBlend) break;
+#pragma unroll
+        for (int h = 0; h < kBatch / kThreadsBlend; ++h) {
+            uint32_t i = base + threadIdx.x + h * kThreadsBlend;
+            if (i < rg.y) {
+                uint32_t gv = ival[i];
+                stage_load<NF>(S, threadIdx.x + h * kThreadsBlend, gv, (int)gv - set_base, xyzo,
+                               conic, color, feat);
+            }
         }
         __syncthreads();
-        int n = min((int)(rg.y - base), kBatch);
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                float4 g = S.xyzo[j];
-                float4 cn = S.conic[j];
-                float dx = fx - g.x, dy = fy - g.y;
-                float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
-                float alpha = fminf(bp.alpha_max, g.w * __expf(power));
-                if (alpha < bp.alpha_min) continue;
-                float Tn = T * (1.f - alpha);
-                if (Tn < bp.t_min) {
-                    done = true;
-                    break;
-                }
-                float w = alpha * T;
-                float4 col = S.color[j];
-                C0 = fmaf(w, col.x, C0);
-                C1 = fmaf(w, col.y, C1);
-                C2 = fmaf(w, col.z, C2);
-                D = fmaf(w, g.z, D);
+        const int n = min((int)(rg.y - base), kBatch);
+        for (int j = 0; j < n && !(done[0] && done[1]); ++j) {
+            const float4 g = S.xyzo[j];
+            const float4 cn = S.conic[j];
+            const float dx = fx - g.x;
 #pragma unroll
-                for (int c = 0; c < NF; ++c) F[c] = fmaf(w, S.feat[c][j], F[c]);
-                T = Tn;
-                last = base - rg.x + j + 1;
+            for (int q = 0; q < 2; ++q) {
+                if (done[q]) continue;
+                const float dy = fy[q] - g.y;
+                const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
+                const float alpha = fminf(bp.alpha_max, g.w * __expf(power));
+                if (alpha < bp.alpha_min) continue;
+                const float Tn = T[q] * (1.f - alpha);
+                if (Tn < bp.t_min) {
+                    done[q] = true;
+                    continue;
+                }
+                const float w = alpha * T[q];
+                const float4 col = S.color[j];
+                C0[q] = fmaf(w, col.x, C0[q]);
+                C1[q] = fmaf(w, col.y, C1[q]);
+                C2[q] = fmaf(w, col.z, C2[q]);
+                D[q] = fmaf(w, g.z, D[q]);
+#pragma unroll
+                for (int c = 0; c < NF; ++c) F[q][c] = fmaf(w, S.feat[c][j], F[q][c]);
+                T[q] = Tn;
+                last[q] = base - rg.x + j + 1;
             }
         }
     }
-    if (tc.inside) {
-        const DevView &cam = *tc.cam;
-        const size_t HW = (size_t)cam.W * cam.H;
-        const size_t p = (size_t)tc.py * cam.W + tc.px;
-        const size_t P = (size_t)cam.pix_off;
-        out_color[3 * P + p] = C0;
-        out_color[3 * P + HW + p] = C1;
-        out_color[3 * P + 2 * HW + p] = C2;
-        out_depth[P + p] = D;
+    const DevView &cam = *tc.cam;
+    const size_t HW = (size_t)cam.W * cam.H;
+    const size_t P = (size_t)cam.pix_off;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) out_feat[NF * P + c * HW + p] = F[c];
-        out_T[P + p] = T;
-        out_nc[P + p] = last;
+    for (int q = 0; q < 2; ++q) {
+        if (!(q == 0 ? tc.in0 : tc.in1)) continue;
+        const size_t p = (size_t)(tc.py0 + 8 * q) * cam.W + tc.px;
+        out_color[3 * P + p] = C0[q];
+        out_color[3 * P + HW + p] = C1[q];
+        out_color[3 * P + 2 * HW + p] = C2[q];
+        out_depth[P + p] = D[q];
+#pragma unroll
+        for (int c = 0; c < NF; ++c) out_feat[NF * P + c * HW + p] = F[q][c];
+        out_T[P + p] = T[q];
+        out_nc[P + p] = last[q];
     }
 }
 
@@ -243,7 +281,7 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[RP], int lane) 
 }
 
 template <int NF>
-__global__ void __launch_bounds__(256) k_composite_bwd(
+__global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
@@ -254,99 +292,110 @@ __global__ void __launch_bounds__(256) k_composite_bwd(
     constexpr int RP = RecPad<NF>::value;
     constexpr int STRIDE = kG2Base + NF;
     __shared__ Stage<NF> S;
-    __shared__ uint32_t s_max[8];
-    const TileCtx tc = tile_ctx(vt);
+    __shared__ uint32_t s_max[kThreadsBlend / 32];
+    const Tile2 tc = tile2(vt);
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[blockIdx.x];
-    const float fx = (float)tc.px, fy = (float)tc.py;
+    const float fx = (float)tc.px;
+    const float fy[2] = {(float)tc.py0, (float)(tc.py0 + 8)};
     const DevView &cam = *tc.cam;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
-    const size_t p = (size_t)(tc.inside ? tc.py : 0) * cam.W + (tc.inside ? tc.px : 0);
-    float T = 1.f, acc = 0.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
-    float gF[NF > 0 ? NF : 1];
+    float T[2] = {1.f, 1.f}, acc[2] = {0.f, 0.f}, gC0[2] = {0.f, 0.f}, gC1[2] = {0.f, 0.f},
+          gC2[2] = {0.f, 0.f}, gD[2] = {0.f, 0.f};
+    float gF[2][NF > 0 ? NF : 1];
+    uint32_t nc[2] = {0u, 0u};
 #pragma unroll
-    for (int c = 0; c < NF; ++c) gF[c] = 0.f;
-    uint32_t nc = 0;
-    if (tc.inside) {
-        T = in_T[P + p];
-        nc = in_nc[P + p];
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int c = 0; c < NF; ++c) gF[q][c] = 0.f;
+        if (!(q == 0 ? tc.in0 : tc.in1)) continue;
+        const size_t p = (size_t)(tc.py0 + 8 * q) * cam.W + tc.px;
+        T[q] = in_T[P + p];
+        nc[q] = in_nc[P + p];
         if (dC) {
-            gC0 = dC[3 * P + p];
-            gC1 = dC[3 * P + HW + p];
-            gC2 = dC[3 * P + 2 * HW + p];
+            gC0[q] = dC[3 * P + p];
+            gC1[q] = dC[3 * P + HW + p];
+            gC2[q] = dC[3 * P + 2 * HW + p];
         }
-        if (dD) gD = dD[P + p];
+        if (dD) gD[q] = dD[P + p];
+        if (dF)
 #pragma unroll
-        for (int c = 0; c < NF; ++c) gF[c] = dF ? dF[NF * P + c * HW + p] : 0.f;
-        if (dT) acc = dT[P + p] * T;
+            for (int c = 0; c < NF; ++c) gF[q][c] = dF[NF * P + c * HW + p];
+        if (dT) acc[q] = dT[P + p] * T[q];
     }
     // longest blended prefix over the tile
-    uint32_t m = __reduce_max_sync(0xffffffffu, nc);
+    uint32_t m = __reduce_max_sync(0xffffffffu, max(nc[0], nc[1]));
     if (lane == 0) s_max[threadIdx.x >> 5] = m;
     __syncthreads();
     uint32_t max_nc = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) max_nc = max(max_nc, s_max[w]);
+    for (int w = 0; w < kThreadsBlend / 32; ++w) max_nc = max(max_nc, s_max[w]);
+    const uint32_t my_nc = max(nc[0], nc[1]);
     const int set_base = per_view ? 0 : tc.v * N;
     for (int hi = (int)max_nc; hi > 0; hi -= kBatch) {
         const int lo = max(0, hi - kBatch);
         __syncthreads();
-        {
-            int i = lo + threadIdx.x;
+#pragma unroll
+        for (int h = 0; h < kBatch / kThreadsBlend; ++h) {
+            int i = lo + threadIdx.x + h * kThreadsBlend;
             if (i < hi) {
                 uint32_t gv = ival[rg.x + i];
-                stage_load<NF>(S, threadIdx.x, gv, (int)gv - set_base, xyzo, conic, color, feat);
+                stage_load<NF>(S, threadIdx.x + h * kThreadsBlend, gv, (int)gv - set_base, xyzo,
+                               conic, color, feat);
             }
         }
         __syncthreads();
-        for (int j = hi - lo - 1; j >= 0; --j) {
+        // warps whose pixels all stop earlier skip the tail of the batch
+        const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, my_nc);
+        int jstart = min(hi - lo, (int)warp_nc - lo) - 1;
+        for (int j = jstart; j >= 0; --j) {
             const int idx = lo + j;
-            bool contrib = idx < (int)nc;
+            const float4 g = S.xyzo[j];
+            const float4 cn = S.conic[j];
+            const float4 col = S.color[j];
+            const float dx = fx - g.x;
             float v[RP];
 #pragma unroll
             for (int k = 0; k < RP; ++k) v[k] = 0.f;
-            if (contrib) {
-                float4 g = S.xyzo[j];
-                float4 cn = S.conic[j];
-                float dx = fx - g.x, dy = fy - g.y;
-                float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
-                float G = __expf(power);
-                float raw = g.w * G;
-                float alpha = fminf(bp.alpha_max, raw);
-                if (alpha < bp.alpha_min) {
-                    contrib = false;
-                } else {
-                    float om = 1.f - alpha;
-                    T = T / om;  // transmittance in front of this Gaussian
-                    float w = alpha * T;
-                    float4 col = S.color[j];
-                    float xg = col.x * gC0 + col.y * gC1 + col.z * gC2 + g.z * gD;
+            bool any = false;
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) {
-                        float f = S.feat[c][j];
-                        xg = fmaf(f, gF[c], xg);
-                        v[kG2Base + c] = w * gF[c];
-                    }
-                    float dalpha = T * xg - acc / om;
-                    acc = fmaf(w, xg, acc);
-                    float dq = 0.f;
-                    if (raw < bp.alpha_max) {
-                        v[3] = dalpha * G;
-                        dq = dalpha * (-0.5f * alpha);
-                    }
-                    v[0] = dq * (-2.f) * (cn.x * dx + cn.y * dy);
-                    v[1] = dq * (-2.f) * (cn.y * dx + cn.z * dy);
-                    v[2] = w * gD;
-                    v[4] = dq * dx * dx;
-                    v[5] = dq * 2.f * dx * dy;
-                    v[6] = dq * dy * dy;
-                    v[8] = w * gC0;
-                    v[9] = w * gC1;
-                    v[10] = w * gC2;
+            for (int q = 0; q < 2; ++q) {
+                if (idx >= (int)nc[q]) continue;
+                const float dy = fy[q] - g.y;
+                const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
+                const float G = __expf(power);
+                const float raw = g.w * G;
+                const float alpha = fminf(bp.alpha_max, raw);
+                if (alpha < bp.alpha_min) continue;
+                any = true;
+                const float om = 1.f - alpha;
+                T[q] = T[q] / om;  // transmittance in front of this Gaussian
+                const float w = alpha * T[q];
+                float xg = col.x * gC0[q] + col.y * gC1[q] + col.z * gC2[q] + g.z * gD[q];
+#pragma unroll
+                for (int c = 0; c < NF; ++c) {
+                    xg = fmaf(S.feat[c][j], gF[q][c], xg);
+                    v[kG2Base + c] = fmaf(w, gF[q][c], v[kG2Base + c]);
                 }
+                const float dalpha = T[q] * xg - acc[q] / om;
+                acc[q] = fmaf(w, xg, acc[q]);
+                float dq = 0.f;
+                if (raw < bp.alpha_max) {
+                    v[3] = fmaf(dalpha, G, v[3]);
+                    dq = dalpha * (-0.5f * alpha);
+                }
+                v[0] = fmaf(dq * (-2.f), cn.x * dx + cn.y * dy, v[0]);
+                v[1] = fmaf(dq * (-2.f), cn.y * dx + cn.z * dy, v[1]);
+                v[2] = fmaf(w, gD[q], v[2]);
+                v[4] = fmaf(dq, dx * dx, v[4]);
+                v[5] = fmaf(dq, 2.f * dx * dy, v[5]);
+                v[6] = fmaf(dq, dy * dy, v[6]);
+                v[8] = fmaf(w, gC0[q], v[8]);
+                v[9] = fmaf(w, gC1[q], v[9]);
+                v[10] = fmaf(w, gC2[q], v[10]);
             }
-            if (__any_sync(0xffffffffu, contrib)) {
+            if (__any_sync(0xffffffffu, any)) {
                 warp_transpose_reduce<RP>(v, lane);
                 float *rec = g2 + (size_t)S.gv[j] * STRIDE;
                 if (RP == 16) {
@@ -377,7 +426,7 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const ups_images &out, cudaStream_t st) {
-    dim3 grid(vt.total_tiles), block(256);
+    dim3 grid(vt.total_tiles), block(kThreadsBlend);
     if (vt.total_tiles == 0) return cudaSuccess;
 #define UPS_FWD(NFV)                                                                          \
     k_composite_fwd<NFV><<<grid, block, 0, st>>>(vt, bp, N, per_view, ranges, ival, xyzo, conic, \
@@ -424,7 +473,7 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const float *T, const uint32_t *nc,
                                  const ups_image_grads &dL, float *g2, cudaStream_t st) {
-    dim3 grid(vt.total_tiles), block(256);
+    dim3 grid(vt.total_tiles), block(kThreadsBlend);
     if (vt.total_tiles == 0) return cudaSuccess;
 #define UPS_BWD(NFV)                                                                          \
     k_composite_bwd<NFV><<<grid, block, 0, st>>>(vt, bp, N, per_view, ranges, ival, xyzo, conic, \
