@@ -53,6 +53,9 @@ cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const u
                               const ups_mlp *d_mlp, const ups_anchors *d_anc, float *d_pose,
                               int num_sms, cudaStream_t st);
 
+size_t decode_bwd_smem_bytes(int K, int NF, int V);
+size_t decode_smem_limit();
+
 cudaError_t DevBuf::reserve(size_t want) {
     if (want <= bytes) return cudaSuccess;
     release();
@@ -282,6 +285,8 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
     if (c.k < 1 || c.k > 16) return fail(nullptr, UPS_ERR_ARG, "k must be in [1, 16]");
     if (c.feat_dim != 32 || c.hidden != 32)
         return fail(nullptr, UPS_ERR_ARG, "feat_dim and hidden must be 32");
+    if (decode_bwd_smem_bytes(c.k, c.n_feat, UPS_MAX_VIEWS) > decode_smem_limit())
+        return fail(nullptr, UPS_ERR_ARG, "k * (11 + n_feat) too large for the decode backward tile");
     if (!(c.alpha_min > 0.f) || !(c.alpha_max >= c.alpha_min) || !(c.alpha_max < 1.f) ||
         !(c.t_min >= 0.f) || !(c.dilation >= 0.f) || !(c.near_z > 0.f) || !(c.guard > 0.f))
         return fail(nullptr, UPS_ERR_ARG, "threshold out of range");

@@ -7,11 +7,8 @@
 // and are read as float4 broadcasts (every lane of a warp reads the same
 // weight), so the inner loops are FMA-bound.
 //
-// Backward: one thread per row recomputes the forward, back-propagates to the
-// input, and produces its share of the weight gradients; the per-row outer
-// products are summed over the 32 rows of a warp with a transposed butterfly
-// (each lane ends up owning one hidden unit) and added to per-block shared
-// accumulators, which are flushed to global memory once per block.
+// Backward: tiles of rows are processed as small GEMMs in shared memory (see
+// k_decode_bwd); weight gradients accumulate per block and are flushed once.
 #include <algorithm>
 
 #include "common.cuh"
@@ -200,29 +197,6 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
 // backward
 // ---------------------------------------------------------------------------
 
-// Sum a 32-vector over the warp; on return lane L holds the sum of element L.
-__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int o = 16, n = 32; o >= 1; o >>= 1, n >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i < n / 2) {
-                float send = up ? v[i] : v[i + n / 2];
-                float keep = up ? v[i + n / 2] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-            }
-        }
-    }
-    return v[0];
-}
-
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 struct DecodeGrads {
     const float4 *d_mean_op, *d_scale, *d_quat, *d_color;
     const float *d_feat;
@@ -232,80 +206,200 @@ struct DecodeGrads {
     unsigned mask;
 };
 
-constexpr int kAccW1Stride = 41;  // odd stride: conflict-free column writes
-constexpr int kXStride = 41;
+// Tiled backward: R rows (anchor-major: row = anchor * V + view) per tile,
+// 8 threads per row.  Per MLP group g, all in shared memory:
+//   Z = X W1_g^T + b1 (H = act(Z), AP = act'(Z));  Y = H W2_g^T + b2 and
+//   DY = dL/dY through the output activation;  DZ = (DY W2_g) * AP;
+//   DX += DZ W1_g;  dW2_g += DY^T H, db2 += 1^T DY;  dW1_g += DZ^T X, db1 += 1^T DZ.
+// The weight-gradient products use 4x4 register micro-tiles over the R rows and
+// accumulate in per-block shared memory, flushed once per block.
+constexpr int kW1S = 132;  // W1^T row stride (conflict-free column walks)
+constexpr int kXS = 44;    // X / DX row stride (col 38 of X is 1: the db1 column)
+constexpr int kHS = 36;    // H / AP / DZ row stride
+constexpr int kW2S = 36;   // W2 row stride (col 32 of the accumulator: db2)
+constexpr int kAccW1S = 44;
+
+__host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
+
+template <int NF> struct BwdTile {
+    static constexpr int R = NF == 32 ? 16 : 32;  // rows per tile
+    static constexpr int T = 8 * R;               // threads
+};
+
+struct BwdLayout {
+    int n_out, DYS, acc_rows;
+    int oW1T, ob1, oW2, ob2, oX, oH, oAP, oDZ, oDY, oDX, oDLS, oDR, oAccW1, oAccW2, oPose, oInfo, total;
+};
+
+__host__ __device__ inline BwdLayout bwd_layout(int K, int NF, int R, int V) {
+    BwdLayout L;
+    L.n_out = K * (11 + NF);
+    int maxg = max(max(K, 7 * K), max(3 * K, K * NF));
+    L.DYS = pad4(maxg) + 4;
+    L.acc_rows = pad4(K) + pad4(7 * K) + pad4(3 * K) + pad4(K * NF);
+    int o = 0;
+    auto take = [&](int n) { int r = o; o += pad4(n); return r; };
+    L.oW1T = take(40 * kW1S);
+    L.ob1 = take(128);
+    L.oW2 = take(L.n_out * kW2S);
+    L.ob2 = take(L.n_out);
+    L.oX = take(R * kXS);
+    L.oH = take(R * kHS);
+    L.oAP = take(R * kHS);
+    L.oDZ = take(R * kHS);
+    L.oDY = take(R * L.DYS);
+    L.oDX = take(R * kXS);
+    L.oDLS = take(R * 4);
+    L.oDR = take(R * 4);
+    L.oAccW1 = take(128 * kAccW1S);
+    L.oAccW2 = take(L.acc_rows * kW2S);
+    L.oPose = take(3 * V);
+    L.oInfo = take(R * 8);  // per row: anchor, view, valid, dist, delta[3]
+    L.total = o;
+    return L;
+}
 
 template <int NF>
-__global__ void __launch_bounds__(128) k_decode_bwd(ViewTable vt, DecodeArgs a, DecodeGrads gr) {
+__global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, DecodeArgs a, DecodeGrads gr) {
+    constexpr int R = BwdTile<NF>::R, NT = BwdTile<NF>::T;
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
-    const int n_out = a.n_out;
-    float *sW1 = sm;
-    float *sb1 = sW1 + 4 * kH * kDinP;
-    float *sW2 = sb1 + 4 * kH;
-    float *sb2 = sW2 + n_out * kH;
-    float *aW1 = sb2 + n_out;                    // [128][41]
-    float *ab1 = aW1 + 4 * kH * kAccW1Stride;    // [128]
-    float *aW2 = ab1 + 4 * kH;                   // [n_out][32]
-    float *ab2 = aW2 + n_out * kH;               // [n_out]
-    float *aPose = ab2 + n_out;                  // [V][3] camera-centre gradient
-    float *sX = aPose + 3 * vt.n;                // [128][41] per-thread MLP input
-    load_weights(a, sW1, sb1, sW2, sb2);
+    const int K = a.K, V = vt.n;
+    const BwdLayout L = bwd_layout(K, NF, R, V);
+    float *W1T = sm + L.oW1T, *sb1 = sm + L.ob1, *W2s = sm + L.oW2, *sb2 = sm + L.ob2;
+    float *X = sm + L.oX, *H = sm + L.oH, *AP = sm + L.oAP, *DZ = sm + L.oDZ, *DY = sm + L.oDY;
+    float *DX = sm + L.oDX, *DLS = sm + L.oDLS, *DR = sm + L.oDR;
+    float *AccW1 = sm + L.oAccW1, *AccW2 = sm + L.oAccW2, *aPose = sm + L.oPose;
+    float *Info = sm + L.oInfo;
+    const int tid = threadIdx.x;
     const bool want_mlp = gr.mask & UPS_GRAD_MLP;
     const bool want_anc = gr.mask & UPS_GRAD_ANCHOR;
     const bool want_pose = gr.mask & UPS_GRAD_POSE;
-    for (int i = threadIdx.x; i < 4 * kH * kAccW1Stride + 4 * kH + n_out * kH + n_out + 3 * vt.n;
-         i += blockDim.x)
-        aW1[i] = 0.f;
+    // weights (W1 transposed) and zeroed accumulators
+    for (int i = tid; i < 40 * kW1S; i += NT) {
+        int ii = i / kW1S, h = i - ii * kW1S;
+        W1T[i] = (ii < kDin && h < 128) ? a.w1[h * kDin + ii] : 0.f;
+    }
+    for (int i = tid; i < 128; i += NT) sb1[i] = a.b1[i];
+    for (int i = tid; i < L.n_out * kW2S; i += NT) {
+        int o = i / kW2S, j = i - o * kW2S;
+        W2s[i] = j < kH ? a.w2[o * kH + j] : 0.f;
+    }
+    for (int i = tid; i < L.n_out; i += NT) sb2[i] = a.b2[i];
+    for (int i = tid; i < 128 * kAccW1S; i += NT) AccW1[i] = 0.f;
+    for (int i = tid; i < L.acc_rows * kW2S; i += NT) AccW2[i] = 0.f;
+    for (int i = tid; i < 3 * V; i += NT) aPose[i] = 0.f;
     __syncthreads();
-    const int K = a.K, V = vt.n;
-    const int lane = threadIdx.x & 31;
     const int rows = a.A * V;
+    const int ntiles = (rows + R - 1) / R;
     const size_t NG = (size_t)a.A * K;
-    const int nrow_iter = (rows + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
-    for (int it = 0; it < nrow_iter; ++it) {
-        const int row = (it * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-        const bool valid = row < rows;
-        const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
-        const DevView &cam = vt.v[v];
-        float x[kDinP], delta[3], dist;
-        mlp_input(a, cam, an, x, delta, dist);
-        float dx[kDinP];
+    const int r = tid >> 3, q8 = tid & 7;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row0 = tile * R;
+        // ---- inputs of each row
+        if (tid < R) {
+            const int row = row0 + tid;
+            const bool valid = row < rows;
+            const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
+            float x[kDinP], delta[3], dist;
+            mlp_input(a, vt.v[v], an, x, delta, dist);
+            float *xr = X + tid * kXS;
 #pragma unroll
-        for (int i = 0; i < kDinP; ++i) {
-            dx[i] = 0.f;
-            sX[threadIdx.x * kXStride + i] = x[i];
+            for (int i = 0; i < kDin; ++i) xr[i] = valid ? x[i] : 0.f;
+            xr[38] = valid ? 1.f : 0.f;
+#pragma unroll
+            for (int i = 39; i < kXS; ++i) xr[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kXS; ++i) DX[tid * kXS + i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) DLS[tid * 4 + i] = 0.f;
+            float *inf = Info + tid * 8;
+            inf[0] = __int_as_float(an);
+            inf[1] = __int_as_float(v);
+            inf[2] = valid ? 1.f : 0.f;
+            inf[3] = dist;
+            inf[4] = delta[0];
+            inf[5] = delta[1];
+            inf[6] = delta[2];
         }
-        const size_t gbase = (size_t)v * NG + (size_t)an * K;
-        float dls[3] = {0.f, 0.f, 0.f};
+        __syncthreads();
+        const int an_r = __float_as_int(Info[r * 8]);
+        const int v_r = __float_as_int(Info[r * 8 + 1]);
+        const bool valid_r = Info[r * 8 + 2] != 0.f;
+        const size_t gbase_r = (size_t)v_r * NG + (size_t)an_r * K;
+        int gacc = 0;
         for (int g = 0; g < 4; ++g) {
-            if (g == 3 && NF == 0) break;
-            float z[kH], h[kH], dh[kH];
-            hidden_pre(sW1, sb1, g, x, z);
-#pragma unroll
-            for (int j = 0; j < kH; ++j) {
-                h[j] = g < 3 ? fmaxf(z[j], 0.f) : softplus(z[j]);
-                dh[j] = 0.f;
-            }
             const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
+            if (m == 0) break;
+            const int ng = K * m, npad = pad4(ng);
             const int r0 = g == 0 ? 0 : g == 1 ? K : g == 2 ? 8 * K : 11 * K;
-            for (int k = 0; k < K; ++k) {
-                const size_t gi = gbase + k;
-                for (int c = 0; c < m; ++c) {
-                    const int r = r0 + m * k + c;
+            // ---- Z, H, act'
+            {
+                float z[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) z[jj] = sb1[g * kH + 4 * q8 + jj];
+                const float *xr = X + r * kXS;
+#pragma unroll 8
+                for (int i = 0; i < 40; ++i) {
+                    const float xi = xr[i];
+                    const float4 w = *reinterpret_cast<const float4 *>(W1T + i * kW1S + g * kH + 4 * q8);
+                    z[0] = fmaf(xi, w.x, z[0]);
+                    z[1] = fmaf(xi, w.y, z[1]);
+                    z[2] = fmaf(xi, w.z, z[2]);
+                    z[3] = fmaf(xi, w.w, z[3]);
+                }
+                float hv[4], ap[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    if (g < 3) {
+                        hv[jj] = fmaxf(z[jj], 0.f);
+                        ap[jj] = z[jj] > 0.f ? 1.f : 0.f;
+                    } else {
+                        hv[jj] = softplus(z[jj]);
+                        ap[jj] = sigm(z[jj]);
+                    }
+                }
+                *reinterpret_cast<float4 *>(H + r * kHS + 4 * q8) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<float4 *>(AP + r * kHS + 4 * q8) = make_float4(ap[0], ap[1], ap[2], ap[3]);
+            }
+            __syncthreads();
+            // ---- Y and dL/dY
+            {
+                float h[kH];
+#pragma unroll
+                for (int q = 0; q < kH / 4; ++q) {
+                    float4 t4 = *reinterpret_cast<const float4 *>(H + r * kHS + 4 * q);
+                    h[4 * q] = t4.x;
+                    h[4 * q + 1] = t4.y;
+                    h[4 * q + 2] = t4.z;
+                    h[4 * q + 3] = t4.w;
+                }
+                for (int o = q8; o < npad; o += 8) {
                     float dy = 0.f;
-                    if (valid) {
-                        float y = out_row(sW2, sb2, r, h);
+                    if (o < ng && valid_r) {
+                        const int row_o = r0 + o;
+                        const float4 *w = reinterpret_cast<const float4 *>(W2s + row_o * kW2S);
+                        float y = sb2[row_o];
+#pragma unroll
+                        for (int q = 0; q < kH / 4; ++q) {
+                            float4 ww = w[q];
+                            y = fmaf(ww.x, h[4 * q], y);
+                            y = fmaf(ww.y, h[4 * q + 1], y);
+                            y = fmaf(ww.z, h[4 * q + 2], y);
+                            y = fmaf(ww.w, h[4 * q + 3], y);
+                        }
+                        const int k = o / m, c = o - k * m;
+                        const size_t gi = gbase_r + k;
                         if (g == 0) {
-                            float o = sigm(y);
-                            dy = gr.d_mean_op[gi].w * o * (1.f - o);
+                            float s = sigm(y);
+                            dy = gr.d_mean_op[gi].w * s * (1.f - s);
                         } else if (g == 1) {
                             if (c < 3) {
                                 float s = sigm(y);
-                                float l = a.ascale[3 * an + c];
+                                float l = a.ascale[3 * an_r + c];
                                 float ds = reinterpret_cast<const float *>(gr.d_scale + gi)[c];
                                 dy = ds * l * s * (1.f - s);
-                                dls[c] += ds * s;
+                                atomicAdd(DLS + r * 4 + c, ds * s);
                             } else {
                                 dy = reinterpret_cast<const float *>(gr.d_quat + gi)[c - 3];
                             }
@@ -316,114 +410,182 @@ __global__ void __launch_bounds__(128) k_decode_bwd(ViewTable vt, DecodeArgs a, 
                             dy = gr.d_feat[gi * NF + c];
                         }
                     }
-                    // dh += dy W2[r]
-                    const float4 *w = reinterpret_cast<const float4 *>(sW2 + r * kH);
-#pragma unroll
-                    for (int q = 0; q < kH / 4; ++q) {
-                        float4 ww = w[q];
-                        dh[4 * q] = fmaf(dy, ww.x, dh[4 * q]);
-                        dh[4 * q + 1] = fmaf(dy, ww.y, dh[4 * q + 1]);
-                        dh[4 * q + 2] = fmaf(dy, ww.z, dh[4 * q + 2]);
-                        dh[4 * q + 3] = fmaf(dy, ww.w, dh[4 * q + 3]);
-                    }
-                    if (want_mlp && __any_sync(0xffffffffu, dy != 0.f)) {
-                        float p[32];
-#pragma unroll
-                        for (int j = 0; j < kH; ++j) p[j] = dy * h[j];
-                        float s = warp_transpose_sum32(p, lane);
-                        atomicAdd(aW2 + r * kH + lane, s);
-                        float sb = warp_sum(dy);
-                        if (lane == 0) atomicAdd(ab2 + r, sb);
-                    }
+                    DY[r * L.DYS + o] = dy;
                 }
             }
-            // through the hidden activation
-            float dz[kH];
+            __syncthreads();
+            // ---- DZ = (DY W2_g) * act'(Z)
+            {
+                float dh[4] = {0.f, 0.f, 0.f, 0.f};
+                const float *dyr = DY + r * L.DYS;
+                for (int o = 0; o < ng; ++o) {
+                    const float d = dyr[o];
+                    const float4 w = *reinterpret_cast<const float4 *>(W2s + (r0 + o) * kW2S + 4 * q8);
+                    dh[0] = fmaf(d, w.x, dh[0]);
+                    dh[1] = fmaf(d, w.y, dh[1]);
+                    dh[2] = fmaf(d, w.z, dh[2]);
+                    dh[3] = fmaf(d, w.w, dh[3]);
+                }
+                const float4 ap = *reinterpret_cast<const float4 *>(AP + r * kHS + 4 * q8);
+                *reinterpret_cast<float4 *>(DZ + r * kHS + 4 * q8) =
+                    make_float4(dh[0] * ap.x, dh[1] * ap.y, dh[2] * ap.z, dh[3] * ap.w);
+            }
+            __syncthreads();
+            // ---- DX += DZ W1_g  (thread owns inputs q8, q8+8, ..., q8+32)
+            {
+                const float *dzr = DZ + r * kHS;
 #pragma unroll
-            for (int j = 0; j < kH; ++j)
-                dz[j] = g < 3 ? (z[j] > 0.f ? dh[j] : 0.f) : dh[j] * sigm(z[j]);
-            // dx += W1_g^T dz
-#pragma unroll 4
-            for (int j = 0; j < kH; ++j) {
-                const float4 *w = reinterpret_cast<const float4 *>(sW1 + (g * kH + j) * kDinP);
-#pragma unroll
-                for (int q = 0; q < kDinP / 4; ++q) {
-                    float4 ww = w[q];
-                    dx[4 * q] = fmaf(dz[j], ww.x, dx[4 * q]);
-                    dx[4 * q + 1] = fmaf(dz[j], ww.y, dx[4 * q + 1]);
-                    dx[4 * q + 2] = fmaf(dz[j], ww.z, dx[4 * q + 2]);
-                    dx[4 * q + 3] = fmaf(dz[j], ww.w, dx[4 * q + 3]);
+                for (int mm = 0; mm < 5; ++mm) {
+                    const int i = q8 + 8 * mm;
+                    float acc = 0.f;
+#pragma unroll 8
+                    for (int j = 0; j < kH; ++j) acc = fmaf(dzr[j], W1T[i * kW1S + g * kH + j], acc);
+                    DX[r * kXS + i] += acc;
                 }
             }
+            // ---- weight gradients (micro-tiles over the R rows)
             if (want_mlp) {
-                // db1 and dW1_g[j][i] = sum over rows dz_j x_i
-                float p[32];
+                const int nA = (npad / 4) * 8;  // dW2_g: (o-block, j-block)
+                const int nB = 8 * 10;          // dW1_g: (j-block, i-block), i < 40 incl. the db1 column
+                for (int mt = tid; mt < nA + nB; mt += NT) {
+                    float acc[4][4];
 #pragma unroll
-                for (int j = 0; j < kH; ++j) p[j] = dz[j];
-                float s = warp_transpose_sum32(p, lane);
-                atomicAdd(ab1 + g * kH + lane, s);
-#pragma unroll 1
-                for (int i = 0; i < kDin; ++i) {
-                    const float xi = sX[threadIdx.x * kXStride + i];
+                    for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int j = 0; j < kH; ++j) p[j] = dz[j] * xi;
-                    float t = warp_transpose_sum32(p, lane);
-                    atomicAdd(aW1 + (g * kH + lane) * kAccW1Stride + i, t);
+                        for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
+                    if (mt < nA) {
+                        const int ob = mt >> 3, jb = mt & 7;
+                        float sb[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int rr = 0; rr < R; ++rr) {
+                            const float4 av = *reinterpret_cast<const float4 *>(DY + rr * L.DYS + 4 * ob);
+                            const float4 bv = *reinterpret_cast<const float4 *>(H + rr * kHS + 4 * jb);
+                            const float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                sb[u] += aa[u];
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(aa[u], bb[w], acc[u][w]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float *dst = AccW2 + (gacc + 4 * ob + u) * kW2S;
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) dst[4 * jb + w] += acc[u][w];
+                            if (jb == 0) dst[32] += sb[u];
+                        }
+                    } else {
+                        const int t2 = mt - nA, jb = t2 / 10, ib = t2 - jb * 10;
+                        for (int rr = 0; rr < R; ++rr) {
+                            const float4 av = *reinterpret_cast<const float4 *>(DZ + rr * kHS + 4 * jb);
+                            const float4 bv = *reinterpret_cast<const float4 *>(X + rr * kXS + 4 * ib);
+                            const float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(aa[u], bb[w], acc[u][w]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float *dst = AccW1 + (g * kH + 4 * jb + u) * kAccW1S + 4 * ib;
+#pragma unroll
+                            for (int w = 0; w < 4; ++w) dst[w] += acc[u][w];
+                        }
+                    }
                 }
             }
+            gacc += npad;
+            __syncthreads();
         }
-        if (!valid) continue;
-        // anchor and camera-centre gradients
-        float dmu[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < K; ++k) {
-            float4 dm = gr.d_mean_op[gbase + k];
-            if (want_anc) {
-                float *o3 = gr.g_offs + ((size_t)an * K + k) * 3;
-                atomicAdd(o3, dm.x);
-                atomicAdd(o3 + 1, dm.y);
-                atomicAdd(o3 + 2, dm.z);
-            }
-            dmu[0] += dm.x;
-            dmu[1] += dm.y;
-            dmu[2] += dm.z;
-        }
-        // delta = r/|r|, d = |r|, r = x_v - o_c
-        float ddl[3] = {dx[kFin], dx[kFin + 1], dx[kFin + 2]}, dd = dx[kFin + 3];
-        float dot = delta[0] * ddl[0] + delta[1] * ddl[1] + delta[2] * ddl[2];
-        float idist = 1.f / dist;
-        float dr[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dr[i] = (ddl[i] - delta[i] * dot) * idist + dd * delta[i];
-        if (want_anc) {
+        // ---- per row: delta_vc, d_vc -> r = x_v - o_c
+        if (tid < R && Info[tid * 8 + 2] != 0.f) {
+            const float *dx = DX + tid * kXS;
+            const float dist = Info[tid * 8 + 3];
+            const float de[3] = {Info[tid * 8 + 4], Info[tid * 8 + 5], Info[tid * 8 + 6]};
+            const float ddl[3] = {dx[kFin], dx[kFin + 1], dx[kFin + 2]}, dd = dx[kFin + 3];
+            const float dot = de[0] * ddl[0] + de[1] * ddl[1] + de[2] * ddl[2];
+            const float idist = 1.f / dist;
+            const int v = __float_as_int(Info[tid * 8 + 1]);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                atomicAdd(gr.g_pos + 3 * an + i, dmu[i] + dr[i]);
-                atomicAdd(gr.g_ascale + 3 * an + i, dls[i]);
+                const float drr = (ddl[i] - de[i] * dot) * idist + dd * de[i];
+                DR[tid * 4 + i] = drr;
+                if (want_pose) atomicAdd(aPose + 3 * v + i, -drr);
             }
-            float *gf = gr.g_afeat + (size_t)an * kFin;
-#pragma unroll
-            for (int i = 0; i < kFin; ++i) atomicAdd(gf + i, dx[i]);
+        } else if (tid < R) {
+            DR[tid * 4] = DR[tid * 4 + 1] = DR[tid * 4 + 2] = 0.f;
         }
-        if (want_pose) {
-            // dL/do_c = -dr
-#pragma unroll
-            for (int i = 0; i < 3; ++i) atomicAdd(aPose + 3 * v + i, -dr[i]);
+        __syncthreads();
+        // ---- anchor gradients: sum the tile's rows of each anchor, one atomic per value
+        if (want_anc) {
+            const int a_first = __float_as_int(Info[0]);
+            const int last_row = min(row0 + R, rows) - 1;
+            const int a_last = last_row / V;
+            const int nseg = a_last - a_first + 1;
+            const int ncomp = kFin + 3 + 3 + 3 * K;
+            for (int it = tid; it < nseg * ncomp; it += NT) {
+                const int seg = it / ncomp, comp = it - seg * ncomp;
+                const int an = a_first + seg;
+                const int rb = max(an * V - row0, 0), re = min((an + 1) * V - row0, last_row - row0 + 1);
+                float s = 0.f;
+                if (comp < kFin) {
+                    for (int rr = rb; rr < re; ++rr) s += DX[rr * kXS + comp];
+                    atomicAdd(gr.g_afeat + (size_t)an * kFin + comp, s);
+                } else if (comp < kFin + 3) {
+                    const int c = comp - kFin;
+                    for (int rr = rb; rr < re; ++rr) {
+                        s += DR[rr * 4 + c];
+                        const int v = __float_as_int(Info[rr * 8 + 1]);
+                        const float4 *dm = gr.d_mean_op + (size_t)v * NG + (size_t)an * K;
+                        for (int k = 0; k < K; ++k) s += reinterpret_cast<const float *>(dm + k)[c];
+                    }
+                    atomicAdd(gr.g_pos + 3 * an + c, s);
+                } else if (comp < kFin + 6) {
+                    const int c = comp - kFin - 3;
+                    for (int rr = rb; rr < re; ++rr) s += DLS[rr * 4 + c];
+                    atomicAdd(gr.g_ascale + 3 * an + c, s);
+                } else {
+                    const int kc = comp - kFin - 6, k = kc / 3, c = kc - 3 * k;
+                    for (int rr = rb; rr < re; ++rr) {
+                        const int v = __float_as_int(Info[rr * 8 + 1]);
+                        s += reinterpret_cast<const float *>(gr.d_mean_op + (size_t)v * NG + (size_t)an * K + k)[c];
+                    }
+                    atomicAdd(gr.g_offs + ((size_t)an * K + k) * 3 + c, s);
+                }
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // flush block accumulators
+    // ---- flush block accumulators
     if (want_mlp) {
-        for (int i = threadIdx.x; i < 4 * kH * kDin; i += blockDim.x) {
-            int r = i / kDin, c = i - r * kDin;
-            atomicAdd(gr.g_w1 + i, aW1[r * kAccW1Stride + c]);
+        for (int i = tid; i < 128 * 39; i += NT) {
+            const int h = i / 39, c = i - h * 39;
+            const float v = AccW1[h * kAccW1S + c];
+            if (c < kDin)
+                atomicAdd(gr.g_w1 + h * kDin + c, v);
+            else
+                atomicAdd(gr.g_b1 + h, v);
         }
-        for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) atomicAdd(gr.g_b1 + i, ab1[i]);
-        for (int i = threadIdx.x; i < n_out * kH; i += blockDim.x) atomicAdd(gr.g_w2 + i, aW2[i]);
-        for (int i = threadIdx.x; i < n_out; i += blockDim.x) atomicAdd(gr.g_b2 + i, ab2[i]);
+        int gacc = 0;
+        for (int g = 0; g < 4; ++g) {
+            const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
+            if (m == 0) break;
+            const int ng = K * m;
+            const int r0 = g == 0 ? 0 : g == 1 ? K : g == 2 ? 8 * K : 11 * K;
+            for (int i = tid; i < ng * 33; i += NT) {
+                const int o = i / 33, j = i - o * 33;
+                const float v = AccW2[(gacc + o) * kW2S + j];
+                if (j < kH)
+                    atomicAdd(gr.g_w2 + (r0 + o) * kH + j, v);
+                else
+                    atomicAdd(gr.g_b2 + r0 + o, v);
+            }
+            gacc += pad4(ng);
+        }
     }
     if (want_pose) {
         // o_c(xi) = t_wc - R_wc rho (first order): d rho = -W dL/do_c
-        for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        for (int v = tid; v < V; v += NT) {
             const DevView &cam = vt.v[v];
             const float *go = aPose + 3 * v;
 #pragma unroll
@@ -436,13 +598,16 @@ __global__ void __launch_bounds__(128) k_decode_bwd(ViewTable vt, DecodeArgs a, 
 }
 
 size_t fwd_smem(int n_out) { return sizeof(float) * (4 * kH * kDinP + 4 * kH + n_out * kH + n_out); }
-size_t bwd_smem(int n_out, int V) {
-    return fwd_smem(n_out) +
-           sizeof(float) * (4 * kH * kAccW1Stride + 4 * kH + n_out * kH + n_out + 3 * V +
-                            128 * kXStride);
-}
 
 }  // namespace
+
+// Shared memory the decode backward needs for K, n_feat and n_views.
+size_t decode_bwd_smem_bytes(int K, int NF, int V) {
+    const int R = NF == 32 ? BwdTile<32>::R : BwdTile<16>::R;
+    return sizeof(float) * (size_t)bwd_layout(K, NF, R, V).total;
+}
+
+size_t decode_smem_limit() { return kMaxSmem; }
 
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
@@ -498,15 +663,16 @@ cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const u
     }
     g.g_pose = d_pose;
     g.mask = mask;
-    size_t smem = bwd_smem(a.n_out, vt.n);
-    if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     int rows = A * vt.n;
-    int blocks = std::max(1, std::min((rows + 127) / 128, num_sms * 2));
 #define UPS_DECB(NFV)                                                                        \
     do {                                                                                     \
+        constexpr int R = BwdTile<NFV>::R, NT = BwdTile<NFV>::T;                              \
+        const size_t smem = sizeof(float) * (size_t)bwd_layout(K, NFV, R, vt.n).total;       \
+        if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;                           \
+        const int blocks = std::max(1, std::min((rows + R - 1) / R, num_sms));               \
         cudaFuncSetAttribute(k_decode_bwd<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                              (int)smem);                                                     \
-        k_decode_bwd<NFV><<<blocks, 128, smem, st>>>(vt, a, g);                              \
+        k_decode_bwd<NFV><<<blocks, NT, smem, st>>>(vt, a, g);                               \
     } while (0)
     switch (NF) {
         case 0: UPS_DECB(0); break;
