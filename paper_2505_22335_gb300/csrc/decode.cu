@@ -223,12 +223,14 @@ __host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
 
 template <int NF> struct BwdTile {
     static constexpr int R = NF == 32 ? 16 : 32;  // rows per tile
-    static constexpr int T = 8 * R;               // threads
+    static constexpr int TPR = 16;                // threads per row
+    static constexpr int T = TPR * R;             // threads
 };
 
 struct BwdLayout {
     int n_out, DYS, acc_rows;
-    int oW1T, ob1, oW2, ob2, oX, oH, oAP, oDZ, oDY, oDX, oDLS, oDR, oAccW1, oAccW2, oPose, oInfo, total;
+    int oW1T, ob1, oW2, ob2, oX, oH, oAP, oDZ, oDY, oDX, oDLS, oDR, oAccW1, oAccW2, oPose, oInfo;
+    int oSG, SGS, oSM, total;
 };
 
 __host__ __device__ inline BwdLayout bwd_layout(int K, int NF, int R, int V) {
@@ -255,6 +257,9 @@ __host__ __device__ inline BwdLayout bwd_layout(int K, int NF, int R, int V) {
     L.oAccW2 = take(L.acc_rows * kW2S);
     L.oPose = take(3 * V);
     L.oInfo = take(R * 8);  // per row: anchor, view, valid, dist, delta[3]
+    L.SGS = pad4(K * max(7, NF));  // staged dL/dG of one group, per row
+    L.oSG = take(R * L.SGS);
+    L.oSM = take(R * K * 4);       // staged dL/d(mean, opacity), per row and Gaussian
     L.total = o;
     return L;
 }
@@ -271,6 +276,8 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
     float *DX = sm + L.oDX, *DLS = sm + L.oDLS, *DR = sm + L.oDR;
     float *AccW1 = sm + L.oAccW1, *AccW2 = sm + L.oAccW2, *aPose = sm + L.oPose;
     float *Info = sm + L.oInfo;
+    float *SG = sm + L.oSG, *SM = sm + L.oSM;
+    constexpr int TPR = BwdTile<NF>::TPR;
     const int tid = threadIdx.x;
     const bool want_mlp = gr.mask & UPS_GRAD_MLP;
     const bool want_anc = gr.mask & UPS_GRAD_ANCHOR;
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
     const int rows = a.A * V;
     const int ntiles = (rows + R - 1) / R;
     const size_t NG = (size_t)a.A * K;
-    const int r = tid >> 3, q8 = tid & 7;
+    const int r = tid / TPR, q = tid % TPR;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * R;
         // ---- inputs of each row
@@ -324,33 +331,72 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
         }
         __syncthreads();
         const int an_r = __float_as_int(Info[r * 8]);
-        const int v_r = __float_as_int(Info[r * 8 + 1]);
         const bool valid_r = Info[r * 8 + 2] != 0.f;
-        const size_t gbase_r = (size_t)v_r * NG + (size_t)an_r * K;
         int gacc = 0;
         for (int g = 0; g < 4; ++g) {
             const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
             if (m == 0) break;
             const int ng = K * m, npad = pad4(ng);
             const int r0 = g == 0 ? 0 : g == 1 ? K : g == 2 ? 8 * K : 11 * K;
-            // ---- Z, H, act'
+            // ---- stage this group's dL/dG of the tile's rows (coalesced, all threads)
+            if (g == 3) {
+                const int per_row = K * NF / 4;
+                for (int it = tid; it < R * per_row; it += NT) {
+                    const int rr = it / per_row, e = it - rr * per_row;
+                    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (Info[rr * 8 + 2] != 0.f) {
+                        const size_t gb = (size_t)__float_as_int(Info[rr * 8 + 1]) * NG +
+                                          (size_t)__float_as_int(Info[rr * 8]) * K;
+                        val = reinterpret_cast<const float4 *>(gr.d_feat + gb * NF)[e];
+                    }
+                    *reinterpret_cast<float4 *>(SG + rr * L.SGS + 4 * e) = val;
+                }
+            } else {
+                for (int it = tid; it < R * K; it += NT) {
+                    const int rr = it / K, k = it - rr * K;
+                    const bool ok = Info[rr * 8 + 2] != 0.f;
+                    const size_t gi = ok ? (size_t)__float_as_int(Info[rr * 8 + 1]) * NG +
+                                               (size_t)__float_as_int(Info[rr * 8]) * K + k
+                                         : 0;
+                    float *dst = SG + rr * L.SGS;
+                    if (g == 0) {
+                        const float4 dm = ok ? gr.d_mean_op[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4 *>(SM + (rr * K + k) * 4) = dm;
+                        dst[k] = dm.w;
+                    } else if (g == 1) {
+                        const float4 ds = ok ? gr.d_scale[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 dq = ok ? gr.d_quat[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        dst[7 * k] = ds.x;
+                        dst[7 * k + 1] = ds.y;
+                        dst[7 * k + 2] = ds.z;
+                        dst[7 * k + 3] = dq.x;
+                        dst[7 * k + 4] = dq.y;
+                        dst[7 * k + 5] = dq.z;
+                        dst[7 * k + 6] = dq.w;
+                    } else {
+                        const float4 dc = ok ? gr.d_color[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        dst[3 * k] = dc.x;
+                        dst[3 * k + 1] = dc.y;
+                        dst[3 * k + 2] = dc.z;
+                    }
+                }
+            }
+            // ---- Z, H, act'  (two hidden units per thread)
             {
-                float z[4];
+                float z[2];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) z[jj] = sb1[g * kH + 4 * q8 + jj];
+                for (int jj = 0; jj < 2; ++jj) z[jj] = sb1[g * kH + 2 * q + jj];
                 const float *xr = X + r * kXS;
 #pragma unroll 8
                 for (int i = 0; i < 40; ++i) {
                     const float xi = xr[i];
-                    const float4 w = *reinterpret_cast<const float4 *>(W1T + i * kW1S + g * kH + 4 * q8);
+                    const float2 w = *reinterpret_cast<const float2 *>(W1T + i * kW1S + g * kH + 2 * q);
                     z[0] = fmaf(xi, w.x, z[0]);
                     z[1] = fmaf(xi, w.y, z[1]);
-                    z[2] = fmaf(xi, w.z, z[2]);
-                    z[3] = fmaf(xi, w.w, z[3]);
                 }
-                float hv[4], ap[4];
+                float hv[2], ap[2];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
+                for (int jj = 0; jj < 2; ++jj) {
                     if (g < 3) {
                         hv[jj] = fmaxf(z[jj], 0.f);
                         ap[jj] = z[jj] > 0.f ? 1.f : 0.f;
@@ -359,56 +405,56 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
                         ap[jj] = sigm(z[jj]);
                     }
                 }
-                *reinterpret_cast<float4 *>(H + r * kHS + 4 * q8) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-                *reinterpret_cast<float4 *>(AP + r * kHS + 4 * q8) = make_float4(ap[0], ap[1], ap[2], ap[3]);
+                *reinterpret_cast<float2 *>(H + r * kHS + 2 * q) = make_float2(hv[0], hv[1]);
+                *reinterpret_cast<float2 *>(AP + r * kHS + 2 * q) = make_float2(ap[0], ap[1]);
             }
             __syncthreads();
             // ---- Y and dL/dY
             {
                 float h[kH];
 #pragma unroll
-                for (int q = 0; q < kH / 4; ++q) {
-                    float4 t4 = *reinterpret_cast<const float4 *>(H + r * kHS + 4 * q);
-                    h[4 * q] = t4.x;
-                    h[4 * q + 1] = t4.y;
-                    h[4 * q + 2] = t4.z;
-                    h[4 * q + 3] = t4.w;
+                for (int qq = 0; qq < kH / 4; ++qq) {
+                    float4 t4 = *reinterpret_cast<const float4 *>(H + r * kHS + 4 * qq);
+                    h[4 * qq] = t4.x;
+                    h[4 * qq + 1] = t4.y;
+                    h[4 * qq + 2] = t4.z;
+                    h[4 * qq + 3] = t4.w;
                 }
-                for (int o = q8; o < npad; o += 8) {
+                for (int o = q; o < npad; o += TPR) {
                     float dy = 0.f;
                     if (o < ng && valid_r) {
                         const int row_o = r0 + o;
                         const float4 *w = reinterpret_cast<const float4 *>(W2s + row_o * kW2S);
                         float y = sb2[row_o];
 #pragma unroll
-                        for (int q = 0; q < kH / 4; ++q) {
-                            float4 ww = w[q];
-                            y = fmaf(ww.x, h[4 * q], y);
-                            y = fmaf(ww.y, h[4 * q + 1], y);
-                            y = fmaf(ww.z, h[4 * q + 2], y);
-                            y = fmaf(ww.w, h[4 * q + 3], y);
+                        for (int qq = 0; qq < kH / 4; ++qq) {
+                            float4 ww = w[qq];
+                            y = fmaf(ww.x, h[4 * qq], y);
+                            y = fmaf(ww.y, h[4 * qq + 1], y);
+                            y = fmaf(ww.z, h[4 * qq + 2], y);
+                            y = fmaf(ww.w, h[4 * qq + 3], y);
                         }
                         const int k = o / m, c = o - k * m;
-                        const size_t gi = gbase_r + k;
+                        const float gin = SG[r * L.SGS + o];
                         if (g == 0) {
                             float s = sigm(y);
-                            dy = gr.d_mean_op[gi].w * s * (1.f - s);
+                            dy = gin * s * (1.f - s);
                         } else if (g == 1) {
                             if (c < 3) {
                                 float s = sigm(y);
                                 float l = a.ascale[3 * an_r + c];
-                                float ds = reinterpret_cast<const float *>(gr.d_scale + gi)[c];
-                                dy = ds * l * s * (1.f - s);
-                                atomicAdd(DLS + r * 4 + c, ds * s);
+                                dy = gin * l * s * (1.f - s);
+                                atomicAdd(DLS + r * 4 + c, gin * s);
                             } else {
-                                dy = reinterpret_cast<const float *>(gr.d_quat + gi)[c - 3];
+                                dy = gin;
                             }
                         } else if (g == 2) {
                             float cc = sigm(y);
-                            dy = reinterpret_cast<const float *>(gr.d_color + gi)[c] * cc * (1.f - cc);
+                            dy = gin * cc * (1.f - cc);
                         } else {
-                            dy = gr.d_feat[gi * NF + c];
+                            dy = gin;
                         }
+                        (void)k;
                     }
                     DY[r * L.DYS + o] = dy;
                 }
@@ -416,27 +462,26 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
             __syncthreads();
             // ---- DZ = (DY W2_g) * act'(Z)
             {
-                float dh[4] = {0.f, 0.f, 0.f, 0.f};
+                float dh[2] = {0.f, 0.f};
                 const float *dyr = DY + r * L.DYS;
+#pragma unroll 4
                 for (int o = 0; o < ng; ++o) {
                     const float d = dyr[o];
-                    const float4 w = *reinterpret_cast<const float4 *>(W2s + (r0 + o) * kW2S + 4 * q8);
+                    const float2 w = *reinterpret_cast<const float2 *>(W2s + (r0 + o) * kW2S + 2 * q);
                     dh[0] = fmaf(d, w.x, dh[0]);
                     dh[1] = fmaf(d, w.y, dh[1]);
-                    dh[2] = fmaf(d, w.z, dh[2]);
-                    dh[3] = fmaf(d, w.w, dh[3]);
                 }
-                const float4 ap = *reinterpret_cast<const float4 *>(AP + r * kHS + 4 * q8);
-                *reinterpret_cast<float4 *>(DZ + r * kHS + 4 * q8) =
-                    make_float4(dh[0] * ap.x, dh[1] * ap.y, dh[2] * ap.z, dh[3] * ap.w);
+                const float2 ap = *reinterpret_cast<const float2 *>(AP + r * kHS + 2 * q);
+                *reinterpret_cast<float2 *>(DZ + r * kHS + 2 * q) = make_float2(dh[0] * ap.x, dh[1] * ap.y);
             }
             __syncthreads();
-            // ---- DX += DZ W1_g  (thread owns inputs q8, q8+8, ..., q8+32)
+            // ---- DX += DZ W1_g  (thread owns inputs q, q+16, q+32)
             {
                 const float *dzr = DZ + r * kHS;
 #pragma unroll
-                for (int mm = 0; mm < 5; ++mm) {
-                    const int i = q8 + 8 * mm;
+                for (int mm = 0; mm < 3; ++mm) {
+                    const int i = q + TPR * mm;
+                    if (i >= 40) break;
                     float acc = 0.f;
 #pragma unroll 8
                     for (int j = 0; j < kH; ++j) acc = fmaf(dzr[j], W1T[i * kW1S + g * kH + j], acc);
@@ -535,9 +580,7 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
                     const int c = comp - kFin;
                     for (int rr = rb; rr < re; ++rr) {
                         s += DR[rr * 4 + c];
-                        const int v = __float_as_int(Info[rr * 8 + 1]);
-                        const float4 *dm = gr.d_mean_op + (size_t)v * NG + (size_t)an * K;
-                        for (int k = 0; k < K; ++k) s += reinterpret_cast<const float *>(dm + k)[c];
+                        for (int k = 0; k < K; ++k) s += SM[(rr * K + k) * 4 + c];
                     }
                     atomicAdd(gr.g_pos + 3 * an + c, s);
                 } else if (comp < kFin + 6) {
@@ -546,10 +589,7 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
                     atomicAdd(gr.g_ascale + 3 * an + c, s);
                 } else {
                     const int kc = comp - kFin - 6, k = kc / 3, c = kc - 3 * k;
-                    for (int rr = rb; rr < re; ++rr) {
-                        const int v = __float_as_int(Info[rr * 8 + 1]);
-                        s += reinterpret_cast<const float *>(gr.d_mean_op + (size_t)v * NG + (size_t)an * K + k)[c];
-                    }
+                    for (int rr = rb; rr < re; ++rr) s += SM[(rr * K + k) * 4 + c];
                     atomicAdd(gr.g_offs + ((size_t)an * K + k) * 3 + c, s);
                 }
             }
