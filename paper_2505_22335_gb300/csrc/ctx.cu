@@ -48,6 +48,10 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
                               cudaStream_t st);
+cudaError_t launch_decode_fwd_tc(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
+                                 const ups_mlp &mlp, const ups_gaussians &out, int bf16, int *err,
+                                 int num_sms, cudaStream_t st);
+size_t decode_tc_smem_bytes(int NF, int bf16);
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask,
                               const ups_mlp *d_mlp, const ups_anchors *d_anc, float *d_pose,
@@ -102,7 +106,8 @@ struct ups_ctx {
     DevBuf ikey0, ikey1, ival0, ival1, ranges, g2;
     SortScratch sort;
     uint32_t *dval_sorted = nullptr, *ikey_sorted = nullptr, *ival_sorted = nullptr;
-    uint64_t *h_total = nullptr;  // pinned
+    uint64_t *h_total = nullptr;  // pinned: [0] instance count, [1] device error flag
+    int *d_err = nullptr;         // set by kernels whose bounded waits ran out
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
     struct Rec {
@@ -300,7 +305,9 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
     ctx->device = device;
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_total, sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_total, 2 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         g_create_error = std::string("ups_create: ") + cudaGetErrorString(e);
         delete ctx;
@@ -319,6 +326,7 @@ ups_status ups_destroy(ups_ctx *c) {
                       &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->sort.hist};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
+    if (c->d_err) cudaFree(c->d_err);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -353,7 +361,14 @@ ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
     stage_begin(c, "decode_fwd", st);
-    UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->num_sms, st));
+    // tensor cores (BF16, or 3xTF32 for FP32-level results) where the operands
+    // fit in shared memory; CUDA-core FP32 otherwise
+    const int bf16 = c->cfg.decode_bf16 ? 1 : 0;
+    if (decode_tc_smem_bytes(c->cfg.n_feat, bf16) + 1024 <= 227 * 1024)
+        UPS_CUDA(c, launch_decode_fwd_tc(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, bf16,
+                                         c->d_err, c->num_sms, st));
+    else
+        UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->num_sms, st));
     stage_end(c, st, 1);
     return UPS_OK;
 }
@@ -426,7 +441,13 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     stage_end(c, st, 4);
     UPS_CUDA(c, cudaMemcpyAsync(c->h_total, c->off.as<uint64_t>() + total, sizeof(uint64_t),
                                 cudaMemcpyDeviceToHost, st));
+    c->h_total[1] = 0;
+    UPS_CUDA(c, cudaMemcpyAsync(c->h_total + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     UPS_CUDA(c, cudaStreamSynchronize(st));
+    if (c->h_total[1] != 0) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+        return fail(c, UPS_ERR_TIMEOUT, "a tensor-core wait ran out of polls in an earlier decode");
+    }
     const uint64_t n_inst = *c->h_total;
     if (n_inst >= (uint64_t)UINT32_MAX) return fail(c, UPS_ERR_CAPACITY, "more than 2^32 tile instances");
     c->n_inst = (size_t)n_inst;

@@ -1,0 +1,123 @@
+// Minimal tcgen05 (5th-generation tensor core) helpers for sm_100a/sm_103a:
+// shared-memory matrix descriptors for canonical K-major, no-swizzle operands,
+// instruction descriptors for kind::f16 (BF16) and kind::tf32 with FP32
+// accumulation, TMEM allocation, MMA issue/commit, bounded mbarrier waits and
+// TMEM loads.  Written from the PTX ISA description of these instructions.
+//
+// Canonical K-major layout (no swizzle): an M x K operand is a grid of "core
+// matrices" of 8 rows x 16 bytes (8 BF16 or 4 TF32 elements per row); the 8
+// rows of a core matrix are 16 bytes apart, core matrices adjacent along K are
+// LBO = 128 bytes apart, 8-row groups are SBO = (K bytes / 16) * 128 apart.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ups {
+namespace umma {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row, k) of a canonical K-major operand whose rows
+// hold `kbytes` bytes (a multiple of 16), element size `esize`.
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int kbytes, int esize) {
+    const int per_core = 16 / esize;
+    return (uint32_t)(((row >> 3) * (kbytes >> 4) + k / per_core) * 128 + (row & 7) * 16 +
+                      (k % per_core) * esize);
+}
+
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t kbytes) {
+    const uint32_t lbo = 128, sbo = (kbytes >> 4) * 128;
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    return d;
+}
+
+enum Kind { kBF16 = 0, kTF32 = 1 };
+
+__host__ __device__ constexpr uint32_t idesc(Kind kind, int M, int N) {
+    return (1u << 4)                                   // D: FP32
+           | ((kind == kBF16 ? 1u : 2u) << 7)           // A format
+           | ((kind == kBF16 ? 1u : 2u) << 10)          // B format
+           | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <Kind K>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if (K == kBF16)
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+                     "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+                     "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_addr(mbar)));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+}
+
+// Waits for the phase with parity `parity`; gives up after `limit` polls and
+// returns false (the caller records the failure and skips the TMEM reads).
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_addr(mbar)), "r"(parity));
+    return done != 0;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+
+// one warp: allocate `ncols` TMEM columns (power of two >= 32), address to *dst
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TF32 split: x = hi + lo with hi a TF32 value (round to nearest) and lo the
+// FP32 remainder; hi*b_hi + hi*b_lo + lo*b_hi recovers FP32-level products.
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+}  // namespace umma
+}  // namespace ups

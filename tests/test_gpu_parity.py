@@ -210,3 +210,50 @@ def test_anchor_decode_10k_anchors_640x480():
     cams = scenes.cameras(0, 1, 640, 480, 600.0)
     res = anchor_case(0, 10000, 10, 16, cams)
     check_anchor(res, 16)
+
+
+# ---------------------------------------------------------------------------
+# BF16 tensor-core decode: error against the FP64 oracle, stated per output
+# ---------------------------------------------------------------------------
+
+BF16_BOUNDS = dict(opacity=2e-2, scale_rel=3e-2, quat_dir=3e-2, color=2e-2, feat=6e-2)
+
+
+def test_bf16_decode_error_per_output():
+    import json
+    import os
+    K, nf = 10, 16
+    anc = round_dict(scenes.anchors(5, 10000, K))
+    mlp = round_dict(scenes.mlp_weights(6, K, nf, bias_sigma=0.05))
+    cams = round_cams(scenes.cameras(5, 2, 640, 480, 600.0))
+    R = B.Renderer(n_feat=nf, k=K, decode_bf16=1)
+    ad, md = B.anchors_to_device(anc, mlp)
+    g = R.decode(ad, md, cams)
+    mo = g.mean_opacity.cpu().numpy().astype(np.float64)
+    sc = g.scale.cpu().numpy().astype(np.float64)
+    qt = g.quat.cpu().numpy().astype(np.float64)
+    co = g.color.cpu().numpy().astype(np.float64)
+    fe = g.feat.cpu().numpy().astype(np.float64)
+    stats = {}
+    for v, c in enumerate(cams):
+        ref = oracle.decode(anc, mlp, c, K, nf)
+        qa = qt[v] / np.linalg.norm(qt[v], axis=1, keepdims=True)
+        qr = ref["quat"] / np.linalg.norm(ref["quat"], axis=1, keepdims=True)
+        qdir = np.minimum(np.linalg.norm(qa - qr, axis=1), np.linalg.norm(qa + qr, axis=1))
+        errs = dict(opacity=np.abs(mo[v, :, 3] - ref["opacity"]),
+                    scale_rel=np.abs(sc[v, :, :3] - ref["scale"]) / ref["scale"],
+                    quat_dir=qdir, color=np.abs(co[v, :, :3] - ref["color"]),
+                    feat=np.abs(fe[v] - ref["feat"]))
+        np.testing.assert_allclose(mo[v, :, :3], ref["mean"], rtol=1e-6, atol=1e-6)
+        for k, e in errs.items():
+            st = stats.setdefault(k, dict(max=0.0, rms2=0.0, n=0))
+            st["max"] = max(st["max"], float(e.max()))
+            st["rms2"] += float((e ** 2).sum())
+            st["n"] += e.size
+    report = {k: dict(max=v["max"], rms=(v["rms2"] / v["n"]) ** 0.5) for k, v in stats.items()}
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open("gpurun_out/bf16_decode_error.json", "w") as f:
+        json.dump(report, f, indent=1)
+    print("bf16 decode error vs FP64 oracle:", json.dumps(report))
+    for k, bound in BF16_BOUNDS.items():
+        assert report[k]["max"] < bound, (k, report[k])
