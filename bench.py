@@ -127,13 +127,13 @@ def make_inputs(wl, seed=0):
 class Step:
     """Preallocated buffers + one fwd+bwd step through the C ABI."""
 
-    def __init__(self, wl, anc, mlp, cams, tg, device):
+    def __init__(self, wl, anc, mlp, cams, tg, device, bf16=False):
         import torch
         from paper_2505_22335_gb300 import binding as B
         self.B = B
         self.wl = wl
         self.cams = cams
-        self.R = B.Renderer(n_feat=wl["NF"], k=wl["K"], device=device)
+        self.R = B.Renderer(n_feat=wl["NF"], k=wl["K"], device=device, decode_bf16=int(bf16))
         self.ad, self.md = B.anchors_to_device(anc, mlp)
         self.tgt = B.targets_to_device(tg)
         V, N = len(cams), wl["A"] * wl["K"]
@@ -224,7 +224,7 @@ def run_ours(args, wl_name):
     torch.cuda.set_device(local)
     wl = WORKLOADS[wl_name]
     anc, mlp, cams, tg = make_inputs(wl, seed=0)
-    st = Step(wl, anc, mlp, cams, tg, local)
+    st = Step(wl, anc, mlp, cams, tg, local, bf16=args.decode_bf16)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         st.run()
@@ -276,11 +276,13 @@ def run_ours(args, wl_name):
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bf16 decode GEMMs)" if args.decode_bf16 else "f32",
             "data": "synthetic (seeded anchors, MLP weights, arc poses, targets)",
             "config": {"workload": wl_name, "anchors": wl["A"], "k": wl["K"], "gaussians": wl["A"] * wl["K"],
                        "views": wl["V"], "width": wl["W"], "height": wl["H"], "n_feat": wl["NF"],
-                       "decode": "fp32", "loss": "weighted l1 + 0.01 mean scale",
+                       "decode": "bf16 tensor cores (tcgen05), fp32 accumulate" if args.decode_bf16 else "fp32",
+                       "loss": "weighted l1 + 0.01 mean scale",
                        "l2_policy": "inputs larger than L2 (decoded set alone is %.2f GB per step)"
                                     % (wl["V"] * wl["A"] * wl["K"] * (64 + 4 * wl["NF"]) / 1e9),
                        "parallelism": f"replicas x{world}"},
@@ -430,6 +432,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--decode-bf16", action="store_true",
+                    help="decode MLP GEMMs in BF16 on the tensor cores (FP32 accumulation)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -361,10 +361,11 @@ ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
     stage_begin(c, "decode_fwd", st);
-    // tensor cores (BF16, or 3xTF32 for FP32-level results) where the operands
-    // fit in shared memory; CUDA-core FP32 otherwise
+    // BF16 decode on the tensor cores; the FP32 decode on the CUDA cores (its
+    // 3xTF32 tensor-core form needs 223 KB of operands, one CTA per SM, and is
+    // slower than the CUDA-core kernel at these sizes)
     const int bf16 = c->cfg.decode_bf16 ? 1 : 0;
-    if (decode_tc_smem_bytes(c->cfg.n_feat, bf16) + 1024 <= 227 * 1024)
+    if (bf16 && decode_tc_smem_bytes(c->cfg.n_feat, bf16) + 1024 <= 227 * 1024)
         UPS_CUDA(c, launch_decode_fwd_tc(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, bf16,
                                          c->d_err, c->num_sms, st));
     else

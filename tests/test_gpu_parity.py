@@ -216,7 +216,10 @@ def test_anchor_decode_10k_anchors_640x480():
 # BF16 tensor-core decode: error against the FP64 oracle, stated per output
 # ---------------------------------------------------------------------------
 
-BF16_BOUNDS = dict(opacity=2e-2, scale_rel=3e-2, quat_dir=3e-2, color=2e-2, feat=6e-2)
+# max over all outputs, and rms; the quaternion direction is ill-conditioned
+# where the raw decoded quaternion is short, hence its larger maximum
+BF16_BOUNDS = dict(opacity=(1e-2, 2e-3), scale_rel=(4e-2, 6e-3), quat_dir=(0.3, 1e-2),
+                   color=(1e-2, 2e-3), feat=(5e-2, 1e-2))
 
 
 def test_bf16_decode_error_per_output():
@@ -255,5 +258,5 @@ def test_bf16_decode_error_per_output():
     with open("gpurun_out/bf16_decode_error.json", "w") as f:
         json.dump(report, f, indent=1)
     print("bf16 decode error vs FP64 oracle:", json.dumps(report))
-    for k, bound in BF16_BOUNDS.items():
-        assert report[k]["max"] < bound, (k, report[k])
+    for k, (bmax, brms) in BF16_BOUNDS.items():
+        assert report[k]["max"] < bmax and report[k]["rms"] < brms, (k, report[k])
