@@ -29,7 +29,8 @@ constexpr int kTCRows = 128;
 constexpr int kH = 32;
 constexpr int kFin = 32;
 constexpr int kDin = kFin + 6;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 128;  // Z: [0, 32), Y chunk of <= 4 components: [32, 96)
+constexpr int kChunk = 4;            // output components per Y chunk
 constexpr int kWaitLimit = 1 << 22;
 
 struct TcArgs {
@@ -120,7 +121,7 @@ __host__ __device__ inline int w2_row_base(int g, int NF) {
 }
 
 template <int NF, Kind KD>
-__global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs a) {
+__global__ void __launch_bounds__(kTCRows, 3) k_decode_fwd_tc(ViewTable vt, TcArgs a) {
     using P = Prec<KD>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar;
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs 
         fence_async_smem();
         __syncthreads();
         const size_t gbase = (size_t)v * NG + (size_t)an * K;
-        float op[16];
+        float op[16], qw[16];
         for (int g = 0; g < 4 && ok; ++g) {
             const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
             if (m == 0) break;
@@ -245,10 +246,10 @@ __global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs 
             fence_async_smem();
             __syncthreads();
             fence_after();
-            // Y_g in chunks of at most 8 components (128 columns) -> TMEM [32, 160)
+            // Y_g in chunks of at most kChunk components (16 columns each) -> TMEM [32, 96)
             const int rbase = w2_row_base(g, NF);
-            for (int c0 = 0; c0 < m && ok; c0 += 8) {
-                const int nc = min(8, m - c0);
+            for (int c0 = 0; c0 < m && ok; c0 += kChunk) {
+                const int nc = min(kChunk, m - c0);
                 if (tid == 0)
                     gemm<KD>(tmem + 32, Hs, Hl, W2 + (rbase + 16 * c0) * P::hbytes,
                              W2l + (rbase + 16 * c0) * P::hbytes, P::hbytes, P::hbytes,
@@ -266,7 +267,8 @@ __global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs 
                     tmem_ld16(lane_addr + 32, y);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) op[k] = sig(y[k] + b2[rbase + k]);
-                } else if (g == 1) {
+                } else if (g == 1 && c0 == 0) {
+                    // components 0..3 = scale x, y, z and quaternion w
                     float s0[16], s1[16], s2[16];
                     tmem_ld16(lane_addr + 32 + 0, s0);
                     tmem_ld16(lane_addr + 32 + 16, s1);
@@ -283,15 +285,19 @@ __global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs 
                             a.mean_op[gbase + k] = make_float4(px + o3[0], py + o3[1], pz + o3[2], op[k]);
                         }
                     }
-                    float q0[16], q1[16], q2[16], q3[16];
-                    tmem_ld16(lane_addr + 32 + 48, q0);
-                    tmem_ld16(lane_addr + 32 + 64, q1);
-                    tmem_ld16(lane_addr + 32 + 80, q2);
-                    tmem_ld16(lane_addr + 32 + 96, q3);
+                    tmem_ld16(lane_addr + 32 + 48, qw);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) qw[k] += b2[rbase + 48 + k];
+                } else if (g == 1) {
+                    // components 4..6 = quaternion x, y, z
+                    float q1[16], q2[16], q3[16];
+                    tmem_ld16(lane_addr + 32 + 0, q1);
+                    tmem_ld16(lane_addr + 32 + 16, q2);
+                    tmem_ld16(lane_addr + 32 + 32, q3);
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
                         if (k < K && valid)
-                            a.quat[gbase + k] = make_float4(q0[k] + b2[rbase + 48 + k], q1[k] + b2[rbase + 64 + k],
+                            a.quat[gbase + k] = make_float4(qw[k], q1[k] + b2[rbase + 64 + k],
                                                             q2[k] + b2[rbase + 80 + k], q3[k] + b2[rbase + 96 + k]);
                 } else if (g == 2) {
                     float c0v[16], c1v[16], c2v[16];
@@ -304,13 +310,13 @@ __global__ void __launch_bounds__(kTCRows) k_decode_fwd_tc(ViewTable vt, TcArgs 
                             a.color[gbase + k] = make_float4(sig(c0v[k] + b2[rbase + k]), sig(c1v[k] + b2[rbase + 16 + k]),
                                                              sig(c2v[k] + b2[rbase + 32 + k]), 0.f);
                 } else {
-                    for (int cq = 0; cq < nc; cq += 4) {
+                    {
                         float f0[16], f1[16], f2[16], f3[16];
-                        tmem_ld16(lane_addr + 32 + 16 * cq, f0);
-                        tmem_ld16(lane_addr + 32 + 16 * (cq + 1), f1);
-                        tmem_ld16(lane_addr + 32 + 16 * (cq + 2), f2);
-                        tmem_ld16(lane_addr + 32 + 16 * (cq + 3), f3);
-                        const int cc = c0 + cq;
+                        tmem_ld16(lane_addr + 32, f0);
+                        tmem_ld16(lane_addr + 32 + 16, f1);
+                        tmem_ld16(lane_addr + 32 + 32, f2);
+                        tmem_ld16(lane_addr + 32 + 48, f3);
+                        const int cc = c0;
                         const float *bb = b2 + rbase + 16 * cc;
 #pragma unroll
                         for (int k = 0; k < 16; ++k)
@@ -346,7 +352,9 @@ cudaError_t launch_decode_fwd_tc(const ViewTable &vt, int A, int K, int NF, cons
     if (K < 1 || K > 16) return cudaErrorInvalidValue;
     const int rows = A * vt.n;
     const int tiles = (rows + kTCRows - 1) / kTCRows;
-    const int blocks = std::max(1, std::min(tiles, num_sms));
+    // several CTAs per SM overlap one CTA's MMA waits with another's epilogue;
+    // each holds 128 TMEM columns (4 x 128 = the SM's 512)
+    const int blocks = std::max(1, std::min(tiles, num_sms * 3));
 #define UPS_TC(NFV, KDV)                                                                             \
     do {                                                                                             \
         const size_t smem = (size_t)tc_layout<KDV>(NFV).total;                                      \
