@@ -287,6 +287,86 @@ ups_status ups_profile_enable(ups_ctx *ctx, int on);
 ups_status ups_profile_read(ups_ctx *ctx, char *buf, size_t len, long long *launches);
 
 /* ---------------------------------------------------------------------- */
+/* serving: request queue with continuous batching                        */
+/* ---------------------------------------------------------------------- */
+
+/* UP-SLAM runs tracking and mapping as parallel threads over one map (Sec. 3,
+ * Sec. 3.4): tracking renders the map at a pose to form residuals, mapping
+ * optimises the map over keyframes.  The server keeps the anchor scene
+ * resident and serves both as requests.  Worker threads (one per slot, each
+ * with its own context, stream and buffers) pack the requests waiting in the
+ * queue, up to max_batch_views views and within the memory budget, into ONE
+ * batched decode + forward + backward; slots run concurrently, so requests
+ * that arrive while other batches are on the GPU are admitted as slots and
+ * memory free up.  Completion is stamped by a stream callback. */
+
+typedef struct ups_server ups_server;
+
+enum { UPS_REQ_TRACK = 0, UPS_REQ_MAP = 1 };
+
+/* One request.  Host fields are copied by ups_submit; device buffers are the
+ * caller's and must stay valid until the request is done.
+ *  kind      UPS_REQ_TRACK: render `cams[0]` at `levels` pyramid levels (level
+ *            l: intrinsics and size divided by 2^l), forward + pose-only
+ *            backward.  UPS_REQ_MAP: render n_views keyframes, full backward.
+ *  targets   device images of the request's own views (level 0 first for
+ *            tracking), layouts as for ups_loss_weighted; weight may be NULL
+ *  loss      device float[1]: weighted image loss of the request (Eq. 4/14
+ *            image part, normalised by the request's pixels)
+ *  d_pose    device float[6 * n_views] (tracking: [6], summed over levels),
+ *            OVERWRITTEN
+ *  d_mlp, d_anchors  mapping only, optional (NULL pointers = not wanted):
+ *            ACCUMULATED (+=) MLP / anchor gradients of the request */
+typedef struct {
+    int kind;
+    int n_views;
+    int levels;
+    const ups_camera *cams;
+    ups_targets targets;
+    float *loss;
+    float *d_pose;
+    ups_mlp d_mlp;
+    ups_anchors d_anchors;
+} ups_request;
+
+typedef struct {
+    int slots;            /* batches in flight at once (worker threads), >= 1 */
+    int max_batch_views;  /* views packed into one batch (<= UPS_MAX_VIEWS) */
+    int batching;         /* 1: continuous batching; 0: one request per batch */
+    double memory_budget_gb; /* admission: estimated scratch of in-flight batches */
+    ups_loss_cfg loss;    /* image-loss weights (lambda_scale unused) */
+} ups_server_config;
+
+typedef struct {
+    int status;          /* UPS_PENDING, UPS_OK, or the error of the request */
+    double submit_ms;    /* host steady-clock times, ms since server creation */
+    double start_ms;
+    double end_ms;       /* stream completion of the request's batch */
+    int batch_id;
+    int batch_requests;  /* requests packed into that batch */
+    int batch_views;
+} ups_result;
+
+/* scene: anchors + MLP weights on the device (caller-owned, kept resident;
+ * must stay valid and unmodified while requests are in flight). */
+ups_status ups_server_create(const ups_config *cfg, const ups_server_config *scfg, int device,
+                             const ups_anchors *scene, const ups_mlp *mlp, ups_server **out);
+/* Finishes every queued request, then stops the workers and frees buffers. */
+ups_status ups_server_destroy(ups_server *srv);
+ups_status ups_submit(ups_server *srv, const ups_request *req, uint64_t *ticket);
+/* UPS_OK and *out filled when the request is done (its entry is then
+ * released), UPS_PENDING while queued or running, UPS_ERR_ARG for an unknown
+ * ticket. */
+ups_status ups_poll(ups_server *srv, uint64_t ticket, ups_result *out);
+/* Removes a request that has not started: UPS_OK (its poll then reports
+ * UPS_ERR_CANCELLED), UPS_ERR_STATE if it already started. */
+ups_status ups_cancel(ups_server *srv, uint64_t ticket);
+/* Blocks until the queue is empty and no batch is in flight, at most
+ * timeout_ms (UPS_ERR_TIMEOUT then). */
+ups_status ups_server_wait_idle(ups_server *srv, double timeout_ms);
+const char *ups_server_last_error(const ups_server *srv);
+
+/* ---------------------------------------------------------------------- */
 /* allocation-free forward                                                */
 /* ---------------------------------------------------------------------- */
 

@@ -65,6 +65,23 @@ class MLP(C.Structure):
     _fields_ = [("w1", _p), ("b1", _p), ("w2", _p), ("b2", _p)]
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", _i), ("n_views", _i), ("levels", _i), ("cams", C.POINTER(Camera)),
+                ("targets", Targets), ("loss", _p), ("d_pose", _p), ("d_mlp", MLP),
+                ("d_anchors", Anchors)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("slots", _i), ("max_batch_views", _i), ("batching", _i),
+                ("memory_budget_gb", C.c_double), ("loss", LossCfg)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", _i), ("submit_ms", C.c_double), ("start_ms", C.c_double),
+                ("end_ms", C.c_double), ("batch_id", _i), ("batch_requests", _i),
+                ("batch_views", _i)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_views", _i), ("n_gaussian_views", _ll), ("n_visible", _ll),
                 ("n_instances", _ll), ("n_tiles", _ll), ("n_pixels", _ll), ("key_bits", _i)]
@@ -74,7 +91,9 @@ class Stats(C.Structure):
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
-           "ups_profile_enable", "ups_profile_read", "ups_render_forward_static"]
+           "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
+           "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
+           "ups_server_wait_idle", "ups_server_last_error"]
 
 _lib = None
 
@@ -116,6 +135,15 @@ def load():
     L.ups_profile_read.argtypes = [_p, C.c_char_p, C.c_size_t, C.POINTER(_ll)]
     L.ups_render_forward_static.argtypes = [C.POINTER(Config), C.POINTER(Gaussians), C.POINTER(Camera),
                                             _i, C.POINTER(Images), _p]
+    L.ups_server_create.argtypes = [C.POINTER(Config), C.POINTER(ServerConfig), _i, C.POINTER(Anchors),
+                                    C.POINTER(MLP), C.POINTER(_p)]
+    L.ups_server_destroy.argtypes = [_p]
+    L.ups_submit.argtypes = [_p, C.POINTER(Request), C.POINTER(C.c_uint64)]
+    L.ups_poll.argtypes = [_p, C.c_uint64, C.POINTER(Result)]
+    L.ups_cancel.argtypes = [_p, C.c_uint64]
+    L.ups_server_wait_idle.argtypes = [_p, C.c_double]
+    L.ups_server_last_error.argtypes = [_p]
+    L.ups_server_last_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -354,6 +382,101 @@ def render_forward_static(g: GaussianSet, cams, out, n_feat, stream=None, **over
     if st != UPS_OK:
         raise UpsError(st, L.ups_last_error(None).decode())
     return out
+
+
+TRACK, MAP = 0, 1
+
+
+class Server:
+    """Request queue with continuous batching over a resident anchor scene."""
+
+    def __init__(self, anchors, mlp, n_feat=16, k=10, slots=2, max_batch_views=16, batching=True,
+                 memory_budget_gb=64.0, device=0, loss=None, **overrides):
+        L = load()
+        cfg = Config()
+        L.ups_config_default(C.byref(cfg))
+        cfg.n_feat = n_feat
+        cfg.k = k
+        for key, val in overrides.items():
+            setattr(cfg, key, val)
+        lc = loss or {}
+        sc = ServerConfig(slots, max_batch_views, int(batching), memory_budget_gb,
+                          LossCfg(lc.get("lambda_color", 1.0), lc.get("lambda_depth", 1.0),
+                                  lc.get("lambda_feat", 1.0), 0.0, int(lc.get("l2", False))))
+        self._keep = (anchors, mlp)
+        A = int(anchors["pos"].shape[0])
+        ca = Anchors(A, _ptr(anchors["pos"]), _ptr(anchors["feat"]), _ptr(anchors["offsets"]),
+                     _ptr(anchors["scaling"]))
+        cm = MLP(_ptr(mlp["w1"]), _ptr(mlp["b1"]), _ptr(mlp["w2"]), _ptr(mlp["b2"]))
+        h = _p()
+        st = L.ups_server_create(C.byref(cfg), C.byref(sc), device, C.byref(ca), C.byref(cm), C.byref(h))
+        if st != UPS_OK:
+            raise UpsError(st, "ups_server_create failed: " + L.ups_last_error(None).decode())
+        self._h, self._L = h, L
+        self.n_feat, self.k, self.A = n_feat, k, A
+        self._live = {}
+
+    def submit(self, kind, cams, targets, loss, d_pose, d_mlp=None, d_anchors=None, levels=3):
+        """targets: dict of device tensors (colour, depth, feature, weight) of the request's views."""
+        cc = make_cameras(cams)
+        req = Request(kind, len(cams), levels, cc,
+                      Targets(_ptr(targets["color"]), _ptr(targets["depth"]),
+                              _ptr(targets.get("feat")) if self.n_feat else None,
+                              _ptr(targets.get("weight"))),
+                      _ptr(loss), _ptr(d_pose),
+                      MLP(*[_ptr(d_mlp[k]) for k in ("w1", "b1", "w2", "b2")]) if d_mlp else MLP(),
+                      Anchors(self.A, *[_ptr(d_anchors[k]) for k in ("pos", "feat", "offsets", "scaling")])
+                      if d_anchors else Anchors())
+        t = C.c_uint64(0)
+        st = self._L.ups_submit(self._h, C.byref(req), C.byref(t))
+        if st != UPS_OK:
+            raise UpsError(st, "ups_submit rejected the request")
+        self._live[t.value] = (targets, loss, d_pose, d_mlp, d_anchors)
+        return t.value
+
+    def poll(self, ticket):
+        """-> None while pending, else a dict (status, times in ms, batch info)."""
+        r = Result()
+        st = self._L.ups_poll(self._h, ticket, C.byref(r))
+        if st == UPS_PENDING:
+            return None
+        if st != UPS_OK:
+            raise UpsError(st, "unknown ticket")
+        self._live.pop(ticket, None)
+        return {k: getattr(r, k) for k, _ in Result._fields_}
+
+    def cancel(self, ticket):
+        return self._L.ups_cancel(self._h, ticket)
+
+    def wait(self, ticket, timeout_s=120.0):
+        import time
+        t_end = time.time() + timeout_s
+        while True:
+            res = self.poll(ticket)
+            if res is not None:
+                return res
+            if time.time() > t_end:
+                raise UpsError(5, "request did not finish in time")
+            time.sleep(0.0005)
+
+    def wait_idle(self, timeout_s=120.0):
+        st = self._L.ups_server_wait_idle(self._h, timeout_s * 1e3)
+        if st != UPS_OK:
+            raise UpsError(st, "server did not drain in time")
+
+    def last_error(self):
+        return self._L.ups_server_last_error(self._h).decode()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ups_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> str:

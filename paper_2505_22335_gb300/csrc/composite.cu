@@ -185,19 +185,21 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_fwd(
 
 template <int NF>
 __global__ void __launch_bounds__(256) k_loss(
-    ViewTable vt, float lc, float ld, float lf, int l2, float inv_norm,
+    ViewTable vt, int v0, int tgt_base, float lc, float ld, float lf, int l2, float inv_norm,
     const float *__restrict__ color, const float *__restrict__ depth,
     const float *__restrict__ feat, const float *__restrict__ t_color,
     const float *__restrict__ t_depth, const float *__restrict__ t_feat,
     const float *__restrict__ weight, float *__restrict__ g_color, float *__restrict__ g_depth,
     float *__restrict__ g_feat, float *__restrict__ loss) {
-    const DevView &cam = vt.v[blockIdx.y];
+    // view v0 + blockIdx.y; targets and weights are indexed from pixel tgt_base
+    const DevView &cam = vt.v[v0 + blockIdx.y];
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
+    const size_t PT = P - (size_t)tgt_base;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     float acc = 0.f;
     if (p < HW) {
-        float w = weight ? weight[P + p] : 1.f;
+        float w = weight ? weight[PT + p] : 1.f;
         auto term = [&](float r, float lam, float *g, size_t idx) {
             float val = l2 ? r * r : fabsf(r);
             float der = l2 ? 2.f * r : (float)((r > 0.f) - (r < 0.f));
@@ -207,13 +209,13 @@ __global__ void __launch_bounds__(256) k_loss(
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             size_t idx = 3 * P + c * HW + p;
-            term(color[idx] - t_color[idx], lc, g_color, idx);
+            term(color[idx] - t_color[3 * PT + c * HW + p], lc, g_color, idx);
         }
-        term(depth[P + p] - t_depth[P + p], ld, g_depth, P + p);
+        term(depth[P + p] - t_depth[PT + p], ld, g_depth, P + p);
 #pragma unroll
         for (int c = 0; c < NF; ++c) {
             size_t idx = NF * P + c * HW + p;
-            term(feat[idx] - t_feat[idx], lf, g_feat, idx);
+            term(feat[idx] - t_feat[NF * PT + c * HW + p], lf, g_feat, idx);
         }
     }
 #pragma unroll
@@ -444,10 +446,13 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
 
 cudaError_t launch_loss(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                         int l2, float inv_norm, const ups_images &img, const ups_targets &tgt,
-                        const ups_images &grad, float *loss, cudaStream_t st) {
-    dim3 grid((max_hw + 255) / 256, vt.n), block(256);
+                        const ups_images &grad, float *loss, cudaStream_t st, int v0, int v1) {
+    if (v1 < 0) v1 = vt.n;
+    if (v1 <= v0) return cudaSuccess;
+    const int tgt_base = vt.v[v0].pix_off;
+    dim3 grid((max_hw + 255) / 256, v1 - v0), block(256);
 #define UPS_LOSS(NFV)                                                                          \
-    k_loss<NFV><<<grid, block, 0, st>>>(vt, lc, ld, lf, l2, inv_norm, img.color, img.depth,    \
+    k_loss<NFV><<<grid, block, 0, st>>>(vt, v0, tgt_base, lc, ld, lf, l2, inv_norm, img.color, img.depth, \
                                         img.feat, tgt.color, tgt.depth, tgt.feat, tgt.weight,   \
                                         grad.color, grad.depth, grad.feat, loss)
     switch (n_feat) {

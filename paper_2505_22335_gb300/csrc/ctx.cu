@@ -37,7 +37,7 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st);
 cudaError_t launch_loss(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                         int l2, float inv_norm, const ups_images &img, const ups_targets &tgt,
-                        const ups_images &grad, float *loss, cudaStream_t st);
+                        const ups_images &grad, float *loss, cudaStream_t st, int v0 = 0, int v1 = -1);
 cudaError_t launch_scale_mean(const float4 *scale, size_t n, float coef, float *loss,
                               cudaStream_t st);
 cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
@@ -254,6 +254,29 @@ ups_status set_device(ups_ctx *c) {
 namespace ups {
 // Message returned by ups_last_error(NULL) (calls made without a context).
 void set_global_error(const std::string &msg) { g_create_error = msg; }
+
+// Loss of views [v0, v1) of the last forward on c, normalised by their pixel
+// count; targets and weights are laid out from view v0 (pixel offset 0).
+ups_status loss_views(ups_ctx *c, const ups_images *img, const ups_targets *tgt,
+                      const ups_loss_cfg *lcfg, int v0, int v1, float *loss_dev, ups_images *dL,
+                      cudaStream_t st) {
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "loss_views needs a forward first");
+    if (v0 < 0 || v1 > c->vt.n || v1 <= v0) return fail(c, UPS_ERR_ARG, "bad view range");
+    size_t pix = 0;
+    int mhw = 0;
+    for (int v = v0; v < v1; ++v) {
+        const size_t hw = (size_t)c->vt.v[v].W * c->vt.v[v].H;
+        pix += hw;
+        mhw = std::max(mhw, (int)hw);
+    }
+    stage_begin(c, "loss", st);
+    UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
+    UPS_CUDA(c, launch_loss(c->vt, c->cfg.n_feat, mhw, lcfg->lambda_color, lcfg->lambda_depth,
+                            lcfg->lambda_feat, lcfg->l2, (float)(1.0 / (double)pix), *img, *tgt, *dL,
+                            loss_dev, st, v0, v1));
+    stage_end(c, st, 1);
+    return UPS_OK;
+}
 }  // namespace ups
 
 extern "C" {
