@@ -423,6 +423,113 @@ def run_reference(args, wl_name):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# serving mix: plain FIFO path vs continuous batching
+# ---------------------------------------------------------------------------
+
+SERVE = dict(A=500_000, K=10, NF=16, W=640, H=480, fx=600.0, track_rate=30.0, map_rate=5.0,
+             levels=3, map_views=(4, 8))
+
+
+def serving_schedule(seconds, seed=2):
+    """Open-loop arrival schedule: (time_s, kind, n_views) sorted by time."""
+    rng = np.random.default_rng(seed)
+    ev = []
+    for kind, rate in ((0, SERVE["track_rate"]), (1, SERVE["map_rate"])):
+        t = rng.exponential(1.0 / rate)
+        while t < seconds:
+            nv = 1 if kind == 0 else int(rng.integers(SERVE["map_views"][0], SERVE["map_views"][1] + 1))
+            ev.append((t, kind, nv))
+            t += rng.exponential(1.0 / rate)
+    ev.sort()
+    return ev
+
+
+def run_serving(args):
+    import torch
+    from paper_2505_22335_gb300 import binding as B
+    from paper_2505_22335_gb300 import scenes
+    torch.cuda.set_device(0)
+    c = SERVE
+    anc = scenes.anchors(0, c["A"], c["K"])
+    mlp = scenes.mlp_weights(1000, c["K"], c["NF"])
+    ad, md = B.anchors_to_device(anc, mlp)
+    sched = serving_schedule(args.serve_seconds)
+    # request inputs from small pools (contents do not change the work)
+    rng = np.random.default_rng(3)
+    poses = scenes.arc_poses(4, 16)
+    def cam(i):
+        return scenes.Camera(c["fx"], c["fx"], c["W"] / 2, c["H"] / 2, c["W"], c["H"], poses[i % 16],
+                             float(rng.uniform()))
+    def pyr(cm):
+        return [scenes.Camera(cm.fx / 2 ** l, cm.fy / 2 ** l, cm.cx / 2 ** l, cm.cy / 2 ** l, cm.width >> l,
+                              cm.height >> l, cm.T_cw, cm.t_norm) for l in range(c["levels"])]
+    track_tg = [B.targets_to_device(scenes.targets(10 + i, pyr(cam(i)), c["NF"], weighted=True)) for i in range(4)]
+    map_tg = {nv: B.targets_to_device(scenes.targets(20 + nv, [cam(j) for j in range(nv)], c["NF"], weighted=True))
+              for nv in range(c["map_views"][0], c["map_views"][1] + 1)}
+    pix_track = sum((c["W"] >> l) * (c["H"] >> l) for l in range(c["levels"]))
+    out = {}
+    for mode in ("plain", "served"):
+        srv = B.Server(ad, md, n_feat=c["NF"], k=c["K"], slots=1 if mode == "plain" else 2,
+                       max_batch_views=24, batching=(mode == "served"), memory_budget_gb=120.0,
+                       decode_bf16=1)
+        pool = [dict(loss=torch.zeros(1, device="cuda"), pose=torch.zeros(6 * 8, device="cuda"),
+                     mlp={k: torch.zeros_like(v) for k, v in md.items()}) for _ in range(64)]
+        def submit(i, kind, nv, cams=None):
+            o = pool[i % len(pool)]
+            if kind == 0:
+                cm = cam(i)
+                return srv.submit(B.TRACK, [cm], track_tg[i % 4], o["loss"], o["pose"], levels=c["levels"])
+            cms = [cam(i + j) for j in range(nv)]
+            return srv.submit(B.MAP, cms, map_tg[nv], o["loss"], o["pose"], d_mlp=o["mlp"])
+        # warm-up: every request shape once
+        for i, (kind, nv) in enumerate([(0, 1)] + [(1, v) for v in map_tg]):
+            srv.wait(submit(1000 + i, kind, nv))
+        srv.wait_idle()
+        torch.cuda.synchronize()
+        lat = {0: [], 1: []}
+        pending = {}
+        t0 = time.perf_counter()
+        done_pix = 0
+        i = 0
+        last_end = t0
+        while i < len(sched) or pending:
+            now = time.perf_counter() - t0
+            while i < len(sched) and sched[i][0] <= now:
+                ta, kind, nv = sched[i]
+                t_sub = time.perf_counter()
+                tk = submit(i, kind, nv)
+                pending[tk] = (ta, kind, nv, t_sub)
+                i += 1
+            for tk in list(pending):
+                res = srv.poll(tk)
+                if res is None:
+                    continue
+                ta, kind, nv, t_sub = pending.pop(tk)
+                # completion in this clock: submit time + (server end - server submit)
+                t_end = (t_sub - t0) + (res["end_ms"] - res["submit_ms"]) / 1e3
+                lat[kind].append((t_end - ta) * 1e3)
+                done_pix += pix_track if kind == 0 else nv * c["W"] * c["H"]
+                last_end = max(last_end, t0 + t_end)
+            time.sleep(0.0002)
+        wall = last_end - t0 - sched[0][0]
+        srv.close()
+        q = lambda a, p: float(np.percentile(np.array(a), p)) if a else None
+        out[mode] = dict(mpix_per_s=round(done_pix / wall / 1e6, 2),
+                         tracking_p50_ms=round(q(lat[0], 50), 2), tracking_p99_ms=round(q(lat[0], 99), 2),
+                         mapping_p50_ms=round(q(lat[1], 50), 2), mapping_p99_ms=round(q(lat[1], 99), 2),
+                         requests=len(lat[0]) + len(lat[1]))
+    line = {"metric": "serving mix: fwd+bwd Mpixel/s and tracking p50/p99 latency, plain vs served",
+            "value": out["served"]["mpix_per_s"], "unit": "Mpixel/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 (bf16 decode GEMMs)", "data": "synthetic",
+            "config": {"workload": f"serving_mix_{c['A'] // 1000}k_anchors_x{c['K']}",
+                       "tracking": f"{c['track_rate']}/s, {c['levels']} pyramid levels from {c['W']}x{c['H']}, fwd + pose-only bwd",
+                       "mapping": f"{c['map_rate']}/s, {c['map_views'][0]}-{c['map_views'][1]} keyframes {c['W']}x{c['H']}, full bwd",
+                       "seconds": args.serve_seconds, "arrivals": "open-loop Poisson, seed 2"},
+            "plain": out["plain"], "served": out["served"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,7 +541,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--decode-bf16", action="store_true",
                     help="decode MLP GEMMs in BF16 on the tensor cores (FP32 accumulation)")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving mix (500k anchors resident): plain FIFO path vs continuous batching")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     args = ap.parse_args()
+    if args.serving:
+        from paper_2505_22335_gb300 import build as _b
+        _b.build()
+        run_serving(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
