@@ -424,17 +424,24 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
                     float dy = 0.f;
                     if (o < ng && valid_r) {
                         const int row_o = r0 + o;
-                        const float4 *w = reinterpret_cast<const float4 *>(W2s + row_o * kW2S);
-                        float y = sb2[row_o];
-#pragma unroll
-                        for (int qq = 0; qq < kH / 4; ++qq) {
-                            float4 ww = w[qq];
-                            y = fmaf(ww.x, h[4 * qq], y);
-                            y = fmaf(ww.y, h[4 * qq + 1], y);
-                            y = fmaf(ww.z, h[4 * qq + 2], y);
-                            y = fmaf(ww.w, h[4 * qq + 3], y);
-                        }
                         const int k = o / m, c = o - k * m;
+                        // the pre-activation is needed only where an output
+                        // activation has a derivative (not for the linear
+                        // quaternion and feature outputs)
+                        const bool need_y = g == 0 || g == 2 || (g == 1 && c < 3);
+                        float y = 0.f;
+                        if (need_y) {
+                            const float4 *w = reinterpret_cast<const float4 *>(W2s + row_o * kW2S);
+                            y = sb2[row_o];
+#pragma unroll
+                            for (int qq = 0; qq < kH / 4; ++qq) {
+                                float4 ww = w[qq];
+                                y = fmaf(ww.x, h[4 * qq], y);
+                                y = fmaf(ww.y, h[4 * qq + 1], y);
+                                y = fmaf(ww.z, h[4 * qq + 2], y);
+                                y = fmaf(ww.w, h[4 * qq + 3], y);
+                            }
+                        }
                         const float gin = SG[r * L.SGS + o];
                         if (g == 0) {
                             float s = sigm(y);
@@ -454,7 +461,6 @@ __global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, Dec
                         } else {
                             dy = gin;
                         }
-                        (void)k;
                     }
                     DY[r * L.DYS + o] = dy;
                 }
