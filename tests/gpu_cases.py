@@ -60,7 +60,21 @@ def feat_magnitude(proj, g, cam, nf):
     return oracle.render(proj, ga, cam, CFG, nf)["feat"]
 
 
-def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None):
+def last_blended_ids(nc, lst, rng, tile_base=0, id_base=0):
+    """Id of the last blended Gaussian of every pixel (-1 if none), from n_contrib
+    and the tile lists.  List positions can shift between two correct renders
+    when a tile list holds an extra Gaussian that blends nothing (a rect edge or
+    depth tie decided differently), so pixels are compared by this id."""
+    H, W = nc.shape
+    tx = (W + 15) // 16
+    t = (np.arange(H)[:, None] // 16) * tx + (np.arange(W)[None, :] // 16) + tile_base
+    pos = rng[t, 0].astype(np.int64) + nc.astype(np.int64) - 1
+    pos = np.clip(pos, 0, max(len(lst) - 1, 0))
+    ids = lst[pos].astype(np.int64) - id_base if len(lst) else np.zeros_like(pos)
+    return np.where(nc > 0, ids, -1)
+
+
+def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None, last_ids=None):
     flagged = 0
     total = 0
     for vi, (gv, rv) in enumerate(zip(gpu_views, ref_views)):
@@ -76,7 +90,11 @@ def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None):
             tol = PIX_ATOL + PIX_RTOL * scale
             bad = (diff > tol) & np.broadcast_to(ok, diff.shape)
             assert not bad.any(), (k, int(bad.sum()), float(diff[bad].max()))
-        assert np.array_equal(gv["n_contrib"][ok], rv["n_contrib"][ok])
+        if last_ids is None:
+            assert np.array_equal(gv["n_contrib"][ok], rv["n_contrib"][ok])
+        else:
+            a, b = last_ids[vi]
+            assert np.array_equal(a[ok], b[ok]), int((a[ok] != b[ok]).sum())
     assert flagged <= max_flag_frac * total, (flagged, total)
     return flagged
 

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_cases import (CFG, MARGIN, PIX_ATOL, PIX_RTOL, assert_pixels, feat_magnitude, rel_l2,
+from gpu_cases import (CFG, MARGIN, PIX_ATOL, PIX_RTOL, assert_pixels, feat_magnitude, last_blended_ids, rel_l2,
                        round_cams, round_dict, split_images)
 from paper_2505_22335_gb300 import binding as B
 from paper_2505_22335_gb300 import scenes
@@ -69,7 +69,12 @@ def _check_view0(res, nf, grads):
     gpu_views = split_images(res["img"], res["cams"], nf)
     _invariants(gpu_views)
     mag = [feat_magnitude(pr, gview, cam, nf)]
-    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag)
+    glist = res["R"].copy_buffer(0)
+    grng = res["R"].copy_buffer(2).reshape(-1, 2)
+    lst, rng = oracle.tile_lists(pr, cam, CFG)
+    ids = [(last_blended_ids(gpu_views[0]["n_contrib"], glist, grng, 0, 0),
+            last_blended_ids(ref["n_contrib"], lst, rng))]
+    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag, last_ids=ids)
     if not grads:
         return
     # 2D gradient records of view 0 against the oracle blending backward fed
