@@ -74,7 +74,15 @@ def last_blended_ids(nc, lst, rng, tile_base=0, id_base=0):
     return np.where(nc > 0, ids, -1)
 
 
-def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None, last_ids=None):
+def depth_tie(za, zb, ulps=4):
+    """True where two depths are within `ulps` float32 ulps (order may flip)."""
+    za = np.asarray(za, np.float32)
+    zb = np.asarray(zb, np.float32)
+    return np.abs(za.view(np.int32).astype(np.int64) - zb.view(np.int32).astype(np.int64)) <= ulps
+
+
+def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None, last_ids=None,
+                  depth=None):
     flagged = 0
     total = 0
     for vi, (gv, rv) in enumerate(zip(gpu_views, ref_views)):
@@ -94,7 +102,16 @@ def assert_pixels(gpu_views, ref_views, nf, max_flag_frac=0.01, feat_mag=None, l
             assert np.array_equal(gv["n_contrib"][ok], rv["n_contrib"][ok])
         else:
             a, b = last_ids[vi]
-            assert np.array_equal(a[ok], b[ok]), int((a[ok] != b[ok]).sum())
+            bad = ok & (a != b)
+            if bad.any() and depth is not None:
+                # the two renders ordered a depth near-tie differently: allowed
+                # only when the two candidates' float32 depths are within 4 ulps
+                z = depth[vi]
+                tie = depth_tie(z[np.maximum(a[bad], 0)], z[np.maximum(b[bad], 0)])
+                assert tie.all(), int((~tie).sum())
+                assert bad.sum() <= 1e-4 * bad.size + 10, int(bad.sum())
+            else:
+                assert not bad.any(), int(bad.sum())
     assert flagged <= max_flag_frac * total, (flagged, total)
     return flagged
 

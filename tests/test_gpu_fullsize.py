@@ -74,7 +74,7 @@ def _check_view0(res, nf, grads):
     lst, rng = oracle.tile_lists(pr, cam, CFG)
     ids = [(last_blended_ids(gpu_views[0]["n_contrib"], glist, grng, 0, 0),
             last_blended_ids(ref["n_contrib"], lst, rng))]
-    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag, last_ids=ids)
+    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag, last_ids=ids, depth=[pr["pcam"][:, 2]])
     if not grads:
         return
     # 2D gradient records of view 0 against the oracle blending backward fed
