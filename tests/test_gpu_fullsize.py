@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_cases import (CFG, MARGIN, PIX_ATOL, PIX_RTOL, assert_pixels, feat_magnitude, last_blended_ids, rel_l2,
+from gpu_cases import (CFG, MARGIN, PIX_ATOL, PIX_RTOL, assert_pixels, feat_magnitude, last_blended_ids, rel_l2, tie_explained,
                        round_cams, round_dict, split_images)
 from paper_2505_22335_gb300 import binding as B
 from paper_2505_22335_gb300 import scenes
@@ -74,7 +74,8 @@ def _check_view0(res, nf, grads):
     lst, rng = oracle.tile_lists(pr, cam, CFG)
     ids = [(last_blended_ids(gpu_views[0]["n_contrib"], glist, grng, 0, 0),
             last_blended_ids(ref["n_contrib"], lst, rng))]
-    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag, last_ids=ids, depth=[pr["pcam"][:, 2]])
+    tie = [tie_explained(gpu_views[0]["n_contrib"], ref["n_contrib"], lst, rng, pr["pcam"][:, 2])]
+    assert_pixels(gpu_views[:1], [ref], nf, feat_mag=mag, last_ids=ids, tie_ok=tie)
     if not grads:
         return
     # 2D gradient records of view 0 against the oracle blending backward fed
