@@ -53,12 +53,11 @@ cudaError_t launch_decode_fwd_tc(const ViewTable &vt, int A, int K, int NF, cons
                                  int num_sms, cudaStream_t st);
 size_t decode_tc_smem_bytes(int NF, int bf16);
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                              const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask,
-                              const ups_mlp *d_mlp, const ups_anchors *d_anc, float *d_pose,
-                              int num_sms, cudaStream_t st);
-
-size_t decode_bwd_smem_bytes(int K, int NF, int V);
-size_t decode_smem_limit();
+                              const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
+                              const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
+                              int num_sms, long long *launches, cudaStream_t st);
+size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF);
+bool decode_bwd_fits(int K, int NF);
 
 cudaError_t DevBuf::reserve(size_t want) {
     if (want <= bytes) return cudaSuccess;
@@ -104,6 +103,7 @@ struct ups_ctx {
     // scratch
     DevBuf xyzo, conic, rect, count, dkey0, dkey1, dval0, dval1, cnt_sorted, off, scan_scr;
     DevBuf ikey0, ikey1, ival0, ival1, ranges, g2;
+    DevBuf dec_scratch;  // decode backward: X, H, dL/dY, dL/dZ rows for the weight gradients
     SortScratch sort;
     uint32_t *dval_sorted = nullptr, *ikey_sorted = nullptr, *ival_sorted = nullptr;
     uint64_t *h_total = nullptr;  // pinned: [0] instance count, [1] device error flag
@@ -313,8 +313,8 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
     if (c.k < 1 || c.k > 16) return fail(nullptr, UPS_ERR_ARG, "k must be in [1, 16]");
     if (c.feat_dim != 32 || c.hidden != 32)
         return fail(nullptr, UPS_ERR_ARG, "feat_dim and hidden must be 32");
-    if (decode_bwd_smem_bytes(c.k, c.n_feat, UPS_MAX_VIEWS) > decode_smem_limit())
-        return fail(nullptr, UPS_ERR_ARG, "k * (11 + n_feat) too large for the decode backward tile");
+    if (!decode_bwd_fits(c.k, c.n_feat))
+        return fail(nullptr, UPS_ERR_ARG, "k * (11 + n_feat) too large for the decode backward tiling");
     if (!(c.alpha_min > 0.f) || !(c.alpha_max >= c.alpha_min) || !(c.alpha_max < 1.f) ||
         !(c.t_min >= 0.f) || !(c.dilation >= 0.f) || !(c.near_z > 0.f) || !(c.guard > 0.f))
         return fail(nullptr, UPS_ERR_ARG, "threshold out of range");
@@ -346,7 +346,7 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->sort.hist};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->d_err) cudaFree(c->d_err);
@@ -608,10 +608,16 @@ ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp
     if ((s = set_device(c)) != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
+    float *scratch = nullptr;
+    if ((mask & UPS_GRAD_MLP) && d_mlp) {
+        UPS_CUDA(c, c->dec_scratch.reserve(decode_bwd_scratch_bytes(anc->n, n_views, c->cfg.k, c->cfg.n_feat)));
+        scratch = c->dec_scratch.as<float>();
+    }
     stage_begin(c, "decode_bwd", st);
-    UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp,
-                                  d_anc, d_pose, c->num_sms, st));
-    stage_end(c, st, 1);
+    long long nk = 0;
+    UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp, d_anc,
+                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, scratch, c->d_err, c->num_sms, &nk, st));
+    stage_end(c, st, nk);
     return UPS_OK;
 }
 

@@ -7,11 +7,14 @@
 // and are read as float4 broadcasts (every lane of a warp reads the same
 // weight), so the inner loops are FMA-bound.
 //
-// Backward: tiles of rows are processed as small GEMMs in shared memory (see
-// k_decode_bwd); weight gradients accumulate per block and are flushed once.
+// Backward (FP32 data path): one thread per row recomputes each MLP group's
+// hidden layer, forms dL/dY of the group's outputs and propagates it to the
+// hidden layer and the MLP input (k_decode_bwd_rows); the hidden activations
+// and pre-activation gradients go to a feature-major scratch from which the
+// weight gradients are reduced by a separate kernel (decode_bwd_tc.cu).
 #include <algorithm>
 
-#include "common.cuh"
+#include "decode_bwd.cuh"
 
 namespace ups {
 
@@ -194,466 +197,211 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
 }
 
 // ---------------------------------------------------------------------------
-// backward
+// backward, per row (FP32)
 // ---------------------------------------------------------------------------
 
-struct DecodeGrads {
-    const float4 *d_mean_op, *d_scale, *d_quat, *d_color;
-    const float *d_feat;
-    float *g_w1, *g_b1, *g_w2, *g_b2;            // MLP (accumulated)
-    float *g_pos, *g_afeat, *g_offs, *g_ascale;  // anchors (accumulated)
-    float *g_pose;                               // [V][6] (accumulated)
-    unsigned mask;
-};
-
-// Tiled backward: R rows (anchor-major: row = anchor * V + view) per tile,
-// 8 threads per row.  Per MLP group g, all in shared memory:
-//   Z = X W1_g^T + b1 (H = act(Z), AP = act'(Z));  Y = H W2_g^T + b2 and
-//   DY = dL/dY through the output activation;  DZ = (DY W2_g) * AP;
-//   DX += DZ W1_g;  dW2_g += DY^T H, db2 += 1^T DY;  dW1_g += DZ^T X, db1 += 1^T DZ.
-// The weight-gradient products use 4x4 register micro-tiles over the R rows and
-// accumulate in per-block shared memory, flushed once per block.
-constexpr int kW1S = 132;  // W1^T row stride (conflict-free column walks)
-constexpr int kXS = 44;    // X / DX row stride (col 38 of X is 1: the db1 column)
-constexpr int kHS = 36;    // H / AP / DZ row stride
-constexpr int kW2S = 36;   // W2 row stride (col 32 of the accumulator: db2)
-constexpr int kAccW1S = 44;
-
-__host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
-
-template <int NF> struct BwdTile {
-    static constexpr int R = NF == 32 ? 16 : 32;  // rows per tile
-    static constexpr int TPR = 16;                // threads per row
-    static constexpr int T = TPR * R;             // threads
-};
-
-struct BwdLayout {
-    int n_out, DYS, acc_rows;
-    int oW1T, ob1, oW2, ob2, oX, oH, oAP, oDZ, oDY, oDX, oDLS, oDR, oAccW1, oAccW2, oPose, oInfo;
-    int oSG, SGS, oSM, total;
-};
-
-__host__ __device__ inline BwdLayout bwd_layout(int K, int NF, int R, int V) {
-    BwdLayout L;
-    L.n_out = K * (11 + NF);
-    int maxg = max(max(K, 7 * K), max(3 * K, K * NF));
-    L.DYS = pad4(maxg) + 4;
-    L.acc_rows = pad4(K) + pad4(7 * K) + pad4(3 * K) + pad4(K * NF);
-    int o = 0;
-    auto take = [&](int n) { int r = o; o += pad4(n); return r; };
-    L.oW1T = take(40 * kW1S);
-    L.ob1 = take(128);
-    L.oW2 = take(L.n_out * kW2S);
-    L.ob2 = take(L.n_out);
-    L.oX = take(R * kXS);
-    L.oH = take(R * kHS);
-    L.oAP = take(R * kHS);
-    L.oDZ = take(R * kHS);
-    L.oDY = take(R * L.DYS);
-    L.oDX = take(R * kXS);
-    L.oDLS = take(R * 4);
-    L.oDR = take(R * 4);
-    L.oAccW1 = take(128 * kAccW1S);
-    L.oAccW2 = take(L.acc_rows * kW2S);
-    L.oPose = take(3 * V);
-    L.oInfo = take(R * 8);  // per row: anchor, view, valid, dist, delta[3]
-    L.SGS = pad4(K * max(7, NF));  // staged dL/dG of one group, per row
-    L.oSG = take(R * L.SGS);
-    L.oSM = take(R * K * 4);       // staged dL/d(mean, opacity), per row and Gaussian
-    L.total = o;
-    return L;
+// One MLP group of one row: Z = W1_g x + b1 (recomputed), H = act(Z); for each
+// output o of the group the pre-activation Y_o (only where the output
+// activation has a derivative: opacity, scale, colour), DY_o = dL/dY_o, and
+// DH += DY_o W2[o]; DZ = DH * act'(Z); dx += DZ W1_g.  H, DY, DZ go to the
+// feature-major scratch for the weight-gradient kernel.
+template <int G, int NF>
+__device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs &da, const float *sW1T,
+                                          const float *sb1, const float *sW2, const float *sb2,
+                                          const DevView &cam, int an, bool valid, size_t gbase, int lr,
+                                          float dx[kDinP], float dls[3]) {
+    constexpr int M = G == 0 ? 1 : G == 1 ? 7 : G == 2 ? 3 : NF;
+    const int K = a.K;
+    const bool want_mlp = a.s.X != nullptr && valid;
+    const int ld = a.s.ld;
+    // Z = W1_g x + b1: input-outer so the 32 accumulators stay in registers
+    float h[kH];
+#pragma unroll
+    for (int j = 0; j < kH; ++j) h[j] = sb1[G * kH + j];
+    {
+        float x[kDinP], delta[3], dist;
+        mlp_input(da, cam, an, x, delta, dist);
+#pragma unroll 1
+        for (int i = 0; i < kDin; ++i) {
+            const float xi = x[i];
+            const float4 *w = reinterpret_cast<const float4 *>(sW1T + i * 128 + G * kH);
+#pragma unroll
+            for (int q = 0; q < kH / 4; ++q) {
+                const float4 ww = w[q];
+                h[4 * q] = fmaf(ww.x, xi, h[4 * q]);
+                h[4 * q + 1] = fmaf(ww.y, xi, h[4 * q + 1]);
+                h[4 * q + 2] = fmaf(ww.z, xi, h[4 * q + 2]);
+                h[4 * q + 3] = fmaf(ww.w, xi, h[4 * q + 3]);
+            }
+        }
+    }
+    unsigned relu_on = 0;  // ReLU derivative as a bit mask
+#pragma unroll
+    for (int j = 0; j < kH; ++j) {
+        if (G < 3) {
+            relu_on |= (h[j] > 0.f ? 1u : 0u) << j;
+            h[j] = fmaxf(h[j], 0.f);
+        } else {
+            h[j] = softplus(h[j]);
+        }
+    }
+    if (want_mlp)
+#pragma unroll
+        for (int j = 0; j < kH; ++j) a.s.H[(size_t)(G * kH + j) * ld + lr] = h[j];
+    float dh[kH];
+#pragma unroll
+    for (int j = 0; j < kH; ++j) dh[j] = 0.f;
+    const int r0 = dbwd::grp_r0(G, K);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const size_t gi = gbase + k;
+        float4 g4a = z4, g4b = z4;
+        if (valid) {
+            if (G == 0) g4a = a.d_mean_op[gi];
+            if (G == 1) {
+                g4a = a.d_scale[gi];
+                g4b = a.d_quat[gi];
+            }
+            if (G == 2) g4a = a.d_color[gi];
+        }
+        float4 f4 = z4;
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const int o = r0 + M * k + c;
+            const bool nl = G == 0 || G == 2 || (G == 1 && c < 3);
+            float gin;
+            if (G == 0) {
+                gin = g4a.w;
+            } else if (G == 1) {
+                gin = c == 0 ? g4a.x : c == 1 ? g4a.y : c == 2 ? g4a.z : c == 3 ? g4b.x : c == 4 ? g4b.y
+                                                                          : c == 5 ? g4b.z : g4b.w;
+            } else if (G == 2) {
+                gin = c == 0 ? g4a.x : c == 1 ? g4a.y : g4a.z;
+            } else {
+                if ((c & 3) == 0 && valid) f4 = reinterpret_cast<const float4 *>(a.d_feat + gi * NF)[c >> 2];
+                gin = (c & 3) == 0 ? f4.x : (c & 3) == 1 ? f4.y : (c & 3) == 2 ? f4.z : f4.w;
+            }
+            float dy = gin;
+            if (nl) {
+                const float s = sigm(out_row(sW2, sb2, o, h));
+                if (G == 1) {
+                    dy = gin * a.ascale[3 * an + c] * s * (1.f - s);
+                    dls[c] += gin * s;
+                } else {
+                    dy = gin * s * (1.f - s);
+                }
+            }
+            if (want_mlp) a.s.DY[(size_t)o * ld + lr] = dy;
+            const float4 *w = reinterpret_cast<const float4 *>(sW2 + o * kH);
+#pragma unroll
+            for (int q = 0; q < kH / 4; ++q) {
+                const float4 ww = w[q];
+                dh[4 * q] = fmaf(dy, ww.x, dh[4 * q]);
+                dh[4 * q + 1] = fmaf(dy, ww.y, dh[4 * q + 1]);
+                dh[4 * q + 2] = fmaf(dy, ww.z, dh[4 * q + 2]);
+                dh[4 * q + 3] = fmaf(dy, ww.w, dh[4 * q + 3]);
+            }
+        }
+    }
+    // DZ = DH * act'(Z): ReLU -> mask; SoftPlus -> sigmoid(Z) = 1 - exp(-H)
+#pragma unroll
+    for (int j = 0; j < kH; ++j) dh[j] *= G < 3 ? (float)((relu_on >> j) & 1u) : -expm1f(-h[j]);
+    if (want_mlp)
+#pragma unroll
+        for (int j = 0; j < kH; ++j) a.s.DZ[(size_t)(G * kH + j) * ld + lr] = dh[j];
+#pragma unroll 1
+    for (int i = 0; i < kDin; ++i) {
+        const float4 *w = reinterpret_cast<const float4 *>(sW1T + i * 128 + G * kH);
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < kH / 4; ++q) {
+            const float4 ww = w[q];
+            acc = fmaf(dh[4 * q], ww.x, acc);
+            acc = fmaf(dh[4 * q + 1], ww.y, acc);
+            acc = fmaf(dh[4 * q + 2], ww.z, acc);
+            acc = fmaf(dh[4 * q + 3], ww.w, acc);
+        }
+        dx[i] += acc;
+    }
 }
 
+// One thread per row (anchor-major), 128 rows per step of a grid-stride loop;
+// weights in shared memory read as broadcasts.
 template <int NF>
-__global__ void __launch_bounds__(BwdTile<NF>::T) k_decode_bwd(ViewTable vt, DecodeArgs a, DecodeGrads gr) {
-    constexpr int R = BwdTile<NF>::R, NT = BwdTile<NF>::T;
+__global__ void __launch_bounds__(dbwd::kRowsPerBlock) k_decode_bwd_rows(ViewTable vt, dbwd::Args a) {
     extern __shared__ float4 smem4[];
+    __shared__ float aPose[3 * UPS_MAX_VIEWS];
     float *sm = reinterpret_cast<float *>(smem4);
-    const int K = a.K, V = vt.n;
-    const BwdLayout L = bwd_layout(K, NF, R, V);
-    float *W1T = sm + L.oW1T, *sb1 = sm + L.ob1, *W2s = sm + L.oW2, *sb2 = sm + L.ob2;
-    float *X = sm + L.oX, *H = sm + L.oH, *AP = sm + L.oAP, *DZ = sm + L.oDZ, *DY = sm + L.oDY;
-    float *DX = sm + L.oDX, *DLS = sm + L.oDLS, *DR = sm + L.oDR;
-    float *AccW1 = sm + L.oAccW1, *AccW2 = sm + L.oAccW2, *aPose = sm + L.oPose;
-    float *Info = sm + L.oInfo;
-    float *SG = sm + L.oSG, *SM = sm + L.oSM;
-    constexpr int TPR = BwdTile<NF>::TPR;
-    const int tid = threadIdx.x;
-    const bool want_mlp = gr.mask & UPS_GRAD_MLP;
-    const bool want_anc = gr.mask & UPS_GRAD_ANCHOR;
-    const bool want_pose = gr.mask & UPS_GRAD_POSE;
-    // weights (W1 transposed) and zeroed accumulators
-    for (int i = tid; i < 40 * kW1S; i += NT) {
-        int ii = i / kW1S, h = i - ii * kW1S;
-        W1T[i] = (ii < kDin && h < 128) ? a.w1[h * kDin + ii] : 0.f;
+    const int n_out = dbwd::n_out(a.K, NF);
+    const DecodeArgs da{a.A, a.K, NF, n_out, a.pos, a.afeat, a.offs, a.ascale, a.w1, a.b1, a.w2, a.b2};
+    // W1 transposed [40][128] (inputs x hidden), b1, W2 [n_out][32], b2
+    float *sW1T = sm, *sb1 = sW1T + 4 * kH * kDinP, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + n_out * kH;
+    for (int i = threadIdx.x; i < kDinP * 4 * kH; i += blockDim.x) {
+        const int ii = i / (4 * kH), h = i - ii * (4 * kH);
+        sW1T[i] = ii < kDin ? a.w1[h * kDin + ii] : 0.f;
     }
-    for (int i = tid; i < 128; i += NT) sb1[i] = a.b1[i];
-    for (int i = tid; i < L.n_out * kW2S; i += NT) {
-        int o = i / kW2S, j = i - o * kW2S;
-        W2s[i] = j < kH ? a.w2[o * kH + j] : 0.f;
-    }
-    for (int i = tid; i < L.n_out; i += NT) sb2[i] = a.b2[i];
-    for (int i = tid; i < 128 * kAccW1S; i += NT) AccW1[i] = 0.f;
-    for (int i = tid; i < L.acc_rows * kW2S; i += NT) AccW2[i] = 0.f;
-    for (int i = tid; i < 3 * V; i += NT) aPose[i] = 0.f;
+    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sb1[i] = a.b1[i];
+    for (int i = threadIdx.x; i < n_out * kH; i += blockDim.x) sW2[i] = a.w2[i];
+    for (int i = threadIdx.x; i < n_out; i += blockDim.x) sb2[i] = a.b2[i];
+    const int V = vt.n;
+    for (int i = threadIdx.x; i < 3 * V; i += blockDim.x) aPose[i] = 0.f;
     __syncthreads();
-    const int rows = a.A * V;
-    const int ntiles = (rows + R - 1) / R;
-    const size_t NG = (size_t)a.A * K;
-    const int r = tid / TPR, q = tid % TPR;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int row0 = tile * R;
-        // ---- inputs of each row
-        if (tid < R) {
-            const int row = row0 + tid;
-            const bool valid = row < rows;
-            const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
-            float x[kDinP], delta[3], dist;
-            mlp_input(a, vt.v[v], an, x, delta, dist);
-            float *xr = X + tid * kXS;
+    const size_t NG = (size_t)a.A * a.K;
+    for (int base = a.row_begin + blockIdx.x * dbwd::kRowsPerBlock; base < a.row_end;
+         base += gridDim.x * dbwd::kRowsPerBlock) {
+        const int row = base + threadIdx.x;
+        const bool valid = row < a.row_end;
+        const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
+        const int lr = row - a.row_begin;
+        const DevView &cam = vt.v[v];
+        const size_t gbase = (size_t)v * NG + (size_t)an * a.K;
+        float dx[kDinP], dls[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int i = 0; i < kDin; ++i) xr[i] = valid ? x[i] : 0.f;
-            xr[38] = valid ? 1.f : 0.f;
+        for (int i = 0; i < kDinP; ++i) dx[i] = 0.f;
+        bwd_group<0, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
+        bwd_group<1, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
+        bwd_group<2, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
+        if (NF > 0) bwd_group<3, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
+        float x[kDinP], delta[3], dist;
+        mlp_input(da, cam, an, x, delta, dist);
+        if (a.s.X && valid) {
+            x[38] = 1.f;
 #pragma unroll
-            for (int i = 39; i < kXS; ++i) xr[i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < kXS; ++i) DX[tid * kXS + i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) DLS[tid * 4 + i] = 0.f;
-            float *inf = Info + tid * 8;
-            inf[0] = __int_as_float(an);
-            inf[1] = __int_as_float(v);
-            inf[2] = valid ? 1.f : 0.f;
-            inf[3] = dist;
-            inf[4] = delta[0];
-            inf[5] = delta[1];
-            inf[6] = delta[2];
+            for (int i = 0; i < kDinP; ++i) a.s.X[(size_t)i * a.s.ld + lr] = x[i];
         }
-        __syncthreads();
-        const int an_r = __float_as_int(Info[r * 8]);
-        const bool valid_r = Info[r * 8 + 2] != 0.f;
-        int gacc = 0;
-        for (int g = 0; g < 4; ++g) {
-            const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
-            if (m == 0) break;
-            const int ng = K * m, npad = pad4(ng);
-            const int r0 = g == 0 ? 0 : g == 1 ? K : g == 2 ? 8 * K : 11 * K;
-            // ---- stage this group's dL/dG of the tile's rows (coalesced, all threads)
-            if (g == 3) {
-                const int per_row = K * NF / 4;
-                for (int it = tid; it < R * per_row; it += NT) {
-                    const int rr = it / per_row, e = it - rr * per_row;
-                    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (Info[rr * 8 + 2] != 0.f) {
-                        const size_t gb = (size_t)__float_as_int(Info[rr * 8 + 1]) * NG +
-                                          (size_t)__float_as_int(Info[rr * 8]) * K;
-                        val = reinterpret_cast<const float4 *>(gr.d_feat + gb * NF)[e];
-                    }
-                    *reinterpret_cast<float4 *>(SG + rr * L.SGS + 4 * e) = val;
-                }
-            } else {
-                for (int it = tid; it < R * K; it += NT) {
-                    const int rr = it / K, k = it - rr * K;
-                    const bool ok = Info[rr * 8 + 2] != 0.f;
-                    const size_t gi = ok ? (size_t)__float_as_int(Info[rr * 8 + 1]) * NG +
-                                               (size_t)__float_as_int(Info[rr * 8]) * K + k
-                                         : 0;
-                    float *dst = SG + rr * L.SGS;
-                    if (g == 0) {
-                        const float4 dm = ok ? gr.d_mean_op[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        *reinterpret_cast<float4 *>(SM + (rr * K + k) * 4) = dm;
-                        dst[k] = dm.w;
-                    } else if (g == 1) {
-                        const float4 ds = ok ? gr.d_scale[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 dq = ok ? gr.d_quat[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        dst[7 * k] = ds.x;
-                        dst[7 * k + 1] = ds.y;
-                        dst[7 * k + 2] = ds.z;
-                        dst[7 * k + 3] = dq.x;
-                        dst[7 * k + 4] = dq.y;
-                        dst[7 * k + 5] = dq.z;
-                        dst[7 * k + 6] = dq.w;
-                    } else {
-                        const float4 dc = ok ? gr.d_color[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        dst[3 * k] = dc.x;
-                        dst[3 * k + 1] = dc.y;
-                        dst[3 * k + 2] = dc.z;
-                    }
-                }
-            }
-            // ---- Z, H, act'  (two hidden units per thread)
-            {
-                float z[2];
-#pragma unroll
-                for (int jj = 0; jj < 2; ++jj) z[jj] = sb1[g * kH + 2 * q + jj];
-                const float *xr = X + r * kXS;
-#pragma unroll 8
-                for (int i = 0; i < 40; ++i) {
-                    const float xi = xr[i];
-                    const float2 w = *reinterpret_cast<const float2 *>(W1T + i * kW1S + g * kH + 2 * q);
-                    z[0] = fmaf(xi, w.x, z[0]);
-                    z[1] = fmaf(xi, w.y, z[1]);
-                }
-                float hv[2], ap[2];
-#pragma unroll
-                for (int jj = 0; jj < 2; ++jj) {
-                    if (g < 3) {
-                        hv[jj] = fmaxf(z[jj], 0.f);
-                        ap[jj] = z[jj] > 0.f ? 1.f : 0.f;
-                    } else {
-                        hv[jj] = softplus(z[jj]);
-                        ap[jj] = sigm(z[jj]);
-                    }
-                }
-                *reinterpret_cast<float2 *>(H + r * kHS + 2 * q) = make_float2(hv[0], hv[1]);
-                *reinterpret_cast<float2 *>(AP + r * kHS + 2 * q) = make_float2(ap[0], ap[1]);
-            }
-            __syncthreads();
-            // ---- Y and dL/dY
-            {
-                float h[kH];
-#pragma unroll
-                for (int qq = 0; qq < kH / 4; ++qq) {
-                    float4 t4 = *reinterpret_cast<const float4 *>(H + r * kHS + 4 * qq);
-                    h[4 * qq] = t4.x;
-                    h[4 * qq + 1] = t4.y;
-                    h[4 * qq + 2] = t4.z;
-                    h[4 * qq + 3] = t4.w;
-                }
-                for (int o = q; o < npad; o += TPR) {
-                    float dy = 0.f;
-                    if (o < ng && valid_r) {
-                        const int row_o = r0 + o;
-                        const int k = o / m, c = o - k * m;
-                        // the pre-activation is needed only where an output
-                        // activation has a derivative (not for the linear
-                        // quaternion and feature outputs)
-                        const bool need_y = g == 0 || g == 2 || (g == 1 && c < 3);
-                        float y = 0.f;
-                        if (need_y) {
-                            const float4 *w = reinterpret_cast<const float4 *>(W2s + row_o * kW2S);
-                            y = sb2[row_o];
-#pragma unroll
-                            for (int qq = 0; qq < kH / 4; ++qq) {
-                                float4 ww = w[qq];
-                                y = fmaf(ww.x, h[4 * qq], y);
-                                y = fmaf(ww.y, h[4 * qq + 1], y);
-                                y = fmaf(ww.z, h[4 * qq + 2], y);
-                                y = fmaf(ww.w, h[4 * qq + 3], y);
-                            }
-                        }
-                        const float gin = SG[r * L.SGS + o];
-                        if (g == 0) {
-                            float s = sigm(y);
-                            dy = gin * s * (1.f - s);
-                        } else if (g == 1) {
-                            if (c < 3) {
-                                float s = sigm(y);
-                                float l = a.ascale[3 * an_r + c];
-                                dy = gin * l * s * (1.f - s);
-                                atomicAdd(DLS + r * 4 + c, gin * s);
-                            } else {
-                                dy = gin;
-                            }
-                        } else if (g == 2) {
-                            float cc = sigm(y);
-                            dy = gin * cc * (1.f - cc);
-                        } else {
-                            dy = gin;
-                        }
-                    }
-                    DY[r * L.DYS + o] = dy;
-                }
-            }
-            __syncthreads();
-            // ---- DZ = (DY W2_g) * act'(Z)
-            {
-                float dh[2] = {0.f, 0.f};
-                const float *dyr = DY + r * L.DYS;
-#pragma unroll 4
-                for (int o = 0; o < ng; ++o) {
-                    const float d = dyr[o];
-                    const float2 w = *reinterpret_cast<const float2 *>(W2s + (r0 + o) * kW2S + 2 * q);
-                    dh[0] = fmaf(d, w.x, dh[0]);
-                    dh[1] = fmaf(d, w.y, dh[1]);
-                }
-                const float2 ap = *reinterpret_cast<const float2 *>(AP + r * kHS + 2 * q);
-                *reinterpret_cast<float2 *>(DZ + r * kHS + 2 * q) = make_float2(dh[0] * ap.x, dh[1] * ap.y);
-            }
-            __syncthreads();
-            // ---- DX += DZ W1_g  (thread owns inputs q, q+16, q+32)
-            {
-                const float *dzr = DZ + r * kHS;
-#pragma unroll
-                for (int mm = 0; mm < 3; ++mm) {
-                    const int i = q + TPR * mm;
-                    if (i >= 40) break;
-                    float acc = 0.f;
-#pragma unroll 8
-                    for (int j = 0; j < kH; ++j) acc = fmaf(dzr[j], W1T[i * kW1S + g * kH + j], acc);
-                    DX[r * kXS + i] += acc;
-                }
-            }
-            // ---- weight gradients (micro-tiles over the R rows)
-            if (want_mlp) {
-                const int nA = (npad / 4) * 8;  // dW2_g: (o-block, j-block)
-                const int nB = 8 * 10;          // dW1_g: (j-block, i-block), i < 40 incl. the db1 column
-                for (int mt = tid; mt < nA + nB; mt += NT) {
-                    float acc[4][4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
-                    if (mt < nA) {
-                        const int ob = mt >> 3, jb = mt & 7;
-                        float sb[4] = {0.f, 0.f, 0.f, 0.f};
-                        for (int rr = 0; rr < R; ++rr) {
-                            const float4 av = *reinterpret_cast<const float4 *>(DY + rr * L.DYS + 4 * ob);
-                            const float4 bv = *reinterpret_cast<const float4 *>(H + rr * kHS + 4 * jb);
-                            const float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                sb[u] += aa[u];
-#pragma unroll
-                                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(aa[u], bb[w], acc[u][w]);
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float *dst = AccW2 + (gacc + 4 * ob + u) * kW2S;
-#pragma unroll
-                            for (int w = 0; w < 4; ++w) dst[4 * jb + w] += acc[u][w];
-                            if (jb == 0) dst[32] += sb[u];
-                        }
-                    } else {
-                        const int t2 = mt - nA, jb = t2 / 10, ib = t2 - jb * 10;
-                        for (int rr = 0; rr < R; ++rr) {
-                            const float4 av = *reinterpret_cast<const float4 *>(DZ + rr * kHS + 4 * jb);
-                            const float4 bv = *reinterpret_cast<const float4 *>(X + rr * kXS + 4 * ib);
-                            const float aa[4] = {av.x, av.y, av.z, av.w}, bb[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(aa[u], bb[w], acc[u][w]);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float *dst = AccW1 + (g * kH + 4 * jb + u) * kAccW1S + 4 * ib;
-#pragma unroll
-                            for (int w = 0; w < 4; ++w) dst[w] += acc[u][w];
-                        }
-                    }
-                }
-            }
-            gacc += npad;
-            __syncthreads();
-        }
-        // ---- per row: delta_vc, d_vc -> r = x_v - o_c
-        if (tid < R && Info[tid * 8 + 2] != 0.f) {
-            const float *dx = DX + tid * kXS;
-            const float dist = Info[tid * 8 + 3];
-            const float de[3] = {Info[tid * 8 + 4], Info[tid * 8 + 5], Info[tid * 8 + 6]};
-            const float ddl[3] = {dx[kFin], dx[kFin + 1], dx[kFin + 2]}, dd = dx[kFin + 3];
-            const float dot = de[0] * ddl[0] + de[1] * ddl[1] + de[2] * ddl[2];
-            const float idist = 1.f / dist;
-            const int v = __float_as_int(Info[tid * 8 + 1]);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float drr = (ddl[i] - de[i] * dot) * idist + dd * de[i];
-                DR[tid * 4 + i] = drr;
-                if (want_pose) atomicAdd(aPose + 3 * v + i, -drr);
-            }
-        } else if (tid < R) {
-            DR[tid * 4] = DR[tid * 4 + 1] = DR[tid * 4 + 2] = 0.f;
-        }
-        __syncthreads();
-        // ---- anchor gradients: sum the tile's rows of each anchor, one atomic per value
-        if (want_anc) {
-            const int a_first = __float_as_int(Info[0]);
-            const int last_row = min(row0 + R, rows) - 1;
-            const int a_last = last_row / V;
-            const int nseg = a_last - a_first + 1;
-            const int ncomp = kFin + 3 + 3 + 3 * K;
-            for (int it = tid; it < nseg * ncomp; it += NT) {
-                const int seg = it / ncomp, comp = it - seg * ncomp;
-                const int an = a_first + seg;
-                const int rb = max(an * V - row0, 0), re = min((an + 1) * V - row0, last_row - row0 + 1);
-                float s = 0.f;
-                if (comp < kFin) {
-                    for (int rr = rb; rr < re; ++rr) s += DX[rr * kXS + comp];
-                    atomicAdd(gr.g_afeat + (size_t)an * kFin + comp, s);
-                } else if (comp < kFin + 3) {
-                    const int c = comp - kFin;
-                    for (int rr = rb; rr < re; ++rr) {
-                        s += DR[rr * 4 + c];
-                        for (int k = 0; k < K; ++k) s += SM[(rr * K + k) * 4 + c];
-                    }
-                    atomicAdd(gr.g_pos + 3 * an + c, s);
-                } else if (comp < kFin + 6) {
-                    const int c = comp - kFin - 3;
-                    for (int rr = rb; rr < re; ++rr) s += DLS[rr * 4 + c];
-                    atomicAdd(gr.g_ascale + 3 * an + c, s);
-                } else {
-                    const int kc = comp - kFin - 6, k = kc / 3, c = kc - 3 * k;
-                    for (int rr = rb; rr < re; ++rr) s += SM[(rr * K + k) * 4 + c];
-                    atomicAdd(gr.g_offs + ((size_t)an * K + k) * 3 + c, s);
-                }
-            }
-        }
-        __syncthreads();
+        dbwd::row_epilogue(a, valid ? an : -1, v, gbase, dx, delta, dist, dls, aPose);
     }
-    // ---- flush block accumulators
-    if (want_mlp) {
-        for (int i = tid; i < 128 * 39; i += NT) {
-            const int h = i / 39, c = i - h * 39;
-            const float v = AccW1[h * kAccW1S + c];
-            if (c < kDin)
-                atomicAdd(gr.g_w1 + h * kDin + c, v);
-            else
-                atomicAdd(gr.g_b1 + h, v);
-        }
-        int gacc = 0;
-        for (int g = 0; g < 4; ++g) {
-            const int m = g == 0 ? 1 : g == 1 ? 7 : g == 2 ? 3 : NF;
-            if (m == 0) break;
-            const int ng = K * m;
-            const int r0 = g == 0 ? 0 : g == 1 ? K : g == 2 ? 8 * K : 11 * K;
-            for (int i = tid; i < ng * 33; i += NT) {
-                const int o = i / 33, j = i - o * 33;
-                const float v = AccW2[(gacc + o) * kW2S + j];
-                if (j < kH)
-                    atomicAdd(gr.g_w2 + (r0 + o) * kH + j, v);
-                else
-                    atomicAdd(gr.g_b2 + r0 + o, v);
-            }
-            gacc += pad4(ng);
-        }
-    }
-    if (want_pose) {
-        // o_c(xi) = t_wc - R_wc rho (first order): d rho = -W dL/do_c
-        for (int v = tid; v < V; v += NT) {
-            const DevView &cam = vt.v[v];
-            const float *go = aPose + 3 * v;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float s = -(cam.R[3 * i] * go[0] + cam.R[3 * i + 1] * go[1] + cam.R[3 * i + 2] * go[2]);
-                atomicAdd(gr.g_pose + 6 * v + i, s);
-            }
-        }
-    }
+    __syncthreads();
+    dbwd::flush_pose(a, vt, aPose);
 }
 
 size_t fwd_smem(int n_out) { return sizeof(float) * (4 * kH * kDinP + 4 * kH + n_out * kH + n_out); }
 
 }  // namespace
 
-// Shared memory the decode backward needs for K, n_feat and n_views.
-size_t decode_bwd_smem_bytes(int K, int NF, int V) {
-    const int R = NF == 32 ? BwdTile<32>::R : BwdTile<16>::R;
-    return sizeof(float) * (size_t)bwd_layout(K, NF, R, V).total;
-}
+size_t decode_bwd_rows_fp32_smem(int K, int NF) { return fwd_smem(dbwd::n_out(K, NF)); }
 
-size_t decode_smem_limit() { return kMaxSmem; }
+cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
+    const size_t smem = fwd_smem(dbwd::n_out(a.K, a.NF));
+    if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+    const int rows = a.row_end - a.row_begin;
+    const int blocks = std::max(1, std::min((rows + dbwd::kRowsPerBlock - 1) / dbwd::kRowsPerBlock, num_sms * 3));
+#define UPS_DECB(NFV)                                                                              \
+    do {                                                                                           \
+        cudaFuncSetAttribute(k_decode_bwd_rows<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             (int)smem);                                                           \
+        k_decode_bwd_rows<NFV><<<blocks, dbwd::kRowsPerBlock, smem, st>>>(vt, a);                  \
+    } while (0)
+    switch (a.NF) {
+        case 0: UPS_DECB(0); break;
+        case 16: UPS_DECB(16); break;
+        case 32: UPS_DECB(32); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef UPS_DECB
+    return cudaGetLastError();
+}
 
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
@@ -680,53 +428,6 @@ cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const u
         default: return cudaErrorInvalidValue;
     }
 #undef UPS_DEC
-    return cudaGetLastError();
-}
-
-cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                              const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask,
-                              const ups_mlp *d_mlp, const ups_anchors *d_anc, float *d_pose,
-                              int num_sms, cudaStream_t st) {
-    DecodeArgs a{A, K, NF, K * (11 + NF), anc.pos, anc.feat, anc.offsets, anc.scaling,
-                 mlp.w1, mlp.b1, mlp.w2, mlp.b2};
-    DecodeGrads g{};
-    g.d_mean_op = reinterpret_cast<const float4 *>(dG.mean_opacity);
-    g.d_scale = reinterpret_cast<const float4 *>(dG.scale);
-    g.d_quat = reinterpret_cast<const float4 *>(dG.quat);
-    g.d_color = reinterpret_cast<const float4 *>(dG.color);
-    g.d_feat = dG.feat;
-    if (d_mlp) {
-        g.g_w1 = d_mlp->w1;
-        g.g_b1 = d_mlp->b1;
-        g.g_w2 = d_mlp->w2;
-        g.g_b2 = d_mlp->b2;
-    }
-    if (d_anc) {
-        g.g_pos = d_anc->pos;
-        g.g_afeat = d_anc->feat;
-        g.g_offs = d_anc->offsets;
-        g.g_ascale = d_anc->scaling;
-    }
-    g.g_pose = d_pose;
-    g.mask = mask;
-    int rows = A * vt.n;
-#define UPS_DECB(NFV)                                                                        \
-    do {                                                                                     \
-        constexpr int R = BwdTile<NFV>::R, NT = BwdTile<NFV>::T;                              \
-        const size_t smem = sizeof(float) * (size_t)bwd_layout(K, NFV, R, vt.n).total;       \
-        if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;                           \
-        const int blocks = std::max(1, std::min((rows + R - 1) / R, num_sms));               \
-        cudaFuncSetAttribute(k_decode_bwd<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                             (int)smem);                                                     \
-        k_decode_bwd<NFV><<<blocks, NT, smem, st>>>(vt, a, g);                               \
-    } while (0)
-    switch (NF) {
-        case 0: UPS_DECB(0); break;
-        case 16: UPS_DECB(16); break;
-        case 32: UPS_DECB(32); break;
-        default: return cudaErrorInvalidValue;
-    }
-#undef UPS_DECB
     return cudaGetLastError();
 }
 

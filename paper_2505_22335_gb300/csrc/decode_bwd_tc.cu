@@ -1,0 +1,674 @@
+// Decode backward (Eq. 8-9 differentiated) with BF16 operands on the tcgen05
+// tensor cores, the weight-gradient reduction shared with the FP32 path, and
+// the host-side driver of both.
+//
+// k_decode_bwd_rows_tc: one 128-row tile per step, thread t = row t = TMEM lane
+// t, rows anchor-major (row = anchor * V + view).  Per MLP group g:
+//   Z_g  = X . W1_g^T                    (MMA)   H_g = act(Z_g + b1)
+//   Y_g  = H_g . W2nl_g^T                (MMA, only the outputs whose activation
+//                                         has a derivative: opacity, scale, colour)
+//   DY_g = dL/dY (CUDA cores, from dL/dG through the output activations)
+//   DH_g = DY_g . W2_g                   (MMA, a few output components per step)
+//   DZ_g = DH_g * act'(Z_g)
+//   DX  += DZ_g . W1_g                   (MMA, accumulated over the groups)
+// then the per-row epilogue (camera centre, pose, per-anchor sums).  Operands
+// are canonical K-major, no swizzle, in shared memory; accumulators in TMEM:
+// Z [0,32) Y [32,80) DH [96,128) DX [128,176).
+//
+// k_decode_wgrad: dW2_g = DY_g^T H_g (+ db2 = 1^T DY_g) and dW1 = DZ^T X (+ db1
+// from the constant-1 column of X), FP32, over the feature-major scratch the
+// per-row kernels wrote: 32-row chunks double-buffered into shared memory with
+// cp.async, 4 x 8 register micro-tiles, one atomic per weight per block.
+#include <algorithm>
+
+#include "decode_bwd.cuh"
+#include "umma.cuh"
+
+namespace ups {
+
+using dbwd::kDin;
+using dbwd::kFin;
+using dbwd::kH;
+using dbwd::kXW;
+
+namespace {
+
+using namespace umma;
+
+constexpr int kRows = dbwd::kRowsPerBlock;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t cZ = 0, cY = 32, cDH = 96, cDX = 128;
+constexpr int kWait = 1 << 22;
+constexpr int kKin = 48;  // X / W1 K extent (38 inputs, zero padded)
+
+__device__ __forceinline__ float sig(float x) { return 1.f / (1.f + __expf(-x)); }
+__device__ __forceinline__ float softplus(float x) { return x > 20.f ? x : log1pf(__expf(x)); }
+
+__device__ __forceinline__ void put(unsigned char *base, int row, int k, int kbytes, float v) {
+    *reinterpret_cast<__nv_bfloat16 *>(base + kmajor_offset(row, k, kbytes, 2)) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint32_t a, uint32_t a_kbytes, uint32_t b,
+                                          uint32_t b_kbytes, int ksteps, uint32_t id, bool accumulate) {
+    for (int ks = 0; ks < ksteps; ++ks)
+        mma<kBF16>(tmem_d, desc(a + 256u * ks, a_kbytes), desc(b + 256u * ks, b_kbytes), id,
+                   (accumulate || ks > 0) ? 1u : 0u);
+}
+
+// nonlinear outputs of group g: opacity (1), scale (3), colour (3); rows of
+// W2nl: g0 [0,16), g1 [16,64), g2 [64,112) (16 slots per component)
+__host__ __device__ constexpr int nl_comps(int g) { return g == 0 ? 1 : g == 3 ? 0 : 3; }
+__host__ __device__ constexpr int nl_base(int g) { return g == 0 ? 0 : g == 1 ? 16 : 64; }
+// output components per DY chunk (one MMA K step of 16 per component)
+__host__ __device__ constexpr int dy_chunk(int NF) { return NF == 32 ? 2 : 4; }
+
+struct Layout {
+    int oW1, oW2nl, oW2T[4], oW1T, ob1, ob2nl, oX, oH, oDY, oDZ, total;
+};
+
+__host__ __device__ inline Layout rows_layout(int NF) {
+    Layout L{};
+    int o = 0;
+    auto take = [&](int bytes) { const int r = o; o += (bytes + 1023) & ~1023; return r; };
+    L.oW1 = take(128 * kKin * 2);
+    L.oW2nl = take(112 * kH * 2);
+    for (int g = 0; g < 4; ++g) {
+        const int npad = 16 * dbwd::grp_m(g, NF);
+        L.oW2T[g] = npad ? take(kH * npad * 2) : o;
+    }
+    L.oW1T = take(kKin * 128 * 2);
+    L.ob1 = take(128 * 4);
+    L.ob2nl = take(112 * 4);
+    L.oX = take(kRows * kKin * 2);
+    L.oH = take(kRows * kH * 2);
+    L.oDY = take(kRows * 16 * dy_chunk(NF) * 2);
+    L.oDZ = take(kRows * kH * 2);
+    L.total = o;
+    return L;
+}
+
+struct Ctl {
+    uint64_t *mbar;
+    uint32_t phase;
+    bool ok;
+    // waits for the last commit; all threads agree on the outcome
+    __device__ __forceinline__ bool wait() {
+        const bool w = mbar_wait(mbar, phase, kWait);
+        phase ^= 1u;
+        if (__syncthreads_or(!w)) {
+            ok = false;
+            return false;
+        }
+        fence_after();
+        return true;
+    }
+};
+
+// operand writes by all threads -> visible to the MMA issued by thread 0
+__device__ __forceinline__ void publish() {
+    fence_before();
+    fence_async_smem();
+    __syncthreads();
+    fence_after();
+}
+
+template <int G, int NF>
+__device__ __forceinline__ void tc_group(const dbwd::Args &a, const Layout &L, unsigned char *smem, uint32_t sbase,
+                                         uint32_t tmem, uint32_t lane, Ctl &ctl, int an, bool valid, size_t gbase,
+                                         int lr, float dls[3]) {
+    constexpr int M = G == 0 ? 1 : G == 1 ? 7 : G == 2 ? 3 : NF;
+    constexpr int NNL = nl_comps(G);
+    constexpr int C = dy_chunk(NF);
+    constexpr int NCH = (M + C - 1) / C;
+    constexpr int UNR = G < 3 ? NCH : 1;
+    const int tid = threadIdx.x;
+    const int K = a.K;
+    const bool want_mlp = a.s.X != nullptr && valid;
+    const int ld = a.s.ld;
+    const float *b1 = reinterpret_cast<const float *>(smem + L.ob1);
+    const float *b2nl = reinterpret_cast<const float *>(smem + L.ob2nl);
+    // ---- Z_g = X W1_g^T
+    if (tid == 0) {
+        mma_chain(tmem + cZ, sbase + L.oX, kKin * 2, sbase + L.oW1 + G * kH * kKin * 2, kKin * 2, kKin * 2 / 32,
+                  idesc(kBF16, kRows, kH), false);
+        commit(ctl.mbar);
+    }
+    if (!ctl.wait()) return;
+    unsigned relu_on = 0;
+    float hs[kH];  // SoftPlus group: H kept for act'
+    {
+        float z[16];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            tmem_ld16(lane + cZ + 16 * half, z);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int jj = 16 * half + j;
+                const float zz = z[j] + b1[G * kH + jj];
+                float hv;
+                if (G < 3) {
+                    relu_on |= (zz > 0.f ? 1u : 0u) << jj;
+                    hv = fmaxf(zz, 0.f);
+                } else {
+                    hv = softplus(zz);
+                }
+                hs[jj] = hv;
+                put(smem + L.oH, tid, jj, kH * 2, hv);
+                if (want_mlp) a.s.H[(size_t)(G * kH + jj) * ld + lr] = hv;
+            }
+        }
+    }
+    publish();
+    // ---- Y of the nonlinear outputs
+    float ynl[NNL > 0 ? NNL : 1][16];
+    if (NNL > 0) {
+        if (tid == 0) {
+            mma_chain(tmem + cY, sbase + L.oH, kH * 2, sbase + L.oW2nl + nl_base(G) * kH * 2, kH * 2, kH * 2 / 32,
+                      idesc(kBF16, kRows, 16 * (NNL > 0 ? NNL : 1)), false);
+            commit(ctl.mbar);
+        }
+        if (!ctl.wait()) return;
+#pragma unroll
+        for (int c = 0; c < NNL; ++c) {
+            tmem_ld16(lane + cY + 16 * c, ynl[c]);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) ynl[c][k] += b2nl[nl_base(G) + 16 * c + k];
+        }
+    }
+    // ---- DY chunks; DH (+)= DY_chunk W2_g[chunk rows]
+    const int r0 = dbwd::grp_r0(G, K);
+#pragma unroll UNR
+    for (int ch = 0; ch < NCH; ++ch) {
+        const int c0 = ch * C;
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) {
+            const int c = c0 + cc;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float dy = 0.f;
+                if (c < M && k < K && valid) {
+                    const size_t gi = gbase + k;
+                    if (G == 0) {
+                        const float o = sig(ynl[0][k]);
+                        dy = a.d_mean_op[gi].w * o * (1.f - o);
+                    } else if (G == 1) {
+                        if (c < 3) {
+                            const float s = sig(ynl[c < NNL ? c : 0][k]);
+                            const float ds = reinterpret_cast<const float *>(a.d_scale + gi)[c];
+                            dy = ds * a.ascale[3 * an + c] * s * (1.f - s);
+                            dls[c < 3 ? c : 0] += ds * s;
+                        } else {
+                            dy = reinterpret_cast<const float *>(a.d_quat + gi)[c - 3];
+                        }
+                    } else if (G == 2) {
+                        const float s = sig(ynl[c < NNL ? c : 0][k]);
+                        dy = reinterpret_cast<const float *>(a.d_color + gi)[c] * s * (1.f - s);
+                    } else {
+                        dy = a.d_feat[gi * NF + c];
+                    }
+                    if (want_mlp) a.s.DY[(size_t)(r0 + M * k + c) * ld + lr] = dy;
+                }
+                put(smem + L.oDY, tid, 16 * cc + k, 16 * C * 2, dy);
+            }
+        }
+        publish();
+        if (tid == 0) {
+            const int nc = min(C, M - c0);
+            mma_chain(tmem + cDH, sbase + L.oDY, 16 * C * 2, sbase + L.oW2T[G] + 256u * c0, 32 * M, nc,
+                      idesc(kBF16, kRows, kH), c0 > 0);
+            commit(ctl.mbar);
+        }
+        if (!ctl.wait()) return;
+    }
+    // ---- DZ = DH * act'(Z): ReLU -> mask; SoftPlus -> sigmoid(Z) = 1 - exp(-H)
+    {
+        float dh[16];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            tmem_ld16(lane + cDH + 16 * half, dh);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int jj = 16 * half + j;
+                const float d = dh[j] * (G < 3 ? (float)((relu_on >> jj) & 1u) : -expm1f(-hs[jj]));
+                const float dz = valid ? d : 0.f;
+                put(smem + L.oDZ, tid, jj, kH * 2, dz);
+                if (want_mlp) a.s.DZ[(size_t)(G * kH + jj) * ld + lr] = dz;
+            }
+        }
+    }
+    publish();
+    // ---- DX += DZ_g W1_g  (B = W1^T at K offset 32 g)
+    if (tid == 0) {
+        mma_chain(tmem + cDX, sbase + L.oDZ, kH * 2, sbase + L.oW1T + 512u * G, 128 * 2, kH * 2 / 32,
+                  idesc(kBF16, kRows, kKin), G > 0);
+        commit(ctl.mbar);
+    }
+    ctl.wait();
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kRows) k_decode_bwd_rows_tc(ViewTable vt, dbwd::Args a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float aPose[3 * UPS_MAX_VIEWS];
+    const Layout L = rows_layout(NF);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int K = a.K, V = vt.n;
+    // ---- weights as B operands (K-major BF16)
+    for (int i = tid; i < 128 * kKin; i += kRows) {
+        const int h = i / kKin, c = i - h * kKin;
+        put(smem + L.oW1, h, c, kKin * 2, c < kDin ? a.w1[h * kDin + c] : 0.f);
+    }
+    for (int i = tid; i < kKin * 128; i += kRows) {  // W1T[i][h] = W1[h][i]
+        const int ii = i / 128, h = i - ii * 128;
+        put(smem + L.oW1T, ii, h, 128 * 2, ii < kDin ? a.w1[h * kDin + ii] : 0.f);
+    }
+    float *b1 = reinterpret_cast<float *>(smem + L.ob1);
+    float *b2nl = reinterpret_cast<float *>(smem + L.ob2nl);
+    for (int i = tid; i < 112 * kH; i += kRows) {
+        const int rr = i / kH, j = i - rr * kH;
+        const int g = rr < 16 ? 0 : rr < 64 ? 1 : 2;
+        const int c = (rr - nl_base(g)) >> 4, k = (rr - nl_base(g)) & 15;
+        float w = 0.f, bb = 0.f;
+        if (k < K) {
+            const int orow = dbwd::grp_r0(g, K) + dbwd::grp_m(g, NF) * k + c;
+            w = a.w2[orow * kH + j];
+            bb = a.b2[orow];
+        }
+        put(smem + L.oW2nl, rr, j, kH * 2, w);
+        if (j == 0) b2nl[rr] = bb;
+    }
+    for (int g = 0; g < 4; ++g) {
+        const int m = dbwd::grp_m(g, NF), npad = 16 * m;
+        for (int i = tid; i < kH * npad; i += kRows) {  // W2T_g[j][16 c + k] = W2[r0 + m k + c][j]
+            const int j = i / npad, e = i - j * npad, c = e >> 4, k = e & 15;
+            const float w = k < K ? a.w2[(dbwd::grp_r0(g, K) + m * k + c) * kH + j] : 0.f;
+            put(smem + L.oW2T[g], j, e, npad * 2, w);
+        }
+    }
+    for (int i = tid; i < 128; i += kRows) b1[i] = a.b1[i];
+    for (int i = tid; i < 3 * V; i += kRows) aPose[i] = 0.f;
+    if (tid == 0) mbar_init(&mbar, 1);
+    if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
+    publish();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t sbase = smem_addr(smem);
+    Ctl ctl{&mbar, 0u, true};
+    const size_t NG = (size_t)a.A * K;
+    for (int base = a.row_begin + blockIdx.x * kRows; base < a.row_end && ctl.ok; base += gridDim.x * kRows) {
+        const int row = base + tid;
+        const bool valid = row < a.row_end;
+        const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
+        const int lr = row - a.row_begin;
+        const DevView &cam = vt.v[v];
+        const size_t gbase = (size_t)v * NG + (size_t)an * K;
+        float delta[3], dist;
+        {
+            float x[kXW];
+            dbwd::mlp_input(a, cam, an, x, delta, dist);
+#pragma unroll
+            for (int i = 0; i < kKin; ++i) put(smem + L.oX, tid, i, kKin * 2, (valid && i < kDin) ? x[i] : 0.f);
+            if (a.s.X && valid)
+#pragma unroll
+                for (int i = 0; i < kXW; ++i) a.s.X[(size_t)i * a.s.ld + lr] = x[i];
+        }
+        publish();
+        float dls[3] = {0.f, 0.f, 0.f};
+        tc_group<0, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
+        if (ctl.ok) tc_group<1, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
+        if (ctl.ok) tc_group<2, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
+        if (NF > 0 && ctl.ok) tc_group<3, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
+        if (!ctl.ok) break;
+        float dx[48];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float t16[16];
+            tmem_ld16(lane + cDX + 16 * q, t16);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dx[16 * q + i] = t16[i];
+        }
+        fence_before();
+        dbwd::row_epilogue(a, valid ? an : -1, v, gbase, dx, delta, dist, dls, aPose);
+        __syncthreads();
+        fence_after();
+    }
+    if (!ctl.ok) {
+        // a wait ran out: record it and give the outstanding MMA a bounded
+        // chance to land before TMEM is released
+        if (tid == 0) {
+            atomicExch(a.err, 1);
+            mbar_wait(&mbar, ctl.phase ^ 1u, kWait);
+        }
+    } else {
+        __syncthreads();
+        dbwd::flush_pose(a, vt, aPose);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// weight gradients
+// ---------------------------------------------------------------------------
+
+constexpr int kWT = 256;  // threads
+constexpr int kWR = 32;   // rows per staged chunk
+
+// Staged feature index space: DY of group g at goff[g] (group sizes padded to
+// 8), H at fH, DZ at fH + 128, X at fH + 256; each feature holds the chunk's
+// 32 rows, float4 q at slot q ^ key(f) to spread shared-memory banks.
+struct WLayout {
+    int goff[4], gn[4], gr0[4], fH, F;
+};
+
+__host__ __device__ inline WLayout wlayout(int K, int NF) {
+    WLayout w{};
+    int o = 0;
+    for (int g = 0; g < 4; ++g) {
+        w.goff[g] = o;
+        w.gn[g] = K * dbwd::grp_m(g, NF);
+        w.gr0[g] = dbwd::grp_r0(g, K);
+        o += (w.gn[g] + 7) & ~7;
+    }
+    w.fH = o;
+    w.F = o + 128 + 128 + kXW;
+    return w;
+}
+
+__device__ __forceinline__ int swz(int f, int q) { return q ^ ((f ^ (f >> 3)) & 7); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes));
+}
+
+struct WArgs {
+    int nrows, K, NF;
+    dbwd::Scratch s;
+    float *g_w1, *g_b1, *g_w2, *g_b2;
+};
+
+// Micro-tile t: A features [fa, fa+4), B features [fb, fb+8); kind 0 = dW2
+// (A = DY, B = H of the group), kind 1 = dW1 (A = DZ, B = X).
+struct MT {
+    int fa, fb, kind, g, o0, cb;
+};
+
+__device__ __forceinline__ MT mt_of(const WLayout &w, int t) {
+    MT m{};
+    if (t < w.fH) {
+        int g = 0;
+        while (g < 3 && t >= w.goff[g + 1]) ++g;
+        const int l = t - w.goff[g], ob = l >> 2, cb = l & 3;
+        m.kind = 0;
+        m.g = g;
+        m.o0 = 4 * ob;
+        m.cb = cb;
+        m.fa = w.goff[g] + 4 * ob;
+        m.fb = w.fH + g * kH + 8 * cb;
+    } else {
+        const int l = t - w.fH, hb = l / 5, ib = l - hb * 5;
+        m.kind = 1;
+        m.o0 = 4 * hb;
+        m.cb = ib;
+        m.fa = w.fH + 128 + 4 * hb;
+        m.fb = w.fH + 256 + 8 * ib;
+    }
+    return m;
+}
+
+// Issues the cp.async copies of local rows [r0, r0 + 32) of every feature
+// (rows at or past nrows and group padding are zero-filled).
+__device__ __forceinline__ void stage_chunk(const WArgs &wa, const WLayout &w, float *buf, int r0) {
+    const int n4 = w.F * (kWR / 4);
+    for (int i = threadIdx.x; i < n4; i += kWT) {
+        const int f = i >> 3, q = i & 7;
+        const float *src = wa.s.X;  // a valid address when nothing is copied
+        bool ok = true;
+        if (f < w.fH) {
+            int g = 0;
+            while (g < 3 && f >= w.goff[g + 1]) ++g;
+            const int l = f - w.goff[g];
+            ok = l < w.gn[g];
+            if (ok) src = wa.s.DY + (size_t)(w.gr0[g] + l) * wa.s.ld;
+        } else if (f < w.fH + 128) {
+            src = wa.s.H + (size_t)(f - w.fH) * wa.s.ld;
+        } else if (f < w.fH + 256) {
+            src = wa.s.DZ + (size_t)(f - w.fH - 128) * wa.s.ld;
+        } else {
+            src = wa.s.X + (size_t)(f - w.fH - 256) * wa.s.ld;
+        }
+        const int row = r0 + 4 * q;
+        const int nb = ok ? 4 * max(0, min(4, wa.nrows - row)) : 0;
+        if (nb > 0) src += row;
+        cp_async16(buf + f * kWR + 4 * swz(f, q), src, nb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int U>
+__global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffer) {
+    extern __shared__ float4 ws4[];
+    float *ws = reinterpret_cast<float *>(ws4);
+    const WLayout w = wlayout(wa.K, wa.NF);
+    const int n_mt = w.fH + 160;
+    float *buf[2] = {ws, ws + (double_buffer ? w.F * kWR : 0)};
+    float acc[U][4][8], bsum[U][4];
+    MT mts[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        mts[u] = mt_of(w, threadIdx.x + u * kWT);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bsum[u][i] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[u][i][j] = 0.f;
+        }
+    }
+    const int nchunks = (wa.nrows + kWR - 1) / kWR;
+    auto compute = [&](const float *sb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (threadIdx.x + u * kWT >= n_mt) continue;
+            const MT m = mts[u];
+#pragma unroll 1
+            for (int q = 0; q < kWR / 4; ++q) {
+                float4 av[4], bv[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    av[i] = *reinterpret_cast<const float4 *>(sb + (m.fa + i) * kWR + 4 * swz(m.fa + i, q));
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    bv[j] = *reinterpret_cast<const float4 *>(sb + (m.fb + j) * kWR + 4 * swz(m.fb + j, q));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    bsum[u][i] += (av[i].x + av[i].y) + (av[i].z + av[i].w);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float t = acc[u][i][j];
+                        t = fmaf(av[i].x, bv[j].x, t);
+                        t = fmaf(av[i].y, bv[j].y, t);
+                        t = fmaf(av[i].z, bv[j].z, t);
+                        t = fmaf(av[i].w, bv[j].w, t);
+                        acc[u][i][j] = t;
+                    }
+                }
+            }
+        }
+    };
+    if (double_buffer) {
+        int ch = blockIdx.x;
+        if (ch < nchunks) stage_chunk(wa, w, buf[0], ch * kWR);
+        for (int it = 0; ch < nchunks; ch += gridDim.x, ++it) {
+            const int nxt = ch + gridDim.x;
+            if (nxt < nchunks) {
+                stage_chunk(wa, w, buf[(it + 1) & 1], nxt * kWR);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
+            compute(buf[it & 1]);
+            __syncthreads();
+        }
+    } else {
+        for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+            stage_chunk(wa, w, buf[0], ch * kWR);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            compute(buf[0]);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (threadIdx.x + u * kWT >= n_mt) continue;
+        const MT m = mts[u];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (m.kind == 0) {
+                const int o = m.o0 + i;
+                if (o >= w.gn[m.g]) continue;
+                const int orow = w.gr0[m.g] + o;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) atomicAdd(wa.g_w2 + (size_t)orow * kH + 8 * m.cb + j, acc[u][i][j]);
+                if (m.cb == 0) atomicAdd(wa.g_b2 + orow, bsum[u][i]);
+            } else {
+                const int h = m.o0 + i;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = 8 * m.cb + j;
+                    if (c < kDin)
+                        atomicAdd(wa.g_w1 + h * kDin + c, acc[u][i][j]);
+                    else if (c == kDin)
+                        atomicAdd(wa.g_b1 + h, acc[u][i][j]);
+                }
+            }
+        }
+    }
+}
+
+// one staged chunk of rows (the kernel double-buffers when two fit)
+size_t wgrad_chunk_smem(int K, int NF) { return sizeof(float) * (size_t)wlayout(K, NF).F * kWR; }
+
+cudaError_t launch_decode_wgrad(const WArgs &wa, int num_sms, cudaStream_t st) {
+    const WLayout w = wlayout(wa.K, wa.NF);
+    const size_t one = wgrad_chunk_smem(wa.K, wa.NF);
+    const int db = 2 * one <= 227 * 1024 ? 1 : 0;
+    const size_t smem = db ? 2 * one : one;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int n_mt = w.fH + 160;
+    const int chunks = (wa.nrows + kWR - 1) / kWR;
+    const int blocks = std::max(1, std::min(chunks, num_sms));
+#define UPS_WG(U)                                                                                    \
+    do {                                                                                             \
+        cudaFuncSetAttribute(k_decode_wgrad<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_decode_wgrad<U><<<blocks, kWT, smem, st>>>(wa, db);                                        \
+    } while (0)
+    if (n_mt <= 2 * kWT)
+        UPS_WG(2);
+    else if (n_mt <= 3 * kWT)
+        UPS_WG(3);
+    else if (n_mt <= 4 * kWT)
+        UPS_WG(4);
+    else
+        return cudaErrorInvalidConfiguration;
+#undef UPS_WG
+    return cudaGetLastError();
+}
+
+// rows per scratch chunk of the decode backward
+constexpr int kChunkRows = 1 << 18;
+
+}  // namespace
+
+size_t decode_bwd_rows_tc_smem(int NF) { return (size_t)rows_layout(NF).total; }
+
+cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
+    const size_t smem = (size_t)rows_layout(a.NF).total;
+    if (smem + 1024 > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const int rows = a.row_end - a.row_begin;
+    const int per_sm = (smem + 2048) * 2 <= 228 * 1024 ? 2 : 1;
+    const int blocks = std::max(1, std::min((rows + kRows - 1) / kRows, num_sms * per_sm));
+#define UPS_BT(NFV)                                                                              \
+    do {                                                                                         \
+        cudaFuncSetAttribute(k_decode_bwd_rows_tc<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                         \
+        k_decode_bwd_rows_tc<NFV><<<blocks, kRows, smem, st>>>(vt, a);                           \
+    } while (0)
+    switch (a.NF) {
+        case 0: UPS_BT(0); break;
+        case 16: UPS_BT(16); break;
+        case 32: UPS_BT(32); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef UPS_BT
+    return cudaGetLastError();
+}
+
+// Scratch bytes the decode backward needs (MLP gradients only).
+size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF) {
+    const int rows = std::min(A * V, kChunkRows);
+    const int ld = (rows + 31) & ~31;
+    return sizeof(float) * dbwd::scratch_floats(ld, dbwd::n_out(K, NF));
+}
+
+// Whether K and n_feat fit the backward kernels' shared memory and tiling.
+bool decode_bwd_fits(int K, int NF) {
+    return rows_layout(NF).total + 1024 <= 227 * 1024 && wgrad_chunk_smem(K, NF) <= 227 * 1024 &&
+           wlayout(K, NF).fH + 160 <= 4 * kWT;
+}
+
+cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
+                              const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
+                              const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
+                              int num_sms, long long *launches, cudaStream_t st) {
+    dbwd::Args a{};
+    a.A = A;
+    a.K = K;
+    a.NF = NF;
+    a.pos = anc.pos;
+    a.afeat = anc.feat;
+    a.offs = anc.offsets;
+    a.ascale = anc.scaling;
+    a.w1 = mlp.w1;
+    a.b1 = mlp.b1;
+    a.w2 = mlp.w2;
+    a.b2 = mlp.b2;
+    a.d_mean_op = reinterpret_cast<const float4 *>(dG.mean_opacity);
+    a.d_scale = reinterpret_cast<const float4 *>(dG.scale);
+    a.d_quat = reinterpret_cast<const float4 *>(dG.quat);
+    a.d_color = reinterpret_cast<const float4 *>(dG.color);
+    a.d_feat = dG.feat;
+    if (d_anc) {
+        a.g_pos = d_anc->pos;
+        a.g_afeat = d_anc->feat;
+        a.g_offs = d_anc->offsets;
+        a.g_ascale = d_anc->scaling;
+    }
+    a.g_pose = d_pose;
+    a.mask = mask;
+    a.err = err;
+    const bool want_mlp = (mask & UPS_GRAD_MLP) && d_mlp;
+    const int rows = A * vt.n;
+    const int chunk = std::min(rows, kChunkRows);
+    const int ld = (chunk + 31) & ~31;
+    if (want_mlp) a.s = dbwd::scratch_at(scratch, ld, dbwd::n_out(K, NF));
+    for (int r = 0; r < rows; r += chunk) {
+        a.row_begin = r;
+        a.row_end = std::min(rows, r + chunk);
+        cudaError_t e = bf16 ? launch_decode_bwd_rows_tc(vt, a, num_sms, st)
+                             : launch_decode_bwd_rows_fp32(vt, a, num_sms, st);
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        if (!want_mlp) continue;
+        WArgs wa{a.row_end - a.row_begin, K, NF, a.s, d_mlp->w1, d_mlp->b1, d_mlp->w2, d_mlp->b2};
+        if ((e = launch_decode_wgrad(wa, num_sms, st)) != cudaSuccess) return e;
+        ++*launches;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ups
