@@ -25,6 +25,7 @@ constexpr int kFin = 32;     // anchor feature width
 constexpr int kDin = kFin + 6;
 constexpr int kDinP = 40;    // padded input width (float4 rows)
 constexpr int kMaxK = 16;
+constexpr int kDX = kFin + 4;  // MLP inputs with a gradient: f_v, delta_vc, d_vc
 constexpr size_t kMaxSmem = 227 * 1024;  // opt-in shared memory per block
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + __expf(-x)); }
@@ -208,31 +209,46 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
 template <int G, int NF>
 __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs &da, const float *sW1T,
                                           const float *sb1, const float *sW2, const float *sb2,
-                                          const DevView &cam, int an, bool valid, size_t gbase, int lr,
-                                          float dx[kDinP], float dls[3]) {
+                                          const float xt[6], int an, bool valid, size_t gbase, int lr,
+                                          float *sDX, float dls[3]) {
     constexpr int M = G == 0 ? 1 : G == 1 ? 7 : G == 2 ? 3 : NF;
     const int K = a.K;
     const bool want_mlp = a.s.X != nullptr && valid;
     const int ld = a.s.ld;
-    // Z = W1_g x + b1: input-outer so the 32 accumulators stay in registers
+    // Z = W1_g x + b1, input-outer so the 32 accumulators stay in registers;
+    // the anchor feature part of x is read through L1 (the rows of one anchor
+    // are adjacent lanes), the camera-dependent tail comes in registers
     float h[kH];
 #pragma unroll
     for (int j = 0; j < kH; ++j) h[j] = sb1[G * kH + j];
-    {
-        float x[kDinP], delta[3], dist;
-        mlp_input(da, cam, an, x, delta, dist);
+    const float4 *f4 = reinterpret_cast<const float4 *>(a.afeat + (size_t)an * kFin);
 #pragma unroll 1
-        for (int i = 0; i < kDin; ++i) {
-            const float xi = x[i];
-            const float4 *w = reinterpret_cast<const float4 *>(sW1T + i * 128 + G * kH);
+    for (int i4 = 0; i4 < kFin / 4; ++i4) {
+        const float4 xv = __ldg(f4 + i4);
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 *w = reinterpret_cast<const float4 *>(sW1T + (4 * i4 + u) * 128 + G * kH);
 #pragma unroll
             for (int q = 0; q < kH / 4; ++q) {
                 const float4 ww = w[q];
-                h[4 * q] = fmaf(ww.x, xi, h[4 * q]);
-                h[4 * q + 1] = fmaf(ww.y, xi, h[4 * q + 1]);
-                h[4 * q + 2] = fmaf(ww.z, xi, h[4 * q + 2]);
-                h[4 * q + 3] = fmaf(ww.w, xi, h[4 * q + 3]);
+                h[4 * q] = fmaf(ww.x, xs[u], h[4 * q]);
+                h[4 * q + 1] = fmaf(ww.y, xs[u], h[4 * q + 1]);
+                h[4 * q + 2] = fmaf(ww.z, xs[u], h[4 * q + 2]);
+                h[4 * q + 3] = fmaf(ww.w, xs[u], h[4 * q + 3]);
             }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        const float4 *w = reinterpret_cast<const float4 *>(sW1T + (kFin + u) * 128 + G * kH);
+#pragma unroll
+        for (int q = 0; q < kH / 4; ++q) {
+            const float4 ww = w[q];
+            h[4 * q] = fmaf(ww.x, xt[u], h[4 * q]);
+            h[4 * q + 1] = fmaf(ww.y, xt[u], h[4 * q + 1]);
+            h[4 * q + 2] = fmaf(ww.z, xt[u], h[4 * q + 2]);
+            h[4 * q + 3] = fmaf(ww.w, xt[u], h[4 * q + 3]);
         }
     }
     unsigned relu_on = 0;  // ReLU derivative as a bit mask
@@ -284,7 +300,18 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
             }
             float dy = gin;
             if (nl) {
-                const float s = sigm(out_row(sW2, sb2, o, h));
+                // Y_o with four partial sums (short dependency chains)
+                const float4 *w = reinterpret_cast<const float4 *>(sW2 + o * kH);
+                float y4[4] = {sb2[o], 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int q = 0; q < kH / 4; ++q) {
+                    const float4 ww = w[q];
+                    y4[0] = fmaf(ww.x, h[4 * q], y4[0]);
+                    y4[1] = fmaf(ww.y, h[4 * q + 1], y4[1]);
+                    y4[2] = fmaf(ww.z, h[4 * q + 2], y4[2]);
+                    y4[3] = fmaf(ww.w, h[4 * q + 3], y4[3]);
+                }
+                const float s = sigm((y4[0] + y4[1]) + (y4[2] + y4[3]));
                 if (G == 1) {
                     dy = gin * a.ascale[3 * an + c] * s * (1.f - s);
                     dls[c] += gin * s;
@@ -310,36 +337,40 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
     if (want_mlp)
 #pragma unroll
         for (int j = 0; j < kH; ++j) a.s.DZ[(size_t)(G * kH + j) * ld + lr] = dh[j];
+    // dx += DZ W1_g for the inputs that have a gradient (f_v, delta_vc, d_vc),
+    // accumulated in shared memory (column tid of sDX)
 #pragma unroll 1
-    for (int i = 0; i < kDin; ++i) {
+    for (int i = 0; i < kDX; ++i) {
         const float4 *w = reinterpret_cast<const float4 *>(sW1T + i * 128 + G * kH);
-        float acc = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < kH / 4; ++q) {
             const float4 ww = w[q];
-            acc = fmaf(dh[4 * q], ww.x, acc);
-            acc = fmaf(dh[4 * q + 1], ww.y, acc);
-            acc = fmaf(dh[4 * q + 2], ww.z, acc);
-            acc = fmaf(dh[4 * q + 3], ww.w, acc);
+            acc[0] = fmaf(dh[4 * q], ww.x, acc[0]);
+            acc[1] = fmaf(dh[4 * q + 1], ww.y, acc[1]);
+            acc[2] = fmaf(dh[4 * q + 2], ww.z, acc[2]);
+            acc[3] = fmaf(dh[4 * q + 3], ww.w, acc[3]);
         }
-        dx[i] += acc;
+        sDX[i * dbwd::kRowsPerBlock] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 }
 
 // One thread per row (anchor-major), 128 rows per step of a grid-stride loop;
 // weights in shared memory read as broadcasts.
 template <int NF>
-__global__ void __launch_bounds__(dbwd::kRowsPerBlock) k_decode_bwd_rows(ViewTable vt, dbwd::Args a) {
+__global__ void __launch_bounds__(dbwd::kRowsPerBlock, 3) k_decode_bwd_rows(ViewTable vt, dbwd::Args a) {
     extern __shared__ float4 smem4[];
     __shared__ float aPose[3 * UPS_MAX_VIEWS];
     float *sm = reinterpret_cast<float *>(smem4);
     const int n_out = dbwd::n_out(a.K, NF);
     const DecodeArgs da{a.A, a.K, NF, n_out, a.pos, a.afeat, a.offs, a.ascale, a.w1, a.b1, a.w2, a.b2};
-    // W1 transposed [40][128] (inputs x hidden), b1, W2 [n_out][32], b2
-    float *sW1T = sm, *sb1 = sW1T + 4 * kH * kDinP, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + n_out * kH;
-    for (int i = threadIdx.x; i < kDinP * 4 * kH; i += blockDim.x) {
+    // W1 transposed [38][128] (inputs x hidden), b1, W2 [n_out][32], b2, and
+    // the per-row input gradients dx [36][128 rows]
+    float *sW1T = sm, *sb1 = sW1T + kDin * 4 * kH, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + n_out * kH;
+    float *sDXall = sb2 + ((n_out + 3) & ~3);
+    for (int i = threadIdx.x; i < kDin * 4 * kH; i += blockDim.x) {
         const int ii = i / (4 * kH), h = i - ii * (4 * kH);
-        sW1T[i] = ii < kDin ? a.w1[h * kDin + ii] : 0.f;
+        sW1T[i] = a.w1[h * kDin + ii];
     }
     for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sb1[i] = a.b1[i];
     for (int i = threadIdx.x; i < n_out * kH; i += blockDim.x) sW2[i] = a.w2[i];
@@ -348,6 +379,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock) k_decode_bwd_rows(ViewTab
     for (int i = threadIdx.x; i < 3 * V; i += blockDim.x) aPose[i] = 0.f;
     __syncthreads();
     const size_t NG = (size_t)a.A * a.K;
+    float *sDX = sDXall + threadIdx.x;
     for (int base = a.row_begin + blockIdx.x * dbwd::kRowsPerBlock; base < a.row_end;
          base += gridDim.x * dbwd::kRowsPerBlock) {
         const int row = base + threadIdx.x;
@@ -356,13 +388,6 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock) k_decode_bwd_rows(ViewTab
         const int lr = row - a.row_begin;
         const DevView &cam = vt.v[v];
         const size_t gbase = (size_t)v * NG + (size_t)an * a.K;
-        float dx[kDinP], dls[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < kDinP; ++i) dx[i] = 0.f;
-        bwd_group<0, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
-        bwd_group<1, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
-        bwd_group<2, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
-        if (NF > 0) bwd_group<3, NF>(a, da, sW1T, sb1, sW2, sb2, cam, an, valid, gbase, lr, dx, dls);
         float x[kDinP], delta[3], dist;
         mlp_input(da, cam, an, x, delta, dist);
         if (a.s.X && valid) {
@@ -370,20 +395,36 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock) k_decode_bwd_rows(ViewTab
 #pragma unroll
             for (int i = 0; i < kDinP; ++i) a.s.X[(size_t)i * a.s.ld + lr] = x[i];
         }
+        const float xt[6] = {x[kFin], x[kFin + 1], x[kFin + 2], x[kFin + 3], x[kFin + 4], x[kFin + 5]};
+#pragma unroll
+        for (int i = 0; i < kDX; ++i) sDX[i * dbwd::kRowsPerBlock] = 0.f;
+        float dls[3] = {0.f, 0.f, 0.f};
+        bwd_group<0, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
+        bwd_group<1, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
+        bwd_group<2, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
+        if (NF > 0) bwd_group<3, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
+        float dx[kDX];
+#pragma unroll
+        for (int i = 0; i < kDX; ++i) dx[i] = sDX[i * dbwd::kRowsPerBlock];
         dbwd::row_epilogue(a, valid ? an : -1, v, gbase, dx, delta, dist, dls, aPose);
     }
     __syncthreads();
     dbwd::flush_pose(a, vt, aPose);
 }
 
+// shared memory of the backward rows kernel
+size_t bwd_rows_smem(int n_out) {
+    return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + ((n_out + 3) & ~3) + kDX * dbwd::kRowsPerBlock);
+}
+
 size_t fwd_smem(int n_out) { return sizeof(float) * (4 * kH * kDinP + 4 * kH + n_out * kH + n_out); }
 
 }  // namespace
 
-size_t decode_bwd_rows_fp32_smem(int K, int NF) { return fwd_smem(dbwd::n_out(K, NF)); }
+size_t decode_bwd_rows_fp32_smem(int K, int NF) { return bwd_rows_smem(dbwd::n_out(K, NF)); }
 
 cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
-    const size_t smem = fwd_smem(dbwd::n_out(a.K, a.NF));
+    const size_t smem = bwd_rows_smem(dbwd::n_out(a.K, a.NF));
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     const int rows = a.row_end - a.row_begin;
     const int blocks = std::max(1, std::min((rows + dbwd::kRowsPerBlock - 1) / dbwd::kRowsPerBlock, num_sms * 3));

@@ -194,6 +194,6 @@ __device__ __forceinline__ void flush_pose(const Args &a, const ViewTable &vt, c
 // operands on the tensor cores) and the weight-gradient kernel
 cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
-size_t decode_bwd_rows_tc_smem(int NF);
+size_t decode_bwd_rows_tc_smem(int NF, int K);
 
 }  // namespace ups

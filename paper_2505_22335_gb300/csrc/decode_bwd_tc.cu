@@ -11,14 +11,18 @@
 //   DH_g = DY_g . W2_g                   (MMA, a few output components per step)
 //   DZ_g = DH_g * act'(Z_g)
 //   DX  += DZ_g . W1_g                   (MMA, accumulated over the groups)
-// then the per-row epilogue (camera centre, pose, per-anchor sums).  Operands
-// are canonical K-major, no swizzle, in shared memory; accumulators in TMEM:
-// Z [0,32) Y [32,80) DH [96,128) DX [128,176).
+// then the per-row epilogue (camera centre, pose, per-anchor sums).  Z of all
+// four groups is one MMA (N = 128) at the start of the tile.  DY is produced
+// Gaussian-major (all components of a few Gaussians per chunk) so each thread
+// reads its dL/dG records as whole float4s.  Operands are canonical K-major,
+// no swizzle, in shared memory, written as 16-byte core-matrix rows;
+// accumulators in TMEM: Z [0,128) Y [128,176) DH [176,208) DX [208,256).
 //
 // k_decode_wgrad: dW2_g = DY_g^T H_g (+ db2 = 1^T DY_g) and dW1 = DZ^T X (+ db1
 // from the constant-1 column of X), FP32, over the feature-major scratch the
 // per-row kernels wrote: 32-row chunks double-buffered into shared memory with
-// cp.async, 4 x 8 register micro-tiles, one atomic per weight per block.
+// cp.async, 4 x 8 register micro-tiles, one atomic per weight per block
+// (db2 from per-feature sums of the staged DY).
 #include <algorithm>
 
 #include "decode_bwd.cuh"
@@ -37,7 +41,7 @@ using namespace umma;
 
 constexpr int kRows = dbwd::kRowsPerBlock;
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t cZ = 0, cY = 32, cDH = 96, cDX = 128;
+constexpr uint32_t cZ = 0, cY = 128, cDH = 176, cDX = 208;  // Z of all groups, Y, DH, DX
 constexpr int kWait = 1 << 22;
 constexpr int kKin = 48;  // X / W1 K extent (38 inputs, zero padded)
 
@@ -59,32 +63,57 @@ __device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint32_t a, uint32_t 
 // W2nl: g0 [0,16), g1 [16,64), g2 [64,112) (16 slots per component)
 __host__ __device__ constexpr int nl_comps(int g) { return g == 0 ? 1 : g == 3 ? 0 : 3; }
 __host__ __device__ constexpr int nl_base(int g) { return g == 0 ? 0 : g == 1 ? 16 : 64; }
-// output components per DY chunk (one MMA K step of 16 per component)
-__host__ __device__ constexpr int dy_chunk(int NF) { return NF == 32 ? 2 : 4; }
+// DY K index of output (Gaussian k, component c) of group g: k * mp + c, the
+// components padded to mp; kc Gaussians fill one 64-element DY chunk
+__host__ __device__ constexpr int mp_of(int g, int NF) { return g == 0 ? 1 : g == 1 ? 8 : g == 2 ? 4 : NF; }
+__host__ __device__ constexpr int kc_of(int g, int NF) { return g == 0 ? 16 : NF == 0 && g == 3 ? 1 : 64 / mp_of(g, NF); }
+// K extent of W2T_g: Gaussians padded so that every chunk is whole MMA K steps
+__host__ __device__ inline int w2t_extent(int g, int NF, int K) {
+    const int mp = mp_of(g, NF);
+    if (mp == 0) return 0;
+    const int step = mp >= 16 ? 1 : 16 / mp;
+    return (K + step - 1) / step * step * mp;
+}
 
 struct Layout {
-    int oW1, oW2nl, oW2T[4], oW1T, ob1, ob2nl, oX, oH, oDY, oDZ, total;
+    int oW1, oW2nl, oW2T[4], eW2T[4], oW1T, ob1, ob2nl, oX, oH, oDY, oDZ, total;
 };
 
-__host__ __device__ inline Layout rows_layout(int NF) {
+__host__ __device__ inline Layout rows_layout(int NF, int K) {
     Layout L{};
     int o = 0;
     auto take = [&](int bytes) { const int r = o; o += (bytes + 1023) & ~1023; return r; };
     L.oW1 = take(128 * kKin * 2);
     L.oW2nl = take(112 * kH * 2);
     for (int g = 0; g < 4; ++g) {
-        const int npad = 16 * dbwd::grp_m(g, NF);
-        L.oW2T[g] = npad ? take(kH * npad * 2) : o;
+        L.eW2T[g] = w2t_extent(g, NF, K);
+        L.oW2T[g] = L.eW2T[g] ? take(kH * L.eW2T[g] * 2) : o;
     }
     L.oW1T = take(kKin * 128 * 2);
     L.ob1 = take(128 * 4);
     L.ob2nl = take(112 * 4);
     L.oX = take(kRows * kKin * 2);
     L.oH = take(kRows * kH * 2);
-    L.oDY = take(kRows * 16 * dy_chunk(NF) * 2);
+    L.oDY = take(kRows * 64 * 2);
     L.oDZ = take(kRows * kH * 2);
     L.total = o;
     return L;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a at the lower address
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// elements [8 k8, 8 k8 + 8) of operand row `row`: one core-matrix row, one
+// 16-byte store (the 8 rows of a core matrix fill all banks once)
+__device__ __forceinline__ void put8(unsigned char *base, int row, int k8, int kbytes, const float *v) {
+    uint4 u;
+    u.x = pack2(v[0], v[1]);
+    u.y = pack2(v[2], v[3]);
+    u.z = pack2(v[4], v[5]);
+    u.w = pack2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(base + kmajor_offset(row, 8 * k8, kbytes, 2)) = u;
 }
 
 struct Ctl {
@@ -118,48 +147,43 @@ __device__ __forceinline__ void tc_group(const dbwd::Args &a, const Layout &L, u
                                          int lr, float dls[3]) {
     constexpr int M = G == 0 ? 1 : G == 1 ? 7 : G == 2 ? 3 : NF;
     constexpr int NNL = nl_comps(G);
-    constexpr int C = dy_chunk(NF);
-    constexpr int NCH = (M + C - 1) / C;
+    constexpr int MP = mp_of(G, NF);
+    constexpr int KC = kc_of(G, NF);
+    constexpr int NCH = (16 + KC - 1) / KC;  // chunks for K = 16
     constexpr int UNR = G < 3 ? NCH : 1;
+    constexpr int NPUT = (KC * MP + 7) / 8;  // 16-byte stores per chunk row
     const int tid = threadIdx.x;
     const int K = a.K;
     const bool want_mlp = a.s.X != nullptr && valid;
     const int ld = a.s.ld;
     const float *b1 = reinterpret_cast<const float *>(smem + L.ob1);
     const float *b2nl = reinterpret_cast<const float *>(smem + L.ob2nl);
-    // ---- Z_g = X W1_g^T
-    if (tid == 0) {
-        mma_chain(tmem + cZ, sbase + L.oX, kKin * 2, sbase + L.oW1 + G * kH * kKin * 2, kKin * 2, kKin * 2 / 32,
-                  idesc(kBF16, kRows, kH), false);
-        commit(ctl.mbar);
-    }
-    if (!ctl.wait()) return;
+    // ---- H_g = act(Z_g + b1) from the Z columns of this group
     unsigned relu_on = 0;
-    float hs[kH];  // SoftPlus group: H kept for act'
-    {
+    float hs[kH];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
         float z[16];
+        tmem_ld16(lane + cZ + G * kH + 16 * half, z);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            tmem_ld16(lane + cZ + 16 * half, z);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int jj = 16 * half + j;
-                const float zz = z[j] + b1[G * kH + jj];
-                float hv;
-                if (G < 3) {
-                    relu_on |= (zz > 0.f ? 1u : 0u) << jj;
-                    hv = fmaxf(zz, 0.f);
-                } else {
-                    hv = softplus(zz);
-                }
-                hs[jj] = hv;
-                put(smem + L.oH, tid, jj, kH * 2, hv);
-                if (want_mlp) a.s.H[(size_t)(G * kH + jj) * ld + lr] = hv;
+        for (int j = 0; j < 16; ++j) {
+            const int jj = 16 * half + j;
+            const float zz = z[j] + b1[G * kH + jj];
+            if (G < 3) {
+                relu_on |= (zz > 0.f ? 1u : 0u) << jj;
+                hs[jj] = fmaxf(zz, 0.f);
+            } else {
+                hs[jj] = softplus(zz);
             }
         }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) put8(smem + L.oH, tid, q, kH * 2, hs + 8 * q);
+    if (want_mlp)
+#pragma unroll
+        for (int j = 0; j < kH; ++j) a.s.H[(size_t)(G * kH + j) * ld + lr] = hs[j];
     publish();
-    // ---- Y of the nonlinear outputs
+    // ---- Y of the nonlinear outputs (columns 16 c + k)
     float ynl[NNL > 0 ? NNL : 1][16];
     if (NNL > 0) {
         if (tid == 0) {
@@ -175,67 +199,93 @@ __device__ __forceinline__ void tc_group(const dbwd::Args &a, const Layout &L, u
             for (int k = 0; k < 16; ++k) ynl[c][k] += b2nl[nl_base(G) + 16 * c + k];
         }
     }
-    // ---- DY chunks; DH (+)= DY_chunk W2_g[chunk rows]
+    // ---- DY in chunks of KC Gaussians (all components); DH (+)= DY W2_g
     const int r0 = dbwd::grp_r0(G, K);
 #pragma unroll UNR
     for (int ch = 0; ch < NCH; ++ch) {
-        const int c0 = ch * C;
+        const int k0 = ch * KC;
+        if (k0 >= K) break;
+        float dyv[KC * MP > 0 ? KC * MP : 1];
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) {
-            const int c = c0 + cc;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
+        for (int kk = 0; kk < KC; ++kk) {
+            const int k = k0 + kk;  // compile-time wherever ynl is indexed (G < 3)
+            const bool live = k < K && valid;
+            const size_t gi = gbase + (live ? k : 0);
+            if (G == 0) {
                 float dy = 0.f;
-                if (c < M && k < K && valid) {
-                    const size_t gi = gbase + k;
-                    if (G == 0) {
-                        const float o = sig(ynl[0][k]);
-                        dy = a.d_mean_op[gi].w * o * (1.f - o);
-                    } else if (G == 1) {
-                        if (c < 3) {
-                            const float s = sig(ynl[c < NNL ? c : 0][k]);
-                            const float ds = reinterpret_cast<const float *>(a.d_scale + gi)[c];
-                            dy = ds * a.ascale[3 * an + c] * s * (1.f - s);
-                            dls[c < 3 ? c : 0] += ds * s;
-                        } else {
-                            dy = reinterpret_cast<const float *>(a.d_quat + gi)[c - 3];
-                        }
-                    } else if (G == 2) {
-                        const float s = sig(ynl[c < NNL ? c : 0][k]);
-                        dy = reinterpret_cast<const float *>(a.d_color + gi)[c] * s * (1.f - s);
-                    } else {
-                        dy = a.d_feat[gi * NF + c];
-                    }
-                    if (want_mlp) a.s.DY[(size_t)(r0 + M * k + c) * ld + lr] = dy;
+                if (live) {
+                    const float o = sig(ynl[0][k & 15]);
+                    dy = a.d_mean_op[gi].w * o * (1.f - o);
                 }
-                put(smem + L.oDY, tid, 16 * cc + k, 16 * C * 2, dy);
+                dyv[kk] = dy;
+            } else if (G == 1) {
+                const float4 ds = live ? a.d_scale[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 dq = live ? a.d_quat[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float dsc[3] = {ds.x, ds.y, ds.z};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float s = sig(ynl[c < NNL ? c : 0][k & 15]);
+                    dyv[kk * MP + c] = live ? dsc[c] * a.ascale[3 * an + c] * s * (1.f - s) : 0.f;
+                    dls[c] += live ? dsc[c] * s : 0.f;
+                }
+                dyv[kk * MP + 3] = dq.x;
+                dyv[kk * MP + 4] = dq.y;
+                dyv[kk * MP + 5] = dq.z;
+                dyv[kk * MP + 6] = dq.w;
+                dyv[kk * MP + 7] = 0.f;
+            } else if (G == 2) {
+                const float4 dc = live ? a.d_color[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float dcc[3] = {dc.x, dc.y, dc.z};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float s = sig(ynl[c < NNL ? c : 0][k & 15]);
+                    dyv[kk * MP + c] = dcc[c] * s * (1.f - s);
+                }
+                dyv[kk * MP + 3] = 0.f;
+            } else {
+#pragma unroll
+                for (int q = 0; q < NF / 4; ++q) {
+                    const float4 f = live ? reinterpret_cast<const float4 *>(a.d_feat + gi * NF)[q]
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                    dyv[kk * MP + 4 * q] = f.x;
+                    dyv[kk * MP + 4 * q + 1] = f.y;
+                    dyv[kk * MP + 4 * q + 2] = f.z;
+                    dyv[kk * MP + 4 * q + 3] = f.w;
+                }
             }
+            if (want_mlp && k < K)
+#pragma unroll
+                for (int c = 0; c < M; ++c) a.s.DY[(size_t)(r0 + M * k + c) * ld + lr] = dyv[kk * MP + c];
         }
+#pragma unroll
+        for (int q = 0; q < NPUT; ++q) put8(smem + L.oDY, tid, q, 64 * 2, dyv + 8 * q);
         publish();
         if (tid == 0) {
-            const int nc = min(C, M - c0);
-            mma_chain(tmem + cDH, sbase + L.oDY, 16 * C * 2, sbase + L.oW2T[G] + 256u * c0, 32 * M, nc,
-                      idesc(kBF16, kRows, kH), c0 > 0);
+            const int steps = (min(KC, K - k0) * MP + 15) / 16;
+            mma_chain(tmem + cDH, sbase + L.oDY, 64 * 2, sbase + L.oW2T[G] + (uint32_t)(k0 * MP * 2 / 16) * 128u,
+                      L.eW2T[G] * 2, steps, idesc(kBF16, kRows, kH), ch > 0);
             commit(ctl.mbar);
         }
         if (!ctl.wait()) return;
     }
     // ---- DZ = DH * act'(Z): ReLU -> mask; SoftPlus -> sigmoid(Z) = 1 - exp(-H)
-    {
+    float dz[kH];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
         float dh[16];
+        tmem_ld16(lane + cDH + 16 * half, dh);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            tmem_ld16(lane + cDH + 16 * half, dh);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int jj = 16 * half + j;
-                const float d = dh[j] * (G < 3 ? (float)((relu_on >> jj) & 1u) : -expm1f(-hs[jj]));
-                const float dz = valid ? d : 0.f;
-                put(smem + L.oDZ, tid, jj, kH * 2, dz);
-                if (want_mlp) a.s.DZ[(size_t)(G * kH + jj) * ld + lr] = dz;
-            }
+        for (int j = 0; j < 16; ++j) {
+            const int jj = 16 * half + j;
+            const float d = dh[j] * (G < 3 ? (float)((relu_on >> jj) & 1u) : -expm1f(-hs[jj]));
+            dz[jj] = valid ? d : 0.f;
         }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) put8(smem + L.oDZ, tid, q, kH * 2, dz + 8 * q);
+    if (want_mlp)
+#pragma unroll
+        for (int j = 0; j < kH; ++j) a.s.DZ[(size_t)(G * kH + j) * ld + lr] = dz[j];
     publish();
     // ---- DX += DZ_g W1_g  (B = W1^T at K offset 32 g)
     if (tid == 0) {
@@ -247,14 +297,14 @@ __device__ __forceinline__ void tc_group(const dbwd::Args &a, const Layout &L, u
 }
 
 template <int NF>
-__global__ void __launch_bounds__(kRows) k_decode_bwd_rows_tc(ViewTable vt, dbwd::Args a) {
+__global__ void __launch_bounds__(kRows, 2) k_decode_bwd_rows_tc(ViewTable vt, dbwd::Args a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ float aPose[3 * UPS_MAX_VIEWS];
-    const Layout L = rows_layout(NF);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int K = a.K, V = vt.n;
+    const Layout L = rows_layout(NF, K);
     // ---- weights as B operands (K-major BF16)
     for (int i = tid; i < 128 * kKin; i += kRows) {
         const int h = i / kKin, c = i - h * kKin;
@@ -280,11 +330,11 @@ __global__ void __launch_bounds__(kRows) k_decode_bwd_rows_tc(ViewTable vt, dbwd
         if (j == 0) b2nl[rr] = bb;
     }
     for (int g = 0; g < 4; ++g) {
-        const int m = dbwd::grp_m(g, NF), npad = 16 * m;
-        for (int i = tid; i < kH * npad; i += kRows) {  // W2T_g[j][16 c + k] = W2[r0 + m k + c][j]
-            const int j = i / npad, e = i - j * npad, c = e >> 4, k = e & 15;
-            const float w = k < K ? a.w2[(dbwd::grp_r0(g, K) + m * k + c) * kH + j] : 0.f;
-            put(smem + L.oW2T[g], j, e, npad * 2, w);
+        const int m = dbwd::grp_m(g, NF), mp = mp_of(g, NF), E = L.eW2T[g];
+        for (int i = tid; i < kH * E; i += kRows) {  // W2T_g[j][k mp + c] = W2[r0 + m k + c][j]
+            const int j = i / E, e = i - j * E, k = e / mp, c = e - k * mp;
+            const float w = (k < K && c < m) ? a.w2[(dbwd::grp_r0(g, K) + m * k + c) * kH + j] : 0.f;
+            put(smem + L.oW2T[g], j, e, E * 2, w);
         }
     }
     for (int i = tid; i < 128; i += kRows) b1[i] = a.b1[i];
@@ -306,15 +356,24 @@ __global__ void __launch_bounds__(kRows) k_decode_bwd_rows_tc(ViewTable vt, dbwd
         const size_t gbase = (size_t)v * NG + (size_t)an * K;
         float delta[3], dist;
         {
-            float x[kXW];
+            float x[kKin];
             dbwd::mlp_input(a, cam, an, x, delta, dist);
-#pragma unroll
-            for (int i = 0; i < kKin; ++i) put(smem + L.oX, tid, i, kKin * 2, (valid && i < kDin) ? x[i] : 0.f);
             if (a.s.X && valid)
 #pragma unroll
                 for (int i = 0; i < kXW; ++i) a.s.X[(size_t)i * a.s.ld + lr] = x[i];
+#pragma unroll
+            for (int i = 0; i < kKin; ++i) x[i] = (valid && i < kDin) ? x[i] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kKin / 8; ++q) put8(smem + L.oX, tid, q, kKin * 2, x + 8 * q);
         }
         publish();
+        // ---- Z of all four groups: X W1^T (N = 128)
+        if (tid == 0) {
+            mma_chain(tmem + cZ, sbase + L.oX, kKin * 2, sbase + L.oW1, kKin * 2, kKin * 2 / 32,
+                      idesc(kBF16, kRows, 128), false);
+            commit(&mbar);
+        }
+        if (!ctl.wait()) break;
         float dls[3] = {0.f, 0.f, 0.f};
         tc_group<0, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
         if (ctl.ok) tc_group<1, NF>(a, L, smem, sbase, tmem, lane, ctl, an, valid, gbase, lr, dls);
@@ -354,7 +413,7 @@ __global__ void __launch_bounds__(kRows) k_decode_bwd_rows_tc(ViewTable vt, dbwd
 // weight gradients
 // ---------------------------------------------------------------------------
 
-constexpr int kWT = 256;  // threads
+constexpr int kWTMax = 512;  // threads (512 with one micro-tile each, else 256)
 constexpr int kWR = 32;   // rows per staged chunk
 
 // Staged feature index space: DY of group g at goff[g] (group sizes padded to
@@ -423,7 +482,7 @@ __device__ __forceinline__ MT mt_of(const WLayout &w, int t) {
 // (rows at or past nrows and group padding are zero-filled).
 __device__ __forceinline__ void stage_chunk(const WArgs &wa, const WLayout &w, float *buf, int r0) {
     const int n4 = w.F * (kWR / 4);
-    for (int i = threadIdx.x; i < n4; i += kWT) {
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         const int f = i >> 3, q = i & 7;
         const float *src = wa.s.X;  // a valid address when nothing is copied
         bool ok = true;
@@ -448,27 +507,41 @@ __device__ __forceinline__ void stage_chunk(const WArgs &wa, const WLayout &w, f
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-template <int U>
+template <int U, int kWT>
 __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffer) {
     extern __shared__ float4 ws4[];
     float *ws = reinterpret_cast<float *>(ws4);
     const WLayout w = wlayout(wa.K, wa.NF);
     const int n_mt = w.fH + 160;
     float *buf[2] = {ws, ws + (double_buffer ? w.F * kWR : 0)};
-    float acc[U][4][8], bsum[U][4];
+    float acc[U][4][8];
     MT mts[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         mts[u] = mt_of(w, threadIdx.x + u * kWT);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            bsum[u][i] = 0.f;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[u][i][j] = 0.f;
-        }
     }
+    // db2: thread t sums staged DY features t and t + kWT (group padding
+    // included, as zeros)
+    float bsum[2] = {0.f, 0.f};
     const int nchunks = (wa.nrows + kWR - 1) / kWR;
     auto compute = [&](const float *sb) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int fb = threadIdx.x + b * kWT;
+            if (fb < w.fH) {
+                float t = 0.f;
+#pragma unroll
+                for (int q = 0; q < kWR / 4; ++q) {
+                    const float4 d = *reinterpret_cast<const float4 *>(sb + fb * kWR + 4 * swz(fb, q));
+                    t += (d.x + d.y) + (d.z + d.w);
+                }
+                bsum[b] += t;
+            }
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (threadIdx.x + u * kWT >= n_mt) continue;
@@ -484,7 +557,6 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
                     bv[j] = *reinterpret_cast<const float4 *>(sb + (m.fb + j) * kWR + 4 * swz(m.fb + j, q));
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    bsum[u][i] += (av[i].x + av[i].y) + (av[i].z + av[i].w);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         float t = acc[u][i][j];
@@ -534,7 +606,6 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
                 const int orow = w.gr0[m.g] + o;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) atomicAdd(wa.g_w2 + (size_t)orow * kH + 8 * m.cb + j, acc[u][i][j]);
-                if (m.cb == 0) atomicAdd(wa.g_b2 + orow, bsum[u][i]);
             } else {
                 const int h = m.o0 + i;
 #pragma unroll
@@ -547,6 +618,15 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
                 }
             }
         }
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int fb = threadIdx.x + b * kWT;
+        if (fb >= w.fH) continue;
+        int g = 0;
+        while (g < 3 && fb >= w.goff[g + 1]) ++g;
+        const int o = fb - w.goff[g];
+        if (o < w.gn[g]) atomicAdd(wa.g_b2 + w.gr0[g] + o, bsum[b]);
     }
 }
 
@@ -562,17 +642,15 @@ cudaError_t launch_decode_wgrad(const WArgs &wa, int num_sms, cudaStream_t st) {
     const int n_mt = w.fH + 160;
     const int chunks = (wa.nrows + kWR - 1) / kWR;
     const int blocks = std::max(1, std::min(chunks, num_sms));
-#define UPS_WG(U)                                                                                    \
-    do {                                                                                             \
-        cudaFuncSetAttribute(k_decode_wgrad<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_decode_wgrad<U><<<blocks, kWT, smem, st>>>(wa, db);                                        \
+#define UPS_WG(U, T)                                                                                   \
+    do {                                                                                               \
+        cudaFuncSetAttribute(k_decode_wgrad<U, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_decode_wgrad<U, T><<<blocks, T, smem, st>>>(wa, db);                                         \
     } while (0)
-    if (n_mt <= 2 * kWT)
-        UPS_WG(2);
-    else if (n_mt <= 3 * kWT)
-        UPS_WG(3);
-    else if (n_mt <= 4 * kWT)
-        UPS_WG(4);
+    if (n_mt <= 512 && w.fH <= 1024)
+        UPS_WG(1, 512);
+    else if (n_mt <= 3 * 256 && w.fH <= 512)
+        UPS_WG(3, 256);
     else
         return cudaErrorInvalidConfiguration;
 #undef UPS_WG
@@ -584,10 +662,10 @@ constexpr int kChunkRows = 1 << 18;
 
 }  // namespace
 
-size_t decode_bwd_rows_tc_smem(int NF) { return (size_t)rows_layout(NF).total; }
+size_t decode_bwd_rows_tc_smem(int NF, int K) { return (size_t)rows_layout(NF, K).total; }
 
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
-    const size_t smem = (size_t)rows_layout(a.NF).total;
+    const size_t smem = (size_t)rows_layout(a.NF, a.K).total;
     if (smem + 1024 > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int rows = a.row_end - a.row_begin;
     const int per_sm = (smem + 2048) * 2 <= 228 * 1024 ? 2 : 1;
@@ -617,8 +695,8 @@ size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF) {
 
 // Whether K and n_feat fit the backward kernels' shared memory and tiling.
 bool decode_bwd_fits(int K, int NF) {
-    return rows_layout(NF).total + 1024 <= 227 * 1024 && wgrad_chunk_smem(K, NF) <= 227 * 1024 &&
-           wlayout(K, NF).fH + 160 <= 4 * kWT;
+    return rows_layout(NF, K).total + 1024 <= 227 * 1024 && wgrad_chunk_smem(K, NF) <= 227 * 1024 &&
+           wlayout(K, NF).fH + 160 <= 3 * 256;
 }
 
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
