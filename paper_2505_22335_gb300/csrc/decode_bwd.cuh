@@ -195,5 +195,8 @@ __device__ __forceinline__ void flush_pose(const Args &a, const ViewTable &vt, c
 cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
 size_t decode_bwd_rows_tc_smem(int NF, int K);
+bool decode_wgrad_tc_fits(int K, int NF);
+cudaError_t launch_decode_wgrad_tc(const float *scratch, int ld, int nrows, int K, int NF, const ups_mlp &d_mlp,
+                                   int *err, int num_sms, cudaStream_t st);
 
 }  // namespace ups

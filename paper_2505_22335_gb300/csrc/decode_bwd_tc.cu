@@ -413,7 +413,6 @@ __global__ void __launch_bounds__(kRows, 2) k_decode_bwd_rows_tc(ViewTable vt, d
 // weight gradients
 // ---------------------------------------------------------------------------
 
-constexpr int kWTMax = 512;  // threads (512 with one micro-tile each, else 256)
 constexpr int kWR = 32;   // rows per staged chunk
 
 // Staged feature index space: DY of group g at goff[g] (group sizes padded to
@@ -480,31 +479,40 @@ __device__ __forceinline__ MT mt_of(const WLayout &w, int t) {
 
 // Issues the cp.async copies of local rows [r0, r0 + 32) of every feature
 // (rows at or past nrows and group padding are zero-filled).
-__device__ __forceinline__ void stage_chunk(const WArgs &wa, const WLayout &w, float *buf, int r0) {
+__device__ __forceinline__ void stage_chunk(const WArgs &wa, const WLayout &w, const int *tbl, float *buf, int r0) {
     const int n4 = w.F * (kWR / 4);
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         const int f = i >> 3, q = i & 7;
-        const float *src = wa.s.X;  // a valid address when nothing is copied
-        bool ok = true;
+        const int r = tbl[f];
+        const int row = r0 + 4 * q;
+        const int nb = r >= 0 ? 4 * max(0, min(4, wa.nrows - row)) : 0;
+        // a valid address even when nothing is copied (zero fill)
+        const float *src = wa.s.X + (nb > 0 ? (size_t)r * wa.s.ld + row : 0);
+        cp_async16(buf + f * kWR + 4 * swz(f, q), src, nb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// staged feature f -> its row in the scratch (X, H, DY, DZ are one buffer
+// starting at X), -1 for group padding
+__device__ __forceinline__ void build_table(const WArgs &wa, const WLayout &w, int *tbl) {
+    const int n_out = dbwd::n_out(wa.K, wa.NF);
+    for (int f = threadIdx.x; f < w.F; f += blockDim.x) {
+        int r;
         if (f < w.fH) {
             int g = 0;
             while (g < 3 && f >= w.goff[g + 1]) ++g;
             const int l = f - w.goff[g];
-            ok = l < w.gn[g];
-            if (ok) src = wa.s.DY + (size_t)(w.gr0[g] + l) * wa.s.ld;
+            r = l < w.gn[g] ? kXW + 128 + w.gr0[g] + l : -1;
         } else if (f < w.fH + 128) {
-            src = wa.s.H + (size_t)(f - w.fH) * wa.s.ld;
+            r = kXW + (f - w.fH);
         } else if (f < w.fH + 256) {
-            src = wa.s.DZ + (size_t)(f - w.fH - 128) * wa.s.ld;
+            r = kXW + 128 + n_out + (f - w.fH - 128);
         } else {
-            src = wa.s.X + (size_t)(f - w.fH - 256) * wa.s.ld;
+            r = f - w.fH - 256;
         }
-        const int row = r0 + 4 * q;
-        const int nb = ok ? 4 * max(0, min(4, wa.nrows - row)) : 0;
-        if (nb > 0) src += row;
-        cp_async16(buf + f * kWR + 4 * swz(f, q), src, nb);
+        tbl[f] = r;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int U, int kWT>
@@ -514,11 +522,16 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
     const WLayout w = wlayout(wa.K, wa.NF);
     const int n_mt = w.fH + 160;
     float *buf[2] = {ws, ws + (double_buffer ? w.F * kWR : 0)};
+    int *tbl = reinterpret_cast<int *>(ws + (double_buffer ? 2 : 1) * w.F * kWR);
+    build_table(wa, w, tbl);
+    __syncthreads();
     float acc[U][4][8];
-    MT mts[U];
+    int fa[U], fb[U];  // micro-tile operand features (the rest is recomputed at the flush)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        mts[u] = mt_of(w, threadIdx.x + u * kWT);
+        const MT m = mt_of(w, threadIdx.x + u * kWT);
+        fa[u] = m.fa;
+        fb[u] = m.fb;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -545,18 +558,18 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (threadIdx.x + u * kWT >= n_mt) continue;
-            const MT m = mts[u];
+            const int ma = fa[u], mb = fb[u];
 #pragma unroll 1
             for (int q = 0; q < kWR / 4; ++q) {
                 float4 av[4], bv[8];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    av[i] = *reinterpret_cast<const float4 *>(sb + (m.fa + i) * kWR + 4 * swz(m.fa + i, q));
+                    av[i] = *reinterpret_cast<const float4 *>(sb + (ma + i) * kWR + 4 * swz(ma + i, q));
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    bv[j] = *reinterpret_cast<const float4 *>(sb + (m.fb + j) * kWR + 4 * swz(m.fb + j, q));
+                    bv[j] = *reinterpret_cast<const float4 *>(sb + (mb + j) * kWR + 4 * swz(mb + j, q));
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         float t = acc[u][i][j];
@@ -566,17 +579,16 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
                         t = fmaf(av[i].w, bv[j].w, t);
                         acc[u][i][j] = t;
                     }
-                }
             }
         }
     };
     if (double_buffer) {
         int ch = blockIdx.x;
-        if (ch < nchunks) stage_chunk(wa, w, buf[0], ch * kWR);
+        if (ch < nchunks) stage_chunk(wa, w, tbl, buf[0], ch * kWR);
         for (int it = 0; ch < nchunks; ch += gridDim.x, ++it) {
             const int nxt = ch + gridDim.x;
             if (nxt < nchunks) {
-                stage_chunk(wa, w, buf[(it + 1) & 1], nxt * kWR);
+                stage_chunk(wa, w, tbl, buf[(it + 1) & 1], nxt * kWR);
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -587,7 +599,7 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
         }
     } else {
         for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-            stage_chunk(wa, w, buf[0], ch * kWR);
+            stage_chunk(wa, w, tbl, buf[0], ch * kWR);
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
             compute(buf[0]);
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(kWT) k_decode_wgrad(WArgs wa, int double_buffe
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (threadIdx.x + u * kWT >= n_mt) continue;
-        const MT m = mts[u];
+        const MT m = mt_of(w, threadIdx.x + u * kWT);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (m.kind == 0) {
@@ -635,9 +647,9 @@ size_t wgrad_chunk_smem(int K, int NF) { return sizeof(float) * (size_t)wlayout(
 
 cudaError_t launch_decode_wgrad(const WArgs &wa, int num_sms, cudaStream_t st) {
     const WLayout w = wlayout(wa.K, wa.NF);
-    const size_t one = wgrad_chunk_smem(wa.K, wa.NF);
-    const int db = 2 * one <= 227 * 1024 ? 1 : 0;
-    const size_t smem = db ? 2 * one : one;
+    const size_t one = wgrad_chunk_smem(wa.K, wa.NF), tbl = sizeof(int) * (size_t)w.F;
+    const int db = 2 * one + tbl <= 227 * 1024 ? 1 : 0;
+    const size_t smem = (db ? 2 * one : one) + tbl;
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int n_mt = w.fH + 160;
     const int chunks = (wa.nrows + kWR - 1) / kWR;
@@ -695,7 +707,8 @@ size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF) {
 
 // Whether K and n_feat fit the backward kernels' shared memory and tiling.
 bool decode_bwd_fits(int K, int NF) {
-    return rows_layout(NF, K).total + 1024 <= 227 * 1024 && wgrad_chunk_smem(K, NF) <= 227 * 1024 &&
+    return rows_layout(NF, K).total + 1024 <= 227 * 1024 &&
+           wgrad_chunk_smem(K, NF) + sizeof(int) * wlayout(K, NF).F <= 227 * 1024 &&
            wlayout(K, NF).fH + 160 <= 3 * 256;
 }
 
@@ -742,8 +755,13 @@ cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const u
         if (e != cudaSuccess) return e;
         ++*launches;
         if (!want_mlp) continue;
-        WArgs wa{a.row_end - a.row_begin, K, NF, a.s, d_mlp->w1, d_mlp->b1, d_mlp->w2, d_mlp->b2};
-        if ((e = launch_decode_wgrad(wa, num_sms, st)) != cudaSuccess) return e;
+        if (decode_wgrad_tc_fits(K, NF)) {
+            e = launch_decode_wgrad_tc(scratch, ld, a.row_end - a.row_begin, K, NF, *d_mlp, err, num_sms, st);
+        } else {
+            WArgs wa{a.row_end - a.row_begin, K, NF, a.s, d_mlp->w1, d_mlp->b1, d_mlp->w2, d_mlp->b2};
+            e = launch_decode_wgrad(wa, num_sms, st);
+        }
+        if (e != cudaSuccess) return e;
         ++*launches;
     }
     return cudaSuccess;
