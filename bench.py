@@ -178,8 +178,21 @@ def processed_instances(img, cams):
     return total
 
 
-def algorithmic(wl, stats, proc_inst):
-    """Algorithmic bytes (HBM-bound stages) and FP32 flops (ALU-bound stages) per launch."""
+def evaluations(img):
+    """Evaluated (pixel, list entry) pairs of the blend: the sum of n_contrib."""
+    return int(img["n_contrib"].to(dtype=__import__("torch").int64).sum().item())
+
+
+def algorithmic(wl, stats, proc_inst, evals=0):
+    """Algorithmic bytes (HBM-bound stages) and FP32 flops (ALU-bound stages) per launch.
+
+    Flops count an FMA as 2 and any other arithmetic op (exp included) as 1.
+    Blend: per evaluated (pixel, entry) pair 2 (NF + 4) + 12 forward (conic
+    quadratic, alpha, weighted colour/depth/features, transmittance) and
+    4 NF + 60 backward (alpha recomputed, transmittance by division, feature
+    and colour gradients, d alpha, conic / mean / opacity terms).  Decode rows
+    (backward, one (anchor, view) row): Z of the four MLPs, Y of the 7 K
+    nonlinear outputs, dL/dH through W2 and dL/dx through W1 (36 inputs)."""
     A, K, NF, V = wl["A"], wl["K"], wl["NF"], wl["V"]
     N = A * K
     GV = V * N
@@ -189,6 +202,9 @@ def algorithmic(wl, stats, proc_inst):
     rec3d = 64 + 4 * NF                         # mean|o, scale, quat, colour, features
     n_out = K * (11 + NF)
     row_fwd = 2 * (38 * 128 + 32 * n_out)       # flops per (anchor, view) row
+    row_bwd = 2 * (38 * 128 + 7 * K * 32 + 32 * n_out + 36 * 128)
+    scratch_row = 4 * (40 + 128 + n_out + 128)  # X, H, dL/dY, dL/dZ per row (feature-major)
+    rows = A * V
     inst_b = 16 + 16 + 16 + 4 * NF + 4         # xyzo, conic, colour, features, id
     pix_out = 4 * (3 + 1 + NF + 1) + 4
     passes = lambda bits: (bits + 7) // 8
@@ -200,15 +216,17 @@ def algorithmic(wl, stats, proc_inst):
         "emit": dict(bytes=GV * 24 + I * 8),
         "tile_sort": dict(bytes=passes(stats["key_bits"]) * I * 20),
         "ranges": dict(bytes=I * 8 + stats["n_tiles"] * 8),
-        "composite_fwd": dict(bytes=proc_inst * inst_b + P * pix_out),
+        "composite_fwd": dict(bytes=proc_inst * inst_b + P * pix_out, flops=evals * (2 * (NF + 4) + 12)),
         "loss": dict(bytes=P * 4 * (3 * (3 + 1 + NF) + 1)),
-        "composite_bwd": dict(bytes=proc_inst * inst_b + P * (pix_out + 4 * (3 + 1 + NF)) + GV * 4 * (12 + NF)),
+        "composite_bwd": dict(bytes=proc_inst * inst_b + P * (pix_out + 4 * (3 + 1 + NF)) + GV * 4 * (12 + NF),
+                              flops=evals * (4 * NF + 60)),
         "project_bwd": dict(bytes=GV * (48 + 4 * (12 + NF) + rec3d)),
-        "decode_bwd": dict(bytes=A * anc_b * 2 + GV * rec3d, flops=A * V * 3 * row_fwd),
+        "decode_bwd_rows": dict(bytes=A * anc_b * 2 + GV * rec3d + rows * scratch_row, flops=rows * row_bwd),
+        "decode_wgrad": dict(bytes=rows * scratch_row),
     }
 
 
-ALU_STAGES = {"decode_fwd", "decode_bwd", "composite_fwd", "composite_bwd"}
+ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
 
 
 def run_ours(args, wl_name):
@@ -258,6 +276,7 @@ def run_ours(args, wl_name):
     pix = sum(c.width * c.height for c in cams)
     value = world * pix / (ms_max / 1e3) / 1e6
     proc = processed_instances(st.img, cams)
+    evals = evaluations(st.img)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -266,7 +285,7 @@ def run_ours(args, wl_name):
 
     if rank == 0:
         peaks = load_peaks()
-        alg = algorithmic(wl, stats, proc)
+        alg = algorithmic(wl, stats, proc, evals)
         stages = {k: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
                   for k, v in prof.items()}
         dom = max(prof, key=lambda k: prof[k][0])
@@ -291,7 +310,7 @@ def run_ours(args, wl_name):
             "clocks": clk,
             "roofline": roof,
             "stages": stages,
-            "counters": dict(stats, processed_instances=proc),
+            "counters": dict(stats, processed_instances=proc, evaluations=evals),
             "cpu_baseline": cpu,
             "e2e": e2e,
         }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "decode_bwd.cuh"
 
 namespace ups {
 
@@ -55,7 +56,7 @@ size_t decode_tc_smem_bytes(int NF, int bf16);
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
                               const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
-                              int num_sms, long long *launches, cudaStream_t st);
+                              int num_sms, const dbwd::StageHook &hook, cudaStream_t st);
 size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF);
 bool decode_bwd_fits(int K, int NF);
 
@@ -613,11 +614,16 @@ ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp
         UPS_CUDA(c, c->dec_scratch.reserve(decode_bwd_scratch_bytes(anc->n, n_views, c->cfg.k, c->cfg.n_feat)));
         scratch = c->dec_scratch.as<float>();
     }
-    stage_begin(c, "decode_bwd", st);
-    long long nk = 0;
+    const dbwd::StageHook hook{[](void *u, const char *name, bool begin, cudaStream_t s) {
+                                   ups_ctx *cc = static_cast<ups_ctx *>(u);
+                                   if (begin)
+                                       stage_begin(cc, name, s);
+                                   else
+                                       stage_end(cc, s, 1);
+                               },
+                               c};
     UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp, d_anc,
-                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, scratch, c->d_err, c->num_sms, &nk, st));
-    stage_end(c, st, nk);
+                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, scratch, c->d_err, c->num_sms, hook, st));
     return UPS_OK;
 }
 

@@ -188,6 +188,13 @@ __device__ __forceinline__ void flush_pose(const Args &a, const ViewTable &vt, c
     }
 }
 
+// Called before (begin) and after each kernel launch of the decode backward
+// (stage timing and launch counting in the context).
+struct StageHook {
+    void (*fn)(void *user, const char *name, bool begin, cudaStream_t st);
+    void *user;
+};
+
 }  // namespace dbwd
 
 // per-row kernels (decode.cu: FP32 on the CUDA cores; decode_bwd_tc.cu: BF16

@@ -715,7 +715,7 @@ bool decode_bwd_fits(int K, int NF) {
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
                               const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
-                              int num_sms, long long *launches, cudaStream_t st) {
+                              int num_sms, const dbwd::StageHook &hook, cudaStream_t st) {
     dbwd::Args a{};
     a.A = A;
     a.K = K;
@@ -750,19 +750,21 @@ cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const u
     for (int r = 0; r < rows; r += chunk) {
         a.row_begin = r;
         a.row_end = std::min(rows, r + chunk);
+        hook.fn(hook.user, "decode_bwd_rows", true, st);
         cudaError_t e = bf16 ? launch_decode_bwd_rows_tc(vt, a, num_sms, st)
                              : launch_decode_bwd_rows_fp32(vt, a, num_sms, st);
+        hook.fn(hook.user, "decode_bwd_rows", false, st);
         if (e != cudaSuccess) return e;
-        ++*launches;
         if (!want_mlp) continue;
+        hook.fn(hook.user, "decode_wgrad", true, st);
         if (decode_wgrad_tc_fits(K, NF)) {
             e = launch_decode_wgrad_tc(scratch, ld, a.row_end - a.row_begin, K, NF, *d_mlp, err, num_sms, st);
         } else {
             WArgs wa{a.row_end - a.row_begin, K, NF, a.s, d_mlp->w1, d_mlp->b1, d_mlp->w2, d_mlp->b2};
             e = launch_decode_wgrad(wa, num_sms, st);
         }
+        hook.fn(hook.user, "decode_wgrad", false, st);
         if (e != cudaSuccess) return e;
-        ++*launches;
     }
     return cudaSuccess;
 }
