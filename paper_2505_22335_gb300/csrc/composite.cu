@@ -2,7 +2,8 @@
 // and transmittance (Eq. 3, Eq. 10), the per-pixel weighted loss (Eq. 4 /
 // Eq. 14), and the reverse-order blending backward.
 //
-// One 256-thread CTA per 16x16 image tile, one pixel per thread.  The tile's
+// One CTA per 16x16 image tile, PX pixels per thread (forward 2; backward 4
+// for up to 16 feature channels, 2 for 32: registers).  The tile's
 // depth-ordered Gaussian list is walked in batches of 256 staged in shared
 // memory; a CTA stops when every pixel has terminated.  The backward walks
 // the same list from each pixel's last blended Gaussian to the front,
@@ -20,24 +21,33 @@ namespace {
 
 constexpr int kBatch = 256;
 
-struct TileCtx {
-    int v, tx, ty, px, py;
-    bool inside;
-    const DevView *cam;
-};
-
-__device__ __forceinline__ TileCtx tile_ctx(const ViewTable &vt) {
-    TileCtx c;
-    const int t = blockIdx.x;
-    c.v = view_of_tile(vt, t);
-    c.cam = &vt.v[c.v];
-    int local = t - c.cam->tile_base;
-    c.ty = local / c.cam->tiles_x;
-    c.tx = local - c.ty * c.cam->tiles_x;
-    c.px = c.tx * kTile + (threadIdx.x & (kTile - 1));
-    c.py = c.ty * kTile + (threadIdx.x / kTile);
-    c.inside = c.px < c.cam->W && c.py < c.cam->H;
-    return c;
+// Packed pairs of f32 (first element in the low half) for fma.rn.f32x2: two
+// channels per instruction, each rounded exactly as a scalar fmaf.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float f2_lo(f2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    return hi;
+}
+// channels [c, c + 4) of staged Gaussian j as two pairs
+template <int NF, class St>
+__device__ __forceinline__ ulonglong2 feat4(const St &S, int j, int c) {
+    return *reinterpret_cast<const ulonglong2 *>(&S.feat[j][c]);
 }
 
 template <int NF>
@@ -45,7 +55,9 @@ struct Stage {
     float4 xyzo[kBatch];
     float4 conic[kBatch];
     float4 color[kBatch];
-    float feat[NF > 0 ? NF : 1][kBatch];  // channel-major: conflict-free broadcast reads
+    // Gaussian-major, rows padded by 4 floats: 16-byte broadcast reads of four
+    // channels, conflict-free 16-byte staging stores
+    float feat[kBatch][NF > 0 ? NF + 4 : 1];
     uint32_t gv[kBatch];
 };
 
@@ -64,26 +76,29 @@ __device__ __forceinline__ void stage_load(Stage<NF> &S, int slot, uint32_t gv, 
 #pragma unroll
         for (int c = 0; c < NF / 4; ++c) {
             float4 f = f4[c];
-            S.feat[4 * c + 0][slot] = f.x;
-            S.feat[4 * c + 1][slot] = f.y;
-            S.feat[4 * c + 2][slot] = f.z;
-            S.feat[4 * c + 3][slot] = f.w;
+            *reinterpret_cast<float4 *>(&S.feat[slot][4 * c]) = f;
         }
     }
 }
 
-// Each thread owns two pixels of the tile, (x, y) and (x, y + 8): the staged
-// Gaussian is read from shared memory once for both.
-constexpr int kThreadsBlend = 128;
+// Each thread owns PX pixels of the tile, (x, y + (16 / PX) q) for q < PX:
+// the staged Gaussian is read from shared memory once for all of them (and,
+// in the backward, reduced across the warp once for all of them).
+template <int PX> struct Px {
+    static constexpr int NT = kTilePix / PX;  // threads per tile
+    static constexpr int RS = kTile / PX;     // row step between a thread's pixels
+};
 
-struct Tile2 {
+template <int PX>
+struct TileP {
     int v, px, py0;
-    bool in0, in1;
+    bool in[PX];
     const DevView *cam;
 };
 
-__device__ __forceinline__ Tile2 tile2(const ViewTable &vt) {
-    Tile2 c;
+template <int PX>
+__device__ __forceinline__ TileP<PX> tilep(const ViewTable &vt) {
+    TileP<PX> c;
     const int t = blockIdx.x;
     c.v = view_of_tile(vt, t);
     c.cam = &vt.v[c.v];
@@ -92,52 +107,67 @@ __device__ __forceinline__ Tile2 tile2(const ViewTable &vt) {
     int tx = local - ty * c.cam->tiles_x;
     c.px = tx * kTile + (threadIdx.x & (kTile - 1));
     c.py0 = ty * kTile + (threadIdx.x / kTile);
-    c.in0 = c.px < c.cam->W && c.py0 < c.cam->H;
-    c.in1 = c.px < c.cam->W && c.py0 + 8 < c.cam->H;
+#pragma unroll
+    for (int q = 0; q < PX; ++q) c.in[q] = c.px < c.cam->W && c.py0 + Px<PX>::RS * q < c.cam->H;
     return c;
 }
 
-template <int NF>
-__global__ void __launch_bounds__(kThreadsBlend) k_composite_fwd(
+// pixels per thread: forward 2; backward 4 up to 16 feature channels (the
+// per-Gaussian warp reduction is shared by more pixels), 2 for 32 (registers)
+__host__ __device__ constexpr int blend_px_fwd(int nf) { return 2; }
+__host__ __device__ constexpr int blend_px_bwd(int nf) { return nf <= 16 ? 4 : 2; }
+
+template <int NF, int PX>
+__global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
     const float *__restrict__ feat, float *__restrict__ out_color, float *__restrict__ out_depth,
     float *__restrict__ out_feat, float *__restrict__ out_T, uint32_t *__restrict__ out_nc) {
+    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS;
     __shared__ Stage<NF> S;
-    const Tile2 tc = tile2(vt);
+    const TileP<PX> tc = tilep<PX>(vt);
     const uint2 rg = ranges[blockIdx.x];
     const float fx = (float)tc.px;
-    const float fy[2] = {(float)tc.py0, (float)(tc.py0 + 8)};
-    float T[2] = {1.f, 1.f}, C0[2] = {0.f, 0.f}, C1[2] = {0.f, 0.f}, C2[2] = {0.f, 0.f},
-          D[2] = {0.f, 0.f};
-    float F[2][NF > 0 ? NF : 1];
+    float fy[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
+    f2 F[PX][NF > 0 ? NF / 2 : 1];  // feature accumulators, channel pairs
+    uint32_t last[PX];
+    bool done[PX];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < PX; ++q) {
+        fy[q] = (float)(tc.py0 + RS * q);
+        T[q] = 1.f;
+        C0[q] = C1[q] = C2[q] = D[q] = 0.f;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) F[q][c] = 0.f;
-    uint32_t last[2] = {0u, 0u};
-    bool done[2] = {!tc.in0, !tc.in1};
+        for (int c = 0; c < NF / 2; ++c) F[q][c] = 0ull;
+        last[q] = 0u;
+        done[q] = !tc.in[q];
+    }
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int q = 0; q < PX; ++q) d = d && done[q];
+        return d;
+    };
     const int set_base = per_view ? 0 : tc.v * N;
     for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
-        if (__syncthreads_count(done[0] && done[1]) == kThreadsBlend) break;
+        if (__syncthreads_count(all_done()) == NT) break;
 #pragma unroll
-        for (int h = 0; h < kBatch / kThreadsBlend; ++h) {
-            uint32_t i = base + threadIdx.x + h * kThreadsBlend;
+        for (int h = 0; h < kBatch / NT; ++h) {
+            uint32_t i = base + threadIdx.x + h * NT;
             if (i < rg.y) {
                 uint32_t gv = ival[i];
-                stage_load<NF>(S, threadIdx.x + h * kThreadsBlend, gv, (int)gv - set_base, xyzo,
-                               conic, color, feat);
+                stage_load<NF>(S, threadIdx.x + h * NT, gv, (int)gv - set_base, xyzo, conic, color, feat);
             }
         }
         __syncthreads();
         const int n = min((int)(rg.y - base), kBatch);
-        for (int j = 0; j < n && !(done[0] && done[1]); ++j) {
+        for (int j = 0; j < n && !all_done(); ++j) {
             const float4 g = S.xyzo[j];
             const float4 cn = S.conic[j];
             const float dx = fx - g.x;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < PX; ++q) {
                 if (done[q]) continue;
                 const float dy = fy[q] - g.y;
                 const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
@@ -154,8 +184,13 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_fwd(
                 C1[q] = fmaf(w, col.y, C1[q]);
                 C2[q] = fmaf(w, col.z, C2[q]);
                 D[q] = fmaf(w, g.z, D[q]);
+                const f2 w2 = f2_make(w, w);
 #pragma unroll
-                for (int c = 0; c < NF; ++c) F[q][c] = fmaf(w, S.feat[c][j], F[q][c]);
+                for (int c = 0; c < NF; c += 4) {
+                    const ulonglong2 f = feat4<NF>(S, j, c);
+                    F[q][c / 2] = f2_fma(w2, f.x, F[q][c / 2]);
+                    F[q][c / 2 + 1] = f2_fma(w2, f.y, F[q][c / 2 + 1]);
+                }
                 T[q] = Tn;
                 last[q] = base - rg.x + j + 1;
             }
@@ -165,15 +200,18 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_fwd(
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (!(q == 0 ? tc.in0 : tc.in1)) continue;
-        const size_t p = (size_t)(tc.py0 + 8 * q) * cam.W + tc.px;
+    for (int q = 0; q < PX; ++q) {
+        if (!tc.in[q]) continue;
+        const size_t p = (size_t)(tc.py0 + RS * q) * cam.W + tc.px;
         out_color[3 * P + p] = C0[q];
         out_color[3 * P + HW + p] = C1[q];
         out_color[3 * P + 2 * HW + p] = C2[q];
         out_depth[P + p] = D[q];
 #pragma unroll
-        for (int c = 0; c < NF; ++c) out_feat[NF * P + c * HW + p] = F[q][c];
+        for (int c = 0; c < NF / 2; ++c) {
+            out_feat[NF * P + 2 * c * HW + p] = f2_lo(F[q][c]);
+            out_feat[NF * P + (2 * c + 1) * HW + p] = f2_hi(F[q][c]);
+        }
         out_T[P + p] = T[q];
         out_nc[P + p] = last[q];
     }
@@ -282,8 +320,8 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[RP], int lane) 
     }
 }
 
-template <int NF>
-__global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
+template <int NF, int PX>
+__global__ void __launch_bounds__(Px<PX>::NT) k_composite_bwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
@@ -291,28 +329,32 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
     const uint32_t *__restrict__ in_nc, const float *__restrict__ dC,
     const float *__restrict__ dD, const float *__restrict__ dF, const float *__restrict__ dT,
     float *__restrict__ g2) {
+    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS;
     constexpr int RP = RecPad<NF>::value;
     constexpr int STRIDE = kG2Base + NF;
     __shared__ Stage<NF> S;
-    __shared__ uint32_t s_max[kThreadsBlend / 32];
-    const Tile2 tc = tile2(vt);
+    __shared__ uint32_t s_max[NT / 32];
+    const TileP<PX> tc = tilep<PX>(vt);
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[blockIdx.x];
     const float fx = (float)tc.px;
-    const float fy[2] = {(float)tc.py0, (float)(tc.py0 + 8)};
     const DevView &cam = *tc.cam;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
-    float T[2] = {1.f, 1.f}, acc[2] = {0.f, 0.f}, gC0[2] = {0.f, 0.f}, gC1[2] = {0.f, 0.f},
-          gC2[2] = {0.f, 0.f}, gD[2] = {0.f, 0.f};
-    float gF[2][NF > 0 ? NF : 1];
-    uint32_t nc[2] = {0u, 0u};
+    float fy[PX], T[PX], acc[PX], gC0[PX], gC1[PX], gC2[PX], gD[PX];
+    f2 gF[PX][NF > 0 ? NF / 2 : 1];  // dL/d(feature image), channel pairs
+    uint32_t nc[PX];
+    uint32_t my_nc = 0;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < PX; ++q) {
+        fy[q] = (float)(tc.py0 + RS * q);
+        T[q] = 1.f;
+        acc[q] = gC0[q] = gC1[q] = gC2[q] = gD[q] = 0.f;
+        nc[q] = 0u;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) gF[q][c] = 0.f;
-        if (!(q == 0 ? tc.in0 : tc.in1)) continue;
-        const size_t p = (size_t)(tc.py0 + 8 * q) * cam.W + tc.px;
+        for (int c = 0; c < NF / 2; ++c) gF[q][c] = 0ull;
+        if (!tc.in[q]) continue;
+        const size_t p = (size_t)(tc.py0 + RS * q) * cam.W + tc.px;
         T[q] = in_T[P + p];
         nc[q] = in_nc[P + p];
         if (dC) {
@@ -323,28 +365,28 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
         if (dD) gD[q] = dD[P + p];
         if (dF)
 #pragma unroll
-            for (int c = 0; c < NF; ++c) gF[q][c] = dF[NF * P + c * HW + p];
+            for (int c = 0; c < NF / 2; ++c)
+                gF[q][c] = f2_make(dF[NF * P + 2 * c * HW + p], dF[NF * P + (2 * c + 1) * HW + p]);
         if (dT) acc[q] = dT[P + p] * T[q];
+        my_nc = max(my_nc, nc[q]);
     }
     // longest blended prefix over the tile
-    uint32_t m = __reduce_max_sync(0xffffffffu, max(nc[0], nc[1]));
+    uint32_t m = __reduce_max_sync(0xffffffffu, my_nc);
     if (lane == 0) s_max[threadIdx.x >> 5] = m;
     __syncthreads();
     uint32_t max_nc = 0;
 #pragma unroll
-    for (int w = 0; w < kThreadsBlend / 32; ++w) max_nc = max(max_nc, s_max[w]);
-    const uint32_t my_nc = max(nc[0], nc[1]);
+    for (int w = 0; w < NT / 32; ++w) max_nc = max(max_nc, s_max[w]);
     const int set_base = per_view ? 0 : tc.v * N;
     for (int hi = (int)max_nc; hi > 0; hi -= kBatch) {
         const int lo = max(0, hi - kBatch);
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < kBatch / kThreadsBlend; ++h) {
-            int i = lo + threadIdx.x + h * kThreadsBlend;
+        for (int h = 0; h < kBatch / NT; ++h) {
+            int i = lo + threadIdx.x + h * NT;
             if (i < hi) {
                 uint32_t gv = ival[rg.x + i];
-                stage_load<NF>(S, threadIdx.x + h * kThreadsBlend, gv, (int)gv - set_base, xyzo,
-                               conic, color, feat);
+                stage_load<NF>(S, threadIdx.x + h * NT, gv, (int)gv - set_base, xyzo, conic, color, feat);
             }
         }
         __syncthreads();
@@ -360,9 +402,12 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
             float v[RP];
 #pragma unroll
             for (int k = 0; k < RP; ++k) v[k] = 0.f;
+            f2 vF[NF > 0 ? NF / 2 : 1];  // feature-gradient sums, channel pairs
+#pragma unroll
+            for (int c = 0; c < NF / 2; ++c) vF[c] = 0ull;
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < PX; ++q) {
                 if (idx >= (int)nc[q]) continue;
                 const float dy = fy[q] - g.y;
                 const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
@@ -372,15 +417,22 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
                 if (alpha < bp.alpha_min) continue;
                 any = true;
                 const float om = 1.f - alpha;
-                T[q] = T[q] / om;  // transmittance in front of this Gaussian
+                const float rom = __frcp_rn(om);
+                T[q] = T[q] * rom;  // transmittance in front of this Gaussian
                 const float w = alpha * T[q];
-                float xg = col.x * gC0[q] + col.y * gC1[q] + col.z * gC2[q] + g.z * gD[q];
+                const f2 w2 = f2_make(w, w);
+                f2 xg2 = 0ull;
 #pragma unroll
-                for (int c = 0; c < NF; ++c) {
-                    xg = fmaf(S.feat[c][j], gF[q][c], xg);
-                    v[kG2Base + c] = fmaf(w, gF[q][c], v[kG2Base + c]);
+                for (int c = 0; c < NF; c += 4) {
+                    const ulonglong2 f = feat4<NF>(S, j, c);
+                    xg2 = f2_fma(f.x, gF[q][c / 2], xg2);
+                    xg2 = f2_fma(f.y, gF[q][c / 2 + 1], xg2);
+                    vF[c / 2] = f2_fma(w2, gF[q][c / 2], vF[c / 2]);
+                    vF[c / 2 + 1] = f2_fma(w2, gF[q][c / 2 + 1], vF[c / 2 + 1]);
                 }
-                const float dalpha = T[q] * xg - acc[q] / om;
+                const float xg = col.x * gC0[q] + col.y * gC1[q] + col.z * gC2[q] + g.z * gD[q] +
+                                 (NF > 0 ? f2_lo(xg2) + f2_hi(xg2) : 0.f);
+                const float dalpha = T[q] * xg - acc[q] * rom;
                 acc[q] = fmaf(w, xg, acc[q]);
                 float dq = 0.f;
                 if (raw < bp.alpha_max) {
@@ -396,6 +448,11 @@ __global__ void __launch_bounds__(kThreadsBlend) k_composite_bwd(
                 v[8] = fmaf(w, gC0[q], v[8]);
                 v[9] = fmaf(w, gC1[q], v[9]);
                 v[10] = fmaf(w, gC2[q], v[10]);
+            }
+#pragma unroll
+            for (int c = 0; c < NF / 2; ++c) {
+                v[kG2Base + 2 * c] = f2_lo(vF[c]);
+                v[kG2Base + 2 * c + 1] = f2_hi(vF[c]);
             }
             if (__any_sync(0xffffffffu, any)) {
                 warp_transpose_reduce<RP>(v, lane);
@@ -428,12 +485,11 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const ups_images &out, cudaStream_t st) {
-    dim3 grid(vt.total_tiles), block(kThreadsBlend);
     if (vt.total_tiles == 0) return cudaSuccess;
-#define UPS_FWD(NFV)                                                                          \
-    k_composite_fwd<NFV><<<grid, block, 0, st>>>(vt, bp, N, per_view, ranges, ival, xyzo, conic, \
-                                                 color, feat, out.color, out.depth, out.feat,  \
-                                                 out.T, out.n_contrib)
+#define UPS_FWD(NFV)                                                                                  \
+    k_composite_fwd<NFV, blend_px_fwd(NFV)><<<vt.total_tiles, Px<blend_px_fwd(NFV)>::NT, 0, st>>>(              \
+        vt, bp, N, per_view, ranges, ival, xyzo, conic, color, feat, out.color, out.depth, out.feat, out.T, \
+        out.n_contrib)
     switch (n_feat) {
         case 0: UPS_FWD(0); break;
         case 16: UPS_FWD(16); break;
@@ -478,12 +534,11 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const float *T, const uint32_t *nc,
                                  const ups_image_grads &dL, float *g2, cudaStream_t st) {
-    dim3 grid(vt.total_tiles), block(kThreadsBlend);
     if (vt.total_tiles == 0) return cudaSuccess;
-#define UPS_BWD(NFV)                                                                          \
-    k_composite_bwd<NFV><<<grid, block, 0, st>>>(vt, bp, N, per_view, ranges, ival, xyzo, conic, \
-                                                 color, feat, T, nc, dL.color, dL.depth,       \
-                                                 dL.feat, dL.T, g2)
+#define UPS_BWD(NFV)                                                                                \
+    k_composite_bwd<NFV, blend_px_bwd(NFV)><<<vt.total_tiles, Px<blend_px_bwd(NFV)>::NT, 0, st>>>(            \
+        vt, bp, N, per_view, ranges, ival, xyzo, conic, color, feat, T, nc, dL.color, dL.depth, dL.feat, \
+        dL.T, g2)
     switch (n_feat) {
         case 0: UPS_BWD(0); break;
         case 16: UPS_BWD(16); break;
