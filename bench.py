@@ -218,7 +218,8 @@ def algorithmic(wl, stats, proc_inst, evals=0):
         "ranges": dict(bytes=I * 8 + stats["n_tiles"] * 8),
         "composite_fwd": dict(bytes=proc_inst * inst_b + P * pix_out, flops=evals * (2 * (NF + 4) + 12)),
         "loss": dict(bytes=P * 4 * (3 * (3 + 1 + NF) + 1)),
-        "composite_bwd": dict(bytes=proc_inst * inst_b + P * (pix_out + 4 * (3 + 1 + NF)) + GV * 4 * (12 + NF),
+        # gradient records: at most one per read instance receives an atomic add
+        "composite_bwd": dict(bytes=proc_inst * (inst_b + 4 * (12 + NF)) + P * (pix_out + 4 * (3 + 1 + NF)),
                               flops=evals * (4 * NF + 60)),
         "project_bwd": dict(bytes=GV * (48 + 4 * (12 + NF) + rec3d)),
         "decode_bwd_rows": dict(bytes=A * anc_b * 2 + GV * rec3d + rows * scratch_row, flops=rows * row_bwd),
@@ -227,6 +228,11 @@ def algorithmic(wl, stats, proc_inst, evals=0):
 
 
 ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
+
+# DRAM bytes (read + write) per launch from one ncu capture of the named kernel on the named
+# workload (profiles/launches_mapping_100k_anchors_x10_8x640x480.md); reported as the roofline's
+# `traffic` only for that kernel and workload.  Re-measure whenever the kernel changes.
+MEASURED_TRAFFIC = {("composite_bwd", "mapping_100k_anchors_x10_8x640x480"): 309.5e6}
 
 
 def run_ours(args, wl_name):
@@ -291,6 +297,7 @@ def run_ours(args, wl_name):
         dom = max(prof, key=lambda k: prof[k][0])
         avg_ms = prof[dom][0] / prof[dom][1]
         roof = roofline(dom, alg, avg_ms, peaks)
+        roof["traffic"] = MEASURED_TRAFFIC.get((dom, wl_name))
         cpu = cpu_baseline(wl, anc, mlp, cams, tg) if not args.no_cpu else None
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
