@@ -170,22 +170,27 @@ def project(g, cam, cfg: RenderCfg):
     lib().orc_project_view(N, *args, C.byref(c), C.byref(cf), valid.ctypes.data_as(_ip),
                            pp, pu, pcv, pcn, rect.ctypes.data_as(_ip), pe)
     return dict(valid=valid, pcam=pcam, uv=uv, cov2d=cov, conic=conic, rect=rect,
-                extent=ext)
+                extent=ext, opacity=np.ascontiguousarray(g["opacity"], dtype=np.float64))
 
 
 def tile_lists(proj, cam, cfg: RenderCfg):
-    """Per-tile Gaussian lists in ascending (float32(z), id) and their ranges."""
+    """Per-tile Gaussian lists in ascending (float32(z), id) and their ranges: a
+    tile of a Gaussian's rect lists it when the alpha >= alpha_min ellipse meets
+    the tile's box of pixel centres."""
     N = proj["valid"].shape[0]
     tx = (cam.width + cfg.tile - 1) // cfg.tile
     ty = (cam.height + cfg.tile - 1) // cfg.tile
     va, pv = _i(proj["valid"])
     pc, ppc = _d(proj["pcam"])
     rc, prc = _i(proj["rect"])
-    total = lib().orc_tile_lists(N, pv, ppc, prc, tx, ty, None, None)
+    uv, puv = _d(proj["uv"])
+    cn, pcn = _d(proj["conic"])
+    op, pop = _d(proj["opacity"])
+    args = (N, pv, ppc, prc, puv, pcn, pop, C.c_double(cfg.alpha_min), cam.width, cam.height, cfg.tile)
+    total = lib().orc_tile_lists(*args, None, None)
     lst = np.zeros(max(total, 1), np.int32)
     rng = np.zeros((tx * ty, 2), np.int32)
-    lib().orc_tile_lists(N, pv, ppc, prc, tx, ty, lst.ctypes.data_as(_ip),
-                         rng.ctypes.data_as(_ip))
+    lib().orc_tile_lists(*args, lst.ctypes.data_as(_ip), rng.ctypes.data_as(_ip))
     return lst[:total], rng
 
 

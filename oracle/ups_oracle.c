@@ -30,8 +30,10 @@
  *  - a Gaussian is culled when Z <= near_z, |X/Z| > guard*W/(2 fx) (same in y),
  *    or o < alpha_min;
  *  - the tile rectangle of a Gaussian is the axis-aligned bounding box of the
- *    ellipse where o exp(-q/2) >= alpha_min, clipped to the image, so the tiled
- *    render equals the all-pairs render exactly;
+ *    ellipse where o exp(-q/2) >= alpha_min, clipped to the image; a tile of
+ *    the rectangle lists the Gaussian when that ellipse meets the tile's box of
+ *    pixel centres (the minimum of q over the box is at most 2 ln(o/alpha_min)),
+ *    so the tiled render equals the all-pairs render exactly;
  *  - depth order is ascending (float32(z), Gaussian id).
  *
  * Pose perturbation: T_cw(xi) = Exp(xi) T_cw, xi = (rho, phi), evaluated at
@@ -327,13 +329,49 @@ static int rect_ntiles(const int *r)
     return (r[2] - r[0] + 1) * (r[3] - r[1] + 1);
 }
 
-/* Per-view tile lists: for each tile t (row-major), the Gaussians whose rect
- * covers t in ascending (float32(z), g).  Writes list_g (concatenated over
- * tiles) and ranges [2*t], [2*t+1] = [start, end).  Returns the number of
- * entries; list_g may be NULL to only count. */
-long orc_tile_lists(int N, const int *valid, const double *pcam, const int *rect,
-                    int tiles_x, int tiles_y, int *list_g, int *ranges)
+/* Minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2 (a positive definite form)
+ * over the box [dx0, dx1] x [dy0, dy1]: zero if the box holds the origin,
+ * otherwise the smallest of the four edge minima (q restricted to an edge is a
+ * 1D convex quadratic, minimised at its vertex clamped to the edge). */
+static double box_min_q(double a, double b, double c, double dx0, double dx1, double dy0, double dy1)
 {
+    if (dx0 <= 0 && 0 <= dx1 && dy0 <= 0 && 0 <= dy1) return 0.0;
+    double best = INFINITY;
+    const double xs[2] = {dx0, dx1}, ys[2] = {dy0, dy1};
+    for (int e = 0; e < 2; ++e) {
+        double dx = xs[e];
+        double dy = fmin(fmax(-b * dx / c, dy0), dy1);
+        best = fmin(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy);
+        dy = ys[e];
+        dx = fmin(fmax(-b * dy / a, dx0), dx1);
+        best = fmin(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy);
+    }
+    return best;
+}
+
+/* Whether tile (tx, ty) lists Gaussian g: the alpha >= alpha_min ellipse meets
+ * the tile's box of pixel centres (clipped to the image). */
+static int tile_hit(const double *uv, const double *conic, double opac, double alpha_min, int width,
+                    int height, int ts, int tx, int ty)
+{
+    if (!(alpha_min > 0)) return 1;
+    double k2 = 2.0 * log(opac / alpha_min);
+    double x0 = tx * ts, x1 = fmin(tx * ts + ts - 1.0, width - 1.0);
+    double y0 = ty * ts, y1 = fmin(ty * ts + ts - 1.0, height - 1.0);
+    double q = box_min_q(conic[0], conic[1], conic[2], x0 - uv[0], x1 - uv[0], y0 - uv[1], y1 - uv[1]);
+    return q <= k2;
+}
+
+/* Per-view tile lists: for each tile t (row-major), the Gaussians whose rect
+ * covers t and whose ellipse meets it (tile_hit), in ascending (float32(z), g).
+ * Writes list_g (concatenated over tiles) and ranges [2*t], [2*t+1] =
+ * [start, end).  Returns the number of entries; list_g may be NULL to only
+ * count. */
+long orc_tile_lists(int N, const int *valid, const double *pcam, const int *rect, const double *uv,
+                    const double *conic, const double *opac, double alpha_min, int width, int height,
+                    int ts, int *list_g, int *ranges)
+{
+    int tiles_x = (width + ts - 1) / ts, tiles_y = (height + ts - 1) / ts;
     zkey *order = malloc(sizeof(zkey) * (N > 0 ? N : 1));
     int n = 0;
     for (int g = 0; g < N; ++g)
@@ -346,9 +384,12 @@ long orc_tile_lists(int N, const int *valid, const double *pcam, const int *rect
     int T = tiles_x * tiles_y;
     long *count = calloc(T + 1, sizeof(long));
     for (int i = 0; i < n; ++i) {
-        const int *r = rect + 4 * order[i].g;
+        const int g = order[i].g;
+        const int *r = rect + 4 * g;
         for (int ty = r[1]; ty <= r[3]; ++ty)
-            for (int tx = r[0]; tx <= r[2]; ++tx) count[ty * tiles_x + tx]++;
+            for (int tx = r[0]; tx <= r[2]; ++tx)
+                if (tile_hit(uv + 2 * g, conic + 3 * g, opac[g], alpha_min, width, height, ts, tx, ty))
+                    count[ty * tiles_x + tx]++;
     }
     long total = 0;
     for (int t = 0; t < T; ++t) {
@@ -362,9 +403,12 @@ long orc_tile_lists(int N, const int *valid, const double *pcam, const int *rect
     }
     if (list_g) {
         for (int i = 0; i < n; ++i) { /* depth order kept within each tile */
-            const int *r = rect + 4 * order[i].g;
+            const int g = order[i].g;
+            const int *r = rect + 4 * g;
             for (int ty = r[1]; ty <= r[3]; ++ty)
-                for (int tx = r[0]; tx <= r[2]; ++tx) list_g[count[ty * tiles_x + tx]++] = order[i].g;
+                for (int tx = r[0]; tx <= r[2]; ++tx)
+                    if (tile_hit(uv + 2 * g, conic + 3 * g, opac[g], alpha_min, width, height, ts, tx, ty))
+                        list_g[count[ty * tiles_x + tx]++] = g;
         }
     }
     free(count);
@@ -385,8 +429,9 @@ typedef struct {
     int n_all;
 } visit_lists;
 
-static void build_visit(int N, const int *valid, const double *pcam, const int *rect,
-                        const orc_camera *cam, const orc_cfg *cfg, visit_lists *vl)
+static void build_visit(int N, const int *valid, const double *pcam, const int *rect, const double *uv,
+                        const double *conic, const double *opac, const orc_camera *cam, const orc_cfg *cfg,
+                        visit_lists *vl)
 {
     int tiles_x = (cam->width + cfg->tile - 1) / cfg->tile;
     int tiles_y = (cam->height + cfg->tile - 1) / cfg->tile;
@@ -406,10 +451,12 @@ static void build_visit(int N, const int *valid, const double *pcam, const int *
         vl->n_all = n;
         free(order);
     } else {
-        long total = orc_tile_lists(N, valid, pcam, rect, tiles_x, tiles_y, NULL, NULL);
+        long total = orc_tile_lists(N, valid, pcam, rect, uv, conic, opac, cfg->alpha_min, cam->width,
+                                    cam->height, cfg->tile, NULL, NULL);
         vl->list = malloc(sizeof(int) * (total > 0 ? total : 1));
         vl->ranges = malloc(sizeof(int) * 2 * tiles_x * tiles_y);
-        orc_tile_lists(N, valid, pcam, rect, tiles_x, tiles_y, vl->list, vl->ranges);
+        orc_tile_lists(N, valid, pcam, rect, uv, conic, opac, cfg->alpha_min, cam->width, cam->height,
+                       cfg->tile, vl->list, vl->ranges);
     }
 }
 
@@ -449,7 +496,7 @@ void orc_render_view(int N, int NL, const int *valid, const double *pcam, const 
                      double *out_T, int *out_nc, double *out_margin)
 {
     visit_lists vl;
-    build_visit(N, valid, pcam, rect, cam, cfg, &vl);
+    build_visit(N, valid, pcam, rect, uv, conic, opac, cam, cfg, &vl);
     int Wd = cam->width, Ht = cam->height;
     size_t P = (size_t)Wd * Ht;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -557,7 +604,7 @@ void orc_render_bwd_view(int N, int NL, const int *valid, const double *pcam, co
                          double *g_opac, double *g_color, double *g_z, double *g_feat)
 {
     visit_lists vl;
-    build_visit(N, valid, pcam, rect, cam, cfg, &vl);
+    build_visit(N, valid, pcam, rect, uv, conic, opac, cam, cfg, &vl);
     int Wd = cam->width, Ht = cam->height;
     size_t P = (size_t)Wd * Ht;
     memset(g_uv, 0, sizeof(double) * 2 * N);

@@ -238,7 +238,7 @@ def test_alpha_min_skip():
 
 @pytest.mark.parametrize("seed,w,h", [(7, 50, 37), (8, 33, 17), (9, 16, 16), (10, 70, 45)])
 def test_tiled_equals_brute(seed, w, h):
-    """Every pixel with alpha >= alpha_min lies in the Gaussian's tile rect."""
+    """Every pixel with alpha >= alpha_min lies in a tile that lists the Gaussian."""
     g, c = _random_scene(seed, 180, nf=3, w=w, h=h)
     # include Gaussians that straddle or leave the image
     g["mean"][:20, 0] = np.linspace(-1.6, 1.6, 20)
@@ -249,27 +249,77 @@ def test_tiled_equals_brute(seed, w, h):
         assert np.array_equal(a[k], b[k]), k
 
 
+def _q(pr, g, x, y):
+    """Quadratic form of Gaussian g at pixel coordinates (x, y) (numpy broadcasting)."""
+    a, b, c = pr["conic"][g]
+    dx, dy = x - pr["uv"][g, 0], y - pr["uv"][g, 1]
+    return a * dx * dx + 2 * b * dx * dy + c * dy * dy
+
+
 def test_tile_lists_match_stable_sort():
+    """Tile lists against independent checks: every tile holding a pixel centre
+    with alpha >= alpha_min lists the Gaussian (brute force over pixels); every
+    listed tile is in the rect and its box of pixel centres meets the ellipse
+    (dense sampling of the box); each list is in ascending (float32 z, id)."""
     g, c = _random_scene(11, 300, w=70, h=45)
     pr = oracle.project(g, c, CFG)
     lst, rng = oracle.tile_lists(pr, c, CFG)
-    tx = (c.width + 15) // 16
-    keys_t, keys_z, keys_g = [], [], []
+    tx, ty = (c.width + 15) // 16, (c.height + 15) // 16
+    listed = [set(lst[rng[t, 0]:rng[t, 1]].tolist()) for t in range(tx * ty)]
+    n_dropped = 0
     for gi in range(300):
         if not pr["valid"][gi]:
+            assert not any(gi in s for s in listed)
             continue
+        k2 = 2 * math.log(g["opacity"][gi] * 255)
         x0, y0, x1, y1 = pr["rect"][gi]
-        for ty in range(y0, y1 + 1):
-            for txx in range(x0, x1 + 1):
-                keys_t.append(ty * tx + txx)
-                keys_z.append(np.float32(pr["pcam"][gi, 2]))
-                keys_g.append(gi)
-    keys_t, keys_z, keys_g = map(np.array, (keys_t, keys_z, keys_g))
-    order = np.lexsort((keys_g, keys_z, keys_t))
-    assert np.array_equal(lst, keys_g[order])
-    counts = np.bincount(keys_t, minlength=rng.shape[0])
-    assert np.array_equal(rng[:, 1] - rng[:, 0], counts)
+        for t in range(tx * ty):
+            ttx, tty = t % tx, t // tx
+            in_rect = x0 <= ttx <= x1 and y0 <= tty <= y1
+            xs = np.arange(16 * ttx, min(16 * ttx + 16, c.width))
+            ys = np.arange(16 * tty, min(16 * tty + 16, c.height))
+            if not in_rect:
+                assert gi not in listed[t]
+                continue
+            qpix = _q(pr, gi, xs[None, :].astype(float), ys[:, None].astype(float)).min()
+            if qpix <= k2 * (1 - 1e-9):
+                assert gi in listed[t], (gi, t)
+            if gi in listed[t]:
+                xf = np.linspace(xs[0], xs[-1], 8 * (len(xs) - 1) + 1)
+                yf = np.linspace(ys[0], ys[-1], 8 * (len(ys) - 1) + 1)
+                assert _q(pr, gi, xf[None, :], yf[:, None]).min() <= k2 * 1.01 + 1e-9, (gi, t)
+            else:
+                n_dropped += 1
+    assert n_dropped > 0  # the ellipse test removes rect tiles
+    for t in range(tx * ty):
+        a = lst[rng[t, 0]:rng[t, 1]]
+        key = [(np.float32(pr["pcam"][x, 2]), x) for x in a]
+        assert key == sorted(key)
+    counts = rng[:, 1] - rng[:, 0]
     assert np.array_equal(rng[:, 0], np.concatenate([[0], np.cumsum(counts)[:-1]]))
+
+
+def test_elongated_gaussian_lists_only_tiles_it_meets():
+    """A long thin Gaussian along the image diagonal: its rect is the full 5 x 5
+    tile grid, but the far corners (0, 4) and (4, 0) lie well outside the
+    alpha >= alpha_min ellipse and are not listed; the diagonal tiles are."""
+    c = cam(fx=100.0, fy=100.0, w=80, h=80)
+    rot = Rotation.from_euler("z", 45, degrees=True).as_quat()  # x, y, z, w
+    q = [rot[3], rot[0], rot[1], rot[2]]
+    g = gauss([[0, 0, 2.0]], [0.8, 0.01, 0.01], quats=[q], opac=[0.9])
+    pr = oracle.project(g, c, CFG)
+    lst, rng = oracle.tile_lists(pr, c, CFG)
+    assert tuple(pr["rect"][0]) == (0, 0, 4, 4)
+    listed = {t for t in range(25) if rng[t, 1] > rng[t, 0]}
+    for k in range(5):
+        assert 5 * k + k in listed
+    assert 4 not in listed and 20 not in listed
+    assert len(listed) < 25
+    # and the render still equals the all-pairs render
+    a = oracle.render(pr, g, c, CFG, 0)
+    b = oracle.render(pr, g, c, BRUTE, 0)
+    for key in ("color", "depth", "T"):
+        assert np.array_equal(a[key], b[key]), key
 
 
 # ---------------------------------------------------------------------------
