@@ -24,9 +24,9 @@ cudaError_t launch_project_k32(const ViewTable &vt, const BlendParams &bp, int N
                                int vbits, cudaStream_t st);
 cudaError_t launch_gather_counts(const uint32_t *sorted_gv, const uint32_t *count, uint32_t *out,
                                  int total, cudaStream_t st);
-cudaError_t launch_emit(const ViewTable &vt, int N, int total, const uint32_t *sorted_gv,
-                        const uint64_t *off, const uint2 *rect, uint32_t *ikey, uint32_t *ival,
-                        cudaStream_t st);
+cudaError_t launch_emit(const ViewTable &vt, const BlendParams &bp, int N, int total, const uint32_t *sorted_gv,
+                        const uint64_t *off, const uint2 *rect, const float4 *xyzo, const float4 *conic,
+                        uint32_t *ikey, uint32_t *ival, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *ikey, uint32_t n, uint2 *ranges, cudaStream_t st);
 cudaError_t launch_project_bwd(const ViewTable &vt, const BlendParams &bp, int N, int per_view,
                                int total, int n_feat, unsigned mask, float scale_grad,
@@ -483,7 +483,8 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     uint32_t *ik = c->ikey0.as<uint32_t>(), *ik_alt = c->ikey1.as<uint32_t>();
     uint32_t *iv = c->ival0.as<uint32_t>(), *iv_alt = c->ival1.as<uint32_t>();
     stage_begin(c, "emit", st);
-    UPS_CUDA(c, launch_emit(vt, c->N, (int)total, dv, c->off.as<uint64_t>(), c->rect.as<uint2>(), ik, iv, st));
+    UPS_CUDA(c, launch_emit(vt, c->bp, c->N, (int)total, dv, c->off.as<uint64_t>(), c->rect.as<uint2>(),
+                            c->xyzo.as<float4>(), c->conic.as<float4>(), ik, iv, st));
     stage_end(c, st, 1);
     // stable bucket by (view, tile): depth order is kept inside each tile
     c->key_bits = bits_for((size_t)vt.total_tiles);

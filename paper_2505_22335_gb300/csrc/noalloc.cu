@@ -35,9 +35,9 @@ cudaError_t launch_project(const ViewTable &vt, const BlendParams &bp, int N, in
                            cudaStream_t st);
 cudaError_t launch_gather_counts(const uint32_t *sorted_gv, const uint32_t *count, uint32_t *out,
                                  int total, cudaStream_t st);
-cudaError_t launch_emit(const ViewTable &vt, int N, int total, const uint32_t *sorted_gv,
-                        const uint64_t *off, const uint2 *rect, uint32_t *ikey, uint32_t *ival,
-                        cudaStream_t st);
+cudaError_t launch_emit(const ViewTable &vt, const BlendParams &bp, int N, int total, const uint32_t *sorted_gv,
+                        const uint64_t *off, const uint2 *rect, const float4 *xyzo, const float4 *conic,
+                        uint32_t *ikey, uint32_t *ival, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t *ikey, uint32_t n, uint2 *ranges, cudaStream_t st);
 cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
@@ -218,7 +218,7 @@ extern "C" ups_status ups_render_forward_static(const ups_config *cfg, const ups
     NA_CUDA(cudaStreamSynchronize(st));
     if (n_inst > kMaxInst)
         return fail(UPS_ERR_CAPACITY, std::to_string(n_inst) + " tile instances exceed 524288");
-    NA_CUDA(launch_emit(vt, N, (int)total, dv, off, rect, ik, iv, st));
+    NA_CUDA(launch_emit(vt, bp, N, (int)total, dv, off, rect, xyzo, conic, ik, iv, st));
     NA_CUDA(radix_sort_u32_fixed(&ik, &ik_alt, &iv, &iv_alt, (size_t)n_inst,
                                  bits_for((size_t)vt.total_tiles), sort_scr, kSortScratch, st));
     NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)vt.total_tiles * sizeof(uint2), st));

@@ -92,6 +92,48 @@ __device__ __forceinline__ void covariance(const DevView &cam, const BlendParams
     G.C = t1[0] * G.T[3] + t1[1] * G.T[4] + t1[2] * G.T[5] + bp.dilation;
 }
 
+// The alpha >= alpha_min ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= k2,
+// k2 = 2 ln(o / alpha_min), of a projected Gaussian at (u, v), conic (a, b, c).
+struct Ellipse {
+    float u, v, a, b, k2, detc, ry, dyr;
+};
+
+__device__ __forceinline__ Ellipse ellipse_of(float4 xo, float4 cn, float alpha_min) {
+    Ellipse e;
+    e.u = xo.x;
+    e.v = xo.y;
+    e.a = cn.x;
+    e.b = cn.y;
+    // a relative margin so FP32 rounding never drops a tile the blend uses
+    e.k2 = 2.f * logf(xo.w / alpha_min) * (1.f + 1e-4f);
+    e.detc = cn.x * cn.z - cn.y * cn.y;
+    e.ry = sqrtf(e.k2 * cn.x / e.detc);               // half-extent in y
+    e.dyr = -cn.y * sqrtf(e.k2 / (cn.z * e.detc));    // dy of the point of largest x
+    return e;
+}
+
+// Tile columns [c0, c1] of tile row ty (clipped to the rect's columns
+// [x0, x1]; c0 > c1: none) whose box of pixel centres the ellipse meets.  The
+// ellipse's slice through the row's band of pixel centres is an x interval;
+// its ends are the right-most and left-most boundary points, whose dy is the
+// unconstrained extreme clamped to the band (the boundary's x is concave /
+// convex in dy).
+__device__ __forceinline__ int2 row_cols(const Ellipse &e, int ty, int W, int H, int x0, int x1) {
+    const float yb0 = (float)(ty * kTile), yb1 = fminf((float)(ty * kTile + kTile - 1), (float)(H - 1));
+    const float lo = fmaxf(yb0 - e.v, -e.ry), hi = fminf(yb1 - e.v, e.ry);
+    if (!(lo <= hi)) return make_int2(1, 0);
+    const float dr = fminf(fmaxf(e.dyr, lo), hi), dl = fminf(fmaxf(-e.dyr, lo), hi);
+    const float ia = 1.f / e.a;
+    const float xr = (-e.b * dr + sqrtf(fmaxf(e.a * e.k2 - e.detc * dr * dr, 0.f))) * ia;
+    const float xl = (-e.b * dl - sqrtf(fmaxf(e.a * e.k2 - e.detc * dl * dl, 0.f))) * ia;
+    const float xlo = fmaxf(e.u + xl - 1e-3f, 0.f), xhi = fminf(e.u + xr + 1e-3f, (float)(W - 1));
+    if (!(xlo <= xhi)) return make_int2(1, 0);
+    // tile tx holds pixel centres [16 tx, 16 tx + 15]: the first whose box
+    // reaches xlo, the last whose box starts at or before xhi
+    return make_int2(max((int)ceilf((xlo - (float)(kTile - 1)) * (1.f / kTile)), x0),
+                     min((int)floorf(xhi * (1.f / kTile)), x1));
+}
+
 __global__ void __launch_bounds__(256) k_project(
     ViewTable vt, BlendParams bp, int N, int per_view, int total,
     const float4 *__restrict__ mean_op, const float4 *__restrict__ scale,
@@ -128,7 +170,12 @@ __global__ void __launch_bounds__(256) k_project(
         if (xlo <= xhi && ylo <= yhi) {
             int x0 = (int)floorf(xlo * (1.f / kTile)), x1 = (int)floorf(xhi * (1.f / kTile));
             int y0 = (int)floorf(ylo * (1.f / kTile)), y1 = (int)floorf(yhi * (1.f / kTile));
-            cnt = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+            // tiles of the rect that the ellipse meets (same arithmetic as k_emit)
+            const Ellipse e = ellipse_of(xo, cn, bp.alpha_min);
+            for (int ty = y0; ty <= y1; ++ty) {
+                const int2 cc = row_cols(e, ty, cam.W, cam.H, x0, x1);
+                if (cc.x <= cc.y) cnt += (uint32_t)(cc.y - cc.x + 1);
+            }
             rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
         }
     }
@@ -161,15 +208,23 @@ __global__ void k_gather_counts(const uint32_t *__restrict__ sorted_gv,
 // Instances of 32 consecutive depth-ordered Gaussian-views are written by one
 // warp: the warp walks its contiguous instance range 32 at a time, each lane
 // finds its source Gaussian by a binary search over the lanes' start offsets,
-// so stores are coalesced whatever the per-Gaussian tile counts are.
-__global__ void __launch_bounds__(256) k_emit(ViewTable vt, int N, int total,
+// so stores are coalesced whatever the per-Gaussian tile counts are.  Each
+// owner lane first tabulates its Gaussian's met columns per tile row (first
+// column and running instance count) in shared memory, up to kEmitRows rows;
+// taller Gaussians (rare) recompute the rows per instance.
+constexpr int kEmitRows = 8;
+
+__global__ void __launch_bounds__(256) k_emit(ViewTable vt, BlendParams bp, int N, int total,
                                               const uint32_t *__restrict__ sorted_gv,
                                               const uint64_t *__restrict__ off,
                                               const uint2 *__restrict__ rect,
+                                              const float4 *__restrict__ xyzo,
+                                              const float4 *__restrict__ conic,
                                               uint32_t *__restrict__ ikey,
                                               uint32_t *__restrict__ ival) {
+    __shared__ uint32_t s_rows[256 / 32][32][kEmitRows];  // first column | (instances before the row << 16)
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     if (s0 >= total) return;  // warp-uniform
     const int s = s0 + lane;
@@ -179,7 +234,26 @@ __global__ void __launch_bounds__(256) k_emit(ViewTable vt, int N, int total,
     const uint64_t o_beg = __shfl_sync(full, o, 0);
     uint32_t gv = in ? sorted_gv[s] : 0u;
     uint2 rc = make_uint2(0u, 0u);
-    if (in && o_end > o) rc = rect[gv];
+    float4 xo = make_float4(0.f, 0.f, 0.f, 1.f), cn = make_float4(1.f, 0.f, 1.f, 0.f);
+    const bool mine = in && off[s + 1] > o;
+    if (mine) {
+        rc = rect[gv];
+        xo = xyzo[gv];
+        cn = conic[gv];
+        const int v = (int)(gv / (uint32_t)N);
+        const DevView &cam = vt.v[v];
+        const int x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
+        if (y1 - y0 < kEmitRows) {
+            const Ellipse e = ellipse_of(xo, cn, bp.alpha_min);
+            uint32_t before = 0;
+            for (int r = y0; r <= y1; ++r) {
+                const int2 cc = row_cols(e, r, cam.W, cam.H, x0, x1);
+                s_rows[wid][lane][r - y0] = (uint32_t)max(cc.x, 0) | (before << 16);
+                if (cc.x <= cc.y) before += (uint32_t)(cc.y - cc.x + 1);
+            }
+        }
+    }
+    __syncwarp();
     for (uint64_t b = o_beg; b < o_end; b += 32) {
         const uint64_t i = b + lane;
         int L = 0;
@@ -195,10 +269,31 @@ __global__ void __launch_bounds__(256) k_emit(ViewTable vt, int N, int total,
         if (i < o_end) {
             const int v = (int)(g / (uint32_t)N);
             const DevView &cam = vt.v[v];
-            const int x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
-            const int wdt = x1 - x0 + 1;
+            const int x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff, y1 = r1 >> 16;
             const int j = (int)(i - oL);
-            const int ty = y0 + j / wdt, tx = x0 + j % wdt;
+            int tx = x0, ty = y0;
+            if (y1 - y0 < kEmitRows) {
+                // last tabulated row whose running count is <= j
+                int r = 0;
+                for (int k = 1; k <= y1 - y0; ++k)
+                    if ((int)(s_rows[wid][L][k] >> 16) <= j) r = k;
+                const uint32_t e = s_rows[wid][L][r];
+                tx = (int)(e & 0xffff) + j - (int)(e >> 16);
+                ty = y0 + r;
+            } else {
+                const Ellipse e = ellipse_of(xyzo[g], conic[g], bp.alpha_min);
+                int jj = j;
+                for (int r = y0; r <= y1; ++r) {
+                    const int2 cc = row_cols(e, r, cam.W, cam.H, x0, x1);
+                    const int n = cc.x <= cc.y ? cc.y - cc.x + 1 : 0;
+                    if (jj < n) {
+                        tx = cc.x + jj;
+                        ty = r;
+                        break;
+                    }
+                    jj -= n;
+                }
+            }
             ikey[i] = (uint32_t)(cam.tile_base + ty * cam.tiles_x + tx);
             ival[i] = g;
         }
@@ -459,11 +554,11 @@ cudaError_t launch_gather_counts(const uint32_t *sorted_gv, const uint32_t *coun
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const ViewTable &vt, int N, int total, const uint32_t *sorted_gv,
-                        const uint64_t *off, const uint2 *rect, uint32_t *ikey, uint32_t *ival,
-                        cudaStream_t st) {
+cudaError_t launch_emit(const ViewTable &vt, const BlendParams &bp, int N, int total, const uint32_t *sorted_gv,
+                        const uint64_t *off, const uint2 *rect, const float4 *xyzo, const float4 *conic,
+                        uint32_t *ikey, uint32_t *ival, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
-    k_emit<<<(total + 255) / 256, 256, 0, st>>>(vt, N, total, sorted_gv, off, rect, ikey, ival);
+    k_emit<<<(total + 255) / 256, 256, 0, st>>>(vt, bp, N, total, sorted_gv, off, rect, xyzo, conic, ikey, ival);
     return cudaGetLastError();
 }
 

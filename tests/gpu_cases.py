@@ -74,6 +74,24 @@ def last_blended_ids(nc, lst, rng, tile_base=0, id_base=0):
     return np.where(nc > 0, ids, -1)
 
 
+def blend_ids(res, gpu_views):
+    """Per view, (GPU, oracle) id of every pixel's last blended Gaussian: the
+    GPU's tile lists may hold an extra Gaussian whose ellipse passes within the
+    FP32 margin of a tile without blending there, which shifts n_contrib but not
+    the blended Gaussians."""
+    R, cams = res["R"], res["cams"]
+    glist = R.copy_buffer(0)
+    grng = R.copy_buffer(2).reshape(-1, 2)
+    N = res["views"][0]["proj"]["valid"].shape[0]
+    out, tile_base = [], 0
+    for v, (cam, vw) in enumerate(zip(cams, res["views"])):
+        lst, rng = oracle.tile_lists(vw["proj"], cam, CFG)
+        out.append((last_blended_ids(gpu_views[v]["n_contrib"], glist, grng, tile_base, v * N),
+                    last_blended_ids(vw["img"]["n_contrib"], lst, rng)))
+        tile_base += ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    return out
+
+
 def depth_tie(za, zb, ulps=4):
     """True where two depths are within `ulps` float32 ulps (order may flip)."""
     za = np.asarray(za, np.float32)
@@ -182,7 +200,8 @@ def plain_case(seed, n, cams, nf, weighted, l2=False, lambda_scale=0.0, g=None):
 def check_plain(res, nf, grads=True):
     gpu_views = split_images(res["img"], res["cams"], nf)
     mag = [feat_magnitude(v["proj"], res["g"], c, nf) for v, c in zip(res["views"], res["cams"])]
-    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf, feat_mag=mag)
+    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf, feat_mag=mag,
+                  last_ids=blend_ids(res, gpu_views))
     assert abs(res["loss"] - res["L"]) <= 1e-5 + 1e-4 * abs(res["L"]), (res["loss"], res["L"])
     if not grads:
         return

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_cases import (CFG, assert_grad, assert_pixels, check_plain, feat_magnitude, gauss_grads,
+from gpu_cases import (CFG, assert_grad, assert_pixels, blend_ids, check_plain, feat_magnitude, gauss_grads,
                        plain_case,
                        r32, rel_l2, round_cams, round_dict, split_images)
 from paper_2505_22335_gb300 import binding as B
@@ -36,8 +36,25 @@ def test_plain_2k_forward_backward():
     check_plain(res, 0)
 
 
-def _ambiguous(proj, cam, eps=1e-3):
-    """Gaussians whose tile rect is decided within eps px of a tile/image edge."""
+def _box_min_q(conic, du0, du1, dv0, dv1):
+    """Minimum of a dx^2 + 2 b dx dy + c dy^2 over the boxes [du0, du1] x [dv0, dv1]
+    (arrays), by dense evaluation on a 1/16-pixel grid plus the vertex rule on each
+    edge; used only to decide which decisions are too close to call."""
+    a, b, c = conic
+    best = np.where((du0 <= 0) & (du1 >= 0) & (dv0 <= 0) & (dv1 >= 0), 0.0, np.inf)
+    for dx_fixed in (du0, du1):
+        dy = np.clip(-b * dx_fixed / c, dv0, dv1)
+        best = np.minimum(best, a * dx_fixed ** 2 + 2 * b * dx_fixed * dy + c * dy ** 2)
+    for dy_fixed in (dv0, dv1):
+        dx = np.clip(-b * dy_fixed / a, du0, du1)
+        best = np.minimum(best, a * dx ** 2 + 2 * b * dx * dy_fixed + c * dy_fixed ** 2)
+    return best
+
+
+def _ambiguous(proj, cam, eps=1e-3, rel=1e-3):
+    """Gaussians whose tile membership is decided within eps px of a tile/image
+    edge (the rect), or whose ellipse passes within `rel` (relative, in q) of a
+    rect tile's box of pixel centres (the FP32 path tests with a small margin)."""
     ext = proj["extent"]
     amb = np.zeros(len(ext), bool)
     for lo, hi, lim in ((ext[:, 0], ext[:, 2], cam.width - 1), (ext[:, 1], ext[:, 3], cam.height - 1)):
@@ -46,6 +63,20 @@ def _ambiguous(proj, cam, eps=1e-3):
             m |= np.abs(e) < eps
             m |= np.abs(e - lim) < eps
             amb |= m
+    for g in np.nonzero(proj["valid"] == 1)[0]:
+        x0, y0, x1, y1 = proj["rect"][g]
+        if x0 > x1 or y0 > y1:
+            continue
+        k2 = 2 * np.log(proj["opacity"][g] * 255)
+        tx, ty = np.meshgrid(np.arange(x0, x1 + 1), np.arange(y0, y1 + 1))
+        bx0, by0 = 16.0 * tx, 16.0 * ty
+        bx1 = np.minimum(bx0 + 15, cam.width - 1)
+        by1 = np.minimum(by0 + 15, cam.height - 1)
+        u, v = proj["uv"][g]
+        q_in = _box_min_q(proj["conic"][g], bx0 - u, bx1 - u, by0 - v, by1 - v)
+        q_out = _box_min_q(proj["conic"][g], bx0 - u - 0.01, bx1 - u + 0.01, by0 - v - 0.01, by1 - v + 0.01)
+        if np.any((q_in > k2 * (1 - rel)) & (q_out <= k2 * (1 + rel))):
+            amb[g] = True
     return amb & (proj["valid"] == 1)
 
 
@@ -58,28 +89,22 @@ def test_plain_2k_tile_lists_and_sort_bit_exact():
     ranges = R.copy_buffer(2).reshape(-1, 2)
     xyzo = R.copy_buffer(3).reshape(-1, 4)
     rect = R.copy_buffer(5).reshape(-1, 2)
-    # (i) the sort stage: the GPU's own keys through numpy's stable sort
-    inst_t, inst_z, inst_g = [], [], []
-    tiles_x = (cam.width + 15) // 16
-    for i in range(len(rect)):
-        x0, y0, x1, y1 = rect[i, 0] & 0xffff, rect[i, 0] >> 16, rect[i, 1] & 0xffff, rect[i, 1] >> 16
-        for ty in range(y0, y1 + 1):
-            for tx in range(x0, x1 + 1):
-                inst_t.append(ty * tiles_x + tx)
-                inst_z.append(np.float32(xyzo[i, 2]).view(np.uint32))
-                inst_g.append(i)
-    # Gaussians with count 0 have rect (0,0,0,0) which also encodes tile 0: drop
-    # them using the GPU's own instance total
-    inst_t, inst_z, inst_g = map(np.array, (inst_t, inst_z, inst_g))
-    valid_g = np.unique(gv)
-    keep = np.isin(inst_g, valid_g)
-    inst_t, inst_z, inst_g = inst_t[keep], inst_z[keep], inst_g[keep]
-    order = np.lexsort((inst_g, inst_z, inst_t))
-    assert len(order) == len(gv)
-    assert np.array_equal(gv, inst_g[order])
-    assert np.array_equal(keys, inst_t[order])
-    counts = np.bincount(inst_t, minlength=len(ranges))
+    # (i) the sort stage: the GPU's instances are in (tile, float32 z, id) order,
+    # each (tile, Gaussian) at most once, and the ranges delimit the tiles
+    z = np.float32(xyzo[gv, 2]).view(np.uint32)
+    order = np.lexsort((gv, z, keys))
+    assert np.array_equal(order, np.arange(len(gv)))
+    pair = keys.astype(np.int64) * (1 << 32) + gv
+    assert len(np.unique(pair)) == len(pair)
+    counts = np.bincount(keys, minlength=len(ranges))
     assert np.array_equal(ranges[:, 1] - ranges[:, 0], counts)
+    nz = counts > 0
+    assert np.array_equal(ranges[nz, 0], np.concatenate([[0], np.cumsum(counts)[:-1]])[nz])
+    # every instance lies in its Gaussian's rect
+    x0, y0 = rect[gv, 0] & 0xffff, rect[gv, 0] >> 16
+    x1, y1 = rect[gv, 1] & 0xffff, rect[gv, 1] >> 16
+    tiles_x = (cam.width + 15) // 16
+    assert np.all((keys % tiles_x >= x0) & (keys % tiles_x <= x1) & (keys // tiles_x >= y0) & (keys // tiles_x <= y1))
     # (ii) tile lists against the oracle's own projection and stable sort
     pr = res["views"][0]["proj"]
     lst, orng = oracle.tile_lists(pr, cam, CFG)
@@ -93,7 +118,7 @@ def test_plain_2k_tile_lists_and_sort_bit_exact():
         if not np.array_equal(a, b):
             n_diff += 1
     assert n_diff == 0
-    assert amb.sum() <= 5
+    assert amb.sum() <= 20  # 1% of the scene
 
 
 def test_multiview_ragged_feat16_weighted_l2():
@@ -185,7 +210,8 @@ def check_anchor(res, nf):
             np.testing.assert_allclose(fe[v], rg["feat"], atol=1e-5, rtol=1e-5)
     gpu_views = split_images(res["img"], res["cams"], nf)
     mag = [feat_magnitude(v["proj"], v["g"], c, nf) for v, c in zip(res["views"], res["cams"])]
-    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf, feat_mag=mag)
+    assert_pixels(gpu_views, [v["img"] for v in res["views"]], nf, feat_mag=mag,
+                  last_ids=blend_ids(res, gpu_views))
     assert abs(res["loss"] - res["L"]) <= 1e-5 + 1e-4 * abs(res["L"]), (res["loss"], res["L"])
     # per-view decoded-Gaussian gradients
     gg = gauss_grads(res["grad"], nf, V)
