@@ -24,7 +24,6 @@ constexpr int kH = 32;       // hidden width per MLP
 constexpr int kFin = 32;     // anchor feature width
 constexpr int kDin = kFin + 6;
 constexpr int kDinP = 40;    // padded input width (float4 rows)
-constexpr int kMaxK = 16;
 constexpr int kDX = kFin + 4;  // MLP inputs with a gradient: f_v, delta_vc, d_vc
 constexpr size_t kMaxSmem = 227 * 1024;  // opt-in shared memory per block
 
@@ -36,18 +35,6 @@ struct DecodeArgs {
     const float *pos, *afeat, *offs, *ascale;
     const float *w1, *b1, *w2, *b2;
 };
-
-// shared layout: W1 [128][40] (padded), b1 [128], W2 [n_out][32], b2 [n_out]
-__device__ __forceinline__ void load_weights(const DecodeArgs &a, float *sW1, float *sb1, float *sW2,
-                                             float *sb2) {
-    for (int i = threadIdx.x; i < 4 * kH * kDinP; i += blockDim.x) {
-        int r = i / kDinP, c = i - r * kDinP;
-        sW1[i] = c < kDin ? a.w1[r * kDin + c] : 0.f;
-    }
-    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sb1[i] = a.b1[i];
-    for (int i = threadIdx.x; i < a.n_out * kH; i += blockDim.x) sW2[i] = a.w2[i];
-    for (int i = threadIdx.x; i < a.n_out; i += blockDim.x) sb2[i] = a.b2[i];
-}
 
 // x (padded to 40) for anchor `an` seen from view `cam`; returns delta and d.
 __device__ __forceinline__ void mlp_input(const DecodeArgs &a, const DevView &cam, int an,
@@ -85,37 +72,73 @@ __device__ __forceinline__ void mlp_input(const DecodeArgs &a, const DevView &ca
     x[39] = 0.f;
 }
 
-// hidden block g: z = W1_g x + b1_g (32 values)
-__device__ __forceinline__ void hidden_pre(const float *sW1, const float *sb1, int g,
-                                           const float x[kDinP], float z[kH]) {
-#pragma unroll 4
-    for (int j = 0; j < kH; ++j) {
-        const float4 *w = reinterpret_cast<const float4 *>(sW1 + (g * kH + j) * kDinP);
-        float acc = sb1[g * kH + j];
+// hidden block g: z = W1_g x + b1_g (32 values), input-outer so the 32
+// accumulators stay in registers.  W1 is transposed in shared memory
+// ([38][128]: input-major); the anchor-feature part of x is read through L1
+// (rows of the same anchor share it), the camera-dependent tail x[32..37]
+// comes in registers.
+__device__ __forceinline__ void hidden_T(const float *sW1T, const float *sb1, int g, const float *afeat_row,
+                                         const float xt[6], float h[kH]) {
 #pragma unroll
-        for (int q = 0; q < kDinP / 4; ++q) {
-            float4 ww = w[q];
-            acc = fmaf(ww.x, x[4 * q], acc);
-            acc = fmaf(ww.y, x[4 * q + 1], acc);
-            acc = fmaf(ww.z, x[4 * q + 2], acc);
-            acc = fmaf(ww.w, x[4 * q + 3], acc);
+    for (int j = 0; j < kH; ++j) h[j] = sb1[g * kH + j];
+    const float4 *f4 = reinterpret_cast<const float4 *>(afeat_row);
+#pragma unroll 1
+    for (int i4 = 0; i4 < kFin / 4; ++i4) {
+        const float4 xv = __ldg(f4 + i4);
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 *w = reinterpret_cast<const float4 *>(sW1T + (4 * i4 + u) * 128 + g * kH);
+#pragma unroll
+            for (int q = 0; q < kH / 4; ++q) {
+                const float4 ww = w[q];
+                h[4 * q] = fmaf(ww.x, xs[u], h[4 * q]);
+                h[4 * q + 1] = fmaf(ww.y, xs[u], h[4 * q + 1]);
+                h[4 * q + 2] = fmaf(ww.z, xs[u], h[4 * q + 2]);
+                h[4 * q + 3] = fmaf(ww.w, xs[u], h[4 * q + 3]);
+            }
         }
-        z[j] = acc;
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        const float4 *w = reinterpret_cast<const float4 *>(sW1T + (kFin + u) * 128 + g * kH);
+#pragma unroll
+        for (int q = 0; q < kH / 4; ++q) {
+            const float4 ww = w[q];
+            h[4 * q] = fmaf(ww.x, xt[u], h[4 * q]);
+            h[4 * q + 1] = fmaf(ww.y, xt[u], h[4 * q + 1]);
+            h[4 * q + 2] = fmaf(ww.z, xt[u], h[4 * q + 2]);
+            h[4 * q + 3] = fmaf(ww.w, xt[u], h[4 * q + 3]);
+        }
     }
 }
 
+// y_r = W2[r] . h + b2[r] with four partial sums (short dependency chains)
 __device__ __forceinline__ float out_row(const float *sW2, const float *sb2, int r, const float h[kH]) {
     const float4 *w = reinterpret_cast<const float4 *>(sW2 + r * kH);
-    float acc = sb2[r];
+    float acc[4] = {sb2[r], 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < kH / 4; ++q) {
         float4 ww = w[q];
-        acc = fmaf(ww.x, h[4 * q], acc);
-        acc = fmaf(ww.y, h[4 * q + 1], acc);
-        acc = fmaf(ww.z, h[4 * q + 2], acc);
-        acc = fmaf(ww.w, h[4 * q + 3], acc);
+        acc[0] = fmaf(ww.x, h[4 * q], acc[0]);
+        acc[1] = fmaf(ww.y, h[4 * q + 1], acc[1]);
+        acc[2] = fmaf(ww.z, h[4 * q + 2], acc[2]);
+        acc[3] = fmaf(ww.w, h[4 * q + 3], acc[3]);
     }
-    return acc;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// shared layout of the decode kernels: W1 transposed [38][128], b1 [128],
+// W2 [n_out][32], b2 [n_out] (padded to 4)
+__device__ __forceinline__ void load_weights_T(const DecodeArgs &a, float *sW1T, float *sb1, float *sW2,
+                                               float *sb2) {
+    for (int i = threadIdx.x; i < kDin * 4 * kH; i += blockDim.x) {
+        const int ii = i / (4 * kH), h = i - ii * (4 * kH);
+        sW1T[i] = a.w1[h * kDin + ii];
+    }
+    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sb1[i] = a.b1[i];
+    for (int i = threadIdx.x; i < a.n_out * kH; i += blockDim.x) sW2[i] = a.w2[i];
+    for (int i = threadIdx.x; i < a.n_out; i += blockDim.x) sb2[i] = a.b2[i];
 }
 
 template <int NF>
@@ -127,8 +150,8 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
                                                     float *__restrict__ feat_out) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
-    float *sW1 = sm, *sb1 = sW1 + 4 * kH * kDinP, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + a.n_out * kH;
-    load_weights(a, sW1, sb1, sW2, sb2);
+    float *sW1T = sm, *sb1 = sW1T + kDin * 4 * kH, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + a.n_out * kH;
+    load_weights_T(a, sW1T, sb1, sW2, sb2);
     __syncthreads();
     const int K = a.K;
     const int rows = a.A * vt.n;
@@ -136,58 +159,60 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < rows; row += gridDim.x * blockDim.x) {
         const int v = row / a.A, an = row - v * a.A;
         const DevView &cam = vt.v[v];
-        float x[kDinP], delta[3], dist;
-        mlp_input(a, cam, an, x, delta, dist);
+        float xt[6];
+        {
+            float x[kDinP], delta[3], dist;
+            mlp_input(a, cam, an, x, delta, dist);
+#pragma unroll
+            for (int u = 0; u < 6; ++u) xt[u] = x[kFin + u];
+        }
+        const float *af = a.afeat + (size_t)an * kFin;
         float z[kH];
-        float op[kMaxK];
-        // opacity
-        hidden_pre(sW1, sb1, 0, x, z);
+        const size_t gbase = (size_t)v * NG + (size_t)an * K;
+        // opacity, and the mean
+        hidden_T(sW1T, sb1, 0, af, xt, z);
 #pragma unroll
         for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
-#pragma unroll 1
-        for (int k = 0; k < K; ++k) op[k] = sigm(out_row(sW2, sb2, k, z));
         const float px = a.pos[3 * an], py = a.pos[3 * an + 1], pz = a.pos[3 * an + 2];
-        const size_t gbase = (size_t)v * NG + (size_t)an * K;
-        // covariance: 3 scale + 4 quaternion per Gaussian, and the mean
-        hidden_pre(sW1, sb1, 1, x, z);
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            const float *o3 = a.offs + ((size_t)an * K + k) * 3;
+            mean_op[gbase + k] = make_float4(px + o3[0], py + o3[1], pz + o3[2], sigm(out_row(sW2, sb2, k, z)));
+        }
+        // covariance: 3 scale + 4 quaternion per Gaussian
+        hidden_T(sW1T, sb1, 1, af, xt, z);
 #pragma unroll
         for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
         const float lx = a.ascale[3 * an], ly = a.ascale[3 * an + 1], lz = a.ascale[3 * an + 2];
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
-            {
-                int r = K + 7 * k;
-                float s0 = lx * sigm(out_row(sW2, sb2, r, z));
-                float s1 = ly * sigm(out_row(sW2, sb2, r + 1, z));
-                float s2 = lz * sigm(out_row(sW2, sb2, r + 2, z));
-                float q0 = out_row(sW2, sb2, r + 3, z), q1 = out_row(sW2, sb2, r + 4, z);
-                float q2 = out_row(sW2, sb2, r + 5, z), q3 = out_row(sW2, sb2, r + 6, z);
-                const float *o3 = a.offs + ((size_t)an * K + k) * 3;
-                mean_op[gbase + k] = make_float4(px + o3[0], py + o3[1], pz + o3[2], op[k]);
-                scale_out[gbase + k] = make_float4(s0, s1, s2, 0.f);
-                quat_out[gbase + k] = make_float4(q0, q1, q2, q3);
-            }
+            const int r = K + 7 * k;
+            const float s0 = lx * sigm(out_row(sW2, sb2, r, z));
+            const float s1 = ly * sigm(out_row(sW2, sb2, r + 1, z));
+            const float s2 = lz * sigm(out_row(sW2, sb2, r + 2, z));
+            const float q0 = out_row(sW2, sb2, r + 3, z), q1 = out_row(sW2, sb2, r + 4, z);
+            const float q2 = out_row(sW2, sb2, r + 5, z), q3 = out_row(sW2, sb2, r + 6, z);
+            scale_out[gbase + k] = make_float4(s0, s1, s2, 0.f);
+            quat_out[gbase + k] = make_float4(q0, q1, q2, q3);
         }
         // colour
-        hidden_pre(sW1, sb1, 2, x, z);
+        hidden_T(sW1T, sb1, 2, af, xt, z);
 #pragma unroll
         for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
-            {
-                int r = 8 * K + 3 * k;
-                color_out[gbase + k] = make_float4(sigm(out_row(sW2, sb2, r, z)),
-                                                   sigm(out_row(sW2, sb2, r + 1, z)),
-                                                   sigm(out_row(sW2, sb2, r + 2, z)), 0.f);
-            }
+            const int r = 8 * K + 3 * k;
+            color_out[gbase + k] = make_float4(sigm(out_row(sW2, sb2, r, z)), sigm(out_row(sW2, sb2, r + 1, z)),
+                                               sigm(out_row(sW2, sb2, r + 2, z)), 0.f);
         }
         if (NF > 0) {
-            hidden_pre(sW1, sb1, 3, x, z);
+            hidden_T(sW1T, sb1, 3, af, xt, z);
 #pragma unroll
             for (int j = 0; j < kH; ++j) z[j] = softplus(z[j]);
+#pragma unroll 1
             for (int k = 0; k < K; ++k) {
                 float4 *dst = reinterpret_cast<float4 *>(feat_out + (gbase + k) * NF);
-                int r = 11 * K + NF * k;
+                const int r = 11 * K + NF * k;
 #pragma unroll
                 for (int c = 0; c < NF / 4; ++c)
                     dst[c] = make_float4(out_row(sW2, sb2, r + 4 * c, z), out_row(sW2, sb2, r + 4 * c + 1, z),
@@ -215,42 +240,8 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
     const int K = a.K;
     const bool want_mlp = a.s.X != nullptr && valid;
     const int ld = a.s.ld;
-    // Z = W1_g x + b1, input-outer so the 32 accumulators stay in registers;
-    // the anchor feature part of x is read through L1 (the rows of one anchor
-    // are adjacent lanes), the camera-dependent tail comes in registers
     float h[kH];
-#pragma unroll
-    for (int j = 0; j < kH; ++j) h[j] = sb1[G * kH + j];
-    const float4 *f4 = reinterpret_cast<const float4 *>(a.afeat + (size_t)an * kFin);
-#pragma unroll 1
-    for (int i4 = 0; i4 < kFin / 4; ++i4) {
-        const float4 xv = __ldg(f4 + i4);
-        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float4 *w = reinterpret_cast<const float4 *>(sW1T + (4 * i4 + u) * 128 + G * kH);
-#pragma unroll
-            for (int q = 0; q < kH / 4; ++q) {
-                const float4 ww = w[q];
-                h[4 * q] = fmaf(ww.x, xs[u], h[4 * q]);
-                h[4 * q + 1] = fmaf(ww.y, xs[u], h[4 * q + 1]);
-                h[4 * q + 2] = fmaf(ww.z, xs[u], h[4 * q + 2]);
-                h[4 * q + 3] = fmaf(ww.w, xs[u], h[4 * q + 3]);
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 6; ++u) {
-        const float4 *w = reinterpret_cast<const float4 *>(sW1T + (kFin + u) * 128 + G * kH);
-#pragma unroll
-        for (int q = 0; q < kH / 4; ++q) {
-            const float4 ww = w[q];
-            h[4 * q] = fmaf(ww.x, xt[u], h[4 * q]);
-            h[4 * q + 1] = fmaf(ww.y, xt[u], h[4 * q + 1]);
-            h[4 * q + 2] = fmaf(ww.z, xt[u], h[4 * q + 2]);
-            h[4 * q + 3] = fmaf(ww.w, xt[u], h[4 * q + 3]);
-        }
-    }
+    hidden_T(sW1T, sb1, G, a.afeat + (size_t)an * kFin, xt, h);
     unsigned relu_on = 0;  // ReLU derivative as a bit mask
 #pragma unroll
     for (int j = 0; j < kH; ++j) {
@@ -368,13 +359,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, 3) k_decode_bwd_rows(View
     // the per-row input gradients dx [36][128 rows]
     float *sW1T = sm, *sb1 = sW1T + kDin * 4 * kH, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + n_out * kH;
     float *sDXall = sb2 + ((n_out + 3) & ~3);
-    for (int i = threadIdx.x; i < kDin * 4 * kH; i += blockDim.x) {
-        const int ii = i / (4 * kH), h = i - ii * (4 * kH);
-        sW1T[i] = a.w1[h * kDin + ii];
-    }
-    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sb1[i] = a.b1[i];
-    for (int i = threadIdx.x; i < n_out * kH; i += blockDim.x) sW2[i] = a.w2[i];
-    for (int i = threadIdx.x; i < n_out; i += blockDim.x) sb2[i] = a.b2[i];
+    load_weights_T(da, sW1T, sb1, sW2, sb2);
     const int V = vt.n;
     for (int i = threadIdx.x; i < 3 * V; i += blockDim.x) aPose[i] = 0.f;
     __syncthreads();
@@ -417,7 +402,7 @@ size_t bwd_rows_smem(int n_out) {
     return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + ((n_out + 3) & ~3) + kDX * dbwd::kRowsPerBlock);
 }
 
-size_t fwd_smem(int n_out) { return sizeof(float) * (4 * kH * kDinP + 4 * kH + n_out * kH + n_out); }
+size_t fwd_smem(int n_out) { return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + n_out); }
 
 }  // namespace
 
