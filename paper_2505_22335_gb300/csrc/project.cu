@@ -453,7 +453,11 @@ __global__ void __launch_bounds__(256) k_project_bwd(
                 d_scale[gs] = make_float4(ds[0] + sreg, ds[1] + sreg, ds[2] + sreg, 0.f);
                 d_quat[gs] = make_float4(dq[0], dq[1], dq[2], dq[3]);
                 d_color[gs] = make_float4(rc.x, rc.y, rc.z, 0.f);
-                for (int c = 0; c < n_feat; ++c) d_feat[(size_t)gs * n_feat + c] = r[kG2Base + c];
+                // feature gradients as 16-byte moves (n_feat is a multiple of 4; the
+                // record's feature part starts 48 bytes into a 16-byte aligned record)
+                const float4 *rf = reinterpret_cast<const float4 *>(r + kG2Base);
+                float4 *df = reinterpret_cast<float4 *>(d_feat + (size_t)gs * n_feat);
+                for (int c = 0; c < n_feat / 4; ++c) df[c] = rf[c];
             } else {
                 float *dm = reinterpret_cast<float *>(d_mean_op + gs);
                 float *dsc = reinterpret_cast<float *>(d_scale + gs);
