@@ -260,19 +260,38 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
     for (int j = 0; j < kH; ++j) dh[j] = 0.f;
     const int r0 = dbwd::grp_r0(G, K);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // dL/dG of Gaussian k for this group, loaded one Gaussian ahead so the
+    // loads of k + 1 are in flight while k is processed
+    constexpr int NQ = G == 3 ? (NF / 4 > 0 ? NF / 4 : 1) : 2;
+    constexpr bool kAhead = NQ <= 4;
+    auto load = [&](int k, float4 (&q)[NQ]) {
+        const size_t gi = gbase + k;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) q[i] = z4;
+        if (!valid || k >= K) return;
+        if (G == 0) q[0] = a.d_mean_op[gi];
+        if (G == 1) {
+            q[0] = a.d_scale[gi];
+            q[1] = a.d_quat[gi];
+        }
+        if (G == 2) q[0] = a.d_color[gi];
+        if (G == 3)
+#pragma unroll
+            for (int i = 0; i < NF / 4; ++i) q[i] = reinterpret_cast<const float4 *>(a.d_feat + gi * NF)[i];
+    };
+    float4 nxt[NQ];
+    if (kAhead) load(0, nxt);
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-        const size_t gi = gbase + k;
-        float4 g4a = z4, g4b = z4;
-        if (valid) {
-            if (G == 0) g4a = a.d_mean_op[gi];
-            if (G == 1) {
-                g4a = a.d_scale[gi];
-                g4b = a.d_quat[gi];
-            }
-            if (G == 2) g4a = a.d_color[gi];
+        float4 cur[NQ];
+        if (kAhead) {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) cur[i] = nxt[i];
+            load(k + 1, nxt);
+        } else {
+            load(k, cur);
         }
-        float4 f4 = z4;
+        const float4 g4a = cur[0], g4b = cur[NQ > 1 ? 1 : 0];
 #pragma unroll
         for (int c = 0; c < M; ++c) {
             const int o = r0 + M * k + c;
@@ -286,7 +305,7 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
             } else if (G == 2) {
                 gin = c == 0 ? g4a.x : c == 1 ? g4a.y : g4a.z;
             } else {
-                if ((c & 3) == 0 && valid) f4 = reinterpret_cast<const float4 *>(a.d_feat + gi * NF)[c >> 2];
+                const float4 f4 = cur[(c >> 2) < NQ ? (c >> 2) : 0];
                 gin = (c & 3) == 0 ? f4.x : (c & 3) == 1 ? f4.y : (c & 3) == 2 ? f4.z : f4.w;
             }
             float dy = gin;
