@@ -52,8 +52,8 @@ def load_peaks():
         with open(p) as f:
             d = json.load(f)
         return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
-                    source="measured")
-    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+                    bf16_tflops_sustained=float(d.get("bf16_tflops_sustained", 1700.0)), source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, bf16_tflops_sustained=1700.0, source="fallback")
 
 
 # ---------------------------------------------------------------------------
@@ -232,7 +232,7 @@ ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
 # DRAM bytes (read + write) per launch from one ncu capture of the named kernel on the named
 # workload (profiles/launches_mapping_100k_anchors_x10_8x640x480.md); reported as the roofline's
 # `traffic` only for that kernel and workload.  Re-measure whenever the kernel changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("composite_bwd", "mapping_100k_anchors_x10_8x640x480"): 304.6e6}
 
 
 def run_ours(args, wl_name):
@@ -295,8 +295,7 @@ def run_ours(args, wl_name):
         stages = {k: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
                   for k, v in prof.items()}
         dom = max(prof, key=lambda k: prof[k][0])
-        avg_ms = prof[dom][0] / prof[dom][1]
-        roof = roofline(dom, alg, avg_ms, peaks)
+        roof = roofline(dom, alg, prof[dom][0] / args.steps, prof[dom][1] / args.steps, peaks, args.decode_bf16)
         roof["traffic"] = MEASURED_TRAFFIC.get((dom, wl_name))
         cpu = cpu_baseline(wl, anc, mlp, cams, tg) if not args.no_cpu else None
         line = {
@@ -326,19 +325,28 @@ def run_ours(args, wl_name):
         dist.destroy_process_group()
 
 
-def roofline(stage, alg, avg_ms, peaks):
+def roofline(stage, alg, stage_ms, launches, peaks, bf16=False):
+    """Roofline of one stage: its algorithmic work per step over its time per step
+    (stages of several launches, e.g. chunked decode backward, are taken whole)."""
     a = alg.get(stage, {})
+    common = dict(kernel=stage, traffic=None, stage_ms=round(stage_ms, 4),
+                  avg_launch_ms=round(stage_ms / max(launches, 1), 4), algorithmic_bytes=a.get("bytes"))
+    if bf16 and stage in ("decode_fwd", "decode_bwd_rows") and "flops" in a:
+        # BF16 operands on the tcgen05 tensor cores; timed inside a long step
+        peak = peaks["bf16_tflops_sustained"]
+        ach = a["flops"] / (stage_ms / 1e3) / 1e12
+        return dict(common, bound="tensor", achieved=round(ach, 3), peak=round(peak, 1), unit="TFLOP/s",
+                    frac=round(ach / peak, 4), peak_source=peaks["source"] + " (bf16, sustained)",
+                    algorithmic_flops=a["flops"])
     if stage in ALU_STAGES and "flops" in a:
         peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
-        ach = a["flops"] / (avg_ms / 1e3) / 1e12
-        return dict(kernel=stage, bound="alu", achieved=round(ach, 3), peak=round(peak, 2), unit="TFLOP/s",
-                    frac=round(ach / peak, 4), traffic=None, peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                    avg_launch_ms=round(avg_ms, 4), algorithmic_flops=a["flops"],
-                    algorithmic_bytes=a.get("bytes"))
-    ach = a.get("bytes", 0) / (avg_ms / 1e3) / 1e9
-    return dict(kernel=stage, bound="hbm", achieved=round(ach, 1), peak=peaks["hbm_gbs"], unit="GB/s",
-                frac=round(ach / peaks["hbm_gbs"], 4), traffic=None,
-                peak_source=peaks["source"], avg_launch_ms=round(avg_ms, 4), algorithmic_bytes=a.get("bytes"))
+        ach = a["flops"] / (stage_ms / 1e3) / 1e12
+        return dict(common, bound="alu", achieved=round(ach, 3), peak=round(peak, 2), unit="TFLOP/s",
+                    frac=round(ach / peak, 4), peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    algorithmic_flops=a["flops"])
+    ach = a.get("bytes", 0) / (stage_ms / 1e3) / 1e9
+    return dict(common, bound="hbm", achieved=round(ach, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=round(ach / peaks["hbm_gbs"], 4), peak_source=peaks["source"])
 
 
 def run_e2e(args, st, anc, mlp, tg, world):
