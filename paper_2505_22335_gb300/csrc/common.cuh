@@ -76,6 +76,15 @@ cudaError_t radix_sort_u32(uint32_t **key_io, uint32_t **key_alt, uint32_t **val
 cudaError_t radix_sort_u64(uint64_t **key_io, uint64_t **key_alt, uint32_t **val_io,
                            uint32_t **val_alt, size_t n, int end_bit, SortScratch &s,
                            cudaStream_t st);
+// One-pass stable sort of (key, value) pairs by keys < nbins <= kMaxBucketBins
+// (tile ids): writes the values in key order to vals_out and the [start, end)
+// range of every key to ranges[nbins].  scratch: bucket_sort_scratch_bytes.
+constexpr int kMaxBucketBins = 1 << 14;
+size_t bucket_sort_scratch_bytes(size_t n, int nbins, int num_sms);
+cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t *vals_out, size_t n, int nbins,
+                            uint2 *ranges, void *scratch, size_t scratch_bytes, int num_sms, cudaStream_t st);
+// keys[i] = t for every i in ranges[t] (the sorted keys of a bucket sort)
+cudaError_t keys_from_ranges(const uint2 *ranges, int nbins, uint32_t *keys, cudaStream_t st);
 // Exclusive scan of n uint32 into uint64 (out has n+1 entries; out[n] = total).
 size_t scan_scratch_bytes(size_t n);
 cudaError_t exclusive_scan_u32_u64(const uint32_t *in, uint64_t *out, size_t n, void *scratch,

@@ -489,17 +489,29 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     // stable bucket by (view, tile): depth order is kept inside each tile
     c->key_bits = bits_for((size_t)vt.total_tiles);
     stage_begin(c, "tile_sort", st);
-    UPS_CUDA(c, radix_sort_u32(&ik, &ik_alt, &iv, &iv_alt, n_inst, c->key_bits, c->sort, st));
-    stage_end(c, st, radix_kernels(n_inst, c->key_bits));
-    c->ikey_sorted = ik;
-    c->ival_sorted = iv;
-    stage_begin(c, "ranges", st);
-    UPS_CUDA(c, cudaMemsetAsync(c->ranges.ptr, 0, (size_t)vt.total_tiles * sizeof(uint2), st));
-    UPS_CUDA(c, launch_ranges(ik, (uint32_t)n_inst, c->ranges.as<uint2>(), st));
-    stage_end(c, st, n_inst ? 1 : 0);
+    if (vt.total_tiles <= kMaxBucketBins) {
+        // one pass: values in tile order and the tile ranges; the sorted keys
+        // are only rebuilt (from the ranges) when inspected
+        const size_t need = bucket_sort_scratch_bytes(n_inst, vt.total_tiles, c->num_sms);
+        UPS_CUDA(c, c->sort.hist.reserve(std::max<size_t>(need, 256)));
+        UPS_CUDA(c, bucket_sort_u32(ik, iv, iv_alt, n_inst, vt.total_tiles, c->ranges.as<uint2>(), c->sort.hist.ptr,
+                                    c->sort.hist.bytes, c->num_sms, st));
+        stage_end(c, st, n_inst ? 6 : 0);
+        c->ikey_sorted = nullptr;
+        c->ival_sorted = iv_alt;
+    } else {
+        UPS_CUDA(c, radix_sort_u32(&ik, &ik_alt, &iv, &iv_alt, n_inst, c->key_bits, c->sort, st));
+        stage_end(c, st, radix_kernels(n_inst, c->key_bits));
+        c->ikey_sorted = ik;
+        c->ival_sorted = iv;
+        stage_begin(c, "ranges", st);
+        UPS_CUDA(c, cudaMemsetAsync(c->ranges.ptr, 0, (size_t)vt.total_tiles * sizeof(uint2), st));
+        UPS_CUDA(c, launch_ranges(ik, (uint32_t)n_inst, c->ranges.as<uint2>(), st));
+        stage_end(c, st, n_inst ? 1 : 0);
+    }
     stage_begin(c, "composite_fwd", st);
     UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
-                                     iv, c->xyzo.as<float4>(), c->conic.as<float4>(),
+                                     c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                      reinterpret_cast<const float4 *>(g->color), g->feat, *out, st));
     stage_end(c, st, 1);
     c->g_in = *g;
@@ -658,7 +670,16 @@ ups_status ups_copy_buffer(ups_ctx *c, int which, void *dst, size_t bytes, size_
     size_t sz = 0;
     switch (which) {
         case 0: src = c->ival_sorted; sz = c->n_inst * 4; break;
-        case 1: src = c->ikey_sorted; sz = c->n_inst * 4; break;
+        case 1:
+            sz = c->n_inst * 4;
+            if (!c->ikey_sorted && sz) {
+                UPS_CUDA(c, cudaSetDevice(c->device));
+                UPS_CUDA(c, keys_from_ranges(c->ranges.as<uint2>(), c->vt.total_tiles, c->ikey1.as<uint32_t>(),
+                                             c->last_stream));
+                c->ikey_sorted = c->ikey1.as<uint32_t>();
+            }
+            src = c->ikey_sorted;
+            break;
         case 2: src = c->ranges.ptr; sz = (size_t)c->vt.total_tiles * 8; break;
         case 3: src = c->xyzo.ptr; sz = c->total_gv * 16; break;
         case 4: src = c->conic.ptr; sz = c->total_gv * 16; break;

@@ -6,6 +6,8 @@
 // One pass = histogram kernel (per-block digit counts, digit-major layout) +
 // exclusive scan of the counts + scatter kernel (stable block-local ranking by
 // ballots, then a scatter to the scanned offsets).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ups {
@@ -332,7 +334,285 @@ cudaError_t radix_fixed(K **key_io, K **key_alt, uint32_t **val_io, uint32_t **v
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// one-pass stable bucket sort by small keys (tile ids)
+// ---------------------------------------------------------------------------
+//
+// Keys are < nbins <= 2^14.  The input is split into nblocks contiguous runs
+// of per_block items (a multiple of the 2048-item sub-tile).  (1) each block
+// counts its keys per bucket; (2) an exclusive scan of the counts in
+// (bucket, block) order gives every (bucket, block) pair its first output
+// slot and every bucket its [start, end) range; (3) each block walks its run
+// in sub-tiles: a stable two-pass (7 + 7 bit) sort of the sub-tile in shared
+// memory groups equal keys, and item i of a group goes to next[bucket] +
+// (i - group start), after which next[bucket] moves past the group.  Only
+// the values are written: the sorted keys follow from the ranges.
+
+constexpr int kBkThreads = 256;
+constexpr int kBkWarps = kBkThreads / 32;
+constexpr int kBkItems = 8;
+constexpr int kBkSub = kBkThreads * kBkItems;  // items per sub-tile
+constexpr int kBkDigit = 7;                    // bits per in-block pass
+constexpr int kBkLocal = 1 << kBkDigit;
+constexpr int kBkHistThreads = 512;
+constexpr uint32_t kBkPad = kMaxBucketBins - 1;  // digit of the empty slots of a partial sub-tile
+
+__host__ __device__ inline int bk_nbp(int nbins) { return (nbins + 3) & ~3; }
+size_t bk_scatter_smem(int nbins) {
+    return (size_t)bk_nbp(nbins) * 4 + kBkSub * (2 + 4) + (kBkWarps + 1) * kBkLocal * 4 + 64;
+}
+
+__global__ void __launch_bounds__(kBkHistThreads) k_bucket_hist(const uint32_t *__restrict__ keys, size_t n,
+                                                                int nbins, size_t per_block,
+                                                                uint32_t *__restrict__ hist, int nblocks) {
+    extern __shared__ uint32_t h[];
+    for (int d = threadIdx.x; d < nbins; d += kBkHistThreads) h[d] = 0;
+    __syncthreads();
+    const size_t beg = (size_t)blockIdx.x * per_block;
+    const size_t end = min(n, beg + per_block);
+    const uint32_t top = (uint32_t)nbins - 1;
+    // beg is a multiple of 2048 items: 16-byte loads up to the last full quad
+    const size_t nq = (end - beg) / 4;
+    const uint4 *q4 = reinterpret_cast<const uint4 *>(keys + beg);
+    for (size_t i = threadIdx.x; i < nq; i += kBkHistThreads) {
+        const uint4 k = q4[i];
+        atomicAdd(&h[min(k.x, top)], 1u);
+        atomicAdd(&h[min(k.y, top)], 1u);
+        atomicAdd(&h[min(k.z, top)], 1u);
+        atomicAdd(&h[min(k.w, top)], 1u);
+    }
+    for (size_t i = beg + 4 * nq + threadIdx.x; i < end; i += kBkHistThreads) atomicAdd(&h[min(keys[i], top)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < nbins; d += kBkHistThreads) hist[(size_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+__global__ void k_bucket_ranges(const uint32_t *__restrict__ offs, int nbins, int nblocks, uint32_t n,
+                                uint2 *__restrict__ ranges) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < nbins)
+        ranges[d] = make_uint2(offs[(size_t)d * nblocks], d + 1 < nbins ? offs[(size_t)(d + 1) * nblocks] : n);
+}
+
+// One stable counting pass over the 7-bit digit (d >> shift) & 127 of the
+// sub-tile's items, held in registers in sub-tile order (item w*256 + j*32 +
+// lane); writes them to (od, ov) in digit order.  (od, ov) may be the buffer
+// the items were read from: the block syncs before the first write.  Ends
+// with the block synced.
+__device__ __forceinline__ void bk_local_pass(const uint32_t (&d)[kBkItems], const uint32_t (&v)[kBkItems],
+                                              int shift, uint16_t *od, uint32_t *ov, uint32_t *wc,
+                                              uint32_t *dstart) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t *mine = wc + w * kBkLocal;
+#pragma unroll
+    for (int b = lane; b < kBkLocal; b += 32) mine[b] = 0u;
+    __syncwarp();
+    uint32_t rank[kBkItems];
+#pragma unroll
+    for (int j = 0; j < kBkItems; ++j) {
+        const uint32_t b = (d[j] >> shift) & (kBkLocal - 1);
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const uint32_t lt = __popc(peers & lt_mask);
+        const uint32_t prior = mine[b];
+        __syncwarp();
+        if (lt == 0) mine[b] = prior + __popc(peers);
+        __syncwarp();
+        rank[j] = prior + lt;
+    }
+    __syncthreads();
+    // exclusive offsets in (digit, warp) order
+    if (tid < kBkLocal) {
+        uint32_t r = 0;
+#pragma unroll
+        for (int ww = 0; ww < kBkWarps; ++ww) {
+            const uint32_t c = wc[ww * kBkLocal + tid];
+            wc[ww * kBkLocal + tid] = r;
+            r += c;
+        }
+        dstart[tid] = r;
+    }
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t[kBkLocal / 32], sum = 0;
+#pragma unroll
+        for (int i = 0; i < kBkLocal / 32; ++i) {
+            t[i] = dstart[(kBkLocal / 32) * lane + i];
+            sum += t[i];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < kBkLocal / 32; ++i) {
+            dstart[(kBkLocal / 32) * lane + i] = run;
+            run += t[i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBkItems; ++j) {
+        const uint32_t b = (d[j] >> shift) & (kBkLocal - 1);
+        const uint32_t pos = dstart[b] + wc[w * kBkLocal + b] + rank[j];
+        od[pos] = (uint16_t)d[j];
+        ov[pos] = v[j];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBkThreads, 3) k_bucket_scatter(const uint32_t *__restrict__ keys,
+                                                                  const uint32_t *__restrict__ vals,
+                                                                  uint32_t *__restrict__ vout, size_t n, int nbins,
+                                                                  size_t per_block,
+                                                                  const uint32_t *__restrict__ offs, int nblocks) {
+    extern __shared__ __align__(16) unsigned char bk_smem[];
+    const int nbp = bk_nbp(nbins);
+    // next[b]: next output slot of bucket b; while a sub-tile is written, the
+    // head of b's group rebases it to next[b] - (group start), so that item i
+    // of the group goes to next[b] + i
+    uint32_t *next = reinterpret_cast<uint32_t *>(bk_smem);
+    uint16_t *sd = reinterpret_cast<uint16_t *>(next + nbp);    // [kBkSub] digits
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sd + kBkSub);    // [kBkSub] values
+    uint32_t *wc = sv + kBkSub;                                 // [kBkWarps][kBkLocal]
+    uint32_t *dstart = wc + kBkWarps * kBkLocal;                // [kBkLocal]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int d = tid; d < nbins; d += kBkThreads) next[d] = offs[(size_t)d * nblocks + blockIdx.x];
+    const size_t beg = (size_t)blockIdx.x * per_block;
+    const size_t end = min(n, beg + per_block);
+    const uint32_t top = (uint32_t)nbins - 1;
+    const int slot0 = w * (32 * kBkItems) + lane;  // item j of this thread: slot0 + 32 j
+    // raw loads of the next sub-tile stay in flight while this one is sorted
+    uint32_t key[kBkItems], val[kBkItems];
+    auto load = [&](size_t s0) {
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            const size_t idx = s0 + (size_t)(slot0 + j * 32);
+            if (idx < end) {
+                key[j] = keys[idx];
+                val[j] = vals[idx];
+            }
+        }
+    };
+    if (beg < end) load(beg);
+    for (size_t s0 = beg; s0 < end; s0 += kBkSub) {
+        const int nvalid = (int)min((size_t)kBkSub, end - s0);
+        uint32_t d[kBkItems], v[kBkItems];
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            // the empty slots of a partial sub-tile sort behind every key
+            const bool ok = slot0 + j * 32 < nvalid;
+            d[j] = ok ? min(key[j], top) : kBkPad;
+            v[j] = val[j];
+        }
+        if (s0 + kBkSub < end) load(s0 + kBkSub);
+        // low then high 7 bits: the sub-tile ends grouped by key in (sd, sv)
+        bk_local_pass(d, v, 0, sd, sv, wc, dstart);
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            d[j] = sd[slot0 + j * 32];
+            v[j] = sv[slot0 + j * 32];
+        }
+        bk_local_pass(d, v, kBkDigit, sd, sv, wc, dstart);
+        // group heads rebase the bucket fronts, every item is written, then
+        // the group tails move the fronts past their groups
+#pragma unroll
+        for (int k = 0; k < kBkItems; ++k) {
+            const int i = tid + k * kBkThreads;
+            if (i < nvalid) {
+                const uint32_t dd = sd[i];
+                if (i == 0 || sd[i - 1] != dd) next[dd] -= (uint32_t)i;
+            }
+        }
+        __syncthreads();
+        uint32_t front[kBkItems];
+#pragma unroll
+        for (int k = 0; k < kBkItems; ++k) {
+            const int i = tid + k * kBkThreads;
+            front[k] = 0u;
+            if (i < nvalid) {
+                const uint32_t dd = sd[i];
+                const uint32_t base = next[dd];
+                vout[base + (uint32_t)i] = sv[i];
+                if (i == nvalid - 1 || sd[i + 1] != dd) front[k] = base + (uint32_t)i + 1u;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kBkItems; ++k) {
+            const int i = tid + k * kBkThreads;
+            if (i < nvalid && (i == nvalid - 1 || sd[i + 1] != sd[i])) next[sd[i]] = front[k];
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+size_t bucket_sort_scratch_bytes(size_t n, int nbins, int num_sms) {
+    if (n == 0 || nbins <= 0) return 0;
+    const size_t nblocks = std::min<size_t>((n + kBkSub - 1) / kBkSub, (size_t)std::max(num_sms, 1) * 4);
+    const size_t hist_n = (size_t)nbins * nblocks;
+    return ((hist_n * 4 + 255) & ~size_t(255)) + scan_scratch_bytes(hist_n);
+}
+
+cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t *vals_out, size_t n, int nbins,
+                            uint2 *ranges, void *scratch, size_t scratch_bytes, int num_sms, cudaStream_t st) {
+    if (nbins <= 0 || nbins > kMaxBucketBins) return cudaErrorInvalidValue;
+    if (n == 0) return cudaMemsetAsync(ranges, 0, (size_t)nbins * sizeof(uint2), st);
+    if (n >= (size_t)UINT32_MAX) return cudaErrorInvalidValue;
+    const size_t smem = bk_scatter_smem(nbins);
+    static thread_local int attr_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bk_scatter_smem(kMaxBucketBins));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxBucketBins * 4);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    int occ = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_scatter, kBkThreads, smem);
+    if (e != cudaSuccess) return e;
+    occ = std::max(1, std::min(occ, 4));
+    // one wave: at most num_sms * occupancy blocks, each a run of whole sub-tiles
+    const size_t subs = (n + kBkSub - 1) / kBkSub;
+    size_t nblocks = std::min(subs, (size_t)std::max(num_sms, 1) * occ);
+    const size_t per_block = ((subs + nblocks - 1) / nblocks) * kBkSub;
+    nblocks = (n + per_block - 1) / per_block;
+    const size_t hist_n = (size_t)nbins * nblocks;
+    const size_t hist_bytes = (hist_n * 4 + 255) & ~size_t(255);
+    if (hist_bytes + scan_scratch_bytes(hist_n) > scratch_bytes) return cudaErrorInvalidValue;
+    uint32_t *hist = static_cast<uint32_t *>(scratch);
+    void *scr = static_cast<char *>(scratch) + hist_bytes;
+    k_bucket_hist<<<(int)nblocks, kBkHistThreads, (size_t)nbins * 4, st>>>(keys, n, nbins, per_block, hist,
+                                                                           (int)nblocks);
+    e = scan_impl<uint32_t>(hist, hist, hist_n, scr, 0, st);
+    if (e != cudaSuccess) return e;
+    k_bucket_ranges<<<(nbins + 255) / 256, 256, 0, st>>>(hist, nbins, (int)nblocks, (uint32_t)n, ranges);
+    k_bucket_scatter<<<(int)nblocks, kBkThreads, smem, st>>>(keys, vals, vals_out, n, nbins, per_block, hist,
+                                                             (int)nblocks);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_keys_from_ranges(const uint2 *__restrict__ ranges, uint32_t *__restrict__ keys) {
+    const uint2 r = ranges[blockIdx.x];
+    for (uint32_t i = r.x + threadIdx.x; i < r.y; i += blockDim.x) keys[i] = blockIdx.x;
+}
+}  // namespace
+
+cudaError_t keys_from_ranges(const uint2 *ranges, int nbins, uint32_t *keys, cudaStream_t st) {
+    if (nbins <= 0) return cudaSuccess;
+    k_keys_from_ranges<<<nbins, 256, 0, st>>>(ranges, keys);
+    return cudaGetLastError();
+}
 
 cudaError_t radix_sort_u32_fixed(uint32_t **key_io, uint32_t **key_alt, uint32_t **val_io,
                                  uint32_t **val_alt, size_t n, int end_bit, void *scratch,
