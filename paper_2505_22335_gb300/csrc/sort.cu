@@ -411,7 +411,15 @@ __device__ __forceinline__ void bk_local_pass(const uint32_t (&d)[kBkItems], con
 #pragma unroll
     for (int j = 0; j < kBkItems; ++j) {
         const uint32_t b = (d[j] >> shift) & (kBkLocal - 1);
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        // lanes holding the same digit, one ballot per bit (a warp match.any
+        // costs several times the seven ballots on this GPU)
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < kBkDigit; ++bit) {
+            const uint32_t x = (b >> bit) & 1u;
+            const uint32_t bb = __ballot_sync(0xffffffffu, x);
+            peers &= x ? bb : ~bb;
+        }
         const uint32_t lt = __popc(peers & lt_mask);
         const uint32_t prior = mine[b];
         __syncwarp();
