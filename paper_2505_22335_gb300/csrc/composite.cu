@@ -21,29 +21,6 @@ namespace {
 
 constexpr int kBatch = 256;
 
-// Packed pairs of f32 (first element in the low half) for fma.rn.f32x2: two
-// channels per instruction, each rounded exactly as a scalar fmaf.
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 f2_make(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ float f2_lo(f2 a) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2 a) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-    return hi;
-}
 // channels [c, c + 4) of staged Gaussian j as two pairs
 template <int NF, class St>
 __device__ __forceinline__ ulonglong2 feat4(const St &S, int j, int c) {

@@ -72,15 +72,18 @@ __device__ __forceinline__ void mlp_input(const DecodeArgs &a, const DevView &ca
     x[39] = 0.f;
 }
 
-// hidden block g: z = W1_g x + b1_g (32 values), input-outer so the 32
-// accumulators stay in registers.  W1 is transposed in shared memory
-// ([38][128]: input-major); the anchor-feature part of x is read through L1
-// (rows of the same anchor share it), the camera-dependent tail x[32..37]
-// comes in registers.
+// hidden block g: z = W1_g x + b1_g (32 values, held as 16 packed pairs
+// (z_2p, z_2p+1) for fma.rn.f32x2), input-outer so the accumulators stay in
+// registers.  W1 is transposed in shared memory ([38][128]: input-major); the
+// anchor-feature part of x is read through L1 (rows of the same anchor share
+// it), the camera-dependent tail x[32..37] comes in registers.  Each element
+// is rounded exactly as a scalar fmaf chain over the inputs in order.
+constexpr int kH2 = kH / 2;
 __device__ __forceinline__ void hidden_T(const float *sW1T, const float *sb1, int g, const float *afeat_row,
-                                         const float xt[6], float h[kH]) {
+                                         const float xt[6], f2 h[kH2]) {
+    const f2 *b2 = reinterpret_cast<const f2 *>(sb1 + g * kH);
 #pragma unroll
-    for (int j = 0; j < kH; ++j) h[j] = sb1[g * kH + j];
+    for (int p = 0; p < kH2; ++p) h[p] = b2[p];
     const float4 *f4 = reinterpret_cast<const float4 *>(afeat_row);
 #pragma unroll 1
     for (int i4 = 0; i4 < kFin / 4; ++i4) {
@@ -88,44 +91,56 @@ __device__ __forceinline__ void hidden_T(const float *sW1T, const float *sb1, in
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float4 *w = reinterpret_cast<const float4 *>(sW1T + (4 * i4 + u) * 128 + g * kH);
+            const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(sW1T + (4 * i4 + u) * 128 + g * kH);
+            const f2 xx = f2_make(xs[u], xs[u]);
 #pragma unroll
             for (int q = 0; q < kH / 4; ++q) {
-                const float4 ww = w[q];
-                h[4 * q] = fmaf(ww.x, xs[u], h[4 * q]);
-                h[4 * q + 1] = fmaf(ww.y, xs[u], h[4 * q + 1]);
-                h[4 * q + 2] = fmaf(ww.z, xs[u], h[4 * q + 2]);
-                h[4 * q + 3] = fmaf(ww.w, xs[u], h[4 * q + 3]);
+                const ulonglong2 ww = w[q];
+                h[2 * q] = f2_fma(ww.x, xx, h[2 * q]);
+                h[2 * q + 1] = f2_fma(ww.y, xx, h[2 * q + 1]);
             }
         }
     }
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
-        const float4 *w = reinterpret_cast<const float4 *>(sW1T + (kFin + u) * 128 + g * kH);
+        const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(sW1T + (kFin + u) * 128 + g * kH);
+        const f2 xx = f2_make(xt[u], xt[u]);
 #pragma unroll
         for (int q = 0; q < kH / 4; ++q) {
-            const float4 ww = w[q];
-            h[4 * q] = fmaf(ww.x, xt[u], h[4 * q]);
-            h[4 * q + 1] = fmaf(ww.y, xt[u], h[4 * q + 1]);
-            h[4 * q + 2] = fmaf(ww.z, xt[u], h[4 * q + 2]);
-            h[4 * q + 3] = fmaf(ww.w, xt[u], h[4 * q + 3]);
+            const ulonglong2 ww = w[q];
+            h[2 * q] = f2_fma(ww.x, xx, h[2 * q]);
+            h[2 * q + 1] = f2_fma(ww.y, xx, h[2 * q + 1]);
         }
     }
 }
 
-// y_r = W2[r] . h + b2[r] with four partial sums (short dependency chains)
-__device__ __forceinline__ float out_row(const float *sW2, const float *sb2, int r, const float h[kH]) {
-    const float4 *w = reinterpret_cast<const float4 *>(sW2 + r * kH);
-    float acc[4] = {sb2[r], 0.f, 0.f, 0.f};
+// element-wise activation of the packed hidden values: ReLU (act 0) or
+// SoftPlus (act 1)
+template <int ACT>
+__device__ __forceinline__ void activate(f2 h[kH2]) {
+#pragma unroll
+    for (int p = 0; p < kH2; ++p) {
+        float lo, hi;
+        f2_split(h[p], lo, hi);
+        h[p] = ACT == 0 ? f2_make(fmaxf(lo, 0.f), fmaxf(hi, 0.f)) : f2_make(softplus(lo), softplus(hi));
+    }
+}
+
+// y_r = W2[r] . h + b2[r] with four partial sums (short dependency chains):
+// the pairs (s0, s1) and (s2, s3) of the scalar form, summed (s0+s1)+(s2+s3)
+__device__ __forceinline__ float out_row(const float *sW2, const float *sb2, int r, const f2 h[kH2]) {
+    const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(sW2 + r * kH);
+    f2 a01 = f2_make(sb2[r], 0.f), a23 = 0ull;
 #pragma unroll
     for (int q = 0; q < kH / 4; ++q) {
-        float4 ww = w[q];
-        acc[0] = fmaf(ww.x, h[4 * q], acc[0]);
-        acc[1] = fmaf(ww.y, h[4 * q + 1], acc[1]);
-        acc[2] = fmaf(ww.z, h[4 * q + 2], acc[2]);
-        acc[3] = fmaf(ww.w, h[4 * q + 3], acc[3]);
+        const ulonglong2 ww = w[q];
+        a01 = f2_fma(ww.x, h[2 * q], a01);
+        a23 = f2_fma(ww.y, h[2 * q + 1], a23);
     }
-    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    float s0, s1, s2, s3;
+    f2_split(a01, s0, s1);
+    f2_split(a23, s2, s3);
+    return (s0 + s1) + (s2 + s3);
 }
 
 // shared layout of the decode kernels: W1 transposed [38][128], b1 [128],
@@ -167,12 +182,11 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
             for (int u = 0; u < 6; ++u) xt[u] = x[kFin + u];
         }
         const float *af = a.afeat + (size_t)an * kFin;
-        float z[kH];
+        f2 z[kH2];
         const size_t gbase = (size_t)v * NG + (size_t)an * K;
         // opacity, and the mean
         hidden_T(sW1T, sb1, 0, af, xt, z);
-#pragma unroll
-        for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
+        activate<0>(z);
         const float px = a.pos[3 * an], py = a.pos[3 * an + 1], pz = a.pos[3 * an + 2];
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
@@ -181,8 +195,7 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
         }
         // covariance: 3 scale + 4 quaternion per Gaussian
         hidden_T(sW1T, sb1, 1, af, xt, z);
-#pragma unroll
-        for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
+        activate<0>(z);
         const float lx = a.ascale[3 * an], ly = a.ascale[3 * an + 1], lz = a.ascale[3 * an + 2];
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
@@ -197,8 +210,7 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
         }
         // colour
         hidden_T(sW1T, sb1, 2, af, xt, z);
-#pragma unroll
-        for (int j = 0; j < kH; ++j) z[j] = fmaxf(z[j], 0.f);
+        activate<0>(z);
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
             const int r = 8 * K + 3 * k;
@@ -207,8 +219,7 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
         }
         if (NF > 0) {
             hidden_T(sW1T, sb1, 3, af, xt, z);
-#pragma unroll
-            for (int j = 0; j < kH; ++j) z[j] = softplus(z[j]);
+            activate<1>(z);
 #pragma unroll 1
             for (int k = 0; k < K; ++k) {
                 float4 *dst = reinterpret_cast<float4 *>(feat_out + (gbase + k) * NF);
@@ -240,24 +251,32 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
     const int K = a.K;
     const bool want_mlp = a.s.X != nullptr && valid;
     const int ld = a.s.ld;
-    float h[kH];
+    f2 h[kH2];
     hidden_T(sW1T, sb1, G, a.afeat + (size_t)an * kFin, xt, h);
     unsigned relu_on = 0;  // ReLU derivative as a bit mask
 #pragma unroll
-    for (int j = 0; j < kH; ++j) {
+    for (int p = 0; p < kH2; ++p) {
+        float lo, hi;
+        f2_split(h[p], lo, hi);
         if (G < 3) {
-            relu_on |= (h[j] > 0.f ? 1u : 0u) << j;
-            h[j] = fmaxf(h[j], 0.f);
+            relu_on |= (lo > 0.f ? 1u : 0u) << (2 * p);
+            relu_on |= (hi > 0.f ? 1u : 0u) << (2 * p + 1);
+            h[p] = f2_make(fmaxf(lo, 0.f), fmaxf(hi, 0.f));
         } else {
-            h[j] = softplus(h[j]);
+            h[p] = f2_make(softplus(lo), softplus(hi));
         }
     }
     if (want_mlp)
 #pragma unroll
-        for (int j = 0; j < kH; ++j) a.s.H[(size_t)(G * kH + j) * ld + lr] = h[j];
-    float dh[kH];
+        for (int p = 0; p < kH2; ++p) {
+            float lo, hi;
+            f2_split(h[p], lo, hi);
+            a.s.H[(size_t)(G * kH + 2 * p) * ld + lr] = lo;
+            a.s.H[(size_t)(G * kH + 2 * p + 1) * ld + lr] = hi;
+        }
+    f2 dh[kH2];
 #pragma unroll
-    for (int j = 0; j < kH; ++j) dh[j] = 0.f;
+    for (int p = 0; p < kH2; ++p) dh[p] = 0ull;
     const int r0 = dbwd::grp_r0(G, K);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     // dL/dG of Gaussian k for this group, loaded one Gaussian ahead so the
@@ -310,18 +329,7 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
             }
             float dy = gin;
             if (nl) {
-                // Y_o with four partial sums (short dependency chains)
-                const float4 *w = reinterpret_cast<const float4 *>(sW2 + o * kH);
-                float y4[4] = {sb2[o], 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int q = 0; q < kH / 4; ++q) {
-                    const float4 ww = w[q];
-                    y4[0] = fmaf(ww.x, h[4 * q], y4[0]);
-                    y4[1] = fmaf(ww.y, h[4 * q + 1], y4[1]);
-                    y4[2] = fmaf(ww.z, h[4 * q + 2], y4[2]);
-                    y4[3] = fmaf(ww.w, h[4 * q + 3], y4[3]);
-                }
-                const float s = sigm((y4[0] + y4[1]) + (y4[2] + y4[3]));
+                const float s = sigm(out_row(sW2, sb2, o, h));
                 if (G == 1) {
                     dy = gin * a.ascale[3 * an + c] * s * (1.f - s);
                     dls[c] += gin * s;
@@ -330,38 +338,47 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
                 }
             }
             if (want_mlp) a.s.DY[(size_t)o * ld + lr] = dy;
-            const float4 *w = reinterpret_cast<const float4 *>(sW2 + o * kH);
+            const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(sW2 + o * kH);
+            const f2 dy2 = f2_make(dy, dy);
 #pragma unroll
             for (int q = 0; q < kH / 4; ++q) {
-                const float4 ww = w[q];
-                dh[4 * q] = fmaf(dy, ww.x, dh[4 * q]);
-                dh[4 * q + 1] = fmaf(dy, ww.y, dh[4 * q + 1]);
-                dh[4 * q + 2] = fmaf(dy, ww.z, dh[4 * q + 2]);
-                dh[4 * q + 3] = fmaf(dy, ww.w, dh[4 * q + 3]);
+                const ulonglong2 ww = w[q];
+                dh[2 * q] = f2_fma(dy2, ww.x, dh[2 * q]);
+                dh[2 * q + 1] = f2_fma(dy2, ww.y, dh[2 * q + 1]);
             }
         }
     }
     // DZ = DH * act'(Z): ReLU -> mask; SoftPlus -> sigmoid(Z) = 1 - exp(-H)
 #pragma unroll
-    for (int j = 0; j < kH; ++j) dh[j] *= G < 3 ? (float)((relu_on >> j) & 1u) : -expm1f(-h[j]);
-    if (want_mlp)
-#pragma unroll
-        for (int j = 0; j < kH; ++j) a.s.DZ[(size_t)(G * kH + j) * ld + lr] = dh[j];
+    for (int p = 0; p < kH2; ++p) {
+        float d0, d1, h0, h1;
+        f2_split(dh[p], d0, d1);
+        f2_split(h[p], h0, h1);
+        d0 *= G < 3 ? (float)((relu_on >> (2 * p)) & 1u) : -expm1f(-h0);
+        d1 *= G < 3 ? (float)((relu_on >> (2 * p + 1)) & 1u) : -expm1f(-h1);
+        dh[p] = f2_make(d0, d1);
+        if (want_mlp) {
+            a.s.DZ[(size_t)(G * kH + 2 * p) * ld + lr] = d0;
+            a.s.DZ[(size_t)(G * kH + 2 * p + 1) * ld + lr] = d1;
+        }
+    }
     // dx += DZ W1_g for the inputs that have a gradient (f_v, delta_vc, d_vc),
-    // accumulated in shared memory (column tid of sDX)
+    // accumulated in shared memory (column tid of sDX); partial sums as in
+    // out_row
 #pragma unroll 1
     for (int i = 0; i < kDX; ++i) {
-        const float4 *w = reinterpret_cast<const float4 *>(sW1T + i * 128 + G * kH);
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const ulonglong2 *w = reinterpret_cast<const ulonglong2 *>(sW1T + i * 128 + G * kH);
+        f2 a01 = 0ull, a23 = 0ull;
 #pragma unroll
         for (int q = 0; q < kH / 4; ++q) {
-            const float4 ww = w[q];
-            acc[0] = fmaf(dh[4 * q], ww.x, acc[0]);
-            acc[1] = fmaf(dh[4 * q + 1], ww.y, acc[1]);
-            acc[2] = fmaf(dh[4 * q + 2], ww.z, acc[2]);
-            acc[3] = fmaf(dh[4 * q + 3], ww.w, acc[3]);
+            const ulonglong2 ww = w[q];
+            a01 = f2_fma(dh[2 * q], ww.x, a01);
+            a23 = f2_fma(dh[2 * q + 1], ww.y, a23);
         }
-        sDX[i * dbwd::kRowsPerBlock] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        float s0, s1, s2, s3;
+        f2_split(a01, s0, s1);
+        f2_split(a23, s2, s3);
+        sDX[i * dbwd::kRowsPerBlock] += (s0 + s1) + (s2 + s3);
     }
 }
 
