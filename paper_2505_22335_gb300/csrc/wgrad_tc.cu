@@ -15,11 +15,11 @@
 // products hi*hi + hi*lo + lo*hi recover FP32 accuracy (the dropped lo*lo term
 // is about 2^-22 relative), with FP32 accumulation in TMEM.
 //
-// Warp roles (one CTA per SM, persistent over chunks): warps 0-10 load a
+// Warp roles (one CTA per SM, persistent over chunks): warps 0-14 load a
 // chunk's 16-row slice of every scratch feature (the next chunk's loads are
 // in flight while the current one is split), split it and store hi and lo as
 // canonical K-major no-swizzle operand tiles, then arrive on the stage's
-// `full` mbarrier; warp 11 waits for `full`, issues the MMAs and commits them
+// `full` mbarrier; warp 15 waits for `full`, issues the MMAs and commits them
 // to the stage's `empty` mbarrier.  Three stages (two for the widest outputs).
 #include <algorithm>
 
@@ -35,9 +35,8 @@ using dbwd::kDin;
 using dbwd::kH;
 using dbwd::kXW;
 
-// 11 converter warps + the MMA warp: registers are allocated per group of
-// four warps, so twelve warps cost what nine did
-constexpr int kConv = 352;            // converter threads (warps 0-10)
+// 15 converter warps + the MMA warp: 512 threads at up to 128 registers
+constexpr int kConv = 480;            // converter threads (warps 0-14)
 constexpr int kT = kConv + 32;        // + the MMA warp
 constexpr int kKR = 16;               // rows per chunk (2 TF32 K steps)
 constexpr int kRowBytes = kKR * 4;    // bytes of one operand row per chunk
@@ -45,7 +44,7 @@ constexpr int kNX = 48;               // X operand rows (40 + zero padding)
 constexpr int kMaxNB = 464;           // DY operand rows: D_w2 + D_w1 <= 512 TMEM columns
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxStages = 3;
-constexpr int kMaxItems = 9;          // (feature, quad) items per converter thread
+constexpr int kMaxItems = 7;          // (feature, quad) items per converter thread
 constexpr int kWait = 1 << 22;
 
 struct WLay {
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
             }
         }
     } else if (tid == kConv) {
-        // ---------------- MMA issue (one thread of warp 11)
+        // ---------------- MMA issue (one thread of warp 15)
         const uint32_t id_w1 = idesc(kTF32, 128, kNX);
         for (int it = 0; it < nmine; ++it) {
             const int s = it % S, use = it / S;
