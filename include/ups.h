@@ -69,9 +69,18 @@ typedef struct {
     int hidden;       /* decode MLP hidden width (32) */
     int decode_bf16;  /* 1: decode GEMMs in BF16 on the tensor cores, FP32 accumulate */
     int check_finite; /* 1: scan inputs for NaN/Inf and fail with UPS_ERR_NONFINITE */
+    int list_cap;     /* tile lists keep their first list_cap entries in depth order
+                         (0: 1024; < 0: no cap; at most 32767).  Blending reads a
+                         list only until every pixel of the tile has stopped (Eq. 3
+                         with the t_min reading), so a cap changes nothing unless a
+                         pixel is still open at the end of a cut list: the forward
+                         then sorts that batch again without the cap and blends it
+                         again (ups_stats.list_refills).  Views of more than 16383
+                         tiles in total are never capped. */
 } ups_config;
 
-/* Fills the defaults listed above (n_feat 16, k 10, feat_dim 32, hidden 32). */
+/* Fills the defaults listed above (n_feat 16, k 10, feat_dim 32, hidden 32,
+ * list_cap 1024). */
 void ups_config_default(ups_config *cfg);
 
 /* Pinhole camera of one view (Sec. 3.1); t_norm feeds the temporal encoding
@@ -189,6 +198,8 @@ typedef struct {
     long long n_tiles;          /* tiles over all views */
     long long n_pixels;
     int key_bits;               /* significant bits of the (view, tile) key */
+    long long n_listed;         /* entries kept in the tile lists (list_cap) */
+    int list_refills;           /* 1: a capped list was too short and the lists were rebuilt */
 } ups_stats;
 
 /* ---------------------------------------------------------------------- */
@@ -265,8 +276,8 @@ ups_status ups_get_stats(ups_ctx *ctx, ups_stats *out);
 
 /* Internal buffers of the last forward, copied to HOST memory `dst` of
  * `bytes` bytes (at most the buffer size; the copy synchronises):
- *   0 sorted instance Gaussian-view ids   uint32 [n_instances] (gv = view*n + g)
- *   1 sorted instance keys                uint32 [n_instances] (tile_base[view] + tile)
+ *   0 sorted instance Gaussian-view ids   uint32 [n_listed] (gv = view*n + g)
+ *   1 sorted instance keys                uint32 [n_listed] (tile_base[view] + tile)
  *   2 tile ranges                         uint32 [n_tiles][2]  ([start, end))
  *   3 projected (u, v, z, o)              float4 [n_gaussian_views]
  *   4 conic (a, b, c, -)                  float4 [n_gaussian_views]

@@ -27,7 +27,7 @@ MAX_VIEWS = 64
 class Config(C.Structure):
     _fields_ = [("alpha_min", _f), ("alpha_max", _f), ("t_min", _f), ("dilation", _f),
                 ("near_z", _f), ("guard", _f), ("n_feat", _i), ("k", _i), ("feat_dim", _i),
-                ("hidden", _i), ("decode_bf16", _i), ("check_finite", _i)]
+                ("hidden", _i), ("decode_bf16", _i), ("check_finite", _i), ("list_cap", _i)]
 
 
 class Camera(C.Structure):
@@ -84,7 +84,8 @@ class Result(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_views", _i), ("n_gaussian_views", _ll), ("n_visible", _ll),
-                ("n_instances", _ll), ("n_tiles", _ll), ("n_pixels", _ll), ("key_bits", _i)]
+                ("n_instances", _ll), ("n_tiles", _ll), ("n_pixels", _ll), ("key_bits", _i),
+                ("n_listed", _ll), ("list_refills", _i)]
 
 
 # every entry point of include/ups.h (checked by the CPU test suite)

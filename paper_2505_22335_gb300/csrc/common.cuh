@@ -104,12 +104,19 @@ cudaError_t radix_sort_u64(uint64_t **key_io, uint64_t **key_alt, uint32_t **val
                            uint32_t **val_alt, size_t n, int end_bit, SortScratch &s,
                            cudaStream_t st);
 // One-pass stable sort of (key, value) pairs by keys < nbins <= kMaxBucketBins
-// (tile ids): writes the values in key order to vals_out and the [start, end)
-// range of every key to ranges[nbins].  scratch: bucket_sort_scratch_bytes.
+// (tile ids).  Bucket d keeps its first min(count_d, cap) values (cap =
+// kNoListCap: all; a finite cap needs cap <= kMaxListCap and nbins <
+// kMaxBucketBins), written in key order to vals_out; ranges[d] is the kept
+// [start, end) and bit d of trunc[(nbins + 31) / 32] is set when bucket d
+// lost values to the cap.  scratch: bucket_sort_scratch_bytes.  gate (no
+// cap only): when non-null the kernels do nothing unless *gate != 0.
 constexpr int kMaxBucketBins = 1 << 14;
+constexpr int kMaxListCap = 32767;
+constexpr uint32_t kNoListCap = 0xffffffffu;
 size_t bucket_sort_scratch_bytes(size_t n, int nbins, int num_sms);
 cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t *vals_out, size_t n, int nbins,
-                            uint2 *ranges, void *scratch, size_t scratch_bytes, int num_sms, cudaStream_t st);
+                            uint32_t cap, uint2 *ranges, uint32_t *trunc, void *scratch, size_t scratch_bytes,
+                            int num_sms, cudaStream_t st, const int *gate = nullptr);
 // keys[i] = t for every i in ranges[t] (the sorted keys of a bucket sort)
 cudaError_t keys_from_ranges(const uint2 *ranges, int nbins, uint32_t *keys, cudaStream_t st);
 // Exclusive scan of n uint32 into uint64 (out has n+1 entries; out[n] = total).

@@ -100,7 +100,11 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
     const float *__restrict__ feat, float *__restrict__ out_color, float *__restrict__ out_depth,
-    float *__restrict__ out_feat, float *__restrict__ out_T, uint32_t *__restrict__ out_nc) {
+    float *__restrict__ out_feat, float *__restrict__ out_T, uint32_t *__restrict__ out_nc,
+    const uint32_t *__restrict__ trunc, int *__restrict__ trunc_flag, const int *__restrict__ gate) {
+    // gate: when non-null, blend only if *gate != 0 (a pass enqueued ahead of
+    // the GPU's decision to run it)
+    if (gate && *gate == 0) return;
     constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS;
     __shared__ Stage<NF> S;
     const TileP<PX> tc = tilep<PX>(vt);
@@ -173,6 +177,10 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
             }
         }
     }
+    // a list cut short by the list cap is exact only if every pixel stopped
+    // inside it; otherwise the caller blends the tile again from a full list
+    if (trunc && ((trunc[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u))
+        if (__syncthreads_count(all_done()) != NT && threadIdx.x == 0) atomicOr(trunc_flag, 1);
     const DevView &cam = *tc.cam;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
@@ -461,12 +469,13 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_bwd(
 cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
-                                 const float *feat, const ups_images &out, cudaStream_t st) {
+                                 const float *feat, const ups_images &out, cudaStream_t st,
+                                 const uint32_t *trunc, int *trunc_flag, const int *gate) {
     if (vt.total_tiles == 0) return cudaSuccess;
 #define UPS_FWD(NFV)                                                                                  \
     k_composite_fwd<NFV, blend_px_fwd(NFV)><<<vt.total_tiles, Px<blend_px_fwd(NFV)>::NT, 0, st>>>(              \
         vt, bp, N, per_view, ranges, ival, xyzo, conic, color, feat, out.color, out.depth, out.feat, out.T, \
-        out.n_contrib)
+        out.n_contrib, trunc, trunc_flag, gate)
     switch (n_feat) {
         case 0: UPS_FWD(0); break;
         case 16: UPS_FWD(16); break;

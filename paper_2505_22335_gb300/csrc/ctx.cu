@@ -35,7 +35,9 @@ cudaError_t launch_project_bwd(const ViewTable &vt, const BlendParams &bp, int N
 cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
-                                 const float *feat, const ups_images &out, cudaStream_t st);
+                                 const float *feat, const ups_images &out, cudaStream_t st,
+                                 const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
+                                 const int *gate = nullptr);
 cudaError_t launch_loss(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                         int l2, float inv_norm, const ups_images &img, const ups_targets &tgt,
                         const ups_images &grad, float *loss, cudaStream_t st, int v0 = 0, int v1 = -1);
@@ -107,8 +109,13 @@ struct ups_ctx {
     DevBuf dec_scratch;  // decode backward: X, H, dL/dY, dL/dZ rows for the weight gradients
     SortScratch sort;
     uint32_t *dval_sorted = nullptr, *ikey_sorted = nullptr, *ival_sorted = nullptr;
-    uint64_t *h_total = nullptr;  // pinned: [0] instance count, [1] device error flag
+    // pinned: [0] instance count, [1] device error / list-cap flag, [2] the
+    // last tile range
+    uint64_t *h_total = nullptr;
     int *d_err = nullptr;         // set by kernels whose bounded waits ran out
+    int *d_trunc_flag = nullptr;  // set by the forward blend: a capped list was too short
+    DevBuf trunc;                 // per-tile bit: the list cap cut the tile's list
+    bool capped = false;          // the last forward capped its tile lists
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
     struct Rec {
@@ -278,6 +285,25 @@ ups_status loss_views(ups_ctx *c, const ups_images *img, const ups_targets *tgt,
     stage_end(c, st, 1);
     return UPS_OK;
 }
+// Entries in the tile lists of the last forward (a capped forward keeps
+// fewer than it emitted unless the GPU rebuilt them whole: *refilled).
+// Synchronises the ctx stream.
+ups_status listed_entries(ups_ctx *c, size_t *listed, int *refilled) {
+    *listed = c->n_inst;
+    *refilled = 0;
+    if (!c->capped) return UPS_OK;
+    UPS_CUDA(c, cudaSetDevice(c->device));
+    UPS_CUDA(c, cudaStreamSynchronize(c->last_stream));
+    uint2 last;
+    int flag = 0;
+    UPS_CUDA(c, cudaMemcpy(&last, c->ranges.as<uint2>() + c->vt.total_tiles - 1, sizeof(uint2),
+                           cudaMemcpyDeviceToHost));
+    UPS_CUDA(c, cudaMemcpy(&flag, c->d_trunc_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    *listed = last.y;
+    *refilled = flag != 0;
+    return UPS_OK;
+}
+
 }  // namespace ups
 
 extern "C" {
@@ -297,6 +323,7 @@ void ups_config_default(ups_config *cfg) {
     cfg->hidden = 32;
     cfg->decode_bf16 = 0;
     cfg->check_finite = 0;
+    cfg->list_cap = 1024;
 }
 
 const char *ups_version(void) { return "ups-gb300 0.1 (sm_103a)"; }
@@ -319,6 +346,7 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
     if (!(c.alpha_min > 0.f) || !(c.alpha_max >= c.alpha_min) || !(c.alpha_max < 1.f) ||
         !(c.t_min >= 0.f) || !(c.dilation >= 0.f) || !(c.near_z > 0.f) || !(c.guard > 0.f))
         return fail(nullptr, UPS_ERR_ARG, "threshold out of range");
+    if (c.list_cap > kMaxListCap) return fail(nullptr, UPS_ERR_ARG, "list_cap must be at most 32767");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || device < 0 || device >= ndev)
@@ -329,9 +357,11 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
     ctx->device = device;
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_total, 2 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_total, 4 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_trunc_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_trunc_flag, 0, sizeof(int));
     if (e != cudaSuccess) {
         g_create_error = std::string("ups_create: ") + cudaGetErrorString(e);
         delete ctx;
@@ -347,10 +377,11 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->d_err) cudaFree(c->d_err);
+    if (c->d_trunc_flag) cudaFree(c->d_trunc_flag);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -489,13 +520,18 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     // stable bucket by (view, tile): depth order is kept inside each tile
     c->key_bits = bits_for((size_t)vt.total_tiles);
     stage_begin(c, "tile_sort", st);
-    if (vt.total_tiles <= kMaxBucketBins) {
+    const uint32_t cap = c->cfg.list_cap < 0 || vt.total_tiles >= kMaxBucketBins
+                             ? kNoListCap
+                             : (uint32_t)(c->cfg.list_cap == 0 ? 1024 : c->cfg.list_cap);
+    const bool bucket = vt.total_tiles <= kMaxBucketBins;
+    if (bucket) {
         // one pass: values in tile order and the tile ranges; the sorted keys
         // are only rebuilt (from the ranges) when inspected
         const size_t need = bucket_sort_scratch_bytes(n_inst, vt.total_tiles, c->num_sms);
         UPS_CUDA(c, c->sort.hist.reserve(std::max<size_t>(need, 256)));
-        UPS_CUDA(c, bucket_sort_u32(ik, iv, iv_alt, n_inst, vt.total_tiles, c->ranges.as<uint2>(), c->sort.hist.ptr,
-                                    c->sort.hist.bytes, c->num_sms, st));
+        UPS_CUDA(c, c->trunc.reserve(((size_t)vt.total_tiles + 31) / 32 * 4));
+        UPS_CUDA(c, bucket_sort_u32(ik, iv, iv_alt, n_inst, vt.total_tiles, cap, c->ranges.as<uint2>(),
+                                    c->trunc.as<uint32_t>(), c->sort.hist.ptr, c->sort.hist.bytes, c->num_sms, st));
         stage_end(c, st, n_inst ? 6 : 0);
         c->ikey_sorted = nullptr;
         c->ival_sorted = iv_alt;
@@ -509,11 +545,29 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
         UPS_CUDA(c, launch_ranges(ik, (uint32_t)n_inst, c->ranges.as<uint2>(), st));
         stage_end(c, st, n_inst ? 1 : 0);
     }
+    const bool capped = bucket && cap != kNoListCap && n_inst > 0;
+    c->capped = capped;
+    if (capped) UPS_CUDA(c, cudaMemsetAsync(c->d_trunc_flag, 0, sizeof(int), st));
     stage_begin(c, "composite_fwd", st);
     UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
                                      c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
-                                     reinterpret_cast<const float4 *>(g->color), g->feat, *out, st));
+                                     reinterpret_cast<const float4 *>(g->color), g->feat, *out, st,
+                                     capped ? c->trunc.as<uint32_t>() : nullptr, capped ? c->d_trunc_flag : nullptr));
     stage_end(c, st, 1);
+    if (capped) {
+        // a pixel still open at the end of a capped list: the GPU rebuilds the
+        // lists without the cap and blends again.  The work is enqueued now
+        // and gated on the blend's flag, so the host never waits for it.
+        stage_begin(c, "list_refill", st);
+        UPS_CUDA(c, bucket_sort_u32(ik, iv, iv_alt, n_inst, vt.total_tiles, kNoListCap, c->ranges.as<uint2>(),
+                                    c->trunc.as<uint32_t>(), c->sort.hist.ptr, c->sort.hist.bytes, c->num_sms, st,
+                                    c->d_trunc_flag));
+        UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
+                                         c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
+                                         reinterpret_cast<const float4 *>(g->color), g->feat, *out, st, nullptr,
+                                         nullptr, c->d_trunc_flag));
+        stage_end(c, st, 7);
+    }
     c->g_in = *g;
     c->img = *out;
     c->have_fwd = true;
@@ -650,6 +704,12 @@ ups_status ups_get_stats(ups_ctx *c, ups_stats *out) {
     out->n_tiles = c->vt.total_tiles;
     out->n_pixels = (long long)c->n_pix;
     out->key_bits = c->key_bits;
+    size_t listed = 0;
+    int refilled = 0;
+    const ups_status ls = listed_entries(c, &listed, &refilled);
+    if (ls != UPS_OK) return ls;
+    out->n_listed = (long long)listed;
+    out->list_refills = refilled;
     // visible = Gaussian-views with at least one tile (count > 0)
     std::vector<uint32_t> h(c->total_gv);
     if (c->total_gv) {
@@ -666,12 +726,18 @@ ups_status ups_get_stats(ups_ctx *c, ups_stats *out) {
 ups_status ups_copy_buffer(ups_ctx *c, int which, void *dst, size_t bytes, size_t *size) {
     if (!c) return UPS_ERR_ARG;
     if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "no forward yet");
+    size_t listed = 0;
+    int refilled = 0;
+    if (which <= 1) {
+        ups_status s = listed_entries(c, &listed, &refilled);
+        if (s != UPS_OK) return s;
+    }
     const void *src = nullptr;
     size_t sz = 0;
     switch (which) {
-        case 0: src = c->ival_sorted; sz = c->n_inst * 4; break;
+        case 0: src = c->ival_sorted; sz = listed * 4; break;
         case 1:
-            sz = c->n_inst * 4;
+            sz = listed * 4;
             if (!c->ikey_sorted && sz) {
                 UPS_CUDA(c, cudaSetDevice(c->device));
                 UPS_CUDA(c, keys_from_ranges(c->ranges.as<uint2>(), c->vt.total_tiles, c->ikey1.as<uint32_t>(),

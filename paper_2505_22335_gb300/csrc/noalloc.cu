@@ -42,7 +42,9 @@ cudaError_t launch_ranges(const uint32_t *ikey, uint32_t n, uint2 *ranges, cudaS
 cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int n_feat, int N,
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
-                                 const float *feat, const ups_images &out, cudaStream_t st);
+                                 const float *feat, const ups_images &out, cudaStream_t st,
+                                 const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
+                                 const int *gate = nullptr);
 cudaError_t radix_sort_u32_fixed(uint32_t **key_io, uint32_t **key_alt, uint32_t **val_io,
                                  uint32_t **val_alt, size_t n, int end_bit, void *scratch,
                                  size_t scratch_bytes, cudaStream_t st);

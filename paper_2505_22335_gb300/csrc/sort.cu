@@ -185,9 +185,14 @@ __device__ T block_exclusive_scan(T x, T *total) {
     return r;
 }
 
+// gate (all scan, histogram, range and scatter kernels): when non-null, the
+// kernel does nothing unless *gate != 0 (work enqueued ahead of a decision
+// the GPU takes)
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                              size_t n, T *__restrict__ partial) {
+                                                              size_t n, T *__restrict__ partial,
+                                                              const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ T tot;
     const size_t base = (size_t)blockIdx.x * kScanTile;
     T s = 0;
@@ -200,7 +205,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__
 }
 
 template <class T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(T *partial, int nb) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(T *partial, int nb, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ T tot;
     T carry = 0;
     for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
@@ -216,7 +222,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(T *partial, int 
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in, T *out, size_t n,
                                                              const T *__restrict__ partial,
-                                                             int write_total) {
+                                                             int write_total, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ uint32_t tile[kScanTile];
     __shared__ T tot;
     const size_t base = (size_t)blockIdx.x * kScanTile;
@@ -262,16 +269,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in,
 
 template <class T>
 cudaError_t scan_impl(const uint32_t *in, T *out, size_t n, void *scratch, int write_total,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int *gate = nullptr) {
     if (n == 0) {
         if (write_total) return cudaMemsetAsync(out, 0, sizeof(T), st);
         return cudaSuccess;
     }
     int nb = (int)((n + kScanTile - 1) / kScanTile);
     T *partial = static_cast<T *>(scratch);
-    k_scan_reduce<T><<<nb, kScanThreads, 0, st>>>(in, n, partial);
-    k_scan_partials<T><<<1, kScanThreads, 0, st>>>(partial, nb);
-    k_scan_apply<T><<<nb, kScanThreads, 0, st>>>(in, out, n, partial, write_total);
+    k_scan_reduce<T><<<nb, kScanThreads, 0, st>>>(in, n, partial, gate);
+    k_scan_partials<T><<<1, kScanThreads, 0, st>>>(partial, nb, gate);
+    k_scan_apply<T><<<nb, kScanThreads, 0, st>>>(in, out, n, partial, write_total, gate);
     return cudaGetLastError();
 }
 
@@ -356,6 +363,7 @@ constexpr int kBkDigit = 7;                    // bits per in-block pass
 constexpr int kBkLocal = 1 << kBkDigit;
 constexpr int kBkHistThreads = 512;
 constexpr uint32_t kBkPad = kMaxBucketBins - 1;  // digit of the empty slots of a partial sub-tile
+constexpr int kBkCapWaves = 4;
 
 __host__ __device__ inline int bk_nbp(int nbins) { return (nbins + 3) & ~3; }
 size_t bk_scatter_smem(int nbins) {
@@ -364,7 +372,9 @@ size_t bk_scatter_smem(int nbins) {
 
 __global__ void __launch_bounds__(kBkHistThreads) k_bucket_hist(const uint32_t *__restrict__ keys, size_t n,
                                                                 int nbins, size_t per_block,
-                                                                uint32_t *__restrict__ hist, int nblocks) {
+                                                                uint32_t *__restrict__ hist, int nblocks,
+                                                                const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ uint32_t h[];
     for (int d = threadIdx.x; d < nbins; d += kBkHistThreads) h[d] = 0;
     __syncthreads();
@@ -386,11 +396,62 @@ __global__ void __launch_bounds__(kBkHistThreads) k_bucket_hist(const uint32_t *
     for (int d = threadIdx.x; d < nbins; d += kBkHistThreads) hist[(size_t)d * nblocks + blockIdx.x] = h[d];
 }
 
-__global__ void k_bucket_ranges(const uint32_t *__restrict__ offs, int nbins, int nblocks, uint32_t n,
-                                uint2 *__restrict__ ranges) {
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d < nbins)
-        ranges[d] = make_uint2(offs[(size_t)d * nblocks], d + 1 < nbins ? offs[(size_t)(d + 1) * nblocks] : n);
+// Bucket d keeps its first min(count_d, cap) items: one block scans the kept
+// counts into ranges[d] = [start, start + kept) (ostart[d] = start) and sets
+// bit d of trunc when count_d > cap.
+constexpr int kBkRangeThreads = 1024;
+__global__ void __launch_bounds__(kBkRangeThreads) k_bucket_ranges(const uint32_t *__restrict__ offs, int nbins,
+                                                                   int nblocks, uint32_t n, uint32_t cap,
+                                                                   uint2 *__restrict__ ranges,
+                                                                   uint32_t *__restrict__ ostart,
+                                                                   uint32_t *__restrict__ trunc,
+                                                                   const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ uint32_t wsum[kBkRangeThreads / 32];
+    __shared__ uint32_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    for (int i = tid; i < (nbins + 31) / 32; i += kBkRangeThreads) trunc[i] = 0u;
+    __syncthreads();
+    for (int d0 = 0; d0 < nbins; d0 += kBkRangeThreads) {
+        const int d = d0 + tid;
+        uint32_t cnt = 0, kept = 0;
+        if (d < nbins) {
+            const uint32_t s = offs[(size_t)d * nblocks];
+            const uint32_t e = d + 1 < nbins ? offs[(size_t)(d + 1) * nblocks] : n;
+            cnt = e - s;
+            kept = min(cnt, cap);
+        }
+        uint32_t incl = kept;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t x = wsum[lane];
+            uint32_t wi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            wsum[lane] = wi - x;
+        }
+        __syncthreads();
+        const uint32_t carry = carry_s;
+        if (d < nbins) {
+            const uint32_t st = carry + wsum[w] + incl - kept;
+            ranges[d] = make_uint2(st, st + kept);
+            ostart[d] = st;
+            if (cnt > cap) atomicOr(trunc + (d >> 5), 1u << (d & 31));
+        }
+        __syncthreads();
+        if (tid == kBkRangeThreads - 1) carry_s = carry + wsum[w] + incl;
+        __syncthreads();
+    }
 }
 
 // One stable counting pass over the 7-bit digit (d >> shift) & 127 of the
@@ -475,7 +536,9 @@ __global__ void __launch_bounds__(kBkThreads, 3) k_bucket_scatter(const uint32_t
                                                                   const uint32_t *__restrict__ vals,
                                                                   uint32_t *__restrict__ vout, size_t n, int nbins,
                                                                   size_t per_block,
-                                                                  const uint32_t *__restrict__ offs, int nblocks) {
+                                                                  const uint32_t *__restrict__ offs, int nblocks,
+                                                                  const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ __align__(16) unsigned char bk_smem[];
     const int nbp = bk_nbp(nbins);
     // next[b]: next output slot of bucket b; while a sub-tile is written, the
@@ -557,21 +620,202 @@ __global__ void __launch_bounds__(kBkThreads, 3) k_bucket_scatter(const uint32_t
     }
 }
 
+// Capped variant: bucket d keeps its first cap items.  A bucket whose cap is
+// reached takes no more items, so each block first drops, in input order,
+// every item whose bucket is already full (most items, once the nearest
+// layers of the scene have filled the lists) and packs the others into a
+// 2048-item buffer; full buffers are grouped by the two-pass sort and
+// written.  The sort carries item indices (relative to the block's run), and
+// values are read only for the items that are written.  room[d] (16 bits,
+// cap <= kMaxListCap) counts the slots bucket d has left; while a buffer is
+// written, the head of d's group rebases next[d] and room[d] by the group
+// start, so that item i of the group goes to next[d] + i while i < room[d].
+size_t bk_scatter_cap_smem(int nbins) {
+    return (size_t)bk_nbp(nbins) * (4 + 2) + 2 * kBkSub * (2 + 4) + (2 * kBkWarps + 1) * kBkLocal * 4 + 64;
+}
+
+// Groups and writes the m buffered items of (sd, sv); ends with the block
+// synced.
+__device__ __forceinline__ void bk_cap_flush(int m, uint16_t *sd, uint32_t *sv, uint32_t *wc, uint32_t *dstart,
+                                             uint32_t *next, uint16_t *room, const uint32_t *__restrict__ vals,
+                                             size_t beg, uint32_t *__restrict__ vout) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int slot0 = w * (32 * kBkItems) + lane;
+    uint32_t d[kBkItems], v[kBkItems];
+#pragma unroll
+    for (int j = 0; j < kBkItems; ++j) {
+        const int i = slot0 + j * 32;
+        d[j] = i < m ? (uint32_t)sd[i] : kBkPad;
+        v[j] = i < m ? sv[i] : 0u;
+    }
+    bk_local_pass(d, v, 0, sd, sv, wc, dstart);
+#pragma unroll
+    for (int j = 0; j < kBkItems; ++j) {
+        d[j] = sd[slot0 + j * 32];
+        v[j] = sv[slot0 + j * 32];
+    }
+    bk_local_pass(d, v, kBkDigit, sd, sv, wc, dstart);
+    // the m items come first (nbins < kMaxBucketBins: no tile id equals the pad)
+#pragma unroll
+    for (int k = 0; k < kBkItems; ++k) {
+        const int i = tid + k * kBkThreads;
+        if (i < m) {
+            const uint32_t dd = sd[i];
+            if (i == 0 || sd[i - 1] != dd) {
+                next[dd] -= (uint32_t)i;
+                room[dd] = (uint16_t)(room[dd] + i);
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t front[kBkItems];
+    uint16_t left[kBkItems];
+#pragma unroll
+    for (int k = 0; k < kBkItems; ++k) {
+        const int i = tid + k * kBkThreads;
+        front[k] = 0xffffffffu;
+        left[k] = 0;
+        if (i < m) {
+            const uint32_t dd = sd[i];
+            const uint32_t lim = room[dd];
+            const uint32_t base = next[dd];
+            if ((uint32_t)i < lim) vout[base + (uint32_t)i] = vals[beg + sv[i]];
+            if (i == m - 1 || sd[i + 1] != dd) {
+                const uint32_t e = min((uint32_t)i + 1u, lim);
+                front[k] = base + e;
+                left[k] = (uint16_t)(lim - e);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBkItems; ++k)
+        if (front[k] != 0xffffffffu) {
+            const uint32_t dd = sd[tid + k * kBkThreads];
+            next[dd] = front[k];
+            room[dd] = left[k];
+        }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBkThreads, 2) k_bucket_scatter_cap(
+    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t *__restrict__ vout, size_t n,
+    int nbins, size_t per_block, const uint32_t *__restrict__ offs, int nblocks,
+    const uint32_t *__restrict__ ostart, uint32_t cap) {
+    extern __shared__ __align__(16) unsigned char bk_smem[];
+    const int nbp = bk_nbp(nbins);
+    uint32_t *next = reinterpret_cast<uint32_t *>(bk_smem);
+    uint16_t *room = reinterpret_cast<uint16_t *>(next + nbp);
+    uint16_t *sd = room + nbp;                                   // [kBkSub] buffered digits
+    uint16_t *cd = sd + kBkSub;                                  // [kBkSub] overflow digits
+    uint32_t *sv = reinterpret_cast<uint32_t *>(cd + kBkSub);    // [kBkSub] buffered item indices
+    uint32_t *cv = sv + kBkSub;                                  // [kBkSub] overflow item indices
+    uint32_t *wc = cv + kBkSub;                                  // [kBkWarps][kBkLocal]
+    uint32_t *dstart = wc + kBkWarps * kBkLocal;                 // [kBkLocal]
+    uint32_t *wlive = dstart + kBkLocal;                         // [kBkWarps] live items per warp
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int d = tid; d < nbins; d += kBkThreads) {
+        const uint32_t before = min(offs[(size_t)d * nblocks + blockIdx.x] - offs[(size_t)d * nblocks], cap);
+        next[d] = ostart[d] + before;
+        room[d] = (uint16_t)(cap - before);
+    }
+    __syncthreads();
+    const size_t beg = (size_t)blockIdx.x * per_block;
+    const size_t end = min(n, beg + per_block);
+    const uint32_t top = (uint32_t)nbins - 1;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int slot0 = w * (32 * kBkItems) + lane;
+    uint32_t key[kBkItems];
+    auto load = [&](size_t s0) {
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            const size_t idx = s0 + (size_t)(slot0 + j * 32);
+            if (idx < end) key[j] = keys[idx];
+        }
+    };
+    if (beg < end) load(beg);
+    int fill = 0;  // buffered items (the same in every thread)
+    for (size_t s0 = beg; s0 < end; s0 += kBkSub) {
+        const int nvalid = (int)min((size_t)kBkSub, end - s0);
+        uint32_t d[kBkItems];
+        bool live[kBkItems];
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            d[j] = min(key[j], top);
+            live[j] = slot0 + j * 32 < nvalid && room[d[j]] > 0;
+        }
+        if (s0 + kBkSub < end) load(s0 + kBkSub);
+        // order-preserving compaction of the live items behind the buffered ones
+        uint32_t mask[kBkItems], wl = 0;
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            mask[j] = __ballot_sync(0xffffffffu, live[j]);
+            wl += __popc(mask[j]);
+        }
+        if (lane == 0) wlive[w] = wl;
+        __syncthreads();
+        uint32_t pos = (uint32_t)fill, total = 0;
+#pragma unroll
+        for (int ww = 0; ww < kBkWarps; ++ww) {
+            const uint32_t c = wlive[ww];
+            pos += ww < w ? c : 0u;
+            total += c;
+        }
+#pragma unroll
+        for (int j = 0; j < kBkItems; ++j) {
+            if (live[j]) {
+                const uint32_t p = pos + __popc(mask[j] & lt_mask);
+                const uint32_t idx = (uint32_t)(s0 - beg) + (uint32_t)(slot0 + j * 32);
+                if (p < (uint32_t)kBkSub) {
+                    sd[p] = (uint16_t)d[j];
+                    sv[p] = idx;
+                } else {
+                    cd[p - kBkSub] = (uint16_t)d[j];
+                    cv[p - kBkSub] = idx;
+                }
+            }
+            pos += __popc(mask[j]);
+        }
+        fill += (int)total;
+        __syncthreads();
+        if (fill >= kBkSub) {
+            bk_cap_flush(kBkSub, sd, sv, wc, dstart, next, room, vals, beg, vout);
+            fill -= kBkSub;
+            for (int i = tid; i < fill; i += kBkThreads) {
+                sd[i] = cd[i];
+                sv[i] = cv[i];
+            }
+            __syncthreads();
+        }
+    }
+    if (fill > 0) bk_cap_flush(fill, sd, sv, wc, dstart, next, room, vals, beg, vout);
+}
+
 }  // namespace
 
 size_t bucket_sort_scratch_bytes(size_t n, int nbins, int num_sms) {
-    if (n == 0 || nbins <= 0) return 0;
-    const size_t nblocks = std::min<size_t>((n + kBkSub - 1) / kBkSub, (size_t)std::max(num_sms, 1) * 4);
+    if (nbins <= 0) return 0;
+    const size_t nblocks = std::max<size_t>(
+        1, std::min<size_t>((n + kBkSub - 1) / kBkSub, (size_t)std::max(num_sms, 1) * 4 * kBkCapWaves));
     const size_t hist_n = (size_t)nbins * nblocks;
-    return ((hist_n * 4 + 255) & ~size_t(255)) + scan_scratch_bytes(hist_n);
+    const size_t aux = ((size_t)nbins * 4 + ((size_t)nbins + 31) / 32 * 4 + 255) & ~size_t(255);
+    return ((hist_n * 4 + 255) & ~size_t(255)) + aux + scan_scratch_bytes(hist_n);
 }
 
 cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t *vals_out, size_t n, int nbins,
-                            uint2 *ranges, void *scratch, size_t scratch_bytes, int num_sms, cudaStream_t st) {
+                            uint32_t cap, uint2 *ranges, uint32_t *trunc, void *scratch, size_t scratch_bytes,
+                            int num_sms, cudaStream_t st, const int *gate) {
+    if (gate && cap != kNoListCap) return cudaErrorInvalidValue;
     if (nbins <= 0 || nbins > kMaxBucketBins) return cudaErrorInvalidValue;
-    if (n == 0) return cudaMemsetAsync(ranges, 0, (size_t)nbins * sizeof(uint2), st);
+    if (cap < kNoListCap && (cap > (uint32_t)kMaxListCap || nbins >= kMaxBucketBins)) return cudaErrorInvalidValue;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)nbins * sizeof(uint2), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(trunc, 0, ((size_t)nbins + 31) / 32 * 4, st);
+        return e;
+    }
     if (n >= (size_t)UINT32_MAX) return cudaErrorInvalidValue;
-    const size_t smem = bk_scatter_smem(nbins);
+    const bool capped = cap < kNoListCap;
+    const size_t smem = capped ? bk_scatter_cap_smem(nbins) : bk_scatter_smem(nbins);
     static thread_local int attr_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -580,32 +824,46 @@ cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t
         e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bk_scatter_smem(kMaxBucketBins));
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_bucket_scatter_cap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bk_scatter_cap_smem(kMaxBucketBins));
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kMaxBucketBins * 4);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
     int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_scatter, kBkThreads, smem);
+    e = capped ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_scatter_cap, kBkThreads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_scatter, kBkThreads, smem);
     if (e != cudaSuccess) return e;
     occ = std::max(1, std::min(occ, 4));
-    // one wave: at most num_sms * occupancy blocks, each a run of whole sub-tiles
+    // uncapped: one wave of at most num_sms * occupancy blocks, each a run of
+    // whole sub-tiles.  Capped: kBkCapWaves times as many shorter runs, since
+    // the runs that hold a view's nearest layers (where the lists are still
+    // filling) carry nearly all the work
     const size_t subs = (n + kBkSub - 1) / kBkSub;
-    size_t nblocks = std::min(subs, (size_t)std::max(num_sms, 1) * occ);
+    size_t nblocks = std::min(subs, (size_t)std::max(num_sms, 1) * occ * (capped ? kBkCapWaves : 1));
     const size_t per_block = ((subs + nblocks - 1) / nblocks) * kBkSub;
     nblocks = (n + per_block - 1) / per_block;
     const size_t hist_n = (size_t)nbins * nblocks;
     const size_t hist_bytes = (hist_n * 4 + 255) & ~size_t(255);
-    if (hist_bytes + scan_scratch_bytes(hist_n) > scratch_bytes) return cudaErrorInvalidValue;
+    const size_t aux = ((size_t)nbins * 4 + ((size_t)nbins + 31) / 32 * 4 + 255) & ~size_t(255);
+    if (hist_bytes + aux + scan_scratch_bytes(hist_n) > scratch_bytes) return cudaErrorInvalidValue;
     uint32_t *hist = static_cast<uint32_t *>(scratch);
-    void *scr = static_cast<char *>(scratch) + hist_bytes;
+    uint32_t *ostart = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + hist_bytes);
+    void *scr = static_cast<char *>(scratch) + hist_bytes + aux;
     k_bucket_hist<<<(int)nblocks, kBkHistThreads, (size_t)nbins * 4, st>>>(keys, n, nbins, per_block, hist,
-                                                                           (int)nblocks);
-    e = scan_impl<uint32_t>(hist, hist, hist_n, scr, 0, st);
+                                                                           (int)nblocks, gate);
+    e = scan_impl<uint32_t>(hist, hist, hist_n, scr, 0, st, gate);
     if (e != cudaSuccess) return e;
-    k_bucket_ranges<<<(nbins + 255) / 256, 256, 0, st>>>(hist, nbins, (int)nblocks, (uint32_t)n, ranges);
-    k_bucket_scatter<<<(int)nblocks, kBkThreads, smem, st>>>(keys, vals, vals_out, n, nbins, per_block, hist,
-                                                             (int)nblocks);
+    k_bucket_ranges<<<1, kBkRangeThreads, 0, st>>>(hist, nbins, (int)nblocks, (uint32_t)n, cap, ranges, ostart,
+                                                   trunc, gate);
+    if (capped)
+        k_bucket_scatter_cap<<<(int)nblocks, kBkThreads, smem, st>>>(keys, vals, vals_out, n, nbins, per_block,
+                                                                     hist, (int)nblocks, ostart, cap);
+    else
+        k_bucket_scatter<<<(int)nblocks, kBkThreads, smem, st>>>(keys, vals, vals_out, n, nbins, per_block, hist,
+                                                                 (int)nblocks, gate);
     return cudaGetLastError();
 }
 

@@ -177,15 +177,16 @@ def gauss_grads(grad, nf, sets):
                 color=co[..., :3], feat=fe)
 
 
-def plain_case(seed, n, cams, nf, weighted, l2=False, lambda_scale=0.0, g=None):
-    """Plain Gaussians shared by all views: GPU forward+loss+backward vs oracle."""
+def plain_case(seed, n, cams, nf, weighted, l2=False, lambda_scale=0.0, g=None, list_cap=0):
+    """Plain Gaussians shared by all views: GPU forward+loss+backward vs oracle
+    (list_cap: 0 the library default, < 0 whole tile lists)."""
     if g is None:
         g = scenes.plain_gaussians(seed, n, nf)
     g = round_dict(g)
     cams = round_cams(cams)
     tg = [round_dict(t) for t in scenes.targets(seed + 1, cams, nf, weighted=weighted)]
     lc = oracle.LossCfg(lambda_scale=lambda_scale, l2=l2)
-    R = B.Renderer(n_feat=nf, k=1)
+    R = B.Renderer(n_feat=nf, k=1, list_cap=list_cap)
     gs = B.to_set(g)
     img = R.forward(gs, cams)
     loss, dimg = R.loss(img, B.targets_to_device(tg), lambda_scale=lambda_scale, l2=l2, g=gs)

@@ -82,7 +82,7 @@ def _ambiguous(proj, cam, eps=1e-3, rel=1e-3):
 
 def test_plain_2k_tile_lists_and_sort_bit_exact():
     g, cams = scenes.workload_plain_2k(0)
-    res = plain_case(0, 2000, cams, 0, weighted=False, g=g)
+    res = plain_case(0, 2000, cams, 0, weighted=False, g=g, list_cap=-1)  # whole lists
     R, cam = res["R"], res["cams"][0]
     gv = R.copy_buffer(0)
     keys = R.copy_buffer(1)
