@@ -385,7 +385,8 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
 // One thread per row (anchor-major), 128 rows per step of a grid-stride loop;
 // weights in shared memory read as broadcasts.
 template <int NF>
-__global__ void __launch_bounds__(dbwd::kRowsPerBlock, 3) k_decode_bwd_rows(ViewTable vt, dbwd::Args a) {
+__global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_decode_bwd_rows(ViewTable vt,
+                                                                                               dbwd::Args a) {
     extern __shared__ float4 smem4[];
     __shared__ float aPose[3 * UPS_MAX_VIEWS];
     float *sm = reinterpret_cast<float *>(smem4);
@@ -448,7 +449,8 @@ cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a
     const size_t smem = bwd_rows_smem(dbwd::n_out(a.K, a.NF));
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     const int rows = a.row_end - a.row_begin;
-    const int blocks = std::max(1, std::min((rows + dbwd::kRowsPerBlock - 1) / dbwd::kRowsPerBlock, num_sms * 3));
+    const int blocks = std::max(
+        1, std::min((rows + dbwd::kRowsPerBlock - 1) / dbwd::kRowsPerBlock, num_sms * dbwd::kRowsCtasPerSm));
 #define UPS_DECB(NFV)                                                                              \
     do {                                                                                           \
         cudaFuncSetAttribute(k_decode_bwd_rows<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \

@@ -18,6 +18,7 @@ constexpr int kFin = 32;      // anchor feature width
 constexpr int kDin = kFin + 6;
 constexpr int kXW = 40;       // stored input width: x[0..37], x[38] = 1 (db1 column), x[39] = 0
 constexpr int kRowsPerBlock = 128;  // per-row kernels: one thread per row
+constexpr int kRowsCtasPerSm = 3;   // FP32 per-row kernel: resident CTAs per SM (its grid)
 
 __host__ __device__ inline int n_out(int K, int NF) { return K * (11 + NF); }
 // group g: outputs per Gaussian and first output row (opacity, covariance,
@@ -202,6 +203,9 @@ struct StageHook {
 cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st);
 size_t decode_bwd_rows_tc_smem(int NF, int K);
+// rows the per-row kernel's resident grid covers in one pass (FP32: 3 CTAs of
+// 128 rows per SM; tcgen05: 1 or 2 CTAs per SM by shared memory)
+int decode_bwd_rows_wave(int bf16, int K, int NF, int num_sms);
 bool decode_wgrad_tc_fits(int K, int NF);
 cudaError_t launch_decode_wgrad_tc(const float *scratch, int ld, int nrows, int K, int NF, const ups_mlp &d_mlp,
                                    int *err, int num_sms, cudaStream_t st);

@@ -676,11 +676,22 @@ constexpr int kChunkRows = 1 << 18;
 
 size_t decode_bwd_rows_tc_smem(int NF, int K) { return (size_t)rows_layout(NF, K).total; }
 
+// tcgen05 per-row kernel: resident CTAs per SM by shared memory
+static int rows_tc_per_sm(int NF, int K) {
+    const size_t smem = (size_t)rows_layout(NF, K).total;
+    return (smem + 2048) * 2 <= 228 * 1024 ? 2 : 1;
+}
+
+int decode_bwd_rows_wave(int bf16, int K, int NF, int num_sms) {
+    const int ctas = bf16 ? rows_tc_per_sm(NF, K) : dbwd::kRowsCtasPerSm;
+    return std::max(1, num_sms) * ctas * dbwd::kRowsPerBlock;
+}
+
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
     const size_t smem = (size_t)rows_layout(a.NF, a.K).total;
     if (smem + 1024 > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int rows = a.row_end - a.row_begin;
-    const int per_sm = (smem + 2048) * 2 <= 228 * 1024 ? 2 : 1;
+    const int per_sm = rows_tc_per_sm(a.NF, a.K);
     const int blocks = std::max(1, std::min((rows + kRows - 1) / kRows, num_sms * per_sm));
 #define UPS_BT(NFV)                                                                              \
     do {                                                                                         \
@@ -744,7 +755,11 @@ cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const u
     a.err = err;
     const bool want_mlp = (mask & UPS_GRAD_MLP) && d_mlp;
     const int rows = A * vt.n;
-    const int chunk = std::min(rows, kChunkRows);
+    // chunks of whole passes of the per-row kernel's resident grid (a chunk of
+    // 4.5 passes costs 5 on its slowest CTAs), at most kChunkRows rows
+    const int wave = decode_bwd_rows_wave(bf16, K, NF, num_sms);
+    int chunk = std::min(rows, kChunkRows);
+    if (rows > kChunkRows && wave <= kChunkRows) chunk = (kChunkRows / wave) * wave;
     const int ld = (chunk + 31) & ~31;
     if (want_mlp) a.s = dbwd::scratch_at(scratch, ld, dbwd::n_out(K, NF));
     for (int r = 0; r < rows; r += chunk) {
