@@ -284,6 +284,9 @@ def run_ours(args, wl_name):
     proc = processed_instances(st.img, cams)
     evals = evaluations(st.img)
 
+    # the next row of the path, timed on its own (not part of the mapping step)
+    unc = run_uncertainty(args, st, wl)
+
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -319,6 +322,9 @@ def run_ours(args, wl_name):
             "counters": dict(stats, processed_instances=proc, evaluations=evals),
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "next_rows": {"tracking_uncertainty": dict(unc, peak=round(peaks["hbm_gbs"], 1),
+                                                       frac=round(unc["achieved_gbs"] / peaks["hbm_gbs"], 4),
+                                                       peak_source=peaks["source"])},
         }
         print(json.dumps(line))
     if world > 1:
@@ -347,6 +353,39 @@ def roofline(stage, alg, stage_ms, launches, peaks, bf16=False):
     ach = a.get("bytes", 0) / (stage_ms / 1e3) / 1e9
     return dict(common, bound="hbm", achieved=round(ach, 1), peak=peaks["hbm_gbs"], unit="GB/s",
                 frac=round(ach / peaks["hbm_gbs"], 4), peak_source=peaks["source"])
+
+
+def run_uncertainty(args, st, wl):
+    """Tracking uncertainty (Eq. 6 residual, Eq. 15 sigma^2 = 2R, motion mask) of
+    the last step's rendered views against the targets, through the public API:
+    CUDA events over repeated launches on the launch stream (inputs of
+    ~0.4 GB, larger than L2).  Algorithmic bytes per pixel: the rendered colour,
+    depth, T and N_l features and the target colour, depth and features read
+    once (the 3x3 depth window through L1), R, sigma^2 (float) and the mask
+    (byte) written."""
+    import torch
+    img = dict(color=st.img["color"], depth=st.img["depth"], feat=st.img["feat"], T=st.img["T"])
+    out = dict(R=torch.empty_like(img["depth"]), sigma2=torch.empty_like(img["depth"]),
+               motion=torch.empty(img["depth"].shape, dtype=torch.uint8, device=img["depth"].device))
+    for _ in range(3):
+        st.R.tracking_uncertainty(img, st.tgt, out=out)
+    n = max(10, args.steps)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        st.R.tracking_uncertainty(img, st.tgt, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    NF = wl["NF"]
+    pix = wl["V"] * wl["W"] * wl["H"]
+    bpp = 4 * ((3 + 1 + 1 + NF) + (3 + 1 + NF)) + 4 + 4 + 1
+    return dict(ms=round(ms, 4), pixels=pix, bytes_per_pixel=bpp, bound="hbm",
+                achieved_gbs=round(pix * bpp / (ms / 1e3) / 1e9, 1), unit="GB/s",
+                motion_frac=round(float(out["motion"].float().mean().item()), 4))
 
 
 def run_e2e(args, st, anc, mlp, tg, world):

@@ -242,6 +242,33 @@ ups_status ups_loss_weighted(ups_ctx *ctx, const ups_images *img, const ups_targ
                              const ups_loss_cfg *lcfg, const ups_gaussians *g,
                              float *loss_dev, ups_images *dL, ups_stream stream);
 
+/* Training-free tracking uncertainty (Sec. 3.4 "Tracking", Eq. 6, Eq. 15) of
+ * the last forward's images against tgt (color, depth, feat; weight unused),
+ * per pixel:
+ *   R      = (T < t_mask) (lambda_color |C~ - C|_1 + lambda_depth |D~ - B(D)|
+ *                          + lambda_feat min(1, 1 - cos(F, F~)))
+ *   sigma2 = 2 R     (Eq. 15 minimises 1/2 (R / sigma^2 + log sigma) per pixel;
+ *                     R = 0 gives the limit 0)
+ *   motion = 2 sigma2 > 1, i.e. R > 1/4 (1: dynamic)
+ * Readings: T is the final transmittance (Eq. 3's T~ read as transmittance, so
+ * the mask keeps covered pixels); |.|_1 sums the colour channels; B is the 3x3
+ * box filter of the target depth, the mean over the window's pixels inside the
+ * view; cos = 0 when either feature vector is zero; n_feat == 0: no feature
+ * term.  img needs color, depth, T (and feat); outputs are device arrays of
+ * sum_v H_v W_v in the depth layout (R, sigma2 float; motion uint8), each may
+ * be NULL.  Defaults (Sec. 4 "Implementation Details"): lambda = (0.25, 0.7,
+ * 0.1), t_mask = 0.1. */
+typedef struct {
+    float lambda_color;
+    float lambda_depth;
+    float lambda_feat;
+    float t_mask;
+} ups_residual_cfg;
+
+ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const ups_targets *tgt,
+                                    const ups_residual_cfg *rcfg, float *R, float *sigma2,
+                                    unsigned char *motion, ups_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */

@@ -9,7 +9,8 @@ per call); this module marshals numpy arrays through ctypes and composes the
 per-view steps into the full loss and its gradients:
 
   decode (Eq. 8-9) -> project (Eq. 1-2) -> blend (Eq. 3, Eq. 10)
-  -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step.
+  -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step;
+  and the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser) in numpy.
 """
 from __future__ import annotations
 
@@ -237,6 +238,63 @@ def loss_view(img, tgt, lcfg: LossCfg, n_feat, norm):
                             int(lcfg.l2), C.c_double(norm), pgc, pgd,
                             pgf if n_feat else None)
     return L, dict(color=gc, depth=gd, feat=gf)
+
+
+@dataclass
+class ResidualCfg:
+    """Residual weights and visibility threshold of the tracking uncertainty
+    (Eq. 6; the values of Sec. 4 "Implementation Details")."""
+    lambda_color: float = 0.25
+    lambda_depth: float = 0.7
+    lambda_feat: float = 0.1
+    t_mask: float = 0.1
+
+
+def box3(d):
+    """B (Eq. 6): 3x3 box filter, the mean over the window's pixels inside the
+    image (reading: the window is cut at the border, not padded)."""
+    H, W = d.shape
+    s = np.zeros((H, W))
+    n = np.zeros((H, W))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ys = slice(max(0, -dy), H - max(0, dy))   # pixels whose neighbour (y+dy, x+dx) is inside
+            xs = slice(max(0, -dx), W - max(0, dx))
+            yn = slice(max(0, dy), H - max(0, -dy))   # those neighbours
+            xn = slice(max(0, dx), W - max(0, -dx))
+            s[ys, xs] += d[yn, xn]
+            n[ys, xs] += 1.0
+    return s / n
+
+
+def tracking_uncertainty(img, tgt, rcfg: ResidualCfg, n_feat):
+    """Training-free uncertainty of one view (Sec. 3.4 "Tracking").
+
+    Eq. 6:  R = (T < t_mask) (l1 |C~ - C|_1 + l2 |D~ - B(D)| + l3 ceil1(1 - cos(F, F~)))
+    with T the final transmittance (Eq. 3's T~ read as transmittance: the mask
+    keeps covered pixels), |.|_1 the sum over the colour channels, ceil1 the cap
+    at 1, and cos = 0 when either feature vector is zero.
+    Eq. 15 minimises 1/2 (R / sigma^2 + log sigma) pixel by pixel; setting the
+    derivative 1/2 (-2R / sigma^3 + 1 / sigma) to zero gives sigma^2 = 2R (R = 0:
+    the limit 0), and the motion mask 2 sigma^2 > 1 (Sec. 3.3) is R > 1/4.
+    Returns R, sigma2 and the motion mask (uint8) as [H, W] arrays."""
+    rc = np.abs(img["color"] - tgt["color"]).sum(axis=0)
+    rd = np.abs(img["depth"] - box3(tgt["depth"]))
+    if n_feat:
+        f, fh = tgt["feat"], img["feat"]
+        dot = (f * fh).sum(axis=0)
+        na = np.sqrt((f * f).sum(axis=0))
+        nb = np.sqrt((fh * fh).sum(axis=0))
+        ok = (na > 0) & (nb > 0)
+        cos = np.where(ok, dot / np.where(ok, na * nb, 1.0), 0.0)
+        rf = np.minimum(1.0, 1.0 - cos)
+    else:
+        rf = np.zeros_like(rd)
+    R = np.where(img["T"] < rcfg.t_mask,
+                 rcfg.lambda_color * rc + rcfg.lambda_depth * rd + rcfg.lambda_feat * rf, 0.0)
+    sigma2 = 2.0 * R
+    motion = (2.0 * sigma2 > 1.0).astype(np.uint8)
+    return R, sigma2, motion
 
 
 def render_bwd(proj, g, cam, cfg: RenderCfg, n_feat, grads_img):

@@ -52,6 +52,10 @@ class Targets(C.Structure):
     _fields_ = [("color", _p), ("depth", _p), ("feat", _p), ("weight", _p)]
 
 
+class ResidualCfg(C.Structure):
+    _fields_ = [("lambda_color", _f), ("lambda_depth", _f), ("lambda_feat", _f), ("t_mask", _f)]
+
+
 class LossCfg(C.Structure):
     _fields_ = [("lambda_color", _f), ("lambda_depth", _f), ("lambda_feat", _f),
                 ("lambda_scale", _f), ("l2", _i)]
@@ -90,7 +94,7 @@ class Stats(C.Structure):
 
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
-           "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted",
+           "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted", "ups_tracking_uncertainty",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
@@ -125,6 +129,8 @@ def load():
                                      C.POINTER(Images), _p]
     L.ups_loss_weighted.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(LossCfg),
                                     C.POINTER(Gaussians), _p, C.POINTER(Images), _p]
+    L.ups_tracking_uncertainty.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(ResidualCfg),
+                                           _p, _p, _p, _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
                                       C.POINTER(Gaussians), _p, _p]
     L.ups_decode_backward.argtypes = [_p, C.POINTER(Anchors), C.POINTER(MLP), C.POINTER(Camera), _i,
@@ -315,6 +321,24 @@ class Renderer:
                                               C.byref(cg) if cg is not None else None,
                                               _ptr(loss_out), C.byref(cd), _stream(stream)))
         return loss_out, grad_out
+
+    def tracking_uncertainty(self, img, tgt, lambda_color=0.25, lambda_depth=0.7, lambda_feat=0.1, t_mask=0.1,
+                             out=None, stream=None):
+        """Eq. 6 residual R, Eq. 15 sigma^2 = 2R and the motion mask R > 1/4 of the
+        last forward's images (dict with color, depth, feat, T) against tgt."""
+        import torch
+        dev = img["depth"].device
+        if out is None:
+            out = dict(R=torch.empty_like(img["depth"]), sigma2=torch.empty_like(img["depth"]),
+                       motion=torch.empty(img["depth"].shape, dtype=torch.uint8, device=dev))
+        ci = Images(_ptr(img["color"]), _ptr(img["depth"]), _ptr(img["feat"]) if self.n_feat else None,
+                    _ptr(img["T"]), None)
+        ct = Targets(_ptr(tgt["color"]), _ptr(tgt["depth"]), _ptr(tgt["feat"]) if self.n_feat else None, None)
+        rc = ResidualCfg(lambda_color, lambda_depth, lambda_feat, t_mask)
+        self._check(self._L.ups_tracking_uncertainty(self._h, C.byref(ci), C.byref(ct), C.byref(rc),
+                                                     _ptr(out.get("R")), _ptr(out.get("sigma2")),
+                                                     _ptr(out.get("motion")), _stream(stream)))
+        return out
 
     # -------------------------------------------------------------- backward
     def backward(self, dL, mask=GRAD_POSE | GRAD_GAUSS, scale_grad=0.0, grad: GaussianSet | None = None,

@@ -38,6 +38,9 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
                                  const int *gate = nullptr);
+cudaError_t launch_uncertainty(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
+                               float t_mask, const ups_images &img, const ups_targets &tgt, float *R, float *sigma2,
+                               uint8_t *motion, cudaStream_t st);
 cudaError_t launch_loss(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                         int l2, float inv_norm, const ups_images &img, const ups_targets &tgt,
                         const ups_images &grad, float *loss, cudaStream_t st, int v0 = 0, int v1 = -1);
@@ -571,6 +574,27 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     c->g_in = *g;
     c->img = *out;
     c->have_fwd = true;
+    return UPS_OK;
+}
+
+ups_status ups_tracking_uncertainty(ups_ctx *c, const ups_images *img, const ups_targets *tgt,
+                                    const ups_residual_cfg *rcfg, float *R, float *sigma2,
+                                    unsigned char *motion, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_tracking_uncertainty needs a forward first");
+    if (!img || !tgt || !rcfg) return fail(c, UPS_ERR_ARG, "NULL argument");
+    const int nf = c->cfg.n_feat;
+    if (!img->color || !img->depth || !img->T || !tgt->color || !tgt->depth ||
+        (nf > 0 && (!img->feat || !tgt->feat)))
+        return fail(c, UPS_ERR_ARG, "NULL image pointer");
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    stage_begin(c, "uncertainty", st);
+    UPS_CUDA(c, launch_uncertainty(c->vt, nf, c->max_hw, rcfg->lambda_color, rcfg->lambda_depth, rcfg->lambda_feat,
+                                   rcfg->t_mask, *img, *tgt, R, sigma2, motion, st));
+    stage_end(c, st, 1);
     return UPS_OK;
 }
 
