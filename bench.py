@@ -284,8 +284,9 @@ def run_ours(args, wl_name):
     proc = processed_instances(st.img, cams)
     evals = evaluations(st.img)
 
-    # the next row of the path, timed on its own (not part of the mapping step)
+    # the next rows of the path, timed on their own (not part of the mapping step)
     unc = run_uncertainty(args, st, wl)
+    lift = run_lift(args, st, wl)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -324,7 +325,11 @@ def run_ours(args, wl_name):
             "e2e": e2e,
             "next_rows": {"tracking_uncertainty": dict(unc, peak=round(peaks["hbm_gbs"], 1),
                                                        frac=round(unc["achieved_gbs"] / peaks["hbm_gbs"], 4),
-                                                       peak_source=peaks["source"])},
+                                                       peak_source=peaks["source"]),
+                          "feature_lifting": dict(lift, peak=round(peaks["bf16_tflops_sustained"] / 2, 1),
+                                                  frac=round(lift["achieved_tflops"]
+                                                             / (peaks["bf16_tflops_sustained"] / 2), 4),
+                                                  peak_source=peaks["source"] + " bf16 sustained x 1/2 (TF32)")},
         }
         print(json.dumps(line))
     if world > 1:
@@ -386,6 +391,47 @@ def run_uncertainty(args, st, wl):
     return dict(ms=round(ms, 4), pixels=pix, bytes_per_pixel=bpp, bound="hbm",
                 achieved_gbs=round(pix * bpp / (ms / 1e3) / 1e9, 1), unit="GB/s",
                 motion_frac=round(float(out["motion"].float().mean().item()), 4))
+
+
+def run_lift(args, st, wl, n_h=384, patch=14):
+    """Feature lifting F_m and distillation loss L_d (Eq. 11-12), forward and
+    backward (weight and feature-map gradients) on the last step's rendered
+    feature map against a seeded synthetic DINO patch grid (n_h = 384, patch
+    14), through the public API; CUDA events over repeated calls.  Algorithmic
+    FLOPs per pixel: 2 (N_l 128 + 128 n_h) forward, 2 (2 128 n_h + 2 N_l 128)
+    backward."""
+    import torch
+    NF = wl["NF"]
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    grids = sum(-(-wl["H"] // patch) * -(-wl["W"] // patch) for _ in range(wl["V"])) * n_h
+    dino = torch.randn(grids, generator=gen, device="cuda")
+    mlp = dict(w1=torch.randn(128, NF, generator=gen, device="cuda") * 0.3,
+               b1=torch.randn(128, generator=gen, device="cuda") * 0.1,
+               w2=torch.randn(n_h, 128, generator=gen, device="cuda") * 0.1,
+               b2=torch.randn(n_h, generator=gen, device="cuda") * 0.1)
+    dmlp = {k: torch.zeros_like(v) for k, v in mlp.items()}
+    dfeat = torch.zeros_like(st.img["feat"])
+    loss = torch.zeros(1, device="cuda")
+    call = lambda: st.R.feature_lift(st.img["feat"], dino, mlp, n_h=n_h, patch=patch, scale=0.4, d_mlp=dmlp,
+                                     d_feat=dfeat, loss_out=loss)
+    for _ in range(3):
+        call()
+    n = max(5, args.steps // 2)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    pix = wl["V"] * wl["W"] * wl["H"]
+    fpp = 2 * (NF * 128 + 128 * n_h) + 2 * (2 * 128 * n_h + 2 * NF * 128)
+    return dict(ms=round(ms, 4), pixels=pix, n_h=n_h, flops_per_pixel=fpp, bound="tensor",
+                achieved_tflops=round(pix * fpp / (ms / 1e3) / 1e12, 2), unit="TFLOP/s",
+                loss=round(float(loss.item()), 6), gemm="cuBLAS TF32 (tensor cores)")
 
 
 def run_e2e(args, st, anc, mlp, tg, world):

@@ -269,6 +269,42 @@ ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const u
                                     const ups_residual_cfg *rcfg, float *R, float *sigma2,
                                     unsigned char *motion, ups_stream stream);
 
+/* Feature lifting and distillation (Sec. 3.3, Eq. 11, Eq. 12; App. "MLP
+ * Implementation Details"): F^ = F_m(F~) per pixel of the last forward's
+ * rendered feature map F~ (n_feat channels), F_m = 1x1 convolution (n_feat ->
+ * 128) -> ReLU -> 1x1 convolution (128 -> n_h), and
+ *   L_d = (1 / P) sum_p (1 - cos(F_p, F^_p))     (P: pixels of all views)
+ * against the DINO features F, given per view on the patch grid (Sec. 3.2:
+ * bilinear upsampling to the image): view v's grid is hp x wp = ceil(H/patch)
+ * x ceil(W/patch) vectors of n_h floats, row-major [hp][wp][n_h], the views'
+ * grids concatenated; pixel (x, y) samples it at ((x + 0.5)/patch - 0.5,
+ * (y + 0.5)/patch - 0.5), clamped to the grid.  cos = 0 (and no gradient)
+ * where either vector is zero.  The layers and their backward run as TF32
+ * tensor-core GEMMs.
+ *  feat      rendered F~ in the image layout (n_feat planes per view)
+ *  mlp       w1 [128][n_feat], b1 [128], w2 [n_h][128], b2 [n_h]
+ *  scale     weight of L_d (e.g. lambda_4 of Eq. 14)
+ *  loss_dev  device float: overwritten with scale * L_d
+ *  d_mlp     if not NULL: scale * dL_d/d(w1, b1, w2, b2) ADDED to its arrays
+ *            (each may be NULL)
+ *  d_feat    if not NULL: scale * dL_d/dF~ ADDED (image layout), e.g. to the
+ *            image loss's feature gradient before ups_render_backward */
+typedef struct {
+    int n_h;    /* DINO feature width (384) */
+    int patch;  /* DINO patch size in pixels (14) */
+} ups_lift_cfg;
+
+typedef struct {
+    float *w1;
+    float *b1;
+    float *w2;
+    float *b2;
+} ups_lift_mlp;
+
+ups_status ups_feature_lift(ups_ctx *ctx, const ups_lift_cfg *lcfg, const float *feat, const float *dino,
+                            const ups_lift_mlp *mlp, float scale, float *loss_dev, ups_lift_mlp *d_mlp,
+                            float *d_feat, ups_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */

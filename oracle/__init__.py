@@ -10,7 +10,8 @@ per-view steps into the full loss and its gradients:
 
   decode (Eq. 8-9) -> project (Eq. 1-2) -> blend (Eq. 3, Eq. 10)
   -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step;
-  and the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser) in numpy.
+  and, in numpy, the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser)
+  and the feature lifting with its distillation loss (Eq. 11-12).
 """
 from __future__ import annotations
 
@@ -295,6 +296,62 @@ def tracking_uncertainty(img, tgt, rcfg: ResidualCfg, n_feat):
     sigma2 = 2.0 * R
     motion = (2.0 * sigma2 > 1.0).astype(np.uint8)
     return R, sigma2, motion
+
+
+@dataclass
+class LiftCfg:
+    """DINO feature width and patch size of the feature lifting (Eq. 11-12)."""
+    n_h: int = 384
+    patch: int = 14
+
+
+def dino_upsample(grid, H, W, patch):
+    """Sec. 3.2: DINO features are per image patch and bilinearly upsampled to
+    the image.  grid [hp][wp][n_h]; pixel (x, y) samples it at
+    ((x + 0.5) / patch - 0.5, (y + 0.5) / patch - 0.5), clamped to the grid.
+    Returns [n_h][H][W]."""
+    hp, wp, _ = grid.shape
+    u = np.clip((np.arange(W) + 0.5) / patch - 0.5, 0.0, wp - 1)
+    v = np.clip((np.arange(H) + 0.5) / patch - 0.5, 0.0, hp - 1)
+    x0 = np.floor(u).astype(int); y0 = np.floor(v).astype(int)
+    x1 = np.minimum(x0 + 1, wp - 1); y1 = np.minimum(y0 + 1, hp - 1)
+    ax = (u - x0)[None, :, None]; ay = (v - y0)[:, None, None]
+    top = (1 - ax) * grid[y0][:, x0] + ax * grid[y0][:, x1]
+    bot = (1 - ax) * grid[y1][:, x0] + ax * grid[y1][:, x1]
+    return np.moveaxis((1 - ay) * top + ay * bot, 2, 0)
+
+
+def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0):
+    """Feature lifting and distillation of one view (Sec. 3.3, Eq. 11-12; App.
+    "MLP Implementation Details": F_m = conv -> ReLU -> conv, hidden 128, read as
+    1x1 convolutions, i.e. the same MLP at every pixel).
+
+    F^_p = W2 relu(W1 F~_p + b1) + b2;  loss = scale / n_pix * sum_p (1 - cos(F_p, F^_p))
+    (n_pix: pixels of all views; cos = 0, and no gradient, where a vector is 0),
+    with F the upsampled DINO feature.  Returns the loss contribution and
+    scale * d(loss)/d(w1, b1, w2, b2, feat)."""
+    nf, H, W = feat.shape
+    X = feat.reshape(nf, H * W).T                       # [P][nf]
+    Z = X @ mlp["w1"].T + mlp["b1"]                     # [P][128]
+    Hh = np.maximum(Z, 0.0)
+    Fh = Hh @ mlp["w2"].T + mlp["b2"]                   # [P][n_h]
+    T = dino_upsample(grid, H, W, lcfg.patch).reshape(lcfg.n_h, H * W).T
+    na = np.sqrt((T * T).sum(1)); nb = np.sqrt((Fh * Fh).sum(1))
+    ok = (na > 0) & (nb > 0)
+    den = np.where(ok, na * nb, 1.0)
+    cos = np.where(ok, (T * Fh).sum(1) / den, 0.0)
+    g = scale / n_pix
+    loss = g * (1.0 - cos).sum()
+    # d(1 - cos)/dF^ = cos F^ / |F^|^2 - F / (|F| |F^|)
+    nb2 = np.where(ok, nb * nb, 1.0)
+    dFh = np.where(ok[:, None], g * (cos[:, None] * Fh / nb2[:, None] - T / den[:, None]), 0.0)
+    dW2 = dFh.T @ Hh
+    db2 = dFh.sum(0)
+    dZ = (dFh @ mlp["w2"]) * (Z > 0)
+    dW1 = dZ.T @ X
+    db1 = dZ.sum(0)
+    dX = dZ @ mlp["w1"]
+    return loss, dict(w1=dW1, b1=db1, w2=dW2, b2=db2, feat=dX.T.reshape(nf, H, W))
 
 
 def render_bwd(proj, g, cam, cfg: RenderCfg, n_feat, grads_img):

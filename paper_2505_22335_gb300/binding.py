@@ -56,6 +56,14 @@ class ResidualCfg(C.Structure):
     _fields_ = [("lambda_color", _f), ("lambda_depth", _f), ("lambda_feat", _f), ("t_mask", _f)]
 
 
+class LiftCfg(C.Structure):
+    _fields_ = [("n_h", _i), ("patch", _i)]
+
+
+class LiftMLP(C.Structure):
+    _fields_ = [("w1", _p), ("b1", _p), ("w2", _p), ("b2", _p)]
+
+
 class LossCfg(C.Structure):
     _fields_ = [("lambda_color", _f), ("lambda_depth", _f), ("lambda_feat", _f),
                 ("lambda_scale", _f), ("l2", _i)]
@@ -95,6 +103,7 @@ class Stats(C.Structure):
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted", "ups_tracking_uncertainty",
+           "ups_feature_lift",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
@@ -131,6 +140,8 @@ def load():
                                     C.POINTER(Gaussians), _p, C.POINTER(Images), _p]
     L.ups_tracking_uncertainty.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(ResidualCfg),
                                            _p, _p, _p, _p]
+    L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _p,
+                                   C.POINTER(LiftMLP), _p, _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
                                       C.POINTER(Gaussians), _p, _p]
     L.ups_decode_backward.argtypes = [_p, C.POINTER(Anchors), C.POINTER(MLP), C.POINTER(Camera), _i,
@@ -339,6 +350,21 @@ class Renderer:
                                                      _ptr(out.get("R")), _ptr(out.get("sigma2")),
                                                      _ptr(out.get("motion")), _stream(stream)))
         return out
+
+    def feature_lift(self, feat, dino, mlp, n_h=384, patch=14, scale=1.0, d_mlp=None, d_feat=None,
+                     loss_out=None, stream=None):
+        """Eq. 11-12: scale * L_d of the rendered feature map `feat` (image layout)
+        against the per-view DINO patch grids `dino` (concatenated [hp][wp][n_h]);
+        mlp / d_mlp: dicts w1, b1, w2, b2 (d_mlp and d_feat are accumulated)."""
+        import torch
+        loss_out = loss_out if loss_out is not None else torch.zeros(1, dtype=torch.float32, device=feat.device)
+        cm = LiftMLP(*(_ptr(mlp[k]) for k in ("w1", "b1", "w2", "b2")))
+        dm = LiftMLP(*(_ptr(d_mlp.get(k)) for k in ("w1", "b1", "w2", "b2"))) if d_mlp is not None else None
+        self._check(self._L.ups_feature_lift(self._h, C.byref(LiftCfg(n_h, patch)), _ptr(feat), _ptr(dino),
+                                             C.byref(cm), float(scale), _ptr(loss_out),
+                                             C.byref(dm) if dm is not None else None, _ptr(d_feat),
+                                             _stream(stream)))
+        return loss_out
 
     # -------------------------------------------------------------- backward
     def backward(self, dL, mask=GRAD_POSE | GRAD_GAUSS, scale_grad=0.0, grad: GaussianSet | None = None,

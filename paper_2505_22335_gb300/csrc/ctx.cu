@@ -38,6 +38,13 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
                                  const int *gate = nullptr);
+size_t lift_scratch_floats(size_t max_hw, int nh);
+cudaError_t lift_handle(void **handle);
+void lift_handle_destroy(void *handle);
+cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
+                      const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
+                      const float *b2, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
+                      float *d_feat, float *scratch, int *launches);
 cudaError_t launch_uncertainty(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                                float t_mask, const ups_images &img, const ups_targets &tgt, float *R, float *sigma2,
                                uint8_t *motion, cudaStream_t st);
@@ -119,6 +126,8 @@ struct ups_ctx {
     int *d_trunc_flag = nullptr;  // set by the forward blend: a capped list was too short
     DevBuf trunc;                 // per-tile bit: the list cap cut the tile's list
     bool capped = false;          // the last forward capped its tile lists
+    void *cublas = nullptr;       // cuBLAS handle of the feature lifting (created on first use)
+    DevBuf lift_scr;              // feature-lifting scratch of one view
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
     struct Rec {
@@ -380,11 +389,12 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_trunc_flag) cudaFree(c->d_trunc_flag);
+    lift_handle_destroy(c->cublas);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -595,6 +605,42 @@ ups_status ups_tracking_uncertainty(ups_ctx *c, const ups_images *img, const ups
     UPS_CUDA(c, launch_uncertainty(c->vt, nf, c->max_hw, rcfg->lambda_color, rcfg->lambda_depth, rcfg->lambda_feat,
                                    rcfg->t_mask, *img, *tgt, R, sigma2, motion, st));
     stage_end(c, st, 1);
+    return UPS_OK;
+}
+
+ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *feat, const float *dino,
+                            const ups_lift_mlp *mlp, float scale, float *loss_dev, ups_lift_mlp *d_mlp,
+                            float *d_feat, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_feature_lift needs a forward first");
+    if (!lcfg || !feat || !dino || !mlp || !mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2 || !loss_dev)
+        return fail(c, UPS_ERR_ARG, "NULL argument");
+    const int nf = c->cfg.n_feat;
+    if (nf <= 0) return fail(c, UPS_ERR_ARG, "feature lifting needs n_feat > 0");
+    if (lcfg->n_h < 1 || lcfg->n_h > 4096 || lcfg->patch < 1) return fail(c, UPS_ERR_ARG, "n_h or patch out of range");
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, lift_handle(&c->cublas));
+    UPS_CUDA(c, c->lift_scr.reserve(lift_scratch_floats((size_t)c->max_hw, lcfg->n_h) * sizeof(float)));
+    stage_begin(c, "lift", st);
+    UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
+    const float g = (float)((double)scale / (double)c->n_pix);
+    size_t grid_off = 0;
+    int launches = 0;
+    for (int v = 0; v < c->vt.n; ++v) {
+        const DevView &cam = c->vt.v[v];
+        const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
+        const size_t P = (size_t)cam.pix_off;
+        UPS_CUDA(c, lift_view(c->cublas, st, cam.W, cam.H, nf, lcfg->n_h, lcfg->patch, feat + (size_t)nf * P,
+                              dino + grid_off, wp, hp, mlp->w1, mlp->b1, mlp->w2, mlp->b2, g, loss_dev,
+                              d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr,
+                              d_mlp ? d_mlp->b2 : nullptr, d_feat ? d_feat + (size_t)nf * P : nullptr,
+                              c->lift_scr.as<float>(), &launches));
+        grid_off += (size_t)hp * wp * lcfg->n_h;
+    }
+    stage_end(c, st, launches);
     return UPS_OK;
 }
 

@@ -1,0 +1,102 @@
+"""Feature lifting and distillation on the GPU (Sec. 3.3, Eq. 11-12) against the
+FP64 oracle, both fed the same seeded synthetic feature maps, DINO patch grids
+and MLP weights (a forward on the same cameras only sets up the views).
+
+The layers run as TF32 tensor-core GEMMs: each product sees both operands
+rounded to 11 significant bits (unit roundoff u = 2^-11 ~ 4.9e-4, FP32
+accumulation).  The bars follow the chain of rounded GEMMs behind each output:
+the loss and dL/dF^ (hence dW2, db2, sums over all pixels) carry one rounded
+layer, ~u: bar 1e-3; dZ = (dL/dF^ W2) relu' adds a rounded product summed over
+n_h mixed-sign terms (db1: 5e-3, dW1 = F~^T dZ: 2e-2); dL/dF~ = dZ W1 sums 128
+mixed-sign terms per pixel, which amplifies the relative error by ~sqrt(128)
+~ 11: bar 5e-2.  Measured (printed): loss <= 1e-5, dW2/db2 <= 1e-4, db1 <=
+1.7e-3, dW1 <= 8.6e-3, dF~ <= 1.7e-2."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_cases import rel_l2, round_cams
+from paper_2505_22335_gb300 import binding as B
+from paper_2505_22335_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+LOSS_RTOL = 1e-3
+GRAD_RTOL = dict(w2=1e-3, b2=1e-3, b1=5e-3, w1=2e-2, feat=5e-2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def run_case(cams, nf, nh, patch, seed, scale=0.4):
+    import torch
+    cams = round_cams(cams)
+    rng = np.random.default_rng(seed)
+    R = B.Renderer(n_feat=nf, k=1)
+    R.forward(B.to_set(scenes.plain_gaussians(seed, 100, nf)), cams)
+    mlp = dict(w1=f32(rng.normal(size=(128, nf)) * 0.3), b1=f32(rng.normal(size=128) * 0.1),
+               w2=f32(rng.normal(size=(nh, 128)) * 0.1), b2=f32(rng.normal(size=nh) * 0.1))
+    feats = [f32(rng.normal(size=(nf, c.height, c.width))) for c in cams]
+    grids = [f32(rng.normal(size=(-(-c.height // patch), -(-c.width // patch), nh))) for c in cams]
+    n_pix = sum(c.width * c.height for c in cams)
+    # d_feat is accumulated: pre-filled at the gradient's own scale (scale / n_pix), so
+    # that FP32 keeps the added gradient when the test subtracts the pre-fill
+    prefill = [f32(rng.normal(size=(nf, c.height, c.width)) * scale / n_pix) for c in cams]
+    dev = lambda arrs: torch.tensor(np.concatenate([a.reshape(-1) for a in arrs]), dtype=torch.float32,
+                                    device="cuda")
+    dmlp = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in mlp.items()}
+    dfeat = dev(prefill)
+    loss = R.feature_lift(dev(feats), dev(grids), {k: dev([v]) for k, v in mlp.items()}, n_h=nh, patch=patch,
+                          scale=scale, d_mlp=dmlp, d_feat=dfeat)
+    torch.cuda.synchronize()
+    ref = {k: np.zeros_like(v) for k, v in mlp.items()}
+    ref_loss = 0.0
+    dfeat_ref = []
+    for c, fe, gr in zip(cams, feats, grids):
+        l, g = oracle.feature_lift(fe, gr, mlp, oracle.LiftCfg(n_h=nh, patch=patch), n_pix, scale)
+        ref_loss += l
+        for k in ref:
+            ref[k] += g[k]
+        dfeat_ref.append(g["feat"])
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in dmlp.items()}
+    got["feat"] = dfeat.cpu().numpy().astype(np.float64) - np.concatenate([p.reshape(-1) for p in prefill])
+    ref["feat"] = np.concatenate([d.reshape(-1) for d in dfeat_ref])
+    errs = {k: rel_l2(got[k], ref[k]) for k in ref}
+    lerr = abs(float(loss.item()) - ref_loss) / abs(ref_loss)
+    print(f"nf={nf} nh={nh} loss rel {lerr:.2e}", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert lerr < LOSS_RTOL, (float(loss.item()), ref_loss)
+    assert all(errs[k] < GRAD_RTOL[k] for k in errs), errs
+    return errs
+
+
+def test_ragged_views_small_nh():
+    cams = scenes.cameras(3, 2, 30, 20, 40.0)
+    cams[1] = cams[1].scaled(0.6)
+    run_case(cams, 16, 64, 14, 5)
+
+
+def test_dino_width_384_feat32():
+    cams = scenes.cameras(4, 2, 47, 33, 50.0)
+    run_case(cams, 32, 384, 14, 6)
+
+
+def test_full_view_640x480():
+    cams = scenes.cameras(0, 1, 640, 480, 600.0, identity=True)
+    run_case(cams, 16, 384, 14, 7, scale=0.4)
+
+
+def test_rejects_renderer_without_features():
+    import torch
+    R = B.Renderer(n_feat=0, k=1)
+    cams = round_cams(scenes.cameras(4, 1, 16, 16, 20.0))
+    R.forward(B.to_set(scenes.plain_gaussians(1, 10, 0)), cams)
+    z = torch.zeros(16, device="cuda")
+    with pytest.raises(B.UpsError):
+        R.feature_lift(z, z, dict(w1=z, b1=z, w2=z, b2=z), n_h=8)
