@@ -282,7 +282,8 @@ ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const u
  * where either vector is zero.  The layers and their backward run as TF32
  * tensor-core GEMMs.
  *  feat      rendered F~ in the image layout (n_feat planes per view)
- *  mlp       w1 [128][n_feat], b1 [128], w2 [n_h][128], b2 [n_h]
+ *  dino      the patch grids (16-byte aligned; UPS_ERR_ARG otherwise)
+ *  mlp       w1 [128][n_feat], b1 [128], w2 [n_h][128], b2 [n_h] (b2 16-byte aligned)
  *  scale     weight of L_d (e.g. lambda_4 of Eq. 14)
  *  loss_dev  device float: overwritten with scale * L_d
  *  d_mlp     if not NULL: scale * dL_d/d(w1, b1, w2, b2) ADDED to its arrays
@@ -290,7 +291,7 @@ ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const u
  *  d_feat    if not NULL: scale * dL_d/dF~ ADDED (image layout), e.g. to the
  *            image loss's feature gradient before ups_render_backward */
 typedef struct {
-    int n_h;    /* DINO feature width (384) */
+    int n_h;    /* DINO feature width (384): a multiple of 4, at most 4096 */
     int patch;  /* DINO patch size in pixels (14) */
 } ups_lift_cfg;
 

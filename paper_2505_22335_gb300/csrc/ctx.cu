@@ -617,7 +617,10 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
         return fail(c, UPS_ERR_ARG, "NULL argument");
     const int nf = c->cfg.n_feat;
     if (nf <= 0) return fail(c, UPS_ERR_ARG, "feature lifting needs n_feat > 0");
-    if (lcfg->n_h < 1 || lcfg->n_h > 4096 || lcfg->patch < 1) return fail(c, UPS_ERR_ARG, "n_h or patch out of range");
+    if (lcfg->n_h < 4 || lcfg->n_h > 4096 || lcfg->n_h % 4 != 0 || lcfg->patch < 1)
+        return fail(c, UPS_ERR_ARG, "n_h must be a multiple of 4 in [4, 4096] and patch >= 1");
+    if (reinterpret_cast<uintptr_t>(dino) % 16 != 0 || reinterpret_cast<uintptr_t>(mlp->b2) % 16 != 0)
+        return fail(c, UPS_ERR_ARG, "dino and mlp->b2 must be 16-byte aligned");
     ups_status s = set_device(c);
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

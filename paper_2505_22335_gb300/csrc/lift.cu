@@ -34,11 +34,23 @@ __global__ void k_relu_mask(float *__restrict__ dh, const float *__restrict__ h,
         if (!(h[i] > 0.f)) dh[i] = 0.f;
 }
 
-// out[r] += sum_p m[r * HW + p]: one block per row
+// out[r] += sum_p m[r * HW + p]: blockIdx.y = row, blockIdx.x = a chunk of
+// kSumChunk pixels, one atomic per block
+constexpr int kSumChunk = 8192;
 __global__ void __launch_bounds__(256) k_row_sums(const float *__restrict__ m, size_t HW, float *__restrict__ out) {
-    const float *row = m + (size_t)blockIdx.x * HW;
-    float s = 0.f;
-    for (size_t p = threadIdx.x; p < HW; p += blockDim.x) s += row[p];
+    const float *row = m + (size_t)blockIdx.y * HW;
+    const size_t p0 = (size_t)blockIdx.x * kSumChunk;
+    const size_t p1 = min(HW, p0 + kSumChunk);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    size_t p = p0 + threadIdx.x;
+    for (; p + 768 < p1; p += 1024) {
+        s0 += row[p];
+        s1 += row[p + 256];
+        s2 += row[p + 512];
+        s3 += row[p + 768];
+    }
+    for (; p < p1; p += 256) s0 += row[p];
+    float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ float red[8];
@@ -47,7 +59,7 @@ __global__ void __launch_bounds__(256) k_row_sums(const float *__restrict__ m, s
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(out + blockIdx.x, t);
+        atomicAdd(out + blockIdx.y, t);
     }
 }
 
@@ -71,26 +83,50 @@ __global__ void __launch_bounds__(256) k_lift_cos(float *__restrict__ fh, const 
         const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
         const float ax = u - (float)x0, ay = v - (float)y0;
         const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay), w10 = (1.f - ax) * ay, w11 = ax * ay;
-        const float *g00 = grid + ((size_t)y0 * wp + x0) * nh, *g01 = grid + ((size_t)y0 * wp + x1) * nh;
-        const float *g10 = grid + ((size_t)y1 * wp + x0) * nh, *g11 = grid + ((size_t)y1 * wp + x1) * nh;
+        // the four patch vectors, four channels per 16-byte load (nh % 4 == 0)
+        const float4 *g00 = reinterpret_cast<const float4 *>(grid + ((size_t)y0 * wp + x0) * nh);
+        const float4 *g01 = reinterpret_cast<const float4 *>(grid + ((size_t)y0 * wp + x1) * nh);
+        const float4 *g10 = reinterpret_cast<const float4 *>(grid + ((size_t)y1 * wp + x0) * nh);
+        const float4 *g11 = reinterpret_cast<const float4 *>(grid + ((size_t)y1 * wp + x1) * nh);
+        const float4 *b4 = reinterpret_cast<const float4 *>(b2);
+        auto target = [&](int q) {
+            const float4 a = __ldg(g00 + q), b = __ldg(g01 + q), c = __ldg(g10 + q), d = __ldg(g11 + q);
+            return make_float4(w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x,
+                               w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y,
+                               w00 * a.z + w01 * b.z + w10 * c.z + w11 * d.z,
+                               w00 * a.w + w01 * b.w + w10 * c.w + w11 * d.w);
+        };
         float dot = 0.f, na = 0.f, nb = 0.f;
-        for (int c = 0; c < nh; ++c) {
-            const float f = w00 * g00[c] + w01 * g01[c] + w10 * g10[c] + w11 * g11[c];
-            const float fb = fh[(size_t)c * HW + p] + b2[c];
-            dot = fmaf(f, fb, dot);
-            na = fmaf(f, f, na);
-            nb = fmaf(fb, fb, nb);
+        const int nq = nh >> 2;
+#pragma unroll 2
+        for (int q = 0; q < nq; ++q) {
+            const float4 f = target(q), bb = __ldg(b4 + q);
+            const float *col = fh + (size_t)(4 * q) * HW + p;
+            const float f4[4] = {f.x, f.y, f.z, f.w};
+            const float fb4[4] = {col[0] + bb.x, col[HW] + bb.y, col[2 * HW] + bb.z, col[3 * HW] + bb.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                dot = fmaf(f4[k], fb4[k], dot);
+                na = fmaf(f4[k], f4[k], na);
+                nb = fmaf(fb4[k], fb4[k], nb);
+            }
         }
         const bool ok = na > 0.f && nb > 0.f;
         const float ia = ok ? rsqrtf(na) : 0.f, ib = ok ? rsqrtf(nb) : 0.f;
         const float cs = dot * ia * ib;
         term = 1.f - cs;
         const float k1 = g * cs * ib * ib, k2 = g * ia * ib;
-        for (int c = 0; c < nh; ++c) {
-            const float f = w00 * g00[c] + w01 * g01[c] + w10 * g10[c] + w11 * g11[c];
-            const size_t i = (size_t)c * HW + p;
-            const float fb = fh[i] + b2[c];
-            fh[i] = ok ? k1 * fb - k2 * f : 0.f;
+#pragma unroll 2
+        for (int q = 0; q < nq; ++q) {
+            const float4 f = target(q), bb = __ldg(b4 + q);
+            float *col = fh + (size_t)(4 * q) * HW + p;
+            const float f4[4] = {f.x, f.y, f.z, f.w};
+            const float b4v[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float fb = col[k * HW] + b4v[k];
+                col[k * HW] = ok ? k1 * fb - k2 * f4[k] : 0.f;
+            }
         }
     }
 #pragma unroll
@@ -158,7 +194,7 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
     const bool want_w = d_w1 || d_b1 || d_w2 || d_b2;
     if (!want_w && !d_feat) return cudaSuccess;
     if (d_b2) {
-        k_row_sums<<<nh, blk, 0, st>>>(Fh, (size_t)HW, d_b2);
+        k_row_sums<<<dim3((unsigned)((HW + kSumChunk - 1) / kSumChunk), nh), blk, 0, st>>>(Fh, (size_t)HW, d_b2);
         ++*launches;
     }
     // dW2 += H^T dF^  ([128 x nh] column-major = [nh][128] row-major)
@@ -170,7 +206,7 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
         dZ, Hm, (size_t)NH * HW);
     ++*launches;
     if (d_b1) {
-        k_row_sums<<<NH, blk, 0, st>>>(dZ, (size_t)HW, d_b1);
+        k_row_sums<<<dim3((unsigned)((HW + kSumChunk - 1) / kSumChunk), NH), blk, 0, st>>>(dZ, (size_t)HW, d_b1);
         ++*launches;
     }
     // dW1 += F~^T dZ1 ([nf x 128] column-major = [128][nf] row-major)
