@@ -287,6 +287,7 @@ def run_ours(args, wl_name):
     # the next rows of the path, timed on their own (not part of the mapping step)
     unc = run_uncertainty(args, st, wl)
     lift = run_lift(args, st, wl)
+    ssim = run_ssim(args, st, wl)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -329,7 +330,10 @@ def run_ours(args, wl_name):
                           "feature_lifting": dict(lift, peak=round(peaks["bf16_tflops_sustained"] / 2, 1),
                                                   frac=round(lift["achieved_tflops"]
                                                              / (peaks["bf16_tflops_sustained"] / 2), 4),
-                                                  peak_source=peaks["source"] + " bf16 sustained x 1/2 (TF32)")},
+                                                  peak_source=peaks["source"] + " bf16 sustained x 1/2 (TF32)"),
+                          "dssim": dict(ssim, peak=round(peaks["hbm_gbs"], 1),
+                                        frac=round(ssim["achieved_gbs"] / peaks["hbm_gbs"], 4),
+                                        peak_source=peaks["source"])},
         }
         print(json.dumps(line))
     if world > 1:
@@ -432,6 +436,35 @@ def run_lift(args, st, wl, n_h=384, patch=14):
     return dict(ms=round(ms, 4), pixels=pix, n_h=n_h, flops_per_pixel=fpp, bound="tensor",
                 achieved_tflops=round(pix * fpp / (ms / 1e3) / 1e12, 2), unit="TFLOP/s",
                 loss=round(float(loss.item()), 6), gemm="cuBLAS TF32 (tensor cores)")
+
+
+def run_ssim(args, st, wl):
+    """The D-SSIM term of Eq. 4, forward and backward (gradient added to a
+    colour-gradient buffer), on the last step's rendered colour against the
+    target colour, through the public API; CUDA events over repeated calls.
+    Algorithmic bytes per channel-pixel: the forward reads both images and
+    writes the three window-term maps, the backward reads those maps and both
+    images and updates the gradient: 48 B."""
+    import torch
+    d = torch.zeros_like(st.img["color"])
+    loss = torch.zeros(1, device="cuda")
+    call = lambda: st.R.ssim_loss(st.img["color"], st.tgt["color"], scale=0.2, d_color=d, loss_out=loss)
+    for _ in range(3):
+        call()
+    n = max(10, args.steps)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    cpx = 3 * wl["V"] * wl["W"] * wl["H"]
+    return dict(ms=round(ms, 4), channel_pixels=cpx, bytes_per_channel_pixel=48, bound="hbm",
+                achieved_gbs=round(cpx * 48 / (ms / 1e3) / 1e9, 1), unit="GB/s", loss=round(float(loss.item()), 6))
 
 
 def run_e2e(args, st, anc, mlp, tg, world):

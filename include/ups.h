@@ -306,6 +306,16 @@ ups_status ups_feature_lift(ups_ctx *ctx, const ups_lift_cfg *lcfg, const float 
                             const ups_lift_mlp *mlp, float scale, float *loss_dev, ups_lift_mlp *d_mlp,
                             float *d_feat, ups_stream stream);
 
+/* The D-SSIM term of the geometric loss (Eq. 4):
+ *   loss_dev[0] = scale (1 - SSIM(C~, C))   (overwritten)
+ * SSIM (Wang et al., cited by the paper) per colour channel of each of the last
+ * forward's views: 11 x 11 Gaussian window (sigma 1.5, normalised), C1 =
+ * 0.01^2, C2 = 0.03^2 (colours in [0, 1]), zero padding at the border,
+ * averaged over the 3 channels and all pixels.  If d_color is not NULL,
+ * scale * d/dC~ is ADDED to it (image layout).  color, t_color: image layout. */
+ups_status ups_ssim_loss(ups_ctx *ctx, const float *color, const float *t_color, float scale, float *loss_dev,
+                         float *d_color, ups_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */

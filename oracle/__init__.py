@@ -10,8 +10,9 @@ per-view steps into the full loss and its gradients:
 
   decode (Eq. 8-9) -> project (Eq. 1-2) -> blend (Eq. 3, Eq. 10)
   -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step;
-  and, in numpy, the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser)
-  and the feature lifting with its distillation loss (Eq. 11-12).
+  and, in numpy, the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser),
+  the feature lifting with its distillation loss (Eq. 11-12) and the D-SSIM
+  term of Eq. 4.
 """
 from __future__ import annotations
 
@@ -352,6 +353,52 @@ def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0):
     db1 = dZ.sum(0)
     dX = dZ @ mlp["w1"]
     return loss, dict(w1=dW1, b1=db1, w2=dW2, b2=db2, feat=dX.T.reshape(nf, H, W))
+
+
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window(radius=5, sigma=1.5):
+    """11 x 11 Gaussian window of SSIM (Wang et al.), sigma 1.5, summing to 1."""
+    k = np.arange(-radius, radius + 1, dtype=float)
+    w = np.exp(-k * k / (2.0 * sigma * sigma))
+    w /= w.sum()
+    return np.outer(w, w)
+
+
+def ssim_loss(color, t_color, n_pix, scale=1.0):
+    """The D-SSIM term of Eq. 4 for one view: scale / (3 n_pix) sum over the three
+    channels and the pixels of (1 - S), S the SSIM map of Wang et al. (the
+    paper's citation): window moments mu, E[x^2], E[xy] with the Gaussian window
+    and zero padding, C1 = 0.01^2, C2 = 0.03^2.  n_pix: pixels of all views.
+    Returns the loss contribution and scale * d/d(color) ([3][H][W]).
+
+    Gradient: S = A1 A2 / (B1 B2) with A1 = 2 mu_x mu_y + C1, A2 = 2 (E[xy] -
+    mu_x mu_y) + C2, B1 = mu_x^2 + mu_y^2 + C1, B2 = E[x^2] - mu_x^2 + E[y^2] -
+    mu_y^2 + C2; a pixel q enters the moments of p with weight w(q - p), so
+    dS_p/dx_q = w(q - p) (dS/dmu_x + 2 x_q dS/dE[x^2] + y_q dS/dE[xy])(p)."""
+    from scipy.ndimage import correlate
+    W2 = ssim_window()
+    conv = lambda a: correlate(a, W2, mode="constant", cval=0.0)             # sum_k w(k) a(p + k)
+    back = lambda a: correlate(a, W2[::-1, ::-1], mode="constant", cval=0.0)  # sum_p w(q - p) a(p)
+    g = scale / (3.0 * n_pix)
+    loss = 0.0
+    grad = np.zeros_like(color, dtype=float)
+    for c in range(3):
+        x, y = color[c], t_color[c]
+        mx, my = conv(x), conv(y)
+        exx, eyy, exy = conv(x * x), conv(y * y), conv(x * y)
+        A1 = 2 * mx * my + SSIM_C1
+        A2 = 2 * (exy - mx * my) + SSIM_C2
+        B1 = mx * mx + my * my + SSIM_C1
+        B2 = (exx - mx * mx) + (eyy - my * my) + SSIM_C2
+        S = A1 * A2 / (B1 * B2)
+        loss += g * (1.0 - S).sum()
+        d_mu = S * (2 * my / A1 - 2 * my / A2 - 2 * mx / B1 + 2 * mx / B2)  # dS/dmu_x (E fixed)
+        d_xx = -S / B2                                                      # dS/dE[x^2]
+        d_xy = 2 * S / A2                                                   # dS/dE[xy]
+        grad[c] = -g * (back(d_mu) + 2 * x * back(d_xx) + y * back(d_xy))
+    return loss, grad
 
 
 def render_bwd(proj, g, cam, cfg: RenderCfg, n_feat, grads_img):

@@ -103,7 +103,7 @@ class Stats(C.Structure):
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted", "ups_tracking_uncertainty",
-           "ups_feature_lift",
+           "ups_feature_lift", "ups_ssim_loss",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
@@ -140,6 +140,7 @@ def load():
                                     C.POINTER(Gaussians), _p, C.POINTER(Images), _p]
     L.ups_tracking_uncertainty.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(ResidualCfg),
                                            _p, _p, _p, _p]
+    L.ups_ssim_loss.argtypes = [_p, _p, _p, _f, _p, _p, _p]
     L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _p,
                                    C.POINTER(LiftMLP), _p, _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
@@ -350,6 +351,15 @@ class Renderer:
                                                      _ptr(out.get("R")), _ptr(out.get("sigma2")),
                                                      _ptr(out.get("motion")), _stream(stream)))
         return out
+
+    def ssim_loss(self, color, t_color, scale=1.0, d_color=None, loss_out=None, stream=None):
+        """Eq. 4's D-SSIM term scale * (1 - SSIM) of the last forward's views;
+        scale * d/dC~ is added to d_color when given."""
+        import torch
+        loss_out = loss_out if loss_out is not None else torch.zeros(1, dtype=torch.float32, device=color.device)
+        self._check(self._L.ups_ssim_loss(self._h, _ptr(color), _ptr(t_color), float(scale), _ptr(loss_out),
+                                          _ptr(d_color), _stream(stream)))
+        return loss_out
 
     def feature_lift(self, feat, dino, mlp, n_h=384, patch=14, scale=1.0, d_mlp=None, d_feat=None,
                      loss_out=None, stream=None):

@@ -38,6 +38,9 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
                                  const int *gate = nullptr);
+cudaError_t ssim_set_window();
+cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, float *G, float g, float *loss,
+                        float *dx, cudaStream_t st);
 size_t lift_scratch_floats(size_t max_hw, int nh);
 cudaError_t lift_handle(void **handle);
 void lift_handle_destroy(void *handle);
@@ -128,6 +131,8 @@ struct ups_ctx {
     bool capped = false;          // the last forward capped its tile lists
     void *cublas = nullptr;       // cuBLAS handle of the feature lifting (created on first use)
     DevBuf lift_scr;              // feature-lifting scratch of one view
+    DevBuf ssim_g;                // D-SSIM window-term maps of all colour planes
+    bool ssim_window = false;     // the SSIM window is in this device's constant memory
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
     struct Rec {
@@ -389,7 +394,7 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr, &c->ssim_g};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->d_err) cudaFree(c->d_err);
@@ -605,6 +610,29 @@ ups_status ups_tracking_uncertainty(ups_ctx *c, const ups_images *img, const ups
     UPS_CUDA(c, launch_uncertainty(c->vt, nf, c->max_hw, rcfg->lambda_color, rcfg->lambda_depth, rcfg->lambda_feat,
                                    rcfg->t_mask, *img, *tgt, R, sigma2, motion, st));
     stage_end(c, st, 1);
+    return UPS_OK;
+}
+
+ups_status ups_ssim_loss(ups_ctx *c, const float *color, const float *t_color, float scale, float *loss_dev,
+                         float *d_color, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_ssim_loss needs a forward first");
+    if (!color || !t_color || !loss_dev) return fail(c, UPS_ERR_ARG, "NULL argument");
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    if (!c->ssim_window) {
+        UPS_CUDA(c, ssim_set_window());
+        c->ssim_window = true;
+    }
+    UPS_CUDA(c, c->ssim_g.reserve((size_t)9 * c->n_pix * sizeof(float)));
+    stage_begin(c, "ssim", st);
+    UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
+    const float g = (float)((double)scale / (3.0 * (double)c->n_pix));
+    UPS_CUDA(c, launch_ssim(c->vt, color, t_color, c->ssim_g.as<float>(), g, loss_dev, d_color, st));
+    const int launches = d_color ? 2 : 1;
+    stage_end(c, st, launches);
     return UPS_OK;
 }
 
