@@ -288,6 +288,7 @@ def run_ours(args, wl_name):
     unc = run_uncertainty(args, st, wl)
     lift = run_lift(args, st, wl)
     ssim = run_ssim(args, st, wl)
+    umlp = run_unc_mlp(args, st, wl)
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -333,7 +334,11 @@ def run_ours(args, wl_name):
                                                   peak_source=peaks["source"] + " bf16 sustained x 1/2 (TF32)"),
                           "dssim": dict(ssim, peak=round(peaks["hbm_gbs"], 1),
                                         frac=round(ssim["achieved_gbs"] / peaks["hbm_gbs"], 4),
-                                        peak_source=peaks["source"])},
+                                        peak_source=peaks["source"]),
+                          "uncertainty_mlp": dict(umlp, peak=round(152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6, 2),
+                                                  frac=round(umlp["achieved_tflops"]
+                                                             / (152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6), 4),
+                                                  peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock")},
         }
         print(json.dumps(line))
     if world > 1:
@@ -465,6 +470,49 @@ def run_ssim(args, st, wl):
     cpx = 3 * wl["V"] * wl["W"] * wl["H"]
     return dict(ms=round(ms, 4), channel_pixels=cpx, bytes_per_channel_pixel=48, bound="hbm",
                 achieved_gbs=round(cpx * 48 / (ms / 1e3) / 1e9, 1), unit="GB/s", loss=round(float(loss.item()), 6))
+
+
+def run_unc_mlp(args, st, wl, n_h=384, patch=14):
+    """Uncertainty MLP F_u and L_u (Eq. 5, Eq. 13) with its gradient, on a seeded
+    synthetic DINO patch grid and residual map of the bench batch, through the
+    public API; CUDA events over repeated calls.  Bound by FP32 arithmetic (9 B
+    of pixel traffic against ~2.9 kFLOP per pixel).  Algorithmic FLOPs: per
+    pixel the 128 first-layer values interpolated from 4 patches (2 * 4 * 128),
+    the output dot (2 * 128), dW2 (2 * 128), dh (128) and its share of the four
+    corners (2 * 4 * 128) and db1 (128); per patch the two 128 x n_h products
+    (2 * 2 * 128 * n_h)."""
+    import torch
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    grids = sum(-(-wl["H"] // patch) * -(-wl["W"] // patch) for _ in range(wl["V"])) * n_h
+    dino = torch.randn(grids, generator=gen, device="cuda")
+    Rm = torch.rand(st.img["depth"].shape, generator=gen, device="cuda")
+    mlp = dict(w1=torch.randn(128, n_h, generator=gen, device="cuda") * 0.1,
+               b1=torch.randn(128, generator=gen, device="cuda") * 0.1,
+               w2=torch.randn(128, generator=gen, device="cuda") * 0.2,
+               b2=torch.full((1,), 0.2, device="cuda"))
+    dm = {k: torch.zeros_like(v) for k, v in mlp.items()}
+    loss = torch.zeros(1, device="cuda")
+    out = dict(sigma=torch.empty_like(Rm), motion=torch.empty(Rm.shape, dtype=torch.uint8, device="cuda"))
+    call = lambda: st.R.uncertainty_mlp(dino, Rm, mlp, n_h=n_h, patch=patch, d_mlp=dm, out=out, loss_out=loss)
+    for _ in range(3):
+        call()
+    n = max(10, args.steps)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    pix = wl["V"] * wl["W"] * wl["H"]
+    patches = wl["V"] * -(-wl["H"] // patch) * -(-wl["W"] // patch)
+    flops = pix * (2 * 4 * 128 + 2 * 128 + 2 * 128 + 128 + 2 * 4 * 128 + 128) + patches * 4 * 128 * n_h
+    return dict(ms=round(ms, 4), pixels=pix, n_h=n_h, algorithmic_flops=flops, bound="alu",
+                achieved_tflops=round(flops / (ms / 1e3) / 1e12, 3), unit="TFLOP/s",
+                note="first layer per DINO patch (exact by linearity), per-pixel rest on CUDA cores")
 
 
 def run_e2e(args, st, anc, mlp, tg, world):

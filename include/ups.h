@@ -316,6 +316,24 @@ ups_status ups_feature_lift(ups_ctx *ctx, const ups_lift_cfg *lcfg, const float 
 ups_status ups_ssim_loss(ups_ctx *ctx, const float *color, const float *t_color, float scale, float *loss_dev,
                          float *d_color, ups_stream stream);
 
+/* Uncertainty MLP F_u and its loss (Sec. 3.3 "Uncertainty Prediction for
+ * Mapping", Eq. 5, Eq. 13; App. "MLP Implementation Details"):
+ *   sigma_p = SoftPlus(w2 . ReLU(W1 F_p + b1) + b2)
+ * (1x1 conv -> ReLU -> 1x1 conv -> SoftPlus, hidden 128, one output) with F_p
+ * the DINO feature of pixel p, bilinear from the patch grids exactly as in
+ * ups_feature_lift (lcfg, dino), and
+ *   loss_dev[0] = scale * (1/P) sum_p [R_p / (2 sigma_p^2) + lambda log sigma_p]
+ * over the last forward's views (overwritten).  R: per-pixel residual in the
+ * depth layout (e.g. ups_tracking_uncertainty's R).  The gradient flows only
+ * into F_u (the paper keeps the mapping and uncertainty gradient flows apart):
+ * if d_mlp is not NULL, scale * dL/d(w1, b1, w2, b2) is ADDED (each may be
+ * NULL).  sigma (float) and motion (uint8, M = 2 sigma^2 > 1 of Sec. 3.3) are
+ * written per pixel when not NULL.
+ *  mlp  w1 [128][n_h], b1 [128], w2 [128], b2 [1] */
+ups_status ups_uncertainty_mlp(ups_ctx *ctx, const ups_lift_cfg *lcfg, const float *dino, const float *R,
+                               const ups_lift_mlp *mlp, float lambda, float scale, float *loss_dev,
+                               ups_lift_mlp *d_mlp, float *sigma, unsigned char *motion, ups_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */

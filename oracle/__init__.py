@@ -11,8 +11,8 @@ per-view steps into the full loss and its gradients:
   decode (Eq. 8-9) -> project (Eq. 1-2) -> blend (Eq. 3, Eq. 10)
   -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step;
   and, in numpy, the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser),
-  the feature lifting with its distillation loss (Eq. 11-12) and the D-SSIM
-  term of Eq. 4.
+  the feature lifting with its distillation loss (Eq. 11-12), the uncertainty
+  MLP with L_u (Eq. 5, Eq. 13) and the D-SSIM term of Eq. 4.
 """
 from __future__ import annotations
 
@@ -353,6 +353,30 @@ def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0):
     db1 = dZ.sum(0)
     dX = dZ @ mlp["w1"]
     return loss, dict(w1=dW1, b1=db1, w2=dW2, b2=db2, feat=dX.T.reshape(nf, H, W))
+
+
+def uncertainty_mlp(grid, R, mlp, lcfg: LiftCfg, n_pix, lam=1.0, scale=1.0):
+    """Uncertainty MLP and its loss for one view (Sec. 3.3 "Uncertainty
+    Prediction for Mapping", Eq. 5, Eq. 13; App.): F_u = conv -> ReLU -> conv ->
+    SoftPlus (1x1, hidden 128, one output) on the upsampled DINO feature F_p:
+        sigma_p = softplus(w2 . relu(W1 F_p + b1) + b2)
+        loss = scale / n_pix sum_p [R_p / (2 sigma_p^2) + lam log sigma_p]   (Eq. 5)
+    The gradient goes to F_u's parameters only.  Returns the loss contribution,
+    scale * d(loss)/d(w1, b1, w2, b2), sigma [H][W] and the mask 2 sigma^2 > 1."""
+    H, W = R.shape
+    F = dino_upsample(grid, H, W, lcfg.patch).reshape(lcfg.n_h, H * W).T   # [P][n_h]
+    Z = F @ mlp["w1"].T + mlp["b1"]
+    Hh = np.maximum(Z, 0.0)
+    z2 = Hh @ mlp["w2"] + mlp["b2"][0]
+    s = np.where(z2 > 20, z2, np.log1p(np.exp(np.minimum(z2, 20))))          # softplus
+    r = R.reshape(-1)
+    g = scale / n_pix
+    loss = g * (r / (2 * s * s) + lam * np.log(s)).sum()
+    dz2 = g * (-r / s ** 3 + lam / s) / (1 + np.exp(-z2))                    # d/ds times softplus' = sigmoid
+    dZ = dz2[:, None] * mlp["w2"][None, :] * (Z > 0)
+    grads = dict(w1=dZ.T @ F, b1=dZ.sum(0), w2=Hh.T @ dz2, b2=np.array([dz2.sum()]))
+    sigma = s.reshape(H, W)
+    return loss, grads, sigma, (2 * sigma * sigma > 1).astype(np.uint8)
 
 
 SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2

@@ -103,7 +103,7 @@ class Stats(C.Structure):
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted", "ups_tracking_uncertainty",
-           "ups_feature_lift", "ups_ssim_loss",
+           "ups_feature_lift", "ups_ssim_loss", "ups_uncertainty_mlp",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
@@ -141,6 +141,8 @@ def load():
     L.ups_tracking_uncertainty.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(ResidualCfg),
                                            _p, _p, _p, _p]
     L.ups_ssim_loss.argtypes = [_p, _p, _p, _f, _p, _p, _p]
+    L.ups_uncertainty_mlp.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _f, _p,
+                                      C.POINTER(LiftMLP), _p, _p, _p]
     L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _p,
                                    C.POINTER(LiftMLP), _p, _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
@@ -351,6 +353,23 @@ class Renderer:
                                                      _ptr(out.get("R")), _ptr(out.get("sigma2")),
                                                      _ptr(out.get("motion")), _stream(stream)))
         return out
+
+    def uncertainty_mlp(self, dino, R, mlp, n_h=384, patch=14, lam=1.0, scale=1.0, d_mlp=None, out=None,
+                        loss_out=None, stream=None):
+        """Eq. 5 / Eq. 13: sigma = F_u(F) per pixel, scale * L_u and (if d_mlp) its
+        gradient into F_u; returns (loss, dict(sigma, motion))."""
+        import torch
+        dev = R.device
+        loss_out = loss_out if loss_out is not None else torch.zeros(1, dtype=torch.float32, device=dev)
+        if out is None:
+            out = dict(sigma=torch.empty_like(R), motion=torch.empty(R.shape, dtype=torch.uint8, device=dev))
+        cm = LiftMLP(*(_ptr(mlp[k]) for k in ("w1", "b1", "w2", "b2")))
+        dm = LiftMLP(*(_ptr(d_mlp.get(k)) for k in ("w1", "b1", "w2", "b2"))) if d_mlp is not None else None
+        self._check(self._L.ups_uncertainty_mlp(self._h, C.byref(LiftCfg(n_h, patch)), _ptr(dino), _ptr(R),
+                                                C.byref(cm), float(lam), float(scale), _ptr(loss_out),
+                                                C.byref(dm) if dm is not None else None, _ptr(out.get("sigma")),
+                                                _ptr(out.get("motion")), _stream(stream)))
+        return loss_out, out
 
     def ssim_loss(self, color, t_color, scale=1.0, d_color=None, loss_out=None, stream=None):
         """Eq. 4's D-SSIM term scale * (1 - SSIM) of the last forward's views;

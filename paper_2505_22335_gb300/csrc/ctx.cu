@@ -38,6 +38,11 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
                                  const int *gate = nullptr);
+size_t unc_scratch_floats(int max_patches);
+cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
+                     int hp, const float *R, const float *w1, const float *b1, const float *w2, const float *b2,
+                     float lambda, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
+                     float *sigma, uint8_t *motion, float *scratch, int *launches);
 cudaError_t ssim_set_window();
 cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, float *G, float g, float *loss,
                         float *dx, cudaStream_t st);
@@ -132,6 +137,7 @@ struct ups_ctx {
     void *cublas = nullptr;       // cuBLAS handle of the feature lifting (created on first use)
     DevBuf lift_scr;              // feature-lifting scratch of one view
     DevBuf ssim_g;                // D-SSIM window-term maps of all colour planes
+    DevBuf unc_scr;               // uncertainty-MLP patch scratch of one view
     bool ssim_window = false;     // the SSIM window is in this device's constant memory
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
@@ -394,7 +400,7 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr, &c->ssim_g};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr, &c->ssim_g, &c->unc_scr};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
     if (c->d_err) cudaFree(c->d_err);
@@ -610,6 +616,45 @@ ups_status ups_tracking_uncertainty(ups_ctx *c, const ups_images *img, const ups
     UPS_CUDA(c, launch_uncertainty(c->vt, nf, c->max_hw, rcfg->lambda_color, rcfg->lambda_depth, rcfg->lambda_feat,
                                    rcfg->t_mask, *img, *tgt, R, sigma2, motion, st));
     stage_end(c, st, 1);
+    return UPS_OK;
+}
+
+ups_status ups_uncertainty_mlp(ups_ctx *c, const ups_lift_cfg *lcfg, const float *dino, const float *R,
+                               const ups_lift_mlp *mlp, float lambda, float scale, float *loss_dev,
+                               ups_lift_mlp *d_mlp, float *sigma, unsigned char *motion, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_uncertainty_mlp needs a forward first");
+    if (!lcfg || !dino || !R || !mlp || !mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2 || !loss_dev)
+        return fail(c, UPS_ERR_ARG, "NULL argument");
+    if (lcfg->n_h < 1 || lcfg->n_h > 4096 || lcfg->patch < 1) return fail(c, UPS_ERR_ARG, "n_h or patch out of range");
+    ups_status s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, lift_handle(&c->cublas));
+    int max_np = 0;
+    for (int v = 0; v < c->vt.n; ++v) {
+        const DevView &cam = c->vt.v[v];
+        max_np = std::max(max_np, ((cam.H + lcfg->patch - 1) / lcfg->patch) * ((cam.W + lcfg->patch - 1) / lcfg->patch));
+    }
+    UPS_CUDA(c, c->unc_scr.reserve(unc_scratch_floats(max_np) * sizeof(float)));
+    stage_begin(c, "uncertainty_mlp", st);
+    UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
+    const float g = (float)((double)scale / (double)c->n_pix);
+    size_t grid_off = 0;
+    int launches = 0;
+    for (int v = 0; v < c->vt.n; ++v) {
+        const DevView &cam = c->vt.v[v];
+        const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
+        const size_t P = (size_t)cam.pix_off;
+        UPS_CUDA(c, unc_view(c->cublas, st, cam.W, cam.H, lcfg->n_h, lcfg->patch, dino + grid_off, wp, hp, R + P,
+                             mlp->w1, mlp->b1, mlp->w2, mlp->b2, lambda, g, loss_dev, d_mlp ? d_mlp->w1 : nullptr,
+                             d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr, d_mlp ? d_mlp->b2 : nullptr,
+                             sigma ? sigma + P : nullptr, motion ? motion + P : nullptr, c->unc_scr.as<float>(),
+                             &launches));
+        grid_off += (size_t)hp * wp * lcfg->n_h;
+    }
+    stage_end(c, st, launches);
     return UPS_OK;
 }
 
