@@ -284,6 +284,8 @@ ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const u
  *  feat      rendered F~ in the image layout (n_feat planes per view)
  *  dino      the patch grids (16-byte aligned; UPS_ERR_ARG otherwise)
  *  mlp       w1 [128][n_feat], b1 [128], w2 [n_h][128], b2 [n_h] (b2 16-byte aligned)
+ *  weight    per-pixel weight w_p of (1 - cos) in the mean (depth layout; NULL: 1), e.g.
+ *            the mask M of Eq. 14 (L = M (L_g + lambda_4 L_d) + ...)
  *  scale     weight of L_d (e.g. lambda_4 of Eq. 14)
  *  loss_dev  device float: overwritten with scale * L_d
  *  d_mlp     if not NULL: scale * dL_d/d(w1, b1, w2, b2) ADDED to its arrays
@@ -303,18 +305,20 @@ typedef struct {
 } ups_lift_mlp;
 
 ups_status ups_feature_lift(ups_ctx *ctx, const ups_lift_cfg *lcfg, const float *feat, const float *dino,
-                            const ups_lift_mlp *mlp, float scale, float *loss_dev, ups_lift_mlp *d_mlp,
-                            float *d_feat, ups_stream stream);
+                            const ups_lift_mlp *mlp, const float *weight, float scale, float *loss_dev,
+                            ups_lift_mlp *d_mlp, float *d_feat, ups_stream stream);
 
 /* The D-SSIM term of the geometric loss (Eq. 4):
  *   loss_dev[0] = scale (1 - SSIM(C~, C))   (overwritten)
  * SSIM (Wang et al., cited by the paper) per colour channel of each of the last
  * forward's views: 11 x 11 Gaussian window (sigma 1.5, normalised), C1 =
  * 0.01^2, C2 = 0.03^2 (colours in [0, 1]), zero padding at the border,
- * averaged over the 3 channels and all pixels.  If d_color is not NULL,
- * scale * d/dC~ is ADDED to it (image layout).  color, t_color: image layout. */
-ups_status ups_ssim_loss(ups_ctx *ctx, const float *color, const float *t_color, float scale, float *loss_dev,
-                         float *d_color, ups_stream stream);
+ * averaged over the 3 channels and all pixels, each pixel's (1 - S) times
+ * weight[p] (depth layout; NULL: 1), e.g. the mask M of Eq. 14.  If d_color is
+ * not NULL, scale * d/dC~ is ADDED to it (image layout).  color, t_color:
+ * image layout. */
+ups_status ups_ssim_loss(ups_ctx *ctx, const float *color, const float *t_color, const float *weight, float scale,
+                         float *loss_dev, float *d_color, ups_stream stream);
 
 /* Uncertainty MLP F_u and its loss (Sec. 3.3 "Uncertainty Prediction for
  * Mapping", Eq. 5, Eq. 13; App. "MLP Implementation Details"):

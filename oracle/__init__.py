@@ -322,7 +322,7 @@ def dino_upsample(grid, H, W, patch):
     return np.moveaxis((1 - ay) * top + ay * bot, 2, 0)
 
 
-def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0):
+def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0, weight=None):
     """Feature lifting and distillation of one view (Sec. 3.3, Eq. 11-12; App.
     "MLP Implementation Details": F_m = conv -> ReLU -> conv, hidden 128, read as
     1x1 convolutions, i.e. the same MLP at every pixel).
@@ -341,11 +341,12 @@ def feature_lift(feat, grid, mlp, lcfg: LiftCfg, n_pix, scale=1.0):
     ok = (na > 0) & (nb > 0)
     den = np.where(ok, na * nb, 1.0)
     cos = np.where(ok, (T * Fh).sum(1) / den, 0.0)
-    g = scale / n_pix
-    loss = g * (1.0 - cos).sum()
+    wp = np.ones(H * W) if weight is None else weight.reshape(-1)   # per-pixel weight (Eq. 14's mask)
+    g = scale / n_pix * wp
+    loss = (g * (1.0 - cos)).sum()
     # d(1 - cos)/dF^ = cos F^ / |F^|^2 - F / (|F| |F^|)
     nb2 = np.where(ok, nb * nb, 1.0)
-    dFh = np.where(ok[:, None], g * (cos[:, None] * Fh / nb2[:, None] - T / den[:, None]), 0.0)
+    dFh = np.where(ok[:, None], g[:, None] * (cos[:, None] * Fh / nb2[:, None] - T / den[:, None]), 0.0)
     dW2 = dFh.T @ Hh
     db2 = dFh.sum(0)
     dZ = (dFh @ mlp["w2"]) * (Z > 0)
@@ -390,7 +391,7 @@ def ssim_window(radius=5, sigma=1.5):
     return np.outer(w, w)
 
 
-def ssim_loss(color, t_color, n_pix, scale=1.0):
+def ssim_loss(color, t_color, n_pix, scale=1.0, weight=None):
     """The D-SSIM term of Eq. 4 for one view: scale / (3 n_pix) sum over the three
     channels and the pixels of (1 - S), S the SSIM map of Wang et al. (the
     paper's citation): window moments mu, E[x^2], E[xy] with the Gaussian window
@@ -417,10 +418,11 @@ def ssim_loss(color, t_color, n_pix, scale=1.0):
         B1 = mx * mx + my * my + SSIM_C1
         B2 = (exx - mx * mx) + (eyy - my * my) + SSIM_C2
         S = A1 * A2 / (B1 * B2)
-        loss += g * (1.0 - S).sum()
-        d_mu = S * (2 * my / A1 - 2 * my / A2 - 2 * mx / B1 + 2 * mx / B2)  # dS/dmu_x (E fixed)
-        d_xx = -S / B2                                                      # dS/dE[x^2]
-        d_xy = 2 * S / A2                                                   # dS/dE[xy]
+        wp = 1.0 if weight is None else weight                              # per-pixel weight (Eq. 14's mask)
+        loss += g * (wp * (1.0 - S)).sum()
+        d_mu = wp * S * (2 * my / A1 - 2 * my / A2 - 2 * mx / B1 + 2 * mx / B2)  # w dS/dmu_x (E fixed)
+        d_xx = wp * (-S / B2)                                                    # w dS/dE[x^2]
+        d_xy = wp * (2 * S / A2)                                                 # w dS/dE[xy]
         grad[c] = -g * (back(d_mu) + 2 * x * back(d_xx) + y * back(d_xy))
     return loss, grad
 

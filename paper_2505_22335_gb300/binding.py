@@ -140,10 +140,10 @@ def load():
                                     C.POINTER(Gaussians), _p, C.POINTER(Images), _p]
     L.ups_tracking_uncertainty.argtypes = [_p, C.POINTER(Images), C.POINTER(Targets), C.POINTER(ResidualCfg),
                                            _p, _p, _p, _p]
-    L.ups_ssim_loss.argtypes = [_p, _p, _p, _f, _p, _p, _p]
+    L.ups_ssim_loss.argtypes = [_p, _p, _p, _p, _f, _p, _p, _p]
     L.ups_uncertainty_mlp.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _f, _p,
                                       C.POINTER(LiftMLP), _p, _p, _p]
-    L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _f, _p,
+    L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _p, _f, _p,
                                    C.POINTER(LiftMLP), _p, _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
                                       C.POINTER(Gaussians), _p, _p]
@@ -371,16 +371,16 @@ class Renderer:
                                                 _ptr(out.get("motion")), _stream(stream)))
         return loss_out, out
 
-    def ssim_loss(self, color, t_color, scale=1.0, d_color=None, loss_out=None, stream=None):
-        """Eq. 4's D-SSIM term scale * (1 - SSIM) of the last forward's views;
-        scale * d/dC~ is added to d_color when given."""
+    def ssim_loss(self, color, t_color, scale=1.0, d_color=None, weight=None, loss_out=None, stream=None):
+        """Eq. 4's D-SSIM term scale * (1 - SSIM) of the last forward's views (each
+        pixel weighted by `weight` when given); scale * d/dC~ is added to d_color."""
         import torch
         loss_out = loss_out if loss_out is not None else torch.zeros(1, dtype=torch.float32, device=color.device)
-        self._check(self._L.ups_ssim_loss(self._h, _ptr(color), _ptr(t_color), float(scale), _ptr(loss_out),
-                                          _ptr(d_color), _stream(stream)))
+        self._check(self._L.ups_ssim_loss(self._h, _ptr(color), _ptr(t_color), _ptr(weight), float(scale),
+                                          _ptr(loss_out), _ptr(d_color), _stream(stream)))
         return loss_out
 
-    def feature_lift(self, feat, dino, mlp, n_h=384, patch=14, scale=1.0, d_mlp=None, d_feat=None,
+    def feature_lift(self, feat, dino, mlp, n_h=384, patch=14, scale=1.0, d_mlp=None, d_feat=None, weight=None,
                      loss_out=None, stream=None):
         """Eq. 11-12: scale * L_d of the rendered feature map `feat` (image layout)
         against the per-view DINO patch grids `dino` (concatenated [hp][wp][n_h]);
@@ -390,7 +390,7 @@ class Renderer:
         cm = LiftMLP(*(_ptr(mlp[k]) for k in ("w1", "b1", "w2", "b2")))
         dm = LiftMLP(*(_ptr(d_mlp.get(k)) for k in ("w1", "b1", "w2", "b2"))) if d_mlp is not None else None
         self._check(self._L.ups_feature_lift(self._h, C.byref(LiftCfg(n_h, patch)), _ptr(feat), _ptr(dino),
-                                             C.byref(cm), float(scale), _ptr(loss_out),
+                                             C.byref(cm), _ptr(weight), float(scale), _ptr(loss_out),
                                              C.byref(dm) if dm is not None else None, _ptr(d_feat),
                                              _stream(stream)))
         return loss_out

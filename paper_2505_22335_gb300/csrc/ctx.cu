@@ -44,15 +44,15 @@ cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int pa
                      float lambda, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
                      float *sigma, uint8_t *motion, float *scratch, int *launches);
 cudaError_t ssim_set_window();
-cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, float *G, float g, float *loss,
-                        float *dx, cudaStream_t st);
+cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, const float *weight, float *G, float g,
+                        float *loss, float *dx, cudaStream_t st);
 size_t lift_scratch_floats(size_t max_hw, int nh);
 cudaError_t lift_handle(void **handle);
 void lift_handle_destroy(void *handle);
 cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
                       const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
-                      const float *b2, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
-                      float *d_feat, float *scratch, int *launches);
+                      const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
+                      float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches);
 cudaError_t launch_uncertainty(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                                float t_mask, const ups_images &img, const ups_targets &tgt, float *R, float *sigma2,
                                uint8_t *motion, cudaStream_t st);
@@ -658,8 +658,8 @@ ups_status ups_uncertainty_mlp(ups_ctx *c, const ups_lift_cfg *lcfg, const float
     return UPS_OK;
 }
 
-ups_status ups_ssim_loss(ups_ctx *c, const float *color, const float *t_color, float scale, float *loss_dev,
-                         float *d_color, ups_stream stream) {
+ups_status ups_ssim_loss(ups_ctx *c, const float *color, const float *t_color, const float *weight, float scale,
+                         float *loss_dev, float *d_color, ups_stream stream) {
     if (!c) return UPS_ERR_ARG;
     if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_ssim_loss needs a forward first");
     if (!color || !t_color || !loss_dev) return fail(c, UPS_ERR_ARG, "NULL argument");
@@ -675,15 +675,15 @@ ups_status ups_ssim_loss(ups_ctx *c, const float *color, const float *t_color, f
     stage_begin(c, "ssim", st);
     UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
     const float g = (float)((double)scale / (3.0 * (double)c->n_pix));
-    UPS_CUDA(c, launch_ssim(c->vt, color, t_color, c->ssim_g.as<float>(), g, loss_dev, d_color, st));
+    UPS_CUDA(c, launch_ssim(c->vt, color, t_color, weight, c->ssim_g.as<float>(), g, loss_dev, d_color, st));
     const int launches = d_color ? 2 : 1;
     stage_end(c, st, launches);
     return UPS_OK;
 }
 
 ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *feat, const float *dino,
-                            const ups_lift_mlp *mlp, float scale, float *loss_dev, ups_lift_mlp *d_mlp,
-                            float *d_feat, ups_stream stream) {
+                            const ups_lift_mlp *mlp, const float *weight, float scale, float *loss_dev,
+                            ups_lift_mlp *d_mlp, float *d_feat, ups_stream stream) {
     if (!c) return UPS_ERR_ARG;
     if (!c->have_fwd) return fail(c, UPS_ERR_STATE, "ups_feature_lift needs a forward first");
     if (!lcfg || !feat || !dino || !mlp || !mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2 || !loss_dev)
@@ -710,7 +710,8 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
         const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
         const size_t P = (size_t)cam.pix_off;
         UPS_CUDA(c, lift_view(c->cublas, st, cam.W, cam.H, nf, lcfg->n_h, lcfg->patch, feat + (size_t)nf * P,
-                              dino + grid_off, wp, hp, mlp->w1, mlp->b1, mlp->w2, mlp->b2, g, loss_dev,
+                              dino + grid_off, wp, hp, mlp->w1, mlp->b1, mlp->w2, mlp->b2, g,
+                              weight ? weight + P : nullptr, loss_dev,
                               d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr,
                               d_mlp ? d_mlp->b2 : nullptr, d_feat ? d_feat + (size_t)nf * P : nullptr,
                               c->lift_scr.as<float>(), &launches));

@@ -70,11 +70,14 @@ __global__ void __launch_bounds__(256) k_row_sums(const float *__restrict__ m, s
 // scale / P.  Zero vectors: cos = 0 and no gradient.
 __global__ void __launch_bounds__(256) k_lift_cos(float *__restrict__ fh, const float *__restrict__ b2, int W,
                                                   int H, int nh, const float *__restrict__ grid, int wp, int hp,
-                                                  int patch, float g, float *__restrict__ loss) {
+                                                  int patch, float g0, const float *__restrict__ weight,
+                                                  float *__restrict__ loss) {
     const size_t HW = (size_t)W * H;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     float term = 0.f;
     if (p < HW) {
+        const float wpx = weight ? weight[p] : 1.f;  // per-pixel weight (the mask of Eq. 14)
+        const float g = g0 * wpx;
         const int y = (int)(p / (size_t)W), x = (int)(p - (size_t)y * W);
         const float inv = 1.f / (float)patch;
         const float u = fminf(fmaxf(((float)x + 0.5f) * inv - 0.5f, 0.f), (float)(wp - 1));
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256) k_lift_cos(float *__restrict__ fh, const 
         const bool ok = na > 0.f && nb > 0.f;
         const float ia = ok ? rsqrtf(na) : 0.f, ib = ok ? rsqrtf(nb) : 0.f;
         const float cs = dot * ia * ib;
-        term = 1.f - cs;
+        term = wpx * (1.f - cs);
         const float k1 = g * cs * ib * ib, k2 = g * ia * ib;
 #pragma unroll 2
         for (int q = 0; q < nq; ++q) {
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) k_lift_cos(float *__restrict__ fh, const 
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(loss, g * t);
+        atomicAdd(loss, g0 * t);
     }
 }
 
@@ -166,13 +169,14 @@ void lift_handle_destroy(void *handle) {
 }
 
 // One view: forward, loss and backward.  feat / d_feat: the view's planes
-// [nf][HW]; grid: its patch grid; scratch: lift_scratch_floats(HW, nh).
+// [nf][HW]; grid: its patch grid; weight: its per-pixel weights (null: 1);
+// scratch: lift_scratch_floats(HW, nh).
 // d_w1 [128][nf], d_b1 [128], d_w2 [nh][128], d_b2 [nh] and d_feat are
 // accumulated (may be null: that gradient is skipped).
 cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
                       const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
-                      const float *b2, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
-                      float *d_feat, float *scratch, int *launches) {
+                      const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
+                      float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches) {
     cublasHandle_t h = static_cast<cublasHandle_t>(handle);
     if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const int HW = W * H;
@@ -188,7 +192,7 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
     k_bias_relu<<<dim3(gx, NH), blk, 0, st>>>(Hm, b1, (size_t)HW);
     // F^ - b2 = H W2^T
     if ((e = gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, HW, nh, NH, Hm, HW, w2, NH, 0.f, Fh, HW)) != cudaSuccess) return e;
-    k_lift_cos<<<gx, blk, 0, st>>>(Fh, b2, W, H, nh, grid, wp, hp, patch, g, loss);
+    k_lift_cos<<<gx, blk, 0, st>>>(Fh, b2, W, H, nh, grid, wp, hp, patch, g, weight, loss);
     *launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const bool want_w = d_w1 || d_b1 || d_w2 || d_b2;

@@ -1,4 +1,5 @@
-// The D-SSIM term of the geometric loss (Eq. 4): scale (1 - SSIM(C~, C)),
+// The D-SSIM term of the geometric loss (Eq. 4): scale (1 - SSIM(C~, C)), each
+// pixel's (1 - S) weighted by an optional per-pixel weight (the mask of Eq. 14),
 // SSIM (Wang et al.) per colour channel of every view with an 11 x 11
 // Gaussian window (sigma 1.5, weights summing to 1), C1 = 0.01^2, C2 = 0.03^2
 // (data range 1), zero padding, averaged over channels and pixels.
@@ -38,14 +39,15 @@ struct Planes {
     int W[kMaxPlanes], H[kMaxPlanes];
     size_t off[kMaxPlanes];   // offset of the plane's pixel 0 in the colour arrays
     size_t goff[kMaxPlanes];  // offset of its window-term maps in G (3 maps of W * H)
+    size_t woff[kMaxPlanes];  // offset of its view's pixel 0 in the weight map
 };
 struct Plane {
     int W, H;
-    size_t off, goff;
+    size_t off, goff, woff;
 };
 __device__ __forceinline__ Plane plane_of(const Planes &t) {
     const int z = blockIdx.z;
-    return Plane{t.W[z], t.H[z], t.off[z], t.goff[z]};
+    return Plane{t.W[z], t.H[z], t.off[z], t.goff[z], t.woff[z]};
 }
 
 // horizontal then vertical window sums of NQ staged quantities
@@ -79,8 +81,8 @@ __device__ __forceinline__ void window_sums(const float (&in)[NQ][kIY][kIX], flo
 }
 
 __global__ void __launch_bounds__(256) k_ssim_fwd(const Planes pt, const float *__restrict__ x,
-                                                  const float *__restrict__ y, float *__restrict__ Gall, float g,
-                                                  float *__restrict__ loss) {
+                                                  const float *__restrict__ y, const float *__restrict__ weight,
+                                                  float *__restrict__ Gall, float g, float *__restrict__ loss) {
     __shared__ float in[5][kIY][kIX];
     __shared__ float hs[5][kIY][kTX];
     const Plane pl = plane_of(pt);
@@ -115,11 +117,12 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const Planes pt, const float *
         const float A1 = 2.f * mx * my + kC1, A2 = 2.f * (m[h][4] - mx * my) + kC2;
         const float B1 = mx * mx + my * my + kC1, B2 = (m[h][2] - mx * mx) + (m[h][3] - my * my) + kC2;
         const float S = (A1 * A2) / (B1 * B2);
-        term += 1.f - S;
         const size_t lp = (size_t)py * pl.W + px;  // the G maps are per plane
-        G[lp] = S * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
-        G[gstride + lp] = -S / B2;
-        G[2 * gstride + lp] = 2.f * S / A2;
+        const float wp = weight ? weight[pl.woff + lp] : 1.f;
+        term += wp * (1.f - S);
+        G[lp] = wp * S * (2.f * my / A1 - 2.f * my / A2 - 2.f * mx / B1 + 2.f * mx / B2);
+        G[gstride + lp] = wp * (-S / B2);
+        G[2 * gstride + lp] = wp * (2.f * S / A2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
@@ -174,11 +177,12 @@ cudaError_t ssim_set_window() {
     return cudaMemcpyToSymbol(c_win, w, sizeof(w));
 }
 
-// Every colour plane of the views in one launch per direction: adds g (1 - S)
-// over all planes to *loss and, if dx, -g dS/dx to dx.  G: scratch of 3 x (sum
+// Every colour plane of the views in one launch per direction: adds g w (1 - S)
+// over all planes to *loss and, if dx, its derivative to dx (w: the per-pixel
+// weight of the view's pixels, 1 when null).  G: scratch of 3 x (sum
 // of the planes' pixels) floats.
-cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, float *G, float g, float *loss,
-                        float *dx, cudaStream_t st) {
+cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, const float *weight, float *G, float g,
+                        float *loss, float *dx, cudaStream_t st) {
     Planes pt{};
     int maxw = 0, maxh = 0;
     size_t goff = 0;
@@ -190,13 +194,14 @@ cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, flo
             const size_t HW = (size_t)pt.W[i] * pt.H[i];
             pt.off[i] = 3 * (size_t)vt.v[v].pix_off + ch * HW;
             pt.goff[i] = goff;
+            pt.woff[i] = (size_t)vt.v[v].pix_off;
             goff += 3 * HW;
             maxw = std::max(maxw, pt.W[i]);
             maxh = std::max(maxh, pt.H[i]);
         }
     if (pt.n == 0) return cudaSuccess;
     const dim3 grid((maxw + kTX - 1) / kTX, (maxh + kTY - 1) / kTY, pt.n), blk(256);
-    k_ssim_fwd<<<grid, blk, 0, st>>>(pt, x, y, G, g, loss);
+    k_ssim_fwd<<<grid, blk, 0, st>>>(pt, x, y, weight, G, g, loss);
     if (dx) k_ssim_bwd<<<grid, blk, 0, st>>>(pt, x, y, G, g, dx);
     return cudaGetLastError();
 }

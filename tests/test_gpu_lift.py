@@ -35,7 +35,7 @@ def f32(a):
     return np.asarray(a, np.float32).astype(np.float64)
 
 
-def run_case(cams, nf, nh, patch, seed, scale=0.4):
+def run_case(cams, nf, nh, patch, seed, scale=0.4, weighted=False):
     import torch
     cams = round_cams(cams)
     rng = np.random.default_rng(seed)
@@ -53,14 +53,16 @@ def run_case(cams, nf, nh, patch, seed, scale=0.4):
                                     device="cuda")
     dmlp = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in mlp.items()}
     dfeat = dev(prefill)
+    ws = [f32((rng.uniform(0, 1, (c.height, c.width)) > 0.3) * rng.uniform(0.5, 1, (c.height, c.width)))
+          for c in cams] if weighted else [None] * len(cams)
     loss = R.feature_lift(dev(feats), dev(grids), {k: dev([v]) for k, v in mlp.items()}, n_h=nh, patch=patch,
-                          scale=scale, d_mlp=dmlp, d_feat=dfeat)
+                          scale=scale, d_mlp=dmlp, d_feat=dfeat, weight=dev(ws) if weighted else None)
     torch.cuda.synchronize()
     ref = {k: np.zeros_like(v) for k, v in mlp.items()}
     ref_loss = 0.0
     dfeat_ref = []
-    for c, fe, gr in zip(cams, feats, grids):
-        l, g = oracle.feature_lift(fe, gr, mlp, oracle.LiftCfg(n_h=nh, patch=patch), n_pix, scale)
+    for c, fe, gr, w in zip(cams, feats, grids, ws):
+        l, g = oracle.feature_lift(fe, gr, mlp, oracle.LiftCfg(n_h=nh, patch=patch), n_pix, scale, weight=w)
         ref_loss += l
         for k in ref:
             ref[k] += g[k]
@@ -90,6 +92,12 @@ def test_dino_width_384_feat32():
 def test_full_view_640x480():
     cams = scenes.cameras(0, 1, 640, 480, 600.0, identity=True)
     run_case(cams, 16, 384, 14, 7, scale=0.4)
+
+
+def test_weighted_ragged_views():
+    cams = scenes.cameras(8, 2, 36, 25, 40.0)
+    cams[1] = cams[1].scaled(0.7)
+    run_case(cams, 16, 64, 14, 9, weighted=True)
 
 
 def test_rejects_renderer_without_features():

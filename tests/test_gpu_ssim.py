@@ -24,7 +24,7 @@ def _built():
     __graft_entry__.build()
 
 
-def run_case(cams, seed, scale=0.2, smooth=False):
+def run_case(cams, seed, scale=0.2, smooth=False, weighted=False):
     import torch
     cams = round_cams(cams)
     rng = np.random.default_rng(seed)
@@ -43,11 +43,14 @@ def run_case(cams, seed, scale=0.2, smooth=False):
                                     device="cuda")
     pre = [f32(rng.normal(size=a.shape) * scale / n_pix) for a in imgs]  # accumulate into a pre-filled buffer
     d = dev(pre)
-    loss = R.ssim_loss(dev(imgs), dev(tgts), scale=scale, d_color=d)
+    # per-pixel weights (Eq. 14's mask): a binary mask with a continuous part
+    ws = [f32((rng.uniform(0, 1, (c.height, c.width)) > 0.3) * rng.uniform(0.5, 1, (c.height, c.width)))
+          for c in cams] if weighted else [None] * len(cams)
+    loss = R.ssim_loss(dev(imgs), dev(tgts), scale=scale, d_color=d, weight=dev(ws) if weighted else None)
     torch.cuda.synchronize()
     ref_loss, ref_g = 0.0, []
-    for x, y in zip(imgs, tgts):
-        l, gr = oracle.ssim_loss(x, y, n_pix, scale)
+    for x, y, w in zip(imgs, tgts, ws):
+        l, gr = oracle.ssim_loss(x, y, n_pix, scale, weight=w)
         ref_loss += l
         ref_g.append(gr.reshape(-1))
     got = d.cpu().numpy().astype(np.float64) - np.concatenate([p.reshape(-1) for p in pre])
@@ -71,3 +74,9 @@ def test_low_variance_content():
 
 def test_full_view_640x480():
     run_case(scenes.cameras(0, 1, 640, 480, 600.0, identity=True), 7, scale=0.5)
+
+
+def test_weighted_ragged_views():
+    cams = scenes.cameras(6, 2, 64, 40, 70.0)
+    cams[1] = cams[1].scaled(0.7)
+    run_case(cams, 8, weighted=True)

@@ -97,3 +97,26 @@ def test_gradients_against_central_differences(seed):
             arr[idx] = old
             fd = (lp - lm) / (2 * h)
             assert gr[name][idx] == pytest.approx(fd, rel=1e-5, abs=1e-10), (name, idx)
+
+
+def test_weighted_loss_gradients_against_central_differences():
+    mlp, feat, grid, cfg = problem(7)
+    nf, H, W = feat.shape
+    w = np.random.default_rng(8).uniform(0, 1, (H, W))
+    w[1, :] = 0.0
+    X = feat.reshape(nf, -1).T
+    assert np.abs(X @ mlp["w1"].T + mlp["b1"]).min() > 1e-5
+    l1, _ = oracle.feature_lift(feat, grid, mlp, cfg, H * W, 0.5)
+    l2, _ = oracle.feature_lift(feat, grid, mlp, cfg, H * W, 0.5, weight=np.ones((H, W)))
+    assert l1 == pytest.approx(l2, rel=1e-14)
+    _, gr = oracle.feature_lift(feat, grid, mlp, cfg, H * W, 0.5, weight=w)
+    h = 1e-6
+    for name, arr in [("w2", mlp["w2"]), ("feat", feat)]:
+        for idx in [(0, 0), (2, 3)] if name == "w2" else [(0, 2, 1), (1, 1, 2), (2, 4, 3)]:
+            old = arr[idx]
+            arr[idx] = old + h
+            lp = oracle.feature_lift(feat, grid, mlp, cfg, H * W, 0.5, weight=w)[0]
+            arr[idx] = old - h
+            lm = oracle.feature_lift(feat, grid, mlp, cfg, H * W, 0.5, weight=w)[0]
+            arr[idx] = old
+            assert gr[name][idx] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-11), (name, idx)

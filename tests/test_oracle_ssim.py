@@ -81,3 +81,23 @@ def test_gradient_against_central_differences():
         xm[idx] -= h
         fd = (oracle.ssim_loss(xp, y, n_pix, 0.6)[0] - oracle.ssim_loss(xm, y, n_pix, 0.6)[0]) / (2 * h)
         assert g[idx] == pytest.approx(fd, rel=1e-6, abs=1e-12), idx
+
+
+def test_weighted_ssim_matches_unit_weight_and_differences():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (3, 11, 12))
+    y = rng.uniform(0, 1, (3, 11, 12))
+    n_pix = 11 * 12
+    l1, g1 = oracle.ssim_loss(x, y, n_pix, 0.5)
+    l2, g2 = oracle.ssim_loss(x, y, n_pix, 0.5, weight=np.ones((11, 12)))
+    assert l1 == pytest.approx(l2, rel=1e-14) and np.allclose(g1, g2, rtol=1e-14, atol=0)
+    w = rng.uniform(0, 1, (11, 12))
+    w[3:6, 2:9] = 0.0  # a masked block (Eq. 14's mask)
+    _, g = oracle.ssim_loss(x, y, n_pix, 0.5, weight=w)
+    h = 1e-6
+    for idx in [(0, 4, 4), (1, 0, 0), (2, 10, 11), (0, 7, 3)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (oracle.ssim_loss(xp, y, n_pix, 0.5, w)[0] - oracle.ssim_loss(xm, y, n_pix, 0.5, w)[0]) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-6, abs=1e-12), idx
