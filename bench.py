@@ -41,6 +41,8 @@ WORKLOADS = {
     "decode_render_10k_anchors_x10_640x480": dict(A=10_000, K=10, NF=16, V=1, W=640, H=480, fx=600.0),
     # smaller case for ncu captures (decoded set 0.26 GB > L2)
     "profile_100k_anchors_x10_2x640x480": dict(A=100_000, K=10, NF=16, V=2, W=640, H=480, fx=600.0),
+    # seconds-long case for checks of the JSON contract (the reference arm on CPU)
+    "tiny_200_anchors_x4_2x64x48": dict(A=200, K=4, NF=16, V=2, W=64, H=48, fx=80.0),
 }
 DEFAULT_WORKLOAD = "mapping_100k_anchors_x10_8x640x480"
 LAMBDA_SCALE = 0.01
