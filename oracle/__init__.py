@@ -12,11 +12,13 @@ per-view steps into the full loss and its gradients:
   -> weighted loss (Eq. 4 / Eq. 14) -> analytic backward of each step;
   and, in numpy, the tracking uncertainty (Eq. 6 residual, Eq. 15 minimiser),
   the feature lifting with its distillation loss (Eq. 11-12), the uncertainty
-  MLP with L_u (Eq. 5, Eq. 13) and the D-SSIM term of Eq. 4.
+  MLP with L_u (Eq. 5, Eq. 13), the D-SSIM term of Eq. 4 and the probabilistic
+  anchor update with pruning and insertion (Eq. 7).
 """
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -601,3 +603,176 @@ def backward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_fe
         per_view.append(dict(g2d=g2, g3d=g3d, pose_project=g3["pose"], pose_decode=pd))
     acc["pose"] = pose
     return L, acc, views, per_view
+
+
+# ----------------------------------------------------------------------------
+# probabilistic anchors (Sec. 3.3 "Adaptively Structured Gaussian", Eq. 7)
+# ----------------------------------------------------------------------------
+
+def logodds(p):
+    """L(p) = log(p / (1 - p)), the log-odds of a probability."""
+    return math.log(p / (1.0 - p))
+
+
+def anchor_posterior(p_obs, p_prev, p_prior):
+    """Eq. 7, in FP64, with the reading of its garbled last factor as
+    P(n) / (1 - P(n)) (the Bayes update of OctoMap, which the paper cites):
+      P(n|z_1:t) = [1 + (1 - P(n|z_t)) / P(n|z_t)
+                          * (1 - P(n|z_1:t-1)) / P(n|z_1:t-1) * P(n) / (1 - P(n))]^-1."""
+    return 1.0 / (1.0 + (1.0 - p_obs) / p_obs * (1.0 - p_prev) / p_prev * p_prior / (1.0 - p_prior))
+
+
+@dataclass
+class AnchorCfg:
+    """Eq. 7 in log-odds form, L(n|z_1:t) = L(n|z_1:t-1) + L(n|z_t) - L(n),
+    and the readings of its observation model (the paper states neither the
+    inverse sensor model nor the thresholds; the probabilities are OctoMap's
+    defaults).  Values are log-odds (FP32 on both implementations)."""
+    l_prior: float = 0.0                     # L(P(n)), P(n) = 0.5
+    l_hit: float = math.log(0.7 / 0.3)       # L(P(n|z_t)) of a static surface observation
+    l_miss: float = math.log(0.4 / 0.6)      # ... of free space or a dynamic surface
+    l_min: float = math.log(0.12 / 0.88)     # clamping of the posterior
+    l_max: float = math.log(0.97 / 0.03)
+    l_prune: float = 0.0                     # delete anchors whose posterior is below P = 0.5
+    voxel: float = 0.05                      # anchor voxel edge (m)
+    margin: float = 0.05                     # half-width of the surface band along the ray (m)
+    near_z: float = 0.2                      # depths at or below this are not observations
+
+
+VOXEL_RANGE = 1 << 20   # voxel indices in [-2^20, 2^20) on every axis
+
+
+def _cam32(cam):
+    T = np.asarray(cam.T_cw, dtype=np.float64).reshape(4, 4).astype(np.float32)
+    f = np.float32
+    return T[:3, :3], T[:3, 3], f(cam.fx), f(cam.fy), f(cam.cx), f(cam.cy)
+
+
+def anchor_observe(pos, cam, depth, motion, acfg: AnchorCfg):
+    """The observation z_t of each anchor in one keyframe (reading of the paper's
+    occupancy observation; decisions in FP32, one rounding per operation in the
+    order written): the anchor centre x goes to the camera, X = R x + t summed
+    left to right, and to pixel (floor(fx X/Z + cx + 1/2), floor(fy Y/Z + cy + 1/2))
+    (pixel (i, j) sits at image coordinate (i, j)).  With D the keyframe depth there:
+      Z <= near_z, outside the image, or D <= near_z   -> no observation (0)
+      Z <  D - margin  (the ray passed through x)      -> miss (2)
+      Z <= D + margin  (x on the observed surface)     -> hit (1), or miss (2)
+                                                          when the pixel is dynamic
+      Z >  D + margin  (x hidden behind the surface)   -> no observation (0).
+    Returns int8 [n]."""
+    R, t, fx, fy, cx, cy = _cam32(cam)
+    f = np.float32
+    P = np.asarray(pos, np.float32).reshape(-1, 3)
+    H, W = depth.shape
+    Xc = [((R[r, 0] * P[:, 0] + R[r, 1] * P[:, 1]) + R[r, 2] * P[:, 2]) + t[r] for r in range(3)]
+    Z = Xc[2]
+    obs = np.zeros(P.shape[0], np.int8)
+    front = Z > f(acfg.near_z)
+    with np.errstate(all="ignore"):
+        u = fx * (Xc[0] / Z) + cx
+        v = fy * (Xc[1] / Z) + cy
+        iu = np.floor(u + f(0.5))
+        iv = np.floor(v + f(0.5))
+    inside = front & (iu >= 0) & (iu < W) & (iv >= 0) & (iv < H)
+    idx = np.nonzero(inside)[0]
+    jj, ii = iv[idx].astype(np.int64), iu[idx].astype(np.int64)
+    D = np.asarray(depth, np.float32)[jj, ii]
+    dyn = (np.asarray(motion)[jj, ii] != 0) if motion is not None else np.zeros(len(idx), bool)
+    z = Z[idx]
+    valid = D > f(acfg.near_z)
+    lo = D - f(acfg.margin)
+    hi = D + f(acfg.margin)
+    free = valid & (z < lo)
+    surf = valid & (z >= lo) & (z <= hi)
+    o = np.zeros(len(idx), np.int8)
+    o[surf & ~dyn] = 1
+    o[free | (surf & dyn)] = 2
+    obs[idx] = o
+    return obs
+
+
+def _voxel(x, voxel):
+    """floor(x / voxel) per axis in FP32 and whether every index is in range."""
+    q = np.floor(np.asarray(x, np.float32) / np.float32(voxel))
+    ok = np.all((q >= -VOXEL_RANGE) & (q < VOXEL_RANGE), axis=-1)
+    return q, ok
+
+
+def anchor_update(anc, logodds_in, cam, depth, motion, acfg: AnchorCfg, capacity):
+    """One keyframe of the probabilistic anchor map (Sec. 3.3, Eq. 7; the
+    probabilistic octree of Sec. 1 read as a voxel grid of edge `voxel` holding
+    the anchors, whose probabilities decide deletion and whose empty voxels
+    decide allocation):
+      1. update: each observed anchor's log-odds l <- clamp(l + (L(z_t) - L(n)),
+         l_min, l_max) (Eq. 7; unobserved anchors keep theirs);
+      2. prune: anchors whose posterior log-odds is below l_prune are deleted,
+         the rest keep their order;
+      3. insert: every static pixel (motion 0) with a valid depth D > near_z is
+         back-projected, x = R^T ((i - cx) / fx D - t_x, (j - cy) / fy D - t_y,
+         D - t_z), to its voxel floor(x / voxel); each voxel that holds no kept
+         anchor gets a new anchor at its centre, in the raster order of the first
+         pixel that reached it, up to `capacity` anchors in total.  A new anchor
+         starts from the prior with this one hit (l = clamp(L(n) + (L_hit - L(n)))),
+         zero feature and offsets, and scaling = voxel (readings).
+    FP32 throughout, one rounding per operation in the order written.
+    anc: dict pos [n,3], feat [n,F], offsets [n,K,3], scaling [n,3]; depth [H,W];
+    motion [H,W] uint8 or None (all static).  Returns a dict with the output
+    arrays (pos, feat, offsets, scaling, logodds), src ([m] int: source row, or
+    -1 - p for an anchor inserted from pixel p), n_kept, n_inserted, n_dropped
+    (new voxels beyond capacity), n_hit, n_miss."""
+    f = np.float32
+    pos = np.asarray(anc["pos"], np.float32).reshape(-1, 3)
+    n = pos.shape[0]
+    l = np.asarray(logodds_in, np.float32).reshape(n).copy()
+    obs = anchor_observe(pos, cam, depth, motion, acfg)
+    dh = f(acfg.l_hit) - f(acfg.l_prior)
+    dm = f(acfg.l_miss) - f(acfg.l_prior)
+    lo, hi = f(acfg.l_min), f(acfg.l_max)
+    upd = np.where(obs == 1, l + dh, l + dm)
+    l = np.where(obs != 0, np.minimum(np.maximum(upd, lo), hi), l)
+    keep = np.nonzero(l >= f(acfg.l_prune))[0]
+    # insertion candidates
+    R, t, fx, fy, cx, cy = _cam32(cam)
+    H, W = depth.shape
+    D = np.asarray(depth, np.float32)
+    cand = D > f(acfg.near_z)
+    if motion is not None:
+        cand &= np.asarray(motion) == 0
+    jj, ii = np.nonzero(cand)            # raster order
+    d = D[jj, ii]
+    Xc = [((ii.astype(np.float32) - cx) / fx) * d, ((jj.astype(np.float32) - cy) / fy) * d, d]
+    dd = [Xc[r] - t[r] for r in range(3)]
+    Xw = np.stack([(R[0, a] * dd[0] + R[1, a] * dd[1]) + R[2, a] * dd[2] for a in range(3)], axis=-1)
+    q, ok = _voxel(Xw, acfg.voxel)
+    pix = (jj * W + ii)[ok]
+    q = q[ok].astype(np.int64)
+    qa, oka = _voxel(pos[keep], acfg.voxel)
+    held = set(map(tuple, qa[oka].astype(np.int64)))
+    new_q, new_p = [], []
+    if len(q):
+        uq, first = np.unique(q, axis=0, return_index=True)
+        order = np.argsort(first, kind="stable")
+        for r in order:
+            key = tuple(uq[r])
+            if key not in held:
+                new_q.append(uq[r])
+                new_p.append(int(pix[first[r]]))
+    n_kept = len(keep)
+    n_ins = max(0, min(len(new_q), capacity - n_kept))
+    nq = np.array(new_q[:n_ins], np.float32).reshape(-1, 3)
+    F = np.asarray(anc["feat"]).shape[-1]
+    K = np.asarray(anc["offsets"]).shape[-2]
+    l_new = np.minimum(np.maximum(f(acfg.l_prior) + dh, lo), hi)
+    vox = f(acfg.voxel)
+    out = dict(
+        pos=np.concatenate([pos[keep], (nq + f(0.5)) * vox]),
+        feat=np.concatenate([np.asarray(anc["feat"], np.float32).reshape(n, F)[keep], np.zeros((n_ins, F), np.float32)]),
+        offsets=np.concatenate([np.asarray(anc["offsets"], np.float32).reshape(n, K, 3)[keep],
+                                np.zeros((n_ins, K, 3), np.float32)]),
+        scaling=np.concatenate([np.asarray(anc["scaling"], np.float32).reshape(n, 3)[keep],
+                                np.full((n_ins, 3), vox, np.float32)]),
+        logodds=np.concatenate([l[keep], np.full(n_ins, l_new, np.float32)]),
+        src=np.concatenate([keep.astype(np.int64), -1 - np.array(new_p[:n_ins], np.int64)]),
+        n_kept=n_kept, n_inserted=n_ins, n_dropped=len(new_q) - n_ins,
+        n_hit=int((obs == 1).sum()), n_miss=int((obs == 2).sum()))
+    return out
