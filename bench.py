@@ -291,6 +291,7 @@ def run_ours(args, wl_name):
     lift = run_lift(args, st, wl)
     ssim = run_ssim(args, st, wl)
     umlp = run_unc_mlp(args, st, wl)
+    anch = run_anchor(args, wl, anc, cams[0])
 
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -340,7 +341,10 @@ def run_ours(args, wl_name):
                           "uncertainty_mlp": dict(umlp, peak=round(152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6, 2),
                                                   frac=round(umlp["achieved_tflops"]
                                                              / (152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6), 4),
-                                                  peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock")},
+                                                  peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"),
+                          "anchor_update": dict(anch, peak=round(peaks["hbm_gbs"], 1),
+                                                frac=round(anch["achieved_gbs"] / peaks["hbm_gbs"], 4),
+                                                peak_source=peaks["source"])},
         }
         print(json.dumps(line))
     if world > 1:
@@ -515,6 +519,47 @@ def run_unc_mlp(args, st, wl, n_h=384, patch=14):
     return dict(ms=round(ms, 4), pixels=pix, n_h=n_h, algorithmic_flops=flops, bound="alu",
                 achieved_tflops=round(flops / (ms / 1e3) / 1e12, 3), unit="TFLOP/s",
                 note="first layer per DINO patch (exact by linearity), per-pixel rest on CUDA cores")
+
+
+def run_anchor(args, wl, anc, cam):
+    """Probabilistic anchor update (Eq. 7) with pruning and insertion: the bench
+    batch's anchors against one seeded synthetic keyframe of view 0 (scenes.keyframe:
+    depth surface with holes and a moving disc), through the public API; the
+    device time of the call's kernels from the library's stage events (the call
+    ends with one synchronisation that reads the counts back), and the host wall
+    time per call.  Algorithmic bytes: every input anchor row read once (pos,
+    feature, offsets, scaling, log-odds), every kept row written with its source
+    index, every keyframe pixel's depth and motion read, every new row written."""
+    import torch
+    from paper_2505_22335_gb300 import binding as B
+    from paper_2505_22335_gb300 import scenes
+    R = B.Renderer(n_feat=wl["NF"], k=wl["K"])
+    depth, motion = scenes.keyframe(7, cam)
+    t = lambda a, dt=torch.float32: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    ga = {k: t(anc[k]) for k in ("pos", "feat", "offsets", "scaling")}
+    lo = t(np.random.default_rng(8).uniform(-2.5, 3.5, wl["A"]))
+    dd, mm = t(depth), t(motion, torch.uint8)
+    call = lambda: R.anchor_update(ga, lo, cam, dd, mm, capacity=wl["A"] * 2)
+    for _ in range(3):
+        call()
+    R.profile_read()
+    R.profile(True)
+    n = max(10, args.steps)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(n):
+        _, _, _, cnt = call()
+    wall = (time.perf_counter() - w0) / n * 1e3
+    prof, launches = R.profile_read()
+    R.profile(False)
+    ms = prof["anchor_update"][0] / n
+    row = 4 * (3 + 32 + 3 * wl["K"] + 3 + 1)  # pos, feature (32), offsets, scaling, log-odds
+    P = cam.width * cam.height
+    nbytes = wl["A"] * row + cnt["n_kept"] * (row + 4) + P * 5 + cnt["n_inserted"] * (row + 4)
+    R.close()
+    return dict(ms=round(ms, 4), wall_ms_per_call=round(wall, 4), launches_per_call=launches / n,
+                anchors=wl["A"], pixels=P, counts=cnt, algorithmic_bytes=nbytes, bound="hbm",
+                achieved_gbs=round(nbytes / (ms / 1e3) / 1e9, 1), unit="GB/s")
 
 
 def run_e2e(args, st, anc, mlp, tg, world):

@@ -338,6 +338,70 @@ ups_status ups_uncertainty_mlp(ups_ctx *ctx, const ups_lift_cfg *lcfg, const flo
                                const ups_lift_mlp *mlp, float lambda, float scale, float *loss_dev,
                                ups_lift_mlp *d_mlp, float *sigma, unsigned char *motion, ups_stream stream);
 
+/* Probabilistic anchors (Sec. 3.3 "Adaptively Structured Gaussian", Eq. 7;
+ * the probabilistic octree of Sec. 1 read as a voxel grid of edge `voxel`
+ * holding the anchors).  One keyframe (cam, its depth map and motion mask):
+ *  1. update: each anchor n observed in the keyframe gets
+ *       L(n|z_1:t) = clamp(L(n|z_1:t-1) + (L(n|z_t) - L(n)), l_min, l_max),
+ *     Eq. 7 in log-odds form L(p) = log(p / (1 - p)), with the garbled last
+ *     factor of Eq. 7 read as P(n) / (1 - P(n)) (OctoMap's update, which the
+ *     paper cites).  Observation (reading; FP32, one rounding per operation):
+ *     the anchor centre x maps to X = R x + t (summed left to right) and to
+ *     pixel (floor(fx X/Z + cx + 1/2), floor(fy Y/Z + cy + 1/2)); with D the
+ *     depth there, Z <= near_z, a pixel outside the image or D <= near_z is no
+ *     observation, Z < D - margin (free space on the ray) a miss, Z <= D +
+ *     margin a hit (a miss on a pixel whose motion is nonzero), Z > D + margin
+ *     (hidden) no observation.  Unobserved anchors keep their log-odds.
+ *  2. prune: anchors whose log-odds is below l_prune are deleted; the others
+ *     keep their order (out rows 0 .. n_kept - 1).
+ *  3. insert: each pixel with D > near_z and motion 0 is back-projected,
+ *     x = R^T ((i - cx) / fx D - t_x, (j - cy) / fy D - t_y, D - t_z), to its
+ *     voxel floor(x / voxel) (indices in [-2^20, 2^20) per axis, others are
+ *     skipped); every voxel holding no kept anchor (an anchor holds the voxel
+ *     floor(pos / voxel)) gets a new anchor at its centre (q + 1/2) voxel, in
+ *     the raster order of the first pixel that reached it, while rows remain
+ *     below `capacity`: zero feature and offsets, scaling = voxel, log-odds =
+ *     clamp(l_prior + (l_hit - l_prior)) (the prior and this one hit).
+ *  in, logodds_in   n anchors (ups_anchors layout, feat_dim and k of the ctx)
+ *                   and their log-odds float [n]; may be empty (n = 0)
+ *  out, logodds_out capacity rows each (capacity >= in->n); must not overlap
+ *                   the inputs; out->n is set on return
+ *  depth            float [H][W] of the keyframe (metres; <= near_z: none)
+ *  motion           uint8 [H][W] (nonzero: dynamic), or NULL: all static
+ *  src_index        int [capacity] or NULL: the input row of each output row,
+ *                   -1 - p for a row inserted from pixel p = j W + i
+ *  res              counts of the call (may be NULL)
+ * Synchronises `stream` once to read the counts.  A voxel table that cannot
+ * hold the keys (it is sized for twice the anchors plus pixels, so this does
+ * not happen) fails with UPS_ERR_CAPACITY. */
+typedef struct {
+    float l_prior; /* L(P(n)), the prior (P(n) = 0.5) */
+    float l_hit;   /* L(P(n|z_t)) of a static surface observation (0.7) */
+    float l_miss;  /* L(P(n|z_t)) of free space or a dynamic surface (0.4) */
+    float l_min;   /* clamping of the posterior (0.12) */
+    float l_max;   /* (0.97) */
+    float l_prune; /* delete anchors below this (P = 0.5, i.e. 0) */
+    float voxel;   /* anchor voxel edge in metres (0.05) */
+    float margin;  /* half-width of the surface band along the ray (0.05) */
+    float near_z;  /* depths at or below this are not observations (0.2) */
+} ups_anchor_cfg;
+
+/* Fills the defaults listed above (OctoMap's probabilities as log-odds). */
+void ups_anchor_cfg_default(ups_anchor_cfg *cfg);
+
+typedef struct {
+    int n_kept;     /* input anchors that survived the pruning */
+    int n_inserted; /* new anchors written after them */
+    int n_dropped;  /* new voxels that found no row below capacity */
+    int n_hit;      /* anchors observed as hits / misses */
+    int n_miss;
+} ups_anchor_result;
+
+ups_status ups_anchor_update(ups_ctx *ctx, const ups_anchor_cfg *acfg, const ups_camera *cam, const float *depth,
+                             const unsigned char *motion, const ups_anchors *in, const float *logodds_in,
+                             ups_anchors *out, float *logodds_out, int capacity, int *src_index,
+                             ups_anchor_result *res, ups_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */

@@ -69,6 +69,15 @@ class LossCfg(C.Structure):
                 ("lambda_scale", _f), ("l2", _i)]
 
 
+class AnchorCfg(C.Structure):
+    _fields_ = [("l_prior", _f), ("l_hit", _f), ("l_miss", _f), ("l_min", _f), ("l_max", _f), ("l_prune", _f),
+                ("voxel", _f), ("margin", _f), ("near_z", _f)]
+
+
+class AnchorResult(C.Structure):
+    _fields_ = [("n_kept", _i), ("n_inserted", _i), ("n_dropped", _i), ("n_hit", _i), ("n_miss", _i)]
+
+
 class Anchors(C.Structure):
     _fields_ = [("n", _i), ("pos", _p), ("feat", _p), ("offsets", _p), ("scaling", _p)]
 
@@ -103,7 +112,8 @@ class Stats(C.Structure):
 # every entry point of include/ups.h (checked by the CPU test suite)
 EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "ups_last_error",
            "ups_decode_anchors", "ups_render_forward", "ups_loss_weighted", "ups_tracking_uncertainty",
-           "ups_feature_lift", "ups_ssim_loss", "ups_uncertainty_mlp",
+           "ups_feature_lift", "ups_ssim_loss", "ups_uncertainty_mlp", "ups_anchor_cfg_default",
+           "ups_anchor_update",
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
@@ -145,6 +155,9 @@ def load():
                                       C.POINTER(LiftMLP), _p, _p, _p]
     L.ups_feature_lift.argtypes = [_p, C.POINTER(LiftCfg), _p, _p, C.POINTER(LiftMLP), _p, _f, _p,
                                    C.POINTER(LiftMLP), _p, _p]
+    L.ups_anchor_cfg_default.argtypes = [C.POINTER(AnchorCfg)]
+    L.ups_anchor_update.argtypes = [_p, C.POINTER(AnchorCfg), C.POINTER(Camera), _p, _p, C.POINTER(Anchors), _p,
+                                    C.POINTER(Anchors), _p, _i, _p, C.POINTER(AnchorResult), _p]
     L.ups_render_backward.argtypes = [_p, C.POINTER(ImageGrads), C.c_uint, _f,
                                       C.POINTER(Gaussians), _p, _p]
     L.ups_decode_backward.argtypes = [_p, C.POINTER(Anchors), C.POINTER(MLP), C.POINTER(Camera), _i,
@@ -394,6 +407,37 @@ class Renderer:
                                              C.byref(dm) if dm is not None else None, _ptr(d_feat),
                                              _stream(stream)))
         return loss_out
+
+    def anchor_update(self, anchors, logodds, cam, depth, motion=None, capacity=None, stream=None, **cfg):
+        """Eq. 7 on one keyframe: update, prune and insert anchors (dicts of device
+        tensors pos [n,3], feat [n,F], offsets [n,K,3], scaling [n,3]; logodds [n]).
+        cfg overrides fields of ups_anchor_cfg.  Returns (anchors, logodds, src_index,
+        counts) with the outputs cut to the new anchor count."""
+        import torch
+        n = int(anchors["pos"].shape[0])
+        cap = n if capacity is None else int(capacity)
+        dev = anchors["pos"].device
+        F = int(anchors["feat"].shape[1])
+        K = int(anchors["offsets"].shape[1])
+        if F != self.cfg.feat_dim or K != self.k:
+            raise ValueError(f"anchors have feat width {F} and k {K}; the context has {self.cfg.feat_dim} and {self.k}")
+        z = lambda *sh: torch.empty(*sh, dtype=torch.float32, device=dev)
+        out = dict(pos=z(cap, 3), feat=z(cap, F), offsets=z(cap, K, 3), scaling=z(cap, 3))
+        lout = z(cap)
+        src = torch.empty(cap, dtype=torch.int32, device=dev)
+        ac = AnchorCfg()
+        self._L.ups_anchor_cfg_default(C.byref(ac))
+        for key, val in cfg.items():
+            setattr(ac, key, float(val))
+        ca = Anchors(n, *(_ptr(anchors[k]) for k in ("pos", "feat", "offsets", "scaling")))
+        co = Anchors(cap, *(_ptr(out[k]) for k in ("pos", "feat", "offsets", "scaling")))
+        res = AnchorResult()
+        self._check(self._L.ups_anchor_update(self._h, C.byref(ac), make_cameras([cam]), _ptr(depth), _ptr(motion),
+                                              C.byref(ca), _ptr(logodds), C.byref(co), _ptr(lout), cap, _ptr(src),
+                                              C.byref(res), _stream(stream)))
+        m = co.n
+        return ({k: v[:m] for k, v in out.items()}, lout[:m], src[:m],
+                {k: getattr(res, k) for k, _ in AnchorResult._fields_})
 
     # -------------------------------------------------------------- backward
     def backward(self, dL, mask=GRAD_POSE | GRAD_GAUSS, scale_grad=0.0, grad: GaussianSet | None = None,

@@ -38,6 +38,13 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
                                  const int *gate = nullptr);
+size_t anchor_scratch_bytes(size_t n, size_t P);
+cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t *motion, int n, const float *pos,
+                          const float *feat, const float *offsets, const float *scaling, const float *lin, int F,
+                          int K3, float l_prior, float l_hit, float l_miss, float l_min, float l_max, float l_prune,
+                          float voxel, float margin, float near_z, long long capacity, float *opos, float *ofeat,
+                          float *ooffsets, float *oscaling, float *olog, int *src_index, void *scratch,
+                          uint64_t **summary_dev, int num_sms, cudaStream_t st, int *launches);
 size_t unc_scratch_floats(int max_patches);
 cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
                      int hp, const float *R, const float *w1, const float *b1, const float *w2, const float *b2,
@@ -138,6 +145,8 @@ struct ups_ctx {
     DevBuf lift_scr;              // feature-lifting scratch of one view
     DevBuf ssim_g;                // D-SSIM window-term maps of all colour planes
     DevBuf unc_scr;               // uncertainty-MLP patch scratch of one view
+    DevBuf anchor_scr;            // probabilistic-anchor update: flags, scans, voxel table
+    uint64_t *h_anchor = nullptr;  // pinned: the anchor update's counts
     bool ssim_window = false;     // the SSIM window is in this device's constant memory
     // stage profiler (CUDA events on the launch stream) and kernel-launch count
     bool prof = false;
@@ -349,6 +358,20 @@ void ups_config_default(ups_config *cfg) {
     cfg->list_cap = 1024;
 }
 
+void ups_anchor_cfg_default(ups_anchor_cfg *cfg) {
+    if (!cfg) return;
+    auto L = [](double p) { return (float)std::log(p / (1.0 - p)); };
+    cfg->l_prior = L(0.5);
+    cfg->l_hit = L(0.7);
+    cfg->l_miss = L(0.4);
+    cfg->l_min = L(0.12);
+    cfg->l_max = L(0.97);
+    cfg->l_prune = L(0.5);
+    cfg->voxel = 0.05f;
+    cfg->margin = 0.05f;
+    cfg->near_z = 0.2f;
+}
+
 const char *ups_version(void) { return "ups-gb300 0.1 (sm_103a)"; }
 
 ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
@@ -400,9 +423,10 @@ ups_status ups_destroy(ups_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *bufs[] = {&c->xyzo, &c->conic, &c->rect, &c->count, &c->dkey0, &c->dkey1, &c->dval0,
                       &c->dval1, &c->cnt_sorted, &c->off, &c->scan_scr, &c->ikey0, &c->ikey1,
-                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr, &c->ssim_g, &c->unc_scr};
+                      &c->ival0, &c->ival1, &c->ranges, &c->g2, &c->dec_scratch, &c->sort.hist, &c->trunc, &c->lift_scr, &c->ssim_g, &c->unc_scr, &c->anchor_scr};
     for (DevBuf *b : bufs) b->release();
     if (c->h_total) cudaFreeHost(c->h_total);
+    if (c->h_anchor) cudaFreeHost(c->h_anchor);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_trunc_flag) cudaFree(c->d_trunc_flag);
     lift_handle_destroy(c->cublas);
@@ -655,6 +679,84 @@ ups_status ups_uncertainty_mlp(ups_ctx *c, const ups_lift_cfg *lcfg, const float
         grid_off += (size_t)hp * wp * lcfg->n_h;
     }
     stage_end(c, st, launches);
+    return UPS_OK;
+}
+
+namespace {
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    if (!a || !b || na == 0 || nb == 0) return false;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+}  // namespace
+
+ups_status ups_anchor_update(ups_ctx *c, const ups_anchor_cfg *a, const ups_camera *cam, const float *depth,
+                             const unsigned char *motion, const ups_anchors *in, const float *logodds_in,
+                             ups_anchors *out, float *logodds_out, int capacity, int *src_index,
+                             ups_anchor_result *res, ups_stream stream) {
+    if (!c) return UPS_ERR_ARG;
+    if (!a || !cam || !depth || !in || !out || !logodds_out) return fail(c, UPS_ERR_ARG, "NULL argument");
+    const int n = in->n;
+    if (n < 0 || capacity < n) return fail(c, UPS_ERR_ARG, "need 0 <= in->n <= capacity");
+    if (n > 0 && (!in->pos || !in->feat || !in->offsets || !in->scaling || !logodds_in))
+        return fail(c, UPS_ERR_ARG, "NULL input anchor array");
+    if (capacity > 0 && (!out->pos || !out->feat || !out->offsets || !out->scaling))
+        return fail(c, UPS_ERR_ARG, "NULL output anchor array");
+    const float lv[6] = {a->l_prior, a->l_hit, a->l_miss, a->l_min, a->l_max, a->l_prune};
+    for (float v : lv)
+        if (!std::isfinite(v)) return fail(c, UPS_ERR_ARG, "non-finite log-odds in the anchor config");
+    if (!(a->l_min <= a->l_max)) return fail(c, UPS_ERR_ARG, "l_min > l_max");
+    if (!(a->voxel > 0.f) || !std::isfinite(a->voxel) || !(a->margin >= 0.f) || !std::isfinite(a->margin) ||
+        !std::isfinite(a->near_z))
+        return fail(c, UPS_ERR_ARG, "voxel must be > 0, margin >= 0, all finite");
+    ViewTable vt;
+    size_t npix = 0;
+    int mhw = 0;
+    ups_status s = build_views(c, cam, 1, vt, npix, mhw);
+    if (s != UPS_OK) return s;
+    if (npix + (size_t)capacity > ((size_t)1 << 29)) return fail(c, UPS_ERR_ARG, "too many anchors plus pixels");
+    const int F = c->cfg.feat_dim, K3 = 3 * c->cfg.k;
+    const size_t fb = sizeof(float), cn = (size_t)capacity, nn = (size_t)n;
+    const void *ins[5] = {in->pos, in->feat, in->offsets, in->scaling, logodds_in};
+    const size_t inb[5] = {3 * nn * fb, F * nn * fb, K3 * nn * fb, 3 * nn * fb, nn * fb};
+    const void *outs[6] = {out->pos, out->feat, out->offsets, out->scaling, logodds_out, src_index};
+    const size_t outb[6] = {3 * cn * fb, F * cn * fb, K3 * cn * fb, 3 * cn * fb, cn * fb, cn * sizeof(int)};
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j < 5; ++j)
+            if (overlaps(outs[i], outb[i], ins[j], inb[j]))
+                return fail(c, UPS_ERR_ARG, "output anchor arrays overlap the inputs");
+        for (int j = 0; j < i; ++j)
+            if (overlaps(outs[i], outb[i], outs[j], outb[j]))
+                return fail(c, UPS_ERR_ARG, "output anchor arrays overlap each other");
+    }
+    s = set_device(c);
+    if (s != UPS_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    UPS_CUDA(c, c->anchor_scr.reserve(anchor_scratch_bytes(nn, npix)));
+    if (!c->h_anchor) UPS_CUDA(c, cudaMallocHost(&c->h_anchor, 8 * sizeof(uint64_t)));
+    stage_begin(c, "anchor_update", st);
+    int launches = 0;
+    uint64_t *summary = nullptr;
+    UPS_CUDA(c, anchor_update(vt.v[0], depth, motion, n, in->pos, in->feat, in->offsets, in->scaling, logodds_in, F,
+                              K3, a->l_prior, a->l_hit, a->l_miss, a->l_min, a->l_max, a->l_prune, a->voxel,
+                              a->margin, a->near_z, capacity, out->pos, out->feat, out->offsets, out->scaling,
+                              logodds_out, src_index, c->anchor_scr.ptr, &summary, c->num_sms, st, &launches));
+    stage_end(c, st, launches);
+    UPS_CUDA(c, cudaMemcpyAsync(c->h_anchor, summary, 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    UPS_CUDA(c, cudaStreamSynchronize(st));
+    const uint64_t *h = c->h_anchor;
+    if (h[4] != 0) return fail(c, UPS_ERR_CAPACITY, "voxel table full");
+    const long long kept = (long long)h[0], fresh = (long long)h[1];
+    const long long ins_n = std::max(0LL, std::min(fresh, (long long)capacity - kept));
+    out->n = (int)(kept + ins_n);
+    if (res) {
+        res->n_kept = (int)kept;
+        res->n_inserted = (int)ins_n;
+        res->n_dropped = (int)(fresh - ins_n);
+        res->n_hit = (int)h[2];
+        res->n_miss = (int)h[3];
+    }
     return UPS_OK;
 }
 

@@ -15,7 +15,12 @@ stand in for them:
   log-uniform in [0.01, 0.1];
 * MLP weights (Eq. 8-9): Kaiming-uniform from a seed, zero biases;
 * keyframe poses on a 3 m arc (radius 2.5 m about the cube centre, +-30 deg),
-  jittered by 0.3 m and 10 deg.
+  jittered by 0.3 m and 10 deg;
+* keyframes for the probabilistic anchor map (Eq. 7): a tilted, bumpy depth
+  surface 1.5-4 m away with 5 % of the pixels missing, a moving object (a disc
+  0.4-0.8 m nearer) marked in the motion mask, and anchors seen from that
+  keyframe: half on the surface (depth +- 3 cm), a fifth in the free space in
+  front of it, the rest hidden behind it or anywhere in a 6 m box.
 
 All arrays are float64 numpy; callers cast to float32 for the GPU.
 """
@@ -200,3 +205,40 @@ def workload_anchor(seed, n_anchor, k, n_feat, n_views, width, height, fx,
     m = mlp_weights(seed + 1000, k, n_feat)
     cams = cameras(seed, n_views, width, height, fx, identity=identity)
     return a, m, cams
+
+
+def keyframe(seed: int, cam: Camera, *, hole_frac=0.05):
+    """Depth map [H, W] (0 = missing) and motion mask [H, W] uint8 of one keyframe."""
+    rng = _rng(seed)
+    H, W = cam.height, cam.width
+    yy, xx = np.mgrid[0:H, 0:W] / max(H, W)
+    a, b, c = rng.uniform(1.0, 1.5, 3)
+    depth = 1.5 + a * xx + 0.5 * b * yy + 0.3 * np.sin(6.0 * c * xx) * np.cos(4.0 * yy)
+    depth = np.clip(depth + rng.uniform(0.0, 0.01, (H, W)), 1.5, 4.0)
+    cx, cy, r = rng.uniform(0.3, 0.7) * W, rng.uniform(0.3, 0.7) * H, rng.uniform(0.08, 0.15) * max(H, W)
+    jj, ii = np.mgrid[0:H, 0:W]
+    disc = (ii - cx) ** 2 + (jj - cy) ** 2 < r * r
+    depth[disc] -= rng.uniform(0.4, 0.8)
+    depth[rng.uniform(size=(H, W)) < hole_frac] = 0.0
+    return depth, disc.astype(np.uint8)
+
+
+def anchor_cloud(seed: int, cam: Camera, depth, n: int, k: int, feat_dim: int = 32):
+    """n anchors around the keyframe's surface (positions from the inverse pose,
+    float64), with features, offsets, scalings and log-odds U(-2.5, 3.5)."""
+    rng = _rng(seed)
+    H, W = depth.shape
+    T_wc = np.linalg.inv(np.asarray(cam.T_cw, float))
+    kind = rng.choice(4, size=n, p=[0.5, 0.2, 0.15, 0.15])
+    i = rng.uniform(-0.5, W - 0.5, n)
+    j = rng.uniform(-0.5, H - 0.5, n)
+    d = depth[np.clip(np.rint(j), 0, H - 1).astype(int), np.clip(np.rint(i), 0, W - 1).astype(int)]
+    d = np.where(d > 0, d, 2.5)
+    z = np.where(kind == 0, d + rng.uniform(-0.03, 0.03, n),
+                 np.where(kind == 1, d * rng.uniform(0.3, 0.9, n), d * rng.uniform(1.1, 1.5, n)))
+    Xc = np.stack([(i - cam.cx) / cam.fx * z, (j - cam.cy) / cam.fy * z, z, np.ones(n)])
+    pos = (T_wc @ Xc)[:3].T
+    box = T_wc[:3, 3] + rng.uniform(-3.0, 3.0, (n, 3))
+    pos = np.where((kind == 3)[:, None], box, pos)
+    return dict(pos=pos, feat=rng.normal(0.0, 0.1, (n, feat_dim)), offsets=rng.normal(0.0, 0.05, (n, k, 3)),
+                scaling=np.exp(rng.uniform(np.log(0.01), np.log(0.1), (n, 3)))), rng.uniform(-2.5, 3.5, n)
