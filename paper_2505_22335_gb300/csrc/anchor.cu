@@ -11,17 +11,18 @@
 // operation in a fixed order (the __f*_rn intrinsics are never contracted into
 // FMAs), so the results do not depend on the compiler.
 //
-// Launches for n anchors and P keyframe pixels:
-//   k_observe       anchor -> pixel -> hit / miss / none, posterior, keep flag
-//   scan(keep)      output row of each kept anchor (3 launches)
-//   k_compact       kept rows into the output arrays, in input order
-//   k_hash_anchors  voxels of the kept anchors into an open-addressing table
-//   k_hash_pixels   voxel of every static pixel into the table; the voxel's
-//                   owner becomes its lowest pixel index (atomicMin)
-//   k_first         flag the pixels that own a voxel no kept anchor holds
-//   scan(flags)     raster-order rank of each new voxel (3 launches)
-//   k_insert        a new anchor at the centre of each new voxel, to capacity
-//   k_summary       the five counts the host reads back
+// Five launches for n anchors and P keyframe pixels, with no separate scan:
+// each producer writes per-block counts and each consumer block sums the
+// counts of the blocks before it to find its output offset.
+//   k_observe      anchor -> pixel -> hit / miss / none, posterior; per block
+//                  of 256 anchors the number kept, hits and misses
+//   k_compact      kept rows into the output arrays in input order, their
+//                  voxels into an open-addressing table (held by an anchor)
+//   k_hash_pixels  the voxel of every static pixel into the table; the voxel's
+//                  owner becomes its lowest pixel index (atomicMin)
+//   k_count_new    per block of 1024 pixels, the new voxels they own; totals
+//   k_insert       a new anchor at the centre of each new voxel, in the raster
+//                  order of the owners, while rows remain below capacity
 #include <algorithm>
 
 #include "common.cuh"
@@ -34,6 +35,8 @@ constexpr int kAThreads = 256;
 constexpr int kVoxRange = 1 << 20;                  // voxel indices in [-2^20, 2^20)
 constexpr unsigned long long kEmptyKey = ~0ull;      // table slot without a key
 constexpr int kNoOwner = 0x7f7f7f7f;                 // memset byte 0x7f: above every pixel index
+constexpr int kPixPerThread = 4;                     // consecutive pixels per thread (k_count_new, k_insert)
+constexpr int kPixBlock = kAThreads * kPixPerThread;
 
 struct AParams {
     float dh, dm;          // L(hit) - L(n), L(miss) - L(n)
@@ -85,15 +88,68 @@ __device__ __forceinline__ float dot3_rn(float a, float b, float c, float x, flo
     return __fadd_rn(__fadd_rn(__fmul_rn(a, x), __fmul_rn(b, y)), __fmul_rn(c, z));
 }
 
-// Observation of each anchor (0 none, 1 hit, 2 miss), its posterior and keep flag.
+// ---------------------------------------------------------------------------
+// block-wide helpers (kAThreads = 8 warps)
+// ---------------------------------------------------------------------------
+
+// Sum of v over the block, returned to every thread.
+__device__ __forceinline__ int block_sum(int v, int *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < kAThreads / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Exclusive prefix of v over the threads of the block; *total gets the sum.
+__device__ __forceinline__ int block_excl_scan(int v, int *red, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) red[w] = x;
+    __syncthreads();
+    int off = 0, t = 0;
+#pragma unroll
+    for (int k = 0; k < kAThreads / 32; ++k) {
+        off += k < w ? red[k] : 0;
+        t += red[k];
+    }
+    __syncthreads();
+    *total = t;
+    return off + x - v;
+}
+
+// Sum of cnt[0 .. b): the output offset of block b.  Every block reads the
+// counts of the blocks before it (a few hundred to a few thousand ints for
+// keyframe-sized inputs), which costs less than separate scan launches.
+__device__ __forceinline__ int block_prefix(const int *__restrict__ cnt, int b, int *red) {
+    int acc = 0;
+    for (int j = threadIdx.x; j < b; j += kAThreads) acc += cnt[j];
+    return block_sum(acc, red);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Observation of each anchor (0 none, 1 hit, 2 miss) and its posterior; per
+// block of kAThreads anchors, the number kept and the hits and misses.
 __global__ void __launch_bounds__(kAThreads) k_observe(int n, const float *__restrict__ pos,
                                                        const float *__restrict__ lin, DevView cam,
                                                        const float *__restrict__ depth,
                                                        const uint8_t *__restrict__ motion, AParams ap,
-                                                       float *__restrict__ lnew, uint32_t *__restrict__ keep,
-                                                       unsigned int *__restrict__ counts) {
+                                                       float *__restrict__ lnew, int *__restrict__ bkept,
+                                                       int *__restrict__ bhit, int *__restrict__ bmiss) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int obs = 0;
+    int obs = 0, kept = 0;
     if (i < n) {
         const float x = pos[3 * (size_t)i], y = pos[3 * (size_t)i + 1], z = pos[3 * (size_t)i + 2];
         const float X = __fadd_rn(dot3_rn(cam.R[0], cam.R[1], cam.R[2], x, y, z), cam.t[0]);
@@ -118,63 +174,60 @@ __global__ void __launch_bounds__(kAThreads) k_observe(int n, const float *__res
         float l = lin[i];
         if (obs) l = fminf(fmaxf(__fadd_rn(l, obs == 1 ? ap.dh : ap.dm), ap.l_min), ap.l_max);
         lnew[i] = l;
-        keep[i] = l >= ap.l_prune ? 1u : 0u;
+        kept = l >= ap.l_prune;
     }
-    const unsigned hb = __ballot_sync(0xffffffffu, obs == 1), mb = __ballot_sync(0xffffffffu, obs == 2);
-    if ((threadIdx.x & 31) == 0) {
-        if (hb) atomicAdd(counts, (unsigned)__popc(hb));
-        if (mb) atomicAdd(counts + 1, (unsigned)__popc(mb));
+    const int k = __syncthreads_count(kept), h = __syncthreads_count(obs == 1), m = __syncthreads_count(obs == 2);
+    if (threadIdx.x == 0) {
+        bkept[blockIdx.x] = k;
+        bhit[blockIdx.x] = h;
+        bmiss[blockIdx.x] = m;
     }
 }
 
-// One output array per blockIdx.y: kept row i goes to row off[i].
-struct CompactArgs {
-    const float *src[5];
+// Kept rows (the same kAThreads-row blocks as k_observe) to their output rows in
+// input order, their source index, and their voxels into the table.
+struct RowArrays {
+    const float *src[5];  // pos, feat, offsets, scaling, posterior log-odds
     float *dst[5];
     int width[5];
     int *src_index;
 };
-__global__ void __launch_bounds__(kAThreads) k_compact(int n, const uint32_t *__restrict__ keep,
-                                                       const uint64_t *__restrict__ off, CompactArgs a) {
-    const int y = blockIdx.y;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    if (y == 5) {
-        if (!a.src_index) return;
-        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n; i += stride)
-            if (keep[i]) a.src_index[off[i]] = (int)i;
-        return;
+__global__ void __launch_bounds__(kAThreads) k_compact(int n, const float *__restrict__ lnew,
+                                                       const int *__restrict__ bkept, float l_prune, RowArrays a,
+                                                       float voxel, unsigned long long *keys, int *vals,
+                                                       uint32_t mask, int *err) {
+    __shared__ int red[kAThreads / 32];
+    __shared__ int s_row[kAThreads];
+    const int r0 = blockIdx.x * kAThreads, i = r0 + threadIdx.x;
+    const int base = block_prefix(bkept, blockIdx.x, red);
+    const int flag = (i < n && lnew[i] >= l_prune) ? 1 : 0;
+    int total;
+    const int row = base + block_excl_scan(flag, red, &total);
+    s_row[threadIdx.x] = flag ? row : -1;
+    if (flag) {
+        if (a.src_index) a.src_index[row] = i;
+        const float *x = a.src[0] + 3 * (size_t)i;
+        unsigned long long key;
+        if (voxel_key(x[0], x[1], x[2], voxel, key)) {
+            const int s = table_slot(keys, mask, key);
+            if (s < 0)
+                atomicExch(err, 1);
+            else
+                atomicMin(vals + s, -1);  // held by an anchor
+        }
     }
-    // a switch, not a.src[y]: indexing the parameter arrays would copy them to the stack
-    int w;
-    const float *s;
-    float *d;
-    switch (y) {
-        case 0: w = a.width[0], s = a.src[0], d = a.dst[0]; break;
-        case 1: w = a.width[1], s = a.src[1], d = a.dst[1]; break;
-        case 2: w = a.width[2], s = a.src[2], d = a.dst[2]; break;
-        case 3: w = a.width[3], s = a.src[3], d = a.dst[3]; break;
-        default: w = a.width[4], s = a.src[4], d = a.dst[4]; break;
+    __syncthreads();
+    const int nrows = min(kAThreads, n - r0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int w = a.width[q];
+        const float *__restrict__ src = a.src[q] + (size_t)r0 * w;
+        float *__restrict__ dst = a.dst[q];
+        for (int e = threadIdx.x; e < nrows * w; e += kAThreads) {
+            const int rl = e / w, r = s_row[rl];
+            if (r >= 0) dst[(size_t)r * w + (e - rl * w)] = src[e];
+        }
     }
-    const size_t total = (size_t)n * w;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += stride) {
-        const size_t i = e / w;
-        if (keep[i]) d[off[i] * w + (e - i * w)] = s[e];
-    }
-}
-
-__global__ void __launch_bounds__(kAThreads) k_hash_anchors(int n, const float *__restrict__ pos,
-                                                            const uint32_t *__restrict__ keep, float voxel,
-                                                            unsigned long long *keys, int *vals, uint32_t mask,
-                                                            int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !keep[i]) return;
-    unsigned long long key;
-    if (!voxel_key(pos[3 * (size_t)i], pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2], voxel, key)) return;
-    const int s = table_slot(keys, mask, key);
-    if (s < 0)
-        atomicExch(err, 1);
-    else
-        atomicMin(vals + s, -1);
 }
 
 // Back-projection of pixel (i, j) at depth D to the world:
@@ -202,18 +255,49 @@ __global__ void __launch_bounds__(kAThreads) k_hash_pixels(DevView cam, const fl
             if (s < 0)
                 atomicExch(err, 1);
             else
-                atomicMin(vals + s, p);
+                atomicMin(vals + s, p);  // the voxel's owner: its first pixel in raster order
         }
     }
     slot_of[p] = s;
 }
 
-__global__ void __launch_bounds__(kAThreads) k_first(int P, const int *__restrict__ slot_of,
-                                                     const int *__restrict__ vals, uint32_t *__restrict__ flags) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+// pixel p is the owner of a voxel that no kept anchor holds
+__device__ __forceinline__ int owns_new(int P, int p, const int *__restrict__ slot_of, const int *__restrict__ vals) {
+    if (p >= P) return 0;
     const int s = slot_of[p];
-    flags[p] = (s >= 0 && vals[s] == p) ? 1u : 0u;
+    return (s >= 0 && vals[s] == p) ? 1 : 0;
+}
+
+// Per block of kPixBlock pixels, the number of new voxels it owns; block 0
+// also totals the anchor counts (n_kept, hits, misses) into the summary.
+__global__ void __launch_bounds__(kAThreads) k_count_new(int P, const int *__restrict__ slot_of,
+                                                         const int *__restrict__ vals, int *__restrict__ pnew,
+                                                         int nb, const int *__restrict__ bkept,
+                                                         const int *__restrict__ bhit, const int *__restrict__ bmiss,
+                                                         uint64_t *__restrict__ summary) {
+    __shared__ int red[kAThreads / 32];
+    const int p0 = blockIdx.x * kPixBlock + kPixPerThread * threadIdx.x;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kPixPerThread; ++k) c += owns_new(P, p0 + k, slot_of, vals);
+    c = block_sum(c, red);
+    if (threadIdx.x == 0) pnew[blockIdx.x] = c;
+    if (blockIdx.x == 0) {
+        int kk = 0, hh = 0, mm = 0;
+        for (int j = threadIdx.x; j < nb; j += kAThreads) {
+            kk += bkept[j];
+            hh += bhit[j];
+            mm += bmiss[j];
+        }
+        kk = block_sum(kk, red);
+        hh = block_sum(hh, red);
+        mm = block_sum(mm, red);
+        if (threadIdx.x == 0) {
+            summary[0] = (uint64_t)kk;
+            summary[2] = (uint64_t)hh;
+            summary[3] = (uint64_t)mm;
+        }
+    }
 }
 
 struct InsertArgs {
@@ -221,38 +305,45 @@ struct InsertArgs {
     int *src_index;
     int F, K3;
 };
-__global__ void __launch_bounds__(kAThreads) k_insert(int P, const uint32_t *__restrict__ flags,
-                                                      const uint64_t *__restrict__ off2,
-                                                      const uint64_t *__restrict__ n_kept, long long capacity,
-                                                      const int *__restrict__ slot_of,
+// A new anchor at the centre of every new voxel, at row n_kept + (its rank in
+// the raster order of the owning pixels), while rows remain below capacity.
+// The last block writes the number of new voxels and the table-overflow flag.
+__global__ void __launch_bounds__(kAThreads) k_insert(int P, const int *__restrict__ slot_of,
+                                                      const int *__restrict__ vals, const int *__restrict__ pnew,
                                                       const unsigned long long *__restrict__ keys, AParams ap,
-                                                      InsertArgs o) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P || !flags[p]) return;
-    const unsigned long long r = *n_kept + off2[p];
-    if (r >= (unsigned long long)capacity) return;
-    const unsigned long long key = keys[slot_of[p]];
-    const int q[3] = {(int)(key >> 42) - kVoxRange, (int)((key >> 21) & 0x1fffff) - kVoxRange,
-                      (int)(key & 0x1fffff) - kVoxRange};
+                                                      long long capacity, InsertArgs o, uint64_t *summary,
+                                                      const int *err) {
+    __shared__ int red[kAThreads / 32];
+    const int p0 = blockIdx.x * kPixBlock + kPixPerThread * threadIdx.x;
+    const int base = block_prefix(pnew, blockIdx.x, red);
+    int f[kPixPerThread], c = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o.pos[3 * r + a] = __fmul_rn(__fadd_rn((float)q[a], 0.5f), ap.voxel);
-        o.scaling[3 * r + a] = ap.voxel;
+    for (int k = 0; k < kPixPerThread; ++k) c += (f[k] = owns_new(P, p0 + k, slot_of, vals));
+    int total;
+    int rank = base + block_excl_scan(c, red, &total);
+    const long long n_kept = (long long)summary[0];
+#pragma unroll
+    for (int k = 0; k < kPixPerThread; ++k) {
+        if (!f[k]) continue;
+        const long long r = n_kept + rank++;
+        if (r >= capacity) continue;
+        const int p = p0 + k;
+        const unsigned long long key = keys[slot_of[p]];
+        const int q[3] = {(int)(key >> 42) - kVoxRange, (int)((key >> 21) & 0x1fffff) - kVoxRange,
+                          (int)(key & 0x1fffff) - kVoxRange};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o.pos[3 * r + a] = __fmul_rn(__fadd_rn((float)q[a], 0.5f), ap.voxel);
+            o.scaling[3 * r + a] = ap.voxel;
+        }
+        for (int cc = 0; cc < o.F; ++cc) o.feat[r * o.F + cc] = 0.f;
+        for (int cc = 0; cc < o.K3; ++cc) o.offsets[r * o.K3 + cc] = 0.f;
+        o.logodds[r] = ap.l_new;
+        if (o.src_index) o.src_index[r] = -1 - p;
     }
-    for (int c = 0; c < o.F; ++c) o.feat[r * o.F + c] = 0.f;
-    for (int c = 0; c < o.K3; ++c) o.offsets[r * o.K3 + c] = 0.f;
-    o.logodds[r] = ap.l_new;
-    if (o.src_index) o.src_index[r] = -1 - p;
-}
-
-__global__ void k_summary(const uint64_t *n_kept, const uint64_t *n_new, const unsigned int *counts,
-                          uint64_t *out) {
-    if (threadIdx.x == 0) {
-        out[0] = *n_kept;
-        out[1] = *n_new;
-        out[2] = counts[0];
-        out[3] = counts[1];
-        out[4] = counts[2];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        summary[1] = (uint64_t)(base + total);
+        summary[4] = (uint64_t)*err;
     }
 }
 
@@ -265,13 +356,14 @@ uint32_t table_size(size_t n, size_t P) {
 }
 
 struct Layout {
-    size_t lnew, keep, off, scan, keys, vals, slot, flags, off2, counts, summary, total;
+    size_t lnew, bkept, bhit, bmiss, keys, vals, slot, pnew, summary, err, total;
     uint32_t S;
 };
 
 Layout layout(size_t n, size_t P) {
     Layout L{};
     L.S = table_size(n, P);
+    const size_t nb = (n + kAThreads - 1) / kAThreads, npb = (P + kPixBlock - 1) / kPixBlock;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
@@ -279,16 +371,15 @@ Layout layout(size_t n, size_t P) {
         return at;
     };
     L.lnew = take(n * sizeof(float));
-    L.keep = take(n * sizeof(uint32_t));
-    L.off = take((n + 1) * sizeof(uint64_t));
-    L.scan = take(scan_scratch_bytes(std::max(n, P)));
+    L.bkept = take(nb * sizeof(int));
+    L.bhit = take(nb * sizeof(int));
+    L.bmiss = take(nb * sizeof(int));
     L.keys = take((size_t)L.S * sizeof(unsigned long long));
     L.vals = take((size_t)L.S * sizeof(int));
     L.slot = take(P * sizeof(int));
-    L.flags = take(P * sizeof(uint32_t));
-    L.off2 = take((P + 1) * sizeof(uint64_t));
-    L.counts = take(3 * sizeof(unsigned int));
+    L.pnew = take(npb * sizeof(int));
     L.summary = take(5 * sizeof(uint64_t));
+    L.err = take(sizeof(int));
     L.total = o;
     return L;
 }
@@ -307,21 +398,20 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
                           float voxel, float margin, float near_z, long long capacity, float *opos, float *ofeat,
                           float *ooffsets, float *oscaling, float *olog, int *src_index, void *scratch,
                           uint64_t **summary_dev, int num_sms, cudaStream_t st, int *launches) {
+    (void)num_sms;
     const size_t P = (size_t)cam.W * cam.H;
     const Layout L = layout((size_t)n, P);
     char *base = static_cast<char *>(scratch);
     float *lnew = reinterpret_cast<float *>(base + L.lnew);
-    uint32_t *keep = reinterpret_cast<uint32_t *>(base + L.keep);
-    uint64_t *off = reinterpret_cast<uint64_t *>(base + L.off);
-    void *scan = base + L.scan;
+    int *bkept = reinterpret_cast<int *>(base + L.bkept);
+    int *bhit = reinterpret_cast<int *>(base + L.bhit);
+    int *bmiss = reinterpret_cast<int *>(base + L.bmiss);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(base + L.keys);
     int *vals = reinterpret_cast<int *>(base + L.vals);
     int *slot_of = reinterpret_cast<int *>(base + L.slot);
-    uint32_t *flags = reinterpret_cast<uint32_t *>(base + L.flags);
-    uint64_t *off2 = reinterpret_cast<uint64_t *>(base + L.off2);
-    unsigned int *counts = reinterpret_cast<unsigned int *>(base + L.counts);  // hits, misses, table overflow
-    int *err = reinterpret_cast<int *>(counts + 2);
+    int *pnew = reinterpret_cast<int *>(base + L.pnew);
     uint64_t *summary = reinterpret_cast<uint64_t *>(base + L.summary);
+    int *err = reinterpret_cast<int *>(base + L.err);
     *summary_dev = summary;
 
     AParams ap;
@@ -336,42 +426,26 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
     ap.near_z = near_z;
 
     cudaError_t e;
-    if ((e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(keys, 0xff, (size_t)L.S * sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(vals, 0x7f, (size_t)L.S * sizeof(int), st)) != cudaSuccess) return e;
     static_assert(kNoOwner == 0x7f7f7f7f, "memset byte of the owner table");
     const uint32_t mask = L.S - 1;
     const int nb = (n + kAThreads - 1) / kAThreads;
     const int pb = (int)((P + kAThreads - 1) / kAThreads);
+    const int npb = (int)((P + kPixBlock - 1) / kPixBlock);
     if (n > 0) {
-        k_observe<<<nb, kAThreads, 0, st>>>(n, pos, lin, cam, depth, motion, ap, lnew, keep, counts);
-        ++*launches;
-    }
-    if ((e = exclusive_scan_u32_u64(keep, off, (size_t)n, scan, st)) != cudaSuccess) return e;
-    if (n > 0) {
-        *launches += 3;
-        CompactArgs ca{{pos, feat, offsets, scaling, lnew}, {opos, ofeat, ooffsets, oscaling, olog}, {3, F, K3, 3, 1},
-                       src_index};
-        const int widest = std::max(std::max(F, K3), 3);
-        const int gx = (int)std::min<size_t>(((size_t)n * widest + kAThreads - 1) / kAThreads, (size_t)num_sms * 8);
-        k_compact<<<dim3(std::max(gx, 1), 6), kAThreads, 0, st>>>(n, keep, off, ca);
-        k_hash_anchors<<<nb, kAThreads, 0, st>>>(n, pos, keep, voxel, keys, vals, mask, err);
+        k_observe<<<nb, kAThreads, 0, st>>>(n, pos, lin, cam, depth, motion, ap, lnew, bkept, bhit, bmiss);
+        RowArrays ra{{pos, feat, offsets, scaling, lnew}, {opos, ofeat, ooffsets, oscaling, olog}, {3, F, K3, 3, 1},
+                     src_index};
+        k_compact<<<nb, kAThreads, 0, st>>>(n, lnew, bkept, l_prune, ra, voxel, keys, vals, mask, err);
         *launches += 2;
     }
-    if (P > 0) {
-        k_hash_pixels<<<pb, kAThreads, 0, st>>>(cam, depth, motion, ap, keys, vals, mask, slot_of, err);
-        k_first<<<pb, kAThreads, 0, st>>>((int)P, slot_of, vals, flags);
-        *launches += 2;
-    }
-    if ((e = exclusive_scan_u32_u64(flags, off2, P, scan, st)) != cudaSuccess) return e;
-    if (P > 0) {
-        *launches += 3;
-        InsertArgs ia{opos, ofeat, ooffsets, oscaling, olog, src_index, F, K3};
-        k_insert<<<pb, kAThreads, 0, st>>>((int)P, flags, off2, off + n, capacity, slot_of, keys, ap, ia);
-        ++*launches;
-    }
-    k_summary<<<1, 32, 0, st>>>(off + n, off2 + P, counts, summary);
-    ++*launches;
+    k_hash_pixels<<<pb, kAThreads, 0, st>>>(cam, depth, motion, ap, keys, vals, mask, slot_of, err);
+    k_count_new<<<npb, kAThreads, 0, st>>>((int)P, slot_of, vals, pnew, nb, bkept, bhit, bmiss, summary);
+    InsertArgs ia{opos, ofeat, ooffsets, oscaling, olog, src_index, F, K3};
+    k_insert<<<npb, kAThreads, 0, st>>>((int)P, slot_of, vals, pnew, keys, ap, capacity, ia, summary, err);
+    *launches += 3;
     return cudaGetLastError();
 }
 
