@@ -35,6 +35,7 @@ constexpr int kAThreads = 256;
 constexpr int kVoxRange = 1 << 20;                  // voxel indices in [-2^20, 2^20)
 constexpr unsigned long long kEmptyKey = ~0ull;      // table slot without a key
 constexpr int kNoOwner = 0x7f7f7f7f;                 // memset byte 0x7f: above every pixel index
+constexpr int kCopyUnroll = 4;                       // row-copy loads in flight per thread (k_compact)
 constexpr int kPixPerThread = 4;                     // consecutive pixels per thread (k_count_new, k_insert)
 constexpr int kPixBlock = kAThreads * kPixPerThread;
 
@@ -217,15 +218,28 @@ __global__ void __launch_bounds__(kAThreads) k_compact(int n, const float *__res
         }
     }
     __syncthreads();
+    // the block's rows of each array are one contiguous run: coalesced reads, four
+    // loads in flight per thread before the (mostly contiguous) stores
     const int nrows = min(kAThreads, n - r0);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        const int w = a.width[q];
+        const int w = a.width[q], tot = nrows * w;
         const float *__restrict__ src = a.src[q] + (size_t)r0 * w;
         float *__restrict__ dst = a.dst[q];
-        for (int e = threadIdx.x; e < nrows * w; e += kAThreads) {
-            const int rl = e / w, r = s_row[rl];
-            if (r >= 0) dst[(size_t)r * w + (e - rl * w)] = src[e];
+        for (int e0 = threadIdx.x; e0 < tot; e0 += kCopyUnroll * kAThreads) {
+            float v[kCopyUnroll];
+#pragma unroll
+            for (int k = 0; k < kCopyUnroll; ++k) {
+                const int e = e0 + k * kAThreads;
+                v[k] = e < tot ? src[e] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kCopyUnroll; ++k) {
+                const int e = e0 + k * kAThreads;
+                if (e >= tot) break;
+                const int rl = e / w, r = s_row[rl];
+                if (r >= 0) dst[(size_t)r * w + (e - rl * w)] = v[k];
+            }
         }
     }
 }
