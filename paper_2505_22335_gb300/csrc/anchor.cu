@@ -16,11 +16,12 @@
 // counts of the blocks before it to find its output offset.
 //   k_observe      anchor -> pixel -> hit / miss / none, posterior; per block
 //                  of 256 anchors the number kept, hits and misses
-//   k_compact      kept rows into the output arrays in input order, their
-//                  voxels into an open-addressing table (held by an anchor)
+//   k_compact      kept rows into the output arrays in input order (one block
+//                  per row block and array), their voxels into an
+//                  open-addressing table (held by an anchor)
 //   k_hash_pixels  the voxel of every static pixel into the table; the voxel's
 //                  owner becomes its lowest pixel index (atomicMin)
-//   k_count_new    per block of 1024 pixels, the new voxels they own; totals
+//   k_count_new    per block of 256 pixels, the new voxels they own; totals
 //   k_insert       a new anchor at the centre of each new voxel, in the raster
 //                  order of the owners, while rows remain below capacity
 #include <algorithm>
@@ -36,7 +37,7 @@ constexpr int kVoxRange = 1 << 20;                  // voxel indices in [-2^20, 
 constexpr unsigned long long kEmptyKey = ~0ull;      // table slot without a key
 constexpr int kNoOwner = 0x7f7f7f7f;                 // memset byte 0x7f: above every pixel index
 constexpr int kCopyUnroll = 4;                       // row-copy loads in flight per thread (k_compact)
-constexpr int kPixPerThread = 4;                     // consecutive pixels per thread (k_count_new, k_insert)
+constexpr int kPixPerThread = 1;                     // consecutive pixels per thread (k_count_new, k_insert)
 constexpr int kPixBlock = kAThreads * kPixPerThread;
 
 struct AParams {
@@ -186,7 +187,10 @@ __global__ void __launch_bounds__(kAThreads) k_observe(int n, const float *__res
 }
 
 // Kept rows (the same kAThreads-row blocks as k_observe) to their output rows in
-// input order, their source index, and their voxels into the table.
+// input order: blockIdx.y picks the array (pos, feat, offsets, scaling,
+// log-odds), so five blocks share a row block and every block recomputes the
+// rows' output offsets (a prefix over the block counts and a block scan); the
+// pos blocks also write the source index and insert the voxels into the table.
 struct RowArrays {
     const float *src[5];  // pos, feat, offsets, scaling, posterior log-odds
     float *dst[5];
@@ -205,9 +209,20 @@ __global__ void __launch_bounds__(kAThreads) k_compact(int n, const float *__res
     int total;
     const int row = base + block_excl_scan(flag, red, &total);
     s_row[threadIdx.x] = flag ? row : -1;
-    if (flag) {
+    // a switch, not a.src[blockIdx.y]: indexing the parameter arrays would copy them to the stack
+    int w;
+    const float *sp;
+    float *dp;
+    switch (blockIdx.y) {
+        case 0: w = a.width[0], sp = a.src[0], dp = a.dst[0]; break;
+        case 1: w = a.width[1], sp = a.src[1], dp = a.dst[1]; break;
+        case 2: w = a.width[2], sp = a.src[2], dp = a.dst[2]; break;
+        case 3: w = a.width[3], sp = a.src[3], dp = a.dst[3]; break;
+        default: w = a.width[4], sp = a.src[4], dp = a.dst[4]; break;
+    }
+    if (blockIdx.y == 0 && flag) {
         if (a.src_index) a.src_index[row] = i;
-        const float *x = a.src[0] + 3 * (size_t)i;
+        const float *x = sp + 3 * (size_t)i;
         unsigned long long key;
         if (voxel_key(x[0], x[1], x[2], voxel, key)) {
             const int s = table_slot(keys, mask, key);
@@ -218,28 +233,24 @@ __global__ void __launch_bounds__(kAThreads) k_compact(int n, const float *__res
         }
     }
     __syncthreads();
-    // the block's rows of each array are one contiguous run: coalesced reads, four
-    // loads in flight per thread before the (mostly contiguous) stores
-    const int nrows = min(kAThreads, n - r0);
+    // the block's rows are one contiguous run: coalesced reads, kCopyUnroll loads
+    // in flight per thread before the (mostly contiguous) stores
+    const int nrows = min(kAThreads, n - r0), tot = nrows * w;
+    const float *__restrict__ src = sp + (size_t)r0 * w;
+    float *__restrict__ dst = dp;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += kCopyUnroll * kAThreads) {
+        float v[kCopyUnroll];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const int w = a.width[q], tot = nrows * w;
-        const float *__restrict__ src = a.src[q] + (size_t)r0 * w;
-        float *__restrict__ dst = a.dst[q];
-        for (int e0 = threadIdx.x; e0 < tot; e0 += kCopyUnroll * kAThreads) {
-            float v[kCopyUnroll];
+        for (int k = 0; k < kCopyUnroll; ++k) {
+            const int e = e0 + k * kAThreads;
+            v[k] = e < tot ? src[e] : 0.f;
+        }
 #pragma unroll
-            for (int k = 0; k < kCopyUnroll; ++k) {
-                const int e = e0 + k * kAThreads;
-                v[k] = e < tot ? src[e] : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < kCopyUnroll; ++k) {
-                const int e = e0 + k * kAThreads;
-                if (e >= tot) break;
-                const int rl = e / w, r = s_row[rl];
-                if (r >= 0) dst[(size_t)r * w + (e - rl * w)] = v[k];
-            }
+        for (int k = 0; k < kCopyUnroll; ++k) {
+            const int e = e0 + k * kAThreads;
+            if (e >= tot) break;
+            const int rl = e / w, r = s_row[rl];
+            if (r >= 0) dst[(size_t)r * w + (e - rl * w)] = v[k];
         }
     }
 }
@@ -452,7 +463,7 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
         k_observe<<<nb, kAThreads, 0, st>>>(n, pos, lin, cam, depth, motion, ap, lnew, bkept, bhit, bmiss);
         RowArrays ra{{pos, feat, offsets, scaling, lnew}, {opos, ofeat, ooffsets, oscaling, olog}, {3, F, K3, 3, 1},
                      src_index};
-        k_compact<<<nb, kAThreads, 0, st>>>(n, lnew, bkept, l_prune, ra, voxel, keys, vals, mask, err);
+        k_compact<<<dim3(nb, 5), kAThreads, 0, st>>>(n, lnew, bkept, l_prune, ra, voxel, keys, vals, mask, err);
         *launches += 2;
     }
     k_hash_pixels<<<pb, kAThreads, 0, st>>>(cam, depth, motion, ap, keys, vals, mask, slot_of, err);
