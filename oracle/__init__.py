@@ -133,8 +133,9 @@ def _zeros(*shape):
 # per-view steps
 # ----------------------------------------------------------------------------
 
-def decode(anc, mlp, cam, k, n_feat):
-    """Eq. 8-9 for one view: returns mean, opacity, scale, quat, color, feat."""
+def decode(anc, mlp, cam, k, n_feat, opacity_tanh=False):
+    """Eq. 8-9 for one view: returns mean, opacity, scale, quat, color, feat
+    (opacity sigmoid, or tanh with opacity_tanh: the Scaffold-GS decode)."""
     A, F = anc["feat"].shape
     H = mlp["w2"].shape[1]
     keep = []
@@ -151,7 +152,7 @@ def decode(anc, mlp, cam, k, n_feat):
     co, pc = _zeros(N, 3)
     fe, pf = _zeros(N, n_feat)
     c = _cam(cam)
-    lib().orc_decode_view(A, k, F, H, n_feat, *args, C.byref(c), C.c_double(cam.t_norm),
+    lib().orc_decode_view(A, k, F, H, n_feat, int(bool(opacity_tanh)), *args, C.byref(c), C.c_double(cam.t_norm),
                           pm, po, ps, pq, pc, pf)
     return dict(mean=mean, opacity=op, scale=sc, quat=qt, color=co, feat=fe)
 
@@ -483,7 +484,7 @@ def project_bwd(g, proj, cam, cfg: RenderCfg, g2d, scale_reg=0.0):
     return dict(mean=gm, scale=gs, quat=gq, pose=pose)
 
 
-def decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc):
+def decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc, opacity_tanh=False):
     """Backward of Eq. 8-9 for one view; accumulates into `acc`, returns pose[6]."""
     A, F = anc["feat"].shape
     H = mlp["w2"].shape[1]
@@ -503,7 +504,8 @@ def decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc):
         outs.append(arr.ctypes.data_as(_dp))
     pose, pp = _zeros(6)
     c = _cam(cam)
-    lib().orc_decode_bwd_view(A, k, F, H, n_feat, *args, C.byref(c), C.c_double(cam.t_norm),
+    lib().orc_decode_bwd_view(A, k, F, H, n_feat, int(bool(opacity_tanh)), *args, C.byref(c),
+                              C.c_double(cam.t_norm),
                               *gin, *outs, pp)
     return pose
 
@@ -559,14 +561,14 @@ def backward_plain(g, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, n_feat):
 
 
 def forward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_feat,
-                   keep=False):
+                   keep=False, opacity_tanh=False):
     """Loss of anchor-decoded Gaussians (decode per view, then render)."""
     norm = _norm(cams)
     L = 0.0
     views = []
     ssum = 0.0
     for cam, tgt in zip(cams, tgts):
-        g = decode(anc, mlp, cam, k, n_feat)
+        g = decode(anc, mlp, cam, k, n_feat, opacity_tanh)
         pr = project(g, cam, cfg)
         img = render(pr, g, cam, cfg, n_feat)
         Lv, gimg = loss_view(img, tgt, lcfg, n_feat, norm)
@@ -579,9 +581,9 @@ def forward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_fea
     return (L, views) if keep else L
 
 
-def backward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_feat):
+def backward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_feat, opacity_tanh=False):
     """Loss and analytic gradients of MLP weights, anchors and per-view pose."""
-    L, views = forward_anchor(anc, mlp, cams, tgts, cfg, lcfg, k, n_feat, keep=True)
+    L, views = forward_anchor(anc, mlp, cams, tgts, cfg, lcfg, k, n_feat, keep=True, opacity_tanh=opacity_tanh)
     A = anc["pos"].shape[0]
     N = A * k
     acc = dict(w1=np.zeros_like(mlp["w1"]), b1=np.zeros_like(mlp["b1"]),
@@ -598,7 +600,7 @@ def backward_anchor(anc, mlp, cams, tgts, cfg: RenderCfg, lcfg: LossCfg, k, n_fe
         g3 = project_bwd(g, vw["proj"], cam, cfg, g2, reg)
         g3d = dict(mean=g3["mean"], opacity=g2["opacity"], scale=g3["scale"],
                    quat=g3["quat"], color=g2["color"], feat=g2["feat"])
-        pd = decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc)
+        pd = decode_bwd(anc, mlp, cam, k, n_feat, g3d, acc, opacity_tanh)
         pose[v] = g3["pose"] + pd
         per_view.append(dict(g2d=g2, g3d=g3d, pose_project=g3["pose"], pose_decode=pd))
     acc["pose"] = pose

@@ -145,7 +145,11 @@ static void decode_mlp(int K, int F, int H, int NL, const double *W1, const doub
     }
 }
 
-void orc_decode_view(int A, int K, int F, int H, int NL, const double *anc_pos,
+/* Opacity activation: sigmoid, or with op_tanh the Scaffold-GS form o = tanh(y)
+ * (the decode the paper cites), whose Gaussians with o <= 0 the projection
+ * drops (o < alpha_min is culled there; with alpha_min = 0, o = 0 blends as
+ * zero alpha). */
+void orc_decode_view(int A, int K, int F, int H, int NL, int op_tanh, const double *anc_pos,
                      const double *anc_feat, const double *anc_off, const double *anc_scale,
                      const double *W1, const double *b1, const double *W2, const double *b2,
                      const orc_camera *cam, double t_norm, double *mean, double *opac,
@@ -169,7 +173,7 @@ void orc_decode_view(int A, int K, int F, int H, int NL, const double *anc_pos,
                 size_t g = (size_t)a * K + k;
                 for (int i = 0; i < 3; ++i)
                     mean[3 * g + i] = anc_pos[3 * a + i] + anc_off[3 * g + i];
-                opac[g] = sigmoid(y[k]);
+                opac[g] = op_tanh ? tanh(y[k]) : sigmoid(y[k]);
                 for (int i = 0; i < 3; ++i)
                     scale[3 * g + i] = anc_scale[3 * a + i] * sigmoid(y[K + 7 * k + i]);
                 for (int i = 0; i < 4; ++i) quat[4 * g + i] = y[K + 7 * k + 3 + i];
@@ -870,7 +874,7 @@ void orc_project_bwd_view(int N, const double *mean, const double *scale, const 
  * Gaussians of one view, ACCUMULATE (+=) the gradients of the MLP weights and
  * anchor parameters, and write g_pose[6] (the camera-centre dependence of the
  * decode inputs delta_vc, d_vc). */
-void orc_decode_bwd_view(int A, int K, int F, int H, int NL, const double *anc_pos,
+void orc_decode_bwd_view(int A, int K, int F, int H, int NL, int op_tanh, const double *anc_pos,
                          const double *anc_feat, const double *anc_off,
                          const double *anc_scale, const double *W1, const double *b1,
                          const double *W2, const double *b2, const orc_camera *cam,
@@ -895,8 +899,13 @@ void orc_decode_bwd_view(int A, int K, int F, int H, int NL, const double *anc_p
         decode_mlp(K, F, H, NL, W1, b1, W2, b2, x, z, h, y);
         for (int k = 0; k < K; ++k) {
             size_t g = (size_t)a * K + k;
-            double o = sigmoid(y[k]);
-            dy[k] = g_opac[g] * o * (1 - o);
+            if (op_tanh) {
+                double o = tanh(y[k]);
+                dy[k] = g_opac[g] * (1 - o * o);
+            } else {
+                double o = sigmoid(y[k]);
+                dy[k] = g_opac[g] * o * (1 - o);
+            }
             for (int i = 0; i < 3; ++i) {
                 double sg = sigmoid(y[K + 7 * k + i]);
                 dy[K + 7 * k + i] = g_scale[3 * g + i] * anc_scale[3 * a + i] * sg * (1 - sg);

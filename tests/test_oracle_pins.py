@@ -564,3 +564,48 @@ def test_fd_anchor_gradients(cfg_name):
     for k in ("pos", "feat", "offsets", "scaling"):
         _fd(f, anc[k], out[k], 24, rng)
     _fd_pose(f, cams, out["pose"])
+
+
+def test_decode_tanh_opacity_against_sigmoid_decode():
+    """opacity_tanh: o = tanh(y) for the same pre-activation y that the sigmoid decode
+    maps to p = sigmoid(y), i.e. o = (p^2 - (1-p)^2) / (p^2 + (1-p)^2); nothing else
+    changes."""
+    K, NL = 4, 3
+    anc = scenes.anchors(21, 9, K)
+    mlp = scenes.mlp_weights(22, K, NL, bias_sigma=1.0)
+    c = cam(T=scenes.look_at([0.1, -0.2, -0.4], [0, 0, 2.5]), t_norm=0.4)
+    s = oracle.decode(anc, mlp, c, K, NL)
+    t = oracle.decode(anc, mlp, c, K, NL, opacity_tanh=True)
+    p, q = s["opacity"], 1.0 - s["opacity"]
+    np.testing.assert_allclose(t["opacity"], (p * p - q * q) / (p * p + q * q), rtol=1e-12, atol=1e-15)
+    assert (t["opacity"] < 0).any() and (t["opacity"] > 0).any()
+    for k in ("mean", "scale", "quat", "color", "feat"):
+        assert np.array_equal(s[k], t[k]), k
+
+
+def test_fd_anchor_gradients_tanh_opacity():
+    """The tanh decode with its o <= 0 Gaussians dropped by the projection: gradients
+    of every group against central differences (thresholds off, so the drop at o = 0
+    is continuous: such a Gaussian blends with zero alpha)."""
+    K, nf = 4, 3
+    lc = oracle.LossCfg(lambda_color=1.0, lambda_depth=0.5, lambda_feat=0.3, lambda_scale=0.01)
+    anc, mlp, cams, tg = _anchor_fd_scene(44, K, nf)
+    mlp["b2"][:K] -= 0.3  # push some opacities below zero
+    g = oracle.decode(anc, mlp, cams[0], K, nf, opacity_tanh=True)
+    assert (g["opacity"] < 0).any() and (g["opacity"] > 0).any()
+    L, out, views, _ = oracle.backward_anchor(anc, mlp, cams, tg, SMOOTH, lc, K, nf, opacity_tanh=True)
+    f = lambda: oracle.forward_anchor(anc, mlp, cams, tg, SMOOTH, lc, K, nf, opacity_tanh=True)
+    rng = np.random.default_rng(3)
+    for k in ("w1", "b1", "w2", "b2"):
+        _fd(f, mlp[k], out[k], 24, rng)
+    for k in ("pos", "feat", "offsets", "scaling"):
+        _fd(f, anc[k], out[k], 16, rng)
+    # the opacity rows of b2 in particular (the tanh derivative)
+    for i in range(K):
+        old = mlp["b2"][i]
+        mlp["b2"][i] = old + 1e-6
+        lp = f()
+        mlp["b2"][i] = old - 1e-6
+        lm = f()
+        mlp["b2"][i] = old
+        assert out["b2"][i] == pytest.approx((lp - lm) / 2e-6, rel=1e-5, abs=1e-9), i
