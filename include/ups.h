@@ -77,10 +77,14 @@ typedef struct {
                          then sorts that batch again without the cap and blends it
                          again (ups_stats.list_refills).  Views of more than 16383
                          tiles in total are never capped. */
+    int opacity_tanh; /* 1: decoded opacity o = tanh(y) (the Scaffold-GS decode the
+                         paper cites for Eq. 8-9) instead of sigmoid(y); the
+                         projection's cull of o < alpha_min then drops every
+                         Gaussian with o <= 0 (alpha_min > 0).  0 (default): sigmoid. */
 } ups_config;
 
 /* Fills the defaults listed above (n_feat 16, k 10, feat_dim 32, hidden 32,
- * list_cap 1024). */
+ * list_cap 1024, opacity_tanh 0). */
 void ups_config_default(ups_config *cfg);
 
 /* Pinhole camera of one view (Sec. 3.1); t_norm feeds the temporal encoding

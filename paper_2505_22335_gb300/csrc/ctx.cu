@@ -74,16 +74,16 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float *feat, const float *T, const uint32_t *nc,
                                  const ups_image_grads &dL, float *g2, cudaStream_t st);
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                              const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
+                              const ups_mlp &mlp, const ups_gaussians &out, int op_tanh, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_decode_fwd_tc(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                                 const ups_mlp &mlp, const ups_gaussians &out, int bf16, int *err,
+                                 const ups_mlp &mlp, const ups_gaussians &out, int bf16, int op_tanh, int *err,
                                  int num_sms, cudaStream_t st);
 size_t decode_tc_smem_bytes(int NF, int bf16);
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
-                              const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
-                              int num_sms, const dbwd::StageHook &hook, cudaStream_t st);
+                              const ups_anchors *d_anc, float *d_pose, int bf16, int op_tanh, float *scratch,
+                              int *err, int num_sms, const dbwd::StageHook &hook, cudaStream_t st);
 size_t decode_bwd_scratch_bytes(int A, int V, int K, int NF);
 bool decode_bwd_fits(int K, int NF);
 
@@ -356,6 +356,7 @@ void ups_config_default(ups_config *cfg) {
     cfg->decode_bf16 = 0;
     cfg->check_finite = 0;
     cfg->list_cap = 1024;
+    cfg->opacity_tanh = 0;
 }
 
 void ups_anchor_cfg_default(ups_anchor_cfg *cfg) {
@@ -393,6 +394,7 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
         !(c.t_min >= 0.f) || !(c.dilation >= 0.f) || !(c.near_z > 0.f) || !(c.guard > 0.f))
         return fail(nullptr, UPS_ERR_ARG, "threshold out of range");
     if (c.list_cap > kMaxListCap) return fail(nullptr, UPS_ERR_ARG, "list_cap must be at most 32767");
+    if (c.opacity_tanh != 0 && c.opacity_tanh != 1) return fail(nullptr, UPS_ERR_ARG, "opacity_tanh must be 0 or 1");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || device < 0 || device >= ndev)
@@ -470,9 +472,10 @@ ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp 
     const int bf16 = c->cfg.decode_bf16 ? 1 : 0;
     if (bf16 && decode_tc_smem_bytes(c->cfg.n_feat, bf16) + 1024 <= 227 * 1024)
         UPS_CUDA(c, launch_decode_fwd_tc(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, bf16,
-                                         c->d_err, c->num_sms, st));
+                                         c->cfg.opacity_tanh, c->d_err, c->num_sms, st));
     else
-        UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->num_sms, st));
+        UPS_CUDA(c, launch_decode_fwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *out, c->cfg.opacity_tanh,
+                                      c->num_sms, st));
     stage_end(c, st, 1);
     return UPS_OK;
 }
@@ -939,7 +942,8 @@ ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp
                                },
                                c};
     UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp, d_anc,
-                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, scratch, c->d_err, c->num_sms, hook, st));
+                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, c->cfg.opacity_tanh, scratch, c->d_err,
+                                  c->num_sms, hook, st));
     return UPS_OK;
 }
 

@@ -29,11 +29,13 @@ constexpr size_t kMaxSmem = 227 * 1024;  // opt-in shared memory per block
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + __expf(-x)); }
 __device__ __forceinline__ float softplus(float x) { return x > 20.f ? x : log1pf(__expf(x)); }
+__device__ __forceinline__ float opacity_act(float y, int op_tanh) { return op_tanh ? tanhf(y) : sigm(y); }
 
 struct DecodeArgs {
     int A, K, NF, n_out;
     const float *pos, *afeat, *offs, *ascale;
     const float *w1, *b1, *w2, *b2;
+    int op_tanh;  // opacity = tanh(y) (Scaffold-GS form) instead of sigmoid(y)
 };
 
 // x (padded to 40) for anchor `an` seen from view `cam`; returns delta and d.
@@ -191,7 +193,8 @@ __global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
             const float *o3 = a.offs + ((size_t)an * K + k) * 3;
-            mean_op[gbase + k] = make_float4(px + o3[0], py + o3[1], pz + o3[2], sigm(out_row(sW2, sb2, k, z)));
+            mean_op[gbase + k] = make_float4(px + o3[0], py + o3[1], pz + o3[2],
+                                             opacity_act(out_row(sW2, sb2, k, z), a.op_tanh));
         }
         // covariance: 3 scale + 4 quaternion per Gaussian
         hidden_T(sW1T, sb1, 1, af, xt, z);
@@ -328,7 +331,10 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
                 gin = (c & 3) == 0 ? f4.x : (c & 3) == 1 ? f4.y : (c & 3) == 2 ? f4.z : f4.w;
             }
             float dy = gin;
-            if (nl) {
+            if (G == 0 && da.op_tanh) {
+                const float t = tanhf(out_row(sW2, sb2, o, h));
+                dy = gin * (1.f - t * t);
+            } else if (nl) {
                 const float s = sigm(out_row(sW2, sb2, o, h));
                 if (G == 1) {
                     dy = gin * a.ascale[3 * an + c] * s * (1.f - s);
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_d
     __shared__ float aPose[3 * UPS_MAX_VIEWS];
     float *sm = reinterpret_cast<float *>(smem4);
     const int n_out = dbwd::n_out(a.K, NF);
-    const DecodeArgs da{a.A, a.K, NF, n_out, a.pos, a.afeat, a.offs, a.ascale, a.w1, a.b1, a.w2, a.b2};
+    const DecodeArgs da{a.A, a.K, NF, n_out, a.pos, a.afeat, a.offs, a.ascale, a.w1, a.b1, a.w2, a.b2, a.op_tanh};
     // W1 transposed [38][128] (inputs x hidden), b1, W2 [n_out][32], b2, and
     // the per-row input gradients dx [36][128 rows]
     float *sW1T = sm, *sb1 = sW1T + kDin * 4 * kH, *sW2 = sb1 + 4 * kH, *sb2 = sW2 + n_out * kH;
@@ -468,10 +474,10 @@ cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a
 }
 
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                              const ups_mlp &mlp, const ups_gaussians &out, int num_sms,
+                              const ups_mlp &mlp, const ups_gaussians &out, int op_tanh, int num_sms,
                               cudaStream_t st) {
     DecodeArgs a{A, K, NF, K * (11 + NF), anc.pos, anc.feat, anc.offsets, anc.scaling,
-                 mlp.w1, mlp.b1, mlp.w2, mlp.b2};
+                 mlp.w1, mlp.b1, mlp.w2, mlp.b2, op_tanh};
     size_t smem = fwd_smem(a.n_out);
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     int rows = A * vt.n;

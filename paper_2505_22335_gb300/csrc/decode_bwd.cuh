@@ -58,6 +58,7 @@ struct Args {
     float *g_pos, *g_afeat, *g_offs, *g_ascale, *g_pose;
     unsigned mask;
     int *err;
+    int op_tanh;  // opacity = tanh(y) instead of sigmoid(y)
 };
 
 // MLP input of anchor `an` seen from `cam`: x = [f_v, delta_vc, d_vc,

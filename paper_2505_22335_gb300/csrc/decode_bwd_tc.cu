@@ -214,8 +214,13 @@ __device__ __forceinline__ void tc_group(const dbwd::Args &a, const Layout &L, u
             if (G == 0) {
                 float dy = 0.f;
                 if (live) {
-                    const float o = sig(ynl[0][k & 15]);
-                    dy = a.d_mean_op[gi].w * o * (1.f - o);
+                    if (a.op_tanh) {
+                        const float t = tanhf(ynl[0][k & 15]);
+                        dy = a.d_mean_op[gi].w * (1.f - t * t);
+                    } else {
+                        const float o = sig(ynl[0][k & 15]);
+                        dy = a.d_mean_op[gi].w * o * (1.f - o);
+                    }
                 }
                 dyv[kk] = dy;
             } else if (G == 1) {
@@ -725,9 +730,10 @@ bool decode_bwd_fits(int K, int NF) {
 
 cudaError_t launch_decode_bwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &dG, unsigned mask, const ups_mlp *d_mlp,
-                              const ups_anchors *d_anc, float *d_pose, int bf16, float *scratch, int *err,
-                              int num_sms, const dbwd::StageHook &hook, cudaStream_t st) {
+                              const ups_anchors *d_anc, float *d_pose, int bf16, int op_tanh, float *scratch,
+                              int *err, int num_sms, const dbwd::StageHook &hook, cudaStream_t st) {
     dbwd::Args a{};
+    a.op_tanh = op_tanh;
     a.A = A;
     a.K = K;
     a.NF = NF;

@@ -40,6 +40,7 @@ struct TcArgs {
     float4 *mean_op, *scale, *quat, *color;
     float *feat;
     int *err;
+    int op_tanh;  // opacity = tanh(y) instead of sigmoid(y)
 };
 
 template <Kind KD> struct Prec {
@@ -266,7 +267,8 @@ __global__ void __launch_bounds__(kTCRows, 3) k_decode_fwd_tc(ViewTable vt, TcAr
                     float y[16];
                     tmem_ld16(lane_addr + 32, y);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) op[k] = sig(y[k] + b2[rbase + k]);
+                    for (int k = 0; k < 16; ++k)
+                        op[k] = a.op_tanh ? tanhf(y[k] + b2[rbase + k]) : sig(y[k] + b2[rbase + k]);
                 } else if (g == 1 && c0 == 0) {
                     // components 0..3 = scale x, y, z and quaternion w
                     float s0[16], s1[16], s2[16];
@@ -344,11 +346,11 @@ size_t decode_tc_smem_bytes(int NF, int bf16) {
 }
 
 cudaError_t launch_decode_fwd_tc(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
-                                 const ups_mlp &mlp, const ups_gaussians &out, int bf16, int *err,
+                                 const ups_mlp &mlp, const ups_gaussians &out, int bf16, int op_tanh, int *err,
                                  int num_sms, cudaStream_t st) {
     TcArgs a{A, K, NF, anc.pos, anc.feat, anc.offsets, anc.scaling, mlp.w1, mlp.b1, mlp.w2, mlp.b2,
              reinterpret_cast<float4 *>(out.mean_opacity), reinterpret_cast<float4 *>(out.scale),
-             reinterpret_cast<float4 *>(out.quat), reinterpret_cast<float4 *>(out.color), out.feat, err};
+             reinterpret_cast<float4 *>(out.quat), reinterpret_cast<float4 *>(out.color), out.feat, err, op_tanh};
     if (K < 1 || K > 16) return cudaErrorInvalidValue;
     const int rows = A * vt.n;
     const int tiles = (rows + kTCRows - 1) / kTCRows;

@@ -46,20 +46,20 @@ def make_case(seed, A, K, nf, V):
     return dict(anc=anc, mlp=mlp, cams=cams, dG=dG, K=K, nf=nf)
 
 
-def oracle_grads(case):
+def oracle_grads(case, opacity_tanh=False):
     anc, mlp = case["anc"], case["mlp"]
     acc = {k: np.zeros_like(np.asarray(v, dtype=np.float64)) for k, v in
            list(mlp.items()) + [(k, anc[k]) for k in ("pos", "feat", "offsets", "scaling")]}
     acc = {k: np.ascontiguousarray(v) for k, v in acc.items()}
-    pose = np.stack([oracle.decode_bwd(anc, mlp, c, case["K"], case["nf"], g, acc)
+    pose = np.stack([oracle.decode_bwd(anc, mlp, c, case["K"], case["nf"], g, acc, opacity_tanh)
                      for c, g in zip(case["cams"], case["dG"])])
     acc["pose"] = pose
     return acc
 
 
-def gpu_grads(case, bf16, mask=B.GRAD_ALL):
+def gpu_grads(case, bf16, mask=B.GRAD_ALL, opacity_tanh=False):
     import torch
-    R = B.Renderer(n_feat=case["nf"], k=case["K"], decode_bf16=int(bf16))
+    R = B.Renderer(n_feat=case["nf"], k=case["K"], decode_bf16=int(bf16), opacity_tanh=int(opacity_tanh))
     ad, md = B.anchors_to_device(case["anc"], case["mlp"])
     dG = B.to_set(case["dG"], per_view=True)
     d_mlp = {k: torch.zeros_like(v) for k, v in md.items()}
@@ -139,3 +139,15 @@ def test_rows_span_two_scratch_chunks():
     assert all(v < FP32_RTOL for v in e.values()), e
     e = errors(gpu_grads(c, bf16=True), ref, "bf16 A=70000 K=10 nf=16 V=4")
     assert all(v < BF16_RTOL for v in e.values()), e
+
+
+def test_tanh_opacity_decode_backward(small):
+    """The tanh opacity decode (o = tanh(y), the Scaffold-GS form): its derivative
+    1 - o^2 in both row kernels."""
+    ref = oracle_grads(small, opacity_tanh=True)
+    e = errors(gpu_grads(small, bf16=False, opacity_tanh=True), ref, "fp32 tanh A=2000 K=10 nf=16 V=3")
+    assert all(v < FP32_RTOL for v in e.values()), e
+    e = errors(gpu_grads(small, bf16=True, opacity_tanh=True), ref, "bf16 tanh A=2000 K=10 nf=16 V=3")
+    assert all(v < BF16_RTOL for v in e.values()), e
+    # the opacity rows of the weights do differ from the sigmoid decode's
+    assert rel_l2(ref["b2"][:small["K"]], small["ref"]["b2"][:small["K"]]) > 0.1

@@ -165,13 +165,14 @@ def test_single_gaussian_peak_alpha():
 # anchor decode + render (Eq. 8-9), FP32 decode
 # ---------------------------------------------------------------------------
 
-def anchor_case(seed, A, K, nf, cams, weighted=True, lambda_scale=0.01, mask=B.GRAD_ALL):
+def anchor_case(seed, A, K, nf, cams, weighted=True, lambda_scale=0.01, mask=B.GRAD_ALL, opacity_tanh=False,
+                bias_sigma=0.05):
     import torch
     anc = round_dict(scenes.anchors(seed, A, K))
-    mlp = round_dict(scenes.mlp_weights(seed + 1, K, nf, bias_sigma=0.05))
+    mlp = round_dict(scenes.mlp_weights(seed + 1, K, nf, bias_sigma=bias_sigma))
     cams = round_cams(cams)
     tg = [round_dict(t) for t in scenes.targets(seed + 2, cams, nf, weighted=weighted)]
-    R = B.Renderer(n_feat=nf, k=K)
+    R = B.Renderer(n_feat=nf, k=K, opacity_tanh=int(opacity_tanh))
     ad, md = B.anchors_to_device(anc, mlp)
     g = R.decode(ad, md, cams)
     img = R.forward(g, cams)
@@ -183,7 +184,7 @@ def anchor_case(seed, A, K, nf, cams, weighted=True, lambda_scale=0.01, mask=B.G
     R.decode_backward(ad, md, cams, grad, mask, d_mlp, d_anc, d_pose)
     torch.cuda.synchronize()
     lc = oracle.LossCfg(lambda_scale=lambda_scale)
-    L, ref, views, per_view = oracle.backward_anchor(anc, mlp, cams, tg, CFG, lc, K, nf)
+    L, ref, views, per_view = oracle.backward_anchor(anc, mlp, cams, tg, CFG, lc, K, nf, opacity_tanh=opacity_tanh)
     return dict(R=R, anc=anc, mlp=mlp, cams=cams, g=g, img=img, loss=float(loss.item()), L=L,
                 ref=ref, views=views, per_view=per_view, grad=grad,
                 d_pose=d_pose.cpu().numpy().astype(np.float64),
@@ -228,6 +229,16 @@ def check_anchor(res, nf):
 def test_anchor_decode_render_small():
     cams = scenes.cameras(21, 2, 160, 120, 150.0)
     res = anchor_case(21, 600, 10, 16, cams)
+    check_anchor(res, 16)
+
+
+def test_anchor_decode_render_tanh_opacity():
+    """The tanh opacity decode: Gaussians with o <= 0 (about half here) are culled
+    by the projection on both sides; images, loss and every gradient as above."""
+    cams = scenes.cameras(23, 2, 160, 120, 150.0)
+    res = anchor_case(23, 600, 10, 16, cams, opacity_tanh=True, bias_sigma=0.5)
+    o = res["g"].mean_opacity.cpu().numpy()[..., 3]
+    assert (o <= 0).mean() > 0.2 and (o > 0.1).mean() > 0.1
     check_anchor(res, 16)
 
 
