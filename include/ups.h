@@ -539,6 +539,16 @@ ups_status ups_cancel(ups_server *srv, uint64_t ticket);
 /* Blocks until the queue is empty and no batch is in flight, at most
  * timeout_ms (UPS_ERR_TIMEOUT then). */
 ups_status ups_server_wait_idle(ups_server *srv, double timeout_ms);
+/* Replaces the resident scene (anchors + MLP weights), e.g. after a mapping
+ * step or a probabilistic anchor update (ups_anchor_update) changed it.  No new
+ * batch starts during the call; it waits, at most timeout_ms (UPS_ERR_TIMEOUT,
+ * scene unchanged), until the batches in flight have finished on the GPU, then
+ * swaps the pointers.  Requests still queued run on the new scene; a queued
+ * mapping request that asked for anchor gradients (d_anchors sized for the old
+ * anchor count) fails with UPS_ERR_STATE when the count changed.  The old
+ * buffers are the caller's again once the call returns UPS_OK. */
+ups_status ups_server_set_scene(ups_server *srv, const ups_anchors *scene, const ups_mlp *mlp,
+                                double timeout_ms);
 const char *ups_server_last_error(const ups_server *srv);
 
 /* ---------------------------------------------------------------------- */

@@ -118,7 +118,7 @@ EXPORTS = ["ups_config_default", "ups_version", "ups_create", "ups_destroy", "up
            "ups_render_backward", "ups_decode_backward", "ups_get_stats", "ups_copy_buffer",
            "ups_profile_enable", "ups_profile_read", "ups_render_forward_static",
            "ups_server_create", "ups_server_destroy", "ups_submit", "ups_poll", "ups_cancel",
-           "ups_server_wait_idle", "ups_server_last_error"]
+           "ups_server_wait_idle", "ups_server_set_scene", "ups_server_last_error"]
 
 _lib = None
 
@@ -177,6 +177,7 @@ def load():
     L.ups_poll.argtypes = [_p, C.c_uint64, C.POINTER(Result)]
     L.ups_cancel.argtypes = [_p, C.c_uint64]
     L.ups_server_wait_idle.argtypes = [_p, C.c_double]
+    L.ups_server_set_scene.argtypes = [_p, C.POINTER(Anchors), C.POINTER(MLP), C.c_double]
     L.ups_server_last_error.argtypes = [_p]
     L.ups_server_last_error.restype = C.c_char_p
     _lib = L
@@ -588,6 +589,18 @@ class Server:
         st = self._L.ups_server_wait_idle(self._h, timeout_s * 1e3)
         if st != UPS_OK:
             raise UpsError(st, "server did not drain in time")
+
+    def set_scene(self, anchors, mlp, timeout_s=120.0):
+        """Swap the resident scene (e.g. after ups_anchor_update changed the anchors)."""
+        A = int(anchors["pos"].shape[0])
+        ca = Anchors(A, _ptr(anchors["pos"]), _ptr(anchors["feat"]), _ptr(anchors["offsets"]),
+                     _ptr(anchors["scaling"]))
+        cm = MLP(_ptr(mlp["w1"]), _ptr(mlp["b1"]), _ptr(mlp["w2"]), _ptr(mlp["b2"]))
+        st = self._L.ups_server_set_scene(self._h, C.byref(ca), C.byref(cm), timeout_s * 1e3)
+        if st != UPS_OK:
+            raise UpsError(st, "ups_server_set_scene failed")
+        self._keep = (anchors, mlp)
+        self.A = A
 
     def last_error(self):
         return self._L.ups_server_last_error(self._h).decode()

@@ -70,6 +70,7 @@ struct Req {
     bool started = false;
     double t_submit = 0, t_start = 0, t_end = 0;
     int batch_id = -1, batch_reqs = 0, batch_views = 0;
+    int anc_n = 0;  // anchors of the scene at submission (the size of d_anchors)
 };
 
 struct Slot {
@@ -94,6 +95,7 @@ struct ups_server {
     std::deque<Req *> queue;
     std::unordered_map<uint64_t, Req *> reqs;
     bool stopping = false;
+    bool paused = false;  // ups_server_set_scene: no new batch starts
     uint64_t next_ticket = 1;
     int next_batch = 0;
     size_t reserved = 0, budget = 0;
@@ -233,13 +235,25 @@ void worker(ups_server *s, int si) {
         int views = 0, id = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stopping || !s->queue.empty(); });
+            s->cv.wait(lk, [&] { return s->stopping || (!s->paused && !s->queue.empty()); });
             if (s->queue.empty()) {
                 if (s->stopping) return;
                 continue;
             }
+            if (s->paused && !s->stopping) continue;
             while (!s->queue.empty()) {
                 Req *r = s->queue.front();
+                if (r->r.kind == UPS_REQ_MAP && r->r.d_anchors.pos && r->anc_n != s->anc.n) {
+                    // its anchor-gradient buffers were sized for the scene before the last
+                    // ups_server_set_scene: fail it rather than write past them
+                    s->queue.pop_front();
+                    r->started = true;
+                    r->status = UPS_ERR_STATE;
+                    r->t_start = r->t_end = s->now_ms();
+                    s->err = "mapping request with anchor gradients submitted for a scene of " +
+                             std::to_string(r->anc_n) + " anchors, scene now has " + std::to_string(s->anc.n);
+                    continue;
+                }
                 if (!batch.empty() && (!s->scfg.batching || views + r->nv > s->scfg.max_batch_views)) break;
                 // admission by memory footprint; an oversized request still runs
                 // alone once nothing else is in flight
@@ -393,9 +407,10 @@ ups_status ups_submit(ups_server *s, const ups_request *req, uint64_t *ticket) {
         return UPS_ERR_ARG;
     }
     for (const ups_camera &c : r->cams) r->pixels += (size_t)c.width * c.height;
-    r->bytes = footprint(s->cfg, (size_t)s->anc.n * s->cfg.k, r->nv, r->pixels);
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        r->anc_n = s->anc.n;
+        r->bytes = footprint(s->cfg, (size_t)s->anc.n * s->cfg.k, r->nv, r->pixels);
         r->ticket = s->next_ticket++;
         r->t_submit = s->now_ms();
         s->reqs[r->ticket] = r;
@@ -445,6 +460,26 @@ ups_status ups_server_wait_idle(ups_server *s, double timeout_ms) {
     std::unique_lock<std::mutex> lk(s->mu);
     bool ok = s->cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
                              [&] { return s->queue.empty() && s->in_flight == 0; });
+    return ok ? UPS_OK : UPS_ERR_TIMEOUT;
+}
+
+ups_status ups_server_set_scene(ups_server *s, const ups_anchors *scene, const ups_mlp *mlp, double timeout_ms) {
+    if (!s || !scene || !mlp || scene->n < 1 || !scene->pos || !scene->feat || !scene->offsets || !scene->scaling ||
+        !mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2)
+        return UPS_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->paused = true;
+    // in_flight drops when a batch's stream work has completed (host callback)
+    const bool ok = s->cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                                   [&] { return s->in_flight == 0; });
+    if (ok) {
+        s->anc = *scene;
+        s->mlp = *mlp;
+        for (Req *r : s->queue) r->bytes = footprint(s->cfg, (size_t)s->anc.n * s->cfg.k, r->nv, r->pixels);
+    }
+    s->paused = false;
+    lk.unlock();
+    s->cv.notify_all();
     return ok ? UPS_OK : UPS_ERR_TIMEOUT;
 }
 

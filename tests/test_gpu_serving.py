@@ -138,3 +138,35 @@ def test_cancel_and_small_budget_admission(scene):
     assert all(r["batch_requests"] == 1 for r in res)
     srv.wait_idle()
     srv.close()
+
+
+def test_scene_swap_after_anchor_update(scene):
+    """The map changes under the server (a probabilistic anchor update prunes and
+    inserts anchors, Eq. 7): after ups_server_set_scene a tracking request renders
+    the new scene, equal to the direct calls on it."""
+    import torch
+    ad, md = scene
+    srv = B.Server(ad, md, n_feat=NF, k=K, slots=2, batching=True)
+    first = make_request(5, B.TRACK)
+    assert srv.wait(submit(srv, first))["status"] == 0
+    R = B.Renderer(n_feat=NF, k=K)
+    cam = first["cams"][0]
+    depth, motion = scenes.keyframe(9, cam)
+    lo = torch.zeros(ad["pos"].shape[0], device="cuda")
+    new, _, _, cnt = R.anchor_update(ad, lo, cam, torch.tensor(depth, dtype=torch.float32, device="cuda"),
+                                     torch.tensor(motion, device="cuda"), capacity=2 * ad["pos"].shape[0],
+                                     voxel=0.1, margin=0.1)
+    assert cnt["n_inserted"] > 0 and cnt["n_kept"] < ad["pos"].shape[0]
+    new = {k: v.contiguous() for k, v in new.items()}
+    srv.set_scene(new, md)
+    req = make_request(3, B.TRACK)
+    assert srv.wait(submit(srv, req))["status"] == 0
+    srv.close()
+    g = R.decode(new, md, req["views"])
+    img = R.forward(g, req["views"])
+    loss, dimg = R.loss(img, req["tg"])
+    grad, d_pose = R.backward(dimg, B.GRAD_POSE | B.GRAD_GAUSS)
+    R.decode_backward(new, md, req["views"], grad, B.GRAD_POSE, d_pose=d_pose)
+    torch.cuda.synchronize()
+    assert abs(req["loss"].item() - loss.item()) <= 1e-5 + 1e-4 * abs(loss.item())
+    assert rel_l2(req["d_pose"].cpu().numpy(), d_pose.sum(0).cpu().numpy()) < 2e-3
