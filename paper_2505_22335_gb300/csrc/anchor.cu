@@ -422,8 +422,7 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
                           int K3, float l_prior, float l_hit, float l_miss, float l_min, float l_max, float l_prune,
                           float voxel, float margin, float near_z, long long capacity, float *opos, float *ofeat,
                           float *ooffsets, float *oscaling, float *olog, int *src_index, void *scratch,
-                          uint64_t **summary_dev, int num_sms, cudaStream_t st, int *launches) {
-    (void)num_sms;
+                          uint64_t **summary_dev, cudaStream_t st, int *launches) {
     const size_t P = (size_t)cam.W * cam.H;
     const Layout L = layout((size_t)n, P);
     char *base = static_cast<char *>(scratch);

@@ -44,7 +44,7 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
                           int K3, float l_prior, float l_hit, float l_miss, float l_min, float l_max, float l_prune,
                           float voxel, float margin, float near_z, long long capacity, float *opos, float *ofeat,
                           float *ooffsets, float *oscaling, float *olog, int *src_index, void *scratch,
-                          uint64_t **summary_dev, int num_sms, cudaStream_t st, int *launches);
+                          uint64_t **summary_dev, cudaStream_t st, int *launches);
 size_t unc_scratch_floats(int max_patches);
 cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
                      int hp, const float *R, const float *w1, const float *b1, const float *w2, const float *b2,
@@ -744,7 +744,7 @@ ups_status ups_anchor_update(ups_ctx *c, const ups_anchor_cfg *a, const ups_came
     UPS_CUDA(c, anchor_update(vt.v[0], depth, motion, n, in->pos, in->feat, in->offsets, in->scaling, logodds_in, F,
                               K3, a->l_prior, a->l_hit, a->l_miss, a->l_min, a->l_max, a->l_prune, a->voxel,
                               a->margin, a->near_z, capacity, out->pos, out->feat, out->offsets, out->scaling,
-                              logodds_out, src_index, c->anchor_scr.ptr, &summary, c->num_sms, st, &launches));
+                              logodds_out, src_index, c->anchor_scr.ptr, &summary, st, &launches));
     stage_end(c, st, launches);
     UPS_CUDA(c, cudaMemcpyAsync(c->h_anchor, summary, 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     UPS_CUDA(c, cudaStreamSynchronize(st));
