@@ -7,7 +7,7 @@ same dL/dG.
   rounded to BF16 (8 significant bits), and the ReLU masks follow the BF16
   hidden pre-activations (as in the BF16 forward), so a hidden unit near zero
   may switch; the stated bound is 5e-2 relative L2 (the measured values are
-  printed and written to gpurun_out/bf16_decode_bwd_error.json);
+  printed, and written to bf16_decode_bwd_error.json in $UPS_REPORT_DIR when set);
 * rows (anchor, view) span two scratch chunks (262144 rows each) in the large
   case, and the grad masks that need no scratch run too.
 """
@@ -86,9 +86,11 @@ def errors(got, ref, tag=None):
         import os
         REPORT[tag] = e
         print(tag, {k: f"{v:.2e}" for k, v in e.items()})
-        os.makedirs("gpurun_out", exist_ok=True)
-        with open("gpurun_out/bf16_decode_bwd_error.json", "w") as f:
-            json.dump(REPORT, f, indent=1)
+        out_dir = os.environ.get("UPS_REPORT_DIR")
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            with open(os.path.join(out_dir, "bf16_decode_bwd_error.json"), "w") as f:
+                json.dump(REPORT, f, indent=1)
     return e
 
 
