@@ -53,7 +53,7 @@ cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int pa
 cudaError_t ssim_set_window();
 cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, const float *weight, float *G, float g,
                         float *loss, float *dx, cudaStream_t st);
-size_t lift_scratch_floats(size_t max_hw, int nh);
+size_t lift_scratch_floats(size_t max_hw, size_t max_np);
 cudaError_t lift_handle(void **handle);
 void lift_handle_destroy(void *handle);
 cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
@@ -795,8 +795,8 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
         return fail(c, UPS_ERR_ARG, "NULL argument");
     const int nf = c->cfg.n_feat;
     if (nf <= 0) return fail(c, UPS_ERR_ARG, "feature lifting needs n_feat > 0");
-    if (lcfg->n_h < 4 || lcfg->n_h > 4096 || lcfg->n_h % 4 != 0 || lcfg->patch < 1)
-        return fail(c, UPS_ERR_ARG, "n_h must be a multiple of 4 in [4, 4096] and patch >= 1");
+    if (lcfg->n_h < 4 || lcfg->n_h > 4096 || lcfg->n_h % 4 != 0 || lcfg->patch < 1 || lcfg->patch > 32)
+        return fail(c, UPS_ERR_ARG, "n_h must be a multiple of 4 in [4, 4096] and patch in [1, 32]");
     if (reinterpret_cast<uintptr_t>(dino) % 16 != 0 || reinterpret_cast<uintptr_t>(mlp->b2) % 16 != 0)
         return fail(c, UPS_ERR_ARG, "dino and mlp->b2 must be 16-byte aligned");
     ups_status s = set_device(c);
@@ -804,7 +804,13 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
     UPS_CUDA(c, lift_handle(&c->cublas));
-    UPS_CUDA(c, c->lift_scr.reserve(lift_scratch_floats((size_t)c->max_hw, lcfg->n_h) * sizeof(float)));
+    size_t max_np = 0;
+    for (int v = 0; v < c->vt.n; ++v) {
+        const DevView &cam = c->vt.v[v];
+        max_np = std::max(max_np, (size_t)((cam.H + lcfg->patch - 1) / lcfg->patch) *
+                                      (size_t)((cam.W + lcfg->patch - 1) / lcfg->patch));
+    }
+    UPS_CUDA(c, c->lift_scr.reserve(lift_scratch_floats((size_t)c->max_hw, max_np) * sizeof(float)));
     stage_begin(c, "lift", st);
     UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
     const float g = (float)((double)scale / (double)c->n_pix);
