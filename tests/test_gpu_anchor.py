@@ -126,3 +126,24 @@ def test_rejects_bad_arguments():
     st = L.ups_anchor_update(R._h, C.byref(ac), B.make_cameras([cam]), B._ptr(dev(depth)), None, C.byref(ca),
                              B._ptr(dev(l)), C.byref(ca), B._ptr(dev(l)), 50, None, C.byref(res), B._stream())
     assert B.STATUS[st] == "ERR_ARG"
+
+
+def test_degenerate_keyframes():
+    """Every pixel dynamic (no insertion, surface anchors missed), every anchor
+    pruned (insertion from row 0), anchors and pixels beyond the voxel index range
+    (no voxel held, none inserted), and a voxel larger than the scene."""
+    cam, anc, l, depth, motion = case(13, 80, 60, 500)
+    R = B.Renderer(n_feat=16, k=4)
+    _, _, ref = run(R, anc, l, cam, depth, np.ones_like(motion), capacity=500 + 80 * 60, **cfg32(voxel=0.02))
+    assert ref["n_inserted"] == 0 and ref["n_hit"] == 0 and ref["n_miss"] > 0
+    _, _, ref = run(R, anc, l, cam, depth, motion, capacity=500 + 80 * 60, **cfg32(voxel=0.02, l_prune=10.0))
+    assert ref["n_kept"] == 0 and ref["n_inserted"] > 0
+    far = dict(anc)
+    far["pos"] = anc["pos"] + np.float32(1e5)
+    _, _, ref = run(R, far, l, cam, depth, motion, capacity=500 + 80 * 60, **cfg32(voxel=0.05))
+    assert ref["n_hit"] == ref["n_miss"] == 0 and ref["n_inserted"] > 0
+    _, _, ref = run(R, anc, l, cam, depth * np.float32(1e5), motion, capacity=500 + 80 * 60,
+                    **cfg32(voxel=0.01, margin=0.05))
+    assert ref["n_inserted"] == 0   # every back-projected voxel index beyond 2^20
+    _, _, ref = run(R, anc, l, cam, depth, motion, capacity=500 + 80 * 60, **cfg32(voxel=50.0, margin=0.05))
+    assert ref["n_inserted"] <= 8
