@@ -231,10 +231,32 @@ def algorithmic(wl, stats, proc_inst, evals=0):
 
 ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
 
-# DRAM bytes (read + write) per launch from one ncu capture of the named kernel on the named
-# workload (profiles/launches_mapping_100k_anchors_x10_8x640x480.md); reported as the roofline's
-# `traffic` only for that kernel and workload.  Re-measure whenever the kernel changes.
-MEASURED_TRAFFIC = {("composite_bwd", "mapping_100k_anchors_x10_8x640x480"): 304.2e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a stage's kernel, from
+# one ncu capture of that kernel on the named workload: (bytes, capture date, SHA-256 prefix of
+# the kernel's source file when it was captured).  Reported as the roofline's `traffic` only while
+# the source file still has that hash; any later change of the kernel makes it null (stale).
+MEASURED_TRAFFIC = {}
+STAGE_SOURCE = {"composite_fwd": "composite.cu", "composite_bwd": "composite.cu", "decode_bwd_rows": "decode.cu",
+                "decode_fwd": "decode.cu", "decode_wgrad": "wgrad_tc.cu", "project_bwd": "project.cu"}
+
+
+def source_hash(stage):
+    import hashlib
+    f = STAGE_SOURCE.get(stage)
+    if f is None:
+        return None
+    with open(os.path.join(ROOT, "paper_2505_22335_gb300", "csrc", f), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_for(stage, wl_name):
+    m = MEASURED_TRAFFIC.get((stage, wl_name))
+    if m is None:
+        return None, "no ncu capture of this kernel on this workload"
+    nbytes, when, sha = m
+    if sha != source_hash(stage):
+        return None, f"stale: the kernel changed since the {when} capture"
+    return nbytes, f"ncu capture of {when} (dram__bytes_read.sum + dram__bytes_write.sum, one launch)"
 
 
 def run_ours(args, wl_name):
@@ -304,9 +326,28 @@ def run_ours(args, wl_name):
         stages = {k: dict(ms_per_step=v[0] / args.steps, launches_per_step=v[1] / args.steps)
                   for k, v in prof.items()}
         dom = max(prof, key=lambda k: prof[k][0])
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peaks["sm_count"] = sms
         roof = roofline(dom, alg, prof[dom][0] / args.steps, prof[dom][1] / args.steps, peaks, args.decode_bf16)
-        roof["traffic"] = MEASURED_TRAFFIC.get((dom, wl_name))
+        roof["traffic"], roof["traffic_source"] = traffic_for(dom, wl_name)
+        # both blend kernels, each against the FP32 pipe and against HBM
+        blend = {}
+        for stg in ("composite_fwd", "composite_bwd"):
+            if stg in prof:
+                r = roofline(stg, alg, prof[stg][0] / args.steps, prof[stg][1] / args.steps, peaks)
+                h = roofline(stg, alg, prof[stg][0] / args.steps, prof[stg][1] / args.steps, peaks, force_hbm=True)
+                tr, trs = traffic_for(stg, wl_name)
+                blend[stg] = dict(alu=dict(achieved=r["achieved"], peak=r["peak"], unit=r["unit"], frac=r["frac"],
+                                           peak_source=r["peak_source"]),
+                                  hbm=dict(achieved=h["achieved"], peak=h["peak"], unit=h["unit"], frac=h["frac"],
+                                           peak_source=h["peak_source"]),
+                                  avg_launch_ms=r["avg_launch_ms"], traffic=tr, traffic_source=trs)
         cpu = cpu_baseline(wl, anc, mlp, cams, tg) if not args.no_cpu else None
+        serving = None
+        if not args.no_serving and world == 1 and wl_name == DEFAULT_WORKLOAD:
+            del st
+            torch.cuda.empty_cache()
+            serving = measure_serving(args.serve_seconds)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
@@ -324,10 +365,12 @@ def run_ours(args, wl_name):
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": roof,
+            "blend_rooflines": blend,
             "stages": stages,
             "counters": dict(stats, processed_instances=proc, evaluations=evals),
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
             "next_rows": {"tracking_uncertainty": dict(unc, peak=round(peaks["hbm_gbs"], 1),
                                                        frac=round(unc["achieved_gbs"] / peaks["hbm_gbs"], 4),
                                                        peak_source=peaks["source"]),
@@ -338,10 +381,9 @@ def run_ours(args, wl_name):
                           "dssim": dict(ssim, peak=round(peaks["hbm_gbs"], 1),
                                         frac=round(ssim["achieved_gbs"] / peaks["hbm_gbs"], 4),
                                         peak_source=peaks["source"]),
-                          "uncertainty_mlp": dict(umlp, peak=round(152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6, 2),
-                                                  frac=round(umlp["achieved_tflops"]
-                                                             / (152 * 128 * 2 * peaks["sm_max_mhz"] / 1e6), 4),
-                                                  peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"),
+                          "uncertainty_mlp": dict(umlp, peak=round(alu_peak(peaks), 2),
+                                                  frac=round(umlp["achieved_tflops"] / alu_peak(peaks), 4),
+                                                  peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock"),
                           "anchor_update": dict(anch, peak=round(peaks["hbm_gbs"], 1),
                                                 frac=round(anch["achieved_gbs"] / peaks["hbm_gbs"], 4),
                                                 peak_source=peaks["source"])},
@@ -351,24 +393,32 @@ def run_ours(args, wl_name):
         dist.destroy_process_group()
 
 
-def roofline(stage, alg, stage_ms, launches, peaks, bf16=False):
+def alu_peak(peaks):
+    """FP32 FMA peak in TFLOP/s: SMs (from the device properties) x 128 FP32
+    lanes x 2 flops x the maximum SM clock."""
+    return peaks["sm_count"] * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+
+
+def roofline(stage, alg, stage_ms, launches, peaks, bf16=False, force_hbm=False):
     """Roofline of one stage: its algorithmic work per step over its time per step
     (stages of several launches, e.g. chunked decode backward, are taken whole)."""
     a = alg.get(stage, {})
     common = dict(kernel=stage, traffic=None, stage_ms=round(stage_ms, 4),
                   avg_launch_ms=round(stage_ms / max(launches, 1), 4), algorithmic_bytes=a.get("bytes"))
-    if bf16 and stage in ("decode_fwd", "decode_bwd_rows") and "flops" in a:
+    if bf16 and not force_hbm and stage in ("decode_fwd", "decode_bwd_rows") and "flops" in a:
         # BF16 operands on the tcgen05 tensor cores; timed inside a long step
         peak = peaks["bf16_tflops_sustained"]
         ach = a["flops"] / (stage_ms / 1e3) / 1e12
         return dict(common, bound="tensor", achieved=round(ach, 3), peak=round(peak, 1), unit="TFLOP/s",
                     frac=round(ach / peak, 4), peak_source=peaks["source"] + " (bf16, sustained)",
                     algorithmic_flops=a["flops"])
-    if stage in ALU_STAGES and "flops" in a:
-        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+    if stage in ALU_STAGES and "flops" in a and not force_hbm:
+        peak = alu_peak(peaks)
         ach = a["flops"] / (stage_ms / 1e3) / 1e12
         return dict(common, bound="alu", achieved=round(ach, 3), peak=round(peak, 2), unit="TFLOP/s",
-                    frac=round(ach / peak, 4), peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    frac=round(ach / peak, 4),
+                    peak_source=f"derived: {peaks['sm_count']} SMs (device properties) x 128 FP32 lanes x 2 x "
+                                f"max SM clock {peaks['sm_max_mhz']:.0f} MHz",
                     algorithmic_flops=a["flops"])
     ach = a.get("bytes", 0) / (stage_ms / 1e3) / 1e9
     return dict(common, bound="hbm", achieved=round(ach, 1), peak=peaks["hbm_gbs"], unit="GB/s",
@@ -727,6 +777,18 @@ def serving_schedule(seconds, seed=2):
 
 
 def run_serving(args):
+    torch_line = measure_serving(args.serve_seconds)
+    print(json.dumps(dict({"metric": "serving mix: fwd+bwd Mpixel/s and tracking p50/p99 latency, plain vs served",
+                           "value": torch_line["served"]["mpix_per_s"], "unit": "Mpixel/s", "n_gpus": 1,
+                           "higher_is_better": True, "dtype": "f32 (bf16 decode GEMMs)", "data": "synthetic"},
+                          **torch_line)))
+
+
+def measure_serving(seconds):
+    """The serving mix on one GPU, both paths on the same open-loop schedule:
+    'plain' = one request per launch, FIFO, one slot; 'served' = continuous
+    batching over two slots.  Returns per path Mpixel/s and p50/p99 latency
+    (completion - scheduled arrival) per request class."""
     import torch
     from paper_2505_22335_gb300 import binding as B
     from paper_2505_22335_gb300 import scenes
@@ -735,7 +797,7 @@ def run_serving(args):
     anc = scenes.anchors(0, c["A"], c["K"])
     mlp = scenes.mlp_weights(1000, c["K"], c["NF"])
     ad, md = B.anchors_to_device(anc, mlp)
-    sched = serving_schedule(args.serve_seconds)
+    sched = serving_schedule(seconds)
     # request inputs from small pools (contents do not change the work)
     rng = np.random.default_rng(3)
     poses = scenes.arc_poses(4, 16)
@@ -800,15 +862,38 @@ def run_serving(args):
                          tracking_p50_ms=round(q(lat[0], 50), 2), tracking_p99_ms=round(q(lat[0], 99), 2),
                          mapping_p50_ms=round(q(lat[1], 50), 2), mapping_p99_ms=round(q(lat[1], 99), 2),
                          requests=len(lat[0]) + len(lat[1]))
-    line = {"metric": "serving mix: fwd+bwd Mpixel/s and tracking p50/p99 latency, plain vs served",
-            "value": out["served"]["mpix_per_s"], "unit": "Mpixel/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32 (bf16 decode GEMMs)", "data": "synthetic",
-            "config": {"workload": f"serving_mix_{c['A'] // 1000}k_anchors_x{c['K']}",
-                       "tracking": f"{c['track_rate']}/s, {c['levels']} pyramid levels from {c['W']}x{c['H']}, fwd + pose-only bwd",
-                       "mapping": f"{c['map_rate']}/s, {c['map_views'][0]}-{c['map_views'][1]} keyframes {c['W']}x{c['H']}, full bwd",
-                       "seconds": args.serve_seconds, "arrivals": "open-loop Poisson, seed 2"},
-            "plain": out["plain"], "served": out["served"]}
-    print(json.dumps(line))
+    del ad, md, track_tg, map_tg
+    torch.cuda.empty_cache()
+    better = (out["served"]["mpix_per_s"] > out["plain"]["mpix_per_s"]
+              and out["served"]["tracking_p99_ms"] < out["plain"]["tracking_p99_ms"])
+    return {"config": {"workload": f"serving_mix_{c['A'] // 1000}k_anchors_x{c['K']}",
+                       "tracking": f"{c['track_rate']}/s, {c['levels']} pyramid levels from {c['W']}x{c['H']}, "
+                                   f"fwd + pose-only bwd",
+                       "mapping": f"{c['map_rate']}/s, {c['map_views'][0]}-{c['map_views'][1]} keyframes "
+                                  f"{c['W']}x{c['H']}, full bwd",
+                       "decode": "bf16 tensor cores", "seconds": seconds, "arrivals": "open-loop Poisson, seed 2",
+                       "latency": "completion - scheduled arrival"},
+            "plain": out["plain"], "served": out["served"],
+            "served_beats_plain_in_mpix_and_tracking_p99": bool(better)}
+
+
+def run_only(args):
+    """One part of the bench on its own, for profiler captures: no timed step,
+    no JSON contract line (prints a short JSON summary)."""
+    import torch
+    torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    anc, mlp, cams, tg = make_inputs(wl, seed=0)
+    if args.only == "anchor_update":
+        res = run_anchor(args, wl, anc, cams[0])
+    else:
+        st = Step(wl, anc, mlp, cams, tg, 0, bf16=args.decode_bf16)
+        for _ in range(args.warmup):
+            st.run()
+        torch.cuda.synchronize()
+        res = dict(tracking_uncertainty=run_uncertainty(args, st, wl), feature_lifting=run_lift(args, st, wl),
+                   dssim=run_ssim(args, st, wl), uncertainty_mlp=run_unc_mlp(args, st, wl))
+    print(json.dumps(dict(only=args.only, workload=args.workload, result=res)))
 
 
 def main():
@@ -824,8 +909,18 @@ def main():
                     help="decode MLP GEMMs in BF16 on the tensor cores (FP32 accumulation)")
     ap.add_argument("--serving", action="store_true",
                     help="serving mix (500k anchors resident): plain FIFO path vs continuous batching")
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave the serving-mix comparison out of the default line")
+    ap.add_argument("--only", choices=["anchor_update", "next_rows"], default=None,
+                    help="run only one part (for profiler captures): the anchor update on the default "
+                         "workload's anchors, or the next-row entry points on one step's images")
     args = ap.parse_args()
+    if args.only:
+        from paper_2505_22335_gb300 import build as _b
+        _b.build()
+        run_only(args)
+        return
     if args.serving:
         from paper_2505_22335_gb300 import build as _b
         _b.build()

@@ -410,7 +410,12 @@ ups_status ups_anchor_update(ups_ctx *ctx, const ups_anchor_cfg *acfg, const ups
 /* backward                                                               */
 /* ---------------------------------------------------------------------- */
 
-/* Reverse-order backward of the last ups_render_forward on ctx.
+/* Reverse-order backward of the last ups_render_forward on ctx: the
+ * derivative of the blending of Eq. 3 and Eq. 10 (walked back to front from
+ * each pixel's last blended Gaussian, transmittance recomputed by division
+ * from the stored final T) and of the projection of Eq. 1-2 (conic, camera
+ * point, 3D covariance from scale and quaternion), and of the pose T_cw <-
+ * Exp(xi) T_cw at xi = 0, xi = (rho, phi).
  *  dL        image gradients (any may be NULL)
  *  grad      UPS_GRAD_GAUSS: dL/d(Gaussian set), same shape as the forward
  *            input; OVERWRITTEN (per_view == 1) or OVERWRITTEN as the sum over
@@ -568,14 +573,16 @@ const char *ups_server_last_error(const ups_server *srv);
  *  cfg       thresholds and n_feat (k, feat_dim, hidden, decode_bf16 unused)
  *  g, cams, n_views, out   as for ups_render_forward; runs on the CURRENT
  *            device, stream-ordered on `stream`, and synchronises it once
- * Limits, checked before any kernel runs (UPS_ERR_CAPACITY, message via
- * ups_last_error(NULL)): n * n_views <= 65536, <= 8192 16x16 tiles over all
- * views, <= 524288 tile instances.  No backward state is kept.
+ * Limits (UPS_ERR_CAPACITY, message via ups_last_error(NULL)): n * n_views
+ * <= 65536 and <= 8192 16x16 tiles over all views, both checked before any
+ * kernel runs; <= 524288 tile instances, known only after the projection and
+ * depth sort have run: on that error the static array has been written and
+ * the output images have not.  No backward state is kept.
  * The static array is shared by every call on a device and keeps the last
  * call's contents (each call writes or clears what it reads); calls that
- * overlap on the GPU race on it and must be serialised by the caller.  The
- * first call on each device looks up the array's device address; make that
- * first call before any stream capture. */
+ * overlap on the GPU race on it and must be serialised by the caller.  Every
+ * call looks up the array's device address on the current device and
+ * synchronises `stream` once (to read the instance count). */
 ups_status ups_render_forward_static(const ups_config *cfg, const ups_gaussians *g,
                                      const ups_camera *cams, int n_views, ups_images *out,
                                      ups_stream stream);

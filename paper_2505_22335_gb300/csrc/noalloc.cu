@@ -10,19 +10,23 @@
 // is the static array below, fixed in size, which every GPU that loads the
 // library keeps until the process exits.
 //
-// Limits (checked before any launch, UPS_ERR_CAPACITY when exceeded):
-//   n * n_views            <= 65,536 Gaussian-views
-//   tiles over all views   <= 8,192 (16x16-pixel tiles)
-//   tile instances         <= 524,288 (known after projection)
+// Limits (UPS_ERR_CAPACITY when exceeded):
+//   n * n_views            <= 65,536 Gaussian-views  (checked before any launch)
+//   tiles over all views   <= 8,192 16x16 tiles      (checked before any launch)
+//   tile instances         <= 524,288                (known only after the
+//       projection, the depth sort and the count scan have run and the stream
+//       has been synchronised: on this error the scratch array has been
+//       written and the output images have not)
 // Scratch size: about 14 MB.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; everything a call reads is written (or cleared) by that call
 // first.  Calls that overlap on the GPU (two streams, two host threads) race
-// on the array: serialise them.  The first call on each device looks up the
-// array's device address (cudaGetSymbolAddress) with that device current; make
-// that first call before any stream capture.
-#include <mutex>
+// on the array: serialise them.  Every call looks up the array's device
+// address (cudaGetSymbolAddress, which allocates nothing) on the caller's
+// current device, so a device reset or a new primary context, which may load
+// the module at another address, is followed.  Every call synchronises its
+// stream once (to read the instance count).
 #include <string>
 
 #include "common.cuh"
@@ -89,25 +93,19 @@ constexpr size_t kScratchBytes = oScan + kScanScratch;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-std::mutex g_addr_mutex;
-unsigned char *g_addr[256] = {};  // device address of g_static_scratch, per device ordinal
-
 ups_status fail(ups_status s, const std::string &msg) {
     set_global_error("ups_render_forward_static: " + msg);
     return s;
 }
 
-ups_status scratch_address(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= 256) return fail(UPS_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_addr_mutex);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(UPS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_addr[dev];
+// device address of g_static_scratch on the current device (the host-side
+// name of the array is not a device address)
+ups_status scratch_address(unsigned char **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(UPS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned char *>(p);
     return UPS_OK;
 }
 
@@ -185,10 +183,8 @@ extern "C" ups_status ups_render_forward_static(const ups_config *cfg, const ups
     const BlendParams bp{cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->near_z};
     const int N = g->n, per_view = g->per_view ? 1 : 0;
 
-    int dev = 0;
-    NA_CUDA(cudaGetDevice(&dev));
     unsigned char *base = nullptr;
-    ups_status s = scratch_address(dev, &base);
+    ups_status s = scratch_address(&base);
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 

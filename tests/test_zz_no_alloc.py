@@ -73,3 +73,37 @@ def test_static_forward_rejects_oversized_input():
         B.render_forward_static(gs, cams, out, 0)
     assert ei.value.status == 8 and "65536" in str(ei.value)
     torch.cuda.synchronize()
+
+
+def test_static_forward_rejects_too_many_tiles():
+    import torch
+    g = scenes.plain_gaussians(2, 100, 0)
+    # 2048 x 1040 pixels = 128 x 65 = 8,320 tiles, above the 8,192 limit
+    cams = [scenes.Camera(1000.0, 1000.0, 1024.0, 520.0, 2048, 1040, np.eye(4))]
+    gs = B.to_set(g)
+    out = B.Renderer(n_feat=0, k=1).alloc_images(cams)
+    with pytest.raises(B.UpsError) as ei:
+        B.render_forward_static(gs, cams, out, 0)
+    assert ei.value.status == 8 and "8192" in str(ei.value)
+    torch.cuda.synchronize()
+
+
+def test_static_forward_instance_overflow_then_normal_call():
+    """Large Gaussians close to the camera cover most of the 1,200 tiles of a
+    640x480 view: more than 524,288 tile instances.  That limit is known only
+    after the projection and the depth sort have written the static array; the
+    call must fail with the capacity status, and the next call (a normal scene)
+    must still match the context forward, i.e. the half-written array must not
+    leak into it."""
+    import torch
+    cams = scenes.cameras(0, 1, 640, 480, 600.0, identity=True)
+    big = scenes.plain_gaussians(3, 3000, 16, scale_lo=0.3, scale_hi=0.6)
+    gs = B.to_set(big)
+    out = B.Renderer(n_feat=16, k=1).alloc_images(cams)
+    with pytest.raises(B.UpsError) as ei:
+        B.render_forward_static(gs, cams, out, 16)
+    assert ei.value.status == 8 and "524288" in str(ei.value)
+    torch.cuda.synchronize()
+    base = scenes.cameras(7, 3, 100, 70, 90.0)
+    cams2 = [base[0], base[1].scaled(0.5), scenes.Camera(40.0, 40.0, 16.5, 8.5, 33, 17, base[2].T_cw)]
+    _case(scenes.plain_gaussians(11, 3000, 16), cams2, 16)
