@@ -94,6 +94,14 @@ __device__ __forceinline__ void covariance(const DevView &cam, const BlendParams
 
 // The alpha >= alpha_min ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= k2,
 // k2 = 2 ln(o / alpha_min), of a projected Gaussian at (u, v), conic (a, b, c).
+// Tile decisions use a margin so that FP32 rounding never drops a tile the
+// blend uses: k2 grown by kMarginQ (relative) and every tile's box of pixel
+// centres grown by kMarginPx on each side; the rectangle is the box of that
+// grown ellipse, grown by kMarginPx.  A list may thus hold, besides the exact
+// tiles, tiles whose box the exact ellipse misses by less than the margin.
+constexpr float kMarginQ = 1e-4f;
+constexpr float kMarginPx = 1e-3f;
+
 struct Ellipse {
     float u, v, a, b, k2, detc, ry, dyr;
 };
@@ -105,7 +113,7 @@ __device__ __forceinline__ Ellipse ellipse_of(float4 xo, float4 cn, float alpha_
     e.a = cn.x;
     e.b = cn.y;
     // a relative margin so FP32 rounding never drops a tile the blend uses
-    e.k2 = 2.f * logf(xo.w / alpha_min) * (1.f + 1e-4f);
+    e.k2 = 2.f * logf(xo.w / alpha_min) * (1.f + kMarginQ);
     e.detc = cn.x * cn.z - cn.y * cn.y;
     e.ry = sqrtf(e.k2 * cn.x / e.detc);               // half-extent in y
     e.dyr = -cn.y * sqrtf(e.k2 / (cn.z * e.detc));    // dy of the point of largest x
@@ -119,14 +127,15 @@ __device__ __forceinline__ Ellipse ellipse_of(float4 xo, float4 cn, float alpha_
 // unconstrained extreme clamped to the band (the boundary's x is concave /
 // convex in dy).
 __device__ __forceinline__ int2 row_cols(const Ellipse &e, int ty, int W, int H, int x0, int x1) {
-    const float yb0 = (float)(ty * kTile), yb1 = fminf((float)(ty * kTile + kTile - 1), (float)(H - 1));
+    const float yb0 = (float)(ty * kTile) - kMarginPx,
+                yb1 = fminf((float)(ty * kTile + kTile - 1), (float)(H - 1)) + kMarginPx;
     const float lo = fmaxf(yb0 - e.v, -e.ry), hi = fminf(yb1 - e.v, e.ry);
     if (!(lo <= hi)) return make_int2(1, 0);
     const float dr = fminf(fmaxf(e.dyr, lo), hi), dl = fminf(fmaxf(-e.dyr, lo), hi);
     const float ia = 1.f / e.a;
     const float xr = (-e.b * dr + sqrtf(fmaxf(e.a * e.k2 - e.detc * dr * dr, 0.f))) * ia;
     const float xl = (-e.b * dl - sqrtf(fmaxf(e.a * e.k2 - e.detc * dl * dl, 0.f))) * ia;
-    const float xlo = fmaxf(e.u + xl - 1e-3f, 0.f), xhi = fminf(e.u + xr + 1e-3f, (float)(W - 1));
+    const float xlo = fmaxf(e.u + xl - kMarginPx, 0.f), xhi = fminf(e.u + xr + kMarginPx, (float)(W - 1));
     if (!(xlo <= xhi)) return make_int2(1, 0);
     // tile tx holds pixel centres [16 tx, 16 tx + 15]: the first whose box
     // reaches xlo, the last whose box starts at or before xhi
@@ -162,9 +171,10 @@ __global__ void __launch_bounds__(256) k_project(
         float vv = fmaf(cam.fy * G.p[1], iz, cam.cy);
         xo.x = u;
         xo.y = vv;
-        // bounding box of the ellipse o exp(-q/2) >= alpha_min
-        float k2 = 2.f * logf(m.w / bp.alpha_min);
-        float rx = sqrtf(k2 * G.A), ry = sqrtf(k2 * G.C);
+        // bounding box of the ellipse o exp(-q/2) >= alpha_min, with the
+        // margin of the tile decisions
+        float k2 = 2.f * logf(m.w / bp.alpha_min) * (1.f + kMarginQ);
+        float rx = sqrtf(k2 * G.A) + kMarginPx, ry = sqrtf(k2 * G.C) + kMarginPx;
         float xlo = fmaxf(u - rx, 0.f), xhi = fminf(u + rx, (float)(cam.W - 1));
         float ylo = fmaxf(vv - ry, 0.f), yhi = fminf(vv + ry, (float)(cam.H - 1));
         if (xlo <= xhi && ylo <= yhi) {

@@ -170,3 +170,42 @@ def test_scene_swap_after_anchor_update(scene):
     torch.cuda.synchronize()
     assert abs(req["loss"].item() - loss.item()) <= 1e-5 + 1e-4 * abs(loss.item())
     assert rel_l2(req["d_pose"].cpu().numpy(), d_pose.sum(0).cpu().numpy()) < 2e-3
+
+
+def test_served_results_match_oracle():
+    """A tracking request (3 pyramid levels of one pose, forward + pose-only
+    backward) and a mapping request (3 keyframes, full backward) submitted
+    together to the continuous-batching server: each request's loss, pose
+    gradient and (mapping) MLP gradient against the FP64 oracle run from the
+    same seeded, float32-rounded scene, cameras and targets (loss normalised by
+    the request's own pixels, pose gradients of the levels summed)."""
+    import torch
+    import oracle
+    from gpu_cases import CFG, round_cams, round_dict
+    anc = round_dict(scenes.anchors(60, 600, K))
+    mlp = round_dict(scenes.mlp_weights(61, K, NF, bias_sigma=0.05))
+    ad, md = B.anchors_to_device(anc, mlp)
+    srv = B.Server(ad, md, n_feat=NF, k=K, slots=2, max_batch_views=16, batching=True)
+    cam_t = round_cams(scenes.cameras(62, 1, 160, 120, 150.0))[0]
+    levels = pyramid(cam_t, 3)
+    tg_t = [round_dict(t) for t in scenes.targets(63, levels, NF, weighted=True)]
+    cams_m = round_cams(scenes.cameras(64, 3, 160, 120, 150.0))
+    tg_m = [round_dict(t) for t in scenes.targets(65, cams_m, NF, weighted=True)]
+    loss_t, pose_t = torch.zeros(1, device="cuda"), torch.zeros(6, device="cuda")
+    loss_m, pose_m = torch.zeros(1, device="cuda"), torch.zeros(18, device="cuda")
+    g_m = zero_mlp(md)
+    t1 = srv.submit(B.TRACK, [cam_t], B.targets_to_device(tg_t), loss_t, pose_t, levels=3)
+    t2 = srv.submit(B.MAP, cams_m, B.targets_to_device(tg_m), loss_m, pose_m, d_mlp=g_m)
+    r1, r2 = srv.wait(t1), srv.wait(t2)
+    assert r1["status"] == 0 and r2["status"] == 0
+    torch.cuda.synchronize()
+    srv.close()
+    lc = oracle.LossCfg()
+    L_t, ref_t, _, _ = oracle.backward_anchor(anc, mlp, levels, tg_t, CFG, lc, K, NF)
+    L_m, ref_m, _, _ = oracle.backward_anchor(anc, mlp, cams_m, tg_m, CFG, lc, K, NF)
+    for L, got in ((L_t, loss_t.item()), (L_m, loss_m.item())):
+        assert abs(got - L) <= 1e-5 + 1e-4 * abs(L), (got, L)
+    assert rel_l2(pose_t.cpu().numpy(), ref_t["pose"].sum(axis=0)) < 2e-3
+    assert rel_l2(pose_m.cpu().numpy().reshape(3, 6), ref_m["pose"]) < 2e-3
+    for k in ("w1", "b1", "w2", "b2"):
+        assert rel_l2(g_m[k].cpu().numpy(), ref_m[k]) < 2e-3, k
