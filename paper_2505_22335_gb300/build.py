@@ -63,10 +63,7 @@ def build(force: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    # cuBLAS (the feature lifting's plain GEMMs), found through the toolkit's
-    # library directory at run time
-    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-Xlinker", "-rpath=" + libdir]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

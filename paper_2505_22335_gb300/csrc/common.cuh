@@ -25,6 +25,8 @@ struct DevView {
     float t[3];     // translation of T_cw
     float limx, limy;  // frustum guard on |X/Z|, |Y/Z|
     float t_norm;
+    int set;        // the Gaussian set this view reads (attribute index set * n + g)
+    int set_first;  // 1: the first view reading that set
 };
 
 struct ViewTable {
@@ -119,6 +121,13 @@ cudaError_t bucket_sort_u32(const uint32_t *keys, const uint32_t *vals, uint32_t
                             int num_sms, cudaStream_t st, const int *gate = nullptr);
 // keys[i] = t for every i in ranges[t] (the sorted keys of a bucket sort)
 cudaError_t keys_from_ranges(const uint2 *ranges, int nbins, uint32_t *keys, cudaStream_t st);
+// C (column-major m x n, leading dimension ldc) = alpha op(A) op(B) + beta C
+// in FP32 on the CUDA cores (op = transpose when ta / tb); column-major A
+// (m x k, or k x m when ta) and B (k x n, or n x k when tb).  Splits K over
+// several CTAs (atomic adds) when the output alone would not fill the GPU.
+// *launches (may be null) counts the kernels launched.
+cudaError_t gemm_f32(cudaStream_t st, bool ta, bool tb, int m, int n, int k, float alpha, const float *A, int lda,
+                     const float *B, int ldb, float beta, float *C, int ldc, int num_sms, int *launches);
 // Exclusive scan of n uint32 into uint64 (out has n+1 entries; out[n] = total).
 size_t scan_scratch_bytes(size_t n);
 cudaError_t exclusive_scan_u32_u64(const uint32_t *in, uint64_t *out, size_t n, void *scratch,

@@ -4,58 +4,70 @@
 //
 // One CTA per 16x16 image tile, PX pixels per thread (forward 2; backward 4
 // for up to 16 feature channels, 2 for 32: registers).  The tile's
-// depth-ordered Gaussian list is walked in batches of 256 staged in shared
-// memory; a CTA stops when every pixel has terminated.  The backward walks
-// the same list from each pixel's last blended Gaussian to the front,
-// recomputing transmittance by division from the stored final T, and reduces
-// per-Gaussian gradients across the warp (transposed butterfly: each lane
-// ends up owning one or two of the record's values) before one coalesced
-// atomic add per warp.
+// depth-ordered Gaussian list is staged in shared memory in batches of kStage
+// entries by the bulk-copy (TMA) engine: one cp.async.bulk per attribute
+// record of an entry, completed on the batch's mbarrier, in a ring of stages
+// so that the next batches load while one is blended.  A CTA stops when every
+// pixel has terminated.  The backward walks the same list from each pixel's
+// last blended Gaussian to the front, recomputing transmittance by division
+// from the stored final T, and reduces per-Gaussian gradients over the warp
+// through a shared-memory transpose before one vector atomic add per record
+// group.
+//
+// Per (pixel, Gaussian) the exponent is evaluated as p(dy) = pa + dy (pb + pc
+// dy), the quadratic form of the conic with the Gaussian's column offset dx
+// fixed per thread (pa = -a dx^2 / 2, pb = -b dx, pc = -c / 2); the forward
+// and the backward share this evaluation, so both take the same alpha
+// decisions.  The four pixels of a thread are processed without branches
+// (a pixel that takes no part contributes zero), which lets their independent
+// dependency chains interleave.
 #include <algorithm>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace ups {
 
 namespace {
 
-constexpr int kBatch = 256;
+constexpr int kStage = 32;       // list entries per staged batch
+constexpr int kWaitPolls = 1 << 22;
 
-// channels [c, c + 4) of staged Gaussian j as two pairs
-template <int NF, class St>
-__device__ __forceinline__ ulonglong2 feat4(const St &S, int j, int c) {
-    return *reinterpret_cast<const ulonglong2 *>(&S.feat[j][c]);
-}
-
+// one staged batch: attribute records of kStage list entries
 template <int NF>
 struct Stage {
-    float4 xyzo[kBatch];
-    float4 conic[kBatch];
-    float4 color[kBatch];
-    // Gaussian-major, rows padded by 4 floats: 16-byte broadcast reads of four
-    // channels, conflict-free 16-byte staging stores
-    float feat[kBatch][NF > 0 ? NF + 4 : 1];
-    uint32_t gv[kBatch];
+    float4 xyzo[kStage];
+    float4 conic[kStage];
+    float4 color[kStage];
+    float feat[kStage][NF > 0 ? NF : 4];  // 16-byte rows
+    uint32_t gv[kStage];
 };
 
+template <int NF> struct StageBytes { static constexpr uint32_t value = 48u + 4u * NF; };
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     umma::smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(umma::smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(umma::smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Entry t of a batch: its Gaussian-view id to shared memory, its four
+// attribute records by bulk copies completing on mbar.
 template <int NF>
-__device__ __forceinline__ void stage_load(Stage<NF> &S, int slot, uint32_t gv, int gs,
-                                           const float4 *__restrict__ xyzo,
-                                           const float4 *__restrict__ conic,
-                                           const float4 *__restrict__ color,
-                                           const float *__restrict__ feat) {
-    S.gv[slot] = gv;
-    S.xyzo[slot] = xyzo[gv];
-    S.conic[slot] = conic[gv];
-    S.color[slot] = color[gs];
-    if (NF > 0) {
-        const float4 *f4 = reinterpret_cast<const float4 *>(feat + (size_t)gs * NF);
-#pragma unroll
-        for (int c = 0; c < NF / 4; ++c) {
-            float4 f = f4[c];
-            *reinterpret_cast<float4 *>(&S.feat[slot][4 * c]) = f;
-        }
-    }
+__device__ __forceinline__ void stage_entry(Stage<NF> &S, int t, uint32_t gv, int gs, const float4 *__restrict__ xyzo,
+                                            const float4 *__restrict__ conic, const float4 *__restrict__ color,
+                                            const float *__restrict__ feat, uint64_t *mbar) {
+    S.gv[t] = gv;
+    bulk_load(&S.xyzo[t], xyzo + gv, 16, mbar);
+    bulk_load(&S.conic[t], conic + gv, 16, mbar);
+    bulk_load(&S.color[t], color + gs, 16, mbar);
+    if (NF > 0) bulk_load(&S.feat[t][0], feat + (size_t)gs * NF, 4 * NF, mbar);
 }
 
 // Each thread owns PX pixels of the tile, (x, y + (16 / PX) q) for q < PX:
@@ -94,6 +106,24 @@ __device__ __forceinline__ TileP<PX> tilep(const ViewTable &vt) {
 __host__ __device__ constexpr int blend_px_fwd(int nf) { return 2; }
 __host__ __device__ constexpr int blend_px_bwd(int nf) { return nf <= 16 ? 4 : 2; }
 
+// exponent coefficients of a staged Gaussian for a thread's pixel column
+struct Expo {
+    float pa, pb, pc;
+};
+__device__ __forceinline__ Expo expo(float4 cn, float dx) {
+    return Expo{-0.5f * cn.x * dx * dx, -cn.y * dx, -0.5f * cn.z};
+}
+__device__ __forceinline__ float expo_at(const Expo &e, float dy) { return fmaf(dy, fmaf(e.pc, dy, e.pb), e.pa); }
+
+// Waits (bounded) for the batches issued but not yet consumed, so that no
+// bulk copy is still writing this CTA's shared memory when it exits.
+__device__ __forceinline__ void drain(uint64_t *mbar, int consumed, int issued, int ns, int *err) {
+    for (int b = consumed; b < issued; ++b)
+        if (!umma::mbar_wait(&mbar[b % ns], (uint32_t)((b / ns) & 1), kWaitPolls) && err) *err = 1;
+}
+
+constexpr int kFwdStages = 4;
+
 template <int NF, int PX>
 __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
@@ -101,14 +131,45 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
     const float *__restrict__ feat, float *__restrict__ out_color, float *__restrict__ out_depth,
     float *__restrict__ out_feat, float *__restrict__ out_T, uint32_t *__restrict__ out_nc,
-    const uint32_t *__restrict__ trunc, int *__restrict__ trunc_flag, const int *__restrict__ gate) {
+    const uint32_t *__restrict__ trunc, int *__restrict__ trunc_flag, const int *__restrict__ gate,
+    int *__restrict__ err) {
     // gate: when non-null, blend only if *gate != 0 (a pass enqueued ahead of
     // the GPU's decision to run it)
     if (gate && *gate == 0) return;
-    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS;
-    __shared__ Stage<NF> S;
+    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS, NS = kFwdStages;
+    static_assert(NT >= kStage, "one thread per staged entry");
+    __shared__ __align__(128) Stage<NF> ring[NS];
+    __shared__ __align__(8) uint64_t mbar[NS];
     const TileP<PX> tc = tilep<PX>(vt);
     const uint2 rg = ranges[blockIdx.x];
+    const int n_list = (int)(rg.y - rg.x);
+    const int nb = (n_list + kStage - 1) / kStage;
+    const int set_base = (tc.v - tc.cam->set) * N;  // gv - set_base: attribute index
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int s = 0; s < NS; ++s) umma::mbar_init(&mbar[s], 1);
+    __syncthreads();
+    // a thread's entry of batch b (t < kStage)
+    auto issue = [&](int b, uint32_t gv) {
+        const int cnt = min(kStage, n_list - b * kStage);
+        Stage<NF> &S = ring[b % NS];
+        if (tid == 0) mbar_expect(&mbar[b % NS], (uint32_t)cnt * StageBytes<NF>::value);
+        if (tid < cnt) stage_entry<NF>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
+    };
+    auto entry_gv = [&](int b) -> uint32_t {
+        const int i = b * kStage + tid;
+        return (tid < kStage && i < n_list) ? ival[rg.x + i] : 0u;
+    };
+    int issued = min(NS, nb);
+    {
+        uint32_t pg[NS];
+#pragma unroll
+        for (int b0 = 0; b0 < NS; ++b0) pg[b0] = b0 < issued ? entry_gv(b0) : 0u;
+#pragma unroll
+        for (int b0 = 0; b0 < NS; ++b0)
+            if (b0 < issued) issue(b0, pg[b0]);
+    }
+
     const float fx = (float)tc.px;
     float fy[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
     f2 F[PX][NF > 0 ? NF / 2 : 1];  // feature accumulators, channel pairs
@@ -130,37 +191,46 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
         for (int q = 0; q < PX; ++q) d = d && done[q];
         return d;
     };
-    const int set_base = per_view ? 0 : tc.v * N;
-    for (uint32_t base = rg.x; base < rg.y; base += kBatch) {
-        if (__syncthreads_count(all_done()) == NT) break;
-#pragma unroll
-        for (int h = 0; h < kBatch / NT; ++h) {
-            uint32_t i = base + threadIdx.x + h * NT;
-            if (i < rg.y) {
-                uint32_t gv = ival[i];
-                stage_load<NF>(S, threadIdx.x + h * NT, gv, (int)gv - set_base, xyzo, conic, color, feat);
-            }
+    int b = 0;
+    bool ok_wait = true;
+    for (; b < nb; ++b) {
+        // prefetch the id of this thread's entry of the batch that will reuse this slot
+        const uint32_t nxt = issued < nb ? entry_gv(issued) : 0u;
+        const bool arrived = umma::mbar_wait(&mbar[b % NS], (uint32_t)((b / NS) & 1), kWaitPolls);
+        if (__syncthreads_or(!arrived)) {
+            ok_wait = false;  // the drain below waits for this batch again
+            if (err && tid == 0) *err = 1;
+            break;
         }
-        __syncthreads();
-        const int n = min((int)(rg.y - base), kBatch);
-        for (int j = 0; j < n && !all_done(); ++j) {
+        const Stage<NF> &S = ring[b % NS];
+        const int n = min(kStage, n_list - b * kStage);
+        for (int j = 0; j < n; ++j) {
+            if (__all_sync(0xffffffffu, all_done())) break;
             const float4 g = S.xyzo[j];
             const float4 cn = S.conic[j];
-            const float dx = fx - g.x;
+            const Expo ex = expo(cn, fx - g.x);
+            const uint32_t pos = (uint32_t)(b * kStage + j + 1);
+            // alpha and the stopping test of every pixel first (independent
+            // chains), then the weighted sums only where a pixel blends
+            float alpha[PX], Tn[PX];
+            bool use[PX];
+            bool any = false;
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
-                if (done[q]) continue;
-                const float dy = fy[q] - g.y;
-                const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
-                const float alpha = fminf(bp.alpha_max, g.w * __expf(power));
-                if (alpha < bp.alpha_min) continue;
-                const float Tn = T[q] * (1.f - alpha);
-                if (Tn < bp.t_min) {
-                    done[q] = true;
-                    continue;
-                }
-                const float w = alpha * T[q];
-                const float4 col = S.color[j];
+                alpha[q] = fminf(bp.alpha_max, g.w * __expf(expo_at(ex, fy[q] - g.y)));
+                Tn[q] = T[q] * (1.f - alpha[q]);
+                use[q] = !done[q] && alpha[q] >= bp.alpha_min;
+                const bool stop = use[q] && Tn[q] < bp.t_min;
+                done[q] = done[q] || stop;
+                use[q] = use[q] && !stop;
+                any = any || use[q];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float4 col = S.color[j];
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                if (!use[q]) continue;
+                const float w = alpha[q] * T[q];
                 C0[q] = fmaf(w, col.x, C0[q]);
                 C1[q] = fmaf(w, col.y, C1[q]);
                 C2[q] = fmaf(w, col.z, C2[q]);
@@ -168,15 +238,28 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
                 const f2 w2 = f2_make(w, w);
 #pragma unroll
                 for (int c = 0; c < NF; c += 4) {
-                    const ulonglong2 f = feat4<NF>(S, j, c);
+                    const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.feat[j][c]);
                     F[q][c / 2] = f2_fma(w2, f.x, F[q][c / 2]);
                     F[q][c / 2 + 1] = f2_fma(w2, f.y, F[q][c / 2 + 1]);
                 }
-                T[q] = Tn;
-                last[q] = base - rg.x + j + 1;
+                T[q] = Tn[q];
+                last[q] = pos;
             }
         }
+        // every thread is done with this slot (and with the batch) here
+        const bool finished = __syncthreads_count(all_done()) == NT;
+        if (finished) {
+            ++b;
+            break;
+        }
+        if (issued < nb) {
+            umma::fence_async_smem();
+            issue(issued, nxt);
+            ++issued;
+        }
     }
+    drain(mbar, b, issued, NS, err);
+    if (!ok_wait) return;
     // a list cut short by the list cap is exact only if every pixel stopped
     // inside it; otherwise the caller blends the tile again from a full list
     if (trunc && ((trunc[blockIdx.x >> 5] >> (blockIdx.x & 31)) & 1u))
@@ -277,62 +360,90 @@ __global__ void k_scale_mean(const float4 *__restrict__ scale, size_t n, float c
 // backward
 // ---------------------------------------------------------------------------
 
-// Number of record slots reduced per warp: next power of two >= 12 + NF.
-template <int NF> struct RecPad { static constexpr int value = NF == 0 ? 16 : (NF <= 20 ? 32 : 64); };
+constexpr int kBwdStages = 3;
+// Tuning of the backward (compile-time): CTAs per SM the register allocation
+// targets at 4 pixels per thread (8 caps registers at 128), and whether a warp
+// skips a pixel row no lane of it blends (a vote per row) or runs it masked.
+#ifndef UPS_BWD_MIN_BLOCKS
+#define UPS_BWD_MIN_BLOCKS 6
+#endif
+#ifndef UPS_BWD_ROW_SKIP
+#define UPS_BWD_ROW_SKIP 0
+#endif
+constexpr int kBwdMinBlocks = UPS_BWD_MIN_BLOCKS;
+constexpr int kRedStride = 36;  // floats per lane row of the reduction scratch
 
-// Transposed butterfly reduction of RP values over the 32 lanes.  On return
-// v[0..max(RP/32,1)-1] holds the warp sums of record indices idx_of(lane, i).
-template <int RP>
-__device__ __forceinline__ void warp_transpose_reduce(float (&v)[RP], int lane) {
-    constexpr unsigned full = 0xffffffffu;
-    int n = RP;
+// Sums over the warp of the per-lane gradient record values v (float4 groups
+// 0..NG-1 of the record: du dv dz do | dca dcb dcc - | dr dg db - | df...) and
+// adds them to rec (16-byte aligned) with one vector atomic per group.  The
+// lanes write their groups to a [32][kRedStride] scratch row (16-byte stores,
+// conflict-free), lane l then sums rows 8 (l / 8) .. 8 (l / 8) + 7 of column
+// group l % 8 (a 32-float chunk at a time), and two butterfly steps over
+// l / 8 finish the sums.  All 32 lanes must call it.
+template <int NG>
+__device__ __forceinline__ void warp_record_add(const float4 (&v)[NG], float (*red)[kRedStride], int lane,
+                                                float *rec) {
+    const int col = lane & 7, rq = lane >> 3;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        if (n > 1) {
-            const bool up = (lane & o) != 0;
+    for (int c0 = 0; c0 < NG; c0 += 8) {
+        constexpr int kMax = 8;
 #pragma unroll
-            for (int i = 0; i < RP / 2; ++i) {
-                if (i < n / 2) {
-                    float send = up ? v[i] : v[i + n / 2];
-                    float keep = up ? v[i + n / 2] : v[i];
-                    v[i] = keep + __shfl_xor_sync(full, send, o);
-                }
+        for (int k = 0; k < kMax; ++k)
+            if (c0 + k < NG) *reinterpret_cast<float4 *>(&red[lane][4 * k]) = v[c0 + k];
+        __syncwarp();
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + col < NG) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 x = *reinterpret_cast<const float4 *>(&red[8 * rq + r][4 * col]);
+                sum.x += x.x;
+                sum.y += x.y;
+                sum.z += x.z;
+                sum.w += x.w;
             }
-            n >>= 1;
-        } else {
-            v[0] += __shfl_xor_sync(full, v[0], o);
         }
+#pragma unroll
+        for (int o = 8; o <= 16; o <<= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, o);
+            sum.w += __shfl_xor_sync(0xffffffffu, sum.w, o);
+        }
+        if (rq == 0 && c0 + col < NG) atomicAdd(reinterpret_cast<float4 *>(rec) + c0 + col, sum);
+        __syncwarp();
     }
 }
 
 template <int NF, int PX>
-__global__ void __launch_bounds__(Px<PX>::NT) k_composite_bwd(
+__global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_composite_bwd(
     ViewTable vt, BlendParams bp, int N, int per_view, const uint2 *__restrict__ ranges,
     const uint32_t *__restrict__ ival, const float4 *__restrict__ xyzo,
     const float4 *__restrict__ conic, const float4 *__restrict__ color,
     const float *__restrict__ feat, const float *__restrict__ in_T,
     const uint32_t *__restrict__ in_nc, const float *__restrict__ dC,
     const float *__restrict__ dD, const float *__restrict__ dF, const float *__restrict__ dT,
-    float *__restrict__ g2) {
-    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS;
-    constexpr int RP = RecPad<NF>::value;
-    constexpr int STRIDE = kG2Base + NF;
-    __shared__ Stage<NF> S;
-    __shared__ uint32_t s_max[NT / 32];
+    float *__restrict__ g2, int *__restrict__ err) {
+    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS, NW = NT / 32, NS = kBwdStages;
+    constexpr int STRIDE = kG2Base + NF;  // record floats, a multiple of 4
+    constexpr int NG = STRIDE / 4;
+    static_assert(NT >= kStage, "one thread per staged entry");
+    __shared__ __align__(128) Stage<NF> ring[NS];
+    __shared__ __align__(8) uint64_t mbar[NS];
+    __shared__ __align__(16) float red[NW][32][kRedStride];
+    __shared__ uint32_t s_max[NW];
     const TileP<PX> tc = tilep<PX>(vt);
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint2 rg = ranges[blockIdx.x];
     const float fx = (float)tc.px;
     const DevView &cam = *tc.cam;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
-    float fy[PX], T[PX], acc[PX], gC0[PX], gC1[PX], gC2[PX], gD[PX];
+    float T[PX], acc[PX], gC0[PX], gC1[PX], gC2[PX], gD[PX];
     f2 gF[PX][NF > 0 ? NF / 2 : 1];  // dL/d(feature image), channel pairs
     uint32_t nc[PX];
     uint32_t my_nc = 0;
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
-        fy[q] = (float)(tc.py0 + RS * q);
         T[q] = 1.f;
         acc[q] = gC0[q] = gC1[q] = gC2[q] = gD[q] = 0.f;
         nc[q] = 0u;
@@ -355,109 +466,139 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_bwd(
         if (dT) acc[q] = dT[P + p] * T[q];
         my_nc = max(my_nc, nc[q]);
     }
+    if (tid == 0)
+        for (int s = 0; s < NS; ++s) umma::mbar_init(&mbar[s], 1);
     // longest blended prefix over the tile
-    uint32_t m = __reduce_max_sync(0xffffffffu, my_nc);
-    if (lane == 0) s_max[threadIdx.x >> 5] = m;
+    const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, my_nc);
+    if (lane == 0) s_max[wid] = warp_nc;
     __syncthreads();
-    uint32_t max_nc = 0;
+    int max_nc = 0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) max_nc = max(max_nc, s_max[w]);
-    const int set_base = per_view ? 0 : tc.v * N;
-    for (int hi = (int)max_nc; hi > 0; hi -= kBatch) {
-        const int lo = max(0, hi - kBatch);
-        __syncthreads();
+    for (int w = 0; w < NW; ++w) max_nc = max(max_nc, (int)s_max[w]);
+    // batch b holds list positions [max(0, max_nc - (b + 1) kStage), max_nc - b kStage), back to front
+    const int nb = (max_nc + kStage - 1) / kStage;
+    const int set_base = (tc.v - tc.cam->set) * N;  // gv - set_base: attribute index
+    auto lo_of = [&](int b) { return max(0, max_nc - (b + 1) * kStage); };
+    auto entry_gv = [&](int b) -> uint32_t {
+        const int lo = lo_of(b), i = lo + tid;
+        return (tid < kStage && i < max_nc - b * kStage) ? ival[rg.x + i] : 0u;
+    };
+    auto issue = [&](int b, uint32_t gv) {
+        const int lo = lo_of(b), cnt = max_nc - b * kStage - lo;
+        Stage<NF> &S = ring[b % NS];
+        if (tid == 0) mbar_expect(&mbar[b % NS], (uint32_t)cnt * StageBytes<NF>::value);
+        if (tid < cnt) stage_entry<NF>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
+    };
+    int issued = min(NS, nb);
+    {
+        uint32_t pg[NS];
 #pragma unroll
-        for (int h = 0; h < kBatch / NT; ++h) {
-            int i = lo + threadIdx.x + h * NT;
-            if (i < hi) {
-                uint32_t gv = ival[rg.x + i];
-                stage_load<NF>(S, threadIdx.x + h * NT, gv, (int)gv - set_base, xyzo, conic, color, feat);
-            }
+        for (int b0 = 0; b0 < NS; ++b0) pg[b0] = b0 < issued ? entry_gv(b0) : 0u;
+#pragma unroll
+        for (int b0 = 0; b0 < NS; ++b0)
+            if (b0 < issued) issue(b0, pg[b0]);
+    }
+    float fy[PX];
+#pragma unroll
+    for (int q = 0; q < PX; ++q) fy[q] = (float)(tc.py0 + RS * q);
+    int b = 0;
+    for (; b < nb; ++b) {
+        const uint32_t nxt = issued < nb ? entry_gv(issued) : 0u;
+        const bool arrived = umma::mbar_wait(&mbar[b % NS], (uint32_t)((b / NS) & 1), kWaitPolls);
+        if (__syncthreads_or(!arrived)) {
+            if (err && tid == 0) *err = 1;
+            break;  // the drain below waits for this batch again
         }
-        __syncthreads();
+        const Stage<NF> &S = ring[b % NS];
+        const int lo = lo_of(b), hi = max_nc - b * kStage;
         // warps whose pixels all stop earlier skip the tail of the batch
-        const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, my_nc);
-        int jstart = min(hi - lo, (int)warp_nc - lo) - 1;
+        const int jstart = min(hi, (int)warp_nc) - lo - 1;
         for (int j = jstart; j >= 0; --j) {
             const int idx = lo + j;
             const float4 g = S.xyzo[j];
             const float4 cn = S.conic[j];
-            const float4 col = S.color[j];
             const float dx = fx - g.x;
-            float v[RP];
-#pragma unroll
-            for (int k = 0; k < RP; ++k) v[k] = 0.f;
-            f2 vF[NF > 0 ? NF / 2 : 1];  // feature-gradient sums, channel pairs
-#pragma unroll
-            for (int c = 0; c < NF / 2; ++c) vF[c] = 0ull;
+            const Expo ex = expo(cn, dx);
+            float G[PX], alpha[PX], dy[PX];
+            bool use[PX];
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
-                if (idx >= (int)nc[q]) continue;
-                const float dy = fy[q] - g.y;
-                const float power = -0.5f * (cn.x * dx * dx + cn.z * dy * dy) - cn.y * dx * dy;
-                const float G = __expf(power);
-                const float raw = g.w * G;
-                const float alpha = fminf(bp.alpha_max, raw);
-                if (alpha < bp.alpha_min) continue;
-                any = true;
-                const float om = 1.f - alpha;
-                const float rom = __frcp_rn(om);
-                T[q] = T[q] * rom;  // transmittance in front of this Gaussian
-                const float w = alpha * T[q];
-                const f2 w2 = f2_make(w, w);
+                dy[q] = fy[q] - g.y;
+                G[q] = __expf(expo_at(ex, dy[q]));
+                alpha[q] = fminf(bp.alpha_max, g.w * G[q]);
+                use[q] = idx < (int)nc[q] && alpha[q] >= bp.alpha_min;
+                any = any || use[q];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const float4 col = S.color[j];
+            f2 fj[NF > 0 ? NF / 2 : 1];
+#pragma unroll
+            for (int c = 0; c < NF; c += 4) {
+                const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.feat[j][c]);
+                fj[c / 2] = f.x;
+                fj[c / 2 + 1] = f.y;
+            }
+            // per-thread sums over its pixels: the conic and mean terms need only
+            // sum dq, sum dq dy and sum dq dy^2 (dx is the thread's)
+            float sdq = 0.f, sdqy = 0.f, sdqyy = 0.f, sop = 0.f, sz = 0.f, sc0 = 0.f, sc1 = 0.f, sc2 = 0.f;
+            f2 vF[NF > 0 ? NF / 2 : 1];
+#pragma unroll
+            for (int c = 0; c < NF / 2; ++c) vF[c] = 0ull;
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                if (UPS_BWD_ROW_SKIP && !__any_sync(0xffffffffu, use[q])) continue;
+                const float a = use[q] ? alpha[q] : 0.f;
+                const float rom = use[q] ? __fdividef(1.f, 1.f - a) : 1.f;
+                T[q] *= rom;  // transmittance in front of this Gaussian
+                const float w = a * T[q];
                 f2 xg2 = 0ull;
+                const f2 w2 = f2_make(w, w);
 #pragma unroll
-                for (int c = 0; c < NF; c += 4) {
-                    const ulonglong2 f = feat4<NF>(S, j, c);
-                    xg2 = f2_fma(f.x, gF[q][c / 2], xg2);
-                    xg2 = f2_fma(f.y, gF[q][c / 2 + 1], xg2);
-                    vF[c / 2] = f2_fma(w2, gF[q][c / 2], vF[c / 2]);
-                    vF[c / 2 + 1] = f2_fma(w2, gF[q][c / 2 + 1], vF[c / 2 + 1]);
+                for (int c = 0; c < NF / 2; ++c) {
+                    xg2 = f2_fma(fj[c], gF[q][c], xg2);
+                    vF[c] = f2_fma(w2, gF[q][c], vF[c]);
                 }
-                const float xg = col.x * gC0[q] + col.y * gC1[q] + col.z * gC2[q] + g.z * gD[q] +
-                                 (NF > 0 ? f2_lo(xg2) + f2_hi(xg2) : 0.f);
-                const float dalpha = T[q] * xg - acc[q] * rom;
+                float xlo = 0.f, xhi = 0.f;
+                if (NF > 0) f2_split(xg2, xlo, xhi);
+                const float xg = fmaf(col.x, gC0[q], fmaf(col.y, gC1[q], fmaf(col.z, gC2[q], fmaf(g.z, gD[q], xlo + xhi))));
+                const float dal = use[q] ? T[q] * xg - acc[q] * rom : 0.f;
                 acc[q] = fmaf(w, xg, acc[q]);
-                float dq = 0.f;
-                if (raw < bp.alpha_max) {
-                    v[3] = fmaf(dalpha, G, v[3]);
-                    dq = dalpha * (-0.5f * alpha);
-                }
-                v[0] = fmaf(dq * (-2.f), cn.x * dx + cn.y * dy, v[0]);
-                v[1] = fmaf(dq * (-2.f), cn.y * dx + cn.z * dy, v[1]);
-                v[2] = fmaf(w, gD[q], v[2]);
-                v[4] = fmaf(dq, dx * dx, v[4]);
-                v[5] = fmaf(dq, 2.f * dx * dy, v[5]);
-                v[6] = fmaf(dq, dy * dy, v[6]);
-                v[8] = fmaf(w, gC0[q], v[8]);
-                v[9] = fmaf(w, gC1[q], v[9]);
-                v[10] = fmaf(w, gC2[q], v[10]);
+                const bool free = g.w * G[q] < bp.alpha_max;  // alpha not clamped
+                sop = fmaf(dal, free ? G[q] : 0.f, sop);
+                const float dq = free ? dal * (-0.5f * a) : 0.f;
+                sdq += dq;
+                const float dqy = dq * dy[q];
+                sdqy += dqy;
+                sdqyy = fmaf(dqy, dy[q], sdqyy);
+                sz = fmaf(w, gD[q], sz);
+                sc0 = fmaf(w, gC0[q], sc0);
+                sc1 = fmaf(w, gC1[q], sc1);
+                sc2 = fmaf(w, gC2[q], sc2);
             }
+            // record groups: du dv dz do | dca dcb dcc - | dr dg db - | df...
+            float4 v[NG];
+            v[0] = make_float4(-2.f * fmaf(cn.x * dx, sdq, cn.y * sdqy), -2.f * fmaf(cn.y * dx, sdq, cn.z * sdqy), sz,
+                               sop);
+            v[1] = make_float4(dx * dx * sdq, 2.f * dx * sdqy, sdqyy, 0.f);
+            v[2] = make_float4(sc0, sc1, sc2, 0.f);
 #pragma unroll
-            for (int c = 0; c < NF / 2; ++c) {
-                v[kG2Base + 2 * c] = f2_lo(vF[c]);
-                v[kG2Base + 2 * c + 1] = f2_hi(vF[c]);
+            for (int c = 0; c < NF / 4; ++c) {
+                float a0, a1, a2, a3;
+                f2_split(vF[2 * c], a0, a1);
+                f2_split(vF[2 * c + 1], a2, a3);
+                v[3 + c] = make_float4(a0, a1, a2, a3);
             }
-            if (__any_sync(0xffffffffu, any)) {
-                warp_transpose_reduce<RP>(v, lane);
-                float *rec = g2 + (size_t)S.gv[j] * STRIDE;
-                if (RP == 16) {
-                    int k = lane >> 1;
-                    if (!(lane & 1) && k != 7 && k != 11 && k < STRIDE) atomicAdd(rec + k, v[0]);
-                } else if (RP == 32) {
-                    int k = lane;
-                    if (k != 7 && k != 11 && k < STRIDE) atomicAdd(rec + k, v[0]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < RP / 32; ++e) {
-                        int k = (RP / 32) * lane + e;
-                        if (k != 7 && k != 11 && k < STRIDE) atomicAdd(rec + k, v[e]);
-                    }
-                }
-            }
+            warp_record_add<NG>(v, red[wid], lane, g2 + (size_t)S.gv[j] * STRIDE);
+        }
+        __syncthreads();  // every thread is done with this slot
+        if (issued < nb) {
+            umma::fence_async_smem();
+            issue(issued, nxt);
+            ++issued;
         }
     }
+    drain(mbar, b, issued, NS, err);
 }
 
 }  // namespace
@@ -470,12 +611,12 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const ups_images &out, cudaStream_t st,
-                                 const uint32_t *trunc, int *trunc_flag, const int *gate) {
+                                 const uint32_t *trunc, int *trunc_flag, const int *gate, int *err) {
     if (vt.total_tiles == 0) return cudaSuccess;
 #define UPS_FWD(NFV)                                                                                  \
     k_composite_fwd<NFV, blend_px_fwd(NFV)><<<vt.total_tiles, Px<blend_px_fwd(NFV)>::NT, 0, st>>>(              \
         vt, bp, N, per_view, ranges, ival, xyzo, conic, color, feat, out.color, out.depth, out.feat, out.T, \
-        out.n_contrib, trunc, trunc_flag, gate)
+        out.n_contrib, trunc, trunc_flag, gate, err)
     switch (n_feat) {
         case 0: UPS_FWD(0); break;
         case 16: UPS_FWD(16); break;
@@ -519,12 +660,12 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const float *T, const uint32_t *nc,
-                                 const ups_image_grads &dL, float *g2, cudaStream_t st) {
+                                 const ups_image_grads &dL, float *g2, cudaStream_t st, int *err) {
     if (vt.total_tiles == 0) return cudaSuccess;
 #define UPS_BWD(NFV)                                                                                \
     k_composite_bwd<NFV, blend_px_bwd(NFV)><<<vt.total_tiles, Px<blend_px_bwd(NFV)>::NT, 0, st>>>(            \
         vt, bp, N, per_view, ranges, ival, xyzo, conic, color, feat, T, nc, dL.color, dL.depth, dL.feat, \
-        dL.T, g2)
+        dL.T, g2, err)
     switch (n_feat) {
         case 0: UPS_BWD(0); break;
         case 16: UPS_BWD(16); break;

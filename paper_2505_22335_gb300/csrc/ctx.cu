@@ -37,7 +37,7 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
-                                 const int *gate = nullptr);
+                                 const int *gate = nullptr, int *err = nullptr);
 size_t anchor_scratch_bytes(size_t n, size_t P);
 cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t *motion, int n, const float *pos,
                           const float *feat, const float *offsets, const float *scaling, const float *lin, int F,
@@ -46,7 +46,7 @@ cudaError_t anchor_update(const DevView &cam, const float *depth, const uint8_t 
                           float *ooffsets, float *oscaling, float *olog, int *src_index, void *scratch,
                           uint64_t **summary_dev, cudaStream_t st, int *launches);
 size_t unc_scratch_floats(int max_patches);
-cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
+cudaError_t unc_view(int num_sms, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
                      int hp, const float *R, const float *w1, const float *b1, const float *w2, const float *b2,
                      float lambda, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
                      float *sigma, uint8_t *motion, float *scratch, int *launches);
@@ -54,9 +54,7 @@ cudaError_t ssim_set_window();
 cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, const float *weight, float *G, float g,
                         float *loss, float *dx, cudaStream_t st);
 size_t lift_scratch_floats(size_t max_hw, size_t max_np);
-cudaError_t lift_handle(void **handle);
-void lift_handle_destroy(void *handle);
-cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
+cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
                       const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
                       const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
                       float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches);
@@ -72,7 +70,7 @@ cudaError_t launch_composite_bwd(const ViewTable &vt, const BlendParams &bp, int
                                  int per_view, const uint2 *ranges, const uint32_t *ival,
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const float *T, const uint32_t *nc,
-                                 const ups_image_grads &dL, float *g2, cudaStream_t st);
+                                 const ups_image_grads &dL, float *g2, cudaStream_t st, int *err);
 cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const ups_anchors &anc,
                               const ups_mlp &mlp, const ups_gaussians &out, int op_tanh, int num_sms,
                               cudaStream_t st);
@@ -122,6 +120,8 @@ struct ups_ctx {
     ViewTable vt{};
     BlendParams bp{};
     int N = 0, per_view = 0;
+    int n_sets = 0;            // Gaussian sets the views read
+    bool shared_sets = false;  // some set is read by several views (gradients summed)
     size_t total_gv = 0;
     size_t n_inst = 0, n_visible = 0, n_pix = 0;
     int key_bits = 0, max_hw = 0;
@@ -141,7 +141,6 @@ struct ups_ctx {
     int *d_trunc_flag = nullptr;  // set by the forward blend: a capped list was too short
     DevBuf trunc;                 // per-tile bit: the list cap cut the tile's list
     bool capped = false;          // the last forward capped its tile lists
-    void *cublas = nullptr;       // cuBLAS handle of the feature lifting (created on first use)
     DevBuf lift_scr;              // feature-lifting scratch of one view
     DevBuf ssim_g;                // D-SSIM window-term maps of all colour planes
     DevBuf unc_scr;               // uncertainty-MLP patch scratch of one view
@@ -431,7 +430,6 @@ ups_status ups_destroy(ups_ctx *c) {
     if (c->h_anchor) cudaFreeHost(c->h_anchor);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_trunc_flag) cudaFree(c->d_trunc_flag);
-    lift_handle_destroy(c->cublas);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -480,8 +478,26 @@ ups_status ups_decode_anchors(ups_ctx *c, const ups_anchors *anc, const ups_mlp 
     return UPS_OK;
 }
 
+// (C++ linkage inside this extern "C" block: an internal entry point of the server)
+extern "C++" {
+namespace ups {
+// The render forward of ups_render_forward.  set_of_view (per_view sets only;
+// NULL: view v reads set v) names the Gaussian set each view reads, so that
+// several views (the pyramid levels of one tracking pose) can share one
+// decoded set; sets read by several views get their gradients summed.
+ups_status render_forward_sets(ups_ctx *c, const ups_gaussians *g, const ups_camera *cams, int n_views,
+                               const int *set_of_view, ups_images *out, ups_stream stream);
+}  // namespace ups
+}
+
 ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_camera *cams,
                               int n_views, ups_images *out, ups_stream stream) {
+    return render_forward_sets(c, g, cams, n_views, nullptr, out, stream);
+}
+
+extern "C++" ups_status ups::render_forward_sets(ups_ctx *c, const ups_gaussians *g, const ups_camera *cams,
+                                                 int n_views, const int *set_of_view, ups_images *out,
+                                                 ups_stream stream) {
     if (!c) return UPS_ERR_ARG;
     c->have_fwd = false;
     c->have_bwd = false;
@@ -490,8 +506,24 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     if (!out || !out->color || !out->depth || !out->T || !out->n_contrib ||
         (c->cfg.n_feat > 0 && !out->feat))
         return fail(c, UPS_ERR_ARG, "out: NULL image pointer");
+    if (set_of_view && !g->per_view) return fail(c, UPS_ERR_ARG, "a view-to-set map needs per_view sets");
     ViewTable &vt = c->vt;
     if ((s = build_views(c, cams, n_views, vt, c->n_pix, c->max_hw)) != UPS_OK) return s;
+    // which set each view reads; whether any set is read by more than one view
+    c->n_sets = g->per_view ? (set_of_view ? 0 : n_views) : 1;
+    c->shared_sets = !g->per_view;
+    for (int v = 0; v < n_views; ++v) {
+        const int sv = !g->per_view ? 0 : set_of_view ? set_of_view[v] : v;
+        if (sv < 0 || sv >= UPS_MAX_VIEWS) return fail(c, UPS_ERR_ARG, "set index out of range");
+        vt.v[v].set = sv;
+        vt.v[v].set_first = 1;
+        for (int u = 0; u < v; ++u)
+            if (vt.v[u].set == sv) {
+                vt.v[v].set_first = 0;
+                c->shared_sets = true;
+            }
+        if (set_of_view) c->n_sets = std::max(c->n_sets, sv + 1);
+    }
     const size_t total = (size_t)g->n * n_views;
     if (total >= (size_t)INT32_MAX) return fail(c, UPS_ERR_ARG, "n * n_views exceeds 2^31");
     if ((s = set_device(c)) != UPS_OK) return s;
@@ -553,7 +585,7 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     UPS_CUDA(c, cudaStreamSynchronize(st));
     if (c->h_total[1] != 0) {
         cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
-        return fail(c, UPS_ERR_TIMEOUT, "a tensor-core wait ran out of polls in an earlier decode");
+        return fail(c, UPS_ERR_TIMEOUT, "a bounded wait of a kernel ran out of polls in an earlier launch");
     }
     const uint64_t n_inst = *c->h_total;
     if (n_inst >= (uint64_t)UINT32_MAX) return fail(c, UPS_ERR_CAPACITY, "more than 2^32 tile instances");
@@ -603,7 +635,8 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
     UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
                                      c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                      reinterpret_cast<const float4 *>(g->color), g->feat, *out, st,
-                                     capped ? c->trunc.as<uint32_t>() : nullptr, capped ? c->d_trunc_flag : nullptr));
+                                     capped ? c->trunc.as<uint32_t>() : nullptr, capped ? c->d_trunc_flag : nullptr,
+                                     nullptr, c->d_err));
     stage_end(c, st, 1);
     if (capped) {
         // a pixel still open at the end of a capped list: the GPU rebuilds the
@@ -616,7 +649,7 @@ ups_status ups_render_forward(ups_ctx *c, const ups_gaussians *g, const ups_came
         UPS_CUDA(c, launch_composite_fwd(vt, c->bp, c->cfg.n_feat, c->N, c->per_view, c->ranges.as<uint2>(),
                                          c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                          reinterpret_cast<const float4 *>(g->color), g->feat, *out, st, nullptr,
-                                         nullptr, c->d_trunc_flag));
+                                         nullptr, c->d_trunc_flag, c->d_err));
         stage_end(c, st, 7);
     }
     c->g_in = *g;
@@ -658,7 +691,6 @@ ups_status ups_uncertainty_mlp(ups_ctx *c, const ups_lift_cfg *lcfg, const float
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    UPS_CUDA(c, lift_handle(&c->cublas));
     int max_np = 0;
     for (int v = 0; v < c->vt.n; ++v) {
         const DevView &cam = c->vt.v[v];
@@ -674,7 +706,7 @@ ups_status ups_uncertainty_mlp(ups_ctx *c, const ups_lift_cfg *lcfg, const float
         const DevView &cam = c->vt.v[v];
         const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
         const size_t P = (size_t)cam.pix_off;
-        UPS_CUDA(c, unc_view(c->cublas, st, cam.W, cam.H, lcfg->n_h, lcfg->patch, dino + grid_off, wp, hp, R + P,
+        UPS_CUDA(c, unc_view(c->num_sms, st, cam.W, cam.H, lcfg->n_h, lcfg->patch, dino + grid_off, wp, hp, R + P,
                              mlp->w1, mlp->b1, mlp->w2, mlp->b2, lambda, g, loss_dev, d_mlp ? d_mlp->w1 : nullptr,
                              d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr, d_mlp ? d_mlp->b2 : nullptr,
                              sigma ? sigma + P : nullptr, motion ? motion + P : nullptr, c->unc_scr.as<float>(),
@@ -803,7 +835,6 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    UPS_CUDA(c, lift_handle(&c->cublas));
     size_t max_np = 0;
     for (int v = 0; v < c->vt.n; ++v) {
         const DevView &cam = c->vt.v[v];
@@ -820,7 +851,7 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
         const DevView &cam = c->vt.v[v];
         const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
         const size_t P = (size_t)cam.pix_off;
-        UPS_CUDA(c, lift_view(c->cublas, st, cam.W, cam.H, nf, lcfg->n_h, lcfg->patch, feat + (size_t)nf * P,
+        UPS_CUDA(c, lift_view(c->num_sms, st, cam.W, cam.H, nf, lcfg->n_h, lcfg->patch, feat + (size_t)nf * P,
                               dino + grid_off, wp, hp, mlp->w1, mlp->b1, mlp->w2, mlp->b2, g,
                               weight ? weight + P : nullptr, loss_dev,
                               d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr,
@@ -852,7 +883,7 @@ ups_status ups_loss_weighted(ups_ctx *c, const ups_images *img, const ups_target
     UPS_CUDA(c, launch_loss(c->vt, nf, c->max_hw, lcfg->lambda_color, lcfg->lambda_depth,
                             lcfg->lambda_feat, lcfg->l2, inv_norm, *img, *tgt, *dL, loss_dev, st));
     if (g && lcfg->lambda_scale != 0.f) {
-        size_t sets = g->per_view ? (size_t)c->vt.n : 1;
+        size_t sets = g->per_view ? (size_t)c->n_sets : 1;
         size_t n = sets * (size_t)g->n;
         UPS_CUDA(c, launch_scale_mean(reinterpret_cast<const float4 *>(g->scale), n,
                                       (float)(lcfg->lambda_scale / (3.0 * (double)n)), loss_dev, st));
@@ -887,12 +918,12 @@ ups_status ups_render_backward(ups_ctx *c, const ups_image_grads *dL, unsigned m
     UPS_CUDA(c, launch_composite_bwd(c->vt, c->bp, nf, c->N, c->per_view, c->ranges.as<uint2>(),
                                      c->ival_sorted, c->xyzo.as<float4>(), c->conic.as<float4>(),
                                      reinterpret_cast<const float4 *>(c->g_in.color), c->g_in.feat,
-                                     c->img.T, c->img.n_contrib, *dL, c->g2.as<float>(), st));
+                                     c->img.T, c->img.n_contrib, *dL, c->g2.as<float>(), st, c->d_err));
     stage_end(c, st, 1);
     if (mask & UPS_GRAD_POSE)
         UPS_CUDA(c, cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * c->vt.n, st));
-    if ((mask & UPS_GRAD_GAUSS) && !c->per_view) {
-        size_t n = (size_t)c->N;
+    if ((mask & UPS_GRAD_GAUSS) && c->shared_sets) {
+        size_t n = (size_t)c->N * (size_t)c->n_sets;
         UPS_CUDA(c, cudaMemsetAsync(grad->mean_opacity, 0, n * sizeof(float4), st));
         UPS_CUDA(c, cudaMemsetAsync(grad->scale, 0, n * sizeof(float4), st));
         UPS_CUDA(c, cudaMemsetAsync(grad->quat, 0, n * sizeof(float4), st));
@@ -901,7 +932,7 @@ ups_status ups_render_backward(ups_ctx *c, const ups_image_grads *dL, unsigned m
     }
     if (mask & (UPS_GRAD_POSE | UPS_GRAD_GAUSS)) {
         stage_begin(c, "project_bwd", st);
-        UPS_CUDA(c, launch_project_bwd(c->vt, c->bp, c->N, c->per_view, (int)c->total_gv, nf, mask,
+        UPS_CUDA(c, launch_project_bwd(c->vt, c->bp, c->N, c->shared_sets ? 0 : 1, (int)c->total_gv, nf, mask,
                                        scale_grad, c->g_in, c->g2.as<float>(), grad, d_pose, st));
         stage_end(c, st, 1);
     }

@@ -26,8 +26,6 @@
 // small per-patch and weight-sized ones in FP32 (pedantic); one kernel per
 // cell of pixels sharing their four patches does the cosine, the loss, dL/dZ
 // and the per-patch sums.
-#include <cublas_v2.h>
-
 #include "common.cuh"
 
 namespace ups {
@@ -239,27 +237,6 @@ __global__ void k_axpy_dev(int n, const float *__restrict__ x, const float *__re
     if (i < n) y[i] = fmaf(x[i], *c, y[i]);
 }
 
-cudaError_t gemm_mode(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                      const float *A, int lda, const float *B, int ldb, float beta, float *Cm, int ldc,
-                      cublasComputeType_t mode) {
-    const float alpha = 1.f;
-    const cublasStatus_t s = cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta,
-                                          Cm, CUDA_R_32F, ldc, mode, CUBLAS_GEMM_DEFAULT);
-    return s == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
-}
-
-// pixel-sized products: TF32 tensor cores
-cudaError_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const float *A,
-                 int lda, const float *B, int ldb, float beta, float *Cm, int ldc) {
-    return gemm_mode(h, ta, tb, m, n, k, A, lda, B, ldb, beta, Cm, ldc, CUBLAS_COMPUTE_32F_FAST_TF32);
-}
-
-// per-patch and weight-sized products: plain FP32
-cudaError_t sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const float *A,
-                  int lda, const float *B, int ldb, float beta, float *Cm, int ldc) {
-    return gemm_mode(h, ta, tb, m, n, k, A, lda, B, ldb, beta, Cm, ldc, CUBLAS_COMPUTE_32F_PEDANTIC);
-}
-
 size_t round64(size_t n) { return (n + 63) & ~size_t(63); }
 
 // scratch of one view, in floats
@@ -305,29 +282,15 @@ int lift_cell_pixels(int patch) {
     return m * m;
 }
 
-cudaError_t lift_handle(void **handle) {
-    if (*handle) return cudaSuccess;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    *handle = h;
-    return cudaSuccess;
-}
-
-void lift_handle_destroy(void *handle) {
-    if (handle) cublasDestroy(static_cast<cublasHandle_t>(handle));
-}
-
 // One view: forward, loss and backward.  feat / d_feat: the view's planes
 // [nf][HW]; grid: its patch grid [hp][wp][nh]; weight: its per-pixel weights
 // (null: 1); scratch: lift_scratch_floats(HW, hp * wp) floats.
 // d_w1 [128][nf], d_b1 [128], d_w2 [nh][128], d_b2 [nh] and d_feat are
 // accumulated (may be null: that gradient is skipped).
-cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
+cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
                       const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
                       const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
                       float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches) {
-    cublasHandle_t h = static_cast<cublasHandle_t>(handle);
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const int HW = W * H, np = wp * hp;
     const int NH = kLiftHidden;
     const LiftLayout L = lift_layout((size_t)HW, (size_t)np);
@@ -341,17 +304,17 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
     const unsigned gx = (unsigned)((HW + 255) / 256);
     cudaError_t e;
     // per patch and weight-sized: E = G W2 ([np][128]), s = G b2, M = W2^T W2, u = W2^T b2, beta = |b2|^2
-    if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, NH, np, nh, w2, NH, grid, nh, 0.f, E, NH)) != cudaSuccess) return e;
-    if ((e = sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, np, 1, nh, grid, nh, b2, nh, 0.f, sv, np)) != cudaSuccess) return e;
-    if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, NH, NH, nh, w2, NH, w2, NH, 0.f, M, NH)) != cudaSuccess) return e;
-    if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, NH, 1, nh, w2, NH, b2, nh, 0.f, u, NH)) != cudaSuccess) return e;
-    if ((e = sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, 1, 1, nh, b2, nh, b2, nh, 0.f, beta, 1)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, false, false, NH, np, nh, 1.f, w2, NH, grid, nh, 0.f, E, NH, num_sms, launches)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, true, false, np, 1, nh, 1.f, grid, nh, b2, nh, 0.f, sv, np, num_sms, launches)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, false, true, NH, NH, nh, 1.f, w2, NH, w2, NH, 0.f, M, NH, num_sms, launches)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, false, false, NH, 1, nh, 1.f, w2, NH, b2, nh, 0.f, u, NH, num_sms, launches)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, true, false, 1, 1, nh, 1.f, b2, nh, b2, nh, 0.f, beta, 1, num_sms, launches)) != cudaSuccess) return e;
     k_cell_gram<<<(unsigned)((np + 7) / 8), blk, 0, st>>>(grid, wp, hp, nh, gram);
     if ((e = cudaMemsetAsync(D, 0, (L.sb + 1 - L.D) * sizeof(float), st)) != cudaSuccess) return e;
     // H = relu(F~ W1^T + b1); MH = H M
-    if ((e = gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, HW, NH, nf, feat, HW, w1, nf, 0.f, Hm, HW)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, false, false, HW, NH, nf, 1.f, feat, HW, w1, nf, 0.f, Hm, HW, num_sms, launches)) != cudaSuccess) return e;
     k_bias_relu<<<dim3(gx, NH), blk, 0, st>>>(Hm, b1, (size_t)HW);
-    if ((e = gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, HW, NH, NH, Hm, HW, M, NH, 0.f, MH, HW)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, false, false, HW, NH, NH, 1.f, Hm, HW, M, NH, 0.f, MH, HW, num_sms, launches)) != cudaSuccess) return e;
     const int npx_max = lift_cell_pixels(patch);
     k_lift_cells<<<dim3(wp, hp), kCellThreads, (size_t)4 * npx_max * sizeof(float), st>>>(
         W, H, wp, hp, patch, npx_max, Hm, MH, bH, E, sv, u, beta, gram, weight, g, loss, D, alpha, sb);
@@ -365,19 +328,19 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
     }
     if (d_w2) {
         // dW2 ([nh][128] row-major = column-major 128 x nh) += D^T-side: D G, Gb W2, hb b2^T
-        if ((e = gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, NH, NH, HW, bH, HW, Hm, HW, 0.f, Gb, NH)) != cudaSuccess) return e;
-        if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, NH, nh, np, D, NH, grid, nh, 1.f, d_w2, NH)) != cudaSuccess)
+        if ((e = gemm_f32(st, true, false, NH, NH, HW, 1.f, bH, HW, Hm, HW, 0.f, Gb, NH, num_sms, launches)) != cudaSuccess) return e;
+        if ((e = gemm_f32(st, false, true, NH, nh, np, 1.f, D, NH, grid, nh, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
             return e;
-        if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, NH, nh, NH, Gb, NH, w2, NH, 1.f, d_w2, NH)) != cudaSuccess)
+        if ((e = gemm_f32(st, false, false, NH, nh, NH, 1.f, Gb, NH, w2, NH, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
             return e;
-        if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, NH, nh, 1, hb, NH, b2, nh, 1.f, d_w2, NH)) != cudaSuccess)
+        if ((e = gemm_f32(st, false, true, NH, nh, 1, 1.f, hb, NH, b2, nh, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
             return e;
     }
     if (d_b2) {
         // db2 += G^T alpha + W2 hb + b2 sum_p b_p
-        if ((e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nh, 1, np, grid, nh, alpha, np, 1.f, d_b2, nh)) != cudaSuccess)
+        if ((e = gemm_f32(st, false, false, nh, 1, np, 1.f, grid, nh, alpha, np, 1.f, d_b2, nh, num_sms, launches)) != cudaSuccess)
             return e;
-        if ((e = sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nh, 1, NH, w2, NH, hb, NH, 1.f, d_b2, nh)) != cudaSuccess)
+        if ((e = gemm_f32(st, true, false, nh, 1, NH, 1.f, w2, NH, hb, NH, 1.f, d_b2, nh, num_sms, launches)) != cudaSuccess)
             return e;
         k_axpy_dev<<<(unsigned)((nh + 255) / 256), blk, 0, st>>>(nh, b2, sb, d_b2);
         ++*launches;
@@ -387,10 +350,10 @@ cudaError_t lift_view(void *handle, cudaStream_t st, int W, int H, int nf, int n
         ++*launches;
     }
     // dW1 += F~^T dZ ([nf x 128] column-major = [128][nf] row-major)
-    if (d_w1 && (e = gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nf, NH, HW, feat, HW, dZ, HW, 1.f, d_w1, nf)) != cudaSuccess)
+    if (d_w1 && (e = gemm_f32(st, true, false, nf, NH, HW, 1.f, feat, HW, dZ, HW, 1.f, d_w1, nf, num_sms, launches)) != cudaSuccess)
         return e;
     // dF~ += dZ W1
-    if (d_feat && (e = gemm(h, CUBLAS_OP_N, CUBLAS_OP_T, HW, nf, NH, dZ, HW, w1, nf, 1.f, d_feat, HW)) != cudaSuccess)
+    if (d_feat && (e = gemm_f32(st, false, true, HW, nf, NH, 1.f, dZ, HW, w1, nf, 1.f, d_feat, HW, num_sms, launches)) != cudaSuccess)
         return e;
     return cudaGetLastError();
 }

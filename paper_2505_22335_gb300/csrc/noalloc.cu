@@ -48,7 +48,7 @@ cudaError_t launch_composite_fwd(const ViewTable &vt, const BlendParams &bp, int
                                  const float4 *xyzo, const float4 *conic, const float4 *color,
                                  const float *feat, const ups_images &out, cudaStream_t st,
                                  const uint32_t *trunc = nullptr, int *trunc_flag = nullptr,
-                                 const int *gate = nullptr);
+                                 const int *gate = nullptr, int *err = nullptr);
 cudaError_t radix_sort_u32_fixed(uint32_t **key_io, uint32_t **key_alt, uint32_t **val_io,
                                  uint32_t **val_alt, size_t n, int end_bit, void *scratch,
                                  size_t scratch_bytes, cudaStream_t st);
@@ -182,6 +182,10 @@ extern "C" ups_status ups_render_forward_static(const ups_config *cfg, const ups
     vt.total_tiles = tiles;
     const BlendParams bp{cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->near_z};
     const int N = g->n, per_view = g->per_view ? 1 : 0;
+    for (int v = 0; v < n_views; ++v) {
+        vt.v[v].set = per_view ? v : 0;
+        vt.v[v].set_first = per_view || v == 0;
+    }
 
     unsigned char *base = nullptr;
     ups_status s = scratch_address(&base);

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(256) k_project(
     int gv = blockIdx.x * blockDim.x + threadIdx.x;
     if (gv >= total) return;
     int v = gv / N;
-    int gs = per_view ? gv : gv - v * N;
     const DevView &cam = vt.v[v];
+    int gs = cam.set * N + (gv - v * N);
     float4 m = mean_op[gs];
     Geo G;
     bool ok = camera_point(cam, bp, m, G.p);
@@ -323,7 +323,7 @@ __global__ void k_ranges(const uint32_t *__restrict__ ikey, uint32_t n, uint2 *_
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_project_bwd(
-    ViewTable vt, BlendParams bp, int N, int per_view, int total, int n_feat, unsigned mask,
+    ViewTable vt, BlendParams bp, int N, int direct, int total, int n_feat, unsigned mask,
     float scale_grad, const float4 *__restrict__ mean_op, const float4 *__restrict__ scale,
     const float4 *__restrict__ quat, const float *__restrict__ g2, float4 *__restrict__ d_mean_op,
     float4 *__restrict__ d_scale, float4 *__restrict__ d_quat, float4 *__restrict__ d_color,
@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     int gv = blockIdx.x * blockDim.x + threadIdx.x;
     bool in = gv < total;
     int v = in ? gv / N : vt.n - 1;
-    int gs = per_view ? gv : gv - v * N;
+    // direct: every set is read by one view, so its gradient is written, not
+    // accumulated (else the caller zeroed the gradient and views add into it)
+    int gs = vt.v[v].set * N + (gv - v * N);
     float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (in) {
         const DevView &cam = vt.v[v];
@@ -455,10 +457,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(
             }
         }
         if (mask & UPS_GRAD_GAUSS) {
-            bool add_reg = per_view || v == 0;
-            float sreg = add_reg ? scale_grad : 0.f;
+            // the mean-scale term enters each set's scale gradient once
+            float sreg = vt.v[v].set_first ? scale_grad : 0.f;
             float4 rc = *reinterpret_cast<const float4 *>(r + 8);  // dr dg db -
-            if (per_view) {
+            if (direct) {
                 d_mean_op[gs] = make_float4(dmu[0], dmu[1], dmu[2], dop);
                 d_scale[gs] = make_float4(ds[0] + sreg, ds[1] + sreg, ds[2] + sreg, 0.f);
                 d_quat[gs] = make_float4(dq[0], dq[1], dq[2], dq[3]);

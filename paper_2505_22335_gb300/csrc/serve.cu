@@ -24,6 +24,8 @@ namespace ups {
 ups_status loss_views(ups_ctx *c, const ups_images *img, const ups_targets *tgt,
                       const ups_loss_cfg *lcfg, int v0, int v1, float *loss_dev, ups_images *dL,
                       cudaStream_t st);
+ups_status render_forward_sets(ups_ctx *c, const ups_gaussians *g, const ups_camera *cams, int n_views,
+                               const int *set_of_view, ups_images *out, ups_stream stream);
 }
 
 using namespace ups;
@@ -151,20 +153,34 @@ size_t footprint(const ups_config &c, size_t n_gauss, int nv, size_t pixels) {
     return (size_t)nv * n_gauss * per_gv + pixels * (8 * (5 + (size_t)c.n_feat) + 8);
 }
 
-// one batched step; returns UPS_OK when queued on the stream
+// one batched step; returns UPS_OK when queued on the stream.  The decode
+// (Eq. 8-9) depends on a view only through its camera centre and time, so the
+// pyramid levels of a tracking request share one decoded set: the batch
+// decodes one set per tracking request and one per mapping keyframe, and the
+// forward maps each rendered view to its set.
 ups_status run_batch(ups_server *s, Slot &sl, std::vector<Req *> &batch, std::string &msg) {
-    std::vector<ups_camera> cams;
-    std::vector<int> v0;
+    std::vector<ups_camera> cams, dcams;  // rendered views; decoded sets
+    std::vector<int> v0, s0, set_of_view;
     size_t P = 0;
     for (Req *r : batch) {
         v0.push_back((int)cams.size());
+        s0.push_back((int)dcams.size());
         cams.insert(cams.end(), r->cams.begin(), r->cams.end());
+        if (r->r.kind == UPS_REQ_TRACK) {
+            dcams.push_back(r->cams[0]);
+            for (int l = 0; l < r->nv; ++l) set_of_view.push_back(s0.back());
+        } else {
+            for (int k = 0; k < r->nv; ++k) {
+                dcams.push_back(r->cams[k]);
+                set_of_view.push_back(s0.back() + k);
+            }
+        }
         P += r->pixels;
     }
-    const int V = (int)cams.size();
+    const int V = (int)cams.size(), S = (int)dcams.size();
     const int NF = s->cfg.n_feat;
     const size_t N = (size_t)s->anc.n * s->cfg.k;
-    const size_t GV = (size_t)V * N;
+    const size_t GV = (size_t)S * N;
     cudaError_t e = cudaSuccess;
     const size_t rec[5] = {16, 16, 16, 16, 4 * (size_t)NF};
     for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
@@ -188,8 +204,8 @@ ups_status run_batch(ups_server *s, Slot &sl, std::vector<Req *> &batch, std::st
     ups_images dl{sl.dl[0].as<float>(), sl.dl[1].as<float>(), NF ? sl.dl[2].as<float>() : nullptr,
                   nullptr, nullptr};
     float *pose = sl.pose.as<float>();
-    ups_status st = ups_decode_anchors(sl.ctx, &s->anc, &s->mlp, cams.data(), V, &G, sl.st);
-    if (st == UPS_OK) st = ups_render_forward(sl.ctx, &G, cams.data(), V, &img, sl.st);
+    ups_status st = ups_decode_anchors(sl.ctx, &s->anc, &s->mlp, dcams.data(), S, &G, sl.st);
+    if (st == UPS_OK) st = render_forward_sets(sl.ctx, &G, cams.data(), V, set_of_view.data(), &img, sl.st);
     for (size_t i = 0; i < batch.size() && st == UPS_OK; ++i)
         st = loss_views(sl.ctx, &img, &batch[i]->r.targets, &s->scfg.loss, v0[i], v0[i] + batch[i]->nv,
                         batch[i]->r.loss, &dl, sl.st);
@@ -199,7 +215,8 @@ ups_status run_batch(ups_server *s, Slot &sl, std::vector<Req *> &batch, std::st
     }
     for (size_t i = 0; i < batch.size() && st == UPS_OK; ++i) {
         Req *r = batch[i];
-        const size_t off = (size_t)v0[i] * N;
+        const size_t off = (size_t)s0[i] * N;
+        const int n_sets = r->r.kind == UPS_REQ_TRACK ? 1 : r->nv;
         ups_gaussians dGr{(int)N, 1, dG.mean_opacity + 4 * off, dG.scale + 4 * off, dG.quat + 4 * off,
                           dG.color + 4 * off, NF ? dG.feat + (size_t)NF * off : nullptr};
         unsigned mask = UPS_GRAD_POSE;
@@ -207,7 +224,9 @@ ups_status run_batch(ups_server *s, Slot &sl, std::vector<Req *> &batch, std::st
         if (r->r.kind == UPS_REQ_MAP && r->r.d_anchors.pos) mask |= UPS_GRAD_ANCHOR;
         ups_anchors da = r->r.d_anchors;
         da.n = s->anc.n;
-        st = ups_decode_backward(sl.ctx, &s->anc, &s->mlp, cams.data() + v0[i], r->nv, &dGr, mask,
+        // the camera-centre part of the pose gradient goes to the request's
+        // first view (a tracking request's levels are summed below)
+        st = ups_decode_backward(sl.ctx, &s->anc, &s->mlp, dcams.data() + s0[i], n_sets, &dGr, mask,
                                  &r->r.d_mlp, &da, pose + 6 * v0[i], sl.st);
         if (st != UPS_OK) break;
         if (r->r.kind == UPS_REQ_TRACK) {

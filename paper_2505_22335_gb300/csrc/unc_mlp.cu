@@ -19,8 +19,6 @@
 // patches, one warp per pixel at a time, each lane owning 4 of the 128 hidden
 // units; the per-lane sums (dW2, db1, D of the four corners) are reduced over
 // the CTA and added once.
-#include <cublas_v2.h>
-
 #include <algorithm>
 
 #include "common.cuh"
@@ -153,14 +151,6 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
     }
 }
 
-cudaError_t sgemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const float *A,
-                  int lda, const float *B, int ldb, float beta, float *Cm, int ldc) {
-    const float alpha = 1.f;
-    const cublasStatus_t s = cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta,
-                                          Cm, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT);
-    return s == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
-}
-
 }  // namespace
 
 size_t unc_scratch_floats(int max_patches) { return (size_t)2 * max_patches * kUH; }
@@ -168,25 +158,23 @@ size_t unc_scratch_floats(int max_patches) { return (size_t)2 * max_patches * kU
 // One view: sigma, motion mask, loss and the F_u gradients (accumulated; any
 // gradient pointer may be null).  grid: the view's patch grid [hp][wp][nh];
 // R, sigma, motion: the view's pixels; scratch: unc_scratch_floats(hp * wp).
-cudaError_t unc_view(void *handle, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
+cudaError_t unc_view(int num_sms, cudaStream_t st, int W, int H, int nh, int patch, const float *grid, int wp,
                      int hp, const float *R, const float *w1, const float *b1, const float *w2, const float *b2,
                      float lambda, float g, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
                      float *sigma, uint8_t *motion, float *scratch, int *launches) {
-    cublasHandle_t h = static_cast<cublasHandle_t>(handle);
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const int np = wp * hp;
     float *Zp = scratch;                     // [np][128]  W1 g of every patch
     float *D = scratch + (size_t)np * kUH;   // [np][128]  interpolation-weighted dL/dh per patch
     cudaError_t e;
     // Zp (column-major [128 x np]) = W1 [128 x nh] G^T
-    if ((e = sgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, kUH, np, nh, w1, nh, grid, nh, 0.f, Zp, kUH)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, true, false, kUH, np, nh, 1.f, w1, nh, grid, nh, 0.f, Zp, kUH, num_sms, launches)) != cudaSuccess) return e;
     if (d_w1 && (e = cudaMemsetAsync(D, 0, (size_t)np * kUH * sizeof(float), st)) != cudaSuccess) return e;
     k_unc_cells<<<dim3(wp, hp), 32 * kUWarps, 0, st>>>(W, H, wp, hp, patch, Zp, b1, w2, b2, R, lambda, g, loss, sigma,
                                                        motion, d_b1, d_w2, d_b2, d_w1 ? D : nullptr);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // dW1 (column-major [nh x 128], i.e. [128][nh] row-major) += G^T D
-    if (d_w1 && (e = sgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, nh, kUH, np, grid, nh, D, kUH, 1.f, d_w1, nh)) != cudaSuccess)
+    if (d_w1 && (e = gemm_f32(st, false, true, nh, kUH, np, 1.f, grid, nh, D, kUH, 1.f, d_w1, nh, num_sms, launches)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }
