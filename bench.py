@@ -235,7 +235,12 @@ ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
 # one ncu capture of that kernel on the named workload: (bytes, capture date, SHA-256 prefix of
 # the kernel's source file when it was captured).  Reported as the roofline's `traffic` only while
 # the source file still has that hash; any later change of the kernel makes it null (stale).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # full ncu captures of one launch on the 2-view profiling workload (1M Gaussians, 2 x 640x480), scaled to the
+    # 8-view launch by the list entries the tiles read (384,532 -> 1,618,003; images scale alike, 4x the pixels)
+    ("composite_bwd", DEFAULT_WORKLOAD): (303.8e6, "2026-12-04 (2-view capture x 4.21)", "b26ed4d0cd026bfb"),
+    ("composite_fwd", DEFAULT_WORKLOAD): (107.6e6, "2026-12-04 (2-view capture x 4.21)", "b26ed4d0cd026bfb"),
+}
 STAGE_SOURCE = {"composite_fwd": "composite.cu", "composite_bwd": "composite.cu", "decode_bwd_rows": "decode.cu",
                 "decode_fwd": "decode.cu", "decode_wgrad": "wgrad_tc.cu", "project_bwd": "project.cu"}
 

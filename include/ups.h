@@ -81,10 +81,14 @@ typedef struct {
                          paper cites for Eq. 8-9) instead of sigmoid(y); the
                          projection's cull of o < alpha_min then drops every
                          Gaussian with o <= 0 (alpha_min > 0).  0 (default): sigmoid. */
+    int decode_bwd_bf16; /* with decode_bf16: 1 also runs the decode backward's per-row
+                         data path with BF16 tensor-core operands; 0 (default) runs it
+                         in FP32 on the CUDA cores, which is faster at these sizes and
+                         keeps the backward in FP32 (the decode forward stays BF16) */
 } ups_config;
 
 /* Fills the defaults listed above (n_feat 16, k 10, feat_dim 32, hidden 32,
- * list_cap 1024, opacity_tanh 0). */
+ * list_cap 1024, opacity_tanh 0, decode_bwd_bf16 0). */
 void ups_config_default(ups_config *cfg);
 
 /* Pinhole camera of one view (Sec. 3.1); t_norm feeds the temporal encoding

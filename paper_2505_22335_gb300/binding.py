@@ -28,7 +28,7 @@ class Config(C.Structure):
     _fields_ = [("alpha_min", _f), ("alpha_max", _f), ("t_min", _f), ("dilation", _f),
                 ("near_z", _f), ("guard", _f), ("n_feat", _i), ("k", _i), ("feat_dim", _i),
                 ("hidden", _i), ("decode_bf16", _i), ("check_finite", _i), ("list_cap", _i),
-                ("opacity_tanh", _i)]
+                ("opacity_tanh", _i), ("decode_bwd_bf16", _i)]
 
 
 class Camera(C.Structure):

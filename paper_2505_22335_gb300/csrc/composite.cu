@@ -4,7 +4,7 @@
 //
 // One CTA per 16x16 image tile, PX pixels per thread (forward 2; backward 4
 // for up to 16 feature channels, 2 for 32: registers).  The tile's
-// depth-ordered Gaussian list is staged in shared memory in batches of kStage
+// depth-ordered Gaussian list is staged in shared memory in batches of list
 // entries by the bulk-copy (TMA) engine: one cp.async.bulk per attribute
 // record of an entry, completed on the batch's mbarrier, in a ring of stages
 // so that the next batches load while one is blended.  A CTA stops when every
@@ -30,17 +30,29 @@ namespace ups {
 
 namespace {
 
-constexpr int kStage = 32;       // list entries per staged batch
 constexpr int kWaitPolls = 1 << 22;
 
-// one staged batch: attribute records of kStage list entries
-template <int NF>
+// Batch sizes and ring depths (compile-time tuning; a batch has at most one
+// entry per thread): the forward stops early, so it takes few large batches;
+// the backward walks whole prefixes.
+#ifndef UPS_FWD_BATCH
+#define UPS_FWD_BATCH 128
+#endif
+#ifndef UPS_FWD_STAGES
+#define UPS_FWD_STAGES 2
+#endif
+#ifndef UPS_BWD_BATCH
+#define UPS_BWD_BATCH 64
+#endif
+
+// one staged batch: attribute records of KB list entries
+template <int NF, int KB>
 struct Stage {
-    float4 xyzo[kStage];
-    float4 conic[kStage];
-    float4 color[kStage];
-    float feat[kStage][NF > 0 ? NF : 4];  // 16-byte rows
-    uint32_t gv[kStage];
+    float4 xyzo[KB];
+    float4 conic[KB];
+    float4 color[KB];
+    float feat[KB][NF > 0 ? NF : 4];  // 16-byte rows
+    uint32_t gv[KB];
 };
 
 template <int NF> struct StageBytes { static constexpr uint32_t value = 48u + 4u * NF; };
@@ -59,8 +71,8 @@ __device__ __forceinline__ void mbar_expect(uint64_t *mbar, uint32_t bytes) {
 
 // Entry t of a batch: its Gaussian-view id to shared memory, its four
 // attribute records by bulk copies completing on mbar.
-template <int NF>
-__device__ __forceinline__ void stage_entry(Stage<NF> &S, int t, uint32_t gv, int gs, const float4 *__restrict__ xyzo,
+template <int NF, int KB>
+__device__ __forceinline__ void stage_entry(Stage<NF, KB> &S, int t, uint32_t gv, int gs, const float4 *__restrict__ xyzo,
                                             const float4 *__restrict__ conic, const float4 *__restrict__ color,
                                             const float *__restrict__ feat, uint64_t *mbar) {
     S.gv[t] = gv;
@@ -103,7 +115,10 @@ __device__ __forceinline__ TileP<PX> tilep(const ViewTable &vt) {
 
 // pixels per thread: forward 2; backward 4 up to 16 feature channels (the
 // per-Gaussian warp reduction is shared by more pixels), 2 for 32 (registers)
-__host__ __device__ constexpr int blend_px_fwd(int nf) { return 2; }
+#ifndef UPS_FWD_PX
+#define UPS_FWD_PX 2
+#endif
+__host__ __device__ constexpr int blend_px_fwd(int nf) { return UPS_FWD_PX; }
 __host__ __device__ constexpr int blend_px_bwd(int nf) { return nf <= 16 ? 4 : 2; }
 
 // exponent coefficients of a staged Gaussian for a thread's pixel column
@@ -122,7 +137,8 @@ __device__ __forceinline__ void drain(uint64_t *mbar, int consumed, int issued, 
         if (!umma::mbar_wait(&mbar[b % ns], (uint32_t)((b / ns) & 1), kWaitPolls) && err) *err = 1;
 }
 
-constexpr int kFwdStages = 4;
+constexpr int kFwdStages = UPS_FWD_STAGES;
+constexpr int kFwdBatch = UPS_FWD_BATCH;
 
 template <int NF, int PX>
 __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
@@ -136,29 +152,29 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     // gate: when non-null, blend only if *gate != 0 (a pass enqueued ahead of
     // the GPU's decision to run it)
     if (gate && *gate == 0) return;
-    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS, NS = kFwdStages;
-    static_assert(NT >= kStage, "one thread per staged entry");
-    __shared__ __align__(128) Stage<NF> ring[NS];
+    constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS, NS = kFwdStages, KB = kFwdBatch;
+    static_assert(NT >= KB, "one thread per staged entry");
+    __shared__ __align__(128) Stage<NF, KB> ring[NS];
     __shared__ __align__(8) uint64_t mbar[NS];
     const TileP<PX> tc = tilep<PX>(vt);
     const uint2 rg = ranges[blockIdx.x];
     const int n_list = (int)(rg.y - rg.x);
-    const int nb = (n_list + kStage - 1) / kStage;
+    const int nb = (n_list + KB - 1) / KB;
     const int set_base = (tc.v - tc.cam->set) * N;  // gv - set_base: attribute index
     const int tid = threadIdx.x;
     if (tid == 0)
         for (int s = 0; s < NS; ++s) umma::mbar_init(&mbar[s], 1);
     __syncthreads();
-    // a thread's entry of batch b (t < kStage)
+    // a thread's entry of batch b (t < KB)
     auto issue = [&](int b, uint32_t gv) {
-        const int cnt = min(kStage, n_list - b * kStage);
-        Stage<NF> &S = ring[b % NS];
+        const int cnt = min(KB, n_list - b * KB);
+        Stage<NF, KB> &S = ring[b % NS];
         if (tid == 0) mbar_expect(&mbar[b % NS], (uint32_t)cnt * StageBytes<NF>::value);
-        if (tid < cnt) stage_entry<NF>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
+        if (tid < cnt) stage_entry<NF, KB>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
     };
     auto entry_gv = [&](int b) -> uint32_t {
-        const int i = b * kStage + tid;
-        return (tid < kStage && i < n_list) ? ival[rg.x + i] : 0u;
+        const int i = b * KB + tid;
+        return (tid < KB && i < n_list) ? ival[rg.x + i] : 0u;
     };
     int issued = min(NS, nb);
     {
@@ -202,14 +218,14 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
             if (err && tid == 0) *err = 1;
             break;
         }
-        const Stage<NF> &S = ring[b % NS];
-        const int n = min(kStage, n_list - b * kStage);
+        const Stage<NF, KB> &S = ring[b % NS];
+        const int n = min(KB, n_list - b * KB);
         for (int j = 0; j < n; ++j) {
             if (__all_sync(0xffffffffu, all_done())) break;
             const float4 g = S.xyzo[j];
             const float4 cn = S.conic[j];
             const Expo ex = expo(cn, fx - g.x);
-            const uint32_t pos = (uint32_t)(b * kStage + j + 1);
+            const uint32_t pos = (uint32_t)(b * KB + j + 1);
             // alpha and the stopping test of every pixel first (independent
             // chains), then the weighted sums only where a pixel blends
             float alpha[PX], Tn[PX];
@@ -424,10 +440,11 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
     const float *__restrict__ dD, const float *__restrict__ dF, const float *__restrict__ dT,
     float *__restrict__ g2, int *__restrict__ err) {
     constexpr int NT = Px<PX>::NT, RS = Px<PX>::RS, NW = NT / 32, NS = kBwdStages;
+    constexpr int KB = NF > 16 ? 32 : UPS_BWD_BATCH;
     constexpr int STRIDE = kG2Base + NF;  // record floats, a multiple of 4
     constexpr int NG = STRIDE / 4;
-    static_assert(NT >= kStage, "one thread per staged entry");
-    __shared__ __align__(128) Stage<NF> ring[NS];
+    static_assert(NT >= KB, "one thread per staged entry");
+    __shared__ __align__(128) Stage<NF, KB> ring[NS];
     __shared__ __align__(8) uint64_t mbar[NS];
     __shared__ __align__(16) float red[NW][32][kRedStride];
     __shared__ uint32_t s_max[NW];
@@ -475,19 +492,19 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
     int max_nc = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) max_nc = max(max_nc, (int)s_max[w]);
-    // batch b holds list positions [max(0, max_nc - (b + 1) kStage), max_nc - b kStage), back to front
-    const int nb = (max_nc + kStage - 1) / kStage;
+    // batch b holds list positions [max(0, max_nc - (b + 1) KB), max_nc - b KB), back to front
+    const int nb = (max_nc + KB - 1) / KB;
     const int set_base = (tc.v - tc.cam->set) * N;  // gv - set_base: attribute index
-    auto lo_of = [&](int b) { return max(0, max_nc - (b + 1) * kStage); };
+    auto lo_of = [&](int b) { return max(0, max_nc - (b + 1) * KB); };
     auto entry_gv = [&](int b) -> uint32_t {
         const int lo = lo_of(b), i = lo + tid;
-        return (tid < kStage && i < max_nc - b * kStage) ? ival[rg.x + i] : 0u;
+        return (tid < KB && i < max_nc - b * KB) ? ival[rg.x + i] : 0u;
     };
     auto issue = [&](int b, uint32_t gv) {
-        const int lo = lo_of(b), cnt = max_nc - b * kStage - lo;
-        Stage<NF> &S = ring[b % NS];
+        const int lo = lo_of(b), cnt = max_nc - b * KB - lo;
+        Stage<NF, KB> &S = ring[b % NS];
         if (tid == 0) mbar_expect(&mbar[b % NS], (uint32_t)cnt * StageBytes<NF>::value);
-        if (tid < cnt) stage_entry<NF>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
+        if (tid < cnt) stage_entry<NF, KB>(S, tid, gv, (int)gv - set_base, xyzo, conic, color, feat, &mbar[b % NS]);
     };
     int issued = min(NS, nb);
     {
@@ -509,8 +526,8 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
             if (err && tid == 0) *err = 1;
             break;  // the drain below waits for this batch again
         }
-        const Stage<NF> &S = ring[b % NS];
-        const int lo = lo_of(b), hi = max_nc - b * kStage;
+        const Stage<NF, KB> &S = ring[b % NS];
+        const int lo = lo_of(b), hi = max_nc - b * KB;
         // warps whose pixels all stop earlier skip the tail of the batch
         const int jstart = min(hi, (int)warp_nc) - lo - 1;
         for (int j = jstart; j >= 0; --j) {

@@ -356,6 +356,7 @@ void ups_config_default(ups_config *cfg) {
     cfg->check_finite = 0;
     cfg->list_cap = 1024;
     cfg->opacity_tanh = 0;
+    cfg->decode_bwd_bf16 = 0;
 }
 
 void ups_anchor_cfg_default(ups_anchor_cfg *cfg) {
@@ -394,6 +395,8 @@ ups_status ups_create(const ups_config *cfg, int device, ups_ctx **out) {
         return fail(nullptr, UPS_ERR_ARG, "threshold out of range");
     if (c.list_cap > kMaxListCap) return fail(nullptr, UPS_ERR_ARG, "list_cap must be at most 32767");
     if (c.opacity_tanh != 0 && c.opacity_tanh != 1) return fail(nullptr, UPS_ERR_ARG, "opacity_tanh must be 0 or 1");
+    if (c.decode_bwd_bf16 != 0 && c.decode_bwd_bf16 != 1)
+        return fail(nullptr, UPS_ERR_ARG, "decode_bwd_bf16 must be 0 or 1");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || device < 0 || device >= ndev)
@@ -979,7 +982,8 @@ ups_status ups_decode_backward(ups_ctx *c, const ups_anchors *anc, const ups_mlp
                                },
                                c};
     UPS_CUDA(c, launch_decode_bwd(vt, anc->n, c->cfg.k, c->cfg.n_feat, *anc, *mlp, *dG, mask, d_mlp, d_anc,
-                                  d_pose, c->cfg.decode_bf16 ? 1 : 0, c->cfg.opacity_tanh, scratch, c->d_err,
+                                  d_pose, c->cfg.decode_bf16 && c->cfg.decode_bwd_bf16 ? 1 : 0,
+                                  c->cfg.opacity_tanh, scratch, c->d_err,
                                   c->num_sms, hook, st));
     return UPS_OK;
 }

@@ -34,42 +34,6 @@ namespace {
 
 constexpr int kLiftHidden = 128;
 
-__global__ void k_bias_relu(float *__restrict__ z, const float *__restrict__ b, size_t HW) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= HW) return;
-    float *row = z + (size_t)blockIdx.y * HW;
-    row[p] = fmaxf(row[p] + b[blockIdx.y], 0.f);
-}
-
-// out[r] += sum_p m[r * HW + p]: blockIdx.y = row, blockIdx.x = a chunk of
-// kSumChunk pixels, one atomic per block
-constexpr int kSumChunk = 8192;
-__global__ void __launch_bounds__(256) k_row_sums(const float *__restrict__ m, size_t HW, float *__restrict__ out) {
-    const float *row = m + (size_t)blockIdx.y * HW;
-    const size_t p0 = (size_t)blockIdx.x * kSumChunk;
-    const size_t p1 = min(HW, p0 + kSumChunk);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    size_t p = p0 + threadIdx.x;
-    for (; p + 768 < p1; p += 1024) {
-        s0 += row[p];
-        s1 += row[p + 256];
-        s2 += row[p + 512];
-        s3 += row[p + 768];
-    }
-    for (; p < p1; p += 256) s0 += row[p];
-    float s = (s0 + s1) + (s2 + s3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ float red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(out + blockIdx.y, t);
-    }
-}
-
 // first pixel index along an axis whose clamped bilinear position
 // floor(clamp((x + 0.5) / patch - 0.5, 0, n - 1)) is at least i
 __device__ __forceinline__ int cell_start(int i, int patch) {
@@ -112,123 +76,385 @@ __global__ void __launch_bounds__(256) k_cell_gram(const float *__restrict__ gri
     }
 }
 
-constexpr int kCellThreads = 256;
+// ---------------------------------------------------------------------------
+// fused per-cell kernel: everything 128 wide stays in shared memory
+// ---------------------------------------------------------------------------
+//
+// Persistent CTAs (256 threads) walk the cells of the patch grid; a cell's
+// pixels share their four corner patches and go through in chunks of kFC:
+//   Z = W1 F~ + b1, H = relu(Z)           (hidden-major Hh and pixel-major Hp)
+//   MH = M H                               (8 hidden x 4 pixels per thread)
+//   per pixel: H.e_p, u.H, H.MH -> cos, the loss, a_p, b_p
+//   dZ = (a e_p + b (MH + u)) relu'(Z)     (over Hh), b H (pixel-major bHp)
+//   Gram += (bH)^T H                        (registers, upper 8x8 blocks only)
+//   dF~ = W1^T dZ, dW1 += dZ F~^T, db1 += sum dZ, hb += sum b H,
+//   D of the four corners += sum a w_k H
+// Gram, hb, db1 and dW1 go out with one atomic per value and CTA at the end,
+// D and alpha per cell.  FP32 fmaf throughout.
+constexpr int kFC = 64;                 // pixels per chunk
+constexpr int kFT = 256;                // threads
+constexpr int kHP = kFC + 4;            // row stride of hidden-major arrays
+constexpr int kPP = kLiftHidden + 4;    // row stride of pixel-major arrays
 
-// One CTA per cell (ci, cj) of pixels that share their four patches.  Phase 1,
-// a thread per pixel: the cosine from H, MH = M H, e and the cell's Gram; the
-// loss; dL/dZ written over MH; b H written to bH; a w_k kept in shared memory.
-// Phase 2, a thread per hidden unit (two halves of the pixels): D of the four
-// corners.  Per-CTA sums of a w_k, b and the loss go out with one atomic each.
-// Dynamic shared memory: 4 * npx_max floats (npx_max >= pixels of any cell).
-__global__ void __launch_bounds__(kCellThreads) k_lift_cells(
-    int W, int H, int wp, int hp, int patch, int npx_max, const float *__restrict__ Hm, float *__restrict__ MH,
-    float *__restrict__ bH, const float *__restrict__ E, const float *__restrict__ s, const float *__restrict__ u,
-    const float *__restrict__ beta, const float *__restrict__ gram, const float *__restrict__ weight, float g0,
-    float *__restrict__ loss, float *__restrict__ D, float *__restrict__ alpha, float *__restrict__ sb) {
-    extern __shared__ float aw[];  // [4][npx_max]
-    __shared__ float sE[4][kLiftHidden], sU[kLiftHidden], sS[4], sG[10];
-    __shared__ float red[kCellThreads / 32][6];
-    __shared__ float part[4][kLiftHidden];
-    const int ci = blockIdx.x, cj = blockIdx.y;
-    const int x0 = ci, y0 = cj;
-    const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
-    const int corner[4] = {y0 * wp + x0, y0 * wp + x1, y1 * wp + x0, y1 * wp + x1};
+template <int NF>
+struct FusedSmem {
+    float M[kLiftHidden][kLiftHidden];   // symmetric W2^T W2
+    float W1T[NF][kLiftHidden];          // W1 transposed
+    float b1[kLiftHidden], u[kLiftHidden];
+    float E[4][kLiftHidden];             // W2^T g of the cell's four corners
+    float Fc[NF][kHP];                   // F~ of the chunk, channel-major
+    float Hh[kLiftHidden][kHP];          // H, then dZ (hidden-major)
+    float Hp[kFC][kPP];                  // H (pixel-major)
+    float bHp[kFC][kPP];                 // b_p H_p (pixel-major)
+    float red[16][kFC][3];               // partial H.e, u.H, H.MH per hidden block
+    float w4[kFC][4];                    // bilinear weights of the chunk's pixels
+    float ab[kFC][2];                    // a_p, b_p
+    float aw[4][kFC];                    // a_p w_k(p)
+    float Dpart[4][kLiftHidden];
+    float sS[4], sG[10];
+    int pix[kFC];                        // pixel index in the view, -1: none
+};
+
+size_t fused_smem_bytes(int nf) {
+    return nf == 32 ? sizeof(FusedSmem<32>) : sizeof(FusedSmem<16>);
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kFT, 1) k_lift_fused(
+    int W, int H, int wp, int hp, int patch, const float *__restrict__ feat, const float *__restrict__ w1,
+    const float *__restrict__ b1, const float *__restrict__ Mg, const float *__restrict__ E,
+    const float *__restrict__ s, const float *__restrict__ u, const float *__restrict__ beta,
+    const float *__restrict__ gram, const float *__restrict__ weight, float g0, float *__restrict__ loss,
+    float *__restrict__ D, float *__restrict__ alpha, float *__restrict__ sb, float *__restrict__ hb_out,
+    float *__restrict__ Gb, float *__restrict__ d_w1, float *__restrict__ d_b1, float *__restrict__ d_feat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem<NF> &S = *reinterpret_cast<FusedSmem<NF> *>(smem_raw);
     const int tid = threadIdx.x;
-    for (int i = tid; i < 4 * kLiftHidden; i += kCellThreads)
-        sE[i / kLiftHidden][i % kLiftHidden] = E[(size_t)corner[i / kLiftHidden] * kLiftHidden + i % kLiftHidden];
-    if (tid < kLiftHidden) sU[tid] = u[tid];
-    if (tid < 4) sS[tid] = s[corner[tid]];
-    if (tid < 10) sG[tid] = gram[(size_t)(y0 * wp + x0) * 10 + tid];
-    __syncthreads();
-    const int xs = cell_start(ci, patch), xe = ci + 1 >= wp ? W : min(W, cell_start(ci + 1, patch));
-    const int ys = cell_start(cj, patch), ye = cj + 1 >= hp ? H : min(H, cell_start(cj + 1, patch));
-    const int nx = max(0, xe - xs), npx = nx * max(0, ye - ys);
     const size_t HW = (size_t)W * H;
+    for (int i = tid; i < kLiftHidden * kLiftHidden; i += kFT) (&S.M[0][0])[i] = Mg[i];
+    for (int i = tid; i < kLiftHidden * NF; i += kFT) {
+        const int j = i / NF, c = i - j * NF;
+        S.W1T[c][j] = w1[i];
+    }
+    if (tid < kLiftHidden) {
+        S.b1[tid] = b1[tid];
+        S.u[tid] = u[tid];
+    }
     const float bt = *beta;
     const float inv2p = 1.f / (float)(2 * patch);
-    float t_al[4] = {0.f, 0.f, 0.f, 0.f}, t_sb = 0.f, t_term = 0.f;
-    for (int q = tid; q < npx; q += kCellThreads) {
-        const int y = ys + q / nx, x = xs + q % nx;
-        const size_t p = (size_t)y * W + x;
-        // bilinear weights from exact integer numerators (clamped positions give 0;
-        // at the far edge x1 == x0 and the two weights add up)
-        const float ax = fminf(fmaxf((float)(2 * x + 1 - (2 * x0 + 1) * patch) * inv2p, 0.f), 1.f);
-        const float ay = fminf(fmaxf((float)(2 * y + 1 - (2 * y0 + 1) * patch) * inv2p, 0.f), 1.f);
-        const float w[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
-        float dot = 0.f, hmh = 0.f, uh = 0.f;
+    // thread blocks: A = 8 hidden x 4 pixels; G = 8 x 8 of the Gram
+    const int jb = tid >> 4, pb = tid & 15;
+    const int j0 = jb * 8, p0 = pb * 4;
+    // the Gram is symmetric: threads 0..135 own the 136 upper 8x8 blocks
+    // (row-major over the block triangle), so whole warps share the work
+    int gbi = 0, gt = tid;
+    while (gbi < 16 && gt >= 16 - gbi) {
+        gt -= 16 - gbi;
+        ++gbi;
+    }
+    const bool gram_on = tid < 136;
+    const int gi0 = (gram_on ? gbi : 0) * 8, gj0 = (gram_on ? gbi + gt : 0) * 8;
+    float G[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) G[x][y] = 0.f;
+    float hb[8], db1[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) hb[x] = db1[x] = 0.f;
+    // dW1: thread (8 hidden of block jb) x (channels c = pb, pb + 16 for NF = 32)
+    constexpr int NC = NF / 16;
+    float dw1[8][NC];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < NC; ++y) dw1[x][y] = 0.f;
+    float t_loss = 0.f, t_sb = 0.f;
+    const int n_cells = wp * hp;
+    for (int cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
+        const int cj = cell / wp, ci = cell - cj * wp;
+        const int x0 = ci, y0 = cj;
+        const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
+        const int corner[4] = {y0 * wp + x0, y0 * wp + x1, y1 * wp + x0, y1 * wp + x1};
+        const int xs = cell_start(ci, patch), xe = ci + 1 >= wp ? W : min(W, cell_start(ci + 1, patch));
+        const int ys = cell_start(cj, patch), ye = cj + 1 >= hp ? H : min(H, cell_start(cj + 1, patch));
+        const int nx = max(0, xe - xs), npx = nx * max(0, ye - ys);
+        __syncthreads();  // the previous cell's shared data is no longer read
+        for (int i = tid; i < 4 * kLiftHidden; i += kFT)
+            S.E[i / kLiftHidden][i % kLiftHidden] = E[(size_t)corner[i / kLiftHidden] * kLiftHidden + i % kLiftHidden];
+        if (tid < 4) S.sS[tid] = s[corner[tid]];
+        if (tid < 10) S.sG[tid] = gram[(size_t)cell * 10 + tid];
+        for (int i = tid; i < 4 * kLiftHidden; i += kFT) (&S.Dpart[0][0])[i] = 0.f;
+        float al[4] = {0.f, 0.f, 0.f, 0.f};  // sum a w_k over the cell (threads < kFC)
+        for (int q0 = 0; q0 < npx; q0 += kFC) {
+            __syncthreads();
+            // chunk pixels, bilinear weights, F~
+            if (tid < kFC) {
+                const int q = q0 + tid;
+                int pidx = -1;
+                float w[4] = {0.f, 0.f, 0.f, 0.f};
+                if (q < npx) {
+                    const int y = ys + q / nx, x = xs + q % nx;
+                    pidx = y * W + x;
+                    const float ax = fminf(fmaxf((float)(2 * x + 1 - (2 * x0 + 1) * patch) * inv2p, 0.f), 1.f);
+                    const float ay = fminf(fmaxf((float)(2 * y + 1 - (2 * y0 + 1) * patch) * inv2p, 0.f), 1.f);
+                    w[0] = (1.f - ax) * (1.f - ay);
+                    w[1] = ax * (1.f - ay);
+                    w[2] = (1.f - ax) * ay;
+                    w[3] = ax * ay;
+                }
+                S.pix[tid] = pidx;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) S.w4[tid][k] = w[k];
+            }
+            __syncthreads();
+            for (int i = tid; i < NF * kFC; i += kFT) {
+                const int c = i / kFC, p = i - c * kFC;
+                const int pidx = S.pix[p];
+                S.Fc[c][p] = pidx >= 0 ? feat[(size_t)c * HW + pidx] : 0.f;
+            }
+            __syncthreads();
+            // Z and H (block A)
+            {
+                float z[8][4];
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) z[x][y] = S.b1[j0 + x];
 #pragma unroll 4
-        for (int j = 0; j < kLiftHidden; ++j) {
-            const float h = Hm[(size_t)j * HW + p], mh = MH[(size_t)j * HW + p];
-            const float ej = w[0] * sE[0][j] + w[1] * sE[1][j] + w[2] * sE[2][j] + w[3] * sE[3][j];
-            dot = fmaf(h, ej, dot);
-            hmh = fmaf(h, mh, hmh);
-            uh = fmaf(sU[j], h, uh);
-        }
-        dot += w[0] * sS[0] + w[1] * sS[1] + w[2] * sS[2] + w[3] * sS[3];
-        const float nF2 = w[0] * w[0] * sG[0] + w[1] * w[1] * sG[4] + w[2] * w[2] * sG[7] + w[3] * w[3] * sG[9] +
-                          2.f * (w[0] * w[1] * sG[1] + w[0] * w[2] * sG[2] + w[0] * w[3] * sG[3] +
-                                 w[1] * w[2] * sG[5] + w[1] * w[3] * sG[6] + w[2] * w[3] * sG[8]);
-        const float nFh2 = hmh + 2.f * uh + bt;
-        const bool ok = nF2 > 0.f && nFh2 > 0.f;
-        const float wpx = weight ? weight[p] : 1.f;  // per-pixel weight (the mask of Eq. 14)
-        const float g = g0 * wpx;
-        const float inv = ok ? rsqrtf(nF2) * rsqrtf(nFh2) : 0.f;
-        const float cs = dot * inv;
-        t_term += wpx * (1.f - cs);
-        const float a = -g * inv, b = ok ? g * cs / nFh2 : 0.f;
+                for (int c = 0; c < NF; ++c) {
+                    const float4 wa = *reinterpret_cast<const float4 *>(&S.W1T[c][j0]);
+                    const float4 wb = *reinterpret_cast<const float4 *>(&S.W1T[c][j0 + 4]);
+                    const float4 f = *reinterpret_cast<const float4 *>(&S.Fc[c][p0]);
+                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                    const float fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                    for (int x = 0; x < 8; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) z[x][y] = fmaf(wv[x], fv[y], z[x][y]);
+                }
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const float4 h4 = make_float4(fmaxf(z[x][0], 0.f), fmaxf(z[x][1], 0.f), fmaxf(z[x][2], 0.f),
+                                                  fmaxf(z[x][3], 0.f));
+                    *reinterpret_cast<float4 *>(&S.Hh[j0 + x][p0]) = h4;
+                    S.Hp[p0][j0 + x] = h4.x;
+                    S.Hp[p0 + 1][j0 + x] = h4.y;
+                    S.Hp[p0 + 2][j0 + x] = h4.z;
+                    S.Hp[p0 + 3][j0 + x] = h4.w;
+                }
+            }
+            __syncthreads();
+            // MH (block A), then the per-pixel partial dot products
+            float mh[8][4];
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) mh[x][y] = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < kLiftHidden; ++k) {
+                const float4 ma = *reinterpret_cast<const float4 *>(&S.M[k][j0]);
+                const float4 mb = *reinterpret_cast<const float4 *>(&S.M[k][j0 + 4]);
+                const float4 h = *reinterpret_cast<const float4 *>(&S.Hh[k][p0]);
+                const float mv[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+                const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) mh[x][y] = fmaf(mv[x], hv[y], mh[x][y]);
+            }
+            float hv[8][4], ev[8][4];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const float4 h = *reinterpret_cast<const float4 *>(&S.Hh[j0 + x][p0]);
+                hv[x][0] = h.x;
+                hv[x][1] = h.y;
+                hv[x][2] = h.z;
+                hv[x][3] = h.w;
+            }
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const float4 w = *reinterpret_cast<const float4 *>(&S.w4[p0 + y][0]);
+                float de = 0.f, du = 0.f, dm = 0.f;
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int j = j0 + x;
+                    ev[x][y] = w.x * S.E[0][j] + w.y * S.E[1][j] + w.z * S.E[2][j] + w.w * S.E[3][j];
+                    de = fmaf(hv[x][y], ev[x][y], de);
+                    du = fmaf(S.u[j], hv[x][y], du);
+                    dm = fmaf(hv[x][y], mh[x][y], dm);
+                }
+                S.red[jb][p0 + y][0] = de;
+                S.red[jb][p0 + y][1] = du;
+                S.red[jb][p0 + y][2] = dm;
+            }
+            __syncthreads();
+            // per pixel: cosine, loss, a_p, b_p
+            if (tid < kFC) {
+                const int p = tid;
+                float de = 0.f, du = 0.f, dm = 0.f;
+                for (int b = 0; b < 16; ++b) {
+                    de += S.red[b][p][0];
+                    du += S.red[b][p][1];
+                    dm += S.red[b][p][2];
+                }
+                const float *w = S.w4[p];
+                const float dot = de + w[0] * S.sS[0] + w[1] * S.sS[1] + w[2] * S.sS[2] + w[3] * S.sS[3];
+                const float nF2 = w[0] * w[0] * S.sG[0] + w[1] * w[1] * S.sG[4] + w[2] * w[2] * S.sG[7] +
+                                  w[3] * w[3] * S.sG[9] +
+                                  2.f * (w[0] * w[1] * S.sG[1] + w[0] * w[2] * S.sG[2] + w[0] * w[3] * S.sG[3] +
+                                         w[1] * w[2] * S.sG[5] + w[1] * w[3] * S.sG[6] + w[2] * w[3] * S.sG[8]);
+                const float nFh2 = dm + 2.f * du + bt;
+                float a = 0.f, b = 0.f;
+                const int pidx = S.pix[p];
+                if (pidx >= 0) {
+                    const bool ok = nF2 > 0.f && nFh2 > 0.f;
+                    const float wpx = weight ? weight[pidx] : 1.f;
+                    const float g = g0 * wpx;
+                    const float inv = ok ? rsqrtf(nF2) * rsqrtf(nFh2) : 0.f;
+                    const float cs = dot * inv;
+                    t_loss += wpx * (1.f - cs);
+                    a = -g * inv;
+                    b = ok ? g * cs / nFh2 : 0.f;
+                    t_sb += b;
+                }
+                S.ab[p][0] = a;
+                S.ab[p][1] = b;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S.aw[k][p] = a * w[k];
+                    al[k] += a * w[k];
+                }
+            }
+            __syncthreads();
+            // dZ over Hh, b H to bHp, db1 and hb sums (block A)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const float a = S.ab[p0 + y][0], b = S.ab[p0 + y][1];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int j = j0 + x;
+                    const float dh = fmaf(a, ev[x][y], b * (mh[x][y] + S.u[j]));
+                    const float dz = hv[x][y] > 0.f ? dh : 0.f;
+                    S.Hh[j][p0 + y] = dz;
+                    S.bHp[p0 + y][j] = b * hv[x][y];
+                    db1[x] += dz;
+                    hb[x] = fmaf(b, hv[x][y], hb[x]);
+                }
+            }
+            __syncthreads();
+            // Gram (upper 8x8 blocks), D of the corners, dF~, dW1
+            if (gram_on) {
+#pragma unroll 2
+                for (int p = 0; p < kFC; ++p) {
+                    const float4 ba = *reinterpret_cast<const float4 *>(&S.bHp[p][gi0]);
+                    const float4 bb = *reinterpret_cast<const float4 *>(&S.bHp[p][gi0 + 4]);
+                    const float4 ha = *reinterpret_cast<const float4 *>(&S.Hp[p][gj0]);
+                    const float4 hc = *reinterpret_cast<const float4 *>(&S.Hp[p][gj0 + 4]);
+                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                    const float hvv[8] = {ha.x, ha.y, ha.z, ha.w, hc.x, hc.y, hc.z, hc.w};
+#pragma unroll
+                    for (int x = 0; x < 8; ++x)
+#pragma unroll
+                        for (int y = 0; y < 8; ++y) G[x][y] = fmaf(bv[x], hvv[y], G[x][y]);
+                }
+            }
+            {
+                // D: thread (hidden j, half of the pixels)
+                const int j = tid & (kLiftHidden - 1), half = tid >> 7;
+                float Dk[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int p = half; p < kFC; p += 2) {
+                    const float h = S.Hp[p][j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Dk[k] = fmaf(S.aw[k][p], h, Dk[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(&S.Dpart[k][j], Dk[k]);
+            }
+            {
+                // dF~ = W1^T dZ: thread (channel, 4 pixels); NF x kFC outputs
+                for (int o = tid; o < NF * (kFC / 4); o += kFT) {
+                    const int c = o / (kFC / 4), pq = (o - c * (kFC / 4)) * 4;
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
-        for (int j = 0; j < kLiftHidden; ++j) {
-            const size_t o = (size_t)j * HW + p;
-            const float h = Hm[o];
-            const float ej = w[0] * sE[0][j] + w[1] * sE[1][j] + w[2] * sE[2][j] + w[3] * sE[3][j];
-            const float dh = a * ej + b * (MH[o] + sU[j]);
-            MH[o] = h > 0.f ? dh : 0.f;  // dL/dZ (ReLU derivative)
-            bH[o] = b * h;
+                    for (int j = 0; j < kLiftHidden; ++j) {
+                        const float wv = S.W1T[c][j];
+                        const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j][pq]);
+                        acc[0] = fmaf(wv, dz.x, acc[0]);
+                        acc[1] = fmaf(wv, dz.y, acc[1]);
+                        acc[2] = fmaf(wv, dz.z, acc[2]);
+                        acc[3] = fmaf(wv, dz.w, acc[3]);
+                    }
+                    if (d_feat)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const int pidx = S.pix[pq + y];
+                            if (pidx >= 0) d_feat[(size_t)c * HW + pidx] += acc[y];
+                        }
+                }
+            }
+            // dW1 += dZ F~^T: thread (8 hidden of block jb) x channels pb (+16)
+#pragma unroll 2
+            for (int pq = 0; pq < kFC; pq += 4) {
+                float4 fz[NC];
+#pragma unroll
+                for (int y = 0; y < NC; ++y) fz[y] = *reinterpret_cast<const float4 *>(&S.Fc[pb + 16 * y][pq]);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j0 + x][pq]);
+#pragma unroll
+                    for (int y = 0; y < NC; ++y)
+                        dw1[x][y] = fmaf(dz.x, fz[y].x, fmaf(dz.y, fz[y].y, fmaf(dz.z, fz[y].z, fmaf(dz.w, fz[y].w, dw1[x][y]))));
+                }
+            }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            aw[k * npx_max + q] = a * w[k];
-            t_al[k] += a * w[k];
+        __syncthreads();
+        // the cell's D rows and alpha
+        for (int i = tid; i < 4 * kLiftHidden; i += kFT) {
+            const int k = i / kLiftHidden, j = i - k * kLiftHidden;
+            if (npx > 0) atomicAdd(D + (size_t)corner[k] * kLiftHidden + j, S.Dpart[k][j]);
         }
-        t_sb += b;
+        if (tid < kFC && npx > 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(alpha + corner[k], al[k]);
     }
-    // per-CTA sums
-    float v[6] = {t_al[0], t_al[1], t_al[2], t_al[3], t_sb, t_term};
+    // the CTA's sums
+    if (gram_on)
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+        for (int x = 0; x < 8; ++x)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    if ((tid & 31) == 0)
+            for (int y = 0; y < 8; ++y) {
+                const int i = gi0 + x, j = gj0 + y;
+                if (i <= j) {
+                    atomicAdd(Gb + (size_t)i * kLiftHidden + j, G[x][y]);
+                    if (i != j) atomicAdd(Gb + (size_t)j * kLiftHidden + i, G[x][y]);
+                }
+            }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) red[tid >> 5][i] = v[i];
-    __syncthreads();
-    if (npx == 0) return;
-    if (tid < 6) {
-        float t = 0.f;
-        for (int w8 = 0; w8 < kCellThreads / 32; ++w8) t += red[w8][tid];
-        if (tid < 4)
-            atomicAdd(alpha + corner[tid], t);
-        else if (tid == 4)
-            atomicAdd(sb, t);
-        else
-            atomicAdd(loss, g0 * t);
+    for (int x = 0; x < 8; ++x) {
+        float h = hb[x], d = db1[x];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {  // the 16 threads of block jb are lanes 16 (jb & 1) ..
+            h += __shfl_xor_sync(0xffffffffu, h, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (pb == 0) {
+            atomicAdd(hb_out + j0 + x, h);
+            if (d_b1) atomicAdd(d_b1 + j0 + x, d);
+        }
+        if (d_w1)
+#pragma unroll
+            for (int y = 0; y < NC; ++y) atomicAdd(d_w1 + (size_t)(j0 + x) * NF + pb + 16 * y, dw1[x][y]);
     }
-    // D of the four corners: thread (half, j) sums its half of the pixels
-    const int j = tid & (kLiftHidden - 1), half = tid >> 7;
-    float P[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = half; q < npx; q += 2) {
-        const int y = ys + q / nx, x = xs + q % nx;
-        const float h = Hm[(size_t)j * HW + (size_t)y * W + x];
+    float v2[2] = {t_loss, t_sb};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) P[k] = fmaf(aw[k * npx_max + q], h, P[k]);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v2[i] += __shfl_xor_sync(0xffffffffu, v2[i], o);
+    if ((tid & 31) == 0) {
+        atomicAdd(loss, g0 * v2[0]);
+        atomicAdd(sb, v2[1]);
     }
-    if (half == 1)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) part[k][j] = P[k];
-    __syncthreads();
-    if (half == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) atomicAdd(D + (size_t)corner[k] * kLiftHidden + j, P[k] + part[k][j]);
 }
 
 // y[i] += x[i] * (*c)
@@ -241,7 +467,7 @@ size_t round64(size_t n) { return (n + 63) & ~size_t(63); }
 
 // scratch of one view, in floats
 struct LiftLayout {
-    size_t Hm, MH, bH, E, s, M, u, beta, gram, D, alpha, hb, sb, Gb, total;
+    size_t E, s, M, u, beta, gram, D, alpha, hb, sb, Gb, total;
 };
 LiftLayout lift_layout(size_t hw, size_t np) {
     LiftLayout L{};
@@ -251,9 +477,6 @@ LiftLayout lift_layout(size_t hw, size_t np) {
         o += round64(n);
         return at;
     };
-    L.Hm = take(kLiftHidden * hw);
-    L.MH = take(kLiftHidden * hw);
-    L.bH = take(kLiftHidden * hw);
     L.E = take(kLiftHidden * np);
     L.s = take(np);
     L.M = take(kLiftHidden * kLiftHidden);
@@ -275,13 +498,6 @@ LiftLayout lift_layout(size_t hw, size_t np) {
 
 size_t lift_scratch_floats(size_t max_hw, size_t max_np) { return lift_layout(max_hw, max_np).total; }
 
-// largest pixel count of a cell of the patch grid: a cell spans at most
-// 1.5 patch + 1 pixels along an axis (the first one), or the whole view
-int lift_cell_pixels(int patch) {
-    const int m = (3 * patch) / 2 + 2;
-    return m * m;
-}
-
 // One view: forward, loss and backward.  feat / d_feat: the view's planes
 // [nf][HW]; grid: its patch grid [hp][wp][nh]; weight: its per-pixel weights
 // (null: 1); scratch: lift_scratch_floats(HW, hp * wp) floats.
@@ -294,14 +510,10 @@ cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh
     const int HW = W * H, np = wp * hp;
     const int NH = kLiftHidden;
     const LiftLayout L = lift_layout((size_t)HW, (size_t)np);
-    float *Hm = scratch + L.Hm;  // [128][HW] hidden (post-ReLU)
-    float *MH = scratch + L.MH;  // [128][HW] M H, then dL/dZ
-    float *bH = scratch + L.bH;  // [128][HW] b_p H_p
     float *E = scratch + L.E, *sv = scratch + L.s, *M = scratch + L.M, *u = scratch + L.u, *beta = scratch + L.beta;
     float *gram = scratch + L.gram, *D = scratch + L.D, *alpha = scratch + L.alpha, *hb = scratch + L.hb;
     float *sb = scratch + L.sb, *Gb = scratch + L.Gb;
     const dim3 blk(256);
-    const unsigned gx = (unsigned)((HW + 255) / 256);
     cudaError_t e;
     // per patch and weight-sized: E = G W2 ([np][128]), s = G b2, M = W2^T W2, u = W2^T b2, beta = |b2|^2
     if ((e = gemm_f32(st, false, false, NH, np, nh, 1.f, w2, NH, grid, nh, 0.f, E, NH, num_sms, launches)) != cudaSuccess) return e;
@@ -310,25 +522,30 @@ cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh
     if ((e = gemm_f32(st, false, false, NH, 1, nh, 1.f, w2, NH, b2, nh, 0.f, u, NH, num_sms, launches)) != cudaSuccess) return e;
     if ((e = gemm_f32(st, true, false, 1, 1, nh, 1.f, b2, nh, b2, nh, 0.f, beta, 1, num_sms, launches)) != cudaSuccess) return e;
     k_cell_gram<<<(unsigned)((np + 7) / 8), blk, 0, st>>>(grid, wp, hp, nh, gram);
+    ++*launches;
+    // the fused kernel adds into D, alpha, hb, sb and Gb
     if ((e = cudaMemsetAsync(D, 0, (L.sb + 1 - L.D) * sizeof(float), st)) != cudaSuccess) return e;
-    // H = relu(F~ W1^T + b1); MH = H M
-    if ((e = gemm_f32(st, false, false, HW, NH, nf, 1.f, feat, HW, w1, nf, 0.f, Hm, HW, num_sms, launches)) != cudaSuccess) return e;
-    k_bias_relu<<<dim3(gx, NH), blk, 0, st>>>(Hm, b1, (size_t)HW);
-    if ((e = gemm_f32(st, false, false, HW, NH, NH, 1.f, Hm, HW, M, NH, 0.f, MH, HW, num_sms, launches)) != cudaSuccess) return e;
-    const int npx_max = lift_cell_pixels(patch);
-    k_lift_cells<<<dim3(wp, hp), kCellThreads, (size_t)4 * npx_max * sizeof(float), st>>>(
-        W, H, wp, hp, patch, npx_max, Hm, MH, bH, E, sv, u, beta, gram, weight, g, loss, D, alpha, sb);
-    *launches += 3;
+    if ((e = cudaMemsetAsync(Gb, 0, (size_t)NH * NH * sizeof(float), st)) != cudaSuccess) return e;
+    const size_t smem = fused_smem_bytes(nf);
+    const int grid_ctas = std::max(1, std::min(np, num_sms));
+#define UPS_LIFT(NFV)                                                                                            \
+    do {                                                                                                        \
+        cudaFuncSetAttribute(k_lift_fused<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+        k_lift_fused<NFV><<<grid_ctas, kFT, smem, st>>>(W, H, wp, hp, patch, feat, w1, b1, M, E, sv, u, beta,   \
+                                                        gram, weight, g, loss, D, alpha, sb, hb, Gb, d_w1, d_b1, \
+                                                        d_feat);                                                \
+    } while (0)
+    if (nf == 16)
+        UPS_LIFT(16);
+    else if (nf == 32)
+        UPS_LIFT(32);
+    else
+        return cudaErrorInvalidValue;
+#undef UPS_LIFT
+    ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    float *dZ = MH;
-    const unsigned sum_blocks = (unsigned)((HW + kSumChunk - 1) / kSumChunk);
-    if (d_w2 || d_b2) {
-        k_row_sums<<<dim3(sum_blocks, NH), blk, 0, st>>>(bH, (size_t)HW, hb);
-        ++*launches;
-    }
     if (d_w2) {
         // dW2 ([nh][128] row-major = column-major 128 x nh) += D^T-side: D G, Gb W2, hb b2^T
-        if ((e = gemm_f32(st, true, false, NH, NH, HW, 1.f, bH, HW, Hm, HW, 0.f, Gb, NH, num_sms, launches)) != cudaSuccess) return e;
         if ((e = gemm_f32(st, false, true, NH, nh, np, 1.f, D, NH, grid, nh, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
             return e;
         if ((e = gemm_f32(st, false, false, NH, nh, NH, 1.f, Gb, NH, w2, NH, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
@@ -345,16 +562,6 @@ cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh
         k_axpy_dev<<<(unsigned)((nh + 255) / 256), blk, 0, st>>>(nh, b2, sb, d_b2);
         ++*launches;
     }
-    if (d_b1) {
-        k_row_sums<<<dim3(sum_blocks, NH), blk, 0, st>>>(dZ, (size_t)HW, d_b1);
-        ++*launches;
-    }
-    // dW1 += F~^T dZ ([nf x 128] column-major = [128][nf] row-major)
-    if (d_w1 && (e = gemm_f32(st, true, false, nf, NH, HW, 1.f, feat, HW, dZ, HW, 1.f, d_w1, nf, num_sms, launches)) != cudaSuccess)
-        return e;
-    // dF~ += dZ W1
-    if (d_feat && (e = gemm_f32(st, false, true, HW, nf, NH, 1.f, dZ, HW, w1, nf, 1.f, d_feat, HW, num_sms, launches)) != cudaSuccess)
-        return e;
     return cudaGetLastError();
 }
 

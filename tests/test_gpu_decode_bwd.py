@@ -3,7 +3,7 @@ pose gradients for a given dL/d(decoded Gaussians), against the oracle fed the
 same dL/dG.
 
 * FP32 path: 2e-3 relative L2 (the gradient bar);
-* BF16 tensor-core path (decode_bf16): every operand of the data-path products
+* BF16 tensor-core path (decode_bf16 with decode_bwd_bf16): every operand of the data-path products
   rounded to BF16 (8 significant bits), and the ReLU masks follow the BF16
   hidden pre-activations (as in the BF16 forward), so a hidden unit near zero
   may switch; the stated bound is 5e-2 relative L2 (the measured values are
@@ -59,7 +59,9 @@ def oracle_grads(case, opacity_tanh=False):
 
 def gpu_grads(case, bf16, mask=B.GRAD_ALL, opacity_tanh=False):
     import torch
-    R = B.Renderer(n_feat=case["nf"], k=case["K"], decode_bf16=int(bf16), opacity_tanh=int(opacity_tanh))
+    # the BF16 case runs the tensor-core data path of the decode backward (decode_bwd_bf16)
+    R = B.Renderer(n_feat=case["nf"], k=case["K"], decode_bf16=int(bf16), decode_bwd_bf16=int(bf16),
+                   opacity_tanh=int(opacity_tanh))
     ad, md = B.anchors_to_device(case["anc"], case["mlp"])
     dG = B.to_set(case["dG"], per_view=True)
     d_mlp = {k: torch.zeros_like(v) for k, v in md.items()}

@@ -2,15 +2,11 @@
 FP64 oracle, both fed the same seeded synthetic feature maps, DINO patch grids
 and MLP weights (a forward on the same cameras only sets up the views).
 
-The layers run as TF32 tensor-core GEMMs: each product sees both operands
-rounded to 11 significant bits (unit roundoff u = 2^-11 ~ 4.9e-4, FP32
-accumulation).  The bars follow the chain of rounded GEMMs behind each output:
-the loss and dL/dF^ (hence dW2, db2, sums over all pixels) carry one rounded
-layer, ~u: bar 1e-3; dZ = (dL/dF^ W2) relu' adds a rounded product summed over
-n_h mixed-sign terms (db1: 5e-3, dW1 = F~^T dZ: 2e-2); dL/dF~ = dZ W1 sums 128
-mixed-sign terms per pixel, which amplifies the relative error by ~sqrt(128)
-~ 11: bar 5e-2.  Measured (printed): loss <= 1e-5, dW2/db2 <= 1e-4, db1 <=
-1.7e-3, dW1 <= 8.6e-3, dF~ <= 1.7e-2."""
+Every product runs in FP32 (fmaf on the CUDA cores, no reduced-precision
+operands), so the loss and every gradient group are held to the path's
+gradient bar, 2e-3 relative L2 (1e-5 + 1e-4 relative for the loss).  Measured
+(printed): loss <= 1.4e-7, dW2/db2 <= 3e-7, db1 <= 8.7e-6, dW1 <= 3.4e-5,
+dF~ <= 1.5e-4 (the last sums 128 mixed-sign terms per pixel)."""
 import numpy as np
 import pytest
 
@@ -21,8 +17,8 @@ from paper_2505_22335_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
 
-LOSS_RTOL = 1e-3
-GRAD_RTOL = dict(w2=1e-3, b2=1e-3, b1=5e-3, w1=2e-2, feat=5e-2)
+LOSS_RTOL = 1e-4
+GRAD_RTOL = dict(w2=2e-3, b2=2e-3, b1=2e-3, w1=2e-3, feat=2e-3)
 
 
 @pytest.fixture(scope="module", autouse=True)
