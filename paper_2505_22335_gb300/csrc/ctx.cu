@@ -53,11 +53,11 @@ cudaError_t unc_view(int num_sms, cudaStream_t st, int W, int H, int nh, int pat
 cudaError_t ssim_set_window();
 cudaError_t launch_ssim(const ViewTable &vt, const float *x, const float *y, const float *weight, float *G, float g,
                         float *loss, float *dx, cudaStream_t st);
-size_t lift_scratch_floats(size_t max_hw, size_t max_np);
-cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
-                      const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
-                      const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
-                      float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches);
+size_t lift_scratch_floats(size_t np_total);
+cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, int nh, int patch, const float *feat,
+                     const float *grid, const float *w1, const float *b1, const float *w2, const float *b2, float g,
+                     const float *weight, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
+                     float *d_feat, float *scratch, int *launches);
 cudaError_t launch_uncertainty(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                                float t_mask, const ups_images &img, const ups_targets &tgt, float *R, float *sigma2,
                                uint8_t *motion, cudaStream_t st);
@@ -838,30 +838,21 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
     if (s != UPS_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    size_t max_np = 0;
+    size_t np_total = 0;
     for (int v = 0; v < c->vt.n; ++v) {
         const DevView &cam = c->vt.v[v];
-        max_np = std::max(max_np, (size_t)((cam.H + lcfg->patch - 1) / lcfg->patch) *
-                                      (size_t)((cam.W + lcfg->patch - 1) / lcfg->patch));
+        np_total += (size_t)((cam.H + lcfg->patch - 1) / lcfg->patch) * (size_t)((cam.W + lcfg->patch - 1) / lcfg->patch);
     }
-    UPS_CUDA(c, c->lift_scr.reserve(lift_scratch_floats((size_t)c->max_hw, max_np) * sizeof(float)));
+    if (np_total >= (size_t)INT32_MAX / 128) return fail(c, UPS_ERR_ARG, "too many DINO patches");
+    UPS_CUDA(c, c->lift_scr.reserve(lift_scratch_floats(np_total) * sizeof(float)));
     stage_begin(c, "lift", st);
     UPS_CUDA(c, cudaMemsetAsync(loss_dev, 0, sizeof(float), st));
     const float g = (float)((double)scale / (double)c->n_pix);
-    size_t grid_off = 0;
     int launches = 0;
-    for (int v = 0; v < c->vt.n; ++v) {
-        const DevView &cam = c->vt.v[v];
-        const int hp = (cam.H + lcfg->patch - 1) / lcfg->patch, wp = (cam.W + lcfg->patch - 1) / lcfg->patch;
-        const size_t P = (size_t)cam.pix_off;
-        UPS_CUDA(c, lift_view(c->num_sms, st, cam.W, cam.H, nf, lcfg->n_h, lcfg->patch, feat + (size_t)nf * P,
-                              dino + grid_off, wp, hp, mlp->w1, mlp->b1, mlp->w2, mlp->b2, g,
-                              weight ? weight + P : nullptr, loss_dev,
-                              d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr, d_mlp ? d_mlp->w2 : nullptr,
-                              d_mlp ? d_mlp->b2 : nullptr, d_feat ? d_feat + (size_t)nf * P : nullptr,
-                              c->lift_scr.as<float>(), &launches));
-        grid_off += (size_t)hp * wp * lcfg->n_h;
-    }
+    UPS_CUDA(c, lift_all(c->num_sms, st, c->vt, nf, lcfg->n_h, lcfg->patch, feat, dino, mlp->w1, mlp->b1, mlp->w2,
+                         mlp->b2, g, weight, loss_dev, d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr,
+                         d_mlp ? d_mlp->w2 : nullptr, d_mlp ? d_mlp->b2 : nullptr, d_feat, c->lift_scr.as<float>(),
+                         &launches));
     stage_end(c, st, launches);
     return UPS_OK;
 }

@@ -87,9 +87,13 @@ __device__ __forceinline__ void hidden_T(const float *sW1T, const float *sb1, in
 #pragma unroll
     for (int p = 0; p < kH2; ++p) h[p] = b2[p];
     const float4 *f4 = reinterpret_cast<const float4 *>(afeat_row);
+    // the next four inputs are loaded while the current four are applied (one
+    // load in flight per step instead of a stall on each)
+    float4 nxt = __ldg(f4);
 #pragma unroll 1
     for (int i4 = 0; i4 < kFin / 4; ++i4) {
-        const float4 xv = __ldg(f4 + i4);
+        const float4 xv = nxt;
+        if (i4 + 1 < kFin / 4) nxt = __ldg(f4 + i4 + 1);
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {

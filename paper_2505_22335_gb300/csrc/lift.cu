@@ -41,18 +41,42 @@ __device__ __forceinline__ int cell_start(int i, int patch) {
     return i == 0 ? 0 : (int)ceilf((float)i * patch + 0.5f * (float)(patch - 1) - 1e-4f);
 }
 
+// The cells of all views' patch grids, numbered view after view (cell c of
+// view v = patch c of its grid; the grids are concatenated in view order):
+// view of global cell `cell`, its grid size and the view's first cell.
+struct CellView {
+    int v, wp, hp, base;
+};
+__device__ __forceinline__ CellView cell_view(const ViewTable &vt, int patch, int cell) {
+    CellView r{0, 0, 0, 0};
+    int base = 0;
+    for (int v = 0; v < vt.n; ++v) {
+        const int wp = (vt.v[v].W + patch - 1) / patch, hp = (vt.v[v].H + patch - 1) / patch;
+        if (cell < base + wp * hp || v == vt.n - 1) {
+            r = CellView{v, wp, hp, base};
+            break;
+        }
+        base += wp * hp;
+    }
+    return r;
+}
+
 // Gram matrix of the four corner patches of every cell (x0, y0) of the grid
 // (x1 = min(x0 + 1, wp - 1), y1 likewise): gram[cell][10] = g00.g00, g00.g01,
 // g00.g10, g00.g11, g01.g01, g01.g10, g01.g11, g10.g10, g10.g11, g11.g11.
 // One warp per cell.
-__global__ void __launch_bounds__(256) k_cell_gram(const float *__restrict__ grid, int wp, int hp, int nh,
-                                                   float *__restrict__ gram) {
+__global__ void __launch_bounds__(256) k_cell_gram(ViewTable vt, int patch, int n_cells, const float *__restrict__ grid,
+                                                   int nh, float *__restrict__ gram) {
     const int cell = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (cell >= wp * hp) return;
-    const int y0 = cell / wp, x0 = cell - y0 * wp;
+    if (cell >= n_cells) return;
+    const CellView cv = cell_view(vt, patch, cell);
+    const int wp = cv.wp, hp = cv.hp;
+    const int local = cell - cv.base;
+    const int y0 = local / wp, x0 = local - y0 * wp;
     const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
-    const float *g[4] = {grid + ((size_t)y0 * wp + x0) * nh, grid + ((size_t)y0 * wp + x1) * nh,
-                         grid + ((size_t)y1 * wp + x0) * nh, grid + ((size_t)y1 * wp + x1) * nh};
+    const float *vg = grid + (size_t)cv.base * nh;
+    const float *g[4] = {vg + ((size_t)y0 * wp + x0) * nh, vg + ((size_t)y0 * wp + x1) * nh,
+                         vg + ((size_t)y1 * wp + x0) * nh, vg + ((size_t)y1 * wp + x1) * nh};
     float d[10] = {};
     for (int o = lane; o < nh; o += 32) {
         const float v0 = g[0][o], v1 = g[1][o], v2 = g[2][o], v3 = g[3][o];
@@ -121,16 +145,15 @@ size_t fused_smem_bytes(int nf) {
 
 template <int NF>
 __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
-    int W, int H, int wp, int hp, int patch, const float *__restrict__ feat, const float *__restrict__ w1,
+    ViewTable vt, int n_cells, int patch, const float *__restrict__ feat_all, const float *__restrict__ w1,
     const float *__restrict__ b1, const float *__restrict__ Mg, const float *__restrict__ E,
     const float *__restrict__ s, const float *__restrict__ u, const float *__restrict__ beta,
-    const float *__restrict__ gram, const float *__restrict__ weight, float g0, float *__restrict__ loss,
+    const float *__restrict__ gram, const float *__restrict__ weight_all, float g0, float *__restrict__ loss,
     float *__restrict__ D, float *__restrict__ alpha, float *__restrict__ sb, float *__restrict__ hb_out,
-    float *__restrict__ Gb, float *__restrict__ d_w1, float *__restrict__ d_b1, float *__restrict__ d_feat) {
+    float *__restrict__ Gb, float *__restrict__ d_w1, float *__restrict__ d_b1, float *__restrict__ d_feat_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedSmem<NF> &S = *reinterpret_cast<FusedSmem<NF> *>(smem_raw);
     const int tid = threadIdx.x;
-    const size_t HW = (size_t)W * H;
     for (int i = tid; i < kLiftHidden * kLiftHidden; i += kFT) (&S.M[0][0])[i] = Mg[i];
     for (int i = tid; i < kLiftHidden * NF; i += kFT) {
         const int j = i / NF, c = i - j * NF;
@@ -154,11 +177,11 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
     }
     const bool gram_on = tid < 136;
     const int gi0 = (gram_on ? gbi : 0) * 8, gj0 = (gram_on ? gbi + gt : 0) * 8;
-    float G[8][8];
+    f2 G2[4][8];  // Gram rows (x, x + 1) packed for fma.rn.f32x2
 #pragma unroll
-    for (int x = 0; x < 8; ++x)
+    for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) G[x][y] = 0.f;
+        for (int y = 0; y < 8; ++y) G2[x][y] = 0ull;
     float hb[8], db1[8];
 #pragma unroll
     for (int x = 0; x < 8; ++x) hb[x] = db1[x] = 0.f;
@@ -170,12 +193,20 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
 #pragma unroll
         for (int y = 0; y < NC; ++y) dw1[x][y] = 0.f;
     float t_loss = 0.f, t_sb = 0.f;
-    const int n_cells = wp * hp;
     for (int cell = blockIdx.x; cell < n_cells; cell += gridDim.x) {
-        const int cj = cell / wp, ci = cell - cj * wp;
+        // the cell's view, its images and its four corner patches (global patch indices)
+        const CellView cv = cell_view(vt, patch, cell);
+        const int wp = cv.wp, hp = cv.hp, W = vt.v[cv.v].W, H = vt.v[cv.v].H;
+        const size_t HW = (size_t)W * H, P = (size_t)vt.v[cv.v].pix_off;
+        const float *feat = feat_all + (size_t)NF * P;
+        float *d_feat = d_feat_all ? d_feat_all + (size_t)NF * P : nullptr;
+        const float *weight = weight_all ? weight_all + P : nullptr;
+        const int local = cell - cv.base;
+        const int cj = local / wp, ci = local - cj * wp;
         const int x0 = ci, y0 = cj;
         const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
-        const int corner[4] = {y0 * wp + x0, y0 * wp + x1, y1 * wp + x0, y1 * wp + x1};
+        const int corner[4] = {cv.base + y0 * wp + x0, cv.base + y0 * wp + x1, cv.base + y1 * wp + x0,
+                               cv.base + y1 * wp + x1};
         const int xs = cell_start(ci, patch), xe = ci + 1 >= wp ? W : min(W, cell_start(ci + 1, patch));
         const int ys = cell_start(cj, patch), ye = cj + 1 >= hp ? H : min(H, cell_start(cj + 1, patch));
         const int nx = max(0, xe - xs), npx = nx * max(0, ye - ys);
@@ -216,23 +247,29 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
             __syncthreads();
             // Z and H (block A)
             {
-                float z[8][4];
+                // hidden pairs (x, x + 1) packed for fma.rn.f32x2 (each half rounded as a scalar fmaf)
+                f2 z2[4][4];
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
+                for (int x = 0; x < 4; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) z[x][y] = S.b1[j0 + x];
+                    for (int y = 0; y < 4; ++y) z2[x][y] = f2_make(S.b1[j0 + 2 * x], S.b1[j0 + 2 * x + 1]);
 #pragma unroll 4
                 for (int c = 0; c < NF; ++c) {
-                    const float4 wa = *reinterpret_cast<const float4 *>(&S.W1T[c][j0]);
-                    const float4 wb = *reinterpret_cast<const float4 *>(&S.W1T[c][j0 + 4]);
+                    const ulonglong2 wa = *reinterpret_cast<const ulonglong2 *>(&S.W1T[c][j0]);
+                    const ulonglong2 wb = *reinterpret_cast<const ulonglong2 *>(&S.W1T[c][j0 + 4]);
                     const float4 f = *reinterpret_cast<const float4 *>(&S.Fc[c][p0]);
-                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-                    const float fv[4] = {f.x, f.y, f.z, f.w};
+                    const f2 wv[4] = {wa.x, wa.y, wb.x, wb.y};
+                    const f2 fv[4] = {f2_make(f.x, f.x), f2_make(f.y, f.y), f2_make(f.z, f.z), f2_make(f.w, f.w)};
 #pragma unroll
-                    for (int x = 0; x < 8; ++x)
+                    for (int x = 0; x < 4; ++x)
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) z[x][y] = fmaf(wv[x], fv[y], z[x][y]);
+                        for (int y = 0; y < 4; ++y) z2[x][y] = f2_fma(wv[x], fv[y], z2[x][y]);
                 }
+                float z[8][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) f2_split(z2[x][y], z[2 * x][y], z[2 * x + 1][y]);
 #pragma unroll
                 for (int x = 0; x < 8; ++x) {
                     const float4 h4 = make_float4(fmaxf(z[x][0], 0.f), fmaxf(z[x][1], 0.f), fmaxf(z[x][2], 0.f),
@@ -247,21 +284,28 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
             __syncthreads();
             // MH (block A), then the per-pixel partial dot products
             float mh[8][4];
+            {
+                f2 m2[4][4];  // hidden pairs (x, x + 1) for fma.rn.f32x2
 #pragma unroll
-            for (int x = 0; x < 8; ++x)
+                for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) mh[x][y] = 0.f;
-#pragma unroll 2
-            for (int k = 0; k < kLiftHidden; ++k) {
-                const float4 ma = *reinterpret_cast<const float4 *>(&S.M[k][j0]);
-                const float4 mb = *reinterpret_cast<const float4 *>(&S.M[k][j0 + 4]);
-                const float4 h = *reinterpret_cast<const float4 *>(&S.Hh[k][p0]);
-                const float mv[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
-                const float hv[4] = {h.x, h.y, h.z, h.w};
+                    for (int y = 0; y < 4; ++y) m2[x][y] = 0ull;
+#pragma unroll 4
+                for (int k = 0; k < kLiftHidden; ++k) {
+                    const ulonglong2 ma = *reinterpret_cast<const ulonglong2 *>(&S.M[k][j0]);
+                    const ulonglong2 mb = *reinterpret_cast<const ulonglong2 *>(&S.M[k][j0 + 4]);
+                    const float4 h = *reinterpret_cast<const float4 *>(&S.Hh[k][p0]);
+                    const f2 mv[4] = {ma.x, ma.y, mb.x, mb.y};
+                    const f2 hv2[4] = {f2_make(h.x, h.x), f2_make(h.y, h.y), f2_make(h.z, h.z), f2_make(h.w, h.w)};
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
+                    for (int x = 0; x < 4; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) mh[x][y] = fmaf(mv[x], hv[y], mh[x][y]);
+                        for (int y = 0; y < 4; ++y) m2[x][y] = f2_fma(mv[x], hv2[y], m2[x][y]);
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) f2_split(m2[x][y], mh[2 * x][y], mh[2 * x + 1][y]);
             }
             float hv[8][4], ev[8][4];
 #pragma unroll
@@ -347,16 +391,18 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
             if (gram_on) {
 #pragma unroll 2
                 for (int p = 0; p < kFC; ++p) {
-                    const float4 ba = *reinterpret_cast<const float4 *>(&S.bHp[p][gi0]);
-                    const float4 bb = *reinterpret_cast<const float4 *>(&S.bHp[p][gi0 + 4]);
+                    const ulonglong2 ba = *reinterpret_cast<const ulonglong2 *>(&S.bHp[p][gi0]);
+                    const ulonglong2 bb = *reinterpret_cast<const ulonglong2 *>(&S.bHp[p][gi0 + 4]);
                     const float4 ha = *reinterpret_cast<const float4 *>(&S.Hp[p][gj0]);
                     const float4 hc = *reinterpret_cast<const float4 *>(&S.Hp[p][gj0 + 4]);
-                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                    const f2 bv[4] = {ba.x, ba.y, bb.x, bb.y};
                     const float hvv[8] = {ha.x, ha.y, ha.z, ha.w, hc.x, hc.y, hc.z, hc.w};
 #pragma unroll
-                    for (int x = 0; x < 8; ++x)
+                    for (int y = 0; y < 8; ++y) {
+                        const f2 h2 = f2_make(hvv[y], hvv[y]);
 #pragma unroll
-                        for (int y = 0; y < 8; ++y) G[x][y] = fmaf(bv[x], hvv[y], G[x][y]);
+                        for (int x = 0; x < 4; ++x) G2[x][y] = f2_fma(bv[x], h2, G2[x][y]);
+                    }
                 }
             }
             {
@@ -421,13 +467,19 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
     // the CTA's sums
     if (gram_on)
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
             for (int y = 0; y < 8; ++y) {
-                const int i = gi0 + x, j = gj0 + y;
-                if (i <= j) {
-                    atomicAdd(Gb + (size_t)i * kLiftHidden + j, G[x][y]);
-                    if (i != j) atomicAdd(Gb + (size_t)j * kLiftHidden + i, G[x][y]);
+                float g0v, g1v;
+                f2_split(G2[x][y], g0v, g1v);
+                const float gv[2] = {g0v, g1v};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = gi0 + 2 * x + h, j = gj0 + y;
+                    if (i <= j) {
+                        atomicAdd(Gb + (size_t)i * kLiftHidden + j, gv[h]);
+                        if (i != j) atomicAdd(Gb + (size_t)j * kLiftHidden + i, gv[h]);
+                    }
                 }
             }
 #pragma unroll
@@ -465,11 +517,11 @@ __global__ void k_axpy_dev(int n, const float *__restrict__ x, const float *__re
 
 size_t round64(size_t n) { return (n + 63) & ~size_t(63); }
 
-// scratch of one view, in floats
+// scratch of one call, in floats (np: patches of all views)
 struct LiftLayout {
     size_t E, s, M, u, beta, gram, D, alpha, hb, sb, Gb, total;
 };
-LiftLayout lift_layout(size_t hw, size_t np) {
+LiftLayout lift_layout(size_t np) {
     LiftLayout L{};
     size_t o = 0;
     auto take = [&](size_t n) {
@@ -483,7 +535,7 @@ LiftLayout lift_layout(size_t hw, size_t np) {
     L.u = take(kLiftHidden);
     L.beta = take(1);
     L.gram = take(10 * np);
-    // D, alpha, hb, sb: one run, cleared per view
+    // D, alpha, hb, sb: one run, cleared per call
     L.D = o;
     L.alpha = L.D + kLiftHidden * np;
     L.hb = L.alpha + np;
@@ -496,44 +548,46 @@ LiftLayout lift_layout(size_t hw, size_t np) {
 
 }  // namespace
 
-size_t lift_scratch_floats(size_t max_hw, size_t max_np) { return lift_layout(max_hw, max_np).total; }
+size_t lift_scratch_floats(size_t np_total) { return lift_layout(np_total).total; }
 
-// One view: forward, loss and backward.  feat / d_feat: the view's planes
-// [nf][HW]; grid: its patch grid [hp][wp][nh]; weight: its per-pixel weights
-// (null: 1); scratch: lift_scratch_floats(HW, hp * wp) floats.
+// All views at once: forward, loss and backward.  feat / d_feat: the image
+// layout (view v's nf planes at nf * P_v); grid: the views' patch grids
+// concatenated ([np_total][nh], view after view); weight: the per-pixel
+// weights in the depth layout (null: 1); scratch: lift_scratch_floats(np_total).
 // d_w1 [128][nf], d_b1 [128], d_w2 [nh][128], d_b2 [nh] and d_feat are
 // accumulated (may be null: that gradient is skipped).
-cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh, int patch, const float *feat,
-                      const float *grid, int wp, int hp, const float *w1, const float *b1, const float *w2,
-                      const float *b2, float g, const float *weight, float *loss, float *d_w1, float *d_b1,
-                      float *d_w2, float *d_b2, float *d_feat, float *scratch, int *launches) {
-    const int HW = W * H, np = wp * hp;
+cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, int nh, int patch, const float *feat,
+                     const float *grid, const float *w1, const float *b1, const float *w2, const float *b2, float g,
+                     const float *weight, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
+                     float *d_feat, float *scratch, int *launches) {
+    int np = 0;
+    for (int v = 0; v < vt.n; ++v) np += ((vt.v[v].H + patch - 1) / patch) * ((vt.v[v].W + patch - 1) / patch);
     const int NH = kLiftHidden;
-    const LiftLayout L = lift_layout((size_t)HW, (size_t)np);
+    const LiftLayout L = lift_layout((size_t)np);
     float *E = scratch + L.E, *sv = scratch + L.s, *M = scratch + L.M, *u = scratch + L.u, *beta = scratch + L.beta;
     float *gram = scratch + L.gram, *D = scratch + L.D, *alpha = scratch + L.alpha, *hb = scratch + L.hb;
     float *sb = scratch + L.sb, *Gb = scratch + L.Gb;
     const dim3 blk(256);
     cudaError_t e;
-    // per patch and weight-sized: E = G W2 ([np][128]), s = G b2, M = W2^T W2, u = W2^T b2, beta = |b2|^2
-    if ((e = gemm_f32(st, false, false, NH, np, nh, 1.f, w2, NH, grid, nh, 0.f, E, NH, num_sms, launches)) != cudaSuccess) return e;
-    if ((e = gemm_f32(st, true, false, np, 1, nh, 1.f, grid, nh, b2, nh, 0.f, sv, np, num_sms, launches)) != cudaSuccess) return e;
+    // weight-sized: M = W2^T W2, u = W2^T b2, beta = |b2|^2; per patch of every
+    // view: E = G W2 ([np][128]), s = G b2
     if ((e = gemm_f32(st, false, true, NH, NH, nh, 1.f, w2, NH, w2, NH, 0.f, M, NH, num_sms, launches)) != cudaSuccess) return e;
     if ((e = gemm_f32(st, false, false, NH, 1, nh, 1.f, w2, NH, b2, nh, 0.f, u, NH, num_sms, launches)) != cudaSuccess) return e;
     if ((e = gemm_f32(st, true, false, 1, 1, nh, 1.f, b2, nh, b2, nh, 0.f, beta, 1, num_sms, launches)) != cudaSuccess) return e;
-    k_cell_gram<<<(unsigned)((np + 7) / 8), blk, 0, st>>>(grid, wp, hp, nh, gram);
+    if ((e = gemm_f32(st, false, false, NH, np, nh, 1.f, w2, NH, grid, nh, 0.f, E, NH, num_sms, launches)) != cudaSuccess) return e;
+    if ((e = gemm_f32(st, true, false, np, 1, nh, 1.f, grid, nh, b2, nh, 0.f, sv, np, num_sms, launches)) != cudaSuccess) return e;
+    k_cell_gram<<<(unsigned)((np + 7) / 8), blk, 0, st>>>(vt, patch, np, grid, nh, gram);
     ++*launches;
     // the fused kernel adds into D, alpha, hb, sb and Gb
     if ((e = cudaMemsetAsync(D, 0, (L.sb + 1 - L.D) * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Gb, 0, (size_t)NH * NH * sizeof(float), st)) != cudaSuccess) return e;
     const size_t smem = fused_smem_bytes(nf);
     const int grid_ctas = std::max(1, std::min(np, num_sms));
-#define UPS_LIFT(NFV)                                                                                            \
-    do {                                                                                                        \
-        cudaFuncSetAttribute(k_lift_fused<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        k_lift_fused<NFV><<<grid_ctas, kFT, smem, st>>>(W, H, wp, hp, patch, feat, w1, b1, M, E, sv, u, beta,   \
-                                                        gram, weight, g, loss, D, alpha, sb, hb, Gb, d_w1, d_b1, \
-                                                        d_feat);                                                \
+#define UPS_LIFT(NFV)                                                                                              \
+    do {                                                                                                          \
+        cudaFuncSetAttribute(k_lift_fused<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+        k_lift_fused<NFV><<<grid_ctas, kFT, smem, st>>>(vt, np, patch, feat, w1, b1, M, E, sv, u, beta, gram,     \
+                                                        weight, g, loss, D, alpha, sb, hb, Gb, d_w1, d_b1, d_feat); \
     } while (0)
     if (nf == 16)
         UPS_LIFT(16);
@@ -545,7 +599,7 @@ cudaError_t lift_view(int num_sms, cudaStream_t st, int W, int H, int nf, int nh
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d_w2) {
-        // dW2 ([nh][128] row-major = column-major 128 x nh) += D^T-side: D G, Gb W2, hb b2^T
+        // dW2 ([nh][128] row-major = column-major 128 x nh) += D G, Gb W2, hb b2^T
         if ((e = gemm_f32(st, false, true, NH, nh, np, 1.f, D, NH, grid, nh, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
             return e;
         if ((e = gemm_f32(st, false, false, NH, nh, NH, 1.f, Gb, NH, w2, NH, 1.f, d_w2, NH, num_sms, launches)) != cudaSuccess)
