@@ -409,8 +409,9 @@ def roofline(stage, alg, stage_ms, launches, peaks, bf16=False, force_hbm=False)
     a = alg.get(stage, {})
     common = dict(kernel=stage, traffic=None, stage_ms=round(stage_ms, 4),
                   avg_launch_ms=round(stage_ms / max(launches, 1), 4), algorithmic_bytes=a.get("bytes"))
-    if bf16 and not force_hbm and stage in ("decode_fwd", "decode_bwd_rows") and "flops" in a:
-        # BF16 operands on the tcgen05 tensor cores; timed inside a long step
+    if bf16 and not force_hbm and stage == "decode_fwd" and "flops" in a:
+        # BF16 operands on the tcgen05 tensor cores; timed inside a long step (the decode
+        # backward's data path stays FP32 on the CUDA cores in this configuration)
         peak = peaks["bf16_tflops_sustained"]
         ach = a["flops"] / (stage_ms / 1e3) / 1e12
         return dict(common, bound="tensor", achieved=round(ach, 3), peak=round(peak, 1), unit="TFLOP/s",

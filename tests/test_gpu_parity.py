@@ -166,13 +166,13 @@ def test_single_gaussian_peak_alpha():
 # ---------------------------------------------------------------------------
 
 def anchor_case(seed, A, K, nf, cams, weighted=True, lambda_scale=0.01, mask=B.GRAD_ALL, opacity_tanh=False,
-                bias_sigma=0.05):
+                bias_sigma=0.05, bf16=False):
     import torch
     anc = round_dict(scenes.anchors(seed, A, K))
     mlp = round_dict(scenes.mlp_weights(seed + 1, K, nf, bias_sigma=bias_sigma))
     cams = round_cams(cams)
     tg = [round_dict(t) for t in scenes.targets(seed + 2, cams, nf, weighted=weighted)]
-    R = B.Renderer(n_feat=nf, k=K, opacity_tanh=int(opacity_tanh))
+    R = B.Renderer(n_feat=nf, k=K, opacity_tanh=int(opacity_tanh), decode_bf16=int(bf16))
     ad, md = B.anchors_to_device(anc, mlp)
     g = R.decode(ad, md, cams)
     img = R.forward(g, cams)
@@ -247,6 +247,47 @@ def test_anchor_decode_10k_anchors_640x480():
     cams = scenes.cameras(0, 1, 640, 480, 600.0)
     res = anchor_case(0, 10000, 10, 16, cams)
     check_anchor(res, 16)
+
+
+def test_anchor_decode_10k_anchors_640x480_bf16():
+    """The same decode + render case with the BF16 tensor-core decode (FP32
+    accumulation; projection, blending and every gradient FP32): pixels against
+    the oracle's render of the GPU-decoded Gaussians (FP32 bar), and the loss and
+    every gradient group against the FP64 oracle run from the seeded inputs within
+    the stated BF16 bound (5e-2 relative L2; 1e-2 relative for the loss)."""
+    cams = scenes.cameras(0, 1, 640, 480, 600.0)
+    res = anchor_case(0, 10000, 10, 16, cams, bf16=True)
+    nf = 16
+    cam = res["cams"][0]
+    mo = res["g"].mean_opacity[0].cpu().numpy().astype(np.float64)
+    gview = dict(mean=mo[:, :3], opacity=mo[:, 3],
+                 scale=res["g"].scale[0].cpu().numpy().astype(np.float64)[:, :3],
+                 quat=res["g"].quat[0].cpu().numpy().astype(np.float64),
+                 color=res["g"].color[0].cpu().numpy().astype(np.float64)[:, :3],
+                 feat=res["g"].feat[0].cpu().numpy().astype(np.float64))
+    pr = oracle.project(gview, cam, CFG)
+    ref_img = oracle.render(pr, gview, cam, CFG, nf)
+    gpu_views = split_images(res["img"], res["cams"], nf)
+    lst, rng = oracle.tile_lists(pr, cam, CFG)
+    from gpu_cases import last_blended_ids
+    glist = res["R"].copy_buffer(0)
+    grng = res["R"].copy_buffer(2).reshape(-1, 2)
+    ids = [(last_blended_ids(gpu_views[0]["n_contrib"], glist, grng, 0, 0),
+            last_blended_ids(ref_img["n_contrib"], lst, rng))]
+    assert_pixels(gpu_views, [ref_img], nf, feat_mag=[feat_magnitude(pr, gview, cam, nf)], last_ids=ids)
+    assert abs(res["loss"] - res["L"]) <= 1e-2 * abs(res["L"]), (res["loss"], res["L"])
+    errs = {}
+    gg = gauss_grads(res["grad"], nf, 1)
+    for k in ("mean", "scale", "quat", "opacity", "color", "feat"):
+        ref = np.stack([pv["g3d"][k] for pv in res["per_view"]])
+        errs["g3d_" + k] = rel_l2(gg[k], ref)
+    for k in ("w1", "b1", "w2", "b2"):
+        errs["mlp_" + k] = rel_l2(res["d_mlp"][k], res["ref"][k])
+    for k in ("pos", "feat", "offsets", "scaling"):
+        errs["anchor_" + k] = rel_l2(res["d_anc"][k], res["ref"][k])
+    errs["pose"] = rel_l2(res["d_pose"], res["ref"]["pose"])
+    print("bf16 decode, 10k anchors x 10, 640x480: gradient rel L2 vs FP64 oracle", errs)
+    assert all(e < 5e-2 for e in errs.values()), errs
 
 
 # ---------------------------------------------------------------------------
