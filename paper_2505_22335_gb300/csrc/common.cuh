@@ -56,7 +56,6 @@ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int t) {
 // host-side helpers (implemented in ctx.cu)
 // ---------------------------------------------------------------------------
 
-// Device buffer that only grows.
 // Packed pairs of f32 (first element in the low half) for fma.rn.f32x2: two
 // channels per instruction, each rounded exactly as a scalar fmaf.
 typedef unsigned long long f2;
@@ -68,6 +67,11 @@ __device__ __forceinline__ f2 f2_make(float a, float b) {
 __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
     f2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ float f2_lo(f2 a) {
@@ -84,6 +88,7 @@ __device__ __forceinline__ void f2_split(f2 a, float &lo, float &hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
 }
 
+// Device buffer that only grows.
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;

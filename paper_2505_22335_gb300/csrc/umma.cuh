@@ -38,6 +38,22 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t kbytes) {
     return d;
 }
 
+// K-major operand in the 64-byte swizzle layout, as a tiled TMA load with
+// 64-byte swizzle writes it: rows of 64 bytes (16 TF32 values of K), 8-row
+// groups 512 bytes apart (SBO), the 16-byte chunks of row r permuted by XOR
+// with (r / 2) % 4 (bits 4-5 of the address XOR bits 7-8).  Operand bases are
+// 512-byte aligned; a K step inside the 64-byte row advances the start
+// address by its byte offset.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                // LBO: unused for a swizzled K-major operand one atom wide
+    d |= (uint64_t)((512 >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                // descriptor version
+    d |= (uint64_t)4 << 61;                // layout: 64-byte swizzle
+    return d;
+}
+
 enum Kind { kBF16 = 0, kTF32 = 1 };
 
 __host__ __device__ constexpr uint32_t idesc(Kind kind, int M, int N) {
@@ -79,6 +95,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int l
                      : "=r"(done)
                      : "r"(smem_addr(mbar)), "r"(parity));
     return done != 0;
+}
+
+// bulk copy (TMA, untiled) global -> shared, completing `bytes` of the
+// transaction count of *mbar; both addresses 16-byte aligned, bytes a multiple
+// of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+// arrive on *mbar (one of its expected arrivals) and add `bytes` to the
+// transaction count of the current phase
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// tiled TMA load of the box at (x, y) of a 2D tensor map (a kernel parameter
+// declared __grid_constant__) into shared memory, completing on *mbar
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }

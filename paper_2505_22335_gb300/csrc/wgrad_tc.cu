@@ -9,18 +9,27 @@
 //   db2[o] = sum of DY[o] over rows (CUDA cores, while the operands are split)
 // D_w2 keeps all four MLPs' hidden units as one M = 128 operand, so only the
 // diagonal 32 x n_g blocks are used: fewer, wider MMAs (N up to 256) instead
-// of one narrow MMA per (output tile, group).
+// of one narrow MMA per (output tile, group).  The B operands' padding rows
+// (DY past n_out, X past 40) hold whatever features follow in the scratch;
+// they only reach D columns that are not read.
 //
 // Each operand value x is split into hi = tf32(x) and lo = tf32(x - hi); the
 // products hi*hi + hi*lo + lo*hi recover FP32 accuracy (the dropped lo*lo term
 // is about 2^-22 relative), with FP32 accumulation in TMEM.
 //
-// Warp roles (one CTA per SM, persistent over chunks): warps 0-14 load a
-// chunk's 16-row slice of every scratch feature (the next chunk's loads are
-// in flight while the current one is split), split it and store hi and lo as
-// canonical K-major no-swizzle operand tiles, then arrive on the stage's
-// `full` mbarrier; warp 15 waits for `full`, issues the MMAs and commits them
-// to the stage's `empty` mbarrier.  Three stages (two for the widest outputs).
+// A chunk's operands arrive by tiled TMA loads with 64-byte swizzle (one box
+// of 16 rows x up to 256 features per operand region), already in the K-major
+// layout the MMAs read; rows past the launch's end read as zero.
+// Warp roles (one CTA per SM, persistent over chunks): warp 16 issues a
+// chunk's loads into a free stage (waiting on the stage's `empty` barrier,
+// completing on `loaded`); warps 0-14 wait for `loaded`, split each value in
+// place (hi) and into the stage's lo tile set, then arrive on `full`; warp 15
+// waits for `full`, issues the MMAs and commits them to `empty`.  Three
+// stages (two for the widest outputs): the loads of the next chunks are in
+// flight while one chunk is split and multiplied.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "decode_bwd.cuh"
@@ -35,83 +44,63 @@ using dbwd::kDin;
 using dbwd::kH;
 using dbwd::kXW;
 
-// 15 converter warps + the MMA warp: 512 threads at up to 128 registers
+// 15 converter warps + the MMA warp + the load warp
 constexpr int kConv = 480;            // converter threads (warps 0-14)
-constexpr int kT = kConv + 32;        // + the MMA warp
+constexpr int kMmaTid = kConv;        // lane 0 of warp 15
+constexpr int kLoadTid = kConv + 32;  // lane 0 of warp 16
+constexpr int kT = kConv + 64;
 constexpr int kKR = 16;               // rows per chunk (2 TF32 K steps)
-constexpr int kRowBytes = kKR * 4;    // bytes of one operand row per chunk
-constexpr int kNX = 48;               // X operand rows (40 + zero padding)
+constexpr int kRowBytes = kKR * 4;    // bytes of one operand row per chunk (one swizzle row)
+constexpr int kNX = 48;               // X operand rows (40 + padding)
+constexpr int kDyBox = 256;           // DY operand rows per load and MMA (the last may be narrower)
 constexpr int kMaxNB = 464;           // DY operand rows: D_w2 + D_w1 <= 512 TMEM columns
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxStages = 3;
-constexpr int kMaxItems = 7;          // (feature, quad) items per converter thread
+constexpr int kMaxItems = 7;          // float4 items per converter thread and chunk
 constexpr int kWait = 1 << 22;
 
+// One chunk's operand tile set (bytes; every region 512-byte aligned).
 struct WLay {
-    int n_out, nb;       // DY rows, padded to 16 (MMA N granularity)
-    int oA_h, oB_dy, oA_dz, oB_x, set_bytes;  // byte offsets in one (hi or lo) operand set
-    int f_dz, f_h, f_x, f_end;  // item feature space: DY [0, nb), DZ, H, X (each a multiple of 8)
-    int stages;                 // 3, or 2 where three do not fit
+    int n_out;
+    int ndy, wlast, nb;             // DY: ndy boxes, the last wlast rows wide; nb rows in all
+    int oA_h, oB_dy, oA_dz, oB_x;   // region offsets
+    int block_bytes;                // bytes the loads of one chunk bring
+    int set_bytes;                  // block_bytes rounded up to 1 KB
+    int stages;                     // 3, or 2 where three do not fit
 };
 
 __host__ __device__ inline WLay wlay(int K, int NF) {
     WLay w{};
     w.n_out = dbwd::n_out(K, NF);
-    w.nb = (w.n_out + 15) & ~15;
-    int o = 0;
-    w.oA_h = o;
-    o += 128 * kRowBytes;
-    w.oB_dy = o;
-    o += w.nb * kRowBytes;
-    w.oA_dz = o;
-    o += 128 * kRowBytes;
-    w.oB_x = o;
-    o += kNX * kRowBytes;
-    w.set_bytes = (o + 1023) & ~1023;
-    w.f_dz = w.nb;
-    w.f_h = w.f_dz + 128;
-    w.f_x = w.f_h + 128;
-    w.f_end = w.f_x + kXW;
+    w.ndy = (w.n_out + kDyBox - 1) / kDyBox;
+    w.wlast = ((w.n_out - kDyBox * (w.ndy - 1)) + 15) & ~15;
+    w.nb = kDyBox * (w.ndy - 1) + w.wlast;
+    w.oA_h = 0;
+    w.oB_dy = 128 * kRowBytes;
+    w.oA_dz = w.oB_dy + w.nb * kRowBytes;
+    w.oB_x = w.oA_dz + 128 * kRowBytes;
+    w.block_bytes = w.oB_x + kNX * kRowBytes;
+    w.set_bytes = (w.block_bytes + 1023) & ~1023;
     w.stages = 2 * w.set_bytes * 3 + 1024 <= 227 * 1024 ? 3 : 2;
     return w;
 }
 
 __host__ __device__ inline bool wlay_ok(const WLay &w) {
     return w.nb <= kMaxNB && 2 * w.set_bytes * w.stages + 1024 <= 227 * 1024 &&
-           4 * w.f_end <= kMaxItems * kConv;
+           w.block_bytes / 16 <= kMaxItems * kConv;
 }
-
-// byte offset of core-matrix row (operand row m, K quad q) in a K-major
-// operand of 16 TF32 K elements per row
-__device__ __forceinline__ int cm_off(int m, int q) { return ((m >> 3) * 4 + q) * 128 + (m & 7) * 16; }
 
 struct WTArgs {
     int nrows, K, NF;
-    const float *scratch;  // X [40][ld], H [128][ld], DY [n_out][ld], DZ [128][ld]
-    int ld;
     float *g_w1, *g_b1, *g_w2, *g_b2;
     int *err;
 };
 
-// Item i of a chunk: feature f = 8 (i >> 5) + (i & 7), row quad q = (i >> 3) & 3,
-// so the 8 lanes of a quarter warp store 8 different operand rows of one
-// core-matrix column (all banks once) and a warp reads 8 features x 64 bytes.
-__device__ __forceinline__ int item_feature(int i) { return 8 * (i >> 5) + (i & 7); }
-__device__ __forceinline__ int item_quad(int i) { return (i >> 3) & 3; }
-
-// scratch row of item feature f (-1: DY padding, nothing to load)
-__device__ __forceinline__ int item_row(const WLay &w, int f) {
-    if (f < w.f_dz) return f < w.n_out ? kXW + 128 + f : -1;  // DY
-    if (f < w.f_h) return kXW + 128 + w.n_out + (f - w.f_dz);  // DZ
-    if (f < w.f_x) return kXW + (f - w.f_h);                    // H
-    return f - w.f_x;                                            // X
-}
-
-__device__ __forceinline__ int item_off(const WLay &w, int f, int q) {
-    if (f < w.f_dz) return w.oB_dy + cm_off(f, q);
-    if (f < w.f_h) return w.oA_dz + cm_off(f - w.f_dz, q);
-    if (f < w.f_x) return w.oA_h + cm_off(f - w.f_h, q);
-    return w.oB_x + cm_off(f - w.f_x, q);
+// output index of the DY operand row holding the 16-byte item at byte offset
+// `off` of a tile set (-1: not in the DY region)
+__device__ __forceinline__ int dy_output_at(const WLay &w, int off) {
+    if (off < w.oB_dy || off >= w.oA_dz) return -1;
+    return (off - w.oB_dy) / kRowBytes;  // DY boxes are adjacent: row o of box j is output 256 j + o
 }
 
 __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, int off, float4 v) {
@@ -128,62 +117,33 @@ __device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo
     *reinterpret_cast<float4 *>(lo + off) = l;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(mbar)) : "memory");
-}
+// Tensor maps over the scratch (rows x features, 64-byte swizzle): boxes of
+// 16 rows x 48 (X), 128 (H, DZ), 256 and the last width (DY) features.
+struct WMaps {
+    CUtensorMap x, h, dy, dy_last;
+};
 
-// this converter thread's items of the chunk starting at row r0 (rows at or
-// past nrows and DY padding read as zero)
-__device__ __forceinline__ void load_items(const WTArgs &a, const WLay &w, int r0, float4 (&v)[kMaxItems]) {
-    const int nitems = 4 * w.f_end;
-#pragma unroll
-    for (int k = 0; k < kMaxItems; ++k) {
-        const int i = threadIdx.x + kConv * k;
-        v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < nitems) {
-            const int row = item_row(w, item_feature(i));
-            if (row >= 0) {
-                const float *src = a.scratch + (size_t)row * a.ld;
-                const int rr = r0 + 4 * item_quad(i);
-                if (rr + 4 <= a.nrows) {
-                    v[k] = __ldg(reinterpret_cast<const float4 *>(src + rr));
-                } else {
-                    v[k].x = rr < a.nrows ? src[rr] : 0.f;
-                    v[k].y = rr + 1 < a.nrows ? src[rr + 1] : 0.f;
-                    v[k].z = rr + 2 < a.nrows ? src[rr + 2] : 0.f;
-                    v[k].w = rr + 3 < a.nrows ? src[rr + 3] : 0.f;
-                }
-            }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+__global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(const __grid_constant__ WMaps maps, WTArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t loaded[kMaxStages], full[kMaxStages], empty[kMaxStages];
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
+    __shared__ int abort_flag, n_issued, n_mma;
+    // operand regions on 1 KB boundaries (the swizzle pattern repeats every 512 bytes)
+    unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const WLay w = wlay(a.K, a.NF);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nchunks = (a.nrows + kKR - 1) / kKR;
     const int nmine = nchunks > (int)blockIdx.x ? (nchunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    // zero the padding rows of every stage: DY rows [n_out, nb), X rows [40, 48)
-    const int npad_dy = w.nb - w.n_out, npad = npad_dy + (kNX - kXW);
     const int S = w.stages;
-    for (int s = 0; s < S; ++s)
-        for (int i = tid; i < 4 * npad; i += kT) {
-            const int r = i >> 2, q = i & 3;
-            const int off = r < npad_dy ? w.oB_dy + cm_off(w.n_out + r, q) : w.oB_x + cm_off(kXW + r - npad_dy, q);
-            unsigned char *hi = smem + (size_t)s * 2 * w.set_bytes;
-            *reinterpret_cast<float4 *>(hi + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4 *>(hi + w.set_bytes + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
+            mbar_init(&loaded[s], 1);
             mbar_init(&full[s], kConv);
             mbar_init(&empty[s], 1);
         }
         abort_flag = 0;
+        n_issued = 0;
+        n_mma = 0;
     }
     if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
     fence_before();
@@ -195,15 +155,13 @@ __global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
 
     if (warp < kConv / 32) {
         // ---------------- converters
-        const int nitems = 4 * w.f_end;
-        float4 v[kMaxItems];
+        const int nitems = w.block_bytes / 16;
         float bs[kMaxItems];  // db2 partial sums of this thread's DY items
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) bs[k] = 0.f;
-        if (nmine > 0) load_items(a, w, (int)blockIdx.x * kKR, v);
         for (int it = 0; it < nmine; ++it) {
             const int s = it % S, use = it / S;
-            if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), kWait)) {
+            if (!mbar_wait(&loaded[s], (uint32_t)(use & 1), kWait)) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
@@ -213,28 +171,28 @@ __global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
             for (int k = 0; k < kMaxItems; ++k) {
                 const int i = tid + kConv * k;
                 if (i < nitems) {
-                    const int f = item_feature(i);
-                    if (f < w.n_out || f >= w.f_dz) split_store(hi, lo, item_off(w, f, item_quad(i)), v[k]);
-                    if (f < w.f_dz) bs[k] += (v[k].x + v[k].y) + (v[k].z + v[k].w);
+                    const float4 v = *reinterpret_cast<const float4 *>(hi + 16 * i);
+                    split_store(hi, lo, 16 * i, v);
+                    bs[k] += (v.x + v.y) + (v.z + v.w);
                 }
             }
             fence_async_smem();
             mbar_arrive(&full[s]);
-            if (it + 1 < nmine) load_items(a, w, ((int)blockIdx.x + (it + 1) * (int)gridDim.x) * kKR, v);
         }
-        // db2: the four quads of a feature sit in lanes l, l + 8, l + 16, l + 24
+        // db2: the four 16-byte items of a DY operand row (64 bytes, its 16
+        // rows of the chunk in some order) sit in lanes 4 l .. 4 l + 3
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k) {
             float t = bs[k];
-            t += __shfl_xor_sync(0xffffffffu, t, 8);
-            t += __shfl_xor_sync(0xffffffffu, t, 16);
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
             const int i = tid + kConv * k;
-            if (i < nitems && item_quad(i) == 0 && nmine > 0) {
-                const int f = item_feature(i);
-                if (f < w.n_out) atomicAdd(a.g_b2 + f, t);
+            if (i < nitems && (i & 3) == 0 && nmine > 0) {
+                const int o = dy_output_at(w, 16 * i);
+                if (o >= 0 && o < w.n_out) atomicAdd(a.g_b2 + o, t);
             }
         }
-    } else if (tid == kConv) {
+    } else if (tid == kMmaTid) {
         // ---------------- MMA issue (one thread of warp 15)
         const uint32_t id_w1 = idesc(kTF32, 128, kNX);
         for (int it = 0; it < nmine; ++it) {
@@ -250,29 +208,56 @@ __global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
                 const uint32_t ab = pass == 2 ? lb : hb, bb = pass == 1 ? lb : hb;
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint32_t acc = (it == 0 && pass == 0 && ks == 0) ? 0u : 1u;
-                    const uint32_t ka = 256u * ks;
-                    for (int n0 = 0; n0 < w.nb; n0 += 256) {
-                        const int n = min(256, w.nb - n0);
-                        mma<kTF32>(tmem + cW2 + n0, desc(ab + w.oA_h + ka, kRowBytes),
-                                   desc(bb + w.oB_dy + n0 * kRowBytes + ka, kRowBytes), idesc(kTF32, 128, n), acc);
+                    const uint32_t ka = 32u * ks;  // 8 TF32 values of K
+                    for (int j = 0; j < w.ndy; ++j) {
+                        const int n = j + 1 < w.ndy ? kDyBox : w.wlast;
+                        mma<kTF32>(tmem + cW2 + kDyBox * j, desc_sw64(ab + w.oA_h + ka),
+                                   desc_sw64(bb + w.oB_dy + kDyBox * kRowBytes * j + ka), idesc(kTF32, 128, n), acc);
                     }
-                    mma<kTF32>(tmem + cW1, desc(ab + w.oA_dz + ka, kRowBytes), desc(bb + w.oB_x + ka, kRowBytes),
-                               id_w1, acc);
+                    mma<kTF32>(tmem + cW1, desc_sw64(ab + w.oA_dz + ka), desc_sw64(bb + w.oB_x + ka), id_w1, acc);
                 }
             }
             commit(&empty[s]);
+            n_mma = it + 1;
+        }
+    } else if (tid == kLoadTid) {
+        // ---------------- tiled loads (one thread of warp 16)
+        const int fH = kXW, fDY = kXW + 128, fDZ = kXW + 128 + w.n_out;  // first scratch feature of each region
+        for (int it = 0; it < nmine; ++it) {
+            const int s = it % S, use = it / S;
+            if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), kWait)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            const int r0 = ((int)blockIdx.x + it * (int)gridDim.x) * kKR;
+            unsigned char *hi = smem + (size_t)s * 2 * w.set_bytes;
+            mbar_arrive_expect(&loaded[s], (uint32_t)w.block_bytes);
+            tma_load_2d(hi + w.oB_x, &maps.x, r0, 0, &loaded[s]);
+            tma_load_2d(hi + w.oA_h, &maps.h, r0, fH, &loaded[s]);
+            for (int j = 0; j < w.ndy; ++j)
+                tma_load_2d(hi + w.oB_dy + kDyBox * kRowBytes * j, j + 1 < w.ndy ? &maps.dy : &maps.dy_last, r0,
+                            fDY + kDyBox * j, &loaded[s]);
+            tma_load_2d(hi + w.oA_dz, &maps.h, r0, fDZ, &loaded[s]);
+            n_issued = it + 1;
         }
     }
     __syncthreads();
-    // all MMAs done: the last use of each stage completed
-    if (tid == 0 && !abort_flag) {
-        for (int s = 0; s < S && s < nmine; ++s) {
-            const int last_use = (nmine - 1 - s) / S;
-            if (!mbar_wait(&empty[s], (uint32_t)(last_use & 1), kWait)) {
-                abort_flag = 1;
-                break;
+    // Before the TMEM reads (and before exit): every issued load has landed
+    // and every issued MMA has completed, each waited for (bounded) through
+    // the last use of its stage.
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            if (s < n_issued) {
+                const int last = (n_issued - 1 - s) / S;
+                if (!mbar_wait(&loaded[s], (uint32_t)(last & 1), kWait)) abort_flag = 1;
+            }
+            if (s < n_mma) {
+                const int last = (n_mma - 1 - s) / S;
+                if (!mbar_wait(&empty[s], (uint32_t)(last & 1), kWait)) abort_flag = 1;
             }
         }
+        if (n_mma < nmine) abort_flag = 1;
     }
     __syncthreads();
     fence_after();
@@ -313,6 +298,35 @@ __global__ void __launch_bounds__(kT, 1) k_decode_wgrad_tc(WTArgs a) {
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// the driver's tensor-map encoder, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// rows x features view of the feature-major scratch (feature f of row r at
+// [f * ld + r]); boxes of 16 rows x box_f features, 64-byte swizzle, rows
+// past nrows and features past nfeat read as zero
+bool make_map(CUtensorMap *m, const float *scratch, int ld, int nrows, int nfeat, int box_f) {
+    const auto fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nrows, (cuuint64_t)nfeat};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kKR, (cuuint32_t)box_f};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(scratch), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool decode_wgrad_tc_fits(int K, int NF) { return wlay_ok(wlay(K, NF)); }
@@ -321,12 +335,22 @@ cudaError_t launch_decode_wgrad_tc(const float *scratch, int ld, int nrows, int 
                                    int *err, int num_sms, cudaStream_t st) {
     const WLay w = wlay(K, NF);
     if (!wlay_ok(w)) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)2 * w.set_bytes * w.stages;
-    WTArgs a{nrows, K, NF, scratch, ld, d_mlp.w1, d_mlp.b1, d_mlp.w2, d_mlp.b2, err};
+    if (nrows <= 0) return cudaSuccess;
+    // TMA: 16-byte aligned base and row stride
+    if ((reinterpret_cast<uintptr_t>(scratch) & 15) != 0 || (ld & 3) != 0 || ld < nrows)
+        return cudaErrorInvalidValue;
+    const int nfeat = kXW + 128 + w.n_out + 128;
+    WMaps maps;
+    if (!make_map(&maps.x, scratch, ld, nrows, nfeat, kNX) || !make_map(&maps.h, scratch, ld, nrows, nfeat, 128) ||
+        !make_map(&maps.dy, scratch, ld, nrows, nfeat, kDyBox) ||
+        !make_map(&maps.dy_last, scratch, ld, nrows, nfeat, w.wlast))
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * w.set_bytes * w.stages + 1024;
+    WTArgs a{nrows, K, NF, d_mlp.w1, d_mlp.b1, d_mlp.w2, d_mlp.b2, err};
     const int chunks = (nrows + kKR - 1) / kKR;
     const int blocks = std::max(1, std::min(chunks, num_sms));
     cudaFuncSetAttribute(k_decode_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_decode_wgrad_tc<<<blocks, kT, smem, st>>>(a);
+    k_decode_wgrad_tc<<<blocks, kT, smem, st>>>(maps, a);
     return cudaGetLastError();
 }
 
