@@ -162,8 +162,19 @@ __device__ __forceinline__ void load_weights_T(const DecodeArgs &a, float *sW1T,
     for (int i = threadIdx.x; i < a.n_out; i += blockDim.x) sb2[i] = a.b2[i];
 }
 
+// forward decode: rows (threads) per CTA and resident CTAs per SM (its grid);
+// 2 x 384 (24 warps at 80 registers) measured 0.90 ms against 0.95 for 4 x 128
+// and 0.93 for 3 x 256 on the bench workload
+#ifndef UPS_DECF_THREADS
+#define UPS_DECF_THREADS 384
+#endif
+#ifndef UPS_DECF_CTAS
+#define UPS_DECF_CTAS 2
+#endif
+constexpr int kFwdThreads = UPS_DECF_THREADS, kFwdCtas = UPS_DECF_CTAS;
+
 template <int NF>
-__global__ void __launch_bounds__(128) k_decode_fwd(ViewTable vt, DecodeArgs a,
+__global__ void __launch_bounds__(kFwdThreads, kFwdCtas) k_decode_fwd(ViewTable vt, DecodeArgs a,
                                                     float4 *__restrict__ mean_op,
                                                     float4 *__restrict__ scale_out,
                                                     float4 *__restrict__ quat_out,
@@ -289,7 +300,7 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
     // dL/dG of Gaussian k for this group, loaded one Gaussian ahead so the
     // loads of k + 1 are in flight while k is processed
     constexpr int NQ = G == 3 ? (NF / 4 > 0 ? NF / 4 : 1) : 2;
-    constexpr bool kAhead = NQ <= 4;
+    constexpr bool kAhead = UPS_DECB_AHEAD && NQ <= 4;
     auto load = [&](int k, float4 (&q)[NQ]) {
         const size_t gi = gbase + k;
 #pragma unroll
@@ -388,14 +399,14 @@ __device__ __forceinline__ void bwd_group(const dbwd::Args &a, const DecodeArgs 
         float s0, s1, s2, s3;
         f2_split(a01, s0, s1);
         f2_split(a23, s2, s3);
-        sDX[i * dbwd::kRowsPerBlock] += (s0 + s1) + (s2 + s3);
+        sDX[i * dbwd::kRowsFp32] += (s0 + s1) + (s2 + s3);
     }
 }
 
 // One thread per row (anchor-major), 128 rows per step of a grid-stride loop;
 // weights in shared memory read as broadcasts.
 template <int NF>
-__global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_decode_bwd_rows(ViewTable vt,
+__global__ void __launch_bounds__(dbwd::kRowsFp32, dbwd::kRowsCtasPerSm) k_decode_bwd_rows(ViewTable vt,
                                                                                                dbwd::Args a) {
     extern __shared__ float4 smem4[];
     __shared__ float aPose[3 * UPS_MAX_VIEWS];
@@ -412,8 +423,8 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_d
     __syncthreads();
     const size_t NG = (size_t)a.A * a.K;
     float *sDX = sDXall + threadIdx.x;
-    for (int base = a.row_begin + blockIdx.x * dbwd::kRowsPerBlock; base < a.row_end;
-         base += gridDim.x * dbwd::kRowsPerBlock) {
+    for (int base = a.row_begin + blockIdx.x * dbwd::kRowsFp32; base < a.row_end;
+         base += gridDim.x * dbwd::kRowsFp32) {
         const int row = base + threadIdx.x;
         const bool valid = row < a.row_end;
         const int an = valid ? row / V : 0, v = valid ? row - an * V : 0;
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_d
         }
         const float xt[6] = {x[kFin], x[kFin + 1], x[kFin + 2], x[kFin + 3], x[kFin + 4], x[kFin + 5]};
 #pragma unroll
-        for (int i = 0; i < kDX; ++i) sDX[i * dbwd::kRowsPerBlock] = 0.f;
+        for (int i = 0; i < kDX; ++i) sDX[i * dbwd::kRowsFp32] = 0.f;
         float dls[3] = {0.f, 0.f, 0.f};
         bwd_group<0, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
         bwd_group<1, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
@@ -437,7 +448,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_d
         if (NF > 0) bwd_group<3, NF>(a, da, sW1T, sb1, sW2, sb2, xt, an, valid, gbase, lr, sDX, dls);
         float dx[kDX];
 #pragma unroll
-        for (int i = 0; i < kDX; ++i) dx[i] = sDX[i * dbwd::kRowsPerBlock];
+        for (int i = 0; i < kDX; ++i) dx[i] = sDX[i * dbwd::kRowsFp32];
         dbwd::row_epilogue(a, valid ? an : -1, v, gbase, dx, delta, dist, dls, aPose);
     }
     __syncthreads();
@@ -446,7 +457,7 @@ __global__ void __launch_bounds__(dbwd::kRowsPerBlock, dbwd::kRowsCtasPerSm) k_d
 
 // shared memory of the backward rows kernel
 size_t bwd_rows_smem(int n_out) {
-    return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + ((n_out + 3) & ~3) + kDX * dbwd::kRowsPerBlock);
+    return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + ((n_out + 3) & ~3) + kDX * dbwd::kRowsFp32);
 }
 
 size_t fwd_smem(int n_out) { return sizeof(float) * (kDin * 4 * kH + 4 * kH + n_out * kH + n_out); }
@@ -460,12 +471,12 @@ cudaError_t launch_decode_bwd_rows_fp32(const ViewTable &vt, const dbwd::Args &a
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     const int rows = a.row_end - a.row_begin;
     const int blocks = std::max(
-        1, std::min((rows + dbwd::kRowsPerBlock - 1) / dbwd::kRowsPerBlock, num_sms * dbwd::kRowsCtasPerSm));
+        1, std::min((rows + dbwd::kRowsFp32 - 1) / dbwd::kRowsFp32, num_sms * dbwd::kRowsCtasPerSm));
 #define UPS_DECB(NFV)                                                                              \
     do {                                                                                           \
         cudaFuncSetAttribute(k_decode_bwd_rows<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                              (int)smem);                                                           \
-        k_decode_bwd_rows<NFV><<<blocks, dbwd::kRowsPerBlock, smem, st>>>(vt, a);                  \
+        k_decode_bwd_rows<NFV><<<blocks, dbwd::kRowsFp32, smem, st>>>(vt, a);                  \
     } while (0)
     switch (a.NF) {
         case 0: UPS_DECB(0); break;
@@ -485,12 +496,12 @@ cudaError_t launch_decode_fwd(const ViewTable &vt, int A, int K, int NF, const u
     size_t smem = fwd_smem(a.n_out);
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     int rows = A * vt.n;
-    int blocks = std::max(1, std::min((rows + 127) / 128, num_sms * 4));
+    int blocks = std::max(1, std::min((rows + kFwdThreads - 1) / kFwdThreads, num_sms * kFwdCtas));
 #define UPS_DEC(NFV)                                                                        \
     do {                                                                                    \
         cudaFuncSetAttribute(k_decode_fwd<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)smem);                                                    \
-        k_decode_fwd<NFV><<<blocks, 128, smem, st>>>(                                       \
+        k_decode_fwd<NFV><<<blocks, kFwdThreads, smem, st>>>(                               \
             vt, a, reinterpret_cast<float4 *>(out.mean_opacity),                            \
             reinterpret_cast<float4 *>(out.scale), reinterpret_cast<float4 *>(out.quat),    \
             reinterpret_cast<float4 *>(out.color), out.feat);                               \

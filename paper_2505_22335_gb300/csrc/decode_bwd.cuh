@@ -17,8 +17,22 @@ constexpr int kH = 32;        // hidden width of each MLP
 constexpr int kFin = 32;      // anchor feature width
 constexpr int kDin = kFin + 6;
 constexpr int kXW = 40;       // stored input width: x[0..37], x[38] = 1 (db1 column), x[39] = 0
-constexpr int kRowsPerBlock = 128;  // per-row kernels: one thread per row
-constexpr int kRowsCtasPerSm = 3;   // FP32 per-row kernel: resident CTAs per SM (its grid)
+constexpr int kRowsPerBlock = 128;  // tcgen05 per-row kernel: one thread (TMEM lane) per row
+// FP32 per-row kernel shape: 2 CTAs of 256 rows per SM (16 warps at 128
+// registers, some spilled) beat 3 CTAs of 128 (12 warps at 168 registers:
+// 1.73 ms) at 1.54 ms on the bench workload; with 16 warps the dL/dG loads
+// need no software prefetch (UPS_DECB_AHEAD 1: 1.57 ms).
+#ifndef UPS_DECB_ROWS
+#define UPS_DECB_ROWS 256
+#endif
+#ifndef UPS_DECB_CTAS
+#define UPS_DECB_CTAS 2
+#endif
+#ifndef UPS_DECB_AHEAD
+#define UPS_DECB_AHEAD 0  // dL/dG of Gaussian k + 1 loaded while k is processed
+#endif
+constexpr int kRowsFp32 = UPS_DECB_ROWS;       // FP32 per-row kernel: rows (threads) per CTA
+constexpr int kRowsCtasPerSm = UPS_DECB_CTAS;  // FP32 per-row kernel: resident CTAs per SM (its grid)
 
 __host__ __device__ inline int n_out(int K, int NF) { return K * (11 + NF); }
 // group g: outputs per Gaussian and first output row (opacity, covariance,

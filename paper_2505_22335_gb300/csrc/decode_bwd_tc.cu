@@ -688,8 +688,8 @@ static int rows_tc_per_sm(int NF, int K) {
 }
 
 int decode_bwd_rows_wave(int bf16, int K, int NF, int num_sms) {
-    const int ctas = bf16 ? rows_tc_per_sm(NF, K) : dbwd::kRowsCtasPerSm;
-    return std::max(1, num_sms) * ctas * dbwd::kRowsPerBlock;
+    if (bf16) return std::max(1, num_sms) * rows_tc_per_sm(NF, K) * dbwd::kRowsPerBlock;
+    return std::max(1, num_sms) * dbwd::kRowsCtasPerSm * dbwd::kRowsFp32;
 }
 
 cudaError_t launch_decode_bwd_rows_tc(const ViewTable &vt, const dbwd::Args &a, int num_sms, cudaStream_t st) {
