@@ -57,7 +57,7 @@ size_t lift_scratch_floats(size_t np_total);
 cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, int nh, int patch, const float *feat,
                      const float *grid, const float *w1, const float *b1, const float *w2, const float *b2, float g,
                      const float *weight, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
-                     float *d_feat, float *scratch, int *launches);
+                     float *d_feat, float *scratch, int *err, int *launches);
 cudaError_t launch_uncertainty(const ViewTable &vt, int n_feat, int max_hw, float lc, float ld, float lf,
                                float t_mask, const ups_images &img, const ups_targets &tgt, float *R, float *sigma2,
                                uint8_t *motion, cudaStream_t st);
@@ -852,7 +852,7 @@ ups_status ups_feature_lift(ups_ctx *c, const ups_lift_cfg *lcfg, const float *f
     UPS_CUDA(c, lift_all(c->num_sms, st, c->vt, nf, lcfg->n_h, lcfg->patch, feat, dino, mlp->w1, mlp->b1, mlp->w2,
                          mlp->b2, g, weight, loss_dev, d_mlp ? d_mlp->w1 : nullptr, d_mlp ? d_mlp->b1 : nullptr,
                          d_mlp ? d_mlp->w2 : nullptr, d_mlp ? d_mlp->b2 : nullptr, d_feat, c->lift_scr.as<float>(),
-                         &launches));
+                         c->d_err, &launches));
     stage_end(c, st, launches);
     return UPS_OK;
 }

@@ -20,13 +20,16 @@
 // Every per-pixel quantity is 128 wide: ~80 kFLOP per pixel instead of
 // ~310 k, and no N_h-wide per-pixel array.
 //
-// The pixel-sized products (F~ W1^T, H M, (bH)^T H and the two backward
-// products with W1) run as cuBLAS TF32 GEMMs on the planar image layout
-// (channel c of pixel p at [c * HW + p] is a column-major HW x C matrix); the
-// small per-patch and weight-sized ones in FP32 (pedantic); one kernel per
-// cell of pixels sharing their four patches does the cosine, the loss, dL/dZ
-// and the per-patch sums.
+// Every pixel-sized product (F~ W1^T, M H, the Gram of b H over pixels and
+// the two backward products with W1) runs inside one fused FP32 kernel
+// (k_lift_fused) over the cells of pixels that share their four patches: the
+// 128-wide per-pixel quantities stay in shared memory, and the kernel also
+// does the cosine, the loss, dL/dZ and the per-patch sums.  The per-patch and
+// weight-sized products are FP32 GEMMs (gemm.cu).
+#include <cstddef>
+
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace ups {
 
@@ -509,6 +512,514 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
     }
 }
 
+// ---------------------------------------------------------------------------
+// fused per-cell kernel with the two 128 x 128 products on the tensor cores
+// ---------------------------------------------------------------------------
+//
+// The walk of k_lift_fused (N_l = 16), with M H and the Gram of b H as tcgen05
+// MMAs whose BF16 operands are split in two (x = hi + lo, hi = bf16(x),
+// lo = bf16(x - hi)): hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM
+// (about 1e-5 relative per product); everything else, Z = W1 F~ + b1 among it
+// (its sign decides ReLU'), FP32 on the CUDA cores.
+//   TMEM columns [0, 64): M H of the chunk (lane = hidden unit, column = pixel)
+//   TMEM columns [128, 256): the Gram, accumulated over all of the CTA's chunks
+// Thread 0 issues the MMAs; `mh_bar` completes when a chunk's M H is in TMEM,
+// `g_bar` when the chunk's Gram MMAs are done with their operands.  A warp
+// reads TMEM lanes 32 (w % 4) .. + 31, so thread (warp w, lane i) owns hidden
+// unit j = 32 (w % 4) + i and the chunk's pixels 32 (w / 4) .. + 31 from Z on,
+// keeping H of them in registers; per-pixel sums over hidden units are
+// reduce-scattered over the warp's lanes and added over the four warps of a
+// pixel half.  H reaches the M H operand (pixel rows) through an FP32
+// transpose in shared memory.
+namespace lt {
+constexpr int kP = 64;       // pixels per chunk
+constexpr int kT = 256;      // threads
+constexpr int kHS = kP + 4;  // row stride of the FP32 hidden-major arrays
+constexpr uint32_t kTmemCols = 256, cMH = 0, cG = 128;
+// BF16 operand tiles, canonical K-major without swizzle (byte offsets)
+constexpr int oMhi = 0, oMlo = 32768;          // M [128 j][128 k] (A of M H)
+constexpr int oHBhi = 65536, oHBlo = 81920;    // H [64 p][128 k] (B of M H)
+constexpr int oHAhi = 98304, oHAlo = 114688;   // H [128 j][64 p] (A of the Gram)
+constexpr int oBHhi = 131072, oBHlo = 147456;  // b H [128 i][64 p] (B of the Gram)
+constexpr int kOpBytes = 163840;
+// in the M H B tile while it is free (after the chunk's M H):
+constexpr int oRed = oHBlo;  // float [4][64][3]: partial H.e, u.H, H.MH per 32 hidden units
+constexpr int kWait = 1 << 22;
+}  // namespace lt
+
+struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
+                     // 16-byte vectors come first, at 16-byte multiples
+    float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
+    float W1T[16][kLiftHidden];      // W1 transposed
+    float b1[kLiftHidden], u[kLiftHidden];
+    float E[4][kLiftHidden];         // W2^T g of the cell's four corners
+    float Fc[16][lt::kHS];           // F~ of the chunk, channel-major
+    float w4[lt::kP][4];             // bilinear weights of the chunk's pixels
+    float ab[lt::kP][2];             // a_p, b_p
+    float aw[4][lt::kP];             // a_p w_k(p)
+    float Dpart[4][kLiftHidden];
+    float sS[4], sG[10];
+    int pix[lt::kP];                 // pixel index in the view, -1: none
+    uint64_t mh_bar, g_bar;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1T) % 16 == 0 &&
+                  offsetof(LiftTcSmem, Fc) % 16 == 0 && offsetof(LiftTcSmem, w4) % 16 == 0 &&
+                  offsetof(LiftTcSmem, ab) % 8 == 0 && offsetof(LiftTcSmem, mh_bar) % 8 == 0,
+              "vector and mbarrier alignment of the lifting kernel's shared arrays");
+
+size_t lift_tc_smem_bytes() { return (size_t)lt::kOpBytes + sizeof(LiftTcSmem) + 1024; }
+
+// hi and lo BF16 pairs of (a, b), a at the lower address
+__device__ __forceinline__ void split2_bf16(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// 8 values as one 16-byte core-matrix row of the hi and of the lo tile
+__device__ __forceinline__ void put8_split(unsigned char *hi, unsigned char *lo, uint32_t off, const float (&v)[8]) {
+    uint4 h, l;
+    split2_bf16(v[0], v[1], h.x, l.x);
+    split2_bf16(v[2], v[3], h.y, l.y);
+    split2_bf16(v[4], v[5], h.z, l.z);
+    split2_bf16(v[6], v[7], h.w, l.w);
+    *reinterpret_cast<uint4 *>(hi + off) = h;
+    *reinterpret_cast<uint4 *>(lo + off) = l;
+}
+
+// Sum over the warp's lanes of v[lane]: the 32 values of every lane are
+// reduce-scattered, lane l keeps the total of entry l.
+__device__ __forceinline__ float warp_rs32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int t = 0; t < s; ++t) {
+            const float send = up ? v[t] : v[t + s];
+            const float keep = up ? v[t + s] : v[t];
+            v[t] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+__global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
+    ViewTable vt, int n_cells, int patch, const float *__restrict__ feat_all, const float *__restrict__ w1,
+    const float *__restrict__ b1, const float *__restrict__ Mg, const float *__restrict__ E,
+    const float *__restrict__ s, const float *__restrict__ u, const float *__restrict__ beta,
+    const float *__restrict__ gram, const float *__restrict__ weight_all, float g0, float *__restrict__ loss,
+    float *__restrict__ D, float *__restrict__ alpha, float *__restrict__ sb, float *__restrict__ hb_out,
+    float *__restrict__ Gb, float *__restrict__ d_w1, float *__restrict__ d_b1, float *__restrict__ d_feat_all,
+    int *__restrict__ err) {
+    using namespace lt;
+    constexpr int NF = 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *op = smem_raw + ((1024u - (umma::smem_addr(smem_raw) & 1023u)) & 1023u);
+    LiftTcSmem &S = *reinterpret_cast<LiftTcSmem *>(op + kOpBytes);
+    const uint32_t sop = umma::smem_addr(op);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // M as BF16 hi/lo tiles (row j, 8 k per 16-byte core-matrix row)
+    for (int i = tid; i < kLiftHidden * (kLiftHidden / 8); i += kT) {
+        const int j = i >> 4, k8 = i & 15;
+        const float4 m0 = *reinterpret_cast<const float4 *>(Mg + (size_t)j * kLiftHidden + 8 * k8);
+        const float4 m1 = *reinterpret_cast<const float4 *>(Mg + (size_t)j * kLiftHidden + 8 * k8 + 4);
+        const float v[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        put8_split(op + oMhi, op + oMlo, umma::kmajor_offset(j, 8 * k8, 2 * kLiftHidden, 2), v);
+    }
+    for (int i = tid; i < kLiftHidden * NF; i += kT) {
+        const int j = i / NF, c = i - j * NF;
+        S.W1T[c][j] = w1[i];
+    }
+    if (tid < kLiftHidden) {
+        S.b1[tid] = b1[tid];
+        S.u[tid] = u[tid];
+    }
+    if (tid == 0) {
+        umma::mbar_init(&S.mh_bar, 1);
+        umma::mbar_init(&S.g_bar, 1);
+        S.abort_flag = 0;
+    }
+    if (warp == 0) umma::tmem_alloc(&S.tmem_base, kTmemCols);
+    umma::fence_before();
+    umma::fence_async_smem();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const float bt = *beta;
+    const float inv2p = 1.f / (float)(2 * patch);
+    // Z phase: thread = 8 hidden (block jb) x 4 pixels (block pb)
+    const int jb = tid >> 4, pb = tid & 15;
+    const int j0 = jb * 8, p0 = pb * 4;
+    // after M H: thread = hidden unit jt x the pixel half ph
+    const int jt = 32 * (warp & 3) + lane, ph = 32 * (warp >> 2);
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    float hb = 0.f, db1 = 0.f;
+    constexpr int NC = NF / 16;
+    float dw1[8][NC];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < NC; ++y) dw1[x][y] = 0.f;
+    float t_loss = 0.f, t_sb = 0.f;
+    uint32_t mh_phase = 0, g_phase = 0;
+    bool g_pending = false, g_started = false, mh_pending = false, ok = true;
+    const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128);
+    float *red = reinterpret_cast<float *>(op + oRed);  // [4][kP][3]
+    for (int cell = blockIdx.x; cell < n_cells && ok; cell += gridDim.x) {
+        const CellView cv = cell_view(vt, patch, cell);
+        const int wp = cv.wp, hp = cv.hp, W = vt.v[cv.v].W, H = vt.v[cv.v].H;
+        const size_t HW = (size_t)W * H, P = (size_t)vt.v[cv.v].pix_off;
+        const float *feat = feat_all + (size_t)NF * P;
+        float *d_feat = d_feat_all ? d_feat_all + (size_t)NF * P : nullptr;
+        const float *weight = weight_all ? weight_all + P : nullptr;
+        const int local = cell - cv.base;
+        const int cj = local / wp, ci = local - cj * wp;
+        const int x0 = ci, y0 = cj;
+        const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
+        const int corner[4] = {cv.base + y0 * wp + x0, cv.base + y0 * wp + x1, cv.base + y1 * wp + x0,
+                               cv.base + y1 * wp + x1};
+        const int xs = cell_start(ci, patch), xe = ci + 1 >= wp ? W : min(W, cell_start(ci + 1, patch));
+        const int ys = cell_start(cj, patch), ye = cj + 1 >= hp ? H : min(H, cell_start(cj + 1, patch));
+        const int nx = max(0, xe - xs), npx = nx * max(0, ye - ys);
+        __syncthreads();  // the previous cell's shared data is no longer read
+        for (int i = tid; i < 4 * kLiftHidden; i += kT)
+            S.E[i / kLiftHidden][i % kLiftHidden] = E[(size_t)corner[i / kLiftHidden] * kLiftHidden + i % kLiftHidden];
+        if (tid < 4) S.sS[tid] = s[corner[tid]];
+        if (tid < 10) S.sG[tid] = gram[(size_t)cell * 10 + tid];
+        for (int i = tid; i < 4 * kLiftHidden; i += kT) (&S.Dpart[0][0])[i] = 0.f;
+        float al[4] = {0.f, 0.f, 0.f, 0.f};  // sum a w_k over the cell (threads < kP)
+        for (int q0 = 0; q0 < npx; q0 += kP) {
+            __syncthreads();
+            // chunk pixels, bilinear weights, F~
+            if (tid < kP) {
+                const int q = q0 + tid;
+                int pidx = -1;
+                float w[4] = {0.f, 0.f, 0.f, 0.f};
+                if (q < npx) {
+                    const int y = ys + q / nx, x = xs + q % nx;
+                    pidx = y * W + x;
+                    const float ax = fminf(fmaxf((float)(2 * x + 1 - (2 * x0 + 1) * patch) * inv2p, 0.f), 1.f);
+                    const float ay = fminf(fmaxf((float)(2 * y + 1 - (2 * y0 + 1) * patch) * inv2p, 0.f), 1.f);
+                    w[0] = (1.f - ax) * (1.f - ay);
+                    w[1] = ax * (1.f - ay);
+                    w[2] = (1.f - ax) * ay;
+                    w[3] = ax * ay;
+                }
+                S.pix[tid] = pidx;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) S.w4[tid][k] = w[k];
+            }
+            __syncthreads();
+            for (int i = tid; i < NF * kP; i += kT) {
+                const int c = i / kP, p = i - c * kP;
+                const int pidx = S.pix[p];
+                S.Fc[c][p] = pidx >= 0 ? feat[(size_t)c * HW + pidx] : 0.f;
+            }
+            // the previous chunk's Gram MMAs still read the H and b H tiles
+            if (g_pending) {
+                const bool w_ok = umma::mbar_wait(&S.g_bar, g_phase, kWait);
+                g_phase ^= 1u;
+                g_pending = false;
+                if (!w_ok) S.abort_flag = 1;
+            }
+            __syncthreads();
+            if (S.abort_flag) {
+                ok = false;
+                break;
+            }
+            umma::fence_after();
+            // H = relu(W1 F~ + b1) of (jt, pixel half) in FP32, each element the
+            // fmaf chain from b1 over the channels in order: registers, the Gram
+            // A tile (row jt) and the FP32 transpose buffer Hh
+            float hv[32];
+            {
+                float wj[NF];
+#pragma unroll
+                for (int c = 0; c < NF; ++c) wj[c] = S.W1T[c][jt];
+                const float bj = S.b1[jt];
+                f2 z2[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) z2[t] = f2_make(bj, bj);
+#pragma unroll 4
+                for (int c = 0; c < NF; ++c) {
+                    const f2 w2v = f2_make(wj[c], wj[c]);
+#pragma unroll
+                    for (int t4 = 0; t4 < 8; ++t4) {
+                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[c][ph + 4 * t4]);
+                        z2[2 * t4] = f2_fma(w2v, f.x, z2[2 * t4]);
+                        z2[2 * t4 + 1] = f2_fma(w2v, f.y, z2[2 * t4 + 1]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    float lo, hi;
+                    f2_split(z2[t], lo, hi);
+                    hv[2 * t] = fmaxf(lo, 0.f);
+                    hv[2 * t + 1] = fmaxf(hi, 0.f);
+                }
+            }
+#pragma unroll
+            for (int c8 = 0; c8 < 4; ++c8) {
+                const float v[8] = {hv[8 * c8],     hv[8 * c8 + 1], hv[8 * c8 + 2], hv[8 * c8 + 3],
+                                    hv[8 * c8 + 4], hv[8 * c8 + 5], hv[8 * c8 + 6], hv[8 * c8 + 7]};
+                put8_split(op + oHAhi, op + oHAlo, umma::kmajor_offset(jt, ph + 8 * c8, 2 * kP, 2), v);
+            }
+#pragma unroll
+            for (int t4 = 0; t4 < 8; ++t4)
+                *reinterpret_cast<float4 *>(&S.Hh[jt][ph + 4 * t4]) =
+                    make_float4(hv[4 * t4], hv[4 * t4 + 1], hv[4 * t4 + 2], hv[4 * t4 + 3]);
+            __syncthreads();
+            // the M H B tile (pixel rows, 8 hidden units per core-matrix row)
+            // from the transpose buffer: thread = (pixel, 8 hidden units)
+#pragma unroll
+            for (int r = 0; r < kP * (kLiftHidden / 8) / kT; ++r) {
+                const int i = tid + kT * r, p = i & (kP - 1), j8 = i / kP;
+                float v[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) v[jj] = S.Hh[8 * j8 + jj][p];
+                put8_split(op + oHBhi, op + oHBlo, umma::kmajor_offset(p, 8 * j8, 2 * kLiftHidden, 2), v);
+            }
+            umma::fence_before();
+            umma::fence_async_smem();
+            __syncthreads();
+            // M H on the tensor cores
+            if (tid == 0) {
+                umma::fence_after();
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t a = sop + (pass == 2 ? oMlo : oMhi), b = sop + (pass == 1 ? oHBlo : oHBhi);
+                    for (int ks = 0; ks < kLiftHidden / 16; ++ks)
+                        umma::mma<umma::kBF16>(tmem + cMH, umma::desc(a + 256u * ks, 2 * kLiftHidden),
+                                               umma::desc(b + 256u * ks, 2 * kLiftHidden), id_mh,
+                                               (pass > 0 || ks > 0) ? 1u : 0u);
+                }
+                umma::commit(&S.mh_bar);
+            }
+            mh_pending = true;
+            {
+                const bool w_ok = umma::mbar_wait(&S.mh_bar, mh_phase, kWait);
+                if (w_ok) {
+                    mh_phase ^= 1u;
+                    mh_pending = false;
+                }
+                if (__syncthreads_or(!w_ok)) {
+                    if (tid == 0) S.abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+            }
+            umma::fence_after();
+            // thread (jt, pixel half ph): its M H row, the corner terms
+            float mh[32];
+            {
+                float t16[16];
+                umma::tmem_ld16(lane_addr + cMH + ph, t16);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) mh[t] = t16[t];
+                umma::tmem_ld16(lane_addr + cMH + ph + 16, t16);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) mh[16 + t] = t16[t];
+            }
+            const float e0 = S.E[0][jt], e1 = S.E[1][jt], e2 = S.E[2][jt], e3 = S.E[3][jt], uj = S.u[jt];
+            auto e_at = [&](int t) {
+                const float4 w = *reinterpret_cast<const float4 *>(&S.w4[ph + t][0]);
+                return w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
+            };
+            // per pixel: H.e, u.H, H.(M H) over this warp's 32 hidden units
+            {
+                float v[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = hv[t] * e_at(t);
+                red[((warp & 3) * kP + ph + lane) * 3 + 0] = warp_rs32(v, lane);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = uj * hv[t];
+                red[((warp & 3) * kP + ph + lane) * 3 + 1] = warp_rs32(v, lane);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = hv[t] * mh[t];
+                red[((warp & 3) * kP + ph + lane) * 3 + 2] = warp_rs32(v, lane);
+            }
+            __syncthreads();
+            // per pixel: cosine, loss, a_p, b_p
+            if (tid < kP) {
+                const int p = tid;
+                float de = 0.f, du = 0.f, dm = 0.f;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    de += red[(b * kP + p) * 3 + 0];
+                    du += red[(b * kP + p) * 3 + 1];
+                    dm += red[(b * kP + p) * 3 + 2];
+                }
+                const float *w = S.w4[p];
+                const float dot = de + w[0] * S.sS[0] + w[1] * S.sS[1] + w[2] * S.sS[2] + w[3] * S.sS[3];
+                const float nF2 = w[0] * w[0] * S.sG[0] + w[1] * w[1] * S.sG[4] + w[2] * w[2] * S.sG[7] +
+                                  w[3] * w[3] * S.sG[9] +
+                                  2.f * (w[0] * w[1] * S.sG[1] + w[0] * w[2] * S.sG[2] + w[0] * w[3] * S.sG[3] +
+                                         w[1] * w[2] * S.sG[5] + w[1] * w[3] * S.sG[6] + w[2] * w[3] * S.sG[8]);
+                const float nFh2 = dm + 2.f * du + bt;
+                float a = 0.f, b = 0.f;
+                const int pidx = S.pix[p];
+                if (pidx >= 0) {
+                    const bool okp = nF2 > 0.f && nFh2 > 0.f;
+                    const float wpx = weight ? weight[pidx] : 1.f;
+                    const float g = g0 * wpx;
+                    const float inv = okp ? rsqrtf(nF2) * rsqrtf(nFh2) : 0.f;
+                    const float cs = dot * inv;
+                    t_loss += wpx * (1.f - cs);
+                    a = -g * inv;
+                    b = okp ? g * cs / nFh2 : 0.f;
+                    t_sb += b;
+                }
+                S.ab[p][0] = a;
+                S.ab[p][1] = b;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    S.aw[k][p] = a * w[k];
+                    al[k] += a * w[k];
+                }
+            }
+            __syncthreads();
+            // dZ (to Hh), b H (to the Gram B tile), db1, hb and D of the corners
+            // (thread jt over its pixel half)
+            {
+                float Dk[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int p = ph + t;
+                    const float2 abp = *reinterpret_cast<const float2 *>(&S.ab[p][0]);
+                    const float dh = fmaf(abp.x, e_at(t), abp.y * (mh[t] + uj));
+                    const float dz = hv[t] > 0.f ? dh : 0.f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Dk[k] = fmaf(S.aw[k][p], hv[t], Dk[k]);
+                    db1 += dz;
+                    hb = fmaf(abp.y, hv[t], hb);
+                    mh[t] = dz;
+                    hv[t] *= abp.y;
+                }
+#pragma unroll
+                for (int t4 = 0; t4 < 8; ++t4)
+                    *reinterpret_cast<float4 *>(&S.Hh[jt][ph + 4 * t4]) =
+                        make_float4(mh[4 * t4], mh[4 * t4 + 1], mh[4 * t4 + 2], mh[4 * t4 + 3]);
+#pragma unroll
+                for (int c8 = 0; c8 < 4; ++c8) {
+                    const float v[8] = {hv[8 * c8],     hv[8 * c8 + 1], hv[8 * c8 + 2], hv[8 * c8 + 3],
+                                        hv[8 * c8 + 4], hv[8 * c8 + 5], hv[8 * c8 + 6], hv[8 * c8 + 7]};
+                    put8_split(op + oBHhi, op + oBHlo, umma::kmajor_offset(jt, ph + 8 * c8, 2 * kP, 2), v);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(&S.Dpart[k][jt], Dk[k]);
+            }
+            umma::fence_before();
+            umma::fence_async_smem();
+            __syncthreads();
+            // Gram += H (b H)^T on the tensor cores, left running
+            if (tid == 0) {
+                umma::fence_after();
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t a = sop + (pass == 2 ? oHAlo : oHAhi), b = sop + (pass == 1 ? oBHlo : oBHhi);
+                    for (int ks = 0; ks < kP / 16; ++ks)
+                        umma::mma<umma::kBF16>(tmem + cG, umma::desc(a + 256u * ks, 2 * kP),
+                                               umma::desc(b + 256u * ks, 2 * kP), id_g,
+                                               (g_started || pass > 0 || ks > 0) ? 1u : 0u);
+                }
+                umma::commit(&S.g_bar);
+            }
+            g_started = true;
+            g_pending = true;
+            {
+                // dF~ = W1^T dZ: thread (channel, 4 pixels); NF x kP outputs
+                for (int o = tid; o < NF * (kP / 4); o += kT) {
+                    const int c = o / (kP / 4), pq = (o - c * (kP / 4)) * 4;
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                    for (int j = 0; j < kLiftHidden; ++j) {
+                        const float wv = S.W1T[c][j];
+                        const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j][pq]);
+                        acc[0] = fmaf(wv, dz.x, acc[0]);
+                        acc[1] = fmaf(wv, dz.y, acc[1]);
+                        acc[2] = fmaf(wv, dz.z, acc[2]);
+                        acc[3] = fmaf(wv, dz.w, acc[3]);
+                    }
+                    if (d_feat)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const int pidx = S.pix[pq + y];
+                            if (pidx >= 0) d_feat[(size_t)c * HW + pidx] += acc[y];
+                        }
+                }
+            }
+            // dW1 += dZ F~^T: thread (8 hidden of block jb) x channel pb
+#pragma unroll 2
+            for (int pq = 0; pq < kP; pq += 4) {
+                float4 fz[NC];
+#pragma unroll
+                for (int y = 0; y < NC; ++y) fz[y] = *reinterpret_cast<const float4 *>(&S.Fc[pb + 16 * y][pq]);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j0 + x][pq]);
+#pragma unroll
+                    for (int y = 0; y < NC; ++y)
+                        dw1[x][y] = fmaf(dz.x, fz[y].x, fmaf(dz.y, fz[y].y, fmaf(dz.z, fz[y].z, fmaf(dz.w, fz[y].w, dw1[x][y]))));
+                }
+            }
+        }
+        if (!ok) break;
+        __syncthreads();
+        // the cell's D rows and alpha
+        for (int i = tid; i < 4 * kLiftHidden; i += kT) {
+            const int k = i / kLiftHidden, j = i - k * kLiftHidden;
+            if (npx > 0) atomicAdd(D + (size_t)corner[k] * kLiftHidden + j, S.Dpart[k][j]);
+        }
+        if (tid < kP && npx > 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(alpha + corner[k], al[k]);
+    }
+    // the last Gram MMAs (and an M H that a wait gave up on), then the CTA's sums
+    if (mh_pending && !umma::mbar_wait(&S.mh_bar, mh_phase, kWait)) S.abort_flag = 1;
+    if (g_pending) {
+        const bool w_ok = umma::mbar_wait(&S.g_bar, g_phase, kWait);
+        g_phase ^= 1u;
+        if (!w_ok) S.abort_flag = 1;
+    }
+    __syncthreads();
+    umma::fence_after();
+    ok = ok && !S.abort_flag;
+    if (ok && g_started) {
+        // Gram (symmetric): thread jt, the half of the columns its warp's pixel half names
+#pragma unroll 1
+        for (int c0 = 0; c0 < kLiftHidden / 2; c0 += 16) {
+            float d[16];
+            umma::tmem_ld16(lane_addr + cG + 2 * ph + c0, d);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) atomicAdd(Gb + (size_t)jt * kLiftHidden + 2 * ph + c0 + t, d[t]);
+        }
+    }
+    if (!ok && tid == 0 && err) atomicExch(err, 1);
+    if (ok) {
+        atomicAdd(hb_out + jt, hb);
+        if (d_b1) atomicAdd(d_b1 + jt, db1);
+        if (d_w1)
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < NC; ++y) atomicAdd(d_w1 + (size_t)(j0 + x) * NF + pb + 16 * y, dw1[x][y]);
+        float v2[2] = {t_loss, t_sb};
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v2[i] += __shfl_xor_sync(0xffffffffu, v2[i], o);
+        if (lane == 0) {
+            atomicAdd(loss, g0 * v2[0]);
+            atomicAdd(sb, v2[1]);
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, kTmemCols);
+}
+
 // y[i] += x[i] * (*c)
 __global__ void k_axpy_dev(int n, const float *__restrict__ x, const float *__restrict__ c, float *__restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -559,7 +1070,7 @@ size_t lift_scratch_floats(size_t np_total) { return lift_layout(np_total).total
 cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, int nh, int patch, const float *feat,
                      const float *grid, const float *w1, const float *b1, const float *w2, const float *b2, float g,
                      const float *weight, float *loss, float *d_w1, float *d_b1, float *d_w2, float *d_b2,
-                     float *d_feat, float *scratch, int *launches) {
+                     float *d_feat, float *scratch, int *err, int *launches) {
     int np = 0;
     for (int v = 0; v < vt.n; ++v) np += ((vt.v[v].H + patch - 1) / patch) * ((vt.v[v].W + patch - 1) / patch);
     const int NH = kLiftHidden;
@@ -581,21 +1092,23 @@ cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, 
     // the fused kernel adds into D, alpha, hb, sb and Gb
     if ((e = cudaMemsetAsync(D, 0, (L.sb + 1 - L.D) * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Gb, 0, (size_t)NH * NH * sizeof(float), st)) != cudaSuccess) return e;
-    const size_t smem = fused_smem_bytes(nf);
     const int grid_ctas = std::max(1, std::min(np, num_sms));
-#define UPS_LIFT(NFV)                                                                                              \
-    do {                                                                                                          \
-        cudaFuncSetAttribute(k_lift_fused<NFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
-        k_lift_fused<NFV><<<grid_ctas, kFT, smem, st>>>(vt, np, patch, feat, w1, b1, M, E, sv, u, beta, gram,     \
-                                                        weight, g, loss, D, alpha, sb, hb, Gb, d_w1, d_b1, d_feat); \
-    } while (0)
-    if (nf == 16)
-        UPS_LIFT(16);
-    else if (nf == 32)
-        UPS_LIFT(32);
-    else
+    if (nf == 16) {
+        // M H and the Gram on the tensor cores
+        const size_t smem = lift_tc_smem_bytes();
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_lift_tc<<<grid_ctas, lt::kT, smem, st>>>(vt, np, patch, feat, w1, b1, M, E, sv, u, beta, gram, weight, g,
+                                                   loss, D, alpha, sb, hb, Gb, d_w1, d_b1, d_feat, err);
+    } else if (nf == 32) {
+        // the BF16 operand tiles and the FP32 arrays of N_l = 32 exceed shared memory: all FP32 on the CUDA cores
+        const size_t smem = fused_smem_bytes(nf);
+        cudaFuncSetAttribute(k_lift_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_lift_fused<32><<<grid_ctas, kFT, smem, st>>>(vt, np, patch, feat, w1, b1, M, E, sv, u, beta, gram, weight,
+                                                       g, loss, D, alpha, sb, hb, Gb, d_w1, d_b1, d_feat);
+    } else {
         return cudaErrorInvalidValue;
-#undef UPS_LIFT
+    }
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d_w2) {
