@@ -523,6 +523,7 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
 // (its sign decides ReLU'), FP32 on the CUDA cores.
 //   TMEM columns [0, 64): M H of the chunk (lane = hidden unit, column = pixel)
 //   TMEM columns [128, 256): the Gram, accumulated over all of the CTA's chunks
+//   TMEM columns [256, 384): M hi, lo; [384, 448): H of the chunk hi, lo (A operands)
 // Thread 0 issues the MMAs; `mh_bar` completes when a chunk's M H is in TMEM,
 // `g_bar` when the chunk's Gram MMAs are done with their operands.  A warp
 // reads TMEM lanes 32 (w % 4) .. + 31, so thread (warp w, lane i) owns hidden
@@ -535,13 +536,13 @@ namespace lt {
 constexpr int kP = 64;       // pixels per chunk
 constexpr int kT = 256;      // threads
 constexpr int kHS = kP + 4;  // row stride of the FP32 hidden-major arrays
-constexpr uint32_t kTmemCols = 256, cMH = 0, cG = 128;
-// BF16 operand tiles, canonical K-major without swizzle (byte offsets)
-constexpr int oMhi = 0, oMlo = 32768;          // M [128 j][128 k] (A of M H)
-constexpr int oHBhi = 65536, oHBlo = 81920;    // H [64 p][128 k] (B of M H)
-constexpr int oHAhi = 98304, oHAlo = 114688;   // H [128 j][64 p] (A of the Gram)
-constexpr int oBHhi = 131072, oBHlo = 147456;  // b H [128 i][64 p] (B of the Gram)
-constexpr int kOpBytes = 163840;
+// TMEM columns; the A operands (M, and H as the Gram's A) sit in TMEM as BF16
+// pairs (row = lane), so the MMAs read only their B operands from shared memory
+constexpr uint32_t kTmemCols = 512, cMH = 0, cG = 128, cMhi = 256, cMlo = 320, cHAhi = 384, cHAlo = 416;
+// BF16 B operand tiles in shared memory, canonical K-major without swizzle (byte offsets)
+constexpr int oHBhi = 0, oHBlo = 16384;        // H [64 p][128 k] (B of M H)
+constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gram)
+constexpr int kOpBytes = 65536;
 // in the M H B tile while it is free (after the chunk's M H):
 constexpr int oRed = oHBlo;  // float [4][64][3]: partial H.e, u.H, H.MH per 32 hidden units
 constexpr int kWait = 1 << 22;
@@ -556,7 +557,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     float Fc[16][lt::kHS];           // F~ of the chunk, channel-major
     float w4[lt::kP][4];             // bilinear weights of the chunk's pixels
     float ab[lt::kP][2];             // a_p, b_p
-    float aw[4][lt::kP];             // a_p w_k(p)
+    float aw[lt::kP][4];             // a_p w_k(p)
     float Dpart[4][kLiftHidden];
     float sS[4], sG[10];
     int pix[lt::kP];                 // pixel index in the view, -1: none
@@ -622,14 +623,6 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     LiftTcSmem &S = *reinterpret_cast<LiftTcSmem *>(op + kOpBytes);
     const uint32_t sop = umma::smem_addr(op);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // M as BF16 hi/lo tiles (row j, 8 k per 16-byte core-matrix row)
-    for (int i = tid; i < kLiftHidden * (kLiftHidden / 8); i += kT) {
-        const int j = i >> 4, k8 = i & 15;
-        const float4 m0 = *reinterpret_cast<const float4 *>(Mg + (size_t)j * kLiftHidden + 8 * k8);
-        const float4 m1 = *reinterpret_cast<const float4 *>(Mg + (size_t)j * kLiftHidden + 8 * k8 + 4);
-        const float v[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-        put8_split(op + oMhi, op + oMlo, umma::kmajor_offset(j, 8 * k8, 2 * kLiftHidden, 2), v);
-    }
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
         S.W1T[c][j] = w1[i];
@@ -649,14 +642,31 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     __syncthreads();
     umma::fence_after();
     const uint32_t tmem = S.tmem_base;
+    const int jt = 32 * (warp & 3) + lane, ph = 32 * (warp >> 2);
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    // M (symmetric) as BF16 hi/lo pairs into TMEM: lane jt = row jt, the
+    // thread's warp half writes k in [64 (w / 4), + 64)
+#pragma unroll 1
+    for (int k0 = 2 * ph; k0 < 2 * ph + 64; k0 += 32) {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 m = *reinterpret_cast<const float4 *>(Mg + (size_t)jt * kLiftHidden + k0 + 4 * q);
+            split2_bf16(m.x, m.y, hi[2 * q], lo[2 * q]);
+            split2_bf16(m.z, m.w, hi[2 * q + 1], lo[2 * q + 1]);
+        }
+        umma::tmem_st16(lane_addr + cMhi + k0 / 2, hi);
+        umma::tmem_st16(lane_addr + cMlo + k0 / 2, lo);
+    }
+    umma::tmem_st_wait();
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
     const float bt = *beta;
     const float inv2p = 1.f / (float)(2 * patch);
     // Z phase: thread = 8 hidden (block jb) x 4 pixels (block pb)
     const int jb = tid >> 4, pb = tid & 15;
     const int j0 = jb * 8, p0 = pb * 4;
-    // after M H: thread = hidden unit jt x the pixel half ph
-    const int jt = 32 * (warp & 3) + lane, ph = 32 * (warp >> 2);
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     float hb = 0.f, db1 = 0.f;
     constexpr int NC = NF / 16;
     float dw1[8][NC];
@@ -762,11 +772,13 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                     hv[2 * t + 1] = fmaxf(hi, 0.f);
                 }
             }
+            {
+                uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int c8 = 0; c8 < 4; ++c8) {
-                const float v[8] = {hv[8 * c8],     hv[8 * c8 + 1], hv[8 * c8 + 2], hv[8 * c8 + 3],
-                                    hv[8 * c8 + 4], hv[8 * c8 + 5], hv[8 * c8 + 6], hv[8 * c8 + 7]};
-                put8_split(op + oHAhi, op + oHAlo, umma::kmajor_offset(jt, ph + 8 * c8, 2 * kP, 2), v);
+                for (int t = 0; t < 16; ++t) split2_bf16(hv[2 * t], hv[2 * t + 1], hi[t], lo[t]);
+                umma::tmem_st16(lane_addr + cHAhi + ph / 2, hi);
+                umma::tmem_st16(lane_addr + cHAlo + ph / 2, lo);
+                umma::tmem_st_wait();
             }
 #pragma unroll
             for (int t4 = 0; t4 < 8; ++t4)
@@ -790,11 +802,10 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             if (tid == 0) {
                 umma::fence_after();
                 for (int pass = 0; pass < 3; ++pass) {
-                    const uint32_t a = sop + (pass == 2 ? oMlo : oMhi), b = sop + (pass == 1 ? oHBlo : oHBhi);
+                    const uint32_t a = tmem + (pass == 2 ? cMlo : cMhi), b = sop + (pass == 1 ? oHBlo : oHBhi);
                     for (int ks = 0; ks < kLiftHidden / 16; ++ks)
-                        umma::mma<umma::kBF16>(tmem + cMH, umma::desc(a + 256u * ks, 2 * kLiftHidden),
-                                               umma::desc(b + 256u * ks, 2 * kLiftHidden), id_mh,
-                                               (pass > 0 || ks > 0) ? 1u : 0u);
+                        umma::mma_f16_ts(tmem + cMH, a + 8u * ks, umma::desc(b + 256u * ks, 2 * kLiftHidden), id_mh,
+                                         (pass > 0 || ks > 0) ? 1u : 0u);
                 }
                 umma::commit(&S.mh_bar);
             }
@@ -876,7 +887,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 S.ab[p][1] = b;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    S.aw[k][p] = a * w[k];
+                    S.aw[p][k] = a * w[k];
                     al[k] += a * w[k];
                 }
             }
@@ -891,8 +902,11 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                     const float2 abp = *reinterpret_cast<const float2 *>(&S.ab[p][0]);
                     const float dh = fmaf(abp.x, e_at(t), abp.y * (mh[t] + uj));
                     const float dz = hv[t] > 0.f ? dh : 0.f;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) Dk[k] = fmaf(S.aw[k][p], hv[t], Dk[k]);
+                    const float4 awp = *reinterpret_cast<const float4 *>(&S.aw[p][0]);
+                    Dk[0] = fmaf(awp.x, hv[t], Dk[0]);
+                    Dk[1] = fmaf(awp.y, hv[t], Dk[1]);
+                    Dk[2] = fmaf(awp.z, hv[t], Dk[2]);
+                    Dk[3] = fmaf(awp.w, hv[t], Dk[3]);
                     db1 += dz;
                     hb = fmaf(abp.y, hv[t], hb);
                     mh[t] = dz;
@@ -918,11 +932,10 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             if (tid == 0) {
                 umma::fence_after();
                 for (int pass = 0; pass < 3; ++pass) {
-                    const uint32_t a = sop + (pass == 2 ? oHAlo : oHAhi), b = sop + (pass == 1 ? oBHlo : oBHhi);
+                    const uint32_t a = tmem + (pass == 2 ? cHAlo : cHAhi), b = sop + (pass == 1 ? oBHlo : oBHhi);
                     for (int ks = 0; ks < kP / 16; ++ks)
-                        umma::mma<umma::kBF16>(tmem + cG, umma::desc(a + 256u * ks, 2 * kP),
-                                               umma::desc(b + 256u * ks, 2 * kP), id_g,
-                                               (g_started || pass > 0 || ks > 0) ? 1u : 0u);
+                        umma::mma_f16_ts(tmem + cG, a + 8u * ks, umma::desc(b + 256u * ks, 2 * kP), id_g,
+                                         (g_started || pass > 0 || ks > 0) ? 1u : 0u);
                 }
                 umma::commit(&S.g_bar);
             }
@@ -1096,7 +1109,8 @@ cudaError_t lift_all(int num_sms, cudaStream_t st, const ViewTable &vt, int nf, 
     if (nf == 16) {
         // M H and the Gram on the tensor cores
         const size_t smem = lift_tc_smem_bytes();
-        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        // one CTA per SM: it holds all 512 TMEM columns
+        if (smem > 227 * 1024 || 2 * (smem + 1024) <= 228 * 1024) return cudaErrorInvalidConfiguration;
         cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_lift_tc<<<grid_ctas, lt::kT, smem, st>>>(vt, np, patch, feat, w1, b1, M, E, sv, u, beta, gram, weight, g,
                                                    loss, D, alpha, sb, hb, Gb, d_w1, d_b1, d_feat, err);
