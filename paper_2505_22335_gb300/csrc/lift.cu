@@ -544,7 +544,7 @@ constexpr int oHBhi = 0, oHBlo = 16384;        // H [64 p][128 k] (B of M H)
 constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gram)
 constexpr int kOpBytes = 65536;
 // in the M H B tile while it is free (after the chunk's M H):
-constexpr int oRed = oHBlo;  // float [4][64][3]: partial H.e, u.H, H.MH per 32 hidden units
+constexpr int oRed = oHBlo;  // float [4][64][2]: partial H.e, H.(MH + 2u) per 32 hidden units
 constexpr int kWait = 1 << 22;
 }  // namespace lt
 
@@ -669,16 +669,16 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     const int j0 = jb * 8, p0 = pb * 4;
     float hb = 0.f, db1 = 0.f;
     constexpr int NC = NF / 16;
-    float dw1[8][NC];
+    f2 dw1[8][NC];  // pixel pairs (p, p + 1) and (p + 2, p + 3) of the sums, added at the end
 #pragma unroll
     for (int x = 0; x < 8; ++x)
 #pragma unroll
-        for (int y = 0; y < NC; ++y) dw1[x][y] = 0.f;
+        for (int y = 0; y < NC; ++y) dw1[x][y] = 0ull;
     float t_loss = 0.f, t_sb = 0.f;
     uint32_t mh_phase = 0, g_phase = 0;
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
     const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128);
-    float *red = reinterpret_cast<float *>(op + oRed);  // [4][kP][3]
+    float *red = reinterpret_cast<float *>(op + oRed);  // [4][kP][2]
     for (int cell = blockIdx.x; cell < n_cells && ok; cell += gridDim.x) {
         const CellView cv = cell_view(vt, patch, cell);
         const int wp = cv.wp, hp = cv.hp, W = vt.v[cv.v].W, H = vt.v[cv.v].H;
@@ -839,29 +839,26 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 const float4 w = *reinterpret_cast<const float4 *>(&S.w4[ph + t][0]);
                 return w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
             };
-            // per pixel: H.e, u.H, H.(M H) over this warp's 32 hidden units
+            // per pixel over this warp's 32 hidden units: H.e and H.(M H + 2 u),
+            // the two sums the cosine needs (|F^|^2 = H.M H + 2 u.H + |b2|^2)
             {
                 float v[32];
 #pragma unroll
                 for (int t = 0; t < 32; ++t) v[t] = hv[t] * e_at(t);
-                red[((warp & 3) * kP + ph + lane) * 3 + 0] = warp_rs32(v, lane);
+                red[((warp & 3) * kP + ph + lane) * 2 + 0] = warp_rs32(v, lane);
 #pragma unroll
-                for (int t = 0; t < 32; ++t) v[t] = uj * hv[t];
-                red[((warp & 3) * kP + ph + lane) * 3 + 1] = warp_rs32(v, lane);
-#pragma unroll
-                for (int t = 0; t < 32; ++t) v[t] = hv[t] * mh[t];
-                red[((warp & 3) * kP + ph + lane) * 3 + 2] = warp_rs32(v, lane);
+                for (int t = 0; t < 32; ++t) v[t] = hv[t] * fmaf(2.f, uj, mh[t]);
+                red[((warp & 3) * kP + ph + lane) * 2 + 1] = warp_rs32(v, lane);
             }
             __syncthreads();
             // per pixel: cosine, loss, a_p, b_p
             if (tid < kP) {
                 const int p = tid;
-                float de = 0.f, du = 0.f, dm = 0.f;
+                float de = 0.f, dmu = 0.f;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    de += red[(b * kP + p) * 3 + 0];
-                    du += red[(b * kP + p) * 3 + 1];
-                    dm += red[(b * kP + p) * 3 + 2];
+                    de += red[(b * kP + p) * 2 + 0];
+                    dmu += red[(b * kP + p) * 2 + 1];
                 }
                 const float *w = S.w4[p];
                 const float dot = de + w[0] * S.sS[0] + w[1] * S.sS[1] + w[2] * S.sS[2] + w[3] * S.sS[3];
@@ -869,7 +866,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                                   w[3] * w[3] * S.sG[9] +
                                   2.f * (w[0] * w[1] * S.sG[1] + w[0] * w[2] * S.sG[2] + w[0] * w[3] * S.sG[3] +
                                          w[1] * w[2] * S.sG[5] + w[1] * w[3] * S.sG[6] + w[2] * w[3] * S.sG[8]);
-                const float nFh2 = dm + 2.f * du + bt;
+                const float nFh2 = dmu + bt;
                 float a = 0.f, b = 0.f;
                 const int pidx = S.pix[p];
                 if (pidx >= 0) {
@@ -945,16 +942,18 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 // dF~ = W1^T dZ: thread (channel, 4 pixels); NF x kP outputs
                 for (int o = tid; o < NF * (kP / 4); o += kT) {
                     const int c = o / (kP / 4), pq = (o - c * (kP / 4)) * 4;
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    f2 a01 = 0ull, a23 = 0ull;  // pixels (pq, pq + 1), (pq + 2, pq + 3)
 #pragma unroll 4
                     for (int j = 0; j < kLiftHidden; ++j) {
                         const float wv = S.W1T[c][j];
-                        const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j][pq]);
-                        acc[0] = fmaf(wv, dz.x, acc[0]);
-                        acc[1] = fmaf(wv, dz.y, acc[1]);
-                        acc[2] = fmaf(wv, dz.z, acc[2]);
-                        acc[3] = fmaf(wv, dz.w, acc[3]);
+                        const f2 w2v = f2_make(wv, wv);
+                        const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
+                        a01 = f2_fma(w2v, dz.x, a01);
+                        a23 = f2_fma(w2v, dz.y, a23);
                     }
+                    float acc[4];
+                    f2_split(a01, acc[0], acc[1]);
+                    f2_split(a23, acc[2], acc[3]);
                     if (d_feat)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
@@ -966,15 +965,14 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             // dW1 += dZ F~^T: thread (8 hidden of block jb) x channel pb
 #pragma unroll 2
             for (int pq = 0; pq < kP; pq += 4) {
-                float4 fz[NC];
+                ulonglong2 fz[NC];
 #pragma unroll
-                for (int y = 0; y < NC; ++y) fz[y] = *reinterpret_cast<const float4 *>(&S.Fc[pb + 16 * y][pq]);
+                for (int y = 0; y < NC; ++y) fz[y] = *reinterpret_cast<const ulonglong2 *>(&S.Fc[pb + 16 * y][pq]);
 #pragma unroll
                 for (int x = 0; x < 8; ++x) {
-                    const float4 dz = *reinterpret_cast<const float4 *>(&S.Hh[j0 + x][pq]);
+                    const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j0 + x][pq]);
 #pragma unroll
-                    for (int y = 0; y < NC; ++y)
-                        dw1[x][y] = fmaf(dz.x, fz[y].x, fmaf(dz.y, fz[y].y, fmaf(dz.z, fz[y].z, fmaf(dz.w, fz[y].w, dw1[x][y]))));
+                    for (int y = 0; y < NC; ++y) dw1[x][y] = f2_fma(dz.y, fz[y].y, f2_fma(dz.x, fz[y].x, dw1[x][y]));
                 }
             }
         }
@@ -1017,7 +1015,11 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
             for (int x = 0; x < 8; ++x)
 #pragma unroll
-                for (int y = 0; y < NC; ++y) atomicAdd(d_w1 + (size_t)(j0 + x) * NF + pb + 16 * y, dw1[x][y]);
+                for (int y = 0; y < NC; ++y) {
+                    float lo, hi;
+                    f2_split(dw1[x][y], lo, hi);
+                    atomicAdd(d_w1 + (size_t)(j0 + x) * NF + pb + 16 * y, lo + hi);
+                }
         float v2[2] = {t_loss, t_sb};
 #pragma unroll
         for (int i = 0; i < 2; ++i)
