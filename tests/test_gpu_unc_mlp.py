@@ -4,7 +4,7 @@ weights (a forward on the same cameras only sets up the views).  The GPU
 evaluates the first layer once per patch and interpolates it (exact by
 linearity); the oracle upsamples the features per pixel.
 
-FP32 arithmetic throughout (pedantic FP32 cuBLAS GEMMs on the patches).
+FP32 arithmetic throughout (the library's own FP32 GEMM on the patches).
 sigma: the first layer sums n_h products and the second 128 in FP32 (the GPU
 interpolates W1 g per patch, the oracle interpolates F first: the same sum in
 another order), n u ~ 384 x 6e-8 ~ 2.3e-5 relative on the pre-activations at
