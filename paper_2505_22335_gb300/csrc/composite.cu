@@ -16,7 +16,8 @@
 //
 // Per (pixel, Gaussian) the exponent is evaluated as p(dy) = pa + dy (pb + pc
 // dy), the quadratic form of the conic with the Gaussian's column offset dx
-// fixed per thread (pa = -a dx^2 / 2, pb = -b dx, pc = -c / 2); the forward
+// fixed per thread (pa = -a dx^2 / 2, pb = -b dx, pc = -c / 2, all times
+// log2 e for a base-2 exponential); the forward
 // and the backward share this evaluation, so both take the same alpha
 // decisions.  The four pixels of a thread are processed without branches
 // (a pixel that takes no part contributes zero), which lets their independent
@@ -121,14 +122,23 @@ __device__ __forceinline__ TileP<PX> tilep(const ViewTable &vt) {
 __host__ __device__ constexpr int blend_px_fwd(int nf) { return UPS_FWD_PX; }
 __host__ __device__ constexpr int blend_px_bwd(int nf) { return nf <= 16 ? 4 : 2; }
 
-// exponent coefficients of a staged Gaussian for a thread's pixel column
+// Exponent coefficients of a staged Gaussian for a thread's pixel column, in
+// base 2: exp(p) = 2^(p log2 e), so the coefficients carry the factor log2 e
+// and the falloff is one hardware base-2 exponential per pixel.
+constexpr float kLog2e = 1.44269504088896341f;
 struct Expo {
     float pa, pb, pc;
 };
 __device__ __forceinline__ Expo expo(float4 cn, float dx) {
-    return Expo{-0.5f * cn.x * dx * dx, -cn.y * dx, -0.5f * cn.z};
+    return Expo{(-0.5f * kLog2e) * cn.x * dx * dx, (-kLog2e * cn.y) * dx, (-0.5f * kLog2e) * cn.z};
 }
 __device__ __forceinline__ float expo_at(const Expo &e, float dy) { return fmaf(dy, fmaf(e.pc, dy, e.pb), e.pa); }
+// G = 2^x (x = expo_at(...) <= 0 for a positive definite conic)
+__device__ __forceinline__ float falloff(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Waits (bounded) for the batches issued but not yet consumed, so that no
 // bulk copy is still writing this CTA's shared memory when it exits.
@@ -187,7 +197,8 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     }
 
     const float fx = (float)tc.px;
-    float fy[PX], T[PX], C0[PX], C1[PX], C2[PX], D[PX];
+    float fy[PX], T[PX];
+    f2 Ca[PX], Cb[PX];  // blended (r, g), (b, depth)
     f2 F[PX][NF > 0 ? NF / 2 : 1];  // feature accumulators, channel pairs
     uint32_t last[PX];
     bool done[PX];
@@ -195,7 +206,7 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     for (int q = 0; q < PX; ++q) {
         fy[q] = (float)(tc.py0 + RS * q);
         T[q] = 1.f;
-        C0[q] = C1[q] = C2[q] = D[q] = 0.f;
+        Ca[q] = Cb[q] = 0ull;
 #pragma unroll
         for (int c = 0; c < NF / 2; ++c) F[q][c] = 0ull;
         last[q] = 0u;
@@ -233,7 +244,7 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
-                alpha[q] = fminf(bp.alpha_max, g.w * __expf(expo_at(ex, fy[q] - g.y)));
+                alpha[q] = fminf(bp.alpha_max, g.w * falloff(expo_at(ex, fy[q] - g.y)));
                 Tn[q] = T[q] * (1.f - alpha[q]);
                 use[q] = !done[q] && alpha[q] >= bp.alpha_min;
                 const bool stop = use[q] && Tn[q] < bp.t_min;
@@ -243,15 +254,14 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             const float4 col = S.color[j];
+            const f2 ca = f2_make(col.x, col.y), cb = f2_make(col.z, g.z);
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
                 if (!use[q]) continue;
                 const float w = alpha[q] * T[q];
-                C0[q] = fmaf(w, col.x, C0[q]);
-                C1[q] = fmaf(w, col.y, C1[q]);
-                C2[q] = fmaf(w, col.z, C2[q]);
-                D[q] = fmaf(w, g.z, D[q]);
                 const f2 w2 = f2_make(w, w);
+                Ca[q] = f2_fma(w2, ca, Ca[q]);
+                Cb[q] = f2_fma(w2, cb, Cb[q]);
 #pragma unroll
                 for (int c = 0; c < NF; c += 4) {
                     const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.feat[j][c]);
@@ -287,10 +297,13 @@ __global__ void __launch_bounds__(Px<PX>::NT) k_composite_fwd(
     for (int q = 0; q < PX; ++q) {
         if (!tc.in[q]) continue;
         const size_t p = (size_t)(tc.py0 + RS * q) * cam.W + tc.px;
-        out_color[3 * P + p] = C0[q];
-        out_color[3 * P + HW + p] = C1[q];
-        out_color[3 * P + 2 * HW + p] = C2[q];
-        out_depth[P + p] = D[q];
+        float c0, c1, c2, d;
+        f2_split(Ca[q], c0, c1);
+        f2_split(Cb[q], c2, d);
+        out_color[3 * P + p] = c0;
+        out_color[3 * P + HW + p] = c1;
+        out_color[3 * P + 2 * HW + p] = c2;
+        out_depth[P + p] = d;
 #pragma unroll
         for (int c = 0; c < NF / 2; ++c) {
             out_feat[NF * P + 2 * c * HW + p] = f2_lo(F[q][c]);
@@ -376,7 +389,10 @@ __global__ void k_scale_mean(const float4 *__restrict__ scale, size_t n, float c
 // backward
 // ---------------------------------------------------------------------------
 
-constexpr int kBwdStages = 3;
+#ifndef UPS_BWD_STAGES
+#define UPS_BWD_STAGES 3
+#endif
+constexpr int kBwdStages = UPS_BWD_STAGES;
 // Tuning of the backward (compile-time): CTAs per SM the register allocation
 // targets at 4 pixels per thread (8 caps registers at 128), and whether a warp
 // skips a pixel row no lane of it blends (a vote per row) or runs it masked.
@@ -394,8 +410,8 @@ constexpr int kRedStride = 36;  // floats per lane row of the reduction scratch
 // adds them to rec (16-byte aligned) with one vector atomic per group.  The
 // lanes write their groups to a [32][kRedStride] scratch row (16-byte stores,
 // conflict-free), lane l then sums rows 8 (l / 8) .. 8 (l / 8) + 7 of column
-// group l % 8 (a 32-float chunk at a time), and two butterfly steps over
-// l / 8 finish the sums.  All 32 lanes must call it.
+// group l % 8 (a 32-float chunk at a time) in packed pairs, and two butterfly
+// steps over l / 8 finish the sums.  All 32 lanes must call it.
 template <int NG>
 __device__ __forceinline__ void warp_record_add(const float4 (&v)[NG], float (*red)[kRedStride], int lane,
                                                 float *rec) {
@@ -407,24 +423,23 @@ __device__ __forceinline__ void warp_record_add(const float4 (&v)[NG], float (*r
         for (int k = 0; k < kMax; ++k)
             if (c0 + k < NG) *reinterpret_cast<float4 *>(&red[lane][4 * k]) = v[c0 + k];
         __syncwarp();
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        f2 s01 = 0ull, s23 = 0ull;  // packed pairs of the group's four sums
         if (c0 + col < NG) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const float4 x = *reinterpret_cast<const float4 *>(&red[8 * rq + r][4 * col]);
-                sum.x += x.x;
-                sum.y += x.y;
-                sum.z += x.z;
-                sum.w += x.w;
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(&red[8 * rq + r][4 * col]);
+                s01 = r == 0 ? x.x : f2_add(s01, x.x);
+                s23 = r == 0 ? x.y : f2_add(s23, x.y);
             }
         }
 #pragma unroll
         for (int o = 8; o <= 16; o <<= 1) {
-            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
-            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
-            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, o);
-            sum.w += __shfl_xor_sync(0xffffffffu, sum.w, o);
+            s01 = f2_add(s01, __shfl_xor_sync(0xffffffffu, s01, o));
+            s23 = f2_add(s23, __shfl_xor_sync(0xffffffffu, s23, o));
         }
+        float4 sum;
+        f2_split(s01, sum.x, sum.y);
+        f2_split(s23, sum.z, sum.w);
         if (rq == 0 && c0 + col < NG) atomicAdd(reinterpret_cast<float4 *>(rec) + c0 + col, sum);
         __syncwarp();
     }
@@ -455,14 +470,16 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
     const DevView &cam = *tc.cam;
     const size_t HW = (size_t)cam.W * cam.H;
     const size_t P = (size_t)cam.pix_off;
-    float T[PX], acc[PX], gC0[PX], gC1[PX], gC2[PX], gD[PX];
+    float T[PX], acc[PX];
+    f2 gCa[PX], gCb[PX];             // (dL/dC_r, dL/dC_g), (dL/dC_b, dL/dD) per pixel
     f2 gF[PX][NF > 0 ? NF / 2 : 1];  // dL/d(feature image), channel pairs
     uint32_t nc[PX];
     uint32_t my_nc = 0;
 #pragma unroll
     for (int q = 0; q < PX; ++q) {
         T[q] = 1.f;
-        acc[q] = gC0[q] = gC1[q] = gC2[q] = gD[q] = 0.f;
+        acc[q] = 0.f;
+        gCa[q] = gCb[q] = 0ull;
         nc[q] = 0u;
 #pragma unroll
         for (int c = 0; c < NF / 2; ++c) gF[q][c] = 0ull;
@@ -470,12 +487,8 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
         const size_t p = (size_t)(tc.py0 + RS * q) * cam.W + tc.px;
         T[q] = in_T[P + p];
         nc[q] = in_nc[P + p];
-        if (dC) {
-            gC0[q] = dC[3 * P + p];
-            gC1[q] = dC[3 * P + HW + p];
-            gC2[q] = dC[3 * P + 2 * HW + p];
-        }
-        if (dD) gD[q] = dD[P + p];
+        gCa[q] = f2_make(dC ? dC[3 * P + p] : 0.f, dC ? dC[3 * P + HW + p] : 0.f);
+        gCb[q] = f2_make(dC ? dC[3 * P + 2 * HW + p] : 0.f, dD ? dD[P + p] : 0.f);
         if (dF)
 #pragma unroll
             for (int c = 0; c < NF / 2; ++c)
@@ -542,13 +555,14 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
                 dy[q] = fy[q] - g.y;
-                G[q] = __expf(expo_at(ex, dy[q]));
+                G[q] = falloff(expo_at(ex, dy[q]));
                 alpha[q] = fminf(bp.alpha_max, g.w * G[q]);
                 use[q] = idx < (int)nc[q] && alpha[q] >= bp.alpha_min;
                 any = any || use[q];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             const float4 col = S.color[j];
+            const f2 ca = f2_make(col.x, col.y), cb = f2_make(col.z, g.z);
             f2 fj[NF > 0 ? NF / 2 : 1];
 #pragma unroll
             for (int c = 0; c < NF; c += 4) {
@@ -556,9 +570,13 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
                 fj[c / 2] = f.x;
                 fj[c / 2 + 1] = f.y;
             }
-            // per-thread sums over its pixels: the conic and mean terms need only
-            // sum dq, sum dq dy and sum dq dy^2 (dx is the thread's)
-            float sdq = 0.f, sdqy = 0.f, sdqyy = 0.f, sop = 0.f, sz = 0.f, sc0 = 0.f, sc1 = 0.f, sc2 = 0.f;
+            // per-thread sums over its pixels.  With t = dL/dalpha * G for an
+            // unclamped alpha (0 otherwise), dL/do = sum t and the exponent
+            // p = pa + dy (pb + pc dy) has dL/dp = o t per pixel, so the conic
+            // and mean terms need only sum t, sum t dy and sum t dy^2 (dx is
+            // the thread's), scaled by o once per Gaussian.
+            float sop = 0.f, sty = 0.f, styy = 0.f;
+            f2 sca = 0ull, scb = 0ull;  // sum w (dL/dC_r, dL/dC_g), sum w (dL/dC_b, dL/dD)
             f2 vF[NF > 0 ? NF / 2 : 1];
 #pragma unroll
             for (int c = 0; c < NF / 2; ++c) vF[c] = 0ull;
@@ -569,35 +587,38 @@ __global__ void __launch_bounds__(Px<PX>::NT, PX == 4 ? kBwdMinBlocks : 1) k_com
                 const float rom = use[q] ? __fdividef(1.f, 1.f - a) : 1.f;
                 T[q] *= rom;  // transmittance in front of this Gaussian
                 const float w = a * T[q];
-                f2 xg2 = 0ull;
                 const f2 w2 = f2_make(w, w);
+                f2 xg2 = f2_fma(cb, gCb[q], f2_fma(ca, gCa[q], 0ull));
 #pragma unroll
                 for (int c = 0; c < NF / 2; ++c) {
                     xg2 = f2_fma(fj[c], gF[q][c], xg2);
                     vF[c] = f2_fma(w2, gF[q][c], vF[c]);
                 }
-                float xlo = 0.f, xhi = 0.f;
-                if (NF > 0) f2_split(xg2, xlo, xhi);
-                const float xg = fmaf(col.x, gC0[q], fmaf(col.y, gC1[q], fmaf(col.z, gC2[q], fmaf(g.z, gD[q], xlo + xhi))));
-                const float dal = use[q] ? T[q] * xg - acc[q] * rom : 0.f;
+                float xlo, xhi;
+                f2_split(xg2, xlo, xhi);
+                const float xg = xlo + xhi;  // dL/d(blended value) . (c, z, f) of this Gaussian
+                // dL/dalpha where alpha is not clamped, 0 elsewhere
+                const float dal = use[q] && alpha[q] < bp.alpha_max ? T[q] * xg - acc[q] * rom : 0.f;
                 acc[q] = fmaf(w, xg, acc[q]);
-                const bool free = g.w * G[q] < bp.alpha_max;  // alpha not clamped
-                sop = fmaf(dal, free ? G[q] : 0.f, sop);
-                const float dq = free ? dal * (-0.5f * a) : 0.f;
-                sdq += dq;
-                const float dqy = dq * dy[q];
-                sdqy += dqy;
-                sdqyy = fmaf(dqy, dy[q], sdqyy);
-                sz = fmaf(w, gD[q], sz);
-                sc0 = fmaf(w, gC0[q], sc0);
-                sc1 = fmaf(w, gC1[q], sc1);
-                sc2 = fmaf(w, gC2[q], sc2);
+                const float t = dal * G[q];
+                sop += t;
+                const float ty = t * dy[q];
+                sty += ty;
+                styy = fmaf(ty, dy[q], styy);
+                sca = f2_fma(w2, gCa[q], sca);
+                scb = f2_fma(w2, gCb[q], scb);
             }
             // record groups: du dv dz do | dca dcb dcc - | dr dg db - | df...
             float4 v[NG];
-            v[0] = make_float4(-2.f * fmaf(cn.x * dx, sdq, cn.y * sdqy), -2.f * fmaf(cn.y * dx, sdq, cn.z * sdqy), sz,
+            // d(u, v) = o sum t (a dx + b dy, b dx + c dy) (dx, dy: pixel minus
+            // mean); d(a, b, c) = -o/2 sum t (dx^2, 2 dx dy, dy^2)
+            const float ho = -0.5f * g.w;
+            float sc0, sc1, sc2, sz;
+            f2_split(sca, sc0, sc1);
+            f2_split(scb, sc2, sz);
+            v[0] = make_float4(g.w * fmaf(cn.x * dx, sop, cn.y * sty), g.w * fmaf(cn.y * dx, sop, cn.z * sty), sz,
                                sop);
-            v[1] = make_float4(dx * dx * sdq, 2.f * dx * sdqy, sdqyy, 0.f);
+            v[1] = make_float4(ho * dx * dx * sop, -g.w * dx * sty, ho * styy, 0.f);
             v[2] = make_float4(sc0, sc1, sc2, 0.f);
 #pragma unroll
             for (int c = 0; c < NF / 4; ++c) {
