@@ -74,18 +74,20 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ void f2_split(f2 a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
 __device__ __forceinline__ float f2_lo(f2 a) {
     float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    f2_split(a, lo, hi);
+    (void)hi;
     return lo;
 }
 __device__ __forceinline__ float f2_hi(f2 a) {
     float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    f2_split(a, lo, hi);
+    (void)lo;
     return hi;
-}
-__device__ __forceinline__ void f2_split(f2 a, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
 }
 
 // Device buffer that only grows.

@@ -551,24 +551,120 @@ constexpr int kWait = 1 << 22;
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
                      // 16-byte vectors come first, at 16-byte multiples
     float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
-    float W1T[16][kLiftHidden];      // W1 transposed
+    f2 W1d[16][kLiftHidden];         // W1 transposed, each weight twice (an f32x2 operand)
     float b1[kLiftHidden], u[kLiftHidden];
-    float E[4][kLiftHidden];         // W2^T g of the cell's four corners
-    float Fc[16][lt::kHS];           // F~ of the chunk, channel-major
+    // a chunk's global inputs, two buffers (chunk parity), filled a chunk ahead
+    float E[2][4][kLiftHidden];      // W2^T g of the cell's four corners
+    float Fc[2][16][lt::kHS];        // F~ of the chunk, channel-major
+    float dF0[2][16][lt::kP];        // dL/dF~ accumulated before this call, channel-major
     float w4[lt::kP][4];             // bilinear weights of the chunk's pixels
     float ab[lt::kP][2];             // a_p, b_p
     float aw[lt::kP][4];             // a_p w_k(p)
     float Dpart[4][kLiftHidden];
-    float sS[4], sG[10];
+    float wpx[2][lt::kP];            // loss weights of the chunk's pixels
+    float sS[2][4], sG[2][12];       // s of the corners, the cell's corner Gram (10 used)
     int pix[lt::kP];                 // pixel index in the view, -1: none
+    int vwp[UPS_MAX_VIEWS], vhp[UPS_MAX_VIEWS], vbase[UPS_MAX_VIEWS];  // each view's patch grid, first cell
     uint64_t mh_bar, g_bar;
     uint32_t tmem_base;
     int abort_flag;
 };
-static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1T) % 16 == 0 &&
-                  offsetof(LiftTcSmem, Fc) % 16 == 0 && offsetof(LiftTcSmem, w4) % 16 == 0 &&
-                  offsetof(LiftTcSmem, ab) % 8 == 0 && offsetof(LiftTcSmem, mh_bar) % 8 == 0,
-              "vector and mbarrier alignment of the lifting kernel's shared arrays");
+static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1d) % 16 == 0 &&
+                  offsetof(LiftTcSmem, E) % 16 == 0 && offsetof(LiftTcSmem, Fc) % 16 == 0 &&
+                  offsetof(LiftTcSmem, dF0) % 16 == 0 &&
+                  offsetof(LiftTcSmem, w4) % 16 == 0 && offsetof(LiftTcSmem, ab) % 8 == 0 &&
+                  offsetof(LiftTcSmem, mh_bar) % 8 == 0,
+              "vector, bulk-copy and mbarrier alignment of the lifting kernel's shared arrays");
+
+// Pixel rectangle of cell `cell` of the patch grids (the pixels whose four
+// nearest patch centres are its corners) and its view, from the per-view grid
+// table in shared memory (the same numbering as cell_view).
+struct CellGeo {
+    int v, W, wp, hp, base, x0, y0, xs, ys, nx, npx;
+    size_t HW, P;
+};
+__device__ __forceinline__ CellGeo cell_geo(const LiftTcSmem &S, const ViewTable &vt, int patch, int cell) {
+    int v = 0;
+    while (v + 1 < vt.n && cell >= S.vbase[v + 1]) ++v;
+    const CellView cv{v, S.vwp[v], S.vhp[v], S.vbase[v]};
+    CellGeo g;
+    g.v = cv.v;
+    g.wp = cv.wp;
+    g.hp = cv.hp;
+    g.base = cv.base;
+    g.W = vt.v[cv.v].W;
+    const int H = vt.v[cv.v].H;
+    g.HW = (size_t)g.W * H;
+    g.P = (size_t)vt.v[cv.v].pix_off;
+    const int local = cell - cv.base;
+    g.y0 = local / cv.wp;
+    g.x0 = local - g.y0 * cv.wp;
+    g.xs = cell_start(g.x0, patch);
+    const int xe = g.x0 + 1 >= cv.wp ? g.W : min(g.W, cell_start(g.x0 + 1, patch));
+    g.ys = cell_start(g.y0, patch);
+    const int ye = g.y0 + 1 >= cv.hp ? H : min(H, cell_start(g.y0 + 1, patch));
+    g.nx = max(0, xe - g.xs);
+    g.npx = g.nx * max(0, ye - g.ys);
+    return g;
+}
+// corner k of the cell (bit 0: next column, bit 1: next row, clamped to the grid)
+__device__ __forceinline__ int cell_corner(const CellGeo &g, int k) {
+    const int x = (k & 1) ? min(g.x0 + 1, g.wp - 1) : g.x0, y = (k & 2) ? min(g.y0 + 1, g.hp - 1) : g.y0;
+    return g.base + y * g.wp + x;
+}
+
+// Asynchronous global-to-shared copies (cp.async): 4 bytes, zero-filled and
+// nothing read where !valid; 16 bytes; groups committed and waited per thread.
+__device__ __forceinline__ void cp_async4(void *dst, const float *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(umma::smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(umma::smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issues the copies of chunk (cell, q0)'s global inputs into buffer B (all
+// kT threads call it): F~ and dL/dF~ accumulated before the call (thread t:
+// pixel t % kP, channels t / kP + 4 r), the loss weights (t < kP), and the
+// cell's corner rows of E, s and its Gram.  Pixels past the cell's end read
+// nothing and hold 0.
+__device__ __forceinline__ void lift_chunk_issue(LiftTcSmem &S, int B, const ViewTable &vt, int patch, int cell,
+                                                 int q0, const float *__restrict__ feat_all,
+                                                 const float *__restrict__ d_feat_all,
+                                                 const float *__restrict__ weight_all, const float *__restrict__ E,
+                                                 const float *__restrict__ s, const float *__restrict__ gram, int tid) {
+    using namespace lt;
+    const CellGeo g = cell_geo(S, vt, patch, cell);
+    {
+        const int p = tid & (kP - 1), q = q0 + p;
+        const bool in = q < g.npx;
+        const int yq = in ? q / g.nx : 0;
+        const size_t pidx = in ? (size_t)(g.ys + yq) * g.W + g.xs + (q - yq * g.nx) : 0;
+        const float *feat = feat_all + (size_t)16 * g.P;
+        const float *df = d_feat_all ? d_feat_all + (size_t)16 * g.P : nullptr;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int c = (tid / kP) + 4 * r;
+            cp_async4(&S.Fc[B][c][p], feat + (size_t)c * g.HW + pidx, in);
+            if (df) cp_async4(&S.dF0[B][c][p], df + (size_t)c * g.HW + pidx, in);
+        }
+        if (weight_all && tid < kP) cp_async4(&S.wpx[B][p], weight_all + g.P + pidx, in);
+    }
+    if (tid < 128) {
+        const int k = tid >> 5, j4 = 4 * (tid & 31);
+        cp_async16(&S.E[B][k][j4], E + (size_t)cell_corner(g, k) * kLiftHidden + j4);
+    } else if (tid < 132) {
+        cp_async4(&S.sS[B][tid - 128], s + cell_corner(g, tid - 128), true);
+    } else if (tid < 142) {
+        cp_async4(&S.sG[B][tid - 132], gram + (size_t)cell * 10 + (tid - 132), true);
+    }
+}
 
 size_t lift_tc_smem_bytes() { return (size_t)lt::kOpBytes + sizeof(LiftTcSmem) + 1024; }
 
@@ -618,20 +714,28 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     int *__restrict__ err) {
     using namespace lt;
     constexpr int NF = 16;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *op = smem_raw + ((1024u - (umma::smem_addr(smem_raw) & 1023u)) & 1023u);
+    extern __shared__ __align__(1024) unsigned char smem_lt[];
+    unsigned char *op = smem_lt + ((1024u - (umma::smem_addr(smem_lt) & 1023u)) & 1023u);
     LiftTcSmem &S = *reinterpret_cast<LiftTcSmem *>(op + kOpBytes);
     const uint32_t sop = umma::smem_addr(op);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
-        S.W1T[c][j] = w1[i];
+        S.W1d[c][j] = f2_make(w1[i], w1[i]);
     }
     if (tid < kLiftHidden) {
         S.b1[tid] = b1[tid];
         S.u[tid] = u[tid];
     }
     if (tid == 0) {
+        int base = 0;
+        for (int v = 0; v < vt.n; ++v) {
+            const int wp = (vt.v[v].W + patch - 1) / patch, hp = (vt.v[v].H + patch - 1) / patch;
+            S.vwp[v] = wp;
+            S.vhp[v] = hp;
+            S.vbase[v] = base;
+            base += wp * hp;
+        }
         umma::mbar_init(&S.mh_bar, 1);
         umma::mbar_init(&S.g_bar, 1);
         S.abort_flag = 0;
@@ -666,7 +770,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     const float inv2p = 1.f / (float)(2 * patch);
     // Z phase: thread = 8 hidden (block jb) x 4 pixels (block pb)
     const int jb = tid >> 4, pb = tid & 15;
-    const int j0 = jb * 8, p0 = pb * 4;
+    const int j0 = jb * 8;
     float hb = 0.f, db1 = 0.f;
     constexpr int NC = NF / 16;
     f2 dw1[8][NC];  // pixel pairs (p, p + 1) and (p + 2, p + 3) of the sums, added at the end
@@ -679,32 +783,26 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
     const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128);
     float *red = reinterpret_cast<float *>(op + oRed);  // [4][kP][2]
+    // the chunk whose inputs are in flight to buffer buf (cell -1: none)
+    int pre_cell = -1, pre_q0 = 0, buf = 0;
+    if ((int)blockIdx.x < n_cells) {
+        lift_chunk_issue(S, 0, vt, patch, blockIdx.x, 0, feat_all, d_feat_all, weight_all, E, s, gram, tid);
+        pre_cell = blockIdx.x;
+    }
+    cp_async_commit();
     for (int cell = blockIdx.x; cell < n_cells && ok; cell += gridDim.x) {
-        const CellView cv = cell_view(vt, patch, cell);
-        const int wp = cv.wp, hp = cv.hp, W = vt.v[cv.v].W, H = vt.v[cv.v].H;
-        const size_t HW = (size_t)W * H, P = (size_t)vt.v[cv.v].pix_off;
-        const float *feat = feat_all + (size_t)NF * P;
+        const CellGeo cg = cell_geo(S, vt, patch, cell);
+        const int W = cg.W, nx = cg.nx, npx = cg.npx, xs = cg.xs, ys = cg.ys, x0 = cg.x0, y0 = cg.y0;
+        const size_t HW = cg.HW, P = cg.P;
         float *d_feat = d_feat_all ? d_feat_all + (size_t)NF * P : nullptr;
         const float *weight = weight_all ? weight_all + P : nullptr;
-        const int local = cell - cv.base;
-        const int cj = local / wp, ci = local - cj * wp;
-        const int x0 = ci, y0 = cj;
-        const int x1 = min(x0 + 1, wp - 1), y1 = min(y0 + 1, hp - 1);
-        const int corner[4] = {cv.base + y0 * wp + x0, cv.base + y0 * wp + x1, cv.base + y1 * wp + x0,
-                               cv.base + y1 * wp + x1};
-        const int xs = cell_start(ci, patch), xe = ci + 1 >= wp ? W : min(W, cell_start(ci + 1, patch));
-        const int ys = cell_start(cj, patch), ye = cj + 1 >= hp ? H : min(H, cell_start(cj + 1, patch));
-        const int nx = max(0, xe - xs), npx = nx * max(0, ye - ys);
+        const int corner[4] = {cell_corner(cg, 0), cell_corner(cg, 1), cell_corner(cg, 2), cell_corner(cg, 3)};
         __syncthreads();  // the previous cell's shared data is no longer read
-        for (int i = tid; i < 4 * kLiftHidden; i += kT)
-            S.E[i / kLiftHidden][i % kLiftHidden] = E[(size_t)corner[i / kLiftHidden] * kLiftHidden + i % kLiftHidden];
-        if (tid < 4) S.sS[tid] = s[corner[tid]];
-        if (tid < 10) S.sG[tid] = gram[(size_t)cell * 10 + tid];
         for (int i = tid; i < 4 * kLiftHidden; i += kT) (&S.Dpart[0][0])[i] = 0.f;
         float al[4] = {0.f, 0.f, 0.f, 0.f};  // sum a w_k over the cell (threads < kP)
         for (int q0 = 0; q0 < npx; q0 += kP) {
             __syncthreads();
-            // chunk pixels, bilinear weights, F~
+            // chunk pixels and their bilinear weights
             if (tid < kP) {
                 const int q = q0 + tid;
                 int pidx = -1;
@@ -723,12 +821,30 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
                 for (int k = 0; k < 4; ++k) S.w4[tid][k] = w[k];
             }
-            __syncthreads();
-            for (int i = tid; i < NF * kP; i += kT) {
-                const int c = i / kP, p = i - c * kP;
-                const int pidx = S.pix[p];
-                S.Fc[c][p] = pidx >= 0 ? feat[(size_t)c * HW + pidx] : 0.f;
+            // this chunk's global inputs were issued a chunk ahead (else now);
+            // the next chunk's go to the other buffer, whose last reader (the
+            // previous chunk) every thread has passed
+            if (pre_cell != cell || pre_q0 != q0) {
+                cp_async_wait<0>();
+                lift_chunk_issue(S, buf, vt, patch, cell, q0, feat_all, d_feat_all, weight_all, E, s, gram, tid);
+                cp_async_commit();
             }
+            {
+                int ncell = cell, nq0 = q0 + kP;
+                if (nq0 >= npx) {
+                    ncell = cell + gridDim.x;
+                    nq0 = 0;
+                }
+                pre_cell = -1;
+                if (ncell < n_cells) {
+                    lift_chunk_issue(S, buf ^ 1, vt, patch, ncell, nq0, feat_all, d_feat_all, weight_all, E, s, gram,
+                                     tid);
+                    pre_cell = ncell;
+                    pre_q0 = nq0;
+                }
+                cp_async_commit();
+            }
+            cp_async_wait<1>();
             // the previous chunk's Gram MMAs still read the H and b H tiles
             if (g_pending) {
                 const bool w_ok = umma::mbar_wait(&S.g_bar, g_phase, kWait);
@@ -747,19 +863,16 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             // A tile (row jt) and the FP32 transpose buffer Hh
             float hv[32];
             {
-                float wj[NF];
-#pragma unroll
-                for (int c = 0; c < NF; ++c) wj[c] = S.W1T[c][jt];
                 const float bj = S.b1[jt];
                 f2 z2[16];
 #pragma unroll
                 for (int t = 0; t < 16; ++t) z2[t] = f2_make(bj, bj);
 #pragma unroll 4
                 for (int c = 0; c < NF; ++c) {
-                    const f2 w2v = f2_make(wj[c], wj[c]);
+                    const f2 w2v = S.W1d[c][jt];
 #pragma unroll
                     for (int t4 = 0; t4 < 8; ++t4) {
-                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[c][ph + 4 * t4]);
+                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][c][ph + 4 * t4]);
                         z2[2 * t4] = f2_fma(w2v, f.x, z2[2 * t4]);
                         z2[2 * t4 + 1] = f2_fma(w2v, f.y, z2[2 * t4 + 1]);
                     }
@@ -834,7 +947,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
                 for (int t = 0; t < 16; ++t) mh[16 + t] = t16[t];
             }
-            const float e0 = S.E[0][jt], e1 = S.E[1][jt], e2 = S.E[2][jt], e3 = S.E[3][jt], uj = S.u[jt];
+            const float e0 = S.E[buf][0][jt], e1 = S.E[buf][1][jt], e2 = S.E[buf][2][jt], e3 = S.E[buf][3][jt],
+                        uj = S.u[jt];
             auto e_at = [&](int t) {
                 const float4 w = *reinterpret_cast<const float4 *>(&S.w4[ph + t][0]);
                 return w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
@@ -861,17 +975,18 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                     dmu += red[(b * kP + p) * 2 + 1];
                 }
                 const float *w = S.w4[p];
-                const float dot = de + w[0] * S.sS[0] + w[1] * S.sS[1] + w[2] * S.sS[2] + w[3] * S.sS[3];
-                const float nF2 = w[0] * w[0] * S.sG[0] + w[1] * w[1] * S.sG[4] + w[2] * w[2] * S.sG[7] +
-                                  w[3] * w[3] * S.sG[9] +
-                                  2.f * (w[0] * w[1] * S.sG[1] + w[0] * w[2] * S.sG[2] + w[0] * w[3] * S.sG[3] +
-                                         w[1] * w[2] * S.sG[5] + w[1] * w[3] * S.sG[6] + w[2] * w[3] * S.sG[8]);
+                const float *sS = S.sS[buf], *sG = S.sG[buf];
+                const float dot = de + w[0] * sS[0] + w[1] * sS[1] + w[2] * sS[2] + w[3] * sS[3];
+                const float nF2 = w[0] * w[0] * sG[0] + w[1] * w[1] * sG[4] + w[2] * w[2] * sG[7] +
+                                  w[3] * w[3] * sG[9] +
+                                  2.f * (w[0] * w[1] * sG[1] + w[0] * w[2] * sG[2] + w[0] * w[3] * sG[3] +
+                                         w[1] * w[2] * sG[5] + w[1] * w[3] * sG[6] + w[2] * w[3] * sG[8]);
                 const float nFh2 = dmu + bt;
                 float a = 0.f, b = 0.f;
                 const int pidx = S.pix[p];
                 if (pidx >= 0) {
                     const bool okp = nF2 > 0.f && nFh2 > 0.f;
-                    const float wpx = weight ? weight[pidx] : 1.f;
+                    const float wpx = weight ? S.wpx[buf][p] : 1.f;
                     const float g = g0 * wpx;
                     const float inv = okp ? rsqrtf(nF2) * rsqrtf(nFh2) : 0.f;
                     const float cs = dot * inv;
@@ -896,18 +1011,20 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const int p = ph + t;
-                    const float2 abp = *reinterpret_cast<const float2 *>(&S.ab[p][0]);
-                    const float dh = fmaf(abp.x, e_at(t), abp.y * (mh[t] + uj));
-                    const float dz = hv[t] > 0.f ? dh : 0.f;
+                    // dL/dH = a e_p + b (M H + u), a e_p = sum_k (a w_k) e_k
+                    const float bp = S.ab[p][1];
                     const float4 awp = *reinterpret_cast<const float4 *>(&S.aw[p][0]);
+                    const float dh =
+                        fmaf(awp.x, e0, fmaf(awp.y, e1, fmaf(awp.z, e2, fmaf(awp.w, e3, bp * (mh[t] + uj)))));
+                    const float dz = hv[t] > 0.f ? dh : 0.f;
                     Dk[0] = fmaf(awp.x, hv[t], Dk[0]);
                     Dk[1] = fmaf(awp.y, hv[t], Dk[1]);
                     Dk[2] = fmaf(awp.z, hv[t], Dk[2]);
                     Dk[3] = fmaf(awp.w, hv[t], Dk[3]);
                     db1 += dz;
-                    hb = fmaf(abp.y, hv[t], hb);
+                    hb = fmaf(bp, hv[t], hb);
                     mh[t] = dz;
-                    hv[t] *= abp.y;
+                    hv[t] *= bp;
                 }
 #pragma unroll
                 for (int t4 = 0; t4 < 8; ++t4)
@@ -942,24 +1059,32 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 // dF~ = W1^T dZ: thread (channel, 4 pixels); NF x kP outputs
                 for (int o = tid; o < NF * (kP / 4); o += kT) {
                     const int c = o / (kP / 4), pq = (o - c * (kP / 4)) * 4;
-                    f2 a01 = 0ull, a23 = 0ull;  // pixels (pq, pq + 1), (pq + 2, pq + 3)
+                    // pixels (pq, pq + 1), (pq + 2, pq + 3); even and odd hidden units apart
+                    f2 a01 = 0ull, a23 = 0ull, b01 = 0ull, b23 = 0ull;
 #pragma unroll 4
-                    for (int j = 0; j < kLiftHidden; ++j) {
-                        const float wv = S.W1T[c][j];
-                        const f2 w2v = f2_make(wv, wv);
-                        const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
-                        a01 = f2_fma(w2v, dz.x, a01);
-                        a23 = f2_fma(w2v, dz.y, a23);
+                    for (int j = 0; j < kLiftHidden; j += 2) {
+                        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W1d[c][j]);
+                        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
+                        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][pq]);
+                        a01 = f2_fma(w.x, z0.x, a01);
+                        a23 = f2_fma(w.x, z0.y, a23);
+                        b01 = f2_fma(w.y, z1.x, b01);
+                        b23 = f2_fma(w.y, z1.y, b23);
                     }
+                    a01 = f2_add(a01, b01);
+                    a23 = f2_add(a23, b23);
                     float acc[4];
                     f2_split(a01, acc[0], acc[1]);
                     f2_split(a23, acc[2], acc[3]);
-                    if (d_feat)
+                    if (d_feat) {
+                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][pq]);
+                        const float d0[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
                             const int pidx = S.pix[pq + y];
-                            if (pidx >= 0) d_feat[(size_t)c * HW + pidx] += acc[y];
+                            if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = d0[y] + acc[y];
                         }
+                    }
                 }
             }
             // dW1 += dZ F~^T: thread (8 hidden of block jb) x channel pb
@@ -967,7 +1092,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             for (int pq = 0; pq < kP; pq += 4) {
                 ulonglong2 fz[NC];
 #pragma unroll
-                for (int y = 0; y < NC; ++y) fz[y] = *reinterpret_cast<const ulonglong2 *>(&S.Fc[pb + 16 * y][pq]);
+                for (int y = 0; y < NC; ++y)
+                    fz[y] = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][pb + 16 * y][pq]);
 #pragma unroll
                 for (int x = 0; x < 8; ++x) {
                     const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j0 + x][pq]);
@@ -975,6 +1101,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                     for (int y = 0; y < NC; ++y) dw1[x][y] = f2_fma(dz.y, fz[y].y, f2_fma(dz.x, fz[y].x, dw1[x][y]));
                 }
             }
+            buf ^= 1;
         }
         if (!ok) break;
         __syncthreads();
@@ -987,6 +1114,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
             for (int k = 0; k < 4; ++k) atomicAdd(alpha + corner[k], al[k]);
     }
+    cp_async_wait<0>();  // no copy still writes shared memory
     // the last Gram MMAs (and an M H that a wait gave up on), then the CTA's sums
     if (mh_pending && !umma::mbar_wait(&S.mh_bar, mh_phase, kWait)) S.abort_flag = 1;
     if (g_pending) {
