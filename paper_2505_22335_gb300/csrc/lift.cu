@@ -551,7 +551,8 @@ constexpr int kWait = 1 << 22;
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
                      // 16-byte vectors come first, at 16-byte multiples
     float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
-    f2 W1d[16][kLiftHidden];         // W1 transposed, each weight twice (an f32x2 operand)
+    f2 W1d[16][kLiftHidden + 2];     // W1 transposed, each weight twice (an f32x2 operand); rows
+                                     // padded so that four rows fall in distinct banks
     float b1[kLiftHidden], u[kLiftHidden];
     // a chunk's global inputs, two buffers (chunk parity), filled a chunk ahead
     float E[2][4][kLiftHidden];      // W2^T g of the cell's four corners
@@ -561,6 +562,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     float ab[lt::kP][2];             // a_p, b_p
     float aw[lt::kP][4];             // a_p w_k(p)
     float Dpart[4][kLiftHidden];
+    float dW1s[16][kLiftHidden + 4]; // the CTA's dL/dW1, transposed (rows padded for the banks)
     float wpx[2][lt::kP];            // loss weights of the chunk's pixels
     float sS[2][4], sG[2][12];       // s of the corners, the cell's corner Gram (10 used)
     int pix[lt::kP];                 // pixel index in the view, -1: none
@@ -722,6 +724,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
         S.W1d[c][j] = f2_make(w1[i], w1[i]);
+        S.dW1s[c][j] = 0.f;
     }
     if (tid < kLiftHidden) {
         S.b1[tid] = b1[tid];
@@ -768,16 +771,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     umma::fence_after();
     const float bt = *beta;
     const float inv2p = 1.f / (float)(2 * patch);
-    // Z phase: thread = 8 hidden (block jb) x 4 pixels (block pb)
-    const int jb = tid >> 4, pb = tid & 15;
-    const int j0 = jb * 8;
     float hb = 0.f, db1 = 0.f;
-    constexpr int NC = NF / 16;
-    f2 dw1[8][NC];  // pixel pairs (p, p + 1) and (p + 2, p + 3) of the sums, added at the end
-#pragma unroll
-    for (int x = 0; x < 8; ++x)
-#pragma unroll
-        for (int y = 0; y < NC; ++y) dw1[x][y] = 0ull;
     float t_loss = 0.f, t_sb = 0.f;
     uint32_t mh_phase = 0, g_phase = 0;
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
@@ -1055,51 +1049,70 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             }
             g_started = true;
             g_pending = true;
-            {
-                // dF~ = W1^T dZ: thread (channel, 4 pixels); NF x kP outputs
-                for (int o = tid; o < NF * (kP / 4); o += kT) {
-                    const int c = o / (kP / 4), pq = (o - c * (kP / 4)) * 4;
-                    // pixels (pq, pq + 1), (pq + 2, pq + 3); even and odd hidden units apart
-                    f2 a01 = 0ull, a23 = 0ull, b01 = 0ull, b23 = 0ull;
+            if (warp < 4) {
+                // dF~ = W1^T dZ (warps 0-3): thread (channel c, pixels 4 g + [0, 4)
+                // and 32 + 4 g + [0, 4)), pixel pairs packed, even and odd hidden
+                // units in separate sums
+                if (d_feat) {
+                    const int c = tid >> 3, g = tid & 7;
+                    f2 a[4] = {0ull, 0ull, 0ull, 0ull}, b[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll 4
                     for (int j = 0; j < kLiftHidden; j += 2) {
                         const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W1d[c][j]);
-                        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
-                        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][pq]);
-                        a01 = f2_fma(w.x, z0.x, a01);
-                        a23 = f2_fma(w.x, z0.y, a23);
-                        b01 = f2_fma(w.y, z1.x, b01);
-                        b23 = f2_fma(w.y, z1.y, b23);
+                        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][4 * g]);
+                        const ulonglong2 z0b = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][32 + 4 * g]);
+                        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][4 * g]);
+                        const ulonglong2 z1b = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][32 + 4 * g]);
+                        a[0] = f2_fma(w.x, z0.x, a[0]);
+                        a[1] = f2_fma(w.x, z0.y, a[1]);
+                        a[2] = f2_fma(w.x, z0b.x, a[2]);
+                        a[3] = f2_fma(w.x, z0b.y, a[3]);
+                        b[0] = f2_fma(w.y, z1.x, b[0]);
+                        b[1] = f2_fma(w.y, z1.y, b[1]);
+                        b[2] = f2_fma(w.y, z1b.x, b[2]);
+                        b[3] = f2_fma(w.y, z1b.y, b[3]);
                     }
-                    a01 = f2_add(a01, b01);
-                    a23 = f2_add(a23, b23);
-                    float acc[4];
-                    f2_split(a01, acc[0], acc[1]);
-                    f2_split(a23, acc[2], acc[3]);
-                    if (d_feat) {
-                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][pq]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int p0 = 4 * g + 32 * h;
+                        float acc[4];
+                        f2_split(f2_add(a[2 * h], b[2 * h]), acc[0], acc[1]);
+                        f2_split(f2_add(a[2 * h + 1], b[2 * h + 1]), acc[2], acc[3]);
+                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][p0]);
                         const float d0[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
-                            const int pidx = S.pix[pq + y];
+                            const int pidx = S.pix[p0 + y];
                             if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = d0[y] + acc[y];
                         }
                     }
                 }
-            }
-            // dW1 += dZ F~^T: thread (8 hidden of block jb) x channel pb
+            } else if (d_w1) {
+                // dW1 += dZ F~^T (warps 4-7): thread (hidden units jb + 16 x, x < 8;
+                // channels cp and cp + 8), pixel pairs packed, into the CTA's sums
+                const int t = tid - 128, jb = t >> 3, cp = t & 7;
+                f2 acc[8][2];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) acc[x][0] = acc[x][1] = 0ull;
 #pragma unroll 2
-            for (int pq = 0; pq < kP; pq += 4) {
-                ulonglong2 fz[NC];
+                for (int pq = 0; pq < kP; pq += 4) {
+                    const ulonglong2 f0 = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][cp][pq]);
+                    const ulonglong2 f1 = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][cp + 8][pq]);
 #pragma unroll
-                for (int y = 0; y < NC; ++y)
-                    fz[y] = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][pb + 16 * y][pq]);
-#pragma unroll
-                for (int x = 0; x < 8; ++x) {
-                    const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j0 + x][pq]);
-#pragma unroll
-                    for (int y = 0; y < NC; ++y) dw1[x][y] = f2_fma(dz.y, fz[y].y, f2_fma(dz.x, fz[y].x, dw1[x][y]));
+                    for (int x = 0; x < 8; ++x) {
+                        const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[jb + 16 * x][pq]);
+                        acc[x][0] = f2_fma(dz.y, f0.y, f2_fma(dz.x, f0.x, acc[x][0]));
+                        acc[x][1] = f2_fma(dz.y, f1.y, f2_fma(dz.x, f1.x, acc[x][1]));
+                    }
                 }
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+#pragma unroll
+                    for (int y = 0; y < 2; ++y) {
+                        float lo, hi;
+                        f2_split(acc[x][y], lo, hi);
+                        S.dW1s[cp + 8 * y][jb + 16 * x] += lo + hi;
+                    }
             }
             buf ^= 1;
         }
@@ -1140,14 +1153,10 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
         atomicAdd(hb_out + jt, hb);
         if (d_b1) atomicAdd(d_b1 + jt, db1);
         if (d_w1)
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < NC; ++y) {
-                    float lo, hi;
-                    f2_split(dw1[x][y], lo, hi);
-                    atomicAdd(d_w1 + (size_t)(j0 + x) * NF + pb + 16 * y, lo + hi);
-                }
+            for (int i = tid; i < kLiftHidden * NF; i += kT) {
+                const int j = i / NF, c = i - j * NF;
+                atomicAdd(d_w1 + i, S.dW1s[c][j]);
+            }
         float v2[2] = {t_loss, t_sb};
 #pragma unroll
         for (int i = 0; i < 2; ++i)
