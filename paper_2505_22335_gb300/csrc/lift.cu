@@ -543,16 +543,15 @@ constexpr uint32_t kTmemCols = 512, cMH = 0, cG = 128, cMhi = 256, cMlo = 320, c
 constexpr int oHBhi = 0, oHBlo = 16384;        // H [64 p][128 k] (B of M H)
 constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gram)
 constexpr int kOpBytes = 65536;
-// in the M H B tile while it is free (after the chunk's M H):
-constexpr int oRed = oHBlo;  // float [4][64][2]: partial H.e, H.(MH + 2u) per 32 hidden units
 constexpr int kWait = 1 << 22;
+constexpr int kGramTid = 128;  // issues the Gram MMAs: a dW1 warp, whose work is the shorter
 }  // namespace lt
 
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
                      // 16-byte vectors come first, at 16-byte multiples
     float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
-    f2 W1d[16][kLiftHidden + 2];     // W1 transposed, each weight twice (an f32x2 operand); rows
-                                     // padded so that four rows fall in distinct banks
+    f2 W1d[16][kLiftHidden + 2];     // W1 transposed, each weight twice (an f32x2 operand)
+    f2 W2p[kLiftHidden][16];         // W1 (hidden-major), each weight twice
     float b1[kLiftHidden], u[kLiftHidden];
     // a chunk's global inputs, two buffers (chunk parity), filled a chunk ahead
     float E[2][4][kLiftHidden];      // W2^T g of the cell's four corners
@@ -562,6 +561,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     float ab[lt::kP][2];             // a_p, b_p
     float aw[lt::kP][4];             // a_p w_k(p)
     float Dpart[4][kLiftHidden];
+    float red[4][lt::kP][2];         // partial H.e, H.(M H + 2 u) per 32 hidden units
     float dW1s[16][kLiftHidden + 4]; // the CTA's dL/dW1, transposed (rows padded for the banks)
     float wpx[2][lt::kP];            // loss weights of the chunk's pixels
     float sS[2][4], sG[2][12];       // s of the corners, the cell's corner Gram (10 used)
@@ -572,6 +572,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     int abort_flag;
 };
 static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1d) % 16 == 0 &&
+                  offsetof(LiftTcSmem, W2p) % 16 == 0 &&
                   offsetof(LiftTcSmem, E) % 16 == 0 && offsetof(LiftTcSmem, Fc) % 16 == 0 &&
                   offsetof(LiftTcSmem, dF0) % 16 == 0 &&
                   offsetof(LiftTcSmem, w4) % 16 == 0 && offsetof(LiftTcSmem, ab) % 8 == 0 &&
@@ -724,6 +725,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
         S.W1d[c][j] = f2_make(w1[i], w1[i]);
+        S.W2p[j][c] = f2_make(w1[i], w1[i]);
         S.dW1s[c][j] = 0.f;
     }
     if (tid < kLiftHidden) {
@@ -776,7 +778,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     uint32_t mh_phase = 0, g_phase = 0;
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
     const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128);
-    float *red = reinterpret_cast<float *>(op + oRed);  // [4][kP][2]
+    float *red = &S.red[0][0][0];  // [4][kP][2]
     // the chunk whose inputs are in flight to buffer buf (cell -1: none)
     int pre_cell = -1, pre_q0 = 0, buf = 0;
     if ((int)blockIdx.x < n_cells) {
@@ -917,6 +919,21 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 umma::commit(&S.mh_bar);
             }
             mh_pending = true;
+            const float e0 = S.E[buf][0][jt], e1 = S.E[buf][1][jt], e2 = S.E[buf][2][jt], e3 = S.E[buf][3][jt],
+                        uj = S.u[jt];
+            auto e_at = [&](int t) {
+                const float4 w = *reinterpret_cast<const float4 *>(&S.w4[ph + t][0]);
+                return w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
+            };
+            // per pixel over this warp's 32 hidden units: H.e (while the M H
+            // MMAs run), then H.(M H + 2 u), the two sums the cosine needs
+            // (|F^|^2 = H.M H + 2 u.H + |b2|^2)
+            {
+                float v[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) v[t] = hv[t] * e_at(t);
+                red[((warp & 3) * kP + ph + lane) * 2 + 0] = warp_rs32(v, lane);
+            }
             {
                 const bool w_ok = umma::mbar_wait(&S.mh_bar, mh_phase, kWait);
                 if (w_ok) {
@@ -941,19 +958,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
 #pragma unroll
                 for (int t = 0; t < 16; ++t) mh[16 + t] = t16[t];
             }
-            const float e0 = S.E[buf][0][jt], e1 = S.E[buf][1][jt], e2 = S.E[buf][2][jt], e3 = S.E[buf][3][jt],
-                        uj = S.u[jt];
-            auto e_at = [&](int t) {
-                const float4 w = *reinterpret_cast<const float4 *>(&S.w4[ph + t][0]);
-                return w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
-            };
-            // per pixel over this warp's 32 hidden units: H.e and H.(M H + 2 u),
-            // the two sums the cosine needs (|F^|^2 = H.M H + 2 u.H + |b2|^2)
             {
                 float v[32];
-#pragma unroll
-                for (int t = 0; t < 32; ++t) v[t] = hv[t] * e_at(t);
-                red[((warp & 3) * kP + ph + lane) * 2 + 0] = warp_rs32(v, lane);
 #pragma unroll
                 for (int t = 0; t < 32; ++t) v[t] = hv[t] * fmaf(2.f, uj, mh[t]);
                 red[((warp & 3) * kP + ph + lane) * 2 + 1] = warp_rs32(v, lane);
@@ -1037,7 +1043,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             umma::fence_async_smem();
             __syncthreads();
             // Gram += H (b H)^T on the tensor cores, left running
-            if (tid == 0) {
+            if (tid == kGramTid) {
                 umma::fence_after();
                 for (int pass = 0; pass < 3; ++pass) {
                     const uint32_t a = tmem + (pass == 2 ? cHAlo : cHAhi), b = sop + (pass == 1 ? oBHlo : oBHhi);
@@ -1050,69 +1056,81 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             g_started = true;
             g_pending = true;
             if (warp < 4) {
-                // dF~ = W1^T dZ (warps 0-3): thread (channel c, pixels 4 g + [0, 4)
-                // and 32 + 4 g + [0, 4)), pixel pairs packed, even and odd hidden
-                // units in separate sums
+                // dF~ = W1^T dZ (warps 0-3): warp w sums hidden units [32 w, 32 w + 32)
+                // for all channels, lane l its pixels (2 l, 2 l + 1) as a packed pair;
+                // W1 comes in warp-uniform loads, and the four warps' partial sums
+                // meet in the M H operand tile, free until the next chunk
                 if (d_feat) {
-                    const int c = tid >> 3, g = tid & 7;
-                    f2 a[4] = {0ull, 0ull, 0ull, 0ull}, b[4] = {0ull, 0ull, 0ull, 0ull};
+                    f2 acc[NF];
+#pragma unroll
+                    for (int c = 0; c < NF; ++c) acc[c] = 0ull;
 #pragma unroll 4
-                    for (int j = 0; j < kLiftHidden; j += 2) {
-                        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W1d[c][j]);
-                        const ulonglong2 z0 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][4 * g]);
-                        const ulonglong2 z0b = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][32 + 4 * g]);
-                        const ulonglong2 z1 = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][4 * g]);
-                        const ulonglong2 z1b = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j + 1][32 + 4 * g]);
-                        a[0] = f2_fma(w.x, z0.x, a[0]);
-                        a[1] = f2_fma(w.x, z0.y, a[1]);
-                        a[2] = f2_fma(w.x, z0b.x, a[2]);
-                        a[3] = f2_fma(w.x, z0b.y, a[3]);
-                        b[0] = f2_fma(w.y, z1.x, b[0]);
-                        b[1] = f2_fma(w.y, z1.y, b[1]);
-                        b[2] = f2_fma(w.y, z1b.x, b[2]);
-                        b[3] = f2_fma(w.y, z1b.y, b[3]);
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int j = 32 * warp + jj;
+                        const f2 dz = *reinterpret_cast<const f2 *>(&S.Hh[j][2 * lane]);
+#pragma unroll
+                        for (int k = 0; k < NF / 2; ++k) {
+                            const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W2p[j][2 * k]);
+                            acc[2 * k] = f2_fma(w.x, dz, acc[2 * k]);
+                            acc[2 * k + 1] = f2_fma(w.y, dz, acc[2 * k + 1]);
+                        }
                     }
+                    float *part = reinterpret_cast<float *>(op + oHBhi);  // [4 warps][NF][kP]
+#pragma unroll
+                    for (int c = 0; c < NF; ++c)
+                        *reinterpret_cast<f2 *>(&part[(warp * NF + c) * kP + 2 * lane]) = acc[c];
+                    asm volatile("bar.sync 1, 128;" ::: "memory");  // warps 0-3 only
+                    // thread t: channel t / 8, pixels 8 (t % 8) + [0, 8)
+                    const int c = tid >> 3, p0 = 8 * (tid & 7);
+                    float o[8];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int p0 = 4 * g + 32 * h;
-                        float acc[4];
-                        f2_split(f2_add(a[2 * h], b[2 * h]), acc[0], acc[1]);
-                        f2_split(f2_add(a[2 * h + 1], b[2 * h + 1]), acc[2], acc[3]);
-                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][p0]);
-                        const float d0[4] = {d4.x, d4.y, d4.z, d4.w};
+                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][p0 + 4 * h]);
+                        o[4 * h] = d4.x;
+                        o[4 * h + 1] = d4.y;
+                        o[4 * h + 2] = d4.z;
+                        o[4 * h + 3] = d4.w;
+                    }
+                    float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) {
-                            const int pidx = S.pix[p0 + y];
-                            if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = d0[y] + acc[y];
+                    for (int w = 0; w < 4; ++w)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float4 v = *reinterpret_cast<const float4 *>(&part[(w * NF + c) * kP + p0 + 4 * h]);
+                            sum[4 * h] += v.x;
+                            sum[4 * h + 1] += v.y;
+                            sum[4 * h + 2] += v.z;
+                            sum[4 * h + 3] += v.w;
                         }
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) {
+                        const int pidx = S.pix[p0 + y];
+                        if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = o[y] + sum[y];
                     }
                 }
             } else if (d_w1) {
-                // dW1 += dZ F~^T (warps 4-7): thread (hidden units jb + 16 x, x < 8;
-                // channels cp and cp + 8), pixel pairs packed, into the CTA's sums
-                const int t = tid - 128, jb = t >> 3, cp = t & 7;
-                f2 acc[8][2];
+                // dW1 += dZ F~^T (warps 4-7): lane = hidden unit 32 (w - 4) + l, all
+                // channels, pixel pairs packed; F~ comes in warp-uniform loads, the
+                // chunk's sums go to the CTA's accumulator
+                const int j = 32 * (warp - 4) + lane;
+                f2 acc[NF];
 #pragma unroll
-                for (int x = 0; x < 8; ++x) acc[x][0] = acc[x][1] = 0ull;
-#pragma unroll 2
+                for (int c = 0; c < NF; ++c) acc[c] = 0ull;
+#pragma unroll 4
                 for (int pq = 0; pq < kP; pq += 4) {
-                    const ulonglong2 f0 = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][cp][pq]);
-                    const ulonglong2 f1 = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][cp + 8][pq]);
+                    const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
 #pragma unroll
-                    for (int x = 0; x < 8; ++x) {
-                        const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[jb + 16 * x][pq]);
-                        acc[x][0] = f2_fma(dz.y, f0.y, f2_fma(dz.x, f0.x, acc[x][0]));
-                        acc[x][1] = f2_fma(dz.y, f1.y, f2_fma(dz.x, f1.x, acc[x][1]));
+                    for (int c = 0; c < NF; ++c) {
+                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][c][pq]);
+                        acc[c] = f2_fma(dz.y, f.y, f2_fma(dz.x, f.x, acc[c]));
                     }
                 }
 #pragma unroll
-                for (int x = 0; x < 8; ++x)
-#pragma unroll
-                    for (int y = 0; y < 2; ++y) {
-                        float lo, hi;
-                        f2_split(acc[x][y], lo, hi);
-                        S.dW1s[cp + 8 * y][jb + 16 * x] += lo + hi;
-                    }
+                for (int c = 0; c < NF; ++c) {
+                    float lo, hi;
+                    f2_split(acc[c], lo, hi);
+                    S.dW1s[c][j] += lo + hi;
+                }
             }
             buf ^= 1;
         }
