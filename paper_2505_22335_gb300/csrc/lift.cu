@@ -539,12 +539,14 @@ constexpr int kHS = kP + 4;  // row stride of the FP32 hidden-major arrays
 // TMEM columns; the A operands (M, and H as the Gram's A) sit in TMEM as BF16
 // pairs (row = lane), so the MMAs read only their B operands from shared memory
 constexpr uint32_t kTmemCols = 512, cMH = 0, cG = 128, cMhi = 256, cMlo = 320, cHAhi = 384, cHAlo = 416;
+// dW1 accumulator (16 columns) and dZ as its A operand (BF16 hi / lo pairs)
+constexpr uint32_t cDW = 64, cDZhi = 448, cDZlo = 480;
 // BF16 B operand tiles in shared memory, canonical K-major without swizzle (byte offsets)
 constexpr int oHBhi = 0, oHBlo = 16384;        // H [64 p][128 k] (B of M H)
 constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gram)
 constexpr int kOpBytes = 65536;
 constexpr int kWait = 1 << 22;
-constexpr int kGramTid = 128;  // issues the Gram MMAs: a dW1 warp, whose work is the shorter
+constexpr int kGramTid = 128;  // issues the Gram and dW1 MMAs
 }  // namespace lt
 
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
@@ -562,7 +564,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     float aw[lt::kP][4];             // a_p w_k(p)
     float Dpart[4][kLiftHidden];
     float red[4][lt::kP][2];         // partial H.e, H.(M H + 2 u) per 32 hidden units
-    float dW1s[16][kLiftHidden + 4]; // the CTA's dL/dW1, transposed (rows padded for the banks)
+    uint32_t FcT[2][512];            // F~ as BF16 hi / lo, K-major [16 channels][64 pixels] (B of dW1)
     float wpx[2][lt::kP];            // loss weights of the chunk's pixels
     float sS[2][4], sG[2][12];       // s of the corners, the cell's corner Gram (10 used)
     int pix[lt::kP];                 // pixel index in the view, -1: none
@@ -572,7 +574,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     int abort_flag;
 };
 static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1d) % 16 == 0 &&
-                  offsetof(LiftTcSmem, W2p) % 16 == 0 &&
+                  offsetof(LiftTcSmem, W2p) % 16 == 0 && offsetof(LiftTcSmem, FcT) % 16 == 0 &&
                   offsetof(LiftTcSmem, E) % 16 == 0 && offsetof(LiftTcSmem, Fc) % 16 == 0 &&
                   offsetof(LiftTcSmem, dF0) % 16 == 0 &&
                   offsetof(LiftTcSmem, w4) % 16 == 0 && offsetof(LiftTcSmem, ab) % 8 == 0 &&
@@ -726,7 +728,6 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
         const int j = i / NF, c = i - j * NF;
         S.W1d[c][j] = f2_make(w1[i], w1[i]);
         S.W2p[j][c] = f2_make(w1[i], w1[i]);
-        S.dW1s[c][j] = 0.f;
     }
     if (tid < kLiftHidden) {
         S.b1[tid] = b1[tid];
@@ -777,7 +778,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     float t_loss = 0.f, t_sb = 0.f;
     uint32_t mh_phase = 0, g_phase = 0;
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
-    const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128);
+    const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128),
+                   id_dw = umma::idesc(umma::kBF16, 128, NF);
     float *red = &S.red[0][0][0];  // [4][kP][2]
     // the chunk whose inputs are in flight to buffer buf (cell -1: none)
     int pre_cell = -1, pre_q0 = 0, buf = 0;
@@ -854,6 +856,16 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 break;
             }
             umma::fence_after();
+            // F~ as the BF16 hi / lo B tile of dW1 (channel rows, pixels along K);
+            // the previous chunk's dW1 MMAs, which read it, completed with the Gram's
+            if (d_w1 && tid < 128) {
+                const int c = tid >> 3, p8 = 8 * (tid & 7);
+                const float4 f0 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8]);
+                const float4 f1 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8 + 4]);
+                const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                put8_split(reinterpret_cast<unsigned char *>(S.FcT[0]), reinterpret_cast<unsigned char *>(S.FcT[1]),
+                           umma::kmajor_offset(c, p8, 2 * kP, 2), v);
+            }
             // H = relu(W1 F~ + b1) of (jt, pixel half) in FP32, each element the
             // fmaf chain from b1 over the channels in order: registers, the Gram
             // A tile (row jt) and the FP32 transpose buffer Hh
@@ -1038,6 +1050,14 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) atomicAdd(&S.Dpart[k][jt], Dk[k]);
+                if (d_w1) {  // dZ as the A operand of dW1 (row jt, pixel pairs)
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) split2_bf16(mh[2 * q], mh[2 * q + 1], hi[q], lo[q]);
+                    umma::tmem_st16(lane_addr + cDZhi + ph / 2, hi);
+                    umma::tmem_st16(lane_addr + cDZlo + ph / 2, lo);
+                    umma::tmem_st_wait();
+                }
             }
             umma::fence_before();
             umma::fence_async_smem();
@@ -1051,85 +1071,61 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                         umma::mma_f16_ts(tmem + cG, a + 8u * ks, umma::desc(b + 256u * ks, 2 * kP), id_g,
                                          (g_started || pass > 0 || ks > 0) ? 1u : 0u);
                 }
+                // dW1 += dZ F~^T: A = dZ in TMEM, B = the F~ tile, accumulated over the CTA's chunks
+                if (d_w1) {
+                    const uint32_t fhi = umma::smem_addr(S.FcT[0]), flo = umma::smem_addr(S.FcT[1]);
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const uint32_t a = tmem + (pass == 2 ? cDZlo : cDZhi), b = pass == 1 ? flo : fhi;
+                        for (int ks = 0; ks < kP / 16; ++ks)
+                            umma::mma_f16_ts(tmem + cDW, a + 8u * ks, umma::desc(b + 256u * ks, 2 * kP), id_dw,
+                                             (g_started || pass > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
                 umma::commit(&S.g_bar);
             }
             g_started = true;
             g_pending = true;
-            if (warp < 4) {
-                // dF~ = W1^T dZ (warps 0-3): warp w sums hidden units [32 w, 32 w + 32)
-                // for all channels, lane l its pixels (2 l, 2 l + 1) as a packed pair;
-                // W1 comes in warp-uniform loads, and the four warps' partial sums
-                // meet in the M H operand tile, free until the next chunk
-                if (d_feat) {
-                    f2 acc[NF];
-#pragma unroll
-                    for (int c = 0; c < NF; ++c) acc[c] = 0ull;
-#pragma unroll 4
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int j = 32 * warp + jj;
-                        const f2 dz = *reinterpret_cast<const f2 *>(&S.Hh[j][2 * lane]);
-#pragma unroll
-                        for (int k = 0; k < NF / 2; ++k) {
-                            const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W2p[j][2 * k]);
-                            acc[2 * k] = f2_fma(w.x, dz, acc[2 * k]);
-                            acc[2 * k + 1] = f2_fma(w.y, dz, acc[2 * k + 1]);
-                        }
-                    }
-                    float *part = reinterpret_cast<float *>(op + oHBhi);  // [4 warps][NF][kP]
-#pragma unroll
-                    for (int c = 0; c < NF; ++c)
-                        *reinterpret_cast<f2 *>(&part[(warp * NF + c) * kP + 2 * lane]) = acc[c];
-                    asm volatile("bar.sync 1, 128;" ::: "memory");  // warps 0-3 only
-                    // thread t: channel t / 8, pixels 8 (t % 8) + [0, 8)
-                    const int c = tid >> 3, p0 = 8 * (tid & 7);
-                    float o[8];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][p0 + 4 * h]);
-                        o[4 * h] = d4.x;
-                        o[4 * h + 1] = d4.y;
-                        o[4 * h + 2] = d4.z;
-                        o[4 * h + 3] = d4.w;
-                    }
-                    float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int w = 0; w < 4; ++w)
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float4 v = *reinterpret_cast<const float4 *>(&part[(w * NF + c) * kP + p0 + 4 * h]);
-                            sum[4 * h] += v.x;
-                            sum[4 * h + 1] += v.y;
-                            sum[4 * h + 2] += v.z;
-                            sum[4 * h + 3] += v.w;
-                        }
-#pragma unroll
-                    for (int y = 0; y < 8; ++y) {
-                        const int pidx = S.pix[p0 + y];
-                        if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = o[y] + sum[y];
-                    }
-                }
-            } else if (d_w1) {
-                // dW1 += dZ F~^T (warps 4-7): lane = hidden unit 32 (w - 4) + l, all
-                // channels, pixel pairs packed; F~ comes in warp-uniform loads, the
-                // chunk's sums go to the CTA's accumulator
-                const int j = 32 * (warp - 4) + lane;
+            if (d_feat) {
+                // dF~ = W1^T dZ: warp w sums hidden units [16 w, 16 w + 16) for all
+                // channels, lane l its pixels (2 l, 2 l + 1) as a packed pair; W1 comes
+                // in warp-uniform loads, and the eight warps' partial sums meet in the
+                // M H operand tile, free until the next chunk
                 f2 acc[NF];
 #pragma unroll
                 for (int c = 0; c < NF; ++c) acc[c] = 0ull;
 #pragma unroll 4
-                for (int pq = 0; pq < kP; pq += 4) {
-                    const ulonglong2 dz = *reinterpret_cast<const ulonglong2 *>(&S.Hh[j][pq]);
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int j = 16 * warp + jj;
+                    const f2 dz = *reinterpret_cast<const f2 *>(&S.Hh[j][2 * lane]);
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) {
-                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][c][pq]);
-                        acc[c] = f2_fma(dz.y, f.y, f2_fma(dz.x, f.x, acc[c]));
+                    for (int k = 0; k < NF / 2; ++k) {
+                        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W2p[j][2 * k]);
+                        acc[2 * k] = f2_fma(w.x, dz, acc[2 * k]);
+                        acc[2 * k + 1] = f2_fma(w.y, dz, acc[2 * k + 1]);
                     }
                 }
+                float *part = reinterpret_cast<float *>(op + oHBhi);  // [8 warps][NF][kP]
 #pragma unroll
-                for (int c = 0; c < NF; ++c) {
-                    float lo, hi;
-                    f2_split(acc[c], lo, hi);
-                    S.dW1s[c][j] += lo + hi;
+                for (int c = 0; c < NF; ++c)
+                    *reinterpret_cast<f2 *>(&part[(warp * NF + c) * kP + 2 * lane]) = acc[c];
+                __syncthreads();
+                // thread t: channel t / 16, pixels 4 (t % 16) + [0, 4)
+                const int c = tid >> 4, p0 = 4 * (tid & 15);
+                const float4 d4 = *reinterpret_cast<const float4 *>(&S.dF0[buf][c][p0]);
+                float sum[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const float4 v = *reinterpret_cast<const float4 *>(&part[(w * NF + c) * kP + p0]);
+                    sum[0] += v.x;
+                    sum[1] += v.y;
+                    sum[2] += v.z;
+                    sum[3] += v.w;
+                }
+                const float o[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int pidx = S.pix[p0 + y];
+                    if (pidx >= 0) d_feat[(size_t)c * HW + pidx] = o[y] + sum[y];
                 }
             }
             buf ^= 1;
@@ -1170,11 +1166,12 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     if (ok) {
         atomicAdd(hb_out + jt, hb);
         if (d_b1) atomicAdd(d_b1 + jt, db1);
-        if (d_w1)
-            for (int i = tid; i < kLiftHidden * NF; i += kT) {
-                const int j = i / NF, c = i - j * NF;
-                atomicAdd(d_w1 + i, S.dW1s[c][j]);
-            }
+        if (d_w1 && g_started && warp < 4) {  // dW1 row jt from TMEM
+            float d[16];
+            umma::tmem_ld16(lane_addr + cDW, d);
+#pragma unroll
+            for (int c = 0; c < NF; ++c) atomicAdd(d_w1 + (size_t)jt * NF + c, d[c]);
+        }
         float v2[2] = {t_loss, t_sb};
 #pragma unroll
         for (int i = 0; i < 2; ++i)
