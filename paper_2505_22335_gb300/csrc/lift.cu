@@ -552,7 +552,8 @@ constexpr int kGramTid = 128;  // issues the Gram and dW1 MMAs
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
                      // 16-byte vectors come first, at 16-byte multiples
     float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
-    f2 W1d[16][kLiftHidden + 2];     // W1 transposed, each weight twice (an f32x2 operand)
+    float W1A[2][kLiftHidden * 16];  // W1 as TF32 hi / lo, K-major [128 hidden][16 channels] (A of Z)
+    float FcN[2][lt::kP * 16];       // F~ as TF32 hi / lo, K-major [64 pixels][16 channels] (B of Z)
     f2 W2p[kLiftHidden][16];         // W1 (hidden-major), each weight twice
     float b1[kLiftHidden], u[kLiftHidden];
     // a chunk's global inputs, two buffers (chunk parity), filled a chunk ahead
@@ -573,7 +574,8 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     uint32_t tmem_base;
     int abort_flag;
 };
-static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1d) % 16 == 0 &&
+static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1A) % 16 == 0 &&
+                  offsetof(LiftTcSmem, FcN) % 16 == 0 &&
                   offsetof(LiftTcSmem, W2p) % 16 == 0 && offsetof(LiftTcSmem, FcT) % 16 == 0 &&
                   offsetof(LiftTcSmem, E) % 16 == 0 && offsetof(LiftTcSmem, Fc) % 16 == 0 &&
                   offsetof(LiftTcSmem, dF0) % 16 == 0 &&
@@ -682,6 +684,22 @@ __device__ __forceinline__ void split2_bf16(float a, float b, uint32_t &hi, uint
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// 4 values as one 16-byte core-matrix row of the TF32 hi and of the lo tile
+// (hi = tf32(x), lo = tf32(x - hi))
+__device__ __forceinline__ void put4_tf32(float *hi, float *lo, uint32_t off, float4 v) {
+    float4 h, l;
+    h.x = umma::tf32_hi(v.x);
+    h.y = umma::tf32_hi(v.y);
+    h.z = umma::tf32_hi(v.z);
+    h.w = umma::tf32_hi(v.w);
+    l.x = umma::tf32_hi(v.x - h.x);
+    l.y = umma::tf32_hi(v.y - h.y);
+    l.z = umma::tf32_hi(v.z - h.z);
+    l.w = umma::tf32_hi(v.w - h.w);
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi) + off) = h;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo) + off) = l;
+}
+
 // 8 values as one 16-byte core-matrix row of the hi and of the lo tile
 __device__ __forceinline__ void put8_split(unsigned char *hi, unsigned char *lo, uint32_t off, const float (&v)[8]) {
     uint4 h, l;
@@ -726,8 +744,13 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
-        S.W1d[c][j] = f2_make(w1[i], w1[i]);
         S.W2p[j][c] = f2_make(w1[i], w1[i]);
+    }
+    for (int i = tid; i < kLiftHidden * (NF / 4); i += kT) {  // W1 row j, channels 4 q + [0, 4)
+        const int j = i / (NF / 4), q = i % (NF / 4);
+        const float4 v = make_float4(w1[j * NF + 4 * q], w1[j * NF + 4 * q + 1], w1[j * NF + 4 * q + 2],
+                                     w1[j * NF + 4 * q + 3]);
+        put4_tf32(S.W1A[0], S.W1A[1], umma::kmajor_offset(j, 4 * q, 4 * NF, 4), v);
     }
     if (tid < kLiftHidden) {
         S.b1[tid] = b1[tid];
@@ -779,7 +802,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     uint32_t mh_phase = 0, g_phase = 0;
     bool g_pending = false, g_started = false, mh_pending = false, ok = true;
     const uint32_t id_mh = umma::idesc(umma::kBF16, 128, kP), id_g = umma::idesc(umma::kBF16, 128, 128),
-                   id_dw = umma::idesc(umma::kBF16, 128, NF);
+                   id_dw = umma::idesc(umma::kBF16, 128, NF), id_z = umma::idesc(umma::kTF32, 128, kP);
     float *red = &S.red[0][0][0];  // [4][kP][2]
     // the chunk whose inputs are in flight to buffer buf (cell -1: none)
     int pre_cell = -1, pre_q0 = 0, buf = 0;
@@ -866,32 +889,63 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 put8_split(reinterpret_cast<unsigned char *>(S.FcT[0]), reinterpret_cast<unsigned char *>(S.FcT[1]),
                            umma::kmajor_offset(c, p8, 2 * kP, 2), v);
             }
-            // H = relu(W1 F~ + b1) of (jt, pixel half) in FP32, each element the
-            // fmaf chain from b1 over the channels in order: registers, the Gram
-            // A tile (row jt) and the FP32 transpose buffer Hh
+            // F~ as the TF32 hi / lo B tile of Z (pixel rows, channels along K)
+            if (tid >= 128) {
+                const int p = (tid - 128) & (kP - 1);
+#pragma unroll
+                for (int q = (tid - 128) >> 6; q < NF / 4; q += 2) {
+                    const float4 v = make_float4(S.Fc[buf][4 * q][p], S.Fc[buf][4 * q + 1][p], S.Fc[buf][4 * q + 2][p],
+                                                 S.Fc[buf][4 * q + 3][p]);
+                    put4_tf32(S.FcN[0], S.FcN[1], umma::kmajor_offset(p, 4 * q, 4 * NF, 4), v);
+                }
+            }
+            umma::fence_async_smem();
+            __syncthreads();
+            // Z = W1 F~ on the tensor cores in 3xTF32 (hi hi + hi lo + lo hi, two K
+            // steps of 8, FP32 accumulation in the M H columns, free until M H): its
+            // sign decides ReLU', so the operands keep about 22 bits (a BF16 hi / lo
+            // split, about 16, flipped enough near-zero units to fail the dF~ bar)
+            if (tid == 0) {
+                umma::fence_after();
+                const uint32_t whi = umma::smem_addr(S.W1A[0]), wlo = umma::smem_addr(S.W1A[1]);
+                const uint32_t fhi = umma::smem_addr(S.FcN[0]), flo = umma::smem_addr(S.FcN[1]);
+                for (int ks = 0; ks < NF / 8; ++ks) {
+                    const uint32_t o = 256u * ks;
+                    umma::mma<umma::kTF32>(tmem + cMH, umma::desc(whi + o, 4 * NF), umma::desc(fhi + o, 4 * NF), id_z,
+                                           ks > 0 ? 1u : 0u);
+                    umma::mma<umma::kTF32>(tmem + cMH, umma::desc(whi + o, 4 * NF), umma::desc(flo + o, 4 * NF), id_z,
+                                           1u);
+                    umma::mma<umma::kTF32>(tmem + cMH, umma::desc(wlo + o, 4 * NF), umma::desc(fhi + o, 4 * NF), id_z,
+                                           1u);
+                }
+                umma::commit(&S.mh_bar);
+            }
+            mh_pending = true;
+            {
+                const bool w_ok = umma::mbar_wait(&S.mh_bar, mh_phase, kWait);
+                if (w_ok) {
+                    mh_phase ^= 1u;
+                    mh_pending = false;
+                }
+                if (__syncthreads_or(!w_ok)) {
+                    if (tid == 0) S.abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+            }
+            umma::fence_after();
+            // H = relu(Z + b1) of (jt, pixel half): registers, the Gram A tile
+            // (row jt) and the FP32 transpose buffer Hh
             float hv[32];
             {
                 const float bj = S.b1[jt];
-                f2 z2[16];
+                float t16[16];
+                umma::tmem_ld16(lane_addr + cMH + ph, t16);
 #pragma unroll
-                for (int t = 0; t < 16; ++t) z2[t] = f2_make(bj, bj);
-#pragma unroll 4
-                for (int c = 0; c < NF; ++c) {
-                    const f2 w2v = S.W1d[c][jt];
+                for (int t = 0; t < 16; ++t) hv[t] = fmaxf(t16[t] + bj, 0.f);
+                umma::tmem_ld16(lane_addr + cMH + ph + 16, t16);
 #pragma unroll
-                    for (int t4 = 0; t4 < 8; ++t4) {
-                        const ulonglong2 f = *reinterpret_cast<const ulonglong2 *>(&S.Fc[buf][c][ph + 4 * t4]);
-                        z2[2 * t4] = f2_fma(w2v, f.x, z2[2 * t4]);
-                        z2[2 * t4 + 1] = f2_fma(w2v, f.y, z2[2 * t4 + 1]);
-                    }
-                }
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    float lo, hi;
-                    f2_split(z2[t], lo, hi);
-                    hv[2 * t] = fmaxf(lo, 0.f);
-                    hv[2 * t + 1] = fmaxf(hi, 0.f);
-                }
+                for (int t = 0; t < 16; ++t) hv[16 + t] = fmaxf(t16[t] + bj, 0.f);
             }
             {
                 uint32_t hi[16], lo[16];
