@@ -288,12 +288,12 @@ ups_status ups_tracking_uncertainty(ups_ctx *ctx, const ups_images *img, const u
  * grids concatenated; pixel (x, y) samples it at ((x + 0.5)/patch - 0.5,
  * (y + 0.5)/patch - 0.5), clamped to the grid.  cos = 0 (and no gradient)
  * where either vector is zero.  Computed without forming F^ (the cosine and
- * the gradients from per-patch products of W2); at n_feat = 16 the two
- * 128 x 128 per-pixel products (M H, the Gram of b H) and the dW1 product
- * (dZ F~^T) run on the tensor cores with BF16 hi/lo operand splits and FP32
- * accumulation (about 1e-5 relative per product), everything else in FP32
- * (the first layer Z, whose sign decides ReLU', among it); at n_feat = 32
- * every product is FP32.
+ * the gradients from per-patch products of W2); at n_feat = 16 the per-pixel
+ * products run on the tensor cores with FP32 accumulation: the first layer
+ * Z = W1 F~ (whose sign decides ReLU') in 3xTF32 (operands split in TF32 hi
+ * and lo, FP32-level products), M H, the Gram of b H and dW1 = dZ F~^T in
+ * 3xBF16 (about 1e-5 relative per product); dF~ and the per-pixel terms are
+ * FP32 on the CUDA cores.  At n_feat = 32 every product is FP32.
  *  feat      rendered F~ in the image layout (n_feat planes per view)
  *  dino      the patch grids (16-byte aligned; UPS_ERR_ARG otherwise)
  *  mlp       w1 [128][n_feat], b1 [128], w2 [n_h][128], b2 [n_h] (b2 16-byte aligned)

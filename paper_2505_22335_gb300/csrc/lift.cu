@@ -554,7 +554,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
     float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
     float W1A[2][kLiftHidden * 16];  // W1 as TF32 hi / lo, K-major [128 hidden][16 channels] (A of Z)
     float FcN[2][lt::kP * 16];       // F~ as TF32 hi / lo, K-major [64 pixels][16 channels] (B of Z)
-    f2 W2p[kLiftHidden][16];         // W1 (hidden-major), each weight twice
+    float W1r[kLiftHidden][16];      // W1 (hidden-major rows)
     float b1[kLiftHidden], u[kLiftHidden];
     // a chunk's global inputs, two buffers (chunk parity), filled a chunk ahead
     float E[2][4][kLiftHidden];      // W2^T g of the cell's four corners
@@ -576,7 +576,7 @@ struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read 
 };
 static_assert(offsetof(LiftTcSmem, Hh) == 0 && offsetof(LiftTcSmem, W1A) % 16 == 0 &&
                   offsetof(LiftTcSmem, FcN) % 16 == 0 &&
-                  offsetof(LiftTcSmem, W2p) % 16 == 0 && offsetof(LiftTcSmem, FcT) % 16 == 0 &&
+                  offsetof(LiftTcSmem, W1r) % 16 == 0 && offsetof(LiftTcSmem, FcT) % 16 == 0 &&
                   offsetof(LiftTcSmem, E) % 16 == 0 && offsetof(LiftTcSmem, Fc) % 16 == 0 &&
                   offsetof(LiftTcSmem, dF0) % 16 == 0 &&
                   offsetof(LiftTcSmem, w4) % 16 == 0 && offsetof(LiftTcSmem, ab) % 8 == 0 &&
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kLiftHidden * NF; i += kT) {
         const int j = i / NF, c = i - j * NF;
-        S.W2p[j][c] = f2_make(w1[i], w1[i]);
+        S.W1r[j][c] = w1[i];
     }
     for (int i = tid; i < kLiftHidden * (NF / 4); i += kT) {  // W1 row j, channels 4 q + [0, 4)
         const int j = i / (NF / 4), q = i % (NF / 4);
@@ -850,22 +850,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 lift_chunk_issue(S, buf, vt, patch, cell, q0, feat_all, d_feat_all, weight_all, E, s, gram, tid);
                 cp_async_commit();
             }
-            {
-                int ncell = cell, nq0 = q0 + kP;
-                if (nq0 >= npx) {
-                    ncell = cell + gridDim.x;
-                    nq0 = 0;
-                }
-                pre_cell = -1;
-                if (ncell < n_cells) {
-                    lift_chunk_issue(S, buf ^ 1, vt, patch, ncell, nq0, feat_all, d_feat_all, weight_all, E, s, gram,
-                                     tid);
-                    pre_cell = ncell;
-                    pre_q0 = nq0;
-                }
-                cp_async_commit();
-            }
-            cp_async_wait<1>();
+            cp_async_wait<0>();
             // the previous chunk's Gram MMAs still read the H and b H tiles
             if (g_pending) {
                 const bool w_ok = umma::mbar_wait(&S.g_bar, g_phase, kWait);
@@ -879,16 +864,6 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 break;
             }
             umma::fence_after();
-            // F~ as the BF16 hi / lo B tile of dW1 (channel rows, pixels along K);
-            // the previous chunk's dW1 MMAs, which read it, completed with the Gram's
-            if (d_w1 && tid < 128) {
-                const int c = tid >> 3, p8 = 8 * (tid & 7);
-                const float4 f0 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8]);
-                const float4 f1 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8 + 4]);
-                const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-                put8_split(reinterpret_cast<unsigned char *>(S.FcT[0]), reinterpret_cast<unsigned char *>(S.FcT[1]),
-                           umma::kmajor_offset(c, p8, 2 * kP, 2), v);
-            }
             // F~ as the TF32 hi / lo B tile of Z (pixel rows, channels along K)
             if (tid >= 128) {
                 const int p = (tid - 128) & (kP - 1);
@@ -921,6 +896,34 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 umma::commit(&S.mh_bar);
             }
             mh_pending = true;
+            // while the Z MMAs run: the next chunk's global inputs to the other
+            // buffer (its last reader, the previous chunk, every thread has
+            // passed) and F~ as the dW1 B tile
+            {
+                int ncell = cell, nq0 = q0 + kP;
+                if (nq0 >= npx) {
+                    ncell = cell + gridDim.x;
+                    nq0 = 0;
+                }
+                pre_cell = -1;
+                if (ncell < n_cells) {
+                    lift_chunk_issue(S, buf ^ 1, vt, patch, ncell, nq0, feat_all, d_feat_all, weight_all, E, s, gram,
+                                     tid);
+                    pre_cell = ncell;
+                    pre_q0 = nq0;
+                }
+                cp_async_commit();
+            }
+            // F~ as the BF16 hi / lo B tile of dW1 (channel rows, pixels along K);
+            // the previous chunk's dW1 MMAs, which read it, completed with the Gram's
+            if (d_w1 && tid < 128) {
+                const int c = tid >> 3, p8 = 8 * (tid & 7);
+                const float4 f0 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8]);
+                const float4 f1 = *reinterpret_cast<const float4 *>(&S.Fc[buf][c][p8 + 4]);
+                const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                put8_split(reinterpret_cast<unsigned char *>(S.FcT[0]), reinterpret_cast<unsigned char *>(S.FcT[1]),
+                           umma::kmajor_offset(c, p8, 2 * kP, 2), v);
+            }
             {
                 const bool w_ok = umma::mbar_wait(&S.mh_bar, mh_phase, kWait);
                 if (w_ok) {
@@ -1140,28 +1143,43 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             g_started = true;
             g_pending = true;
             if (d_feat) {
-                // dF~ = W1^T dZ: warp w sums hidden units [16 w, 16 w + 16) for all
-                // channels, lane l its pixels (2 l, 2 l + 1) as a packed pair; W1 comes
-                // in warp-uniform loads, and the eight warps' partial sums meet in the
-                // M H operand tile, free until the next chunk
-                f2 acc[NF];
+                // dF~ = W1^T dZ: each warp sums a range of hidden units for all
+                // channels of lane l's pixels 2 l and 2 l + 1, channel pairs packed
+                // (the warp that issued the Gram and dW1 MMAs takes 2 units, the
+                // other seven 18); W1 rows come in warp-uniform loads, and the eight
+                // warps' partial sums meet in the M H operand tile, free until the
+                // next chunk
+                constexpr int kIssueWarp = kGramTid / 32, kShort = 2, kLong = (kLiftHidden - kShort) / 7;
+                static_assert(7 * kLong + kShort == kLiftHidden, "hidden units over the dF~ warps");
+                const int j0 = warp < kIssueWarp ? kLong * warp : warp == kIssueWarp ? kLong * warp
+                                                                                     : kLong * (warp - 1) + kShort;
+                const int nj = warp == kIssueWarp ? kShort : kLong;
+                f2 acc[NF / 2][2];  // [channel pair][pixel]
 #pragma unroll
-                for (int c = 0; c < NF; ++c) acc[c] = 0ull;
-#pragma unroll 4
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = 16 * warp + jj;
-                    const f2 dz = *reinterpret_cast<const f2 *>(&S.Hh[j][2 * lane]);
+                for (int k = 0; k < NF / 2; ++k) acc[k][0] = acc[k][1] = 0ull;
+#pragma unroll 2
+                for (int jj = 0; jj < nj; ++jj) {
+                    const int j = j0 + jj;
+                    const float2 dz = *reinterpret_cast<const float2 *>(&S.Hh[j][2 * lane]);
+                    const f2 d0 = f2_make(dz.x, dz.x), d1 = f2_make(dz.y, dz.y);
 #pragma unroll
-                    for (int k = 0; k < NF / 2; ++k) {
-                        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W2p[j][2 * k]);
-                        acc[2 * k] = f2_fma(w.x, dz, acc[2 * k]);
-                        acc[2 * k + 1] = f2_fma(w.y, dz, acc[2 * k + 1]);
+                    for (int k4 = 0; k4 < NF / 4; ++k4) {
+                        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(&S.W1r[j][4 * k4]);
+                        acc[2 * k4][0] = f2_fma(w.x, d0, acc[2 * k4][0]);
+                        acc[2 * k4][1] = f2_fma(w.x, d1, acc[2 * k4][1]);
+                        acc[2 * k4 + 1][0] = f2_fma(w.y, d0, acc[2 * k4 + 1][0]);
+                        acc[2 * k4 + 1][1] = f2_fma(w.y, d1, acc[2 * k4 + 1][1]);
                     }
                 }
                 float *part = reinterpret_cast<float *>(op + oHBhi);  // [8 warps][NF][kP]
 #pragma unroll
-                for (int c = 0; c < NF; ++c)
-                    *reinterpret_cast<f2 *>(&part[(warp * NF + c) * kP + 2 * lane]) = acc[c];
+                for (int k = 0; k < NF / 2; ++k) {
+                    float a0, b0, a1, b1;  // (channel 2 k, 2 k + 1) at pixels 2 l and 2 l + 1
+                    f2_split(acc[k][0], a0, b0);
+                    f2_split(acc[k][1], a1, b1);
+                    *reinterpret_cast<float2 *>(&part[(warp * NF + 2 * k) * kP + 2 * lane]) = make_float2(a0, a1);
+                    *reinterpret_cast<float2 *>(&part[(warp * NF + 2 * k + 1) * kP + 2 * lane]) = make_float2(b0, b1);
+                }
                 __syncthreads();
                 // thread t: channel t / 16, pixels 4 (t % 16) + [0, 4)
                 const int c = tid >> 4, p0 = 4 * (tid & 15);

@@ -2,13 +2,13 @@
 FP64 oracle, both fed the same seeded synthetic feature maps, DINO patch grids
 and MLP weights (a forward on the same cameras only sets up the views).
 
-The products run in FP32 (fmaf on the CUDA cores), except at N_l = 16 the two
-128 x 128 per-pixel ones (M H and the Gram of b H) and dW1 = dZ F~^T, which run
-on the tensor cores with BF16 operands split in hi and lo (about 1e-5 relative
-per product) and FP32 accumulation; the loss and every gradient group are held to the
-path's gradient bar, 2e-3 relative L2 (1e-5 + 1e-4 relative for the loss).
-Measured (printed): loss <= 2.4e-7, dW2/db2 <= 5.2e-7, db1 <= 8.7e-6,
-dW1 <= 3.4e-5, dF~ <= 1.5e-4 (the last sums 128 mixed-sign terms per pixel)."""
+At N_l = 32 the products run in FP32 (fmaf on the CUDA cores).  At N_l = 16 the
+per-pixel ones run on the tensor cores with FP32 accumulation: Z = W1 F~, whose
+sign decides ReLU', in 3xTF32 (TF32 hi/lo operands), M H, the Gram of b H and
+dW1 = dZ F~^T in 3xBF16 (about 1e-5 relative per product); dF~ stays FP32.  The
+loss and every gradient group are held to the path's gradient bar, 2e-3
+relative L2 (1e-4 relative for the loss).  Measured (printed): loss <= 2.1e-7,
+dW2/db2 <= 6.2e-7, db1 <= 7.1e-7, dW1 <= 6.4e-6, dF~ <= 2.7e-6."""
 import numpy as np
 import pytest
 
