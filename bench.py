@@ -238,8 +238,8 @@ ALU_STAGES = {"decode_fwd", "decode_bwd_rows", "composite_fwd", "composite_bwd"}
 MEASURED_TRAFFIC = {
     # full ncu captures of one launch on the 2-view profiling workload (1M Gaussians, 2 x 640x480), scaled to the
     # 8-view launch by the list entries the tiles read (384,532 -> 1,618,003; images scale alike, 4x the pixels)
-    ("composite_bwd", DEFAULT_WORKLOAD): (303.8e6, "2026-12-04 (2-view capture x 4.21)", "b26ed4d0cd026bfb"),
-    ("composite_fwd", DEFAULT_WORKLOAD): (107.6e6, "2026-12-04 (2-view capture x 4.21)", "b26ed4d0cd026bfb"),
+    ("composite_bwd", DEFAULT_WORKLOAD): (301.7e6, "2026-12-04 (2-view capture x 4.21)", "cb96ae212ea91e15"),
+    ("composite_fwd", DEFAULT_WORKLOAD): (107.4e6, "2026-12-04 (2-view capture x 4.21)", "cb96ae212ea91e15"),
     # full ncu capture of one 200,000-row launch on the 2-view profiling workload; the 8-view step's 4 launches
     # average the same 200,000 rows, and the traffic is per row (dL/dG read, scratch written)
     ("decode_bwd_rows", DEFAULT_WORKLOAD): (786.9e6, "2026-12-04 (2-view capture, 200k rows = the average launch)",
