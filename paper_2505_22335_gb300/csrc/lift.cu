@@ -547,11 +547,28 @@ constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gr
 constexpr int kOpBytes = 65536;
 constexpr int kWait = 1 << 22;
 constexpr int kGramTid = 128;  // issues the Gram and dW1 MMAs
+// M H's B operand H (K = 128 hidden units x N = 64 pixels) in the MN-major layout
+// without swizzle: core matrices of 8 hidden rows x 8 pixels (16 bytes per row, 128
+// bytes each), 8 along N then 16 along K, so that a thread writes its hidden unit's
+// pixels from registers; the descriptor takes LBO = 1024 (the stride between core
+// matrices along K) and SBO = 128 (along N), a K step of 16 hidden units advances the
+// start by 2048 bytes, and the instruction descriptor's B-major bit selects MN-major.
+__device__ __forceinline__ uint32_t hb_mn_offset(int j, int p) {
+    return (uint32_t)((j >> 3) * 1024 + (p >> 3) * 128 + (j & 7) * 16 + (p & 7) * 2);
+}
+__device__ __forceinline__ uint64_t desc_strides(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    return d;
+}
 }  // namespace lt
 
 struct LiftTcSmem {  // after the operand tiles (1 KB aligned); the arrays read as
                      // 16-byte vectors come first, at 16-byte multiples
-    float Hh[kLiftHidden][lt::kHS];  // H, then dZ (hidden-major)
+    float Hh[kLiftHidden][lt::kHS];  // dZ (hidden-major), for dF~
     float W1A[2][kLiftHidden * 16];  // W1 as TF32 hi / lo, K-major [128 hidden][16 channels] (A of Z)
     float FcN[2][lt::kP * 16];       // F~ as TF32 hi / lo, K-major [64 pixels][16 channels] (B of Z)
     float W1r[kLiftHidden][16];      // W1 (hidden-major rows)
@@ -938,7 +955,7 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
             }
             umma::fence_after();
             // H = relu(Z + b1) of (jt, pixel half): registers, the Gram A tile
-            // (row jt) and the FP32 transpose buffer Hh
+            // (row jt) and M H's B tile
             float hv[32];
             {
                 const float bj = S.b1[jt];
@@ -958,20 +975,12 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 umma::tmem_st16(lane_addr + cHAlo + ph / 2, lo);
                 umma::tmem_st_wait();
             }
+            // H as M H's B tile, pixel rows of 8 straight from the registers
 #pragma unroll
-            for (int t4 = 0; t4 < 8; ++t4)
-                *reinterpret_cast<float4 *>(&S.Hh[jt][ph + 4 * t4]) =
-                    make_float4(hv[4 * t4], hv[4 * t4 + 1], hv[4 * t4 + 2], hv[4 * t4 + 3]);
-            __syncthreads();
-            // the M H B tile (pixel rows, 8 hidden units per core-matrix row)
-            // from the transpose buffer: thread = (pixel, 8 hidden units)
-#pragma unroll
-            for (int r = 0; r < kP * (kLiftHidden / 8) / kT; ++r) {
-                const int i = tid + kT * r, p = i & (kP - 1), j8 = i / kP;
-                float v[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) v[jj] = S.Hh[8 * j8 + jj][p];
-                put8_split(op + oHBhi, op + oHBlo, umma::kmajor_offset(p, 8 * j8, 2 * kLiftHidden, 2), v);
+            for (int q = 0; q < 4; ++q) {
+                const float v[8] = {hv[8 * q],     hv[8 * q + 1], hv[8 * q + 2], hv[8 * q + 3],
+                                    hv[8 * q + 4], hv[8 * q + 5], hv[8 * q + 6], hv[8 * q + 7]};
+                put8_split(op + oHBhi, op + oHBlo, hb_mn_offset(jt, ph + 8 * q), v);
             }
             umma::fence_before();
             umma::fence_async_smem();
@@ -982,8 +991,8 @@ __global__ void __launch_bounds__(lt::kT, 1) k_lift_tc(
                 for (int pass = 0; pass < 3; ++pass) {
                     const uint32_t a = tmem + (pass == 2 ? cMlo : cMhi), b = sop + (pass == 1 ? oHBlo : oHBhi);
                     for (int ks = 0; ks < kLiftHidden / 16; ++ks)
-                        umma::mma_f16_ts(tmem + cMH, a + 8u * ks, umma::desc(b + 256u * ks, 2 * kLiftHidden), id_mh,
-                                         (pass > 0 || ks > 0) ? 1u : 0u);
+                        umma::mma_f16_ts(tmem + cMH, a + 8u * ks, desc_strides(b + 2048u * ks, 1024, 128),
+                                         id_mh | (1u << 16), (pass > 0 || ks > 0) ? 1u : 0u);
                 }
                 umma::commit(&S.mh_bar);
             }
