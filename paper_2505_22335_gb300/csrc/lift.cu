@@ -21,11 +21,12 @@
 // ~310 k, and no N_h-wide per-pixel array.
 //
 // Every pixel-sized product (F~ W1^T, M H, the Gram of b H over pixels and
-// the two backward products with W1) runs inside one fused FP32 kernel
-// (k_lift_fused) over the cells of pixels that share their four patches: the
-// 128-wide per-pixel quantities stay in shared memory, and the kernel also
-// does the cosine, the loss, dL/dZ and the per-patch sums.  The per-patch and
-// weight-sized products are FP32 GEMMs (gemm.cu).
+// the two backward products with W1) runs inside one fused kernel over the
+// cells of pixels that share their four patches: the 128-wide per-pixel
+// quantities stay on chip, and the kernel also does the cosine, the loss,
+// dL/dZ and the per-patch sums.  At N_l = 16 that is k_lift_tc (the products
+// but dF~ on the tensor cores, below), at N_l = 32 the all-FP32 k_lift_fused.
+// The per-patch and weight-sized products are FP32 GEMMs (gemm.cu).
 #include <cstddef>
 
 #include "common.cuh"
@@ -513,25 +514,28 @@ __global__ void __launch_bounds__(kFT, 1) k_lift_fused(
 }
 
 // ---------------------------------------------------------------------------
-// fused per-cell kernel with the two 128 x 128 products on the tensor cores
+// fused per-cell kernel with the per-pixel products on the tensor cores
 // ---------------------------------------------------------------------------
 //
-// The walk of k_lift_fused (N_l = 16), with M H and the Gram of b H as tcgen05
-// MMAs whose BF16 operands are split in two (x = hi + lo, hi = bf16(x),
-// lo = bf16(x - hi)): hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM
-// (about 1e-5 relative per product); everything else, Z = W1 F~ + b1 among it
-// (its sign decides ReLU'), FP32 on the CUDA cores.
-//   TMEM columns [0, 64): M H of the chunk (lane = hidden unit, column = pixel)
-//   TMEM columns [128, 256): the Gram, accumulated over all of the CTA's chunks
-//   TMEM columns [256, 384): M hi, lo; [384, 448): H of the chunk hi, lo (A operands)
-// Thread 0 issues the MMAs; `mh_bar` completes when a chunk's M H is in TMEM,
-// `g_bar` when the chunk's Gram MMAs are done with their operands.  A warp
-// reads TMEM lanes 32 (w % 4) .. + 31, so thread (warp w, lane i) owns hidden
-// unit j = 32 (w % 4) + i and the chunk's pixels 32 (w / 4) .. + 31 from Z on,
-// keeping H of them in registers; per-pixel sums over hidden units are
+// The walk of k_lift_fused (N_l = 16) in chunks of 64 pixels, with every
+// per-pixel product but dF~ as tcgen05 MMAs accumulating in FP32 in TMEM:
+// Z = W1 F~ in 3xTF32 (x = hi + lo, hi = tf32(x), lo = tf32(x - hi); its sign
+// decides ReLU', which a BF16 split flips too often), M H, the Gram of b H and
+// dW1 = dZ F~^T in 3xBF16 (hi = bf16(x), lo = bf16(x - hi); about 1e-5
+// relative per product), each as hi*hi + hi*lo + lo*hi.  dF~ = W1^T dZ and the
+// per-pixel terms run in FP32 on the CUDA cores.
+//   TMEM columns [0, 64): Z, then M H of the chunk (lane = hidden unit, column = pixel)
+//   TMEM columns [64, 80): dW1, accumulated over all of the CTA's chunks
+//   TMEM columns [128, 256): the Gram, likewise
+//   TMEM columns [256, 384): M hi, lo; [384, 448): H hi, lo; [448, 512): dZ hi, lo (A operands)
+// Thread 0 issues the Z and M H MMAs (`mh_bar` completes each), thread kGramTid
+// the Gram and dW1 MMAs (`g_bar` completes them, waited at the next chunk).  A
+// warp reads TMEM lanes 32 (w % 4) .. + 31, so thread (warp w, lane i) owns
+// hidden unit j = 32 (w % 4) + i and the chunk's pixels 32 (w / 4) .. + 31 from
+// Z on, keeping H of them in registers; per-pixel sums over hidden units are
 // reduce-scattered over the warp's lanes and added over the four warps of a
-// pixel half.  H reaches the M H operand (pixel rows) through an FP32
-// transpose in shared memory.
+// pixel half.  H reaches M H's B operand in the MN-major layout straight from
+// the registers; a chunk's global inputs arrive by cp.async a chunk ahead.
 namespace lt {
 constexpr int kP = 64;       // pixels per chunk
 constexpr int kT = 256;      // threads
@@ -541,8 +545,9 @@ constexpr int kHS = kP + 4;  // row stride of the FP32 hidden-major arrays
 constexpr uint32_t kTmemCols = 512, cMH = 0, cG = 128, cMhi = 256, cMlo = 320, cHAhi = 384, cHAlo = 416;
 // dW1 accumulator (16 columns) and dZ as its A operand (BF16 hi / lo pairs)
 constexpr uint32_t cDW = 64, cDZhi = 448, cDZlo = 480;
-// BF16 B operand tiles in shared memory, canonical K-major without swizzle (byte offsets)
-constexpr int oHBhi = 0, oHBlo = 16384;        // H [64 p][128 k] (B of M H)
+// BF16 B operand tiles in shared memory (byte offsets): H of M H (MN-major), b H of
+// the Gram (K-major, no swizzle)
+constexpr int oHBhi = 0, oHBlo = 16384;        // H [128 k][64 p] (B of M H)
 constexpr int oBHhi = 32768, oBHlo = 49152;    // b H [128 i][64 p] (B of the Gram)
 constexpr int kOpBytes = 65536;
 constexpr int kWait = 1 << 22;
