@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
     const float *__restrict__ w2, const float *__restrict__ b2, const float *__restrict__ R, float lambda, float g,
     float *__restrict__ loss, float *__restrict__ sigma_out, uint8_t *__restrict__ motion_out,
     float *__restrict__ d_b1, float *__restrict__ d_w2, float *__restrict__ d_b2, float *__restrict__ D) {
-    __shared__ float zc[4][kUH];          // the four corner patches' W1 g
+    __shared__ __align__(16) float zc[4][kUH];  // the four corner patches' W1 g
     __shared__ float red[kUWarps][6][kUH];  // per-warp sums: d_w2, d_b1, D[4]
     __shared__ float sred[kUWarps][2];      // loss, d_b2
     const int ci = blockIdx.x, cj = blockIdx.y;
@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
     float a_D[4][4] = {};
     float a_loss = 0.f, a_db2 = 0.f;
     const float inv2p = 1.f / (float)(2 * patch);
+    // the warp's pixels q = w, w + kUWarps, ... in row-major order over the cell,
+    // their coordinates stepped from the first
+    int y = ys + (nx > 0 ? w / nx : 0), x = xs + (nx > 0 ? w % nx : 0);
     for (int q = w; q < npx; q += kUWarps) {
-        const int y = ys + q / nx, x = xs + q % nx;
         // bilinear weight u - x0 = ((2x + 1) - (2 x0 + 1) patch) / (2 patch): an exact
         // integer numerator, one rounding (u itself is ~45 at 640 px, where a float
         // ulp would already move the weight by 4e-6); clamped positions give 0
@@ -82,10 +84,15 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
         const float ay = fminf(fmaxf((float)(2 * y + 1 - (2 * y0 + 1) * patch) * inv2p, 0.f), 1.f);
         const float a[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
         float z[4], h[4], part = 0.f;
+        const float4 z0 = *reinterpret_cast<const float4 *>(&zc[0][4 * lane]);
+        const float4 z1 = *reinterpret_cast<const float4 *>(&zc[1][4 * lane]);
+        const float4 z2v = *reinterpret_cast<const float4 *>(&zc[2][4 * lane]);
+        const float4 z3 = *reinterpret_cast<const float4 *>(&zc[3][4 * lane]);
+        const float c0[4] = {z0.x, z0.y, z0.z, z0.w}, c1[4] = {z1.x, z1.y, z1.z, z1.w};
+        const float c2[4] = {z2v.x, z2v.y, z2v.z, z2v.w}, c3[4] = {z3.x, z3.y, z3.z, z3.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int j = 4 * lane + k;
-            z[k] = bb1[k] + a[0] * zc[0][j] + a[1] * zc[1][j] + a[2] * zc[2][j] + a[3] * zc[3][j];
+            z[k] = bb1[k] + a[0] * c0[k] + a[1] * c1[k] + a[2] * c2[k] + a[3] * c3[k];
             h[k] = fmaxf(z[k], 0.f);
             part = fmaf(ww2[k], h[k], part);
         }
@@ -95,8 +102,9 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
         const float s = softplus_f(z2);
         const size_t p = (size_t)y * W + x;
         const float r = R[p];
-        // L_u = R / (2 s^2) + lambda log s;  dL_u/ds = -R / s^3 + lambda / s
-        const float ds = g * (-r / (s * s * s) + lambda / s);
+        // L_u = R / (2 s^2) + lambda log s;  dL_u/ds = -R / s^3 + lambda / s = (lambda - R / s^2) / s
+        const float is = 1.f / s;
+        const float ds = g * is * (lambda - r * is * is);
         const float dz2 = ds * sigmoid_f(z2);
         if (lane == 0) {
             a_loss += r / (2.f * s * s) + lambda * logf(s);
@@ -111,6 +119,11 @@ __global__ void __launch_bounds__(32 * kUWarps) k_unc_cells(
             a_db1[k] += dh;
 #pragma unroll
             for (int c = 0; c < 4; ++c) a_D[c][k] = fmaf(a[c], dh, a_D[c][k]);
+        }
+        x += kUWarps;
+        while (x >= xe) {
+            x -= nx;
+            ++y;
         }
     }
     // reduce over the CTA's warps, then one atomic per value
